@@ -1,0 +1,179 @@
+/*
+ * gbk.h -- C ABI of the GB300 Galactic-Binary likelihood library (libgbk.so).
+ *
+ * The library computes the hot path of the GPU global fit of arXiv:2405.04690 for
+ * Galactic binaries (GBs): the TDI A/E frequency-domain waveform of each source over its
+ * local band by the fast/slow decomposition (Sec. II.A, App. F), the noise-weighted
+ * inner products against a residual and PSD (Eq. inner), the change in log-likelihood
+ * for in-model, birth/death and swap moves (Eq. addsource, Eq. swapsource), the
+ * residual update when templates enter or leave the model (Alg. 1, Alg. 2), the
+ * parametric noise PSD (Eq. psd) and the full log-likelihood (Eq. like).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every pointer argument whose name is not `ctx`, `out_ctx` or a host struct is a
+ *   DEVICE pointer owned by the caller. The library reads or writes it only during the
+ *   stream-ordered execution of the call and never frees or keeps it.
+ * - Host structs (gbk_grid, gbk_residual, gbk_psd) are read during the call only.
+ * - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy default
+ *   stream) and returns a gbk_status for argument and launch errors, with a message in
+ *   gbk_last_error(). Errors found by a kernel (a band outside the residual window, an
+ *   unsupported band length, a walker index out of range) set a device error word that
+ *   gbk_sync_status() reads after synchronising the stream; the offending item is
+ *   skipped, nothing out of bounds is touched.
+ * - Source parameters are SoA float64 [8][n] in the order
+ *   A (strain amplitude, >= 0; 0 gives an identically zero template), f0 [Hz],
+ *   fdot [Hz/s], phi0 [rad], psi [rad], cos(iota), sin(beta) (ecliptic latitude),
+ *   lambda [rad] (ecliptic longitude).
+ * - Band lengths N are 128, 256, 512 or 1024 bins; the band of a source covers absolute
+ *   frequency bins [q - N/2, q + N/2) with q = floor(f0 * Tobs) (bin k is f = k / Tobs).
+ * - Frequency-domain values are complex, stored as interleaved (re, im) pairs, in the
+ *   physical normalisation x~(f_k) = dt * sum_n x(t_n) exp(-2 pi i k n / N_t).
+ * - A and E share one PSD per walker, given by its two amplitudes
+ *   (sqrt(S_oms) [m/sqrt(Hz)], sqrt(S_acc) [m s^-2/sqrt(Hz)]) through Eq. psd.
+ */
+#ifndef GBK_H
+#define GBK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gbk_status {
+  GBK_OK = 0,
+  GBK_EINVAL = 1,    /* bad argument (null pointer, size, enum value) */
+  GBK_ERANGE = 2,    /* a band fell outside the residual window, or an index out of range */
+  GBK_ENOMEM = 3,    /* device allocation failed (only gbk_create allocates) */
+  GBK_ECUDA = 4,     /* a CUDA runtime call or kernel launch failed */
+  GBK_ETIMEOUT = 5,  /* a device-side wait gave up after its iteration limit */
+  GBK_ENOTIMPL = 6   /* combination not implemented */
+} gbk_status;
+
+/* Arithmetic of the waveform and inner-product steps.
+ * GBK_FP64: everything in float64 (the plain method).
+ * GBK_MIXED: float64 only for the carrier-bin offset delta = f0 T - q, fdot T^2 and the
+ *            final per-result sums; slow-part response, band FFT and per-bin products in
+ *            float32 with compensated float32 accumulation. */
+typedef enum gbk_precision { GBK_FP64 = 0, GBK_MIXED = 1 } gbk_precision;
+
+/* Observation grid and residual window. */
+typedef struct gbk_grid {
+  double tobs;     /* observation time T [s]; df = 1 / T (Eq. inner's Delta f) */
+  double dt;       /* sampling cadence [s]; T / dt must be a multiple of 1024 */
+  int64_t k0;      /* first absolute frequency bin of the residual window, >= 1 */
+  int64_t n_bins;  /* bins in the window, >= 1 */
+} gbk_grid;
+
+/* Residual d - H of every walker as int64 fixed point: value = integer * 2^-frac_bits.
+ * Layout [n_walkers][2 channels (A, E)][n_bins][2 (re, im)], row-major, on the device.
+ * Fixed point makes adding and then removing a template restore the residual bit for
+ * bit (each template value is rounded to the grid, half to even, before the add). */
+typedef struct gbk_residual {
+  int64_t* data;
+  int32_t n_walkers;
+  int32_t frac_bits;  /* 40 .. 120 */
+} gbk_residual;
+
+/* Per-walker parametric PSD: params[n_psd][2] = (sqrt(S_oms), sqrt(S_acc)), float64,
+ * device. n_psd == 1 shares one PSD by all walkers; otherwise n_psd must cover every
+ * walker index used. */
+typedef struct gbk_psd {
+  const double* params;
+  int32_t n_psd;
+} gbk_psd;
+
+typedef struct gbk_ctx gbk_ctx;
+
+/* Create a context on the current CUDA device: orbit tables for every band length,
+ * FFT twiddles, PSD shape tables over the window and scratch. Allocates device memory
+ * (the only call that does). Returns GBK_ENOMEM / GBK_ECUDA on failure. */
+gbk_status gbk_create(gbk_ctx** out_ctx, const gbk_grid* grid);
+
+/* Free everything the context owns. Synchronises the device first. */
+gbk_status gbk_destroy(gbk_ctx* ctx);
+
+/* Message describing the last error returned on the calling host thread ("" if none). */
+const char* gbk_last_error(void);
+
+/* Synchronise `stream`, then read and clear the context's device error word.
+ * GBK_OK if no kernel reported an error since the last call. */
+gbk_status gbk_sync_status(gbk_ctx* ctx, void* stream);
+
+/* Library ABI version (major * 100 + minor). */
+int gbk_version(void);
+
+/*
+ * gb_waveform_batch -- TDI A and E band of n sources (Sec. II.A, App. F).
+ * Fast/slow decomposition: slow-part response on N coarse samples t_p = p T / N, band
+ * FFT, heterodyne of offset m in [-N/2, N/2) to bin q + m; scaled by T / (2 N) so the
+ * result is the positive-frequency DFT of the real TDI signal.
+ *   params    [8][n] float64
+ *   n_band    [n] int32, each in {128, 256, 512, 1024}, <= n_band_max
+ *   k_start   [n] int64, out: q - N/2 (first bin of each band)
+ *   h_a, h_e  out: complex bands, source i at complex element offset out_off[i];
+ *             float32 pairs for GBK_MIXED, float64 pairs for GBK_FP64
+ *   out_off   [n] int64
+ */
+gbk_status gb_waveform_batch(gbk_ctx* ctx, const double* params, const int32_t* n_band,
+                             int32_t n_band_max, int64_t n, int64_t* k_start, void* h_a,
+                             void* h_e, const int64_t* out_off, gbk_precision precision,
+                             void* stream);
+
+/*
+ * gb_delta_loglike_batch -- Delta ln L of n independent proposals (Eq. swapsource).
+ * Proposal i swaps template r = h(params_old[:, i]) for a = h(params_new[:, i]) in
+ * walker walker[i]'s model, whose current residual d - H (H including r) is R:
+ *   Delta ln L = -1/2 [<a|a> + <r|r> - 2<a|r> - 2<d-H|a> + 2<d-H|r>]
+ * evaluated in the equivalent form -1/2 <a-r|a-r> + <d-H|a-r> over the union of the two
+ * bands. Amplitude 0 in params_old gives a birth (Eq. addsource), 0 in params_new a
+ * death. Both bands must lie inside the window (else GBK_ERANGE via gbk_sync_status and
+ * dlogl[i] = NaN).
+ *   params_new, params_old [8][n] float64;  n_band [n] int32 (both templates use it)
+ *   walker [n] int32;  dlogl [n] float64 out
+ */
+gbk_status gb_delta_loglike_batch(gbk_ctx* ctx, const double* params_new,
+                                  const double* params_old, const int32_t* n_band,
+                                  int32_t n_band_max, const int32_t* walker, int64_t n,
+                                  const gbk_residual* residual, const gbk_psd* psd,
+                                  double* dlogl, gbk_precision precision, void* stream);
+
+/*
+ * residual_add_sub -- move n templates into or out of the model (Alg. 1 write-back).
+ * sign = +1: the templates enter the model, R <- R - h; sign = -1: they leave, R <- R + h.
+ * Each template value is rounded to the fixed-point grid before the integer update, so
+ * residual_add_sub(+1) followed by residual_add_sub(-1) with the same arguments restores
+ * R bit for bit, in any order and with any overlap (int64 atomics).
+ *   params [8][n] float64; n_band [n] int32; walker [n] int32
+ */
+gbk_status residual_add_sub(gbk_ctx* ctx, const gbk_residual* residual, const double* params,
+                            const int32_t* n_band, int32_t n_band_max, const int32_t* walker,
+                            int64_t n, int32_t sign, gbk_precision precision, void* stream);
+
+/*
+ * psd_eval -- Eq. psd on the context window for W walkers.
+ *   psd_params [W][2] float64 (sqrt(S_oms), sqrt(S_acc))
+ *   s_out      [W][n_bins] float64 out, or NULL (then nothing is written)
+ * S_n(x) = 8 sin^2 x [2 S_pm (3 + 2 cos x + cos 2x) + S_op (2 + cos x)], x = 2 pi f L / c.
+ */
+gbk_status psd_eval(gbk_ctx* ctx, const double* psd_params, int32_t n_walkers, double* s_out,
+                    void* stream);
+
+/*
+ * total_loglike -- Eq. like over the window for W walkers, both channels:
+ *   ln L_w = -1/2 <R_w|R_w> - sum_{A,E} sum_k ln S_w(f_k)
+ *   residual   [W][2][n_bins][2] float32 (physical units)
+ *   psd_params [W][2] float64;  logl [W] float64 out
+ * Per-bin terms in float32, per-block sums compensated, cross-block sums in float64 in a
+ * fixed order (deterministic). Uses context scratch: concurrent calls on one context
+ * must be ordered on one stream.
+ */
+gbk_status total_loglike(gbk_ctx* ctx, const float* residual, const double* psd_params,
+                         int32_t n_walkers, double* logl, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBK_H */

@@ -1,0 +1,184 @@
+"""ctypes binding of libgbk.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and passes device
+pointers of torch tensors straight through; all arithmetic runs in the library's
+kernels. A missing library or a non-CUDA tensor raises immediately: there is no CPU
+fallback.
+"""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgbk.so")
+
+GBK_FP64 = 0
+GBK_MIXED = 1
+PRECISION = {"fp64": GBK_FP64, "mixed": GBK_MIXED}
+
+STATUS = {0: "GBK_OK", 1: "GBK_EINVAL", 2: "GBK_ERANGE", 3: "GBK_ENOMEM", 4: "GBK_ECUDA",
+          5: "GBK_ETIMEOUT", 6: "GBK_ENOTIMPL"}
+
+# Every symbol the C header declares, with (restype, argtypes).
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+
+
+class GbkGrid(ctypes.Structure):
+    _fields_ = [("tobs", ctypes.c_double), ("dt", ctypes.c_double), ("k0", ctypes.c_int64), ("n_bins", ctypes.c_int64)]
+
+
+class GbkResidual(ctypes.Structure):
+    _fields_ = [("data", _vp), ("n_walkers", _i32), ("frac_bits", _i32)]
+
+
+class GbkPsd(ctypes.Structure):
+    _fields_ = [("params", _vp), ("n_psd", _i32)]
+
+
+SIGNATURES = {
+    "gbk_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(GbkGrid)]),
+    "gbk_destroy": (ctypes.c_int, [_vp]),
+    "gbk_last_error": (ctypes.c_char_p, []),
+    "gbk_sync_status": (ctypes.c_int, [_vp, _vp]),
+    "gbk_version": (ctypes.c_int, []),
+    "gb_waveform_batch": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i64, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
+    "gb_delta_loglike_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _vp, _i64, ctypes.POINTER(GbkResidual),
+                                              ctypes.POINTER(GbkPsd), _vp, ctypes.c_int, _vp]),
+    "residual_add_sub": (ctypes.c_int, [_vp, ctypes.POINTER(GbkResidual), _vp, _vp, _i32, _vp, _i64, _i32,
+                                        ctypes.c_int, _vp]),
+    "psd_eval": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
+    "total_loglike": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp]),
+}
+
+_LIB = None
+
+
+class GbkError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = lib().gbk_last_error().decode(errors="replace")
+        super().__init__("%s: %s (%s)" % (where, STATUS.get(status, status), msg))
+
+
+def lib():
+    """Load libgbk.so (once); raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libgbk.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        h = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(h, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = h
+    return _LIB
+
+
+def _check(status, where):
+    if status != 0:
+        raise GbkError(status, where)
+
+
+def _dev(t, dtype, name, writable=False):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """Owns a gbk_ctx (orbit/twiddle/PSD tables and scratch on the current device)."""
+
+    def __init__(self, tobs, dt, k0, n_bins):
+        self.grid = GbkGrid(float(tobs), float(dt), int(k0), int(n_bins))
+        h = _vp()
+        _check(lib().gbk_create(ctypes.byref(h), ctypes.byref(self.grid)), "gbk_create")
+        self.handle = h
+
+    @property
+    def k0(self):
+        return self.grid.k0
+
+    @property
+    def n_bins(self):
+        return self.grid.n_bins
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().gbk_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gbk_sync_status(ctx, stream=None):
+    _check(lib().gbk_sync_status(ctx.handle, _stream(stream)), "gbk_sync_status")
+
+
+def gb_waveform_batch(ctx, params, n_band, n_band_max, k_start, h_a, h_e, out_off, precision, stream=None):
+    n = params.shape[1]
+    cdt = torch.complex64 if precision == GBK_MIXED else torch.complex128
+    _check(lib().gb_waveform_batch(ctx.handle, _dev(params, torch.float64, "params"), _dev(n_band, torch.int32, "n_band"),
+                                   int(n_band_max), n, _dev(k_start, torch.int64, "k_start"),
+                                   _dev(h_a, cdt, "h_a"), _dev(h_e, cdt, "h_e"), _dev(out_off, torch.int64, "out_off"),
+                                   int(precision), _stream(stream)), "gb_waveform_batch")
+
+
+def residual_struct(resid, frac_bits):
+    """gbk_residual for an int64 tensor [W][2][n_bins][2]."""
+    _dev(resid, torch.int64, "residual")
+    return GbkResidual(ctypes.c_void_p(resid.data_ptr()), int(resid.shape[0]), int(frac_bits))
+
+
+def psd_struct(psd_params):
+    _dev(psd_params, torch.float64, "psd_params")
+    return GbkPsd(ctypes.c_void_p(psd_params.data_ptr()), int(psd_params.shape[0]))
+
+
+def gb_delta_loglike_batch(ctx, params_new, params_old, n_band, n_band_max, walker, residual, psd, dlogl,
+                           precision, stream=None):
+    n = params_new.shape[1]
+    _check(lib().gb_delta_loglike_batch(ctx.handle, _dev(params_new, torch.float64, "params_new"),
+                                        _dev(params_old, torch.float64, "params_old"), _dev(n_band, torch.int32, "n_band"),
+                                        int(n_band_max), _dev(walker, torch.int32, "walker"), n,
+                                        ctypes.byref(residual), ctypes.byref(psd), _dev(dlogl, torch.float64, "dlogl"),
+                                        int(precision), _stream(stream)), "gb_delta_loglike_batch")
+
+
+def residual_add_sub(ctx, residual, params, n_band, n_band_max, walker, sign, precision, stream=None):
+    n = params.shape[1]
+    _check(lib().residual_add_sub(ctx.handle, ctypes.byref(residual), _dev(params, torch.float64, "params"),
+                                  _dev(n_band, torch.int32, "n_band"), int(n_band_max), _dev(walker, torch.int32, "walker"),
+                                  n, int(sign), int(precision), _stream(stream)), "residual_add_sub")
+
+
+def psd_eval(ctx, psd_params, s_out, stream=None):
+    w = psd_params.shape[0]
+    _check(lib().psd_eval(ctx.handle, _dev(psd_params, torch.float64, "psd_params"), w,
+                          _dev(s_out, torch.float64, "s_out") if s_out is not None else None, _stream(stream)), "psd_eval")
+
+
+def total_loglike(ctx, residual, psd_params, logl, stream=None):
+    w = psd_params.shape[0]
+    _check(lib().total_loglike(ctx.handle, _dev(residual, torch.float32, "residual"),
+                               _dev(psd_params, torch.float64, "psd_params"), w, _dev(logl, torch.float64, "logl"),
+                               _stream(stream)), "total_loglike")

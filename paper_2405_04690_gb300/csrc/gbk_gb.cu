@@ -1,0 +1,374 @@
+// GB waveform, Delta lnL and residual add/sub kernels and their C-ABI entry points.
+#include <math.h>
+#include <stdio.h>
+
+#include "gbk_internal.cuh"
+#include "gbk_wave.cuh"
+#include "gbk_reduce.cuh"
+
+namespace gbk {
+
+constexpr int kWarpsPerCta = 4;
+
+template <typename T>
+__device__ __forceinline__ const T* orb_table(const gbk_ctx& c, int bi);
+template <>
+__device__ __forceinline__ const float* orb_table<float>(const gbk_ctx& c, int bi) { return c.orb_f[bi]; }
+template <>
+__device__ __forceinline__ const double* orb_table<double>(const gbk_ctx& c, int bi) { return c.orb_d[bi]; }
+template <typename T>
+__device__ __forceinline__ const typename CT<T>::C* tw_table(const gbk_ctx& c, int bi);
+template <>
+__device__ __forceinline__ const float2* tw_table<float>(const gbk_ctx& c, int bi) { return c.tw_f[bi]; }
+template <>
+__device__ __forceinline__ const double2* tw_table<double>(const gbk_ctx& c, int bi) { return c.tw_d[bi]; }
+
+// Dispatch a warp to gen_band<T, N> for its runtime N (<= NMAX).
+template <typename T, int NMAX>
+__device__ __forceinline__ bool gen_any(const gbk_ctx& c, const Src<T>& s, int n,
+                                        typename CT<T>::C* b0, typename CT<T>::C* b1, int lane) {
+  const double tobs = c.grid.tobs;
+  switch (n) {
+    case 128: gen_band<T, 128>(s, orb_table<T>(c, 0), tw_table<T>(c, 0), tobs, b0, b1, lane); return true;
+    case 256: if (NMAX >= 256) { gen_band<T, 256>(s, orb_table<T>(c, 1), tw_table<T>(c, 1), tobs, b0, b1, lane); return true; } break;
+    case 512: if (NMAX >= 512) { gen_band<T, 512>(s, orb_table<T>(c, 2), tw_table<T>(c, 2), tobs, b0, b1, lane); return true; } break;
+    case 1024: if (NMAX >= 1024) { gen_band<T, 1024>(s, orb_table<T>(c, 3), tw_table<T>(c, 3), tobs, b0, b1, lane); return true; } break;
+    default: break;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------- gb_waveform_batch
+template <typename T, int NMAX>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+k_waveform(const gbk_ctx c, const double* __restrict__ params, const int32_t* __restrict__ nb,
+           int64_t n, int64_t* __restrict__ k_start, typename CT<T>::C* __restrict__ ha,
+           typename CT<T>::C* __restrict__ he, const int64_t* __restrict__ off) {
+  typedef typename CT<T>::C C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  C* b0 = reinterpret_cast<C*>(smem_raw) + (size_t)wid * 4 * NMAX;
+  C* b1 = b0 + 2 * NMAX;
+  const int64_t stride_w = (int64_t)gridDim.x * kWarpsPerCta;
+  for (int64_t i = (int64_t)blockIdx.x * kWarpsPerCta + wid; i < n; i += stride_w) {
+    const int nbi = nb[i];
+    const Src<T> s = make_src<T>(params, n, i, c.grid.tobs);
+    if (nbi > NMAX || band_index(nbi) < 0) {
+      if (lane == 0) atomicOr(c.err, kErrBand);
+      continue;
+    }
+    gen_any<T, NMAX>(c, s, nbi, b0, b1, lane);
+    const T down = (T)5.421010862427522170e-20;  // 2^-64 back to strain units
+    const int64_t o = off[i];
+    for (int j = lane; j < nbi; j += 32) {
+      ha[o + j] = cscale(b0[j], down);
+      he[o + j] = cscale(b0[nbi + j], down);
+    }
+    if (lane == 0) k_start[i] = s.q - nbi / 2;
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------- Delta lnL
+template <typename T> struct Acc;
+template <> struct Acc<float> { typedef CompF S; };
+template <> struct Acc<double> { typedef PlainD S; };
+
+// Per-walker PSD weight: 4 df / (S_k 2^128) = cw * iq_k / (1 + aw rho_k).
+template <typename T>
+struct PsdW {
+  T cw, aw;
+};
+template <typename T>
+__device__ __forceinline__ PsdW<T> psd_walker(const gbk_ctx& c, const double* __restrict__ pp, int npsd, int w) {
+  const int j = (npsd == 1) ? 0 : w;
+  const double so = pp[2 * j] * pp[2 * j];
+  const double sa = pp[2 * j + 1] * pp[2 * j + 1];
+  PsdW<T> r;
+  r.cw = (T)(4.0 / c.grid.tobs / so);
+  r.aw = (T)(sa / so);
+  return r;
+}
+__device__ __forceinline__ float iq_at(const gbk_ctx& c, int64_t k, float) { return __ldg(&c.iq_f[k]); }
+__device__ __forceinline__ double iq_at(const gbk_ctx& c, int64_t k, double) { return __ldg(&c.iq_d[k]); }
+__device__ __forceinline__ float rho_at(const gbk_ctx& c, int64_t k, float) { return __ldg(&c.rho_f[k]); }
+__device__ __forceinline__ double rho_at(const gbk_ctx& c, int64_t k, double) { return __ldg(&c.rho_d[k]); }
+__device__ __forceinline__ float i2r(long long v, float) { return __ll2float_rn(v); }
+__device__ __forceinline__ double i2r(long long v, double) { return __ll2double_rn(v); }
+__device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+
+// Accumulate -1/2 |D|^2 w and Re(R* D) w over one bin (both channels).
+template <typename T>
+__device__ __forceinline__ void acc_bin(const gbk_ctx& c, const long long* __restrict__ rw,
+                                        int64_t kloc, typename CT<T>::C da, typename CT<T>::C de,
+                                        const PsdW<T>& pw, T rscale,
+                                        typename Acc<T>::S& sdd, typename Acc<T>::S& srd) {
+  const int64_t nbins = c.grid.n_bins;
+  const longlong2 ra = *reinterpret_cast<const longlong2*>(rw + 2 * kloc);
+  const longlong2 re = *reinterpret_cast<const longlong2*>(rw + 2 * (nbins + kloc));
+  const T w = pw.cw * iq_at(c, kloc, T()) * rcp_((T)1 + pw.aw * rho_at(c, kloc, T()));
+  const T rax = i2r(ra.x, T()) * rscale, ray = i2r(ra.y, T()) * rscale;
+  const T rex = i2r(re.x, T()) * rscale, rey = i2r(re.y, T()) * rscale;
+  sdd.add(w * (da.x * da.x + da.y * da.y + de.x * de.x + de.y * de.y));
+  srd.add(w * (rax * da.x + ray * da.y + rex * de.x + rey * de.y));
+}
+
+template <typename T, int NMAX>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+k_dlogl(const gbk_ctx c, const double* __restrict__ pnew, const double* __restrict__ pold,
+        const int32_t* __restrict__ nb, const int32_t* __restrict__ walker, int64_t n,
+        const long long* __restrict__ resid, int32_t n_walkers, int32_t frac_bits,
+        const double* __restrict__ psdp, int32_t npsd, double* __restrict__ dlogl) {
+  typedef typename CT<T>::C C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  C* ba = reinterpret_cast<C*>(smem_raw) + (size_t)wid * 6 * NMAX;
+  C* br = ba + 2 * NMAX;
+  C* bs = br + 2 * NMAX;
+  const int64_t stride_w = (int64_t)gridDim.x * kWarpsPerCta;
+  const int64_t nbins = c.grid.n_bins;
+  const T rscale = (T)ldexp(1.0, kStrainExp - frac_bits);
+  for (int64_t i = (int64_t)blockIdx.x * kWarpsPerCta + wid; i < n; i += stride_w) {
+    const int nbi = nb[i];
+    const int w = walker[i];
+    if (nbi > NMAX || band_index(nbi) < 0 || w < 0 || w >= n_walkers || (npsd != 1 && w >= npsd)) {
+      if (lane == 0) {
+        atomicOr(c.err, (w < 0 || w >= n_walkers || (npsd != 1 && w >= npsd)) ? kErrWalker : kErrBand);
+        dlogl[i] = __longlong_as_double(0x7ff8000000000000LL);
+      }
+      continue;
+    }
+    const Src<T> sa = make_src<T>(pnew, n, i, c.grid.tobs);
+    const Src<T> sr = make_src<T>(pold, n, i, c.grid.tobs);
+    const int64_t ka = sa.q - nbi / 2 - c.grid.k0;
+    const int64_t kr = sr.q - nbi / 2 - c.grid.k0;
+    const bool bad = (!sa.zero && (ka < 0 || ka + nbi > nbins)) || (!sr.zero && (kr < 0 || kr + nbi > nbins));
+    if (bad) {
+      if (lane == 0) {
+        atomicOr(c.err, kErrRange);
+        dlogl[i] = __longlong_as_double(0x7ff8000000000000LL);
+      }
+      continue;
+    }
+    if (!sa.zero) gen_any<T, NMAX>(c, sa, nbi, ba, bs, lane);
+    if (!sr.zero) gen_any<T, NMAX>(c, sr, nbi, br, bs, lane);
+    const PsdW<T> pw = psd_walker<T>(c, psdp, npsd, w);
+    const long long* rw = resid + (int64_t)w * 2 * nbins * 2;
+    typename Acc<T>::S sdd, srd;
+    sdd.init();
+    srd.init();
+    const C zero = mkc((T)0, (T)0);
+    // bins of a's band: D = a - r (r where the bands overlap)
+    if (!sa.zero) {
+      for (int j = lane; j < nbi; j += 32) {
+        const int64_t k = ka + j;
+        C ra = zero, re = zero;
+        const int64_t jr = k - kr;
+        if (!sr.zero && jr >= 0 && jr < nbi) { ra = br[jr]; re = br[nbi + jr]; }
+        acc_bin<T>(c, rw, k, csub(ba[j], ra), csub(ba[nbi + j], re), pw, rscale, sdd, srd);
+      }
+    }
+    // bins of r's band outside a's band: D = -r
+    if (!sr.zero) {
+      for (int j = lane; j < nbi; j += 32) {
+        const int64_t k = kr + j;
+        const int64_t ja = k - ka;
+        if (!sa.zero && ja >= 0 && ja < nbi) continue;
+        const C ra = br[j], re = br[nbi + j];
+        acc_bin<T>(c, rw, k, mkc(-ra.x, -ra.y), mkc(-re.x, -re.y), pw, rscale, sdd, srd);
+      }
+    }
+    const double dd = sdd.warp_total();
+    const double rd = srd.warp_total();
+    if (lane == 0) dlogl[i] = -0.5 * dd + rd;
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------- residual add/sub
+__device__ __forceinline__ long long to_grid(float v, float s) { return __float2ll_rn(v * s); }
+__device__ __forceinline__ long long to_grid(double v, double s) { return __double2ll_rn(v * s); }
+
+template <typename T, int NMAX>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+k_addsub(const gbk_ctx c, const double* __restrict__ params, const int32_t* __restrict__ nb,
+         const int32_t* __restrict__ walker, int64_t n, long long* __restrict__ resid,
+         int32_t n_walkers, int32_t frac_bits, int sign) {
+  typedef typename CT<T>::C C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  C* b0 = reinterpret_cast<C*>(smem_raw) + (size_t)wid * 4 * NMAX;
+  C* b1 = b0 + 2 * NMAX;
+  const int64_t stride_w = (int64_t)gridDim.x * kWarpsPerCta;
+  const int64_t nbins = c.grid.n_bins;
+  const T gs = (T)ldexp(1.0, frac_bits - kStrainExp);
+  for (int64_t i = (int64_t)blockIdx.x * kWarpsPerCta + wid; i < n; i += stride_w) {
+    const int nbi = nb[i];
+    const int w = walker[i];
+    if (nbi > NMAX || band_index(nbi) < 0 || w < 0 || w >= n_walkers) {
+      if (lane == 0) atomicOr(c.err, (w < 0 || w >= n_walkers) ? kErrWalker : kErrBand);
+      continue;
+    }
+    const Src<T> s = make_src<T>(params, n, i, c.grid.tobs);
+    if (s.zero) continue;
+    const int64_t k = s.q - nbi / 2 - c.grid.k0;
+    if (k < 0 || k + nbi > nbins) {
+      if (lane == 0) atomicOr(c.err, kErrRange);
+      continue;
+    }
+    gen_any<T, NMAX>(c, s, nbi, b0, b1, lane);
+    unsigned long long* rw = reinterpret_cast<unsigned long long*>(resid) + (int64_t)w * 2 * nbins * 2;
+    for (int j = lane; j < nbi; j += 32) {
+      for (int ch = 0; ch < 2; ++ch) {
+        const C h = b0[ch * nbi + j];
+        long long hx = to_grid(h.x, gs), hy = to_grid(h.y, gs);
+        if (sign > 0) { hx = -hx; hy = -hy; }   // template enters the model: R -= h
+        unsigned long long* dst = rw + 2 * (ch * nbins + k + j);
+        atomicAdd(dst, (unsigned long long)hx);
+        atomicAdd(dst + 1, (unsigned long long)hy);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------- launch helpers
+template <typename T>
+size_t warp_smem(int nmax, int nbuf) { return (size_t)nbuf * 2 * nmax * sizeof(typename CT<T>::C); }
+
+template <typename K>
+static gbk_status launch_cfg(K kernel, size_t smem, int64_t items, int* grid_out) {
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return set_error(GBK_ECUDA, "cudaFuncSetAttribute(smem=%zu) failed", smem);
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarpsPerCta * 32, smem) != cudaSuccess || per_sm < 1)
+    return set_error(GBK_ECUDA, "kernel does not fit on an SM (smem=%zu)", smem);
+  int64_t need = (items + kWarpsPerCta - 1) / kWarpsPerCta;
+  int64_t cap = (int64_t)sms * per_sm;
+  *grid_out = (int)(need < cap ? (need > 0 ? need : 1) : cap);
+  return GBK_OK;
+}
+
+static bool valid_nmax(int nmax) { return band_index(nmax) >= 0; }
+
+template <typename T>
+static gbk_status waveform_t(gbk_ctx* ctx, const double* params, const int32_t* nb, int nmax, int64_t n,
+                             int64_t* ks, void* ha, void* he, const int64_t* off, cudaStream_t st) {
+  typedef typename CT<T>::C C;
+  size_t smem = kWarpsPerCta * warp_smem<T>(nmax, 2);
+  int grid = 0;
+  gbk_status s = GBK_OK;
+#define GBK_WF(NM)                                                                            \
+  case NM:                                                                                    \
+    s = launch_cfg(k_waveform<T, NM>, smem, n, &grid);                                        \
+    if (s) return s;                                                                          \
+    k_waveform<T, NM><<<grid, kWarpsPerCta * 32, smem, st>>>(*ctx, params, nb, n, ks, (C*)ha, \
+                                                               (C*)he, off);                  \
+    break;
+  switch (nmax) { GBK_WF(128) GBK_WF(256) GBK_WF(512) GBK_WF(1024) }
+#undef GBK_WF
+  return check_launch("gb_waveform_batch");
+}
+
+template <typename T>
+static gbk_status dlogl_t(gbk_ctx* ctx, const double* pn, const double* po, const int32_t* nb, int nmax,
+                          const int32_t* walker, int64_t n, const gbk_residual* R, const gbk_psd* psd,
+                          double* out, cudaStream_t st) {
+  size_t smem = kWarpsPerCta * warp_smem<T>(nmax, 3);
+  int grid = 0;
+  gbk_status s = GBK_OK;
+#define GBK_DL(NM)                                                                                      \
+  case NM:                                                                                              \
+    s = launch_cfg(k_dlogl<T, NM>, smem, n, &grid);                                                     \
+    if (s) return s;                                                                                    \
+    k_dlogl<T, NM><<<grid, kWarpsPerCta * 32, smem, st>>>(*ctx, pn, po, nb, walker, n,                  \
+                                                          (const long long*)R->data, R->n_walkers,      \
+                                                          R->frac_bits, psd->params, psd->n_psd, out);  \
+    break;
+  switch (nmax) { GBK_DL(128) GBK_DL(256) GBK_DL(512) GBK_DL(1024) }
+#undef GBK_DL
+  return check_launch("gb_delta_loglike_batch");
+}
+
+template <typename T>
+static gbk_status addsub_t(gbk_ctx* ctx, const gbk_residual* R, const double* params, const int32_t* nb,
+                           int nmax, const int32_t* walker, int64_t n, int sign, cudaStream_t st) {
+  size_t smem = kWarpsPerCta * warp_smem<T>(nmax, 2);
+  int grid = 0;
+  gbk_status s = GBK_OK;
+#define GBK_AS(NM)                                                                               \
+  case NM:                                                                                       \
+    s = launch_cfg(k_addsub<T, NM>, smem, n, &grid);                                             \
+    if (s) return s;                                                                             \
+    k_addsub<T, NM><<<grid, kWarpsPerCta * 32, smem, st>>>(*ctx, params, nb, walker, n,          \
+                                                           (long long*)R->data, R->n_walkers,    \
+                                                           R->frac_bits, sign);                  \
+    break;
+  switch (nmax) { GBK_AS(128) GBK_AS(256) GBK_AS(512) GBK_AS(1024) }
+#undef GBK_AS
+  return check_launch("residual_add_sub");
+}
+
+}  // namespace gbk
+
+using namespace gbk;
+
+extern "C" gbk_status gb_waveform_batch(gbk_ctx* ctx, const double* params, const int32_t* n_band,
+                                        int32_t n_band_max, int64_t n, int64_t* k_start, void* h_a,
+                                        void* h_e, const int64_t* out_off, gbk_precision precision,
+                                        void* stream) {
+  if (!ctx) return set_error(GBK_EINVAL, "gb_waveform_batch: null context");
+  if (n < 0) return set_error(GBK_EINVAL, "gb_waveform_batch: n < 0");
+  if (n == 0) return GBK_OK;
+  if (!params || !n_band || !k_start || !h_a || !h_e || !out_off)
+    return set_error(GBK_EINVAL, "gb_waveform_batch: null device pointer");
+  if (!valid_nmax(n_band_max)) return set_error(GBK_EINVAL, "gb_waveform_batch: n_band_max %d not in {128,256,512,1024}", n_band_max);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == GBK_MIXED) return waveform_t<float>(ctx, params, n_band, n_band_max, n, k_start, h_a, h_e, out_off, st);
+  if (precision == GBK_FP64) return waveform_t<double>(ctx, params, n_band, n_band_max, n, k_start, h_a, h_e, out_off, st);
+  return set_error(GBK_EINVAL, "gb_waveform_batch: bad precision %d", (int)precision);
+}
+
+extern "C" gbk_status gb_delta_loglike_batch(gbk_ctx* ctx, const double* params_new,
+                                             const double* params_old, const int32_t* n_band,
+                                             int32_t n_band_max, const int32_t* walker, int64_t n,
+                                             const gbk_residual* residual, const gbk_psd* psd,
+                                             double* dlogl, gbk_precision precision, void* stream) {
+  if (!ctx || !residual || !psd) return set_error(GBK_EINVAL, "gb_delta_loglike_batch: null context/struct");
+  if (n < 0) return set_error(GBK_EINVAL, "gb_delta_loglike_batch: n < 0");
+  if (n == 0) return GBK_OK;
+  if (!params_new || !params_old || !n_band || !walker || !dlogl || !residual->data || !psd->params)
+    return set_error(GBK_EINVAL, "gb_delta_loglike_batch: null device pointer");
+  if (!valid_nmax(n_band_max)) return set_error(GBK_EINVAL, "gb_delta_loglike_batch: bad n_band_max %d", n_band_max);
+  if (residual->n_walkers < 1 || residual->frac_bits < 40 || residual->frac_bits > 120 || psd->n_psd < 1)
+    return set_error(GBK_EINVAL, "gb_delta_loglike_batch: bad residual/psd description");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == GBK_MIXED) return dlogl_t<float>(ctx, params_new, params_old, n_band, n_band_max, walker, n, residual, psd, dlogl, st);
+  if (precision == GBK_FP64) return dlogl_t<double>(ctx, params_new, params_old, n_band, n_band_max, walker, n, residual, psd, dlogl, st);
+  return set_error(GBK_EINVAL, "gb_delta_loglike_batch: bad precision %d", (int)precision);
+}
+
+extern "C" gbk_status residual_add_sub(gbk_ctx* ctx, const gbk_residual* residual, const double* params,
+                                       const int32_t* n_band, int32_t n_band_max, const int32_t* walker,
+                                       int64_t n, int32_t sign, gbk_precision precision, void* stream) {
+  if (!ctx || !residual) return set_error(GBK_EINVAL, "residual_add_sub: null context/struct");
+  if (n < 0) return set_error(GBK_EINVAL, "residual_add_sub: n < 0");
+  if (sign != 1 && sign != -1) return set_error(GBK_EINVAL, "residual_add_sub: sign must be +1 or -1");
+  if (n == 0) return GBK_OK;
+  if (!params || !n_band || !walker || !residual->data) return set_error(GBK_EINVAL, "residual_add_sub: null device pointer");
+  if (!valid_nmax(n_band_max)) return set_error(GBK_EINVAL, "residual_add_sub: bad n_band_max %d", n_band_max);
+  if (residual->n_walkers < 1 || residual->frac_bits < 40 || residual->frac_bits > 120)
+    return set_error(GBK_EINVAL, "residual_add_sub: bad residual description");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == GBK_MIXED) return addsub_t<float>(ctx, residual, params, n_band, n_band_max, walker, n, sign, st);
+  if (precision == GBK_FP64) return addsub_t<double>(ctx, residual, params, n_band, n_band_max, walker, n, sign, st);
+  return set_error(GBK_EINVAL, "residual_add_sub: bad precision %d", (int)precision);
+}

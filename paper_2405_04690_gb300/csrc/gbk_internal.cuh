@@ -1,0 +1,71 @@
+// Internal definitions of libgbk: context, constants, device helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbk.h"
+
+namespace gbk {
+
+// Physical constants (standard LISA / LDC values; the paper fixes only f* = c / L).
+constexpr double kC = 299792458.0;          // m/s
+constexpr double kLArm = 2.5e9;             // m
+constexpr double kAU = 1.495978707e11;      // m
+constexpr double kYear = 31557600.0;        // s
+constexpr double kLc = kLArm / kC;          // s, one-arm light time
+
+// Internal strain scale: strain-like values are carried as value * 2^64 and PSDs as
+// S * 2^128 so that float32 never meets denormals (S_n ~ 1e-42 in these units is
+// below float32's normal range). Powers of two: the rescaling is exact.
+constexpr int kStrainExp = 64;
+
+// Band lengths: 128 << i for i = 0..3.
+constexpr int kNumBandSizes = 4;
+inline __host__ __device__ int band_index(int n) {
+  return n == 128 ? 0 : n == 256 ? 1 : n == 512 ? 2 : n == 1024 ? 3 : -1;
+}
+
+// Orbit table rows, SoA [kOrbRows][N] per band length: guiding-centre direction
+// (cos alpha, sin alpha) times AU/c, spacecraft offsets from the guiding centre in
+// light-seconds (3 craft x 3), arm unit vectors n12, n23, n31 (3 x 3).
+constexpr int kOrbRows = 20;
+
+// Device error bits (OR-ed into the context's error word).
+constexpr int kErrRange = 1;
+constexpr int kErrBand = 2;
+constexpr int kErrWalker = 4;
+constexpr int kErrTimeout = 8;
+
+}  // namespace gbk
+
+struct gbk_ctx {
+  gbk_grid grid;
+  int device;
+  // per band length: orbit tables and FFT twiddles W_N^k = exp(-2 pi i k / N)
+  float* orb_f[gbk::kNumBandSizes];
+  double* orb_d[gbk::kNumBandSizes];
+  float2* tw_f[gbk::kNumBandSizes];
+  double2* tw_d[gbk::kNumBandSizes];
+  // PSD shape over the window: S = S_oms * Q_k + S_acc * P_k (physical),
+  // rho = P / Q, iq = 2^-128 / Q, lnq = ln Q.
+  double* psd_q;
+  double* psd_p;
+  float* iq_f;
+  float* rho_f;
+  double* iq_d;
+  double* rho_d;
+  double sum_lnq;      // sum_k ln Q_k over the window, float64
+  int* err;            // device error word
+  // scratch for cross-block partial sums of total_loglike
+  double* scratch;
+  size_t scratch_bytes;
+};
+
+namespace gbk {
+
+// Record an error message for gbk_last_error() and return the status.
+gbk_status set_error(gbk_status st, const char* fmt, ...);
+gbk_status check_launch(const char* what);
+
+}  // namespace gbk

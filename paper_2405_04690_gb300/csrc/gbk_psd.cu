@@ -1,0 +1,172 @@
+// Parametric PSD (Eq. psd) and the full log-likelihood pass (Eq. like).
+#include <math.h>
+
+#include "gbk_internal.cuh"
+#include "gbk_reduce.cuh"
+
+namespace gbk {
+
+constexpr int kTlThreads = 256;
+constexpr int kTlChunk = 4096;      // bins per block
+constexpr int kTlWalkers = 8;       // walkers per block
+constexpr int kTlMaxW = 4096;       // walkers per launch pair (scratch sizing)
+
+size_t total_loglike_scratch_bytes(int64_t n_bins) {
+  const int64_t chunks = (n_bins + kTlChunk - 1) / kTlChunk;
+  return (size_t)chunks * kTlMaxW * 2 * sizeof(double);
+}
+
+__global__ void k_psd_eval(const double* __restrict__ q, const double* __restrict__ p,
+                           const double* __restrict__ pp, int32_t nw, int64_t nb, double* __restrict__ out) {
+  const int64_t total = (int64_t)nw * nb;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = i / nb, k = i - w * nb;
+    const double so = pp[2 * w] * pp[2 * w], sa = pp[2 * w + 1] * pp[2 * w + 1];
+    out[i] = so * q[k] + sa * p[k];
+  }
+}
+
+// One block: bins [chunk * kTlChunk, +kTlChunk) of walkers [w0, w0 + kTlWalkers).
+// Per bin k and walker w (u = 1 + a_w rho_k, iq_k = 2^-128 / Q_k):
+//   q-term (|R_A|^2 + |R_E|^2) 2^128 iq_k / u,   l-term ln u.
+// Writes compensated block sums to part[(chunk * nwl + wl) * 2 + {0, 1}].
+__global__ void __launch_bounds__(kTlThreads)
+k_total_loglike_part(const float* __restrict__ R, const float* __restrict__ iq, const float* __restrict__ rho,
+                     const double* __restrict__ pp, int32_t w0, int32_t nwl, int64_t nb, double* __restrict__ part) {
+  const int chunk = blockIdx.x;
+  const int wg = blockIdx.y * kTlWalkers;  // local walker offset within this launch
+  const int64_t kbeg = (int64_t)chunk * kTlChunk;
+  const int64_t kend = min(kbeg + (int64_t)kTlChunk, nb);
+  float aw[kTlWalkers];
+  const float* rw[kTlWalkers];
+  bool act[kTlWalkers];
+#pragma unroll
+  for (int j = 0; j < kTlWalkers; ++j) {
+    const int wl = wg + j;
+    act[j] = wl < nwl;
+    const int w = w0 + (act[j] ? wl : 0);
+    const double so = pp[2 * w] * pp[2 * w], sa = pp[2 * w + 1] * pp[2 * w + 1];
+    aw[j] = (float)(sa / so);
+    rw[j] = R + (int64_t)w * 2 * nb * 2;
+  }
+  CompF sq[kTlWalkers], sl[kTlWalkers];
+#pragma unroll
+  for (int j = 0; j < kTlWalkers; ++j) { sq[j].init(); sl[j].init(); }
+  const float up = 18446744073709551616.0f;  // 2^64
+  const bool even = (nb & 1) == 0;
+  for (int64_t k = kbeg + 2 * threadIdx.x; k < kend; k += 2 * kTlThreads) {
+    if (even && k + 1 < kend) {
+      const float2 iq2 = __ldg(reinterpret_cast<const float2*>(iq + k));
+      const float2 rh2 = __ldg(reinterpret_cast<const float2*>(rho + k));
+      float4 a[kTlWalkers], e[kTlWalkers];
+#pragma unroll
+      for (int j = 0; j < kTlWalkers; ++j) {
+        if (act[j]) {
+          a[j] = __ldcs(reinterpret_cast<const float4*>(rw[j] + 2 * k));
+          e[j] = __ldcs(reinterpret_cast<const float4*>(rw[j] + 2 * (nb + k)));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kTlWalkers; ++j) {
+        if (!act[j]) continue;
+        const float u0 = fmaf(aw[j], rh2.x, 1.0f), u1 = fmaf(aw[j], rh2.y, 1.0f);
+        const float ax = a[j].x * up, ay = a[j].y * up, az = a[j].z * up, aww = a[j].w * up;
+        const float ex = e[j].x * up, ey = e[j].y * up, ez = e[j].z * up, ew = e[j].w * up;
+        const float m0 = ax * ax + ay * ay + ex * ex + ey * ey;
+        const float m1 = az * az + aww * aww + ez * ez + ew * ew;
+        sq[j].add(m0 * iq2.x * __frcp_rn(u0));
+        sq[j].add(m1 * iq2.y * __frcp_rn(u1));
+        sl[j].add(logf(u0));
+        sl[j].add(logf(u1));
+      }
+    } else {
+      for (int64_t kk = k; kk < min(k + 2, kend); ++kk) {
+        const float iqk = __ldg(iq + kk), rhk = __ldg(rho + kk);
+#pragma unroll
+        for (int j = 0; j < kTlWalkers; ++j) {
+          if (!act[j]) continue;
+          const float2 a = *reinterpret_cast<const float2*>(rw[j] + 2 * kk);
+          const float2 e = *reinterpret_cast<const float2*>(rw[j] + 2 * (nb + kk));
+          const float u = fmaf(aw[j], rhk, 1.0f);
+          const float ax = a.x * up, ay = a.y * up, ex = e.x * up, ey = e.y * up;
+          sq[j].add((ax * ax + ay * ay + ex * ex + ey * ey) * iqk * __frcp_rn(u));
+          sl[j].add(logf(u));
+        }
+      }
+    }
+  }
+  __shared__ double red[kTlThreads / 32][kTlWalkers][2];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < kTlWalkers; ++j) {
+    const double tq = sq[j].warp_total();
+    const double tl = sl[j].warp_total();
+    if (lane == 0) { red[wid][j][0] = tq; red[wid][j][1] = tl; }
+  }
+  __syncthreads();
+  if (threadIdx.x < kTlWalkers * 2) {
+    const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
+    if (wg + j < nwl) {
+      double s = 0.0;
+      for (int w = 0; w < kTlThreads / 32; ++w) s += red[w][j][which];
+      part[((int64_t)chunk * nwl + wg + j) * 2 + which] = s;
+    }
+  }
+}
+
+// Sum the chunk partials of each walker in chunk order and assemble Eq. like.
+__global__ void k_total_loglike_final(const double* __restrict__ part, int nchunks, const double* __restrict__ pp,
+                                      int32_t w0, int32_t nwl, int64_t nb, double df, double sum_lnq,
+                                      double* __restrict__ logl) {
+  const int wl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (wl >= nwl) return;
+  const int w = w0 + wl;
+  double q = 0.0, l = 0.0;
+  for (int c = 0; c < nchunks; ++c) {
+    q += part[((int64_t)c * nwl + wl) * 2];
+    l += part[((int64_t)c * nwl + wl) * 2 + 1];
+  }
+  const double so = pp[2 * w] * pp[2 * w];
+  // -1/2 <R|R> = -1/2 (4 df / S_oms) sum |R~|^2 iq / u ; -sum_ch sum_k ln S = -2 (n ln S_oms + sum ln Q + sum ln u)
+  logl[w] = -0.5 * (4.0 * df / so) * q - 2.0 * ((double)nb * log(so) + sum_lnq + l);
+}
+
+}  // namespace gbk
+
+using namespace gbk;
+
+extern "C" gbk_status psd_eval(gbk_ctx* ctx, const double* psd_params, int32_t n_walkers, double* s_out,
+                               void* stream) {
+  if (!ctx) return set_error(GBK_EINVAL, "psd_eval: null context");
+  if (n_walkers < 0) return set_error(GBK_EINVAL, "psd_eval: n_walkers < 0");
+  if (n_walkers == 0 || !s_out) return GBK_OK;
+  if (!psd_params) return set_error(GBK_EINVAL, "psd_eval: null psd_params");
+  const int64_t total = (int64_t)n_walkers * ctx->grid.n_bins;
+  const int threads = 256;
+  int64_t blocks = (total + threads - 1) / threads;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_psd_eval<<<(int)blocks, threads, 0, (cudaStream_t)stream>>>(ctx->psd_q, ctx->psd_p, psd_params, n_walkers,
+                                                                 ctx->grid.n_bins, s_out);
+  return check_launch("psd_eval");
+}
+
+extern "C" gbk_status total_loglike(gbk_ctx* ctx, const float* residual, const double* psd_params,
+                                    int32_t n_walkers, double* logl, void* stream) {
+  if (!ctx) return set_error(GBK_EINVAL, "total_loglike: null context");
+  if (n_walkers < 0) return set_error(GBK_EINVAL, "total_loglike: n_walkers < 0");
+  if (n_walkers == 0) return GBK_OK;
+  if (!residual || !psd_params || !logl) return set_error(GBK_EINVAL, "total_loglike: null device pointer");
+  if (((uintptr_t)residual & 15) != 0) return set_error(GBK_EINVAL, "total_loglike: residual must be 16-byte aligned");
+  const int64_t nb = ctx->grid.n_bins;
+  const int nchunks = (int)((nb + kTlChunk - 1) / kTlChunk);
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int32_t w0 = 0; w0 < n_walkers; w0 += kTlMaxW) {
+    const int32_t nwl = n_walkers - w0 < kTlMaxW ? n_walkers - w0 : kTlMaxW;
+    dim3 grid(nchunks, (nwl + kTlWalkers - 1) / kTlWalkers);
+    k_total_loglike_part<<<grid, kTlThreads, 0, st>>>(residual, ctx->iq_f, ctx->rho_f, psd_params, w0, nwl, nb,
+                                                       ctx->scratch);
+    k_total_loglike_final<<<(nwl + 127) / 128, 128, 0, st>>>(ctx->scratch, nchunks, psd_params, w0, nwl, nb,
+                                                            1.0 / ctx->grid.tobs, ctx->sum_lnq, logl);
+  }
+  return check_launch("total_loglike");
+}

@@ -1,0 +1,311 @@
+// Warp-level GB waveform generator: slow-part TDI response, shared-memory Stockham
+// FFT and heterodyne, in float32 (mixed) or float64 (plain) arithmetic.
+//
+// Model (arXiv:2405.04690 Sec. II.A and App. F name FastGB; the response below is the
+// standard equal-arm one, derived in the accompanying design notes):
+//   H(t) = Re[Hc e^{i Phi(t)}], Hc = A(1+cos^2 i) e+(psi) + 2i A cos i ex(psi),
+//   Phi(t) = phi0 + 2 pi f0 t + pi fdot t^2.
+//   Link i->j (unit vector n from craft i to j, receiver position x_j), slow part:
+//   Y_ij = n.Hc.n (-i pi f L/c) sinc(pi f L/c (1 - k.n)) e^{-i pi f L/c (1 - k.n)}
+//          e^{-2 pi i f k.x_j / c},  f = f0 + fdot t.
+//   X = (1 - D^2)[(Y31 - Y21) + D (Y13 - Y12)], D = e^{-2 pi i f L/c}; Y, Z cyclic.
+//   A = (Z - X)/sqrt2, E = (X - 2Y + Z)/sqrt6 (Sec. II, A_1/E_1).
+//   Band: (T / 2N) FFT_N[ slow(t_p) e^{i(phi0 + 2 pi delta p/N + pi fdot t_p^2)} ],
+//   offset m in [-N/2, N/2) -> bin q + m, q = floor(f0 T), delta = f0 T - q.
+//
+// One warp computes one band. Every kernel that needs a waveform calls gen_band<T, N>,
+// which is __noinline__ so that all call sites run the same machine code: the same
+// parameters then give bit-identical bands in every kernel, which the fixed-point
+// residual bookkeeping relies on (a template removed by one kernel cancels the one
+// another kernel added).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbk_internal.cuh"
+
+namespace gbk {
+
+template <typename T> struct CT;
+template <> struct CT<float> { typedef float2 C; };
+template <> struct CT<double> { typedef double2 C; };
+
+__device__ __forceinline__ float2 mkc(float r, float i) { return make_float2(r, i); }
+__device__ __forceinline__ double2 mkc(double r, double i) { return make_double2(r, i); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// multiply by -i
+__device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
+__device__ __forceinline__ double2 cmul_mi(double2 a) { return make_double2(a.y, -a.x); }
+
+// (cos, sin) of 2 pi x for x in cycles: reduce to [-1/2, 1/2] first.
+__device__ __forceinline__ float2 expi_cycles(float x) {
+  float r = x - rintf(x);
+  float s, c;
+  __sincosf(6.283185307179586f * r, &s, &c);
+  return make_float2(c, s);
+}
+__device__ __forceinline__ double2 expi_cycles(double x) {
+  double r = x - rint(x);
+  double s, c;
+  sincospi(2.0 * r, &s, &c);
+  return make_double2(c, s);
+}
+
+__device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
+
+// sin(pi s) / (pi s) by its Taylor series in z = (pi s)^2 (truncation < 1e-9 for
+// float, < 2e-15 for double, for |pi s| <= 1.8, i.e. f up to the 1/30 Hz Nyquist).
+__device__ __forceinline__ float sincpi_poly(float s) {
+  float x = 3.14159265358979f * s;
+  float z = x * x;
+  float p = -1.0f / 1307674368000.0f;
+  p = p * z + 1.0f / 6227020800.0f;
+  p = p * z - 1.0f / 39916800.0f;
+  p = p * z + 1.0f / 362880.0f;
+  p = p * z - 1.0f / 5040.0f;
+  p = p * z + 1.0f / 120.0f;
+  p = p * z - 1.0f / 6.0f;
+  p = p * z + 1.0f;
+  return p;
+}
+__device__ __forceinline__ double sincpi_poly(double s) {
+  double x = 3.141592653589793 * s;
+  double z = x * x;
+  double p = 1.0 / 51090942171709440000.0;
+  p = p * z - 1.0 / 121645100408832000.0;
+  p = p * z + 1.0 / 355687428096000.0;
+  p = p * z - 1.0 / 1307674368000.0;
+  p = p * z + 1.0 / 6227020800.0;
+  p = p * z - 1.0 / 39916800.0;
+  p = p * z + 1.0 / 362880.0;
+  p = p * z - 1.0 / 5040.0;
+  p = p * z + 1.0 / 120.0;
+  p = p * z - 1.0 / 6.0;
+  p = p * z + 1.0;
+  return p;
+}
+
+// Per-source constants. float64 only for the carrier-bin split of f0 T and fdot T^2.
+template <typename T>
+struct Src {
+  long long q;     // carrier bin
+  T delta;         // f0 T - q in [0, 1)
+  T fdt2h;         // fdot T^2 / 2 (cycles at t = T)
+  T phi0c;         // phi0 / (2 pi)
+  T f0, fdot;
+  T kx, ky, kz;    // propagation direction
+  T ux, uy, uz, vx, vy, vz;
+  T c2p, s2p;      // cos 2psi, sin 2psi
+  T ap, ac;        // A (1 + cos^2 i) 2^64, 2 A cos i 2^64
+  bool zero;       // amplitude exactly zero
+};
+
+template <typename T>
+__device__ __forceinline__ Src<T> make_src(const double* __restrict__ prm, int64_t stride,
+                                           int64_t i, double tobs) {
+  Src<T> s;
+  const double amp = prm[0 * stride + i];
+  const double f0 = prm[1 * stride + i];
+  const double fdot = prm[2 * stride + i];
+  const double phi0 = prm[3 * stride + i];
+  const double psi = prm[4 * stride + i];
+  const double cosi = prm[5 * stride + i];
+  const double sinb = prm[6 * stride + i];
+  const double lam = prm[7 * stride + i];
+  const double ft = f0 * tobs;
+  const double qd = floor(ft);
+  s.q = (long long)qd;
+  s.delta = (T)(ft - qd);
+  s.fdt2h = (T)(0.5 * fdot * tobs * tobs);
+  s.phi0c = (T)(phi0 * 0.15915494309189535);
+  s.f0 = (T)f0;
+  s.fdot = (T)fdot;
+  const T sb = (T)sinb;
+  const T cb = sqrt((T)1 - sb * sb);
+  T sl, cl, s2, c2;
+  sincos_((T)lam, &sl, &cl);
+  sincos_((T)(2.0 * psi), &s2, &c2);
+  s.kx = -cb * cl; s.ky = -cb * sl; s.kz = -sb;
+  s.ux = sb * cl; s.uy = sb * sl; s.uz = -cb;
+  s.vx = sl; s.vy = -cl; s.vz = (T)0;
+  s.c2p = c2; s.s2p = s2;
+  const double scale = 18446744073709551616.0;  // 2^64
+  s.ap = (T)(amp * (1.0 + cosi * cosi) * scale);
+  s.ac = (T)(2.0 * amp * cosi * scale);
+  s.zero = (amp == 0.0);
+  return s;
+}
+
+// Radix-4 and radix-2 Stockham stages over both channels of a warp's buffers
+// (layout [2][N]); twiddles tw[m] = exp(-2 pi i m / N).
+template <typename C, int N>
+__device__ __forceinline__ void stage_r4(const C* __restrict__ in, C* __restrict__ out,
+                                         const C* __restrict__ tw, int ns, int lane) {
+  constexpr int NB = N / 4;
+  const int step = N / (ns * 4);
+#pragma unroll 2
+  for (int b = lane; b < 2 * NB; b += 32) {
+    const int ch = b / NB;
+    const int j = b - ch * NB;
+    const C* x = in + ch * N;
+    C* y = out + ch * N;
+    const int k = j & (ns - 1);
+    C v0 = x[j], v1 = x[j + NB], v2 = x[j + 2 * NB], v3 = x[j + 3 * NB];
+    if (ns > 1) {
+      v1 = cmul(v1, __ldg(&tw[k * step]));
+      v2 = cmul(v2, __ldg(&tw[2 * k * step]));
+      v3 = cmul(v3, __ldg(&tw[3 * k * step]));
+    }
+    // 4-point DFT with w = -i
+    const C s02 = cadd(v0, v2), d02 = csub(v0, v2);
+    const C s13 = cadd(v1, v3), d13 = cmul_mi(csub(v1, v3));
+    const int d = (j - k) * 4 + k;
+    y[d] = cadd(s02, s13);
+    y[d + ns] = cadd(d02, d13);
+    y[d + 2 * ns] = csub(s02, s13);
+    y[d + 3 * ns] = csub(d02, d13);
+  }
+}
+
+template <typename C, int N>
+__device__ __forceinline__ void stage_r2_first(const C* __restrict__ in, C* __restrict__ out,
+                                               int lane) {
+  constexpr int NB = N / 2;
+  for (int b = lane; b < 2 * NB; b += 32) {
+    const int ch = b / NB;
+    const int j = b - ch * NB;
+    const C* x = in + ch * N;
+    C* y = out + ch * N;
+    const C v0 = x[j], v1 = x[j + NB];
+    y[2 * j] = cadd(v0, v1);
+    y[2 * j + 1] = csub(v0, v1);
+  }
+}
+
+// Generate the A/E band of one source into buf0 ([2][N], band order: element i is bin
+// q - N/2 + i), in strain units times 2^64. buf1 is scratch of the same size.
+// Called by all 32 lanes of a warp; returns with the warp synchronised.
+template <typename T, int N>
+__device__ __noinline__ void gen_band(const Src<T> src, const T* __restrict__ orb,
+                                      const typename CT<T>::C* __restrict__ tw, double tobs,
+                                      typename CT<T>::C* buf0, typename CT<T>::C* buf1,
+                                      int lane) {
+  typedef typename CT<T>::C C;
+  const T lc = (T)kLc;
+  const T dtp = (T)(tobs / N);
+  const T inv_n = (T)1 / (T)N;
+  const T scale = (T)(0.5 * tobs / N);
+  const T rs2 = (T)0.70710678118654752440;
+  const T rs6 = (T)0.40824829046386301637;
+  for (int p = lane; p < N; p += 32) {
+    const T* o = orb + p;
+    const T gcc = o[0 * N], gcs = o[1 * N];
+    T dx[3][3], na[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        dx[c][d] = o[(2 + 3 * c + d) * N];
+        na[c][d] = o[(11 + 3 * c + d) * N];
+      }
+    const T tp = (T)p * dtp;
+    const T f = src.f0 + src.fdot * tp;
+    const T flc = f * lc;
+    const T kr = src.kx * gcc + src.ky * gcs;  // k . R_gc / c (guiding centre in the ecliptic)
+    T kd[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) kd[c] = src.kx * dx[c][0] + src.ky * dx[c][1] + src.kz * dx[c][2];
+    // arm projections n.Hc.n (same for both directions) and k.n
+    C nhn[3];
+    T kn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T un = src.ux * na[a][0] + src.uy * na[a][1] + src.uz * na[a][2];
+      const T vn = src.vx * na[a][0] + src.vy * na[a][1] + src.vz * na[a][2];
+      kn[a] = src.kx * na[a][0] + src.ky * na[a][1] + src.kz * na[a][2];
+      const T xp = un * un - vn * vn;
+      const T xc = (T)2 * un * vn;
+      nhn[a] = mkc(src.ap * (src.c2p * xp - src.s2p * xc), src.ac * (src.s2p * xp + src.c2p * xc));
+    }
+    // links: arm a, direction sign sg (k.n_ij = sg k.n_a), receiver craft j
+    // 12: (0,+,1) 21: (0,-,0) 23: (1,+,2) 32: (1,-,1) 31: (2,+,0) 13: (2,-,2)
+    C y[6];
+    const int arm[6] = {0, 0, 1, 1, 2, 2};
+    const int rcv[6] = {1, 0, 2, 1, 0, 2};
+#pragma unroll
+    for (int l = 0; l < 6; ++l) {
+      const T sg = (l & 1) ? (T)-1 : (T)1;
+      const T sarg = flc * ((T)1 - sg * kn[arm[l]]);
+      const T cyc = -((T)0.5 * sarg + f * kd[rcv[l]]);
+      const C e = expi_cycles(cyc);
+      const T sc = sincpi_poly(sarg);
+      y[l] = cmul(nhn[arm[l]], mkc(sc * e.x, sc * e.y));
+    }
+    // y index: 0=12 1=21 2=23 3=32 4=31 5=13
+    const C dd = expi_cycles(-flc);
+    const C X = cadd(csub(y[4], y[1]), cmul(dd, csub(y[5], y[0])));
+    const C Y = cadd(csub(y[0], y[3]), cmul(dd, csub(y[1], y[2])));
+    const C Z = cadd(csub(y[2], y[5]), cmul(dd, csub(y[3], y[4])));
+    const C As = cscale(csub(Z, X), rs2);
+    const C Es = cscale(cadd(csub(X, cscale(Y, (T)2)), Z), rs6);
+    // common factor (-i pi f L/c)(1 - D^2) e^{i(carrier - 2 pi f k.R_gc/c)} T/(2N)
+    const T pn = (T)p * inv_n;
+    const T cyc0 = src.phi0c + src.delta * pn + src.fdt2h * pn * pn - f * kr;
+    const C car = expi_cycles(cyc0);
+    const C d2 = cmul(dd, dd);
+    const C one_m_d2 = mkc((T)1 - d2.x, -d2.y);
+    const T tf = (T)3.14159265358979323846 * flc * scale;
+    const C com = cmul_mi(cscale(cmul(one_m_d2, car), tf));
+    buf0[p] = cmul(com, As);
+    buf0[N + p] = cmul(com, Es);
+  }
+  __syncwarp();
+  // Stockham FFT: optional radix-2 first stage, then radix-4 stages.
+  C* in = buf0;
+  C* out = buf1;
+  int ns = 1;
+  if (N == 128 || N == 512) {
+    stage_r2_first<C, N>(in, out, lane);
+    __syncwarp();
+    C* t = in; in = out; out = t;
+    ns = 2;
+  }
+  for (; ns < N; ns *= 4) {
+    stage_r4<C, N>(in, out, tw, ns, lane);
+    __syncwarp();
+    C* t = in; in = out; out = t;
+  }
+  // result is in `in`; rotate by N/2 into buf0 (band order)
+  if (in == buf0) {
+    for (int i = lane; i < N; i += 32) {   // swap halves, one lane per pair
+      const int ch = i / (N / 2);
+      const int ii = i - ch * (N / 2);
+      C* b = buf0 + ch * N;
+      const C lo = b[ii], hi = b[ii + N / 2];
+      b[ii] = hi;
+      b[ii + N / 2] = lo;
+    }
+  } else {
+    for (int i = lane; i < 2 * N; i += 32) {
+      const int ch = i / N;
+      const int ii = i - ch * N;
+      buf0[i] = in[ch * N + ((ii + N / 2) & (N - 1))];
+    }
+  }
+  __syncwarp();
+}
+
+}  // namespace gbk
