@@ -1,0 +1,370 @@
+"""Sampler steps of the GB module, FP64 (test infrastructure).
+
+Follows arXiv:2405.04690:
+
+* Eq. rj-acceptance: alpha_RJ = min[1, L(theta_{k,+1}) p(theta_{+1}) / (L(theta_k) q(theta_{+1}))],
+  inverted for a removal; likelihoods tempered as L^beta (App. D).
+* Eq. temp-orig and Eq. temp-final (App. D): swap acceptance between two walkers with
+  walker-attached residuals.
+* Alg. 1 (App. A): per band (t, w, b) form the 3-sub-band residual r', subtract the
+  band's sources, run n_prop in-model proposals with accept/reject inside the band,
+  and for t = 0 write accepted changes back to the cold-chain residual.
+* App. C: reversible jump by the "flip-all" basis over n_max slots in random order,
+  each a birth (empty slot) or death (occupied slot) accepted or rejected on its own.
+* Alg. 2 (App. E): per band, walkers permuted per temperature; current and swapped
+  likelihoods from the top temperature down, swap by Eq. temp-final; a swap that
+  changes the cold chain updates its residual.
+* Sec. V.D: odd bands first, then even bands; three sub-bands per band window.
+
+Readings where the paper is silent (listed in the design doc): see ``SweepConfig``.
+Random numbers come from Philox4x32-10 at fixed counters (``oracle.philox``).
+"""
+import math
+
+import numpy as np
+
+from . import likelihood as LK
+from . import philox as PX
+from . import residual as RS
+from . import waveform as WF
+from .constants import GM_SUN_C3
+
+SQRT3 = 1.7320508075688772
+TWO_PI = 6.283185307179586
+K_CHIRP = 96.0 / 5.0 * math.pi ** (8.0 / 3.0)
+
+
+# ---------------------------------------------------------------- acceptance rules
+def rj_log_alpha(dloglike, beta, log_p_new, log_q_new, birth=True):
+    """ln of the Eq. rj-acceptance ratio (tempered); removal is the inverse ratio."""
+    if birth:
+        return beta * dloglike + log_p_new - log_q_new
+    return beta * dloglike - log_p_new + log_q_new
+
+
+def temp_orig_log_alpha(loglike_n, loglike_m, beta_i, beta_j):
+    """ln of Eq. temp-orig: (L_n / L_m)^(beta_j - beta_i)."""
+    return (beta_j - beta_i) * (loglike_n - loglike_m)
+
+
+def temp_final_log_alpha(ll_i_m, ll_j_n, ll_i_n, ll_j_m, beta_I, beta_II):
+    """ln of Eq. temp-final: L_{i,m}^bI L_{j,n}^bII / (L_{i,n}^bI L_{j,m}^bII)."""
+    return beta_I * (ll_i_m - ll_i_n) + beta_II * (ll_j_n - ll_j_m)
+
+
+# ---------------------------------------------------------------- configuration
+class SweepConfig:
+    """Sampler set-up. Readings of the paper:
+
+    * bands of ``nb`` bins starting at bin ``band_k0``; band b owns f0 in
+      [band_k0 + b nb, band_k0 + (b+1) nb) / T and its sources may move half a band
+      into each neighbour (Sec. V.D); a birth in band b draws f0 uniformly over that
+      allowance (so the prior proposal equals the band's prior, p/q = 1);
+    * slot occupancy prior: independent, P(occupied) = pi_occ (log odds
+      ``log_occ_odds``; 0 reproduces Eq. rj-acceptance with no count prior);
+    * priors: ln A uniform on [ln A_min, ln A_max]; chirp mass uniform on
+      [mc_min, mc_max] (fdot induced, density ~ fdot^-2/5 f0^-11/5); phi0, psi,
+      lambda uniform and periodic; cos iota, sin beta uniform on [-1, 1];
+    * in-model move: every coordinate perturbed by sigma_c z_c with z_c the
+      Irwin-Hall(4) variable (sum of four uniforms, centred, unit variance), ln A
+      perturbed instead of A (its Hastings factor cancels the 1/A prior);
+    * n_prop = round(props_per_source * g) in-model proposals per band task, g the
+      number of sources in the band at the start of the task.
+    """
+
+    def __init__(self, **kw):
+        self.tobs = kw["tobs"]
+        self.k0 = kw["k0"]                 # residual window start bin
+        self.n_bins = kw["n_bins"]
+        self.band_k0 = kw["band_k0"]
+        self.nb = kw.get("nb", 256)
+        self.n_bands = kw["n_bands"]
+        self.n_temps = kw["n_temps"]
+        self.n_walkers = kw["n_walkers"]
+        self.n_max = kw["n_max"]
+        self.frac_bits = kw.get("frac_bits", 98)
+        self.betas = np.asarray(kw["betas"], dtype=np.float64)        # [n_bands][n_temps]
+        self.psd = np.asarray(kw["psd"], dtype=np.float64)            # [n_walkers][n_bins] PSD values
+        self.sigma = np.asarray(kw["sigma"], dtype=np.float64)        # 8 widths (ln A first)
+        self.log_occ_odds = kw.get("log_occ_odds", 0.0)
+        self.props_per_source = kw.get("props_per_source", 1.0)
+        self.key = kw.get("key", (0x1234, 0x5678))
+        self.ln_a_min = kw.get("ln_a_min", math.log(1e-23))
+        self.ln_a_max = kw.get("ln_a_max", math.log(10 ** -21.5))
+        self.mc_min = kw.get("mc_min", 0.3)
+        self.mc_max = kw.get("mc_max", 0.8)
+        self.f_min = kw.get("f_min", 1e-3)
+        self.f_max = kw.get("f_max", 4e-3)
+        self.df = 1.0 / self.tobs
+
+    def band_bins(self, b):
+        lo = self.band_k0 + b * self.nb
+        return lo, lo + self.nb
+
+    def allowance(self, b):
+        lo, hi = self.band_bins(b)
+        return max(self.f_min, (lo - self.nb / 2) / self.tobs), min(self.f_max, (hi + self.nb / 2) / self.tobs)
+
+    def window(self, b):
+        """Residual window of band b: sub-bands b-1, b, b+1 (local offset into the grid, length)."""
+        lo, _ = self.band_bins(b)
+        return lo - self.nb - self.k0, 3 * self.nb
+
+
+def chirp_mass(f0, fdot):
+    return (fdot / (K_CHIRP * f0 ** (11.0 / 3.0))) ** 0.6 / GM_SUN_C3
+
+
+def fdot_from_mc(f0, mc):
+    return K_CHIRP * f0 ** (11.0 / 3.0) * (mc * GM_SUN_C3) ** (5.0 / 3.0)
+
+
+def in_support(cfg, th, b):
+    a, f0, fd, _, _, ci, sb, _ = th
+    lo, hi = cfg.allowance(b)
+    if not (lo <= f0 < hi):
+        return False
+    if not (a > 0) or not (cfg.ln_a_min <= math.log(a) <= cfg.ln_a_max):
+        return False
+    if not (-1.0 <= ci <= 1.0 and -1.0 <= sb <= 1.0):
+        return False
+    if not (fd > 0):
+        return False
+    mc = chirp_mass(f0, fd)
+    return cfg.mc_min <= mc <= cfg.mc_max
+
+
+def log_prior_shape(th):
+    """Non-uniform part of the prior in the sampled coordinates: ln p(fdot | f0)."""
+    return -0.4 * math.log(th[2]) - 2.2 * math.log(th[1])
+
+
+def _wrap(x, period):
+    if x >= period:
+        return x - period
+    if x < 0.0:
+        return x + period
+    return x
+
+
+def _block_words(key, c0, c1, c2, c3, n_blocks):
+    out = []
+    for m in range(n_blocks):
+        out.extend(PX.philox4x32_10((c0 + m, c1, c2, c3), key))
+    return out
+
+
+def propose_in_model(cfg, th, words):
+    """In-model proposal from the 48 words of one proposal (word 0 picks the source)."""
+    z = [((PX.u24(words[1 + 4 * c]) + PX.u24(words[2 + 4 * c]) + PX.u24(words[3 + 4 * c])
+           + PX.u24(words[4 + 4 * c])) - 2.0) * SQRT3 for c in range(8)]
+    s = cfg.sigma
+    new = list(th)
+    new[0] = math.exp(math.log(th[0]) + s[0] * z[0])
+    new[1] = th[1] + s[1] * z[1]
+    new[2] = th[2] + s[2] * z[2]
+    new[3] = _wrap(th[3] + s[3] * z[3], TWO_PI)
+    new[4] = _wrap(th[4] + s[4] * z[4], math.pi)
+    new[5] = th[5] + s[5] * z[5]
+    new[6] = th[6] + s[6] * z[6]
+    new[7] = _wrap(th[7] + s[7] * z[7], TWO_PI)
+    return new
+
+
+def draw_birth(cfg, b, words):
+    """Prior draw of a new source in band b from 8 words (u32 each)."""
+    lo, hi = cfg.allowance(b)
+    u = [PX.u32(w) for w in words[:8]]
+    f0 = lo + (hi - lo) * u[0]
+    a = math.exp(cfg.ln_a_min + (cfg.ln_a_max - cfg.ln_a_min) * u[1])
+    mc = cfg.mc_min + (cfg.mc_max - cfg.mc_min) * u[2]
+    return [a, f0, fdot_from_mc(f0, mc), TWO_PI * u[3], math.pi * u[4], 2.0 * u[5] - 1.0, 2.0 * u[6] - 1.0,
+            TWO_PI * u[7]]
+
+
+def task_id(cfg, t, w, b):
+    return (t * cfg.n_walkers + w) * cfg.n_bands + b
+
+
+# ---------------------------------------------------------------- band likelihood pieces
+def _band_window(cfg, th, b):
+    """h(theta) placed on band b's window (complex [2][3 nb])."""
+    off, n = cfg.window(b)
+    return LK.place(WF.fastslow_band(th, cfg.nb, cfg.tobs), cfg.k0 + off, n)
+
+
+def _swap_dll(cfg, rwin, psd_w, b, th_new, th_old):
+    off, n = cfg.window(b)
+    bn = WF.fastslow_band(th_new, cfg.nb, cfg.tobs) if th_new is not None else None
+    bo = WF.fastslow_band(th_old, cfg.nb, cfg.tobs) if th_old is not None else None
+    return LK.delta_loglike_swap(rwin, psd_w, cfg.df, cfg.k0 + off, bn, bo)
+
+
+def open_band(cfg, state, r_snap, w, b):
+    """rho_{w,b}: cold residual of walker w on band b's window with band b's cold sources added back."""
+    off, n = cfg.window(b)
+    rho = RS.from_fixed(r_snap[w][:, off:off + n], cfg.frac_bits)
+    for s in range(cfg.n_max):
+        if state["exists"][0, w, b, s]:
+            rho = rho + _band_window(cfg, state["params"][0, w, b, s], b)
+    return rho
+
+
+def band_task(cfg, state, r_snap, rho, t, w, b, parity, sweep, trace):
+    """Alg. 1 (in-model) followed by the flip-all RJ pass (App. C) for band (t, w, b)."""
+    off, n = cfg.window(b)
+    psd_w = cfg.psd[w][off:off + n]
+    beta = cfg.betas[b, t]
+    P = state["params"]
+    E = state["exists"]
+    R = state["resid"]
+    if t == 0:
+        rp = RS.from_fixed(r_snap[w][:, off:off + n], cfg.frac_bits)
+    else:
+        rp = rho.copy()
+        for s in range(cfg.n_max):
+            if E[t, w, b, s]:
+                rp = rp - _band_window(cfg, P[t, w, b, s], b)
+    tid = task_id(cfg, t, w, b)
+
+    def apply(th_new, th_old):
+        nonlocal rp
+        if th_new is not None:
+            rp = rp - _band_window(cfg, th_new, b)
+        if th_old is not None:
+            rp = rp + _band_window(cfg, th_old, b)
+        if t == 0:
+            if th_old is not None:
+                R[w] = RS.add_sub(R[w], cfg.k0, WF.fastslow_band(th_old, cfg.nb, cfg.tobs), -1, cfg.frac_bits)
+            if th_new is not None:
+                R[w] = RS.add_sub(R[w], cfg.k0, WF.fastslow_band(th_new, cfg.nb, cfg.tobs), +1, cfg.frac_bits)
+
+    existing = [s for s in range(cfg.n_max) if E[t, w, b, s]]
+    g = len(existing)
+    n_prop = int(round(cfg.props_per_source * g))
+    for j in range(n_prop):
+        words = _block_words(cfg.key, 12 * j, tid, 0 | (parity << 4), sweep, 12)
+        k = existing[PX.ranged(words[0], g)]
+        th = list(P[t, w, b, k])
+        new = propose_in_model(cfg, th, words)
+        lu = math.log(PX.u53(words[33], words[34])) if PX.u53(words[33], words[34]) > 0 else -math.inf
+        if not in_support(cfg, new, b):
+            trace.append(("in", t, w, b, k, new, float("nan"), -math.inf, False))
+            continue
+        dll = _swap_dll(cfg, rp, psd_w, b, new, th)
+        la = beta * dll + log_prior_shape(new) - log_prior_shape(th)
+        acc = lu < la
+        trace.append(("in", t, w, b, k, new, dll, la, acc))
+        if acc:
+            P[t, w, b, k] = new
+            apply(new, th)
+    # flip-all reversible jump
+    perm_words = _block_words(cfg.key, 0, tid, 1 | (parity << 4), sweep, (cfg.n_max + 3) // 4)
+    order = list(range(cfg.n_max))
+    wi = 0
+    for i in range(cfg.n_max - 1, 0, -1):
+        jx = PX.ranged(perm_words[wi], i + 1)
+        wi += 1
+        order[i], order[jx] = order[jx], order[i]
+    for j, s in enumerate(order):
+        words = _block_words(cfg.key, 4 * j, tid, 2 | (parity << 4), sweep, 4)
+        u = PX.u53(words[8], words[9])
+        lu = math.log(u) if u > 0 else -math.inf
+        if E[t, w, b, s]:
+            th = list(P[t, w, b, s])
+            dll = _swap_dll(cfg, rp, psd_w, b, None, th)
+            la = beta * dll - cfg.log_occ_odds
+            acc = lu < la
+            trace.append(("death", t, w, b, s, th, dll, la, acc))
+            if acc:
+                E[t, w, b, s] = False
+                apply(None, th)
+        else:
+            new = draw_birth(cfg, b, words)
+            dll = _swap_dll(cfg, rp, psd_w, b, new, None)
+            la = beta * dll + cfg.log_occ_odds
+            acc = lu < la
+            trace.append(("birth", t, w, b, s, new, dll, la, acc))
+            if acc:
+                E[t, w, b, s] = True
+                P[t, w, b, s] = new
+                apply(new, None)
+
+
+def _set_sum(cfg, state, t, w, b):
+    off, n = cfg.window(b)
+    h = np.zeros((2, n), complex)
+    for s in range(cfg.n_max):
+        if state["exists"][t, w, b, s]:
+            h = h + _band_window(cfg, state["params"][t, w, b, s], b)
+    return h
+
+
+def band_loglike(cfg, rho, psd_w, h):
+    """Band-local likelihood -1/2 <rho - H|rho - H> on the window (terms outside it cancel in every ratio)."""
+    d = rho - h
+    return -0.5 * LK.inner(d, d, psd_w, cfg.df)
+
+
+def swap_band(cfg, state, rhos, b, parity, sweep, trace):
+    """Alg. 2 for band b with ensemble-permuted walkers (Eq. temp-final)."""
+    T, W = cfg.n_temps, cfg.n_walkers
+    off, n = cfg.window(b)
+    perms = []
+    for t in range(T):
+        words = _block_words(cfg.key, 0, b * T + t, 3 | (parity << 4), sweep, (W + 3) // 4)
+        order = list(range(W))
+        wi = 0
+        for i in range(W - 1, 0, -1):
+            jx = PX.ranged(words[wi], i + 1)
+            wi += 1
+            order[i], order[jx] = order[jx], order[i]
+        perms.append(order)
+    P, E, R = state["params"], state["exists"], state["resid"]
+    for c in range(W):
+        ws = [perms[t][c] for t in range(T)]
+        for t in range(T - 1, 0, -1):
+            wt, wm = ws[t], ws[t - 1]
+            h_t = _set_sum(cfg, state, t, wt, b)
+            h_m = _set_sum(cfg, state, t - 1, wm, b)
+            pt, pm = cfg.psd[wt][off:off + n], cfg.psd[wm][off:off + n]
+            l_t_at_m = band_loglike(cfg, rhos[(wt, b)], pt, h_m)
+            l_t_at_t = band_loglike(cfg, rhos[(wt, b)], pt, h_t)
+            l_m_at_t = band_loglike(cfg, rhos[(wm, b)], pm, h_t)
+            l_m_at_m = band_loglike(cfg, rhos[(wm, b)], pm, h_m)
+            la = temp_final_log_alpha(l_t_at_m, l_m_at_t, l_t_at_t, l_m_at_m, cfg.betas[b, t], cfg.betas[b, t - 1])
+            words = PX.philox4x32_10((t, b * W + c, 4 | (parity << 4), sweep), cfg.key)
+            u = PX.u53(words[0], words[1])
+            lu = math.log(u) if u > 0 else -math.inf
+            acc = lu < la
+            trace.append(("swap", t, wt, b, c, None, la, la, acc))
+            if acc:
+                old_cold = [list(P[0, wm, b, s]) for s in range(cfg.n_max) if E[0, wm, b, s]] if t == 1 else None
+                pa, ea = P[t, wt, b].copy(), E[t, wt, b].copy()
+                P[t, wt, b], E[t, wt, b] = P[t - 1, wm, b].copy(), E[t - 1, wm, b].copy()
+                P[t - 1, wm, b], E[t - 1, wm, b] = pa, ea
+                if t == 1:
+                    for th in old_cold:
+                        R[wm] = RS.add_sub(R[wm], cfg.k0, WF.fastslow_band(th, cfg.nb, cfg.tobs), -1, cfg.frac_bits)
+                    for s in range(cfg.n_max):
+                        if E[0, wm, b, s]:
+                            R[wm] = RS.add_sub(R[wm], cfg.k0, WF.fastslow_band(P[0, wm, b, s], cfg.nb, cfg.tobs), +1,
+                                               cfg.frac_bits)
+
+
+def sweep(cfg, state, sweep_index, trace=None, do_swap=True):
+    """One sweep: odd bands, then even bands; each half: open, band tasks (Alg. 1 + RJ), swaps (Alg. 2)."""
+    if trace is None:
+        trace = []
+    for parity in (1, 0):
+        bands = [b for b in range(cfg.n_bands) if b % 2 == parity]
+        r_snap = state["resid"].copy()
+        rhos = {(w, b): open_band(cfg, state, r_snap, w, b) for w in range(cfg.n_walkers) for b in bands}
+        for b in bands:
+            for t in range(cfg.n_temps):
+                for w in range(cfg.n_walkers):
+                    band_task(cfg, state, r_snap, rhos[(w, b)], t, w, b, parity, sweep_index, trace)
+        if do_swap:
+            for b in bands:
+                swap_band(cfg, state, rhos, b, parity, sweep_index, trace)
+    return trace

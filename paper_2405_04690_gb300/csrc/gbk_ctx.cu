@@ -41,8 +41,9 @@ static void craft_position(double t, int n, double out[3]) {
   out[2] = -sqrt(3.0) * ecc * kAU * cos(a - b);
 }
 
-// Rows (SoA [kOrbRows][N]): 0-1 guiding centre (cos a, sin a) AU/c; 2-10 craft
-// offsets from the guiding centre / c; 11-19 arm unit vectors n12, n23, n31.
+// Rows (SoA [kOrbRows][N]): 0-1 guiding-centre direction (cos a, sin a); 2-10 craft
+// offsets from the guiding centre / c; 11-19 arm unit vectors n12, n23, n31;
+// 20-21 remainders of rows 0-1 after rounding to the table's type (0 in float64).
 static void build_orbit_table(double tobs, int n, std::vector<double>& tab) {
   tab.assign((size_t)kOrbRows * n, 0.0);
   for (int p = 0; p < n; ++p) {
@@ -51,8 +52,9 @@ static void build_orbit_table(double tobs, int n, std::vector<double>& tab) {
     const double gc[3] = {kAU * cos(a), kAU * sin(a), 0.0};
     double x[3][3];
     for (int c = 0; c < 3; ++c) craft_position(t, c, x[c]);
-    tab[0 * n + p] = gc[0] / kC;
-    tab[1 * n + p] = gc[1] / kC;
+    tab[0 * n + p] = cos(a);
+    tab[1 * n + p] = sin(a);
+    // rows 20-21: float remainders of cos a, sin a (filled by the caller for float tables)
     for (int c = 0; c < 3; ++c)
       for (int d = 0; d < 3; ++d) tab[(size_t)(2 + 3 * c + d) * n + p] = (x[c][d] - gc[d]) / kC;
     const int from[3] = {0, 1, 2}, to[3] = {1, 2, 0};
@@ -137,6 +139,10 @@ extern "C" gbk_status gbk_create(gbk_ctx** out_ctx, const gbk_grid* grid) {
     const int n = 128 << bi;
     build_orbit_table(grid->tobs, n, tab);
     std::vector<float> tabf(tab.begin(), tab.end());
+    for (int p = 0; p < n; ++p) {
+      tabf[(size_t)20 * n + p] = (float)(tab[(size_t)0 * n + p] - (double)tabf[(size_t)0 * n + p]);
+      tabf[(size_t)21 * n + p] = (float)(tab[(size_t)1 * n + p] - (double)tabf[(size_t)1 * n + p]);
+    }
     e = upload(&c->orb_d[bi], tab.data(), tab.size() * sizeof(double));
     if (e == cudaSuccess) e = upload(&c->orb_f[bi], tabf.data(), tabf.size() * sizeof(float));
     std::vector<double2> twd(n);

@@ -50,14 +50,15 @@ k_waveform(const gbk_ctx c, const double* __restrict__ params, const int32_t* __
   const int wid = threadIdx.x >> 5;
   C* b0 = reinterpret_cast<C*>(smem_raw) + (size_t)wid * 4 * NMAX;
   C* b1 = b0 + 2 * NMAX;
-  const int64_t stride_w = (int64_t)gridDim.x * kWarpsPerCta;
-  for (int64_t i = (int64_t)blockIdx.x * kWarpsPerCta + wid; i < n; i += stride_w) {
+  const int wpc = blockDim.x >> 5;
+  const int64_t stride_w = (int64_t)gridDim.x * wpc;
+  for (int64_t i = (int64_t)blockIdx.x * wpc + wid; i < n; i += stride_w) {
     const int nbi = nb[i];
-    const Src<T> s = make_src<T>(params, n, i, c.grid.tobs);
     if (nbi > NMAX || band_index(nbi) < 0) {
       if (lane == 0) atomicOr(c.err, kErrBand);
       continue;
     }
+    const Src<T> s = make_src<T>(params, n, i, c.grid.tobs, nbi);
     gen_any<T, NMAX>(c, s, nbi, b0, b1, lane);
     const T down = (T)5.421010862427522170e-20;  // 2^-64 back to strain units
     const int64_t o = off[i];
@@ -75,10 +76,12 @@ template <typename T> struct Acc;
 template <> struct Acc<float> { typedef CompF S; };
 template <> struct Acc<double> { typedef PlainD S; };
 
-// Per-walker PSD weight: 4 df / (S_k 2^128) = cw * iq_k / (1 + aw rho_k).
+// Per-walker PSD weight: 4 df / (S_k 2^128) = cw * iq_k / (1 + aw rho_k); the bins
+// carry iq_k / (1 + aw rho_k) and cw (float64) multiplies the final sums.
 template <typename T>
 struct PsdW {
-  T cw, aw;
+  double cw;
+  T aw;
 };
 template <typename T>
 __device__ __forceinline__ PsdW<T> psd_walker(const gbk_ctx& c, const double* __restrict__ pp, int npsd, int w) {
@@ -86,7 +89,7 @@ __device__ __forceinline__ PsdW<T> psd_walker(const gbk_ctx& c, const double* __
   const double so = pp[2 * j] * pp[2 * j];
   const double sa = pp[2 * j + 1] * pp[2 * j + 1];
   PsdW<T> r;
-  r.cw = (T)(4.0 / c.grid.tobs / so);
+  r.cw = 4.0 / c.grid.tobs / so;
   r.aw = (T)(sa / so);
   return r;
 }
@@ -108,7 +111,7 @@ __device__ __forceinline__ void acc_bin(const gbk_ctx& c, const long long* __res
   const int64_t nbins = c.grid.n_bins;
   const longlong2 ra = *reinterpret_cast<const longlong2*>(rw + 2 * kloc);
   const longlong2 re = *reinterpret_cast<const longlong2*>(rw + 2 * (nbins + kloc));
-  const T w = pw.cw * iq_at(c, kloc, T()) * rcp_((T)1 + pw.aw * rho_at(c, kloc, T()));
+  const T w = iq_at(c, kloc, T()) * rcp_((T)1 + pw.aw * rho_at(c, kloc, T()));
   const T rax = i2r(ra.x, T()) * rscale, ray = i2r(ra.y, T()) * rscale;
   const T rex = i2r(re.x, T()) * rscale, rey = i2r(re.y, T()) * rscale;
   sdd.add(w * (da.x * da.x + da.y * da.y + de.x * de.x + de.y * de.y));
@@ -128,10 +131,11 @@ k_dlogl(const gbk_ctx c, const double* __restrict__ pnew, const double* __restri
   C* ba = reinterpret_cast<C*>(smem_raw) + (size_t)wid * 6 * NMAX;
   C* br = ba + 2 * NMAX;
   C* bs = br + 2 * NMAX;
-  const int64_t stride_w = (int64_t)gridDim.x * kWarpsPerCta;
+  const int wpc = blockDim.x >> 5;
+  const int64_t stride_w = (int64_t)gridDim.x * wpc;
   const int64_t nbins = c.grid.n_bins;
   const T rscale = (T)ldexp(1.0, kStrainExp - frac_bits);
-  for (int64_t i = (int64_t)blockIdx.x * kWarpsPerCta + wid; i < n; i += stride_w) {
+  for (int64_t i = (int64_t)blockIdx.x * wpc + wid; i < n; i += stride_w) {
     const int nbi = nb[i];
     const int w = walker[i];
     if (nbi > NMAX || band_index(nbi) < 0 || w < 0 || w >= n_walkers || (npsd != 1 && w >= npsd)) {
@@ -141,8 +145,8 @@ k_dlogl(const gbk_ctx c, const double* __restrict__ pnew, const double* __restri
       }
       continue;
     }
-    const Src<T> sa = make_src<T>(pnew, n, i, c.grid.tobs);
-    const Src<T> sr = make_src<T>(pold, n, i, c.grid.tobs);
+    const Src<T> sa = make_src<T>(pnew, n, i, c.grid.tobs, nbi);
+    const Src<T> sr = make_src<T>(pold, n, i, c.grid.tobs, nbi);
     const int64_t ka = sa.q - nbi / 2 - c.grid.k0;
     const int64_t kr = sr.q - nbi / 2 - c.grid.k0;
     const bool bad = (!sa.zero && (ka < 0 || ka + nbi > nbins)) || (!sr.zero && (kr < 0 || kr + nbi > nbins));
@@ -183,7 +187,7 @@ k_dlogl(const gbk_ctx c, const double* __restrict__ pnew, const double* __restri
     }
     const double dd = sdd.warp_total();
     const double rd = srd.warp_total();
-    if (lane == 0) dlogl[i] = -0.5 * dd + rd;
+    if (lane == 0) dlogl[i] = pw.cw * (-0.5 * dd + rd);
     __syncwarp();
   }
 }
@@ -203,17 +207,18 @@ k_addsub(const gbk_ctx c, const double* __restrict__ params, const int32_t* __re
   const int wid = threadIdx.x >> 5;
   C* b0 = reinterpret_cast<C*>(smem_raw) + (size_t)wid * 4 * NMAX;
   C* b1 = b0 + 2 * NMAX;
-  const int64_t stride_w = (int64_t)gridDim.x * kWarpsPerCta;
+  const int wpc = blockDim.x >> 5;
+  const int64_t stride_w = (int64_t)gridDim.x * wpc;
   const int64_t nbins = c.grid.n_bins;
   const T gs = (T)ldexp(1.0, frac_bits - kStrainExp);
-  for (int64_t i = (int64_t)blockIdx.x * kWarpsPerCta + wid; i < n; i += stride_w) {
+  for (int64_t i = (int64_t)blockIdx.x * wpc + wid; i < n; i += stride_w) {
     const int nbi = nb[i];
     const int w = walker[i];
     if (nbi > NMAX || band_index(nbi) < 0 || w < 0 || w >= n_walkers) {
       if (lane == 0) atomicOr(c.err, (w < 0 || w >= n_walkers) ? kErrWalker : kErrBand);
       continue;
     }
-    const Src<T> s = make_src<T>(params, n, i, c.grid.tobs);
+    const Src<T> s = make_src<T>(params, n, i, c.grid.tobs, nbi);
     if (s.zero) continue;
     const int64_t k = s.q - nbi / 2 - c.grid.k0;
     if (k < 0 || k + nbi > nbins) {
@@ -240,20 +245,36 @@ k_addsub(const gbk_ctx c, const double* __restrict__ params, const int32_t* __re
 template <typename T>
 size_t warp_smem(int nmax, int nbuf) { return (size_t)nbuf * 2 * nmax * sizeof(typename CT<T>::C); }
 
+// Warps per CTA: up to kWarpsPerCta, fewer when a warp's buffers are large.
+static int warps_for(size_t per_warp) {
+  const size_t cap = 220 * 1024;
+  int w = (int)(cap / per_warp);
+  return w < 1 ? 1 : (w > kWarpsPerCta ? kWarpsPerCta : w);
+}
+
 template <typename K>
-static gbk_status launch_cfg(K kernel, size_t smem, int64_t items, int* grid_out) {
+static gbk_status launch_cfg(K kernel, size_t per_warp, int64_t items, int* grid_out, int* threads_out,
+                             size_t* smem_out) {
+  const int wpc = warps_for(per_warp);
+  const size_t smem = per_warp * wpc;
   if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
       return set_error(GBK_ECUDA, "cudaFuncSetAttribute(smem=%zu) failed", smem);
+    }
   }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarpsPerCta * 32, smem) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, wpc * 32, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
     return set_error(GBK_ECUDA, "kernel does not fit on an SM (smem=%zu)", smem);
-  int64_t need = (items + kWarpsPerCta - 1) / kWarpsPerCta;
+  }
+  int64_t need = (items + wpc - 1) / wpc;
   int64_t cap = (int64_t)sms * per_sm;
   *grid_out = (int)(need < cap ? (need > 0 ? need : 1) : cap);
+  *threads_out = wpc * 32;
+  *smem_out = smem;
   return GBK_OK;
 }
 
@@ -263,15 +284,15 @@ template <typename T>
 static gbk_status waveform_t(gbk_ctx* ctx, const double* params, const int32_t* nb, int nmax, int64_t n,
                              int64_t* ks, void* ha, void* he, const int64_t* off, cudaStream_t st) {
   typedef typename CT<T>::C C;
-  size_t smem = kWarpsPerCta * warp_smem<T>(nmax, 2);
-  int grid = 0;
+  const size_t pw = warp_smem<T>(nmax, 2);
+  int grid = 0, thr = 0;
+  size_t smem = 0;
   gbk_status s = GBK_OK;
-#define GBK_WF(NM)                                                                            \
-  case NM:                                                                                    \
-    s = launch_cfg(k_waveform<T, NM>, smem, n, &grid);                                        \
-    if (s) return s;                                                                          \
-    k_waveform<T, NM><<<grid, kWarpsPerCta * 32, smem, st>>>(*ctx, params, nb, n, ks, (C*)ha, \
-                                                               (C*)he, off);                  \
+#define GBK_WF(NM)                                                                              \
+  case NM:                                                                                      \
+    s = launch_cfg(k_waveform<T, NM>, pw, n, &grid, &thr, &smem);                               \
+    if (s) return s;                                                                            \
+    k_waveform<T, NM><<<grid, thr, smem, st>>>(*ctx, params, nb, n, ks, (C*)ha, (C*)he, off);   \
     break;
   switch (nmax) { GBK_WF(128) GBK_WF(256) GBK_WF(512) GBK_WF(1024) }
 #undef GBK_WF
@@ -282,14 +303,15 @@ template <typename T>
 static gbk_status dlogl_t(gbk_ctx* ctx, const double* pn, const double* po, const int32_t* nb, int nmax,
                           const int32_t* walker, int64_t n, const gbk_residual* R, const gbk_psd* psd,
                           double* out, cudaStream_t st) {
-  size_t smem = kWarpsPerCta * warp_smem<T>(nmax, 3);
-  int grid = 0;
+  const size_t pw = warp_smem<T>(nmax, 3);
+  int grid = 0, thr = 0;
+  size_t smem = 0;
   gbk_status s = GBK_OK;
 #define GBK_DL(NM)                                                                                      \
   case NM:                                                                                              \
-    s = launch_cfg(k_dlogl<T, NM>, smem, n, &grid);                                                     \
+    s = launch_cfg(k_dlogl<T, NM>, pw, n, &grid, &thr, &smem);                                          \
     if (s) return s;                                                                                    \
-    k_dlogl<T, NM><<<grid, kWarpsPerCta * 32, smem, st>>>(*ctx, pn, po, nb, walker, n,                  \
+    k_dlogl<T, NM><<<grid, thr, smem, st>>>(*ctx, pn, po, nb, walker, n,                                \
                                                           (const long long*)R->data, R->n_walkers,      \
                                                           R->frac_bits, psd->params, psd->n_psd, out);  \
     break;
@@ -301,14 +323,15 @@ static gbk_status dlogl_t(gbk_ctx* ctx, const double* pn, const double* po, cons
 template <typename T>
 static gbk_status addsub_t(gbk_ctx* ctx, const gbk_residual* R, const double* params, const int32_t* nb,
                            int nmax, const int32_t* walker, int64_t n, int sign, cudaStream_t st) {
-  size_t smem = kWarpsPerCta * warp_smem<T>(nmax, 2);
-  int grid = 0;
+  const size_t pw = warp_smem<T>(nmax, 2);
+  int grid = 0, thr = 0;
+  size_t smem = 0;
   gbk_status s = GBK_OK;
 #define GBK_AS(NM)                                                                               \
   case NM:                                                                                       \
-    s = launch_cfg(k_addsub<T, NM>, smem, n, &grid);                                             \
+    s = launch_cfg(k_addsub<T, NM>, pw, n, &grid, &thr, &smem);                                  \
     if (s) return s;                                                                             \
-    k_addsub<T, NM><<<grid, kWarpsPerCta * 32, smem, st>>>(*ctx, params, nb, walker, n,          \
+    k_addsub<T, NM><<<grid, thr, smem, st>>>(*ctx, params, nb, walker, n,                        \
                                                            (long long*)R->data, R->n_walkers,    \
                                                            R->frac_bits, sign);                  \
     break;

@@ -27,9 +27,10 @@ inline __host__ __device__ int band_index(int n) {
 }
 
 // Orbit table rows, SoA [kOrbRows][N] per band length: guiding-centre direction
-// (cos alpha, sin alpha) times AU/c, spacecraft offsets from the guiding centre in
-// light-seconds (3 craft x 3), arm unit vectors n12, n23, n31 (3 x 3).
-constexpr int kOrbRows = 20;
+// (cos alpha, sin alpha), spacecraft offsets from the guiding centre in
+// light-seconds (3 craft x 3), arm unit vectors n12, n23, n31 (3 x 3), and the
+// rounding remainders of the two direction rows (2).
+constexpr int kOrbRows = 22;
 
 // Device error bits (OR-ed into the context's error word).
 constexpr int kErrRange = 1;

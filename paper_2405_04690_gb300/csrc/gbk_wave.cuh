@@ -63,6 +63,38 @@ __device__ __forceinline__ double2 expi_cycles(double x) {
   return make_double2(c, s);
 }
 
+// exp(i x) for |x| <= 1.1 rad by Taylor series (truncation < 2e-10): used for the
+// slowly varying link and arm-delay phases, whose errors would otherwise be the same
+// in every sample of a band and add up coherently. float64 uses sincos.
+__device__ __forceinline__ float2 expi_small(float x) {
+  const float z = x * x;
+  float sp = 1.0f / 39916800.0f;
+  sp = sp * -z + 1.0f / 362880.0f;
+  sp = sp * -z + 1.0f / 5040.0f;
+  sp = sp * -z + 1.0f / 120.0f;
+  sp = sp * -z + 1.0f / 6.0f;
+  sp = sp * -z + 1.0f;
+  float cp = 1.0f / 479001600.0f;
+  cp = cp * -z + 1.0f / 3628800.0f;
+  cp = cp * -z + 1.0f / 40320.0f;
+  cp = cp * -z + 1.0f / 720.0f;
+  cp = cp * -z + 1.0f / 24.0f;
+  cp = cp * -z + 0.5f;
+  cp = cp * -z + 1.0f;
+  return make_float2(cp, x * sp);
+}
+__device__ __forceinline__ double2 expi_small(double x) {
+  double s, c;
+  sincos(x, &s, &c);
+  return make_double2(c, s);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ void fma_err(float a, float b, float p, float& e) { e = fmaf(a, b, -p); }
+__device__ __forceinline__ void fma_err(double a, double b, double p, double& e) { e = fma(a, b, -p); }
+
+__device__ __forceinline__ float rint_(float x) { return rintf(x); }
+__device__ __forceinline__ double rint_(double x) { return rint(x); }
 __device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
 
@@ -98,24 +130,35 @@ __device__ __forceinline__ double sincpi_poly(double s) {
   return p;
 }
 
-// Per-source constants. float64 only for the carrier-bin split of f0 T and fdot T^2.
+// Per-source constants, computed in float64 and rounded once. Phases are in cycles.
+// Every phase coefficient that multiplies an O(1) quantity is split into a float hi
+// part and the float remainder lo, so that its rounding error does not become a
+// systematic phase error of the band (the guiding-centre Doppler phase is ~2 cycles at
+// 4 mHz and must be right to ~1e-7 cycles for Delta lnL to 1e-2 at SNR ~ 200).
 template <typename T>
 struct Src {
   long long q;     // carrier bin
-  T delta;         // f0 T - q in [0, 1)
-  T fdt2h;         // fdot T^2 / 2 (cycles at t = T)
-  T phi0c;         // phi0 / (2 pi)
+  T dhi, dlo;      // delta = f0 T - q in [0, 1)
+  T fdh, fdl;      // fdot T^2 / 2 (up to ~100 cycles at 20 mHz: split as well)
+  T phh, phl;      // phi0 / (2 pi)
+  T dxh, dxl, dyh, dyl;  // f0 k_x AU/c, f0 k_y AU/c: guiding-centre Doppler amplitudes
+  T fkx, fky;      // fdot k_x AU/c, fdot k_y AU/c
   T f0, fdot;
   T kx, ky, kz;    // propagation direction
   T ux, uy, uz, vx, vy, vz;
   T c2p, s2p;      // cos 2psi, sin 2psi
-  T ap, ac;        // A (1 + cos^2 i) 2^64, 2 A cos i 2^64
+  T hp, hc;        // A (1 + cos^2 i) S, 2 A cos i S with S = 2^64 (T / 2N) pi L / c
   bool zero;       // amplitude exactly zero
 };
 
+template <typename T> __device__ __forceinline__ void split(double x, T& hi, T& lo) {
+  hi = (T)x;
+  lo = (T)(x - (double)hi);
+}
+
 template <typename T>
 __device__ __forceinline__ Src<T> make_src(const double* __restrict__ prm, int64_t stride,
-                                           int64_t i, double tobs) {
+                                           int64_t i, double tobs, int n) {
   Src<T> s;
   const double amp = prm[0 * stride + i];
   const double f0 = prm[1 * stride + i];
@@ -128,23 +171,35 @@ __device__ __forceinline__ Src<T> make_src(const double* __restrict__ prm, int64
   const double ft = f0 * tobs;
   const double qd = floor(ft);
   s.q = (long long)qd;
-  s.delta = (T)(ft - qd);
-  s.fdt2h = (T)(0.5 * fdot * tobs * tobs);
-  s.phi0c = (T)(phi0 * 0.15915494309189535);
+  split<T>(ft - qd, s.dhi, s.dlo);
+  split<T>(0.5 * fdot * tobs * tobs, s.fdh, s.fdl);
+  {
+    double ph = phi0 * 0.15915494309189535;
+    ph -= rint(ph);
+    split<T>(ph, s.phh, s.phl);
+  }
+  const double cbd = sqrt(1.0 - sinb * sinb);
+  double sld, cld;
+  sincos(lam, &sld, &cld);
+  const double aoc = kAU / kC;
+  split<T>(-cbd * cld * f0 * aoc, s.dxh, s.dxl);
+  split<T>(-cbd * sld * f0 * aoc, s.dyh, s.dyl);
+  s.fkx = (T)(-cbd * cld * fdot * aoc);
+  s.fky = (T)(-cbd * sld * fdot * aoc);
   s.f0 = (T)f0;
   s.fdot = (T)fdot;
   const T sb = (T)sinb;
-  const T cb = sqrt((T)1 - sb * sb);
-  T sl, cl, s2, c2;
-  sincos_((T)lam, &sl, &cl);
+  const T cb = (T)cbd;
+  const T sl = (T)sld, cl = (T)cld;
+  T s2, c2;
   sincos_((T)(2.0 * psi), &s2, &c2);
   s.kx = -cb * cl; s.ky = -cb * sl; s.kz = -sb;
   s.ux = sb * cl; s.uy = sb * sl; s.uz = -cb;
   s.vx = sl; s.vy = -cl; s.vz = (T)0;
   s.c2p = c2; s.s2p = s2;
-  const double scale = 18446744073709551616.0;  // 2^64
-  s.ap = (T)(amp * (1.0 + cosi * cosi) * scale);
-  s.ac = (T)(2.0 * amp * cosi * scale);
+  const double scale = 18446744073709551616.0 * (0.5 * tobs / n) * 3.141592653589793 * kLc;  // 2^64 (T/2N) pi L/c
+  s.hp = (T)(amp * (1.0 + cosi * cosi) * scale);
+  s.hc = (T)(2.0 * amp * cosi * scale);
   s.zero = (amp == 0.0);
   return s;
 }
@@ -207,12 +262,11 @@ __device__ __noinline__ void gen_band(const Src<T> src, const T* __restrict__ or
   const T lc = (T)kLc;
   const T dtp = (T)(tobs / N);
   const T inv_n = (T)1 / (T)N;
-  const T scale = (T)(0.5 * tobs / N);
   const T rs2 = (T)0.70710678118654752440;
   const T rs6 = (T)0.40824829046386301637;
   for (int p = lane; p < N; p += 32) {
     const T* o = orb + p;
-    const T gcc = o[0 * N], gcs = o[1 * N];
+    const T cah = o[0 * N], sah = o[1 * N], cal = o[20 * N], sal = o[21 * N];
     T dx[3][3], na[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -224,13 +278,18 @@ __device__ __noinline__ void gen_band(const Src<T> src, const T* __restrict__ or
     const T tp = (T)p * dtp;
     const T f = src.f0 + src.fdot * tp;
     const T flc = f * lc;
-    const T kr = src.kx * gcc + src.ky * gcs;  // k . R_gc / c (guiding centre in the ecliptic)
-    T kd[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) kd[c] = src.kx * dx[c][0] + src.ky * dx[c][1] + src.kz * dx[c][2];
-    // arm projections n.Hc.n (same for both directions) and k.n
-    C nhn[3];
+    const T pif = (T)3.14159265358979323846 * flc;
+    // exponentials with small arguments: E0 = e^{-i pi f L/c}, Ea = e^{i pi f L/c k.n_a},
+    // Ej = e^{-2 pi i f k.dx_j / c}; D = E0^2
+    const C e0 = expi_small(-pif);
+    C ea[3], ej[3];
     T kn[3];
+    C nhn[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T kd = src.kx * dx[c][0] + src.ky * dx[c][1] + src.kz * dx[c][2];
+      ej[c] = expi_small((T)-6.28318530717958647692 * f * kd);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const T un = src.ux * na[a][0] + src.uy * na[a][1] + src.uz * na[a][2];
@@ -238,37 +297,58 @@ __device__ __noinline__ void gen_band(const Src<T> src, const T* __restrict__ or
       kn[a] = src.kx * na[a][0] + src.ky * na[a][1] + src.kz * na[a][2];
       const T xp = un * un - vn * vn;
       const T xc = (T)2 * un * vn;
-      nhn[a] = mkc(src.ap * (src.c2p * xp - src.s2p * xc), src.ac * (src.s2p * xp + src.c2p * xc));
+      nhn[a] = mkc(src.hp * (src.c2p * xp - src.s2p * xc), src.hc * (src.s2p * xp + src.c2p * xc));
+      ea[a] = expi_small(pif * kn[a]);
     }
-    // links: arm a, direction sign sg (k.n_ij = sg k.n_a), receiver craft j
+    // link i->j (arm a, direction sign sg, receiver j), common factor E0 removed:
+    //   y_ij = n.Hc.n sinc(pi f L/c (1 - sg k.n_a)) Ea^sg Ej
     // 12: (0,+,1) 21: (0,-,0) 23: (1,+,2) 32: (1,-,1) 31: (2,+,0) 13: (2,-,2)
     C y[6];
     const int arm[6] = {0, 0, 1, 1, 2, 2};
     const int rcv[6] = {1, 0, 2, 1, 0, 2};
 #pragma unroll
     for (int l = 0; l < 6; ++l) {
-      const T sg = (l & 1) ? (T)-1 : (T)1;
-      const T sarg = flc * ((T)1 - sg * kn[arm[l]]);
-      const T cyc = -((T)0.5 * sarg + f * kd[rcv[l]]);
-      const C e = expi_cycles(cyc);
+      const bool plus = (l & 1) == 0;
+      const T sarg = flc * ((T)1 - (plus ? kn[arm[l]] : -kn[arm[l]]));
       const T sc = sincpi_poly(sarg);
-      y[l] = cmul(nhn[arm[l]], mkc(sc * e.x, sc * e.y));
+      const C ph = cmul(plus ? ea[arm[l]] : cconj(ea[arm[l]]), ej[rcv[l]]);
+      y[l] = cmul(mkc(nhn[arm[l]].x * sc, nhn[arm[l]].y * sc), ph);
     }
     // y index: 0=12 1=21 2=23 3=32 4=31 5=13
-    const C dd = expi_cycles(-flc);
+    const C dd = cmul(e0, e0);
     const C X = cadd(csub(y[4], y[1]), cmul(dd, csub(y[5], y[0])));
     const C Y = cadd(csub(y[0], y[3]), cmul(dd, csub(y[1], y[2])));
     const C Z = cadd(csub(y[2], y[5]), cmul(dd, csub(y[3], y[4])));
     const C As = cscale(csub(Z, X), rs2);
     const C Es = cscale(cadd(csub(X, cscale(Y, (T)2)), Z), rs6);
-    // common factor (-i pi f L/c)(1 - D^2) e^{i(carrier - 2 pi f k.R_gc/c)} T/(2N)
+    // common factor: (-i f)(1 - D^2) E0 e^{2 pi i cyc0} = 2 f sin(2 pi f L/c) e^{2 pi i (cyc0 - 3/2 f L/c)},
+    // cyc0 = phi0/2pi + delta p/N + fdot T^2 (p/N)^2 / 2 - f k.R_gc/c. The guiding-centre
+    // Doppler phase (O(f0 AU/c) cycles) is formed in double-float and reduced exactly.
+    T dop_h, dop_l;
+    {
+      const T p1 = src.dxh * cah, p2 = src.dyh * sah;
+      T e1, e2;
+      fma_err(src.dxh, cah, p1, e1);
+      fma_err(src.dyh, sah, p2, e2);
+      dop_h = p1 + p2;
+      const T bp = dop_h - p1;
+      const T es = (p1 - (dop_h - bp)) + (p2 - bp);
+      dop_l = es + e1 + e2 + (src.dxh * cal + src.dyh * sal) + (src.dxl * cah + src.dyl * sah);
+    }
     const T pn = (T)p * inv_n;
-    const T cyc0 = src.phi0c + src.delta * pn + src.fdt2h * pn * pn - f * kr;
-    const C car = expi_cycles(cyc0);
-    const C d2 = cmul(dd, dd);
-    const C one_m_d2 = mkc((T)1 - d2.x, -d2.y);
-    const T tf = (T)3.14159265358979323846 * flc * scale;
-    const C com = cmul_mi(cscale(cmul(one_m_d2, car), tf));
+    const T pn2 = pn * pn;  // exact: p^2 < 2^24
+    T xd = src.dhi * pn;
+    xd -= rint_(xd);
+    const T q1 = src.fdh * pn2;
+    T q1e;
+    fma_err(src.fdh, pn2, q1, q1e);
+    T big = (src.phh - (dop_h - rint_(dop_h))) + (xd + (q1 - rint_(q1)));
+    big -= rint_(big);
+    const T small = (src.dlo * pn + src.phl) + (q1e + src.fdl * pn2) - dop_l
+                    - tp * (src.fkx * cah + src.fky * sah) - (T)1.5 * flc;
+    const C car = expi_cycles(big + small);
+    const T amp = (T)2 * f * ((T)6.28318530717958647692 * flc) * sincpi_poly((T)2 * flc);
+    const C com = cscale(car, amp);
     buf0[p] = cmul(com, As);
     buf0[N + p] = cmul(com, Es);
   }
