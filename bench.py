@@ -136,7 +136,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload on the GPU
-def build_workload(torch, L, dev, seed):
+def build_workload(torch, L, dev, seed, n_temps=N_T):
     from paper_2405_04690_gb300 import synth
     g = synth.rng(seed)
     k0, nbins = synth.window_for(1e-3, 4e-3, 600)
@@ -159,9 +159,9 @@ def build_workload(torch, L, dev, seed):
                            torch.full((N_SRC,), w, dtype=torch.int32, device=dev), -1, L.GBK_MIXED)
     # per (t, w): walker-specific small jitter of the truth; cold chain (t = 0) is the model
     widths = synth.proposal_widths(truth) * 0.2
-    cur = np.empty((8, N_T * N_W * N_SRC))
-    walker = np.empty(N_T * N_W * N_SRC, dtype=np.int32)
-    for t in range(N_T):
+    cur = np.empty((8, n_temps * N_W * N_SRC))
+    walker = np.empty(n_temps * N_W * N_SRC, dtype=np.int32)
+    for t in range(n_temps):
         for w in range(N_W):
             i0 = (t * N_W + w) * N_SRC
             cur[:, i0:i0 + N_SRC] = synth.perturb(g, truth, widths)
@@ -199,7 +199,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     from paper_2405_04690_gb300 import _lib as L
     L.lib()
-    W = build_workload(torch, L, dev, seed=1 + 1000 * rank)
+    W = build_workload(torch, L, dev, seed=1 + 1000 * rank, n_temps=args.n_temps)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
 
@@ -314,6 +314,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-temps", type=int, default=N_T, help="smaller ensemble for profiling captures")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
