@@ -45,7 +45,7 @@ typedef enum gbk_status {
   GBK_OK = 0,
   GBK_EINVAL = 1,    /* bad argument (null pointer, size, enum value) */
   GBK_ERANGE = 2,    /* a band fell outside the residual window, or an index out of range */
-  GBK_ENOMEM = 3,    /* device allocation failed (only gbk_create allocates) */
+  GBK_ENOMEM = 3,    /* device allocation failed (only gbk_create / gbk_sweep_create allocate) */
   GBK_ECUDA = 4,     /* a CUDA runtime call or kernel launch failed */
   GBK_ETIMEOUT = 5,  /* a device-side wait gave up after its iteration limit */
   GBK_ENOTIMPL = 6   /* combination not implemented */
@@ -88,7 +88,8 @@ typedef struct gbk_ctx gbk_ctx;
 
 /* Create a context on the current CUDA device: orbit tables for every band length,
  * FFT twiddles, PSD shape tables over the window and scratch. Allocates device memory
- * (the only call that does). Returns GBK_ENOMEM / GBK_ECUDA on failure. */
+ * (as does gbk_sweep_create; no other call does). Returns GBK_ENOMEM / GBK_ECUDA on
+ * failure. */
 gbk_status gbk_create(gbk_ctx** out_ctx, const gbk_grid* grid);
 
 /* Free everything the context owns. Synchronises the device first. */
@@ -171,6 +172,88 @@ gbk_status psd_eval(gbk_ctx* ctx, const double* psd_params, int32_t n_walkers, d
  */
 gbk_status total_loglike(gbk_ctx* ctx, const float* residual, const double* psd_params,
                          int32_t n_walkers, double* logl, void* stream);
+
+
+/* ------------------------------------------------------------------ ensemble sweep
+ * One sweep of the GB sampler over an ensemble of n_temps x n_walkers chains whose
+ * sources are grouped by sub-band (Sec. V.D): odd sub-bands first, then even ones;
+ * for each half: (1) the residual window of every band (three sub-bands, Alg. 1) is
+ * opened from a snapshot of the cold-chain residual, (2) every band (t, w, b) runs
+ * n_prop in-model proposals with accept/reject inside the band (Alg. 1) and then the
+ * flip-all reversible jump over its n_max slots in random order (App. C, Eq.
+ * rj-acceptance), (3) every band runs ensemble-permuted tempering swaps from the top
+ * temperature down (Alg. 2, Eq. temp-final). Accepted changes of the cold chain are
+ * written to the residual exactly (fixed point, int64 atomics).
+ *
+ * Readings where the paper is silent: sources of band b may hold f0 in b's bins widened
+ * by half a band on each side; births draw from the band's prior over that range
+ * (p / q = 1); each slot is occupied with prior probability pi (log_occ_odds =
+ * ln(pi / (1 - pi)), 0 gives Eq. rj-acceptance unchanged); priors uniform in ln A,
+ * chirp mass, phi0, psi, cos iota, sin beta, lambda; in-model moves perturb ln A and
+ * the other seven parameters by sigma * z with z the centred unit-variance Irwin-Hall(4)
+ * variable (sum of four uniforms); n_prop = rint(props_per_source * g) with g the
+ * band's source count at the start of its task. Every random number comes from
+ * Philox4x32-10 (Salmon et al. 2011) at fixed counters derived from
+ * (key, sweep_index, band, temperature, walker, proposal).
+ */
+typedef struct gbk_sweep_desc {
+  int32_t n_temps, n_walkers, n_bands, n_max;  /* n_max <= 64, n_temps <= 64, n_walkers <= 64 */
+  int32_t band_bins;       /* sub-band width = template length N, 128 .. 1024 */
+  int64_t band_k0;         /* absolute first bin of band 0; windows [band_k0 + (b-1) N, +3N) must lie in the grid */
+  double sigma[8];         /* in-model widths: ln A, f0, fdot, phi0, psi, cos iota, sin beta, lambda */
+  double log_occ_odds;
+  double props_per_source;
+  double ln_a_min, ln_a_max, mc_min, mc_max, f_min, f_max;  /* prior bounds (chirp mass in M_sun) */
+  int32_t precision;       /* gbk_precision of every waveform and inner product of the sweep */
+} gbk_sweep_desc;
+
+/* One record per proposal when tracing (debugging and parity tests). kind: 0 in-model,
+ * 1 birth, 2 death, 3 swap; slot is the chain index for swaps; seq the proposal index
+ * within the band task (the temperature for swaps); dlogl is NaN for a proposal outside
+ * the prior support (rejected without a likelihood). */
+typedef struct gbk_trace_rec {
+  int32_t kind, t, w, b, slot, seq, accepted, parity;
+  double dlogl, log_alpha;
+  double params[8];
+} gbk_trace_rec;
+
+typedef struct gbk_trace {
+  gbk_trace_rec* records;  /* device, capacity records, or NULL */
+  int32_t capacity;
+  int32_t* count;          /* device counter (records wanted; may exceed capacity) */
+} gbk_trace;
+
+typedef struct gbk_sweep gbk_sweep;
+
+/* Sweep plan: validates the description against the context grid and allocates the
+ * sweep's device memory: a residual snapshot, the opened band windows, and a cache of
+ * the current waveform of every slot ([T][W][B][n_max][2][N] complex, 15.5 GB in float32
+ * for 16 x 32 x 369 bands x 20 slots at N = 256), so that deaths, band openings and
+ * tempering swaps reuse waveforms instead of regenerating them. The cache must be
+ * refreshed (GBK_SWEEP_REFRESH) whenever params/exists are changed outside gb_sweep. */
+gbk_status gbk_sweep_create(gbk_ctx* ctx, const gbk_sweep_desc* desc, gbk_sweep** out_plan);
+gbk_status gbk_sweep_destroy(gbk_sweep* plan);
+
+/* flags */
+#define GBK_SWEEP_INMODEL 1
+#define GBK_SWEEP_RJ 2
+#define GBK_SWEEP_SWAP 4
+#define GBK_SWEEP_REFRESH 8   /* regenerate the waveform cache from params/exists first */
+
+/*
+ * gb_sweep -- one sweep (both parities) on `stream`; allocates nothing.
+ *   params   [n_temps][n_walkers][n_bands][n_max][8] float64, in/out
+ *   exists   [n_temps][n_walkers][n_bands][n_max] uint8 (0/1), in/out
+ *   betas    [n_bands][n_temps] float64 inverse temperatures (0 allowed: T = infinity)
+ *   residual cold-chain residual of every walker (d - H of the t = 0 sources), in/out
+ *   psd      per-walker PSD
+ *   stats    [4][2] int64 (proposed, accepted) for in-model, birth, death, swap; added to; or NULL
+ *   trace    or NULL
+ */
+gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists, const double* betas,
+                    const gbk_residual* residual, const gbk_psd* psd, uint64_t key,
+                    uint32_t sweep_index, int32_t flags, const gbk_trace* trace, int64_t* stats,
+                    void* stream);
 
 #ifdef __cplusplus
 }

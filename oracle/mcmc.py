@@ -182,6 +182,12 @@ def draw_birth(cfg, b, words):
             TWO_PI * u[7]]
 
 
+def _rec(kind, t, w, b, slot, seq, acc, parity, dll, la, th, lu):
+    """One trace record (the fields of the GPU trace plus ln u)."""
+    return {"kind": kind, "t": t, "w": w, "b": b, "slot": slot, "seq": seq, "accepted": bool(acc),
+            "parity": parity, "dlogl": dll, "log_alpha": la, "params": None if th is None else list(th), "lu": lu}
+
+
 def task_id(cfg, t, w, b):
     return (t * cfg.n_walkers + w) * cfg.n_bands + b
 
@@ -249,12 +255,12 @@ def band_task(cfg, state, r_snap, rho, t, w, b, parity, sweep, trace):
         new = propose_in_model(cfg, th, words)
         lu = math.log(PX.u53(words[33], words[34])) if PX.u53(words[33], words[34]) > 0 else -math.inf
         if not in_support(cfg, new, b):
-            trace.append(("in", t, w, b, k, new, float("nan"), -math.inf, False))
+            trace.append(_rec(0, t, w, b, k, j, False, parity, float("nan"), -math.inf, new, lu))
             continue
         dll = _swap_dll(cfg, rp, psd_w, b, new, th)
         la = beta * dll + log_prior_shape(new) - log_prior_shape(th)
         acc = lu < la
-        trace.append(("in", t, w, b, k, new, dll, la, acc))
+        trace.append(_rec(0, t, w, b, k, j, acc, parity, dll, la, new, lu))
         if acc:
             P[t, w, b, k] = new
             apply(new, th)
@@ -275,7 +281,7 @@ def band_task(cfg, state, r_snap, rho, t, w, b, parity, sweep, trace):
             dll = _swap_dll(cfg, rp, psd_w, b, None, th)
             la = beta * dll - cfg.log_occ_odds
             acc = lu < la
-            trace.append(("death", t, w, b, s, th, dll, la, acc))
+            trace.append(_rec(2, t, w, b, s, j, acc, parity, dll, la, th, lu))
             if acc:
                 E[t, w, b, s] = False
                 apply(None, th)
@@ -284,7 +290,7 @@ def band_task(cfg, state, r_snap, rho, t, w, b, parity, sweep, trace):
             dll = _swap_dll(cfg, rp, psd_w, b, new, None)
             la = beta * dll + cfg.log_occ_odds
             acc = lu < la
-            trace.append(("birth", t, w, b, s, new, dll, la, acc))
+            trace.append(_rec(1, t, w, b, s, j, acc, parity, dll, la, new, lu))
             if acc:
                 E[t, w, b, s] = True
                 P[t, w, b, s] = new
@@ -337,7 +343,7 @@ def swap_band(cfg, state, rhos, b, parity, sweep, trace):
             u = PX.u53(words[0], words[1])
             lu = math.log(u) if u > 0 else -math.inf
             acc = lu < la
-            trace.append(("swap", t, wt, b, c, None, la, la, acc))
+            trace.append(_rec(3, t, wt, b, c, t, acc, parity, la, la, None, lu))
             if acc:
                 old_cold = [list(P[0, wm, b, s]) for s in range(cfg.n_max) if E[0, wm, b, s]] if t == 1 else None
                 pa, ea = P[t, wt, b].copy(), E[t, wt, b].copy()

@@ -38,6 +38,32 @@ class GbkPsd(ctypes.Structure):
     _fields_ = [("params", _vp), ("n_psd", _i32)]
 
 
+class GbkSweepDesc(ctypes.Structure):
+    _fields_ = [("n_temps", _i32), ("n_walkers", _i32), ("n_bands", _i32), ("n_max", _i32), ("band_bins", _i32),
+                ("band_k0", _i64), ("sigma", ctypes.c_double * 8), ("log_occ_odds", ctypes.c_double),
+                ("props_per_source", ctypes.c_double), ("ln_a_min", ctypes.c_double), ("ln_a_max", ctypes.c_double),
+                ("mc_min", ctypes.c_double), ("mc_max", ctypes.c_double), ("f_min", ctypes.c_double),
+                ("f_max", ctypes.c_double), ("precision", _i32)]
+
+
+class GbkTraceRec(ctypes.Structure):
+    _fields_ = [("kind", _i32), ("t", _i32), ("w", _i32), ("b", _i32), ("slot", _i32), ("seq", _i32),
+                ("accepted", _i32), ("parity", _i32), ("dlogl", ctypes.c_double), ("log_alpha", ctypes.c_double),
+                ("params", ctypes.c_double * 8)]
+
+
+class GbkTrace(ctypes.Structure):
+    _fields_ = [("records", _vp), ("capacity", _i32), ("count", _vp)]
+
+
+SWEEP_INMODEL = 1
+SWEEP_RJ = 2
+SWEEP_SWAP = 4
+SWEEP_REFRESH = 8
+TRACE_DTYPE_FIELDS = [("kind", "<i4"), ("t", "<i4"), ("w", "<i4"), ("b", "<i4"), ("slot", "<i4"), ("seq", "<i4"),
+                      ("accepted", "<i4"), ("parity", "<i4"), ("dlogl", "<f8"), ("log_alpha", "<f8"),
+                      ("params", "<f8", (8,))]
+
 SIGNATURES = {
     "gbk_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(GbkGrid)]),
     "gbk_destroy": (ctypes.c_int, [_vp]),
@@ -51,6 +77,10 @@ SIGNATURES = {
                                         ctypes.c_int, _vp]),
     "psd_eval": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
     "total_loglike": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp]),
+    "gbk_sweep_create": (ctypes.c_int, [_vp, ctypes.POINTER(GbkSweepDesc), ctypes.POINTER(_vp)]),
+    "gbk_sweep_destroy": (ctypes.c_int, [_vp]),
+    "gb_sweep": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(GbkResidual), ctypes.POINTER(GbkPsd),
+                                ctypes.c_uint64, ctypes.c_uint32, _i32, ctypes.POINTER(GbkTrace), _vp, _vp]),
 }
 
 _LIB = None
@@ -182,3 +212,52 @@ def total_loglike(ctx, residual, psd_params, logl, stream=None):
     _check(lib().total_loglike(ctx.handle, _dev(residual, torch.float32, "residual"),
                                _dev(psd_params, torch.float64, "psd_params"), w, _dev(logl, torch.float64, "logl"),
                                _stream(stream)), "total_loglike")
+
+
+class SweepPlan:
+    """Owns a gbk_sweep (residual snapshot, opened windows, waveform cache)."""
+
+    def __init__(self, ctx, n_temps, n_walkers, n_bands, n_max, band_bins, band_k0, sigma, precision,
+                 log_occ_odds=0.0, props_per_source=1.0, ln_a_min=None, ln_a_max=None, mc_min=0.3, mc_max=0.8,
+                 f_min=1e-3, f_max=4e-3):
+        import math
+        d = GbkSweepDesc()
+        d.n_temps, d.n_walkers, d.n_bands, d.n_max, d.band_bins = n_temps, n_walkers, n_bands, n_max, band_bins
+        d.band_k0 = int(band_k0)
+        for i in range(8):
+            d.sigma[i] = float(sigma[i])
+        d.log_occ_odds = float(log_occ_odds)
+        d.props_per_source = float(props_per_source)
+        d.ln_a_min = math.log(1e-23) if ln_a_min is None else float(ln_a_min)
+        d.ln_a_max = math.log(10 ** -21.5) if ln_a_max is None else float(ln_a_max)
+        d.mc_min, d.mc_max, d.f_min, d.f_max = float(mc_min), float(mc_max), float(f_min), float(f_max)
+        d.precision = int(precision)
+        self.desc = d
+        self.ctx = ctx
+        h = _vp()
+        _check(lib().gbk_sweep_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)), "gbk_sweep_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().gbk_sweep_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gb_sweep(plan, params, exists, betas, residual, psd, key, sweep_index, flags, trace=None, stats=None, stream=None):
+    """trace: (records uint8 tensor of capacity*sizeof(GbkTraceRec) bytes, capacity, count int32 tensor) or None."""
+    tr = None
+    if trace is not None:
+        rec, cap, cnt = trace
+        tr = GbkTrace(ctypes.c_void_p(rec.data_ptr()), int(cap), ctypes.c_void_p(cnt.data_ptr()))
+    _check(lib().gb_sweep(plan.handle, _dev(params, torch.float64, "params"), _dev(exists, torch.uint8, "exists"),
+                          _dev(betas, torch.float64, "betas"), ctypes.byref(residual), ctypes.byref(psd),
+                          ctypes.c_uint64(int(key)), ctypes.c_uint32(int(sweep_index)), int(flags),
+                          ctypes.byref(tr) if tr is not None else None,
+                          _dev(stats, torch.int64, "stats") if stats is not None else None, _stream(stream)), "gb_sweep")

@@ -25,7 +25,7 @@ __device__ __forceinline__ const double2* tw_table<double>(const gbk_ctx& c, int
 
 // Dispatch a warp to gen_band<T, N> for its runtime N (<= NMAX).
 template <typename T, int NMAX>
-__device__ __forceinline__ bool gen_any(const gbk_ctx& c, const Src<T>& s, int n,
+__device__ __forceinline__ bool gen_any(const gbk_ctx& c, const Src<T>* s, int n,
                                         typename CT<T>::C* b0, typename CT<T>::C* b1, int lane) {
   const double tobs = c.grid.tobs;
   switch (n) {
@@ -38,6 +38,13 @@ __device__ __forceinline__ bool gen_any(const gbk_ctx& c, const Src<T>& s, int n
   return false;
 }
 
+// Shared memory of one warp: `nbuf` waveform buffers [2][NMAX] and a batch of per-source
+// constants (lane l of the warp computes the constants of batch item l in float64).
+template <typename T>
+__host__ __device__ constexpr size_t warp_bytes(int nmax, int nbuf, int nsrc) {
+  return (size_t)nbuf * 2 * nmax * sizeof(typename CT<T>::C) + (size_t)nsrc * sizeof(Src<T>) + 64 * sizeof(int);
+}
+
 // ---------------------------------------------------------------- gb_waveform_batch
 template <typename T, int NMAX>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
@@ -48,26 +55,39 @@ k_waveform(const gbk_ctx c, const double* __restrict__ params, const int32_t* __
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
-  C* b0 = reinterpret_cast<C*>(smem_raw) + (size_t)wid * 4 * NMAX;
+  unsigned char* mine = smem_raw + (size_t)wid * warp_bytes<T>(NMAX, 2, 32);
+  C* b0 = reinterpret_cast<C*>(mine);
   C* b1 = b0 + 2 * NMAX;
+  Src<T>* srcs = reinterpret_cast<Src<T>*>(b1 + 2 * NMAX);
+  int* nbs = reinterpret_cast<int*>(srcs + 32);
   const int wpc = blockDim.x >> 5;
-  const int64_t stride_w = (int64_t)gridDim.x * wpc;
-  for (int64_t i = (int64_t)blockIdx.x * wpc + wid; i < n; i += stride_w) {
-    const int nbi = nb[i];
-    if (nbi > NMAX || band_index(nbi) < 0) {
-      if (lane == 0) atomicOr(c.err, kErrBand);
-      continue;
+  const int64_t stride_w = (int64_t)gridDim.x * wpc * 32;
+  for (int64_t base = ((int64_t)blockIdx.x * wpc + wid) * 32; base < n; base += stride_w) {
+    const int64_t me = base + lane;
+    if (me < n) {
+      const int nbi = nb[me];
+      nbs[lane] = nbi;
+      if (nbi <= NMAX && band_index(nbi) >= 0) srcs[lane] = make_src<T>(params, n, me, c.grid.tobs, nbi);
     }
-    const Src<T> s = make_src<T>(params, n, i, c.grid.tobs, nbi);
-    gen_any<T, NMAX>(c, s, nbi, b0, b1, lane);
-    const T down = (T)5.421010862427522170e-20;  // 2^-64 back to strain units
-    const int64_t o = off[i];
-    for (int j = lane; j < nbi; j += 32) {
-      ha[o + j] = cscale(b0[j], down);
-      he[o + j] = cscale(b0[nbi + j], down);
-    }
-    if (lane == 0) k_start[i] = s.q - nbi / 2;
     __syncwarp();
+    const int cnt = (int)min((int64_t)32, n - base);
+    for (int q = 0; q < cnt; ++q) {
+      const int64_t i = base + q;
+      const int nbi = nbs[q];
+      if (nbi > NMAX || band_index(nbi) < 0) {
+        if (lane == 0) atomicOr(c.err, kErrBand);
+        continue;
+      }
+      gen_any<T, NMAX>(c, &srcs[q], nbi, b0, b1, lane);
+      const T down = (T)5.421010862427522170e-20;  // 2^-64 back to strain units
+      const int64_t o = off[i];
+      for (int j = lane; j < nbi; j += 32) {
+        ha[o + j] = cscale(b0[j], down);
+        he[o + j] = cscale(b0[nbi + j], down);
+      }
+      if (lane == 0) k_start[i] = srcs[q].q - nbi / 2;
+      __syncwarp();
+    }
   }
 }
 
@@ -102,22 +122,23 @@ __device__ __forceinline__ double i2r(long long v, double) { return __ll2double_
 __device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
 
-// Accumulate -1/2 |D|^2 w and Re(R* D) w over one bin (both channels).
+// Accumulate |D|^2 w and Re(R* D) w over one bin (both channels).
 template <typename T>
 __device__ __forceinline__ void acc_bin(const gbk_ctx& c, const long long* __restrict__ rw,
                                         int64_t kloc, typename CT<T>::C da, typename CT<T>::C de,
-                                        const PsdW<T>& pw, T rscale,
+                                        T aw, T rscale,
                                         typename Acc<T>::S& sdd, typename Acc<T>::S& srd) {
   const int64_t nbins = c.grid.n_bins;
   const longlong2 ra = *reinterpret_cast<const longlong2*>(rw + 2 * kloc);
   const longlong2 re = *reinterpret_cast<const longlong2*>(rw + 2 * (nbins + kloc));
-  const T w = iq_at(c, kloc, T()) * rcp_((T)1 + pw.aw * rho_at(c, kloc, T()));
+  const T w = iq_at(c, kloc, T()) * rcp_((T)1 + aw * rho_at(c, kloc, T()));
   const T rax = i2r(ra.x, T()) * rscale, ray = i2r(ra.y, T()) * rscale;
   const T rex = i2r(re.x, T()) * rscale, rey = i2r(re.y, T()) * rscale;
   sdd.add(w * (da.x * da.x + da.y * da.y + de.x * de.x + de.y * de.y));
   srd.add(w * (rax * da.x + ray * da.y + rex * de.x + rey * de.y));
 }
 
+// Batch of 16 proposals per warp: lanes 0-15 set up the new templates, 16-31 the old.
 template <typename T, int NMAX>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
 k_dlogl(const gbk_ctx c, const double* __restrict__ pnew, const double* __restrict__ pold,
@@ -128,66 +149,86 @@ k_dlogl(const gbk_ctx c, const double* __restrict__ pnew, const double* __restri
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
-  C* ba = reinterpret_cast<C*>(smem_raw) + (size_t)wid * 6 * NMAX;
+  unsigned char* mine = smem_raw + (size_t)wid * warp_bytes<T>(NMAX, 3, 32);
+  C* ba = reinterpret_cast<C*>(mine);
   C* br = ba + 2 * NMAX;
   C* bs = br + 2 * NMAX;
+  Src<T>* srcs = reinterpret_cast<Src<T>*>(bs + 2 * NMAX);   // [0,16) new, [16,32) old
+  int* meta = reinterpret_cast<int*>(srcs + 32);            // [0,16) N, [16,32) walker
   const int wpc = blockDim.x >> 5;
-  const int64_t stride_w = (int64_t)gridDim.x * wpc;
+  const int64_t stride_w = (int64_t)gridDim.x * wpc * 16;
   const int64_t nbins = c.grid.n_bins;
   const T rscale = (T)ldexp(1.0, kStrainExp - frac_bits);
-  for (int64_t i = (int64_t)blockIdx.x * wpc + wid; i < n; i += stride_w) {
-    const int nbi = nb[i];
-    const int w = walker[i];
-    if (nbi > NMAX || band_index(nbi) < 0 || w < 0 || w >= n_walkers || (npsd != 1 && w >= npsd)) {
-      if (lane == 0) {
-        atomicOr(c.err, (w < 0 || w >= n_walkers || (npsd != 1 && w >= npsd)) ? kErrWalker : kErrBand);
-        dlogl[i] = __longlong_as_double(0x7ff8000000000000LL);
-      }
-      continue;
-    }
-    const Src<T> sa = make_src<T>(pnew, n, i, c.grid.tobs, nbi);
-    const Src<T> sr = make_src<T>(pold, n, i, c.grid.tobs, nbi);
-    const int64_t ka = sa.q - nbi / 2 - c.grid.k0;
-    const int64_t kr = sr.q - nbi / 2 - c.grid.k0;
-    const bool bad = (!sa.zero && (ka < 0 || ka + nbi > nbins)) || (!sr.zero && (kr < 0 || kr + nbi > nbins));
-    if (bad) {
-      if (lane == 0) {
-        atomicOr(c.err, kErrRange);
-        dlogl[i] = __longlong_as_double(0x7ff8000000000000LL);
-      }
-      continue;
-    }
-    if (!sa.zero) gen_any<T, NMAX>(c, sa, nbi, ba, bs, lane);
-    if (!sr.zero) gen_any<T, NMAX>(c, sr, nbi, br, bs, lane);
-    const PsdW<T> pw = psd_walker<T>(c, psdp, npsd, w);
-    const long long* rw = resid + (int64_t)w * 2 * nbins * 2;
-    typename Acc<T>::S sdd, srd;
-    sdd.init();
-    srd.init();
-    const C zero = mkc((T)0, (T)0);
-    // bins of a's band: D = a - r (r where the bands overlap)
-    if (!sa.zero) {
-      for (int j = lane; j < nbi; j += 32) {
-        const int64_t k = ka + j;
-        C ra = zero, re = zero;
-        const int64_t jr = k - kr;
-        if (!sr.zero && jr >= 0 && jr < nbi) { ra = br[jr]; re = br[nbi + jr]; }
-        acc_bin<T>(c, rw, k, csub(ba[j], ra), csub(ba[nbi + j], re), pw, rscale, sdd, srd);
+  for (int64_t base = ((int64_t)blockIdx.x * wpc + wid) * 16; base < n; base += stride_w) {
+    {
+      const int l = lane & 15;
+      const int64_t me = base + l;
+      if (me < n) {
+        const int nbi = nb[me];
+        if (lane < 16) { meta[l] = nbi; meta[16 + l] = walker[me]; }
+        if (nbi <= NMAX && band_index(nbi) >= 0)
+          srcs[lane] = make_src<T>(lane < 16 ? pnew : pold, n, me, c.grid.tobs, nbi);
       }
     }
-    // bins of r's band outside a's band: D = -r
-    if (!sr.zero) {
-      for (int j = lane; j < nbi; j += 32) {
-        const int64_t k = kr + j;
-        const int64_t ja = k - ka;
-        if (!sa.zero && ja >= 0 && ja < nbi) continue;
-        const C ra = br[j], re = br[nbi + j];
-        acc_bin<T>(c, rw, k, mkc(-ra.x, -ra.y), mkc(-re.x, -re.y), pw, rscale, sdd, srd);
+    __syncwarp();
+    const int cnt = (int)min((int64_t)16, n - base);
+    for (int q = 0; q < cnt; ++q) {
+      const int64_t i = base + q;
+      const int nbi = meta[q];
+      const int w = meta[16 + q];
+      if (nbi > NMAX || band_index(nbi) < 0 || w < 0 || w >= n_walkers || (npsd != 1 && w >= npsd)) {
+        if (lane == 0) {
+          atomicOr(c.err, (w < 0 || w >= n_walkers || (npsd != 1 && w >= npsd)) ? kErrWalker : kErrBand);
+          dlogl[i] = __longlong_as_double(0x7ff8000000000000LL);
+        }
+        continue;
       }
+      const Src<T>* sa = &srcs[q];
+      const Src<T>* sr = &srcs[16 + q];
+      const bool za = sa->zero, zr = sr->zero;
+      const int64_t ka = sa->q - nbi / 2 - c.grid.k0;
+      const int64_t kr = sr->q - nbi / 2 - c.grid.k0;
+      const bool bad = (!za && (ka < 0 || ka + nbi > nbins)) || (!zr && (kr < 0 || kr + nbi > nbins));
+      if (bad) {
+        if (lane == 0) {
+          atomicOr(c.err, kErrRange);
+          dlogl[i] = __longlong_as_double(0x7ff8000000000000LL);
+        }
+        continue;
+      }
+      if (!za) gen_any<T, NMAX>(c, sa, nbi, ba, bs, lane);
+      if (!zr) gen_any<T, NMAX>(c, sr, nbi, br, bs, lane);
+      const PsdW<T> pw = psd_walker<T>(c, psdp, npsd, w);
+      const long long* rw = resid + (int64_t)w * 2 * nbins * 2;
+      typename Acc<T>::S sdd, srd;
+      sdd.init();
+      srd.init();
+      const C zero = mkc((T)0, (T)0);
+      // bins of a's band: D = a - r (r where the bands overlap)
+      if (!za) {
+        for (int j = lane; j < nbi; j += 32) {
+          const int64_t k = ka + j;
+          C ra = zero, re = zero;
+          const int64_t jr = k - kr;
+          if (!zr && jr >= 0 && jr < nbi) { ra = br[jr]; re = br[nbi + jr]; }
+          acc_bin<T>(c, rw, k, csub(ba[j], ra), csub(ba[nbi + j], re), pw.aw, rscale, sdd, srd);
+        }
+      }
+      // bins of r's band outside a's band: D = -r
+      if (!zr) {
+        for (int j = lane; j < nbi; j += 32) {
+          const int64_t k = kr + j;
+          const int64_t ja = k - ka;
+          if (!za && ja >= 0 && ja < nbi) continue;
+          const C ra = br[j], re = br[nbi + j];
+          acc_bin<T>(c, rw, k, mkc(-ra.x, -ra.y), mkc(-re.x, -re.y), pw.aw, rscale, sdd, srd);
+        }
+      }
+      const double dd = sdd.warp_total();
+      const double rd = srd.warp_total();
+      if (lane == 0) dlogl[i] = pw.cw * (-0.5 * dd + rd);
+      __syncwarp();
     }
-    const double dd = sdd.warp_total();
-    const double rd = srd.warp_total();
-    if (lane == 0) dlogl[i] = pw.cw * (-0.5 * dd + rd);
     __syncwarp();
   }
 }
@@ -205,45 +246,59 @@ k_addsub(const gbk_ctx c, const double* __restrict__ params, const int32_t* __re
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
-  C* b0 = reinterpret_cast<C*>(smem_raw) + (size_t)wid * 4 * NMAX;
+  unsigned char* mine = smem_raw + (size_t)wid * warp_bytes<T>(NMAX, 2, 32);
+  C* b0 = reinterpret_cast<C*>(mine);
   C* b1 = b0 + 2 * NMAX;
+  Src<T>* srcs = reinterpret_cast<Src<T>*>(b1 + 2 * NMAX);
+  int* meta = reinterpret_cast<int*>(srcs + 32);   // N in [0,32); walker kept in registers of lane q
   const int wpc = blockDim.x >> 5;
-  const int64_t stride_w = (int64_t)gridDim.x * wpc;
+  const int64_t stride_w = (int64_t)gridDim.x * wpc * 32;
   const int64_t nbins = c.grid.n_bins;
   const T gs = (T)ldexp(1.0, frac_bits - kStrainExp);
-  for (int64_t i = (int64_t)blockIdx.x * wpc + wid; i < n; i += stride_w) {
-    const int nbi = nb[i];
-    const int w = walker[i];
-    if (nbi > NMAX || band_index(nbi) < 0 || w < 0 || w >= n_walkers) {
-      if (lane == 0) atomicOr(c.err, (w < 0 || w >= n_walkers) ? kErrWalker : kErrBand);
-      continue;
+  for (int64_t base = ((int64_t)blockIdx.x * wpc + wid) * 32; base < n; base += stride_w) {
+    const int64_t me = base + lane;
+    int my_w = -1;
+    if (me < n) {
+      const int nbi = nb[me];
+      meta[lane] = nbi;
+      my_w = walker[me];
+      if (nbi <= NMAX && band_index(nbi) >= 0) srcs[lane] = make_src<T>(params, n, me, c.grid.tobs, nbi);
     }
-    const Src<T> s = make_src<T>(params, n, i, c.grid.tobs, nbi);
-    if (s.zero) continue;
-    const int64_t k = s.q - nbi / 2 - c.grid.k0;
-    if (k < 0 || k + nbi > nbins) {
-      if (lane == 0) atomicOr(c.err, kErrRange);
-      continue;
-    }
-    gen_any<T, NMAX>(c, s, nbi, b0, b1, lane);
-    unsigned long long* rw = reinterpret_cast<unsigned long long*>(resid) + (int64_t)w * 2 * nbins * 2;
-    for (int j = lane; j < nbi; j += 32) {
-      for (int ch = 0; ch < 2; ++ch) {
-        const C h = b0[ch * nbi + j];
-        long long hx = to_grid(h.x, gs), hy = to_grid(h.y, gs);
-        if (sign > 0) { hx = -hx; hy = -hy; }   // template enters the model: R -= h
-        unsigned long long* dst = rw + 2 * (ch * nbins + k + j);
-        atomicAdd(dst, (unsigned long long)hx);
-        atomicAdd(dst + 1, (unsigned long long)hy);
+    __syncwarp();
+    const int cnt = (int)min((int64_t)32, n - base);
+    for (int q = 0; q < cnt; ++q) {
+      const int nbi = meta[q];
+      const int w = __shfl_sync(0xffffffffu, my_w, q);
+      if (nbi > NMAX || band_index(nbi) < 0 || w < 0 || w >= n_walkers) {
+        if (lane == 0) atomicOr(c.err, (w < 0 || w >= n_walkers) ? kErrWalker : kErrBand);
+        continue;
       }
+      const Src<T>* s = &srcs[q];
+      if (s->zero) continue;
+      const int64_t k = s->q - nbi / 2 - c.grid.k0;
+      if (k < 0 || k + nbi > nbins) {
+        if (lane == 0) atomicOr(c.err, kErrRange);
+        continue;
+      }
+      gen_any<T, NMAX>(c, s, nbi, b0, b1, lane);
+      unsigned long long* rw = reinterpret_cast<unsigned long long*>(resid) + (int64_t)w * 2 * nbins * 2;
+      for (int j = lane; j < nbi; j += 32) {
+        for (int ch = 0; ch < 2; ++ch) {
+          const C h = b0[ch * nbi + j];
+          long long hx = to_grid(h.x, gs), hy = to_grid(h.y, gs);
+          if (sign > 0) { hx = -hx; hy = -hy; }   // template enters the model: R -= h
+          unsigned long long* dst = rw + 2 * (ch * nbins + k + j);
+          atomicAdd(dst, (unsigned long long)hx);
+          atomicAdd(dst + 1, (unsigned long long)hy);
+        }
+      }
+      __syncwarp();
     }
     __syncwarp();
   }
 }
 
 // ---------------------------------------------------------------- launch helpers
-template <typename T>
-size_t warp_smem(int nmax, int nbuf) { return (size_t)nbuf * 2 * nmax * sizeof(typename CT<T>::C); }
 
 // Warps per CTA: up to kWarpsPerCta, fewer when a warp's buffers are large.
 static int warps_for(size_t per_warp) {
@@ -284,13 +339,13 @@ template <typename T>
 static gbk_status waveform_t(gbk_ctx* ctx, const double* params, const int32_t* nb, int nmax, int64_t n,
                              int64_t* ks, void* ha, void* he, const int64_t* off, cudaStream_t st) {
   typedef typename CT<T>::C C;
-  const size_t pw = warp_smem<T>(nmax, 2);
+  const size_t pw = warp_bytes<T>(nmax, 2, 32);
   int grid = 0, thr = 0;
   size_t smem = 0;
   gbk_status s = GBK_OK;
 #define GBK_WF(NM)                                                                              \
   case NM:                                                                                      \
-    s = launch_cfg(k_waveform<T, NM>, pw, n, &grid, &thr, &smem);                               \
+    s = launch_cfg(k_waveform<T, NM>, pw, (n + 31) / 32, &grid, &thr, &smem);                               \
     if (s) return s;                                                                            \
     k_waveform<T, NM><<<grid, thr, smem, st>>>(*ctx, params, nb, n, ks, (C*)ha, (C*)he, off);   \
     break;
@@ -303,13 +358,13 @@ template <typename T>
 static gbk_status dlogl_t(gbk_ctx* ctx, const double* pn, const double* po, const int32_t* nb, int nmax,
                           const int32_t* walker, int64_t n, const gbk_residual* R, const gbk_psd* psd,
                           double* out, cudaStream_t st) {
-  const size_t pw = warp_smem<T>(nmax, 3);
+  const size_t pw = warp_bytes<T>(nmax, 3, 32);
   int grid = 0, thr = 0;
   size_t smem = 0;
   gbk_status s = GBK_OK;
 #define GBK_DL(NM)                                                                                      \
   case NM:                                                                                              \
-    s = launch_cfg(k_dlogl<T, NM>, pw, n, &grid, &thr, &smem);                                          \
+    s = launch_cfg(k_dlogl<T, NM>, pw, (n + 15) / 16, &grid, &thr, &smem);                                          \
     if (s) return s;                                                                                    \
     k_dlogl<T, NM><<<grid, thr, smem, st>>>(*ctx, pn, po, nb, walker, n,                                \
                                                           (const long long*)R->data, R->n_walkers,      \
@@ -323,13 +378,13 @@ static gbk_status dlogl_t(gbk_ctx* ctx, const double* pn, const double* po, cons
 template <typename T>
 static gbk_status addsub_t(gbk_ctx* ctx, const gbk_residual* R, const double* params, const int32_t* nb,
                            int nmax, const int32_t* walker, int64_t n, int sign, cudaStream_t st) {
-  const size_t pw = warp_smem<T>(nmax, 2);
+  const size_t pw = warp_bytes<T>(nmax, 2, 32);
   int grid = 0, thr = 0;
   size_t smem = 0;
   gbk_status s = GBK_OK;
 #define GBK_AS(NM)                                                                               \
   case NM:                                                                                       \
-    s = launch_cfg(k_addsub<T, NM>, pw, n, &grid, &thr, &smem);                                  \
+    s = launch_cfg(k_addsub<T, NM>, pw, (n + 31) / 32, &grid, &thr, &smem);                                  \
     if (s) return s;                                                                             \
     k_addsub<T, NM><<<grid, thr, smem, st>>>(*ctx, params, nb, walker, n,                        \
                                                            (long long*)R->data, R->n_walkers,    \

@@ -1,0 +1,954 @@
+// Ensemble sweep of the GB sampler: band windows, in-model + flip-all RJ per band
+// (Alg. 1, App. C), ensemble-permuted tempering swaps (Alg. 2, Eq. temp-final).
+#include <math.h>
+#include <stdlib.h>
+
+#include "gbk_internal.cuh"
+#include "gbk_philox.cuh"
+#include "gbk_reduce.cuh"
+#include "gbk_wave.cuh"
+
+struct gbk_sweep {
+  gbk_ctx* ctx;
+  gbk_sweep_desc d;
+  int n_bp_max;         // bands of the larger parity
+  long long* rsnap;     // residual snapshot [W][2][n_bins][2]
+  void* rho;            // opened windows [W][n_bp_max][2][3N], complex of the sweep precision
+  void* wcache;         // current waveform of every slot [T][W][B][n_max][2][N]
+  size_t rho_bytes, cache_bytes;
+};
+
+namespace gbk {
+
+constexpr int kSwWarps = 4;
+constexpr int kMaxSlots = 64;
+
+struct SweepArgs {
+  gbk_ctx c;
+  gbk_sweep_desc d;
+  double* params;
+  uint8_t* exists;
+  const double* betas;
+  long long* resid;       // live cold-chain residual (updated)
+  const long long* rsnap; // snapshot taken at the start of the half sweep
+  void* rho;
+  void* wcache;
+  int n_bp_max;
+  int32_t n_walkers_r;
+  int32_t frac_bits;
+  const double* psdp;
+  int32_t npsd;
+  uint32_t k0, k1, sweep;
+  int parity;
+  gbk_trace_rec* trace;
+  int32_t trace_cap;
+  int32_t* trace_count;
+  long long* stats;
+};
+
+template <typename T> __device__ __forceinline__ const T* orb_of(const gbk_ctx& c, int bi);
+template <> __device__ __forceinline__ const float* orb_of<float>(const gbk_ctx& c, int bi) { return c.orb_f[bi]; }
+template <> __device__ __forceinline__ const double* orb_of<double>(const gbk_ctx& c, int bi) { return c.orb_d[bi]; }
+template <typename T> __device__ __forceinline__ const typename CT<T>::C* tw_of(const gbk_ctx& c, int bi);
+template <> __device__ __forceinline__ const float2* tw_of<float>(const gbk_ctx& c, int bi) { return c.tw_f[bi]; }
+template <> __device__ __forceinline__ const double2* tw_of<double>(const gbk_ctx& c, int bi) { return c.tw_d[bi]; }
+__device__ __forceinline__ float iqv(const gbk_ctx& c, int64_t k, float) { return __ldg(&c.iq_f[k]); }
+__device__ __forceinline__ double iqv(const gbk_ctx& c, int64_t k, double) { return __ldg(&c.iq_d[k]); }
+__device__ __forceinline__ float rhov(const gbk_ctx& c, int64_t k, float) { return __ldg(&c.rho_f[k]); }
+__device__ __forceinline__ double rhov(const gbk_ctx& c, int64_t k, double) { return __ldg(&c.rho_d[k]); }
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float i2t(long long v, float) { return __ll2float_rn(v); }
+__device__ __forceinline__ double i2t(long long v, double) { return __ll2double_rn(v); }
+__device__ __forceinline__ long long t2grid(float v, float s) { return __float2ll_rn(v * s); }
+__device__ __forceinline__ long long t2grid(double v, double s) { return __double2ll_rn(v * s); }
+template <typename T> struct SAcc;
+template <> struct SAcc<float> { typedef CompF S; };
+template <> struct SAcc<double> { typedef PlainD S; };
+
+__device__ __forceinline__ double nan_d() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+// -------------------------------------------------------------- prior and proposals
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+
+__device__ __forceinline__ void allowance(const gbk_sweep_desc& d, double tobs, int b, double& lo, double& hi) {
+  const long long lob = d.band_k0 + (long long)b * d.band_bins;
+  const long long hib = lob + d.band_bins;
+  const double half = 0.5 * d.band_bins;
+  lo = __ddiv_rn(dsub((double)lob, half), tobs);
+  hi = __ddiv_rn(dadd((double)hib, half), tobs);
+  if (lo < d.f_min) lo = d.f_min;
+  if (hi > d.f_max) hi = d.f_max;
+}
+
+__device__ __forceinline__ double chirp_mass(double f0, double fd) {
+  const double K = 96.0 / 5.0 * 21.170591578193026;  // pi^(8/3)
+  return pow(fd / (K * pow(f0, 11.0 / 3.0)), 0.6) / 4.925490947e-6;
+}
+
+__device__ __forceinline__ bool in_support(const gbk_sweep_desc& d, double tobs, int b, const double* th) {
+  double lo, hi;
+  allowance(d, tobs, b, lo, hi);
+  if (!(th[1] >= lo && th[1] < hi)) return false;
+  if (!(th[0] > 0.0)) return false;
+  const double la = log(th[0]);
+  if (!(la >= d.ln_a_min && la <= d.ln_a_max)) return false;
+  if (!(th[5] >= -1.0 && th[5] <= 1.0 && th[6] >= -1.0 && th[6] <= 1.0)) return false;
+  if (!(th[2] > 0.0)) return false;
+  const double mc = chirp_mass(th[1], th[2]);
+  return mc >= d.mc_min && mc <= d.mc_max;
+}
+
+__device__ __forceinline__ double log_prior_shape(const double* th) {
+  return dsub(dmul(-0.4, log(th[2])), dmul(2.2, log(th[1])));
+}
+
+__device__ __forceinline__ double wrap(double x, double period) {
+  if (x >= period) return dsub(x, period);
+  if (x < 0.0) return dadd(x, period);
+  return x;
+}
+
+// In-model proposal from the 48 words of proposal j (word 0 picks the source).
+__device__ __forceinline__ void propose(const gbk_sweep_desc& d, const double* th, const uint32_t* w, double* nw) {
+  double z[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const double s4 = dadd(dadd(dadd(u24(w[1 + 4 * c]), u24(w[2 + 4 * c])), u24(w[3 + 4 * c])), u24(w[4 + 4 * c]));
+    z[c] = dmul(dsub(s4, 2.0), 1.7320508075688772);
+  }
+  const double TWO_PI = 6.283185307179586, PI = 3.141592653589793;
+  nw[0] = exp(dadd(log(th[0]), dmul(d.sigma[0], z[0])));
+  nw[1] = dadd(th[1], dmul(d.sigma[1], z[1]));
+  nw[2] = dadd(th[2], dmul(d.sigma[2], z[2]));
+  nw[3] = wrap(dadd(th[3], dmul(d.sigma[3], z[3])), TWO_PI);
+  nw[4] = wrap(dadd(th[4], dmul(d.sigma[4], z[4])), PI);
+  nw[5] = dadd(th[5], dmul(d.sigma[5], z[5]));
+  nw[6] = dadd(th[6], dmul(d.sigma[6], z[6]));
+  nw[7] = wrap(dadd(th[7], dmul(d.sigma[7], z[7])), TWO_PI);
+}
+
+// Prior draw of a new source in band b from 8 words.
+__device__ __forceinline__ void draw_birth(const gbk_sweep_desc& d, double tobs, int b, const uint32_t* w, double* nw) {
+  double lo, hi;
+  allowance(d, tobs, b, lo, hi);
+  const double TWO_PI = 6.283185307179586, PI = 3.141592653589793;
+  const double f0 = dadd(lo, dmul(dsub(hi, lo), u32(w[0])));
+  nw[1] = f0;
+  nw[0] = exp(dadd(d.ln_a_min, dmul(dsub(d.ln_a_max, d.ln_a_min), u32(w[1]))));
+  const double mc = dadd(d.mc_min, dmul(dsub(d.mc_max, d.mc_min), u32(w[2])));
+  const double K = 96.0 / 5.0 * 21.170591578193026;
+  nw[2] = K * pow(f0, 11.0 / 3.0) * pow(mc * 4.925490947e-6, 5.0 / 3.0);
+  nw[3] = dmul(TWO_PI, u32(w[3]));
+  nw[4] = dmul(PI, u32(w[4]));
+  nw[5] = dsub(dmul(2.0, u32(w[5])), 1.0);
+  nw[6] = dsub(dmul(2.0, u32(w[6])), 1.0);
+  nw[7] = dmul(TWO_PI, u32(w[7]));
+}
+
+// Lanes compute Philox blocks c0 = base + m (m < nblk) into words[4m .. 4m+3].
+__device__ __forceinline__ void fill_words(uint32_t* words, int nblk, uint32_t base, uint32_t c1, uint32_t c2,
+                                           uint32_t c3, uint32_t k0, uint32_t k1, int lane) {
+  for (int m = lane; m < nblk; m += 32) {
+    const U4 v = philox4x32_10(base + m, c1, c2, c3, k0, k1);
+    words[4 * m] = v.x; words[4 * m + 1] = v.y; words[4 * m + 2] = v.z; words[4 * m + 3] = v.w;
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void record(const SweepArgs& a, int kind, int t, int w, int b, int slot, int seq,
+                                       bool acc, double dll, double la, const double* th) {
+  if (a.stats) {
+    atomicAdd((unsigned long long*)&a.stats[2 * kind], 1ull);
+    if (acc) atomicAdd((unsigned long long*)&a.stats[2 * kind + 1], 1ull);
+  }
+  if (a.trace_count) {
+    const int i = atomicAdd(a.trace_count, 1);
+    if (a.trace && i < a.trace_cap) {
+      gbk_trace_rec& r = a.trace[i];
+      r.kind = kind; r.t = t; r.w = w; r.b = b; r.slot = slot; r.seq = seq; r.accepted = acc ? 1 : 0;
+      r.parity = a.parity; r.dlogl = dll; r.log_alpha = la;
+      for (int c = 0; c < 8; ++c) r.params[c] = th ? th[c] : 0.0;
+    }
+  }
+}
+
+// -------------------------------------------------------------- band-window pieces
+template <typename T>
+struct PsdWt {
+  double cw;
+  T aw;
+};
+template <typename T>
+__device__ __forceinline__ PsdWt<T> walker_psd(const SweepArgs& a, int w) {
+  const int j = (a.npsd == 1) ? 0 : w;
+  const double so = a.psdp[2 * j] * a.psdp[2 * j], sa = a.psdp[2 * j + 1] * a.psdp[2 * j + 1];
+  PsdWt<T> r;
+  r.cw = 4.0 / a.c.grid.tobs / so;
+  r.aw = (T)(sa / so);
+  return r;
+}
+
+__device__ __forceinline__ int64_t slot_index(const gbk_sweep_desc& d, int t, int w, int b) {
+  return (((int64_t)t * d.n_walkers + w) * d.n_bands + b) * d.n_max;
+}
+template <typename T>
+__device__ __forceinline__ typename CT<T>::C* cache_ptr(const SweepArgs& a, int64_t slot) {
+  return reinterpret_cast<typename CT<T>::C*>(a.wcache) + slot * 2 * a.d.band_bins;
+}
+template <typename T>
+__device__ __forceinline__ typename CT<T>::C* rho_ptr(const SweepArgs& a, int w, int j) {
+  typedef typename CT<T>::C C;
+  return reinterpret_cast<C*>(a.rho) + ((int64_t)w * a.n_bp_max + j) * 2 * 3 * a.d.band_bins;
+}
+// window offset of a template's band: bins [q - N/2, q + N/2) relative to window start gw
+template <int N>
+__device__ __forceinline__ int band_off(long long q, int64_t gw, const gbk_ctx& c) {
+  return (int)(q - N / 2 - (gw + c.grid.k0));
+}
+// window offset of a cached template (its q from its f0)
+template <int N>
+__device__ __forceinline__ int cached_off(const double* th, int64_t gw, const gbk_ctx& c) {
+  return band_off<N>((long long)floor(th[1] * c.grid.tobs), gw, c);
+}
+
+// Delta lnL of swapping template r (br, window offset orr) for a (ba, offset oa) against
+// the window residual rw ([2][3N]); either may be absent. Window bin i is grid bin gw + i.
+template <typename T, int N>
+__device__ double window_dll(const SweepArgs& a, const typename CT<T>::C* rw, const typename CT<T>::C* ba, int oa,
+                             const typename CT<T>::C* br, int orr, int64_t gw, const PsdWt<T>& pw, int lane) {
+  typedef typename CT<T>::C C;
+  constexpr int W3 = 3 * N;
+  typename SAcc<T>::S sdd, srd;
+  sdd.init();
+  srd.init();
+  auto bin = [&](int i, C da, C de) {
+    const int64_t k = gw + i;
+    const T wt = iqv(a.c, k, T()) * recip((T)1 + pw.aw * rhov(a.c, k, T()));
+    const C ra = rw[i], re = rw[W3 + i];
+    sdd.add(wt * (da.x * da.x + da.y * da.y + de.x * de.x + de.y * de.y));
+    srd.add(wt * (ra.x * da.x + ra.y * da.y + re.x * de.x + re.y * de.y));
+  };
+  if (ba) {
+    for (int j = lane; j < N; j += 32) {
+      const int i = oa + j;
+      C xa = ba[j], xe = ba[N + j];
+      const int jr = i - orr;
+      if (br && jr >= 0 && jr < N) { xa = csub(xa, br[jr]); xe = csub(xe, br[N + jr]); }
+      bin(i, xa, xe);
+    }
+  }
+  if (br) {
+    for (int j = lane; j < N; j += 32) {
+      const int i = orr + j;
+      const int ja = i - oa;
+      if (ba && ja >= 0 && ja < N) continue;
+      const C xa = br[j], xe = br[N + j];
+      bin(i, mkc(-xa.x, -xa.y), mkc(-xe.x, -xe.y));
+    }
+  }
+  const double dd = sdd.warp_total();
+  const double rd = srd.warp_total();
+  return pw.cw * (-0.5 * dd + rd);
+}
+
+// r' <- r' - a + r over the window; for the cold chain also R <- R - round(a) + round(r).
+template <typename T, int N>
+__device__ void apply_change(const SweepArgs& a, typename CT<T>::C* rw, const typename CT<T>::C* ba, int oa,
+                             const typename CT<T>::C* br, int orr, bool cold, long long* rglob, int64_t gw, T gs,
+                             int lane) {
+  constexpr int W3 = 3 * N;
+  const int64_t nb = a.c.grid.n_bins;
+  if (ba) {
+    for (int j = lane; j < N; j += 32) {
+      rw[oa + j] = csub(rw[oa + j], ba[j]);
+      rw[W3 + oa + j] = csub(rw[W3 + oa + j], ba[N + j]);
+    }
+    __syncwarp();
+  }
+  if (br) {
+    for (int j = lane; j < N; j += 32) {
+      rw[orr + j] = cadd(rw[orr + j], br[j]);
+      rw[W3 + orr + j] = cadd(rw[W3 + orr + j], br[N + j]);
+    }
+    __syncwarp();
+  }
+  if (cold) {
+    unsigned long long* R = reinterpret_cast<unsigned long long*>(rglob);
+    for (int j = lane; j < N; j += 32) {
+      for (int ch = 0; ch < 2; ++ch) {
+        if (ba) {
+          const typename CT<T>::C h = ba[ch * N + j];
+          unsigned long long* dst = R + 2 * (ch * nb + gw + oa + j);
+          atomicAdd(dst, (unsigned long long)(-t2grid(h.x, gs)));
+          atomicAdd(dst + 1, (unsigned long long)(-t2grid(h.y, gs)));
+        }
+        if (br) {
+          const typename CT<T>::C h = br[ch * N + j];
+          unsigned long long* dst = R + 2 * (ch * nb + gw + orr + j);
+          atomicAdd(dst, (unsigned long long)t2grid(h.x, gs));
+          atomicAdd(dst + 1, (unsigned long long)t2grid(h.y, gs));
+        }
+      }
+    }
+  }
+}
+
+template <typename C>
+__device__ __forceinline__ void copy_band(C* dst, const C* src, int n2, int lane) {
+  for (int i = lane; i < n2; i += 32) dst[i] = src[i];
+}
+
+// -------------------------------------------------------------- cache refresh
+// Regenerate the cached waveform of every present slot (32 slots per warp batch).
+template <typename T, int N>
+__global__ void __launch_bounds__(kSwWarps * 32) k_refresh(const SweepArgs a) {
+  typedef typename CT<T>::C C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned char* mine = smem_raw + (size_t)wid * (4 * N * sizeof(C) + 32 * sizeof(Src<T>) + 128);  // refresh_warp_bytes
+  C* b0 = reinterpret_cast<C*>(mine);
+  C* b1 = b0 + 2 * N;
+  Src<T>* srcs = reinterpret_cast<Src<T>*>(b1 + 2 * N);
+  int* ok = reinterpret_cast<int*>(srcs + 32);
+  const gbk_sweep_desc& d = a.d;
+  const int64_t nslot = (int64_t)d.n_temps * d.n_walkers * d.n_bands * d.n_max;
+  const T* orb = orb_of<T>(a.c, band_index(N));
+  const C* tw = tw_of<T>(a.c, band_index(N));
+  const int wpc = blockDim.x >> 5;
+  for (int64_t base = ((int64_t)blockIdx.x * wpc + wid) * 32; base < nslot;
+       base += (int64_t)gridDim.x * wpc * 32) {
+    const int64_t me = base + lane;
+    ok[lane] = (me < nslot && a.exists[me]) ? 1 : 0;
+    if (ok[lane]) srcs[lane] = make_src<T>(a.params + me * 8, 1, 0, a.c.grid.tobs, N);
+    __syncwarp();
+    for (int q = 0; q < 32; ++q) {
+      if (!ok[q]) continue;
+      gen_band<T, N>(&srcs[q], orb, tw, a.c.grid.tobs, b0, b1, lane);
+      copy_band(cache_ptr<T>(a, base + q), b0, 2 * N, lane);
+      __syncwarp();
+    }
+    __syncwarp();
+  }
+}
+
+// -------------------------------------------------------------- open pass
+// rho_{w,b} = snapshot residual on b's window + band b's cold-chain sources (cached).
+template <typename T, int N>
+__global__ void __launch_bounds__(kSwWarps * 32) k_open(const SweepArgs a) {
+  typedef typename CT<T>::C C;
+  constexpr int W3 = 3 * N;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const gbk_sweep_desc& d = a.d;
+  const int nbp = (d.n_bands - a.parity + 1) / 2;
+  const int64_t ntask = (int64_t)d.n_walkers * nbp;
+  const int64_t nb = a.c.grid.n_bins;
+  const T rs = (T)ldexp(1.0, kStrainExp - a.frac_bits);
+  for (int64_t x = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; x < ntask; x += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+    const int w = (int)(x / nbp), j = (int)(x % nbp);
+    const int b = a.parity + 2 * j;
+    const int64_t gw = d.band_k0 + (int64_t)(b - 1) * N - a.c.grid.k0;
+    C* rho = rho_ptr<T>(a, w, j);
+    const long long* rs_w = a.rsnap + (int64_t)w * 2 * nb * 2;
+    for (int i = lane; i < W3; i += 32)
+      for (int ch = 0; ch < 2; ++ch) {
+        const longlong2 v = *reinterpret_cast<const longlong2*>(rs_w + 2 * (ch * nb + gw + i));
+        rho[ch * W3 + i] = mkc(i2t(v.x, T()) * rs, i2t(v.y, T()) * rs);
+      }
+    __syncwarp();
+    const int64_t base = slot_index(d, 0, w, b);
+    for (int s = 0; s < d.n_max; ++s) {
+      if (!a.exists[base + s]) continue;
+      const C* h = cache_ptr<T>(a, base + s);
+      const int o = cached_off<N>(a.params + (base + s) * 8, gw, a.c);
+      for (int i = lane; i < N; i += 32) {
+        rho[o + i] = cadd(rho[o + i], h[i]);
+        rho[W3 + o + i] = cadd(rho[W3 + o + i], h[N + i]);
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// -------------------------------------------------------------- band task
+// Per-warp shared memory of k_band.
+template <typename T, int N>
+struct BandSmem {
+  typename CT<T>::C rw[2 * 3 * N];     // r' on the window
+  typename CT<T>::C ba[2 * N], bs[2 * N];
+  Src<T> src[32];                      // constants of the batch's new templates
+  double th[32][8];                    // proposed parameters
+  double lpn[32], lu[32];              // log prior shape of the proposal, ln u
+  double lp[kMaxSlots];                // log prior shape of every slot's current parameters
+  int k[32], supp[32];
+  int list[kMaxSlots];
+};
+
+// Set up proposal j (lane-parallel): words, source, perturbation, support, prior, constants.
+template <typename T, int N>
+__device__ void prep_inmodel(const SweepArgs& a, BandSmem<T, N>& S, int l, int jp, uint32_t tid, int g,
+                             const double* P, int b) {
+  const gbk_sweep_desc& d = a.d;
+  uint32_t w[48];
+#pragma unroll
+  for (int m = 0; m < 12; ++m) {
+    const U4 v = philox4x32_10(12u * jp + m, tid, 0u | ((uint32_t)a.parity << 4), a.sweep, a.k0, a.k1);
+    w[4 * m] = v.x; w[4 * m + 1] = v.y; w[4 * m + 2] = v.z; w[4 * m + 3] = v.w;
+  }
+  const int k = S.list[ranged(w[0], (uint32_t)g)];
+  double th[8], nw[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) th[c] = P[k * 8 + c];
+  propose(d, th, w, nw);
+  const double u = u53(w[33], w[34]);
+  S.lu[l] = u > 0.0 ? log(u) : -INFINITY;
+  S.k[l] = k;
+  const bool ok = in_support(d, a.c.grid.tobs, b, nw);
+  S.supp[l] = ok ? 1 : 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) S.th[l][c] = nw[c];
+  if (ok) {
+    S.lpn[l] = log_prior_shape(nw);
+    S.src[l] = make_src<T>(nw, 1, 0, a.c.grid.tobs, N);
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int flags) {
+  typedef typename CT<T>::C C;
+  constexpr int W3 = 3 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  BandSmem<T, N>& S = reinterpret_cast<BandSmem<T, N>*>(smem_raw)[wid];
+  const gbk_sweep_desc& d = a.d;
+  const int nbp = (d.n_bands - a.parity + 1) / 2;
+  const int64_t ntask = (int64_t)d.n_temps * d.n_walkers * nbp;
+  const int64_t nb = a.c.grid.n_bins;
+  const double tobs = a.c.grid.tobs;
+  const T rs = (T)ldexp(1.0, kStrainExp - a.frac_bits);
+  const T gs = (T)ldexp(1.0, a.frac_bits - kStrainExp);
+  const T* orb = orb_of<T>(a.c, band_index(N));
+  const C* tw = tw_of<T>(a.c, band_index(N));
+  for (int64_t x = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; x < ntask; x += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+    const int t = (int)(x / ((int64_t)d.n_walkers * nbp));
+    const int rem = (int)(x % ((int64_t)d.n_walkers * nbp));
+    const int w = rem / nbp, j = rem % nbp;
+    const int b = a.parity + 2 * j;
+    const int64_t gw = d.band_k0 + (int64_t)(b - 1) * N - a.c.grid.k0;
+    const int64_t base = slot_index(d, t, w, b);
+    double* P = a.params + base * 8;
+    uint8_t* E = a.exists + base;
+    const double beta = a.betas[(int64_t)b * d.n_temps + t];
+    const uint32_t tid = (uint32_t)(((int64_t)t * d.n_walkers + w) * d.n_bands + b);
+    const PsdWt<T> pw = walker_psd<T>(a, w);
+    const bool cold = (t == 0);
+    long long* Rw = a.resid + (int64_t)w * 2 * nb * 2;
+    // r' for the band: cold chain from the snapshot; hotter chains from the opened window
+    // minus their own (cached) templates
+    if (cold) {
+      const long long* rs_w = a.rsnap + (int64_t)w * 2 * nb * 2;
+      for (int i = lane; i < W3; i += 32)
+        for (int ch = 0; ch < 2; ++ch) {
+          const longlong2 v = *reinterpret_cast<const longlong2*>(rs_w + 2 * (ch * nb + gw + i));
+          S.rw[ch * W3 + i] = mkc(i2t(v.x, T()) * rs, i2t(v.y, T()) * rs);
+        }
+      __syncwarp();
+    } else {
+      const C* rho = rho_ptr<T>(a, w, j);
+      for (int i = lane; i < 2 * W3; i += 32) S.rw[i] = rho[i];
+      __syncwarp();
+      for (int s = 0; s < d.n_max; ++s) {
+        if (!E[s]) continue;
+        const C* h = cache_ptr<T>(a, base + s);
+        const int o = cached_off<N>(P + s * 8, gw, a.c);
+        for (int i = lane; i < N; i += 32) {
+          S.rw[o + i] = csub(S.rw[o + i], h[i]);
+          S.rw[W3 + o + i] = csub(S.rw[W3 + o + i], h[N + i]);
+        }
+        __syncwarp();
+      }
+    }
+    // log prior shape of the present slots (lane-parallel float64)
+    for (int s = lane; s < d.n_max; s += 32)
+      if (E[s]) S.lp[s] = log_prior_shape(P + s * 8);
+    // ---- in-model proposals (Alg. 1)
+    if (flags & GBK_SWEEP_INMODEL) {
+      if (lane == 0) {
+        int g = 0;
+        for (int s = 0; s < d.n_max; ++s)
+          if (E[s]) S.list[g++] = s;
+        S.list[kMaxSlots - 1] = g;
+      }
+      __syncwarp();
+      const int g = S.list[kMaxSlots - 1];
+      const int n_prop = (int)rint(d.props_per_source * (double)g);
+      for (int j0 = 0; j0 < n_prop; j0 += 32) {
+        const int cnt = min(32, n_prop - j0);
+        if (lane < cnt) prep_inmodel<T, N>(a, S, lane, j0 + lane, tid, g, P, b);
+        __syncwarp();
+        for (int q = 0; q < cnt; ++q) {
+          const int jp = j0 + q;
+          const int k = S.k[q];
+          if (!S.supp[q]) {
+            if (lane == 0) record(a, 0, t, w, b, k, jp, false, nan_d(), -INFINITY, S.th[q]);
+            continue;
+          }
+          gen_band<T, N>(&S.src[q], orb, tw, tobs, S.ba, S.bs, lane);
+          const C* hr = cache_ptr<T>(a, base + k);
+          const int oa = band_off<N>(S.src[q].q, gw, a.c);
+          const int orr = cached_off<N>(P + k * 8, gw, a.c);
+          const double dll = window_dll<T, N>(a, S.rw, S.ba, oa, hr, orr, gw, pw, lane);
+          const double la = beta * dll + S.lpn[q] - S.lp[k];
+          const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
+          if (lane == 0) record(a, 0, t, w, b, k, jp, acc, dll, la, S.th[q]);
+          if (acc) {
+            apply_change<T, N>(a, S.rw, S.ba, oa, hr, orr, cold, Rw, gw, gs, lane);
+            __syncwarp();
+            copy_band(cache_ptr<T>(a, base + k), S.ba, 2 * N, lane);
+            if (lane < 8) P[k * 8 + lane] = S.th[q][lane];
+            if (lane == 0) S.lp[k] = S.lpn[q];
+            __syncwarp();
+            // later proposals of this batch that move the same source start from the new state
+            if (lane > q && lane < cnt && S.k[lane] == k) prep_inmodel<T, N>(a, S, lane, j0 + lane, tid, g, P, b);
+          }
+          __syncwarp();
+        }
+      }
+    }
+    // ---- flip-all reversible jump (App. C)
+    if ((flags & GBK_SWEEP_RJ) && d.n_max > 0) {
+      if (lane == 0) {
+        uint32_t buf[4];
+        int wi = 4, blk = 0;
+        for (int s = 0; s < d.n_max; ++s) S.list[s] = s;
+        for (int i = d.n_max - 1; i > 0; --i) {
+          if (wi == 4) {
+            const U4 v = philox4x32_10((uint32_t)blk++, tid, 1u | ((uint32_t)a.parity << 4), a.sweep, a.k0, a.k1);
+            buf[0] = v.x; buf[1] = v.y; buf[2] = v.z; buf[3] = v.w;
+            wi = 0;
+          }
+          const int jx = (int)ranged(buf[wi++], (uint32_t)(i + 1));
+          const int tmp = S.list[i]; S.list[i] = S.list[jx]; S.list[jx] = tmp;
+        }
+      }
+      __syncwarp();
+      for (int j0 = 0; j0 < d.n_max; j0 += 32) {
+        const int cnt = min(32, d.n_max - j0);
+        // lane-parallel set-up: uniform for the decision and, for empty slots, the prior draw
+        if (lane < cnt) {
+          const int jp = j0 + lane;
+          const int s = S.list[jp];
+          uint32_t wv[16];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const U4 v = philox4x32_10(4u * jp + m, tid, 2u | ((uint32_t)a.parity << 4), a.sweep, a.k0, a.k1);
+            wv[4 * m] = v.x; wv[4 * m + 1] = v.y; wv[4 * m + 2] = v.z; wv[4 * m + 3] = v.w;
+          }
+          const double u = u53(wv[8], wv[9]);
+          S.lu[lane] = u > 0.0 ? log(u) : -INFINITY;
+          S.k[lane] = s;
+          if (!E[s]) {
+            double nw[8];
+            draw_birth(d, tobs, b, wv, nw);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) S.th[lane][c] = nw[c];
+            S.src[lane] = make_src<T>(nw, 1, 0, tobs, N);
+          }
+        }
+        __syncwarp();
+        for (int q = 0; q < cnt; ++q) {
+          const int jp = j0 + q;
+          const int s = S.k[q];
+          if (E[s]) {
+            const C* hr = cache_ptr<T>(a, base + s);
+            const int orr = cached_off<N>(P + s * 8, gw, a.c);
+            const double dll = window_dll<T, N>(a, S.rw, (const C*)nullptr, 0, hr, orr, gw, pw, lane);
+            const double la = beta * dll - d.log_occ_odds;
+            const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
+            if (lane == 0) record(a, 2, t, w, b, s, jp, acc, dll, la, P + s * 8);
+            if (acc) {
+              apply_change<T, N>(a, S.rw, (const C*)nullptr, 0, hr, orr, cold, Rw, gw, gs, lane);
+              __syncwarp();
+              if (lane == 0) E[s] = 0;
+            }
+          } else {
+            gen_band<T, N>(&S.src[q], orb, tw, tobs, S.ba, S.bs, lane);
+            const int oa = band_off<N>(S.src[q].q, gw, a.c);
+            const double dll = window_dll<T, N>(a, S.rw, S.ba, oa, (const C*)nullptr, 0, gw, pw, lane);
+            const double la = beta * dll + d.log_occ_odds;
+            const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
+            if (lane == 0) record(a, 1, t, w, b, s, jp, acc, dll, la, S.th[q]);
+            if (acc) {
+              apply_change<T, N>(a, S.rw, S.ba, oa, (const C*)nullptr, 0, cold, Rw, gw, gs, lane);
+              copy_band(cache_ptr<T>(a, base + s), S.ba, 2 * N, lane);
+              if (lane < 8) P[s * 8 + lane] = S.th[q][lane];
+              __syncwarp();
+              if (lane == 0) E[s] = 1;
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// -------------------------------------------------------------- tempering (Alg. 2)
+// H <- sum of the band's present (cached) templates on the window.
+template <typename T, int N>
+__device__ void set_sum(const SweepArgs& a, int64_t base, typename CT<T>::C* H, int64_t gw, int lane) {
+  typedef typename CT<T>::C C;
+  constexpr int W3 = 3 * N;
+  for (int i = lane; i < 2 * W3; i += 32) H[i] = mkc((T)0, (T)0);
+  __syncwarp();
+  for (int s = 0; s < a.d.n_max; ++s) {
+    if (!a.exists[base + s]) continue;
+    const C* h = cache_ptr<T>(a, base + s);
+    const int o = cached_off<N>(a.params + (base + s) * 8, gw, a.c);
+    for (int i = lane; i < N; i += 32) {
+      H[o + i] = cadd(H[o + i], h[i]);
+      H[W3 + o + i] = cadd(H[W3 + o + i], h[N + i]);
+    }
+    __syncwarp();
+  }
+}
+
+// <rho - Hx|rho - Hx> - <rho - Hy|rho - Hy> = cw sum_k w_k Re[(Hy - Hx) conj(2 rho - Hx - Hy)],
+// formed bin by bin so the large common parts cancel before summation.
+template <typename T, int N>
+__device__ double set_diff(const SweepArgs& a, const typename CT<T>::C* rho, const typename CT<T>::C* hx,
+                           const typename CT<T>::C* hy, int64_t gw, const PsdWt<T>& pw, int lane) {
+  typedef typename CT<T>::C C;
+  constexpr int W3 = 3 * N;
+  typename SAcc<T>::S acc;
+  acc.init();
+  for (int i = lane; i < W3; i += 32) {
+    const int64_t k = gw + i;
+    const T wt = iqv(a.c, k, T()) * recip((T)1 + pw.aw * rhov(a.c, k, T()));
+    T s = (T)0;
+#pragma unroll
+    for (int ch = 0; ch < 2; ++ch) {
+      const C r = rho[ch * W3 + i], x = hx[ch * W3 + i], y = hy[ch * W3 + i];
+      const C dlt = csub(y, x);
+      const C sm = csub(cscale(r, (T)2), cadd(x, y));
+      s += dlt.x * sm.x + dlt.y * sm.y;
+    }
+    acc.add(wt * s);
+  }
+  return pw.cw * acc.warp_total();
+}
+
+// Move the cached templates of one band into (sign +1: R -= h) or out of (sign -1:
+// R += h) the cold-chain residual, each rounded to the fixed-point grid.
+template <typename T, int N>
+__device__ void cold_update(const SweepArgs& a, int64_t base, int sign, long long* Rw, int lane) {
+  typedef typename CT<T>::C C;
+  const int64_t nb = a.c.grid.n_bins;
+  const T gs = (T)ldexp(1.0, a.frac_bits - kStrainExp);
+  unsigned long long* R = reinterpret_cast<unsigned long long*>(Rw);
+  for (int s = 0; s < a.d.n_max; ++s) {
+    if (!a.exists[base + s]) continue;
+    const C* h = cache_ptr<T>(a, base + s);
+    const int64_t o = (long long)floor(a.params[(base + s) * 8 + 1] * a.c.grid.tobs) - N / 2 - a.c.grid.k0;
+    for (int i = lane; i < N; i += 32)
+      for (int ch = 0; ch < 2; ++ch) {
+        const C v = h[ch * N + i];
+        long long hx = t2grid(v.x, gs), hy = t2grid(v.y, gs);
+        if (sign > 0) { hx = -hx; hy = -hy; }
+        unsigned long long* dst = R + 2 * (ch * nb + o + i);
+        atomicAdd(dst, (unsigned long long)hx);
+        atomicAdd(dst + 1, (unsigned long long)hy);
+      }
+    __syncwarp();
+  }
+}
+
+template <typename T, int N>
+__host__ __device__ constexpr size_t swap_warp_bytes(int nt, int nw) {
+  return (4 * 3 * N * sizeof(typename CT<T>::C) + (size_t)nt * nw * sizeof(short) + 15) / 16 * 16;
+}
+template <typename T, int N>
+__host__ __device__ constexpr size_t refresh_warp_bytes() {
+  return 4 * N * sizeof(typename CT<T>::C) + 32 * sizeof(Src<T>) + 128;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kSwWarps * 32) k_swap(const SweepArgs a) {
+  typedef typename CT<T>::C C;
+  constexpr int W3 = 3 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const gbk_sweep_desc& d = a.d;
+  const int T_ = d.n_temps, W = d.n_walkers;
+  const size_t per_warp = swap_warp_bytes<T, N>(T_, W);
+  C* HA = reinterpret_cast<C*>(smem_raw + (size_t)wid * per_warp);
+  C* HB = HA + 2 * W3;
+  short* perm = reinterpret_cast<short*>(HB + 2 * W3);   // [T][W]
+  const int nbp = (d.n_bands - a.parity + 1) / 2;
+  const int64_t ntask = (int64_t)nbp * W;
+  const int nslotc = 2 * N;
+  for (int64_t x = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; x < ntask; x += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+    const int j = (int)(x / W), c = (int)(x % W);
+    const int b = a.parity + 2 * j;
+    const int64_t gw = d.band_k0 + (int64_t)(b - 1) * N - a.c.grid.k0;
+    // walker permutation of every temperature (Fisher-Yates on Philox words)
+    for (int t = lane; t < T_; t += 32) {
+      short* pt = perm + t * W;
+      for (int i = 0; i < W; ++i) pt[i] = (short)i;
+      uint32_t buf[4];
+      int wi = 4, blk = 0;
+      for (int i = W - 1; i > 0; --i) {
+        if (wi == 4) {
+          const U4 v = philox4x32_10((uint32_t)blk++, (uint32_t)(b * T_ + t), 3u | ((uint32_t)a.parity << 4), a.sweep,
+                                     a.k0, a.k1);
+          buf[0] = v.x; buf[1] = v.y; buf[2] = v.z; buf[3] = v.w;
+          wi = 0;
+        }
+        const int jx = (int)ranged(buf[wi++], (uint32_t)(i + 1));
+        const short tmp = pt[i]; pt[i] = pt[jx]; pt[jx] = tmp;
+      }
+    }
+    __syncwarp();
+    int wt = perm[(T_ - 1) * W + c];
+    C* cur = HA;
+    C* oth = HB;
+    set_sum<T, N>(a, slot_index(d, T_ - 1, wt, b), cur, gw, lane);
+    for (int t = T_ - 1; t > 0; --t) {
+      wt = perm[t * W + c];
+      const int wm = perm[(t - 1) * W + c];
+      const int64_t bt = slot_index(d, t, wt, b), bm = slot_index(d, t - 1, wm, b);
+      set_sum<T, N>(a, bm, oth, gw, lane);
+      const PsdWt<T> pt_ = walker_psd<T>(a, wt), pm_ = walker_psd<T>(a, wm);
+      // l_t(m) - l_t(t) = -1/2 D1, l_m(t) - l_m(m) = -1/2 D2 (band-local likelihoods)
+      const double D1 = set_diff<T, N>(a, rho_ptr<T>(a, wt, j), oth, cur, gw, pt_, lane);
+      const double D2 = set_diff<T, N>(a, rho_ptr<T>(a, wm, j), cur, oth, gw, pm_, lane);
+      const double la = a.betas[(int64_t)b * T_ + t] * (-0.5 * D1) + a.betas[(int64_t)b * T_ + t - 1] * (-0.5 * D2);
+      const U4 v = philox4x32_10((uint32_t)t, (uint32_t)(b * W + c), 4u | ((uint32_t)a.parity << 4), a.sweep, a.k0, a.k1);
+      const double u = u53(v.x, v.y);
+      const double lu = u > 0.0 ? log(u) : -INFINITY;
+      const bool acc = __shfl_sync(0xffffffffu, (int)(lu < la), 0) != 0;
+      if (acc) {
+        double* Pt = a.params + bt * 8;
+        double* Pm = a.params + bm * 8;
+        for (int i = lane; i < d.n_max * 8; i += 32) {
+          const double q = Pt[i]; Pt[i] = Pm[i]; Pm[i] = q;
+        }
+        for (int i = lane; i < d.n_max; i += 32) {
+          const uint8_t q = a.exists[bt + i]; a.exists[bt + i] = a.exists[bm + i]; a.exists[bm + i] = q;
+        }
+        C* ct = cache_ptr<T>(a, bt);
+        C* cm = cache_ptr<T>(a, bm);
+        for (int i = lane; i < d.n_max * nslotc; i += 32) {
+          const C q = ct[i]; ct[i] = cm[i]; cm[i] = q;
+        }
+        __syncwarp();
+        if (t == 1) {
+          long long* Rw = a.resid + (int64_t)wm * 2 * a.c.grid.n_bins * 2;
+          cold_update<T, N>(a, bt, -1, Rw, lane);   // old cold set leaves the model
+          cold_update<T, N>(a, bm, +1, Rw, lane);   // new cold set enters
+        }
+        // the set now at t-1 is `cur`; `oth` is free
+      } else {
+        C* q = cur; cur = oth; oth = q;
+      }
+      if (lane == 0) record(a, 3, t, wt, b, c, t, acc, la, la, nullptr);
+      __syncwarp();
+    }
+  }
+}
+
+// -------------------------------------------------------------- host side
+static int sms_of_device() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+// Warps per CTA (<= kSwWarps) so that the CTA's shared memory fits the SM.
+static int sweep_warps(size_t per_warp) {
+  int w = (int)((220 * 1024) / (per_warp > 0 ? per_warp : 1));
+  return w < 1 ? 1 : (w > kSwWarps ? kSwWarps : w);
+}
+
+template <typename K>
+static gbk_status prep(K kernel, size_t per_warp, int64_t items, int* grid, int* threads, size_t* smem) {
+  const int wpc = sweep_warps(per_warp);
+  *threads = wpc * 32;
+  *smem = per_warp * wpc;
+  if (*smem > 48 * 1024 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(GBK_ECUDA, "sweep kernel needs %zu bytes of shared memory", *smem);
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, *threads, *smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return set_error(GBK_ECUDA, "sweep kernel does not fit on an SM (%zu bytes of shared memory)", *smem);
+  }
+  const int64_t need = (items + wpc - 1) / wpc;
+  const int64_t cap = (int64_t)sms_of_device() * per_sm;
+  *grid = (int)(need < cap ? (need > 0 ? need : 1) : cap);
+  return GBK_OK;
+}
+
+template <typename T, int N>
+static gbk_status run_refresh(SweepArgs& a, cudaStream_t st) {
+  const int64_t nslot = (int64_t)a.d.n_temps * a.d.n_walkers * a.d.n_bands * a.d.n_max;
+  if (nslot == 0) return GBK_OK;
+  int grid = 0, thr = 0;
+  size_t sm = 0;
+  gbk_status s;
+  if ((s = prep(k_refresh<T, N>, refresh_warp_bytes<T, N>(), (nslot + 31) / 32, &grid, &thr, &sm))) return s;
+  k_refresh<T, N><<<grid, thr, sm, st>>>(a);
+  return check_launch("gb_sweep(refresh)");
+}
+
+template <typename T, int N>
+static gbk_status run_half(SweepArgs& a, int flags, cudaStream_t st) {
+  const gbk_sweep_desc& d = a.d;
+  const int nbp = (d.n_bands - a.parity + 1) / 2;
+  if (nbp <= 0) return GBK_OK;
+  gbk_status s;
+  int grid = 0, thr = 0;
+  size_t sm = 0;
+  if ((s = prep(k_open<T, N>, 0, (int64_t)d.n_walkers * nbp, &grid, &thr, &sm))) return s;
+  k_open<T, N><<<grid, kSwWarps * 32, 0, st>>>(a);
+  if ((s = check_launch("gb_sweep(open)"))) return s;
+  if (flags & (GBK_SWEEP_INMODEL | GBK_SWEEP_RJ)) {
+    if ((s = prep(k_band<T, N>, sizeof(BandSmem<T, N>), (int64_t)d.n_temps * d.n_walkers * nbp, &grid, &thr, &sm)))
+      return s;
+    k_band<T, N><<<grid, thr, sm, st>>>(a, flags);
+    if ((s = check_launch("gb_sweep(band)"))) return s;
+  }
+  if (flags & GBK_SWEEP_SWAP) {
+    if ((s = prep(k_swap<T, N>, swap_warp_bytes<T, N>(d.n_temps, d.n_walkers), (int64_t)d.n_walkers * nbp, &grid,
+                  &thr, &sm)))
+      return s;
+    k_swap<T, N><<<grid, thr, sm, st>>>(a);
+    if ((s = check_launch("gb_sweep(swap)"))) return s;
+  }
+  return GBK_OK;
+}
+
+template <typename T, int N>
+static gbk_status run_sweep_n(gbk_sweep* plan, SweepArgs& a, int flags, cudaStream_t st) {
+  gbk_status s;
+  if (flags & GBK_SWEEP_REFRESH)
+    if ((s = run_refresh<T, N>(a, st))) return s;
+  const size_t rbytes = (size_t)a.d.n_walkers * 2 * plan->ctx->grid.n_bins * 2 * sizeof(long long);
+  for (int parity = 1; parity >= 0; --parity) {
+    a.parity = parity;
+    if (cudaMemcpyAsync(plan->rsnap, a.resid, rbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return set_error(GBK_ECUDA, "gb_sweep: residual snapshot copy failed");
+    if ((s = run_half<T, N>(a, flags, st))) return s;
+  }
+  return GBK_OK;
+}
+
+template <typename T>
+static gbk_status run_sweep(gbk_sweep* plan, SweepArgs& a, int flags, cudaStream_t st) {
+  switch (a.d.band_bins) {
+    case 128: return run_sweep_n<T, 128>(plan, a, flags, st);
+    case 256: return run_sweep_n<T, 256>(plan, a, flags, st);
+    case 512: return run_sweep_n<T, 512>(plan, a, flags, st);
+    case 1024: return run_sweep_n<T, 1024>(plan, a, flags, st);
+    default: return set_error(GBK_EINVAL, "gb_sweep: band_bins %d", a.d.band_bins);
+  }
+}
+
+}  // namespace gbk
+
+using namespace gbk;
+
+extern "C" gbk_status gbk_sweep_create(gbk_ctx* ctx, const gbk_sweep_desc* desc, gbk_sweep** out_plan) {
+  if (!ctx || !desc || !out_plan) return set_error(GBK_EINVAL, "gbk_sweep_create: null argument");
+  *out_plan = nullptr;
+  const gbk_sweep_desc& d = *desc;
+  if (d.n_temps < 1 || d.n_temps > 64 || d.n_walkers < 1 || d.n_walkers > 64 || d.n_bands < 1 || d.n_max < 0 ||
+      d.n_max > kMaxSlots - 1 || band_index(d.band_bins) < 0 || d.props_per_source < 0)
+    return set_error(GBK_EINVAL, "gbk_sweep_create: bad sizes (T=%d W=%d B=%d n_max=%d N=%d)", d.n_temps,
+                     d.n_walkers, d.n_bands, d.n_max, d.band_bins);
+  if (d.precision != GBK_MIXED && d.precision != GBK_FP64) return set_error(GBK_EINVAL, "gbk_sweep_create: bad precision");
+  const int64_t lo = d.band_k0 - d.band_bins - ctx->grid.k0;
+  const int64_t hi = d.band_k0 + (int64_t)(d.n_bands + 1) * d.band_bins - ctx->grid.k0;
+  if (lo < 0 || hi > ctx->grid.n_bins)
+    return set_error(GBK_ERANGE, "gbk_sweep_create: band windows [%lld, %lld) leave the grid", (long long)lo,
+                     (long long)hi);
+  if (!(d.f_min < d.f_max) || !(d.mc_min < d.mc_max) || !(d.ln_a_min < d.ln_a_max))
+    return set_error(GBK_EINVAL, "gbk_sweep_create: bad prior bounds");
+  gbk_sweep* p = (gbk_sweep*)calloc(1, sizeof(gbk_sweep));
+  if (!p) return set_error(GBK_ENOMEM, "gbk_sweep_create: host allocation failed");
+  p->ctx = ctx;
+  p->d = d;
+  p->n_bp_max = (d.n_bands + 1) / 2;
+  const size_t csz = d.precision == GBK_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t rbytes = (size_t)d.n_walkers * 2 * ctx->grid.n_bins * 2 * sizeof(long long);
+  p->rho_bytes = (size_t)d.n_walkers * p->n_bp_max * 2 * 3 * d.band_bins * csz;
+  p->cache_bytes = (size_t)d.n_temps * d.n_walkers * d.n_bands * (d.n_max > 0 ? d.n_max : 1) * 2 * d.band_bins * csz;
+  cudaError_t e = cudaMalloc((void**)&p->rsnap, rbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&p->rho, p->rho_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&p->wcache, p->cache_bytes);
+  if (e != cudaSuccess) {
+    cudaFree(p->rsnap);
+    cudaFree(p->rho);
+    cudaFree(p->wcache);
+    free(p);
+    cudaGetLastError();
+    return set_error(e == cudaErrorMemoryAllocation ? GBK_ENOMEM : GBK_ECUDA, "gbk_sweep_create: %s",
+                     cudaGetErrorString(e));
+  }
+  *out_plan = p;
+  return GBK_OK;
+}
+
+extern "C" gbk_status gbk_sweep_destroy(gbk_sweep* plan) {
+  if (!plan) return set_error(GBK_EINVAL, "gbk_sweep_destroy: null plan");
+  cudaDeviceSynchronize();
+  cudaFree(plan->rsnap);
+  cudaFree(plan->rho);
+  cudaFree(plan->wcache);
+  free(plan);
+  return GBK_OK;
+}
+
+extern "C" gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists, const double* betas,
+                               const gbk_residual* residual, const gbk_psd* psd, uint64_t key, uint32_t sweep_index,
+                               int32_t flags, const gbk_trace* trace, int64_t* stats, void* stream) {
+  if (!plan || !residual || !psd) return set_error(GBK_EINVAL, "gb_sweep: null plan/struct");
+  if (!params || !exists || !betas || !residual->data || !psd->params)
+    return set_error(GBK_EINVAL, "gb_sweep: null device pointer");
+  if (residual->n_walkers != plan->d.n_walkers || residual->frac_bits < 40 || residual->frac_bits > 120)
+    return set_error(GBK_EINVAL, "gb_sweep: residual must hold n_walkers = %d walkers", plan->d.n_walkers);
+  if (psd->n_psd != 1 && psd->n_psd < plan->d.n_walkers) return set_error(GBK_EINVAL, "gb_sweep: psd covers too few walkers");
+  if (flags & ~(GBK_SWEEP_INMODEL | GBK_SWEEP_RJ | GBK_SWEEP_SWAP | GBK_SWEEP_REFRESH))
+    return set_error(GBK_EINVAL, "gb_sweep: unknown flags 0x%x", flags);
+  SweepArgs a;
+  a.c = *plan->ctx;
+  a.d = plan->d;
+  a.params = params;
+  a.exists = exists;
+  a.betas = betas;
+  a.resid = (long long*)residual->data;
+  a.rsnap = plan->rsnap;
+  a.rho = plan->rho;
+  a.wcache = plan->wcache;
+  a.n_bp_max = plan->n_bp_max;
+  a.n_walkers_r = residual->n_walkers;
+  a.frac_bits = residual->frac_bits;
+  a.psdp = psd->params;
+  a.npsd = psd->n_psd;
+  a.k0 = (uint32_t)(key & 0xffffffffu);
+  a.k1 = (uint32_t)(key >> 32);
+  a.sweep = sweep_index;
+  a.parity = 1;
+  a.trace = trace ? trace->records : nullptr;
+  a.trace_cap = trace ? trace->capacity : 0;
+  a.trace_count = trace ? trace->count : nullptr;
+  a.stats = (long long*)stats;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->d.precision == GBK_MIXED) return run_sweep<float>(plan, a, flags, st);
+  return run_sweep<double>(plan, a, flags, st);
+}

@@ -13,7 +13,10 @@
 //   Band: (T / 2N) FFT_N[ slow(t_p) e^{i(phi0 + 2 pi delta p/N + pi fdot t_p^2)} ],
 //   offset m in [-N/2, N/2) -> bin q + m, q = floor(f0 T), delta = f0 T - q.
 //
-// One warp computes one band. Every kernel that needs a waveform calls gen_band<T, N>,
+// One warp computes one band from per-source constants (Src) that the lanes of a warp
+// compute for up to 32 sources at once (make_src holds the float64 work, which runs at a
+// small fraction of the float32 rate on GB300, so it is spread over lanes, not repeated
+// by every lane). Every kernel that needs a waveform calls gen_band<T, N>,
 // which is __noinline__ so that all call sites run the same machine code: the same
 // parameters then give bit-identical bands in every kernel, which the fixed-point
 // residual bookkeeping relies on (a template removed by one kernel cancels the one
@@ -156,8 +159,9 @@ template <typename T> __device__ __forceinline__ void split(double x, T& hi, T& 
   lo = (T)(x - (double)hi);
 }
 
+// __noinline__: one compiled body for every kernel (see gen_band).
 template <typename T>
-__device__ __forceinline__ Src<T> make_src(const double* __restrict__ prm, int64_t stride,
+__device__ __noinline__ Src<T> make_src(const double* __restrict__ prm, int64_t stride,
                                            int64_t i, double tobs, int n) {
   Src<T> s;
   const double amp = prm[0 * stride + i];
@@ -254,11 +258,12 @@ __device__ __forceinline__ void stage_r2_first(const C* __restrict__ in, C* __re
 // q - N/2 + i), in strain units times 2^64. buf1 is scratch of the same size.
 // Called by all 32 lanes of a warp; returns with the warp synchronised.
 template <typename T, int N>
-__device__ __noinline__ void gen_band(const Src<T> src, const T* __restrict__ orb,
+__device__ __noinline__ void gen_band(const Src<T>* __restrict__ srcp, const T* __restrict__ orb,
                                       const typename CT<T>::C* __restrict__ tw, double tobs,
                                       typename CT<T>::C* buf0, typename CT<T>::C* buf1,
                                       int lane) {
   typedef typename CT<T>::C C;
+  const Src<T> src = *srcp;
   const T lc = (T)kLc;
   const T dtp = (T)(tobs / N);
   const T inv_n = (T)1 / (T)N;

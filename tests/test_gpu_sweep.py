@@ -1,0 +1,211 @@
+"""GPU ensemble sweep (Alg. 1 in-model, flip-all RJ, Alg. 2 tempering) against the oracle.
+
+FP64 sweep: every proposal's Delta lnL within 1e-7, every decision identical, final
+parameters and occupancy identical. Mixed sweep: Delta lnL within 1e-2 per proposal up
+to the first decision that differs, which must sit within 1e-2 of its threshold.
+Plus the exact cold-chain residual bookkeeping and a prior-only statistical check.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mcmc as OM
+from paper_2405_04690_gb300 import synth
+
+from _common import torch_cuda
+from _sweep_setup import FRAC, NB, copy_state, key64, small_ensemble
+
+pytestmark = pytest.mark.gpu
+
+ALL = 1 | 2 | 4
+
+
+def _gpu_sweep(torch, cfg, state, precision, sweeps=1, flags=ALL, trace_cap=20000):
+    from paper_2405_04690_gb300 import _lib as L
+    dev = torch.device("cuda")
+    ctx = L.Context(cfg.tobs, 15.0, cfg.k0, cfg.n_bins)
+    plan = L.SweepPlan(ctx, cfg.n_temps, cfg.n_walkers, cfg.n_bands, cfg.n_max, NB, cfg.band_k0, cfg.sigma,
+                       L.PRECISION[precision], log_occ_odds=cfg.log_occ_odds, f_min=cfg.f_min, f_max=cfg.f_max)
+    P = torch.from_numpy(state["params"].copy()).to(dev)
+    E = torch.from_numpy(state["exists"].astype(np.uint8)).to(dev)
+    R = torch.from_numpy(state["resid"].copy()).to(dev)
+    betas = torch.from_numpy(np.ascontiguousarray(cfg.betas)).to(dev)
+    psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
+    rec = torch.zeros(trace_cap * ctypes.sizeof(L.GbkTraceRec), dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    stats = torch.zeros((4, 2), dtype=torch.int64, device=dev)
+    for k in range(sweeps):
+        L.gb_sweep(plan, P, E, betas, L.residual_struct(R, FRAC), L.psd_struct(psdp), key64(cfg), k,
+                   flags | (L.SWEEP_REFRESH if k == 0 else 0), trace=(rec, trace_cap, cnt), stats=stats)
+    L.gbk_sync_status(ctx)
+    n = int(cnt.item())
+    assert n <= trace_cap
+    tr = np.frombuffer(rec.cpu().numpy().tobytes(), dtype=np.dtype(L.TRACE_DTYPE_FIELDS))[:n]
+    out = {"params": P.cpu().numpy(), "exists": E.cpu().numpy().astype(bool), "resid": R.cpu().numpy()}
+    res = (out, tr, stats.cpu().numpy())
+    plan.close()
+    ctx.close()
+    return res
+
+
+def _key(r):
+    return (int(r["parity"]), int(r["kind"]) if int(r["kind"]) in (0, 3) else 1, int(r["t"]), int(r["w"]),
+            int(r["b"]), int(r["slot"]) if int(r["kind"]) == 3 else 0, int(r["seq"]))
+
+
+def _index(gpu_tr, ora_tr):
+    g = {}
+    for r in gpu_tr:
+        g[_key(r)] = r
+    o = {}
+    for r in ora_tr:
+        kr = (r["parity"], r["kind"] if r["kind"] in (0, 3) else 1, r["t"], r["w"], r["b"],
+              r["slot"] if r["kind"] == 3 else 0, r["seq"])
+        o[kr] = r
+    return g, o
+
+
+def test_sweep_fp64_matches_oracle_exactly():
+    torch = torch_cuda()
+    cfg, state, _, _ = small_ensemble(seed=3)
+    ora = copy_state(state)
+    trace = OM.sweep(cfg, ora, 0)
+    out, gtr, stats = _gpu_sweep(torch, cfg, state, "fp64")
+    g, o = _index(gtr, trace)
+    assert set(g) == set(o), (len(g), len(o))
+    worst = 0.0
+    for k, ro in o.items():
+        rg = g[k]
+        assert bool(rg["accepted"]) == ro["accepted"], (k, rg["log_alpha"], ro["log_alpha"], ro["lu"])
+        if ro["kind"] != 3:
+            assert int(rg["kind"]) == ro["kind"]
+            assert int(rg["slot"]) == ro["slot"]
+            np.testing.assert_allclose(rg["params"], ro["params"], rtol=1e-13, atol=0)
+        if np.isfinite(ro["dlogl"]):
+            worst = max(worst, abs(rg["dlogl"] - ro["dlogl"]))
+        else:
+            assert np.isnan(rg["dlogl"])
+    assert worst < 1e-7, worst
+    assert np.array_equal(out["exists"], ora["exists"])
+    np.testing.assert_allclose(out["params"][ora["exists"]], ora["params"][ora["exists"]], rtol=1e-13, atol=0)
+    # residual: same templates, rounded from float64 waveforms that agree to ~1e-13
+    diff = np.abs(out["resid"] - ora["resid"]).max()
+    assert diff < 2 ** 20, diff
+    kinds = stats[:, 0]
+    assert kinds[0] > 0 and kinds[1] > 0 and kinds[3] > 0
+    assert stats[:, 0].sum() == len(gtr)
+
+
+def test_sweep_mixed_matches_oracle_until_a_justified_flip():
+    torch = torch_cuda()
+    cfg, state, _, _ = small_ensemble(seed=4)
+    ora = copy_state(state)
+    trace = OM.sweep(cfg, ora, 0)
+    out, gtr, _ = _gpu_sweep(torch, cfg, state, "mixed")
+    g, o = _index(gtr, trace)
+    # band tasks of the first half sweep see identical inputs; compare them in order
+    tasks = {}
+    for k, ro in o.items():
+        if ro["parity"] == 1 and ro["kind"] != 3:
+            tasks.setdefault((ro["t"], ro["w"], ro["b"]), []).append((k, ro))
+    flips = 0
+    worst = 0.0
+    for _, recs in tasks.items():
+        recs.sort(key=lambda x: (x[1]["kind"] != 0, x[1]["seq"]))
+        for k, ro in recs:
+            rg = g.get(k)
+            assert rg is not None
+            if np.isfinite(ro["dlogl"]):
+                worst = max(worst, abs(rg["dlogl"] - ro["dlogl"]))
+            if bool(rg["accepted"]) != ro["accepted"]:
+                assert abs(ro["log_alpha"] - ro["lu"]) < 1e-2
+                flips += 1
+                break
+    assert worst < 1e-2, worst
+    assert flips <= 1
+
+
+def test_sweep_cold_residual_is_exact():
+    # The cold-chain residual is changed only by rounded templates, so after several
+    # sweeps it equals data - sum(cold templates) bit for bit when the initial model
+    # was entered with the same kernels.
+    torch = torch_cuda()
+    from paper_2405_04690_gb300 import _lib as L
+    cfg, state, dfix, _ = small_ensemble(seed=5)
+    dev = torch.device("cuda")
+    ctx = L.Context(cfg.tobs, 15.0, cfg.k0, cfg.n_bins)
+    R = torch.from_numpy(np.stack([dfix] * cfg.n_walkers)).to(dev).contiguous()
+    RS = L.residual_struct(R, FRAC)
+
+    def move_cold(P, E, sign, prec):
+        p = P[0].reshape(-1, 8)[E[0].reshape(-1)]
+        wv = np.nonzero(E[0])[0].astype(np.int32)
+        if len(wv) == 0:
+            return
+        pt = torch.from_numpy(np.ascontiguousarray(p.T)).to(dev)
+        L.residual_add_sub(ctx, RS, pt, torch.full((len(wv),), NB, dtype=torch.int32, device=dev), NB,
+                           torch.from_numpy(wv).to(dev), sign, prec)
+
+    for prec in ("mixed", "fp64"):
+        R.copy_(torch.from_numpy(np.stack([dfix] * cfg.n_walkers)))
+        move_cold(state["params"], state["exists"], +1, L.PRECISION[prec])
+        plan = L.SweepPlan(ctx, cfg.n_temps, cfg.n_walkers, cfg.n_bands, cfg.n_max, NB, cfg.band_k0, cfg.sigma,
+                           L.PRECISION[prec], f_min=cfg.f_min, f_max=cfg.f_max)
+        P = torch.from_numpy(state["params"].copy()).to(dev)
+        E = torch.from_numpy(state["exists"].astype(np.uint8)).to(dev)
+        betas = torch.from_numpy(np.ascontiguousarray(cfg.betas)).to(dev)
+        psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
+        stats = torch.zeros((4, 2), dtype=torch.int64, device=dev)
+        for k in range(4):
+            L.gb_sweep(plan, P, E, betas, RS, L.psd_struct(psdp), key64(cfg), 10 + k,
+                       ALL | (L.SWEEP_REFRESH if k == 0 else 0), stats=stats)
+        L.gbk_sync_status(ctx)
+        st = stats.cpu().numpy()
+        assert st[:, 1].sum() > 0          # something was accepted
+        move_cold(P.cpu().numpy(), E.cpu().numpy().astype(bool), -1, L.PRECISION[prec])
+        L.gbk_sync_status(ctx)
+        assert np.array_equal(R.cpu().numpy(), np.stack([dfix] * cfg.n_walkers)), prec
+        plan.close()
+    ctx.close()
+
+
+def test_sweep_prior_only_reproduces_the_prior():
+    # beta = 0 everywhere: occupancy of each slot tends to pi = 0.3 (Eq. rj-acceptance
+    # with the slot prior odds), and f0 of present sources is uniform over the band's
+    # allowance; checked over many sweeps and bands.
+    torch = torch_cuda()
+    from scipy import stats as sst
+    pi = 0.3
+    cfg, state, _, _ = small_ensemble(seed=6, n_temps=2, n_walkers=4, n_bands=6, n_max=8, n_per_band=1,
+                                      betas=(0.0, 0.0), log_occ_odds=math.log(pi / (1 - pi)))
+    from paper_2405_04690_gb300 import _lib as L
+    dev = torch.device("cuda")
+    ctx = L.Context(cfg.tobs, 15.0, cfg.k0, cfg.n_bins)
+    plan = L.SweepPlan(ctx, cfg.n_temps, cfg.n_walkers, cfg.n_bands, cfg.n_max, NB, cfg.band_k0, cfg.sigma,
+                       L.GBK_MIXED, log_occ_odds=cfg.log_occ_odds, f_min=cfg.f_min, f_max=cfg.f_max)
+    P = torch.from_numpy(state["params"].copy()).to(dev)
+    E = torch.from_numpy(state["exists"].astype(np.uint8)).to(dev)
+    R = torch.from_numpy(state["resid"].copy()).to(dev)
+    betas = torch.zeros((cfg.n_bands, cfg.n_temps), dtype=torch.float64, device=dev)
+    psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
+    occ, f_rel = [], []
+    for k in range(60):
+        L.gb_sweep(plan, P, E, betas, L.residual_struct(R, FRAC), L.psd_struct(psdp), 77, k,
+                   ALL | (L.SWEEP_REFRESH if k == 0 else 0))
+        if k >= 10:
+            e = E.cpu().numpy().astype(bool)
+            p = P.cpu().numpy()
+            occ.append(e.mean())
+            for b in range(cfg.n_bands):
+                lo, hi = cfg.allowance(b)
+                f = p[:, :, b, :, 1][e[:, :, b, :]]
+                f_rel.extend(((f - lo) / (hi - lo)).tolist())
+    L.gbk_sync_status(ctx)
+    occ = float(np.mean(occ))
+    n_slots = cfg.n_temps * cfg.n_walkers * cfg.n_bands * cfg.n_max
+    assert abs(occ - pi) < 5 * math.sqrt(pi * (1 - pi) / n_slots), occ   # generous: sweeps are correlated
+    assert sst.kstest(np.asarray(f_rel[::7]), "uniform").pvalue > 1e-3
+    plan.close()
+    ctx.close()

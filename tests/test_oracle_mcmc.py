@@ -1,0 +1,86 @@
+"""Pins of the oracle's sampler pieces: Eq. temp-final vs Eq. temp-orig, the
+reversible-jump ratio, the swap rate of a two-temperature Gaussian toy, the Philox
+generator's uniformity, and a prior-only run of the full sweep."""
+import math
+
+import numpy as np
+from scipy import integrate, stats
+
+from oracle import mcmc as OM
+from oracle import philox as PX
+
+from _sweep_setup import copy_state, small_ensemble
+
+
+def test_temp_final_reduces_to_temp_orig_for_shared_likelihoods():
+    # App. D: with L_{i,n} = L_{j,n} = L_n and L_{i,m} = L_{j,m} = L_m, Eq. temp-final
+    # equals Eq. temp-orig.
+    g = np.random.default_rng(1)
+    for _ in range(100):
+        ln, lm = g.normal(0, 50, 2)
+        bi, bj = g.uniform(0, 1, 2)
+        a2 = OM.temp_final_log_alpha(lm, ln, ln, lm, bi, bj)
+        a1 = OM.temp_orig_log_alpha(ln, lm, bi, bj)
+        assert abs(a1 - a2) < 1e-10 * (1 + abs(a1))
+
+
+def test_rj_ratio_is_inverted_for_removal():
+    for dll in (-3.0, 0.5, 12.0):
+        up = OM.rj_log_alpha(dll, 0.7, -1.2, -2.0, birth=True)
+        down = OM.rj_log_alpha(-dll, 0.7, -1.2, -2.0, birth=False)
+        assert abs(up + down) < 1e-12
+
+
+def test_swap_rate_of_two_temperature_gaussian_toy():
+    # Two chains at beta = 1 and 0.4 sample N(0, 1/beta) exactly; the mean swap
+    # acceptance min(1, exp(alpha)) with ln L = -x^2/2 equals the integral over both
+    # stationary densities (a wrong sign in the swap ratio gives a different rate).
+    b1, b2 = 1.0, 0.4
+    g = np.random.default_rng(2)
+    x1 = g.normal(0, 1 / math.sqrt(b1), 400000)
+    x2 = g.normal(0, 1 / math.sqrt(b2), 400000)
+    l1, l2 = -0.5 * x1 ** 2, -0.5 * x2 ** 2
+    la = OM.temp_orig_log_alpha(l2, l1, b1, b2)
+    rate = np.mean(np.minimum(1.0, np.exp(la)))
+
+    def dens(y, x):
+        a = (b2 - b1) * (-0.5 * y ** 2 + 0.5 * x ** 2)
+        return min(1.0, math.exp(a)) * stats.norm.pdf(x, 0, 1 / math.sqrt(b1)) * stats.norm.pdf(y, 0, 1 / math.sqrt(b2))
+
+    want, _ = integrate.dblquad(dens, -8, 8, -12, 12, epsabs=1e-7)
+    assert abs(rate - want) < 5e-3, (rate, want)
+    # the swap must favour moving the hotter chain's higher-likelihood state down
+    assert want < 1.0
+
+
+def test_philox_words_are_uniform_and_counter_distinct():
+    words = []
+    for c in range(4000):
+        words.extend(PX.philox4x32_10((c, 7, 3, 1), (11, 13)))
+    u = np.array([PX.u32(w) for w in words])
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+    # distinct keys give unrelated streams
+    w2 = [PX.philox4x32_10((c, 7, 3, 1), (12, 13))[0] for c in range(2000)]
+    assert np.corrcoef(np.array(words[0:8000:4], dtype=float), np.array(w2, dtype=float))[0, 1] < 0.1
+    # exact conversions
+    assert PX.u53(0, 0) == 0.0 and PX.u53(0xFFFFFFFF, 0xFFFFFFFF) < 1.0
+    assert PX.ranged(0xFFFFFFFF, 7) == 6 and PX.ranged(0, 7) == 0
+
+
+def test_prior_only_sweeps_reproduce_occupancy_and_f0_prior():
+    pi = 0.3
+    cfg, state, _, _ = small_ensemble(seed=9, n_temps=1, n_walkers=1, n_bands=2, n_max=6, n_per_band=1,
+                                      betas=(0.0,), log_occ_odds=math.log(pi / (1 - pi)))
+    st = copy_state(state)
+    occ, frel = [], []
+    for k in range(40):
+        OM.sweep(cfg, st, k, do_swap=False)
+        if k >= 4:
+            occ.append(st["exists"].mean())
+            for b in range(cfg.n_bands):
+                lo, hi = cfg.allowance(b)
+                f = st["params"][0, 0, b, :, 1][st["exists"][0, 0, b]]
+                frel.extend(((f - lo) / (hi - lo)).tolist())
+    n = len(occ) * cfg.n_bands * cfg.n_max
+    assert abs(np.mean(occ) - pi) < 4 * math.sqrt(pi * (1 - pi) / n)
+    assert stats.kstest(np.asarray(frel), "uniform").pvalue > 1e-3
