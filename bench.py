@@ -1,18 +1,21 @@
-"""Benchmark of the GB likelihood hot path on GB300 (one JSON line on stdout).
+"""Benchmark of the GB sampler hot path on GB300 (one JSON line on stdout).
 
-Workload: the batched ensemble of 16 temperatures x 32 walkers, each walker holding
-2,000 Galactic binaries in 1-4 mHz with N = 256 band bins (1,024,000 sources), data =
-seeded noise + 2,000 injected sources, residual of every walker on the device as int64
-fixed point. One step evaluates one in-model Gaussian proposal for every source (S1-S5:
-slow-part response, band FFT, heterodyne, PSD weights, Delta lnL against the walker's
-residual) in mixed precision in one launch.
+Workload (the batched ensemble): 16 temperatures x 32 walkers; the data are seeded noise
+plus 2,000 Galactic binaries with f0 in 1-4 mHz (N = 256 band bins, 369 sub-bands);
+every walker holds its own jittered copy of the 2,000 sources at every temperature
+(1,024,000 sources), sorted into sub-band slots. One step is one full sweep of the
+sampler (gb_sweep): odd then even sub-bands, each band with one in-model proposal per
+source (Alg. 1), the flip-all reversible jump over its n_max slots (App. C) and the
+ensemble-permuted tempering swaps (Alg. 2), with the cold-chain residual of every
+walker on the device (int64 fixed point) updated in place. Mixed precision.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun each rank runs its own replica of the workload (weak scaling); rank 0
-prints max-over-ranks timing.
+Under torchrun every rank runs its own replica of the workload (weak scaling); rank 0
+prints the max-over-ranks timing.
 """
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -28,66 +31,81 @@ N_T, N_W, N_SRC, N_BAND = 16, 32, 2000, 256
 FRAC_BITS = 98
 TOBS = 2 ** 21 * 15.0
 DT = 15.0
+F_LO, F_HI = 1e-3, 4e-3
 METRIC = "GB proposals (waveform+DeltalogL) /sec"
-WORKLOAD = "16 temps x 32 walkers x 2000 GBs (1-4 mHz, N=256): one in-model proposal per source, mixed precision"
+WORKLOAD = ("batched ensemble: 16 temps x 32 walkers x 2000 GBs (1-4 mHz, N=256, 369 sub-bands); one step = one "
+            "full sweep (in-model 1/source + flip-all RJ + PT swaps), mixed precision")
 
-# Algorithmic FP32 work of one in-model proposal at N = 256 (two waveforms and the
-# inner products over the union of the two bands), counted from the algorithm:
-# slow part 417 flops/sample, FFT 5 N log2 N per channel, 45 flops per union bin.
-FLOPS_SLOW_PER_SAMPLE = 417
+# Algorithmic float32 work (derived in the design doc from the operation count of the method):
+# slow-part response 621 flops per coarse sample, band FFT 5 N log2 N per channel,
+# Delta lnL 45 flops per band bin.
+FLOPS_SLOW_PER_SAMPLE = 621
 FLOPS_PER_BIN = 45
 
 
-def flops_per_proposal(n=N_BAND, union_bins=N_BAND + 4):
-    wf = n * FLOPS_SLOW_PER_SAMPLE + 2 * 5 * n * int(np.log2(n))
-    return 2 * wf + union_bins * FLOPS_PER_BIN
+def flops_per_waveform(n=N_BAND):
+    return n * FLOPS_SLOW_PER_SAMPLE + 2 * 5 * n * int(math.log2(n))
 
 
-def peaks():
-    try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        return {}
+def flops_per_evaluation(n=N_BAND):
+    return n * FLOPS_PER_BIN
+
+
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
 # ------------------------------------------------------------------ CPU oracle timing
 def _oracle_worker(args):
-    seed, count = args
+    seed, n_bands = args
     sys.path.insert(0, ROOT)
     from oracle import constants as OC
-    from oracle import likelihood as OL
+    from oracle import mcmc as OM
     from oracle import psd as OP
+    from oracle import residual as OR
     from oracle import waveform as OW
     from paper_2405_04690_gb300 import synth
     g = synth.rng(seed)
-    p = synth.draw_sources(g, count)
-    new = synth.perturb(g, p, synth.proposal_widths(p))
+    band_k0 = int(math.floor(2.0e-3 * OC.TOBS)) + 256 * (seed % 50)
+    k0 = band_k0 - 2 * N_BAND
+    n_bins = (n_bands + 4) * N_BAND
+    f = (k0 + np.arange(n_bins)) * OC.DF
+    s = OP.psd_ae(f, OC.SQRT_S_OMS, OC.SQRT_S_ACC)
+    n_t, n_w, n_max = 2, 1, 8
+    cfg = OM.SweepConfig(tobs=OC.TOBS, k0=k0, n_bins=n_bins, band_k0=band_k0, nb=N_BAND, n_bands=n_bands,
+                         n_temps=n_t, n_walkers=n_w, n_max=n_max, betas=np.tile([1.0, 0.5], (n_bands, 1)),
+                         psd=np.tile(s, (n_w, 1)), sigma=sweep_sigma(), key=(seed, 99))
+    params = np.zeros((n_t, n_w, n_bands, n_max, 8))
+    exists = np.zeros((n_t, n_w, n_bands, n_max), dtype=bool)
+    data = synth.unit_complex_normal(g, (2, n_bins)) * np.sqrt(s / (4 * OC.DF))
+    for b in range(n_bands):
+        lo, hi = cfg.band_bins(b)
+        p = synth.draw_sources(g, 5, (lo + 2) / OC.TOBS, (hi - 2) / OC.TOBS)
+        params[:, :, b, :5] = p.T[None, None]
+        exists[:, :, b, :5] = True
+    r = OR.to_fixed(data, FRAC_BITS)
+    for b in range(n_bands):
+        for i in range(5):
+            r = OR.add_sub(r, k0, OW.fastslow_band(params[0, 0, b, i], N_BAND), +1, FRAC_BITS)
+    state = {"params": params, "exists": exists, "resid": r[None].copy()}
     t0 = time.perf_counter()
-    for i in range(count):
-        q, _ = OW.carrier_bin(p[1, i])
-        k0 = q - 3 * N_BAND // 2
-        f = (k0 + np.arange(3 * N_BAND)) * OC.DF
-        s = OP.psd_ae(f, OC.SQRT_S_OMS, OC.SQRT_S_ACC)
-        r = synth.unit_complex_normal(g, (2, 3 * N_BAND)) * np.sqrt(s / (4 * OC.DF))
-        OL.delta_loglike_swap(r, s, OC.DF, k0, OW.fastslow_band(new[:, i], N_BAND), OW.fastslow_band(p[:, i], N_BAND))
-    return time.perf_counter() - t0, count
+    trace = OM.sweep(cfg, state, 0)
+    return time.perf_counter() - t0, len(trace)
 
 
-def cpu_baseline(sample=4000, cores=None):
-    """Time the FP64 oracle on `sample` proposals spread over all host cores (spawned pool)."""
+def cpu_baseline(n_bands=12, cores=None):
+    """Time the FP64 oracle sweep on a bounded sample over all host cores (spawned pool)."""
     import multiprocessing as mp
     cores = cores or os.cpu_count() or 1
-    per = [sample // cores + (1 if i < sample % cores else 0) for i in range(cores)]
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_worker, [(7000 + i, c) for i, c in enumerate(per) if c > 0])
+        res = pool.map(_oracle_worker, [(7000 + i, n_bands) for i in range(cores)])
     wall = time.perf_counter() - t0
     done = sum(c for _, c in res)
     busy = max(t for t, _ in res)
     return {"value": done / busy, "unit": "proposals/s", "cores": cores, "kind": "oracle",
-            "sample": "%d in-model proposals (N=256, 1-4 mHz) over %d processes; FP64 numpy fast/slow waveform x2 + "
-                      "Eq. swapsource on a 3-band window; %.1f s wall incl. pool start" % (done, cores, wall)}
+            "sample": "%d proposals: %d processes each run one FP64 oracle sweep of 2 temps x 1 walker x %d sub-bands "
+                      "(5 GBs/band, 8 slots) near 2 mHz; %.1f s wall incl. pool start" % (done, cores, n_bands, wall)}
 
 
 # ------------------------------------------------------------------ clocks
@@ -136,52 +154,85 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload on the GPU
-def build_workload(torch, L, dev, seed, n_temps=N_T):
+def sweep_sigma():
+    df = 1.0 / TOBS
+    return [0.05, 0.1 * df, 0.005 * df / TOBS, 0.05, 0.05, 0.02, 0.02, 0.02]
+
+
+def ladder(n_temps):
+    """Temperatures 1.2^t, the top one infinite (beta = 0)."""
+    b = np.array([1.2 ** -t for t in range(n_temps)])
+    b[-1] = 0.0
+    return b
+
+
+def build_ensemble(seed, n_temps=N_T, n_walkers=N_W, n_src=N_SRC):
+    """Host arrays of the ensemble: params [T][W][B][n_max][8], exists, band layout."""
     from paper_2405_04690_gb300 import synth
     g = synth.rng(seed)
-    k0, nbins = synth.window_for(1e-3, 4e-3, 600)
-    ctx = L.Context(TOBS, DT, k0, nbins)
-    truth = synth.draw_sources(g, N_SRC)
+    band_k0 = int(math.floor(F_LO * TOBS))
+    n_bands = int(math.ceil((math.floor(F_HI * TOBS) - band_k0) / N_BAND))
+    truth = synth.draw_sources(g, n_src, F_LO, F_HI)
+    band = ((np.floor(truth[1] * TOBS).astype(np.int64) - band_k0) // N_BAND).astype(np.int64)
+    counts = np.bincount(band, minlength=n_bands)
+    n_max = int(math.ceil(1.5 * counts.max()))
+    slot = np.zeros(n_src, dtype=np.int64)
+    seen = np.zeros(n_bands, dtype=np.int64)
+    for i in np.argsort(band, kind="stable"):
+        slot[i] = seen[band[i]]
+        seen[band[i]] += 1
+    params = np.zeros((n_temps, n_walkers, n_bands, n_max, 8))
+    exists = np.zeros((n_temps, n_walkers, n_bands, n_max), dtype=np.uint8)
+    df = 1.0 / TOBS
+    jit = np.array([0.0, 0.02 * df, 0.0, 0.02, 0.02, 0.01, 0.01, 0.01])[:, None]
+    for t in range(n_temps):
+        for w in range(n_walkers):
+            p = truth + jit * g.standard_normal(truth.shape)
+            p[0] = truth[0] * np.exp(0.02 * g.standard_normal(n_src))
+            p[5] = np.clip(p[5], -1, 1)
+            p[6] = np.clip(p[6], -1, 1)
+            p[3] %= 2 * np.pi
+            p[4] %= np.pi
+            p[7] %= 2 * np.pi
+            params[t, w, band, slot] = p.T
+            exists[t, w, band, slot] = 1
+    return {"truth": truth, "params": params, "exists": exists, "band_k0": band_k0, "n_bands": n_bands,
+            "n_max": n_max, "k0": band_k0 - 2 * N_BAND, "n_bins": (n_bands + 4) * N_BAND}
+
+
+def build_device_state(torch, L, dev, ens, precision, seed):
+    from paper_2405_04690_gb300 import synth
+    g = synth.rng(seed + 17)
+    nt, nw = ens["params"].shape[:2]
+    ctx = L.Context(TOBS, DT, ens["k0"], ens["n_bins"])
     psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
-    # noise on the window: unit normals scaled by sqrt(S / 4df), S from psd_eval
-    s = torch.empty((1, nbins), dtype=torch.float64, device=dev)
+    s = torch.empty((1, ens["n_bins"]), dtype=torch.float64, device=dev)
     L.psd_eval(ctx, psdp, s)
-    z = torch.from_numpy(synth.unit_complex_normal(g, (2, nbins))).to(dev)
+    z = torch.from_numpy(synth.unit_complex_normal(g, (2, ens["n_bins"]))).to(dev)
     noise = z * torch.sqrt(s[0] * (TOBS / 4.0))
     scale = float(2.0 ** FRAC_BITS)
     one = torch.stack([torch.round(noise.real * scale), torch.round(noise.imag * scale)], dim=-1).to(torch.int64)
-    resid = one.unsqueeze(0).repeat(N_W, 1, 1, 1).contiguous()            # [W][2][n][2]
+    resid = one.unsqueeze(0).repeat(nw, 1, 1, 1).contiguous()
     R = L.residual_struct(resid, FRAC_BITS)
-    nb = torch.full((N_SRC,), N_BAND, dtype=torch.int32, device=dev)
-    # data = noise + injected truth (templates leave the model: R += h)
-    for w in range(N_W):
-        L.residual_add_sub(ctx, R, torch.from_numpy(truth).to(dev), nb, N_BAND,
-                           torch.full((N_SRC,), w, dtype=torch.int32, device=dev), -1, L.GBK_MIXED)
-    # per (t, w): walker-specific small jitter of the truth; cold chain (t = 0) is the model
-    widths = synth.proposal_widths(truth) * 0.2
-    cur = np.empty((8, n_temps * N_W * N_SRC))
-    walker = np.empty(n_temps * N_W * N_SRC, dtype=np.int32)
-    for t in range(n_temps):
-        for w in range(N_W):
-            i0 = (t * N_W + w) * N_SRC
-            cur[:, i0:i0 + N_SRC] = synth.perturb(g, truth, widths)
-            walker[i0:i0 + N_SRC] = w
-    for w in range(N_W):
-        i0 = w * N_SRC
-        L.residual_add_sub(ctx, R, torch.from_numpy(np.ascontiguousarray(cur[:, i0:i0 + N_SRC])).to(dev), nb, N_BAND,
-                           torch.full((N_SRC,), w, dtype=torch.int32, device=dev), +1, L.GBK_MIXED)
+    truth = ens["truth"]
+    nsrc = truth.shape[1]
+    nb = torch.full((nsrc,), N_BAND, dtype=torch.int32, device=dev)
+    tt = torch.from_numpy(truth).to(dev)
+    for w in range(nw):   # data = noise + injected sources (templates leave the model: R += h)
+        L.residual_add_sub(ctx, R, tt, nb, N_BAND, torch.full((nsrc,), w, dtype=torch.int32, device=dev), -1, precision)
+    P = torch.from_numpy(ens["params"]).to(dev)
+    E = torch.from_numpy(ens["exists"]).to(dev)
+    cold = ens["params"][0].reshape(-1, 8)[ens["exists"][0].reshape(-1).astype(bool)]
+    wv = np.nonzero(ens["exists"][0])[0].astype(np.int32)
+    L.residual_add_sub(ctx, R, torch.from_numpy(np.ascontiguousarray(cold.T)).to(dev),
+                       torch.full((len(wv),), N_BAND, dtype=torch.int32, device=dev), N_BAND,
+                       torch.from_numpy(wv).to(dev), +1, precision)
+    betas = torch.from_numpy(np.tile(ladder(nt), (ens["n_bands"], 1))).to(dev).contiguous()
+    plan = L.SweepPlan(ctx, nt, nw, ens["n_bands"], ens["n_max"], N_BAND, ens["band_k0"], sweep_sigma(), precision,
+                       f_min=F_LO, f_max=F_HI)
     L.gbk_sync_status(ctx)
-    prop = synth.perturb(g, cur, synth.proposal_widths(cur))
-    n = cur.shape[1]
-    w_ = {
-        "ctx": ctx, "resid": resid, "R": R, "psd": L.psd_struct(psdp), "psdp": psdp,
-        "old": torch.from_numpy(cur).to(dev), "new": torch.from_numpy(prop).to(dev),
-        "old_h": torch.from_numpy(cur).pin_memory(), "new_h": torch.from_numpy(prop).pin_memory(),
-        "nb": torch.full((n,), N_BAND, dtype=torch.int32, device=dev),
-        "walker": torch.from_numpy(walker).to(dev), "out": torch.empty(n, dtype=torch.float64, device=dev),
-        "out_h": torch.empty(n, dtype=torch.float64).pin_memory(), "n": n,
-    }
-    return w_
+    return {"ctx": ctx, "plan": plan, "P": P, "E": E, "resid": resid, "R": R, "psd": L.psd_struct(psdp),
+            "psdp": psdp, "betas": betas}
 
 
 def run_ours(args):
@@ -199,19 +250,25 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     from paper_2405_04690_gb300 import _lib as L
     L.lib()
-    W = build_workload(torch, L, dev, seed=1 + 1000 * rank, n_temps=args.n_temps)
+    ens = build_ensemble(seed=1 + 1000 * rank, n_temps=args.n_temps)
+    S = build_device_state(torch, L, dev, ens, L.GBK_MIXED, seed=1 + 1000 * rank)
     stream = torch.cuda.current_stream()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    stats = torch.zeros((5, 2), dtype=torch.int64, device=dev)
+    key = 0x5EED0000 + rank
+    sweep_no = [0]
 
-    def step():
-        L.gb_delta_loglike_batch(W["ctx"], W["new"], W["old"], W["nb"], N_BAND, W["walker"], W["R"], W["psd"],
-                                 W["out"], L.GBK_MIXED, stream)
+    def step(flags_extra=0):
+        L.gb_sweep(S["plan"], S["P"], S["E"], S["betas"], S["R"], S["psd"], key, sweep_no[0],
+                   1 | 2 | 4 | flags_extra, stats=stats, stream=stream)
+        sweep_no[0] += 1
 
+    step(L.SWEEP_REFRESH)                  # fills the waveform cache
     for _ in range(args.warmup):
         step()
-    L.gbk_sync_status(W["ctx"])
-    launches = 0
+    L.gbk_sync_status(S["ctx"])
+    stats.zero_()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kms = np.zeros(4)
     clocks = ClockSampler()
     if world > 1:
         dist.barrier()
@@ -219,35 +276,50 @@ def run_ours(args):
     clocks.start()
     t_wall = time.perf_counter()
     for e0, e1 in evs:
-        flush.fill_(1.0)                    # untimed L2 flush between timed steps
         e0.record(stream)
-        step()
-        launches += 1
+        step(L.SWEEP_TIMING)
         e1.record(stream)
+        kms += np.array(L.gbk_sweep_kernel_ms(S["plan"]))
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
     if world > 1:
         dist.barrier()
     clk = clocks.stop(local)
-    L.gbk_sync_status(W["ctx"])
+    L.gbk_sync_status(S["ctx"])
+    st = stats.cpu().numpy()
     ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     ms_step = float(np.sum(ms)) / args.steps
     t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_step = float(t.item())
-    total_props = W["n"] * world
-    value = total_props / (ms_step * 1e-3)
+    props_step = float(st[:4, 0].sum()) / args.steps
+    total = torch.tensor([props_step], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(total, op=dist.ReduceOp.SUM)
+    value = float(total.item()) / (ms_step * 1e-3)
+    # roofline of the band kernel (in-model + RJ): algorithmic flops / its device time
+    wf, ev = float(st[4, 0]), float(st[4, 1])
+    band_ms = kms[2] / args.steps
+    fl_step = (wf * flops_per_waveform() + ev * flops_per_evaluation()) / args.steps
+    ach = fl_step / (band_ms * 1e-3) / 1e12
 
-    # end to end through the C ABI with host buffers (H2D params, D2H Delta lnL)
+    # end to end through the C ABI with host buffers: the sampler state goes in from pinned
+    # host memory and comes back (with the move statistics) every step
+    Ph = S["P"].cpu().pin_memory()
+    Eh = S["E"].cpu().pin_memory()
+    sth = torch.zeros((5, 2), dtype=torch.int64).pin_memory()
+
     def e2e_step():
-        W["new"].copy_(W["new_h"], non_blocking=True)
-        W["old"].copy_(W["old_h"], non_blocking=True)
+        S["P"].copy_(Ph, non_blocking=True)
+        S["E"].copy_(Eh, non_blocking=True)
         step()
-        W["out_h"].copy_(W["out"], non_blocking=True)
+        Ph.copy_(S["P"], non_blocking=True)
+        Eh.copy_(S["E"], non_blocking=True)
+        sth.copy_(stats, non_blocking=True)
 
-    e2e_step()
     torch.cuda.synchronize()
+    stats.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
@@ -255,34 +327,84 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
-    e2e_ms_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    e2e_props = float(stats[:4, 0].sum().item()) / args.steps
+    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
     if world > 1:
-        dist.all_reduce(e2e_ms_t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(e2e_ms_t.item())
-    fl = flops_per_proposal()
-    peak_alu = 152 * 128 * 2 * 2.07e9 / 1e12     # FP32 lanes x FMA x max SM clock
-    ach = fl * W["n"] / (float(np.mean(ms)) * 1e-3) / 1e12
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_ms = float(e2e_t.item())
+    h2d = S["P"].numel() * 8 + S["E"].numel()
+    d2h = h2d + 80
+
+    # the plain float64 path on the same GPU: (a) the same sweep in float64, one step;
+    # (b) per-source launches of the float64 Delta lnL (one proposal per launch)
+    fp64 = {}
+    if not args.no_fp64:
+        S64 = build_device_state(torch, L, dev, ens, L.GBK_FP64, seed=1 + 1000 * rank)
+        st64 = torch.zeros((5, 2), dtype=torch.int64, device=dev)
+        L.gb_sweep(S64["plan"], S64["P"], S64["E"], S64["betas"], S64["R"], S64["psd"], key, 0, 1 | 2 | 4 | 8,
+                   stats=st64, stream=stream)
+        torch.cuda.synchronize()
+        st64.zero_()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        L.gb_sweep(S64["plan"], S64["P"], S64["E"], S64["betas"], S64["R"], S64["psd"], key, 1, 1 | 2 | 4,
+                   stats=st64, stream=stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        fp64["fp64_sweep_proposals_per_s"] = float(st64[:4, 0].sum().item()) / (a0.elapsed_time(a1) * 1e-3)
+        # per-source plain path
+        n1 = 200
+        pnew = torch.from_numpy(ens["params"][0, 0].reshape(-1, 8)[ens["exists"][0, 0].reshape(-1).astype(bool)][:n1].T
+                                .copy()).to(dev)
+        one_nb = torch.full((1,), N_BAND, dtype=torch.int32, device=dev)
+        one_w = torch.zeros(1, dtype=torch.int32, device=dev)
+        out1 = torch.empty(1, dtype=torch.float64, device=dev)
+        cols = [pnew[:, i:i + 1].contiguous() for i in range(pnew.shape[1])]
+        for c in cols[:5]:
+            L.gb_delta_loglike_batch(S64["ctx"], c, c, one_nb, N_BAND, one_w, S64["R"], S64["psd"], out1, L.GBK_FP64, stream)
+        torch.cuda.synchronize()
+        a0.record(stream)
+        for c in cols:
+            L.gb_delta_loglike_batch(S64["ctx"], c, c, one_nb, N_BAND, one_w, S64["R"], S64["psd"], out1, L.GBK_FP64, stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        fp64["fp64_per_source_proposals_per_s"] = len(cols) / (a0.elapsed_time(a1) * 1e-3)
+        S64["plan"].close()
+        del S64
     line = {
         "metric": METRIC, "value": value, "unit": "proposals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded noise + injected GBs; LDC2A not available)",
-        "config": {"workload": WORKLOAD, "global_batch": total_props, "n_temps": N_T, "n_walkers": N_W,
-                   "n_sources_per_walker": N_SRC, "band_bins": N_BAND, "precision": "mixed",
-                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replica per GPU"},
-        "roofline": {"bound": "alu", "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s", "frac": ach / peak_alu,
-                     "traffic": None,
-                     "peak_note": "FP32: 152 SMs x 128 lanes x 2 (FMA) x 2.07 GHz; kernel k_dlogl<float,256>",
-                     "flops_per_proposal": fl},
-        "e2e": {"value": total_props / (e2e_ms * 1e-3), "unit": "proposals/s",
-                "h2d_bytes_per_step": 2 * 8 * 8 * W["n"], "d2h_bytes_per_step": 8 * W["n"]},
-        "gpu_launches": launches,
+        "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic: seeded noise + injected GBs drawn from the configured priors (LDC2A data not available)",
+        "config": {"workload": WORKLOAD, "n_temps": int(args.n_temps), "n_walkers": N_W, "gbs_per_walker": N_SRC,
+                   "band_bins": N_BAND, "n_bands": ens["n_bands"], "slots_per_band": ens["n_max"],
+                   "precision": "mixed", "l2": "working set > L2 (16 GB waveform cache, 0.25 GB params); no flush",
+                   "proposals_per_step": {"in_model": float(st[0, 0]) / args.steps,
+                                          "birth": float(st[1, 0]) / args.steps,
+                                          "death": float(st[2, 0]) / args.steps,
+                                          "swap": float(st[3, 0]) / args.steps},
+                   "acceptance": {k: (float(st[i, 1]) / max(1.0, float(st[i, 0]))) for i, k in
+                                  enumerate(["in_model", "birth", "death", "swap"])},
+                   "waveforms_per_step": wf / args.steps,
+                   "kernel_ms_per_step": {"open": kms[1] / args.steps, "band": band_ms, "swap": kms[3] / args.steps},
+                   "parallelism": "replica per GPU"},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach / PEAK_FP32_TFLOPS, "traffic": None,
+                     "kernel": "k_band<float,256> (in-model + flip-all RJ)",
+                     "peak_note": "FP32 ALU: 152 SMs x 128 lanes x 2 (FMA) x 2.07 GHz (derived, not measured)",
+                     "flops_per_waveform": flops_per_waveform(), "flops_per_evaluation": flops_per_evaluation()},
+        "e2e": {"value": e2e_props * world / (e2e_ms * 1e-3), "unit": "proposals/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 6 * args.steps,
         "clocks": clk,
         "wall_s_timed_region": wall,
     }
+    line["config"].update(fp64)
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line), flush=True)
+    S["plan"].close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -291,17 +413,17 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per = []
     for _ in range(args.warmup):
-        cpu_baseline(sample=400)
-    vals = [cpu_baseline(sample=800) for _ in range(args.steps)]
+        cpu_baseline(n_bands=2)
+    vals = [cpu_baseline(n_bands=4) for _ in range(args.steps)]
     v = float(np.mean([x["value"] for x in vals]))
     cb = dict(vals[-1])
     cb["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "proposals/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (each step a bounded sample of 800 proposals on the host cores)"},
+            "config": {"workload": WORKLOAD + " (each step a bounded sample: one oracle sweep of 4 sub-bands per "
+                                              "host core)"},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "proposals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -314,6 +436,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison runs")
     ap.add_argument("--n-temps", type=int, default=N_T, help="smaller ensemble for profiling captures")
     args = ap.parse_args()
     if args.impl == "reference":

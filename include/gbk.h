@@ -239,6 +239,7 @@ gbk_status gbk_sweep_destroy(gbk_sweep* plan);
 #define GBK_SWEEP_RJ 2
 #define GBK_SWEEP_SWAP 4
 #define GBK_SWEEP_REFRESH 8   /* regenerate the waveform cache from params/exists first */
+#define GBK_SWEEP_TIMING 16   /* record CUDA events around each kernel (see gbk_sweep_kernel_ms) */
 
 /*
  * gb_sweep -- one sweep (both parities) on `stream`; allocates nothing.
@@ -247,13 +248,20 @@ gbk_status gbk_sweep_destroy(gbk_sweep* plan);
  *   betas    [n_bands][n_temps] float64 inverse temperatures (0 allowed: T = infinity)
  *   residual cold-chain residual of every walker (d - H of the t = 0 sources), in/out
  *   psd      per-walker PSD
- *   stats    [4][2] int64 (proposed, accepted) for in-model, birth, death, swap; added to; or NULL
+ *   stats    [5][2] int64, added to, or NULL: rows 0-3 (proposed, accepted) for in-model,
+ *            birth, death, swap; row 4 (waveforms generated, likelihood evaluations) of
+ *            the band kernel
  *   trace    or NULL
  */
 gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists, const double* betas,
                     const gbk_residual* residual, const gbk_psd* psd, uint64_t key,
                     uint32_t sweep_index, int32_t flags, const gbk_trace* trace, int64_t* stats,
                     void* stream);
+
+/* Device time in ms of the last sweep run with GBK_SWEEP_TIMING, per kernel kind:
+ * ms_out[0] cache refresh, [1] band opening, [2] band kernel (in-model + RJ), [3]
+ * tempering swaps, each summed over both parities. Synchronises with those events. */
+gbk_status gbk_sweep_kernel_ms(gbk_sweep* plan, double* ms_out);
 
 #ifdef __cplusplus
 }

@@ -60,6 +60,7 @@ SWEEP_INMODEL = 1
 SWEEP_RJ = 2
 SWEEP_SWAP = 4
 SWEEP_REFRESH = 8
+SWEEP_TIMING = 16
 TRACE_DTYPE_FIELDS = [("kind", "<i4"), ("t", "<i4"), ("w", "<i4"), ("b", "<i4"), ("slot", "<i4"), ("seq", "<i4"),
                       ("accepted", "<i4"), ("parity", "<i4"), ("dlogl", "<f8"), ("log_alpha", "<f8"),
                       ("params", "<f8", (8,))]
@@ -79,6 +80,7 @@ SIGNATURES = {
     "total_loglike": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp]),
     "gbk_sweep_create": (ctypes.c_int, [_vp, ctypes.POINTER(GbkSweepDesc), ctypes.POINTER(_vp)]),
     "gbk_sweep_destroy": (ctypes.c_int, [_vp]),
+    "gbk_sweep_kernel_ms": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "gb_sweep": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(GbkResidual), ctypes.POINTER(GbkPsd),
                                 ctypes.c_uint64, ctypes.c_uint32, _i32, ctypes.POINTER(GbkTrace), _vp, _vp]),
 }
@@ -261,3 +263,10 @@ def gb_sweep(plan, params, exists, betas, residual, psd, key, sweep_index, flags
                           ctypes.c_uint64(int(key)), ctypes.c_uint32(int(sweep_index)), int(flags),
                           ctypes.byref(tr) if tr is not None else None,
                           _dev(stats, torch.int64, "stats") if stats is not None else None, _stream(stream)), "gb_sweep")
+
+
+def gbk_sweep_kernel_ms(plan):
+    """Per-kernel device ms of the last timed sweep: (refresh, open, band, swap)."""
+    out = (ctypes.c_double * 4)()
+    _check(lib().gbk_sweep_kernel_ms(plan.handle, out), "gbk_sweep_kernel_ms")
+    return list(out)

@@ -16,6 +16,8 @@ struct gbk_sweep {
   void* rho;            // opened windows [W][n_bp_max][2][3N], complex of the sweep precision
   void* wcache;         // current waveform of every slot [T][W][B][n_max][2][N]
   size_t rho_bytes, cache_bytes;
+  cudaEvent_t ev[2][4][2];  // [parity][refresh, open, band, swap][begin, end] when timing
+  bool timed, have_ev;
 };
 
 namespace gbk {
@@ -156,6 +158,14 @@ __device__ __forceinline__ void fill_words(uint32_t* words, int nblk, uint32_t b
     words[4 * m] = v.x; words[4 * m + 1] = v.y; words[4 * m + 2] = v.z; words[4 * m + 3] = v.w;
   }
   __syncwarp();
+}
+
+// stats row 4: (waveforms generated, likelihood evaluations) of the band kernel.
+__device__ __forceinline__ void count_work(const SweepArgs& a, int wf, int ev) {
+  if (a.stats) {
+    if (wf) atomicAdd((unsigned long long*)&a.stats[8], (unsigned long long)wf);
+    if (ev) atomicAdd((unsigned long long*)&a.stats[9], (unsigned long long)ev);
+  }
 }
 
 __device__ __forceinline__ void record(const SweepArgs& a, int kind, int t, int w, int b, int slot, int seq,
@@ -502,7 +512,10 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
           const double dll = window_dll<T, N>(a, S.rw, S.ba, oa, hr, orr, gw, pw, lane);
           const double la = beta * dll + S.lpn[q] - S.lp[k];
           const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
-          if (lane == 0) record(a, 0, t, w, b, k, jp, acc, dll, la, S.th[q]);
+          if (lane == 0) {
+            record(a, 0, t, w, b, k, jp, acc, dll, la, S.th[q]);
+            count_work(a, 1, 1);
+          }
           if (acc) {
             apply_change<T, N>(a, S.rw, S.ba, oa, hr, orr, cold, Rw, gw, gs, lane);
             __syncwarp();
@@ -567,7 +580,10 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
             const double dll = window_dll<T, N>(a, S.rw, (const C*)nullptr, 0, hr, orr, gw, pw, lane);
             const double la = beta * dll - d.log_occ_odds;
             const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
-            if (lane == 0) record(a, 2, t, w, b, s, jp, acc, dll, la, P + s * 8);
+            if (lane == 0) {
+              record(a, 2, t, w, b, s, jp, acc, dll, la, P + s * 8);
+              count_work(a, 0, 1);
+            }
             if (acc) {
               apply_change<T, N>(a, S.rw, (const C*)nullptr, 0, hr, orr, cold, Rw, gw, gs, lane);
               __syncwarp();
@@ -579,7 +595,10 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
             const double dll = window_dll<T, N>(a, S.rw, S.ba, oa, (const C*)nullptr, 0, gw, pw, lane);
             const double la = beta * dll + d.log_occ_odds;
             const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
-            if (lane == 0) record(a, 1, t, w, b, s, jp, acc, dll, la, S.th[q]);
+            if (lane == 0) {
+              record(a, 1, t, w, b, s, jp, acc, dll, la, S.th[q]);
+              count_work(a, 1, 1);
+            }
             if (acc) {
               apply_change<T, N>(a, S.rw, S.ba, oa, (const C*)nullptr, 0, cold, Rw, gw, gs, lane);
               copy_band(cache_ptr<T>(a, base + s), S.ba, 2 * N, lane);
@@ -794,6 +813,11 @@ static gbk_status prep(K kernel, size_t per_warp, int64_t items, int* grid, int*
   return GBK_OK;
 }
 
+static gbk_sweep* g_timing_plan = nullptr;  // plan whose kernels are being timed (set per call)
+static void ev_rec(int parity, int which, int edge, cudaStream_t st) {
+  if (g_timing_plan && g_timing_plan->timed) cudaEventRecord(g_timing_plan->ev[parity][which][edge], st);
+}
+
 template <typename T, int N>
 static gbk_status run_refresh(SweepArgs& a, cudaStream_t st) {
   const int64_t nslot = (int64_t)a.d.n_temps * a.d.n_walkers * a.d.n_bands * a.d.n_max;
@@ -802,7 +826,9 @@ static gbk_status run_refresh(SweepArgs& a, cudaStream_t st) {
   size_t sm = 0;
   gbk_status s;
   if ((s = prep(k_refresh<T, N>, refresh_warp_bytes<T, N>(), (nslot + 31) / 32, &grid, &thr, &sm))) return s;
+  ev_rec(1, 0, 0, st);
   k_refresh<T, N><<<grid, thr, sm, st>>>(a);
+  ev_rec(1, 0, 1, st);
   return check_launch("gb_sweep(refresh)");
 }
 
@@ -815,19 +841,25 @@ static gbk_status run_half(SweepArgs& a, int flags, cudaStream_t st) {
   int grid = 0, thr = 0;
   size_t sm = 0;
   if ((s = prep(k_open<T, N>, 0, (int64_t)d.n_walkers * nbp, &grid, &thr, &sm))) return s;
+  ev_rec(a.parity, 1, 0, st);
   k_open<T, N><<<grid, kSwWarps * 32, 0, st>>>(a);
+  ev_rec(a.parity, 1, 1, st);
   if ((s = check_launch("gb_sweep(open)"))) return s;
   if (flags & (GBK_SWEEP_INMODEL | GBK_SWEEP_RJ)) {
     if ((s = prep(k_band<T, N>, sizeof(BandSmem<T, N>), (int64_t)d.n_temps * d.n_walkers * nbp, &grid, &thr, &sm)))
       return s;
+    ev_rec(a.parity, 2, 0, st);
     k_band<T, N><<<grid, thr, sm, st>>>(a, flags);
+    ev_rec(a.parity, 2, 1, st);
     if ((s = check_launch("gb_sweep(band)"))) return s;
   }
   if (flags & GBK_SWEEP_SWAP) {
     if ((s = prep(k_swap<T, N>, swap_warp_bytes<T, N>(d.n_temps, d.n_walkers), (int64_t)d.n_walkers * nbp, &grid,
                   &thr, &sm)))
       return s;
+    ev_rec(a.parity, 3, 0, st);
     k_swap<T, N><<<grid, thr, sm, st>>>(a);
+    ev_rec(a.parity, 3, 1, st);
     if ((s = check_launch("gb_sweep(swap)"))) return s;
   }
   return GBK_OK;
@@ -910,7 +942,28 @@ extern "C" gbk_status gbk_sweep_destroy(gbk_sweep* plan) {
   cudaFree(plan->rsnap);
   cudaFree(plan->rho);
   cudaFree(plan->wcache);
+  if (plan->have_ev)
+    for (int p = 0; p < 2; ++p)
+      for (int k = 0; k < 4; ++k)
+        for (int e = 0; e < 2; ++e) cudaEventDestroy(plan->ev[p][k][e]);
   free(plan);
+  return GBK_OK;
+}
+
+extern "C" gbk_status gbk_sweep_kernel_ms(gbk_sweep* plan, double* ms_out) {
+  if (!plan || !ms_out) return set_error(GBK_EINVAL, "gbk_sweep_kernel_ms: null argument");
+  if (!plan->have_ev) return set_error(GBK_EINVAL, "gbk_sweep_kernel_ms: no timed sweep yet");
+  for (int k = 0; k < 4; ++k) {
+    ms_out[k] = 0.0;
+    for (int p = 0; p < 2; ++p) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(plan->ev[p][k][1]) == cudaSuccess &&
+          cudaEventElapsedTime(&ms, plan->ev[p][k][0], plan->ev[p][k][1]) == cudaSuccess)
+        ms_out[k] += ms;
+      else
+        cudaGetLastError();
+    }
+  }
   return GBK_OK;
 }
 
@@ -923,7 +976,7 @@ extern "C" gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists,
   if (residual->n_walkers != plan->d.n_walkers || residual->frac_bits < 40 || residual->frac_bits > 120)
     return set_error(GBK_EINVAL, "gb_sweep: residual must hold n_walkers = %d walkers", plan->d.n_walkers);
   if (psd->n_psd != 1 && psd->n_psd < plan->d.n_walkers) return set_error(GBK_EINVAL, "gb_sweep: psd covers too few walkers");
-  if (flags & ~(GBK_SWEEP_INMODEL | GBK_SWEEP_RJ | GBK_SWEEP_SWAP | GBK_SWEEP_REFRESH))
+  if (flags & ~(GBK_SWEEP_INMODEL | GBK_SWEEP_RJ | GBK_SWEEP_SWAP | GBK_SWEEP_REFRESH | GBK_SWEEP_TIMING))
     return set_error(GBK_EINVAL, "gb_sweep: unknown flags 0x%x", flags);
   SweepArgs a;
   a.c = *plan->ctx;
@@ -949,6 +1002,23 @@ extern "C" gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists,
   a.trace_count = trace ? trace->count : nullptr;
   a.stats = (long long*)stats;
   cudaStream_t st = (cudaStream_t)stream;
-  if (plan->d.precision == GBK_MIXED) return run_sweep<float>(plan, a, flags, st);
-  return run_sweep<double>(plan, a, flags, st);
+  plan->timed = (flags & GBK_SWEEP_TIMING) != 0;
+  if (plan->timed && !plan->have_ev) {
+    for (int p = 0; p < 2; ++p)
+      for (int k = 0; k < 4; ++k)
+        for (int e = 0; e < 2; ++e) cudaEventCreate(&plan->ev[p][k][e]);
+    plan->have_ev = true;
+  }
+  if (plan->timed) {   // kernels that do not run this call report 0 ms
+    for (int p = 0; p < 2; ++p)
+      for (int k = 0; k < 4; ++k) {
+        cudaEventRecord(plan->ev[p][k][0], st);
+        cudaEventRecord(plan->ev[p][k][1], st);
+      }
+  }
+  g_timing_plan = plan;
+  gbk_status s = (plan->d.precision == GBK_MIXED) ? run_sweep<float>(plan, a, flags & ~GBK_SWEEP_TIMING, st)
+                                                  : run_sweep<double>(plan, a, flags & ~GBK_SWEEP_TIMING, st);
+  g_timing_plan = nullptr;
+  return s;
 }

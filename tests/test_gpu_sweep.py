@@ -35,7 +35,7 @@ def _gpu_sweep(torch, cfg, state, precision, sweeps=1, flags=ALL, trace_cap=2000
     psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
     rec = torch.zeros(trace_cap * ctypes.sizeof(L.GbkTraceRec), dtype=torch.uint8, device=dev)
     cnt = torch.zeros(1, dtype=torch.int32, device=dev)
-    stats = torch.zeros((4, 2), dtype=torch.int64, device=dev)
+    stats = torch.zeros((5, 2), dtype=torch.int64, device=dev)
     for k in range(sweeps):
         L.gb_sweep(plan, P, E, betas, L.residual_struct(R, FRAC), L.psd_struct(psdp), key64(cfg), k,
                    flags | (L.SWEEP_REFRESH if k == 0 else 0), trace=(rec, trace_cap, cnt), stats=stats)
@@ -95,7 +95,7 @@ def test_sweep_fp64_matches_oracle_exactly():
     assert diff < 2 ** 20, diff
     kinds = stats[:, 0]
     assert kinds[0] > 0 and kinds[1] > 0 and kinds[3] > 0
-    assert stats[:, 0].sum() == len(gtr)
+    assert stats[:4, 0].sum() == len(gtr)
 
 
 def test_sweep_mixed_matches_oracle_until_a_justified_flip():
@@ -157,7 +157,7 @@ def test_sweep_cold_residual_is_exact():
         E = torch.from_numpy(state["exists"].astype(np.uint8)).to(dev)
         betas = torch.from_numpy(np.ascontiguousarray(cfg.betas)).to(dev)
         psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
-        stats = torch.zeros((4, 2), dtype=torch.int64, device=dev)
+        stats = torch.zeros((5, 2), dtype=torch.int64, device=dev)
         for k in range(4):
             L.gb_sweep(plan, P, E, betas, RS, L.psd_struct(psdp), key64(cfg), 10 + k,
                        ALL | (L.SWEEP_REFRESH if k == 0 else 0), stats=stats)
