@@ -66,8 +66,9 @@ class SweepConfig:
       [mc_min, mc_max] (fdot induced, density ~ fdot^-2/5 f0^-11/5); phi0, psi,
       lambda uniform and periodic; cos iota, sin beta uniform on [-1, 1];
     * in-model move: every coordinate perturbed by sigma_c z_c with z_c the
-      Irwin-Hall(4) variable (sum of four uniforms, centred, unit variance), ln A
-      perturbed instead of A (its Hastings factor cancels the 1/A prior);
+      Irwin-Hall(4) variable (sum of four uniforms, centred, unit variance), except A,
+      which is multiplied by exp(sigma_A z) (a symmetric move in ln A, whose Hastings
+      factor cancels the 1/A prior);
     * n_prop = round(props_per_source * g) in-model proposals per band task, g the
       number of sources in the band at the start of the task.
     """
@@ -120,23 +121,31 @@ def fdot_from_mc(f0, mc):
 
 
 def in_support(cfg, th, b):
+    """Prior support of a source of band b: f0 in the band's allowance, A in
+    [A_min, A_max], |cos iota|, |sin beta| <= 1, chirp mass in [mc_min, mc_max] (written
+    as an fdot interval at the source's f0)."""
     a, f0, fd, _, _, ci, sb, _ = th
     lo, hi = cfg.allowance(b)
     if not (lo <= f0 < hi):
         return False
-    if not (a > 0) or not (cfg.ln_a_min <= math.log(a) <= cfg.ln_a_max):
+    if not (math.exp(cfg.ln_a_min) <= a <= math.exp(cfg.ln_a_max)):
         return False
     if not (-1.0 <= ci <= 1.0 and -1.0 <= sb <= 1.0):
         return False
-    if not (fd > 0):
-        return False
-    mc = chirp_mass(f0, fd)
-    return cfg.mc_min <= mc <= cfg.mc_max
+    f113 = f0 ** (11.0 / 3.0)
+    c_lo = K_CHIRP * (cfg.mc_min * GM_SUN_C3) ** (5.0 / 3.0)
+    c_hi = K_CHIRP * (cfg.mc_max * GM_SUN_C3) ** (5.0 / 3.0)
+    return c_lo * f113 <= fd <= c_hi * f113
 
 
 def log_prior_shape(th):
     """Non-uniform part of the prior in the sampled coordinates: ln p(fdot | f0)."""
     return -0.4 * math.log(th[2]) - 2.2 * math.log(th[1])
+
+
+def dlog_prior(new, th):
+    """ln p(new) - ln p(th) of the non-uniform prior factor, from logs of ratios."""
+    return -0.4 * math.log(new[2] / th[2]) - 2.2 * math.log(new[1] / th[1])
 
 
 def _wrap(x, period):
@@ -160,7 +169,7 @@ def propose_in_model(cfg, th, words):
            + PX.u24(words[4 + 4 * c])) - 2.0) * SQRT3 for c in range(8)]
     s = cfg.sigma
     new = list(th)
-    new[0] = math.exp(math.log(th[0]) + s[0] * z[0])
+    new[0] = th[0] * math.exp(s[0] * z[0])
     new[1] = th[1] + s[1] * z[1]
     new[2] = th[2] + s[2] * z[2]
     new[3] = _wrap(th[3] + s[3] * z[3], TWO_PI)
@@ -258,7 +267,7 @@ def band_task(cfg, state, r_snap, rho, t, w, b, parity, sweep, trace):
             trace.append(_rec(0, t, w, b, k, j, False, parity, float("nan"), -math.inf, new, lu))
             continue
         dll = _swap_dll(cfg, rp, psd_w, b, new, th)
-        la = beta * dll + log_prior_shape(new) - log_prior_shape(th)
+        la = beta * dll + dlog_prior(new, th)
         acc = lu < la
         trace.append(_rec(0, t, w, b, k, j, acc, parity, dll, la, new, lu))
         if acc:

@@ -85,27 +85,43 @@ __device__ __forceinline__ void allowance(const gbk_sweep_desc& d, double tobs, 
   if (hi > d.f_max) hi = d.f_max;
 }
 
-__device__ __forceinline__ double chirp_mass(double f0, double fd) {
+// Prior support of a source of band b (lo <= f0 < hi over the band's allowance;
+// A_min <= A <= A_max; |cos i|, |sin b| <= 1; chirp mass in [mc_min, mc_max] written as
+// c_lo f0^(11/3) <= fdot <= c_hi f0^(11/3) with c = 96/5 pi^(8/3) (mc G M_sun / c^3)^(5/3)).
+struct PriorK {
+  double a_min, a_max, c_lo, c_hi;
+};
+__device__ __forceinline__ PriorK prior_consts(const gbk_sweep_desc& d) {
   const double K = 96.0 / 5.0 * 21.170591578193026;  // pi^(8/3)
-  return pow(fd / (K * pow(f0, 11.0 / 3.0)), 0.6) / 4.925490947e-6;
+  PriorK p;
+  p.a_min = exp(d.ln_a_min);
+  p.a_max = exp(d.ln_a_max);
+  p.c_lo = K * pow(d.mc_min * 4.925490947e-6, 5.0 / 3.0);
+  p.c_hi = K * pow(d.mc_max * 4.925490947e-6, 5.0 / 3.0);
+  return p;
 }
 
-__device__ __forceinline__ bool in_support(const gbk_sweep_desc& d, double tobs, int b, const double* th) {
+__device__ __forceinline__ bool in_support(const gbk_sweep_desc& d, const PriorK& pk, double tobs, int b,
+                                           const double* th) {
   double lo, hi;
   allowance(d, tobs, b, lo, hi);
   if (!(th[1] >= lo && th[1] < hi)) return false;
-  if (!(th[0] > 0.0)) return false;
-  const double la = log(th[0]);
-  if (!(la >= d.ln_a_min && la <= d.ln_a_max)) return false;
+  if (!(th[0] >= pk.a_min && th[0] <= pk.a_max)) return false;
   if (!(th[5] >= -1.0 && th[5] <= 1.0 && th[6] >= -1.0 && th[6] <= 1.0)) return false;
-  if (!(th[2] > 0.0)) return false;
-  const double mc = chirp_mass(th[1], th[2]);
-  return mc >= d.mc_min && mc <= d.mc_max;
+  const double f113 = pow(th[1], 11.0 / 3.0);
+  return th[2] >= dmul(pk.c_lo, f113) && th[2] <= dmul(pk.c_hi, f113);
 }
 
-__device__ __forceinline__ double log_prior_shape(const double* th) {
-  return dsub(dmul(-0.4, log(th[2])), dmul(2.2, log(th[1])));
+// ln p(theta') - ln p(theta) of the non-uniform prior factor p(fdot | f0) ~ fdot^-2/5 f0^-11/5,
+// from logarithms of ratios (precision of the sweep's arithmetic type).
+__device__ __forceinline__ double dlog_prior(const double* nw, const double* th, float) {
+  return (double)(-0.4f * logf((float)(nw[2] / th[2])) - 2.2f * logf((float)(nw[1] / th[1])));
 }
+__device__ __forceinline__ double dlog_prior(const double* nw, const double* th, double) {
+  return dsub(dmul(-0.4, log(nw[2] / th[2])), dmul(2.2, log(nw[1] / th[1])));
+}
+__device__ __forceinline__ double log_u(double u, float) { return u > 0.0 ? (double)logf((float)u) : -INFINITY; }
+__device__ __forceinline__ double log_u(double u, double) { return u > 0.0 ? log(u) : -INFINITY; }
 
 __device__ __forceinline__ double wrap(double x, double period) {
   if (x >= period) return dsub(x, period);
@@ -122,7 +138,7 @@ __device__ __forceinline__ void propose(const gbk_sweep_desc& d, const double* t
     z[c] = dmul(dsub(s4, 2.0), 1.7320508075688772);
   }
   const double TWO_PI = 6.283185307179586, PI = 3.141592653589793;
-  nw[0] = exp(dadd(log(th[0]), dmul(d.sigma[0], z[0])));
+  nw[0] = dmul(th[0], exp(dmul(d.sigma[0], z[0])));
   nw[1] = dadd(th[1], dmul(d.sigma[1], z[1]));
   nw[2] = dadd(th[2], dmul(d.sigma[2], z[2]));
   nw[3] = wrap(dadd(th[3], dmul(d.sigma[3], z[3])), TWO_PI);
@@ -160,20 +176,28 @@ __device__ __forceinline__ void fill_words(uint32_t* words, int nblk, uint32_t b
   __syncwarp();
 }
 
-// stats row 4: (waveforms generated, likelihood evaluations) of the band kernel.
-__device__ __forceinline__ void count_work(const SweepArgs& a, int wf, int ev) {
-  if (a.stats) {
-    if (wf) atomicAdd((unsigned long long*)&a.stats[8], (unsigned long long)wf);
-    if (ev) atomicAdd((unsigned long long*)&a.stats[9], (unsigned long long)ev);
+// Move statistics are counted per warp (lane 0) and added to the global counters once
+// per kernel: same-address atomics from every proposal would serialise in L2.
+struct WarpStats {
+  unsigned long long c[10];  // rows 0-3 (proposed, accepted) per kind, row 4 (waveforms, evaluations)
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) c[i] = 0ull;
   }
-}
+  __device__ __forceinline__ void flush(const long long* stats) {
+    if (!stats) return;
+#pragma unroll
+    for (int i = 0; i < 10; ++i)
+      if (c[i]) atomicAdd((unsigned long long*)&stats[i], c[i]);
+  }
+};
 
-__device__ __forceinline__ void record(const SweepArgs& a, int kind, int t, int w, int b, int slot, int seq,
-                                       bool acc, double dll, double la, const double* th) {
-  if (a.stats) {
-    atomicAdd((unsigned long long*)&a.stats[2 * kind], 1ull);
-    if (acc) atomicAdd((unsigned long long*)&a.stats[2 * kind + 1], 1ull);
-  }
+__device__ __forceinline__ void record(const SweepArgs& a, WarpStats& ws, int kind, int t, int w, int b, int slot,
+                                       int seq, bool acc, double dll, double la, const double* th, int wf, int ev) {
+  ws.c[2 * kind] += 1ull;
+  if (acc) ws.c[2 * kind + 1] += 1ull;
+  ws.c[8] += (unsigned long long)wf;
+  ws.c[9] += (unsigned long long)ev;
   if (a.trace_count) {
     const int i = atomicAdd(a.trace_count, 1);
     if (a.trace && i < a.trace_cap) {
@@ -390,16 +414,15 @@ struct BandSmem {
   typename CT<T>::C ba[2 * N], bs[2 * N];
   Src<T> src[32];                      // constants of the batch's new templates
   double th[32][8];                    // proposed parameters
-  double lpn[32], lu[32];              // log prior shape of the proposal, ln u
-  double lp[kMaxSlots];                // log prior shape of every slot's current parameters
+  double lpn[32], lu[32];              // prior log-ratio of the proposal, ln u
   int k[32], supp[32];
   int list[kMaxSlots];
 };
 
 // Set up proposal j (lane-parallel): words, source, perturbation, support, prior, constants.
 template <typename T, int N>
-__device__ void prep_inmodel(const SweepArgs& a, BandSmem<T, N>& S, int l, int jp, uint32_t tid, int g,
-                             const double* P, int b) {
+__device__ void prep_inmodel(const SweepArgs& a, const PriorK& pk, BandSmem<T, N>& S, int l, int jp, uint32_t tid,
+                             int g, const double* P, int b) {
   const gbk_sweep_desc& d = a.d;
   uint32_t w[48];
 #pragma unroll
@@ -412,15 +435,14 @@ __device__ void prep_inmodel(const SweepArgs& a, BandSmem<T, N>& S, int l, int j
 #pragma unroll
   for (int c = 0; c < 8; ++c) th[c] = P[k * 8 + c];
   propose(d, th, w, nw);
-  const double u = u53(w[33], w[34]);
-  S.lu[l] = u > 0.0 ? log(u) : -INFINITY;
+  S.lu[l] = log_u(u53(w[33], w[34]), T());
   S.k[l] = k;
-  const bool ok = in_support(d, a.c.grid.tobs, b, nw);
+  const bool ok = in_support(d, pk, a.c.grid.tobs, b, nw);
   S.supp[l] = ok ? 1 : 0;
 #pragma unroll
   for (int c = 0; c < 8; ++c) S.th[l][c] = nw[c];
   if (ok) {
-    S.lpn[l] = log_prior_shape(nw);
+    S.lpn[l] = dlog_prior(nw, th, T());
     S.src[l] = make_src<T>(nw, 1, 0, a.c.grid.tobs, N);
   }
 }
@@ -441,6 +463,9 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
   const T gs = (T)ldexp(1.0, a.frac_bits - kStrainExp);
   const T* orb = orb_of<T>(a.c, band_index(N));
   const C* tw = tw_of<T>(a.c, band_index(N));
+  WarpStats ws;
+  ws.init();
+  const PriorK pk = prior_consts(d);
   for (int64_t x = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; x < ntask; x += (int64_t)gridDim.x * (blockDim.x >> 5)) {
     const int t = (int)(x / ((int64_t)d.n_walkers * nbp));
     const int rem = (int)(x % ((int64_t)d.n_walkers * nbp));
@@ -480,9 +505,6 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
         __syncwarp();
       }
     }
-    // log prior shape of the present slots (lane-parallel float64)
-    for (int s = lane; s < d.n_max; s += 32)
-      if (E[s]) S.lp[s] = log_prior_shape(P + s * 8);
     // ---- in-model proposals (Alg. 1)
     if (flags & GBK_SWEEP_INMODEL) {
       if (lane == 0) {
@@ -496,13 +518,13 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
       const int n_prop = (int)rint(d.props_per_source * (double)g);
       for (int j0 = 0; j0 < n_prop; j0 += 32) {
         const int cnt = min(32, n_prop - j0);
-        if (lane < cnt) prep_inmodel<T, N>(a, S, lane, j0 + lane, tid, g, P, b);
+        if (lane < cnt) prep_inmodel<T, N>(a, pk, S, lane, j0 + lane, tid, g, P, b);
         __syncwarp();
         for (int q = 0; q < cnt; ++q) {
           const int jp = j0 + q;
           const int k = S.k[q];
           if (!S.supp[q]) {
-            if (lane == 0) record(a, 0, t, w, b, k, jp, false, nan_d(), -INFINITY, S.th[q]);
+            if (lane == 0) record(a, ws, 0, t, w, b, k, jp, false, nan_d(), -INFINITY, S.th[q], 0, 0);
             continue;
           }
           gen_band<T, N>(&S.src[q], orb, tw, tobs, S.ba, S.bs, lane);
@@ -510,21 +532,17 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
           const int oa = band_off<N>(S.src[q].q, gw, a.c);
           const int orr = cached_off<N>(P + k * 8, gw, a.c);
           const double dll = window_dll<T, N>(a, S.rw, S.ba, oa, hr, orr, gw, pw, lane);
-          const double la = beta * dll + S.lpn[q] - S.lp[k];
+          const double la = beta * dll + S.lpn[q];
           const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
-          if (lane == 0) {
-            record(a, 0, t, w, b, k, jp, acc, dll, la, S.th[q]);
-            count_work(a, 1, 1);
-          }
+          if (lane == 0) record(a, ws, 0, t, w, b, k, jp, acc, dll, la, S.th[q], 1, 1);
           if (acc) {
             apply_change<T, N>(a, S.rw, S.ba, oa, hr, orr, cold, Rw, gw, gs, lane);
             __syncwarp();
             copy_band(cache_ptr<T>(a, base + k), S.ba, 2 * N, lane);
             if (lane < 8) P[k * 8 + lane] = S.th[q][lane];
-            if (lane == 0) S.lp[k] = S.lpn[q];
             __syncwarp();
             // later proposals of this batch that move the same source start from the new state
-            if (lane > q && lane < cnt && S.k[lane] == k) prep_inmodel<T, N>(a, S, lane, j0 + lane, tid, g, P, b);
+            if (lane > q && lane < cnt && S.k[lane] == k) prep_inmodel<T, N>(a, pk, S, lane, j0 + lane, tid, g, P, b);
           }
           __syncwarp();
         }
@@ -559,8 +577,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
             const U4 v = philox4x32_10(4u * jp + m, tid, 2u | ((uint32_t)a.parity << 4), a.sweep, a.k0, a.k1);
             wv[4 * m] = v.x; wv[4 * m + 1] = v.y; wv[4 * m + 2] = v.z; wv[4 * m + 3] = v.w;
           }
-          const double u = u53(wv[8], wv[9]);
-          S.lu[lane] = u > 0.0 ? log(u) : -INFINITY;
+          S.lu[lane] = log_u(u53(wv[8], wv[9]), T());
           S.k[lane] = s;
           if (!E[s]) {
             double nw[8];
@@ -580,10 +597,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
             const double dll = window_dll<T, N>(a, S.rw, (const C*)nullptr, 0, hr, orr, gw, pw, lane);
             const double la = beta * dll - d.log_occ_odds;
             const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
-            if (lane == 0) {
-              record(a, 2, t, w, b, s, jp, acc, dll, la, P + s * 8);
-              count_work(a, 0, 1);
-            }
+            if (lane == 0) record(a, ws, 2, t, w, b, s, jp, acc, dll, la, P + s * 8, 0, 1);
             if (acc) {
               apply_change<T, N>(a, S.rw, (const C*)nullptr, 0, hr, orr, cold, Rw, gw, gs, lane);
               __syncwarp();
@@ -595,10 +609,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
             const double dll = window_dll<T, N>(a, S.rw, S.ba, oa, (const C*)nullptr, 0, gw, pw, lane);
             const double la = beta * dll + d.log_occ_odds;
             const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
-            if (lane == 0) {
-              record(a, 1, t, w, b, s, jp, acc, dll, la, S.th[q]);
-              count_work(a, 1, 1);
-            }
+            if (lane == 0) record(a, ws, 1, t, w, b, s, jp, acc, dll, la, S.th[q], 1, 1);
             if (acc) {
               apply_change<T, N>(a, S.rw, S.ba, oa, (const C*)nullptr, 0, cold, Rw, gw, gs, lane);
               copy_band(cache_ptr<T>(a, base + s), S.ba, 2 * N, lane);
@@ -613,6 +624,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
     }
     __syncwarp();
   }
+  if (lane == 0) ws.flush(a.stats);
 }
 
 // -------------------------------------------------------------- tempering (Alg. 2)
@@ -709,6 +721,8 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_swap(const SweepArgs a) {
   const int nbp = (d.n_bands - a.parity + 1) / 2;
   const int64_t ntask = (int64_t)nbp * W;
   const int nslotc = 2 * N;
+  WarpStats ws;
+  ws.init();
   for (int64_t x = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; x < ntask; x += (int64_t)gridDim.x * (blockDim.x >> 5)) {
     const int j = (int)(x / W), c = (int)(x % W);
     const int b = a.parity + 2 * j;
@@ -773,10 +787,11 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_swap(const SweepArgs a) {
       } else {
         C* q = cur; cur = oth; oth = q;
       }
-      if (lane == 0) record(a, 3, t, wt, b, c, t, acc, la, la, nullptr);
+      if (lane == 0) record(a, ws, 3, t, wt, b, c, t, acc, la, la, nullptr, 0, 0);
       __syncwarp();
     }
   }
+  if (lane == 0) ws.flush(a.stats);
 }
 
 // -------------------------------------------------------------- host side

@@ -182,19 +182,20 @@ __device__ __noinline__ Src<T> make_src(const double* __restrict__ prm, int64_t 
     ph -= rint(ph);
     split<T>(ph, s.phh, s.phl);
   }
-  const double cbd = sqrt(1.0 - sinb * sinb);
-  double sld, cld;
-  sincos(lam, &sld, &cld);
+  // Sky angles in the arithmetic type: a relative error e in the Doppler amplitude is a
+  // phase error of ~e f0 AU/c cycles, which moves <a|a> not at all and <d-H|a> by
+  // ~SNR e f0 AU/c (far below 1e-2 for e ~ 1e-7); products with f0 are formed in float64.
+  const T sb = (T)sinb;
+  const T cb = sqrt((T)1 - sb * sb);
+  T sl, cl;
+  sincos_((T)lam, &sl, &cl);
   const double aoc = kAU / kC;
-  split<T>(-cbd * cld * f0 * aoc, s.dxh, s.dxl);
-  split<T>(-cbd * sld * f0 * aoc, s.dyh, s.dyl);
-  s.fkx = (T)(-cbd * cld * fdot * aoc);
-  s.fky = (T)(-cbd * sld * fdot * aoc);
+  split<T>(-(double)cb * (double)cl * f0 * aoc, s.dxh, s.dxl);
+  split<T>(-(double)cb * (double)sl * f0 * aoc, s.dyh, s.dyl);
+  s.fkx = (T)(-(double)cb * (double)cl * fdot * aoc);
+  s.fky = (T)(-(double)cb * (double)sl * fdot * aoc);
   s.f0 = (T)f0;
   s.fdot = (T)fdot;
-  const T sb = (T)sinb;
-  const T cb = (T)cbd;
-  const T sl = (T)sld, cl = (T)cld;
   T s2, c2;
   sincos_((T)(2.0 * psi), &s2, &c2);
   s.kx = -cb * cl; s.ky = -cb * sl; s.kz = -sb;
