@@ -226,10 +226,11 @@ typedef struct gbk_trace {
 typedef struct gbk_sweep gbk_sweep;
 
 /* Sweep plan: validates the description against the context grid and allocates the
- * sweep's device memory: a residual snapshot, the opened band windows, and a cache of
- * the current waveform of every slot ([T][W][B][n_max][2][N] complex, 15.5 GB in float32
- * for 16 x 32 x 369 bands x 20 slots at N = 256), so that deaths, band openings and
- * tempering swaps reuse waveforms instead of regenerating them. The cache must be
+ * sweep's device memory: a residual snapshot, the opened band windows, a cache of the
+ * current waveform of every slot ([T][W][B][n_max][2][N] complex, 15.5 GB in float32
+ * for 16 x 32 x 369 bands x 20 slots at N = 256) and a cache of every band's template
+ * sum on its window ([T][W][B][2][3N] complex, 1.2 GB), so that deaths, band openings
+ * and tempering swaps reuse waveforms instead of regenerating them. The caches must be
  * refreshed (GBK_SWEEP_REFRESH) whenever params/exists are changed outside gb_sweep. */
 gbk_status gbk_sweep_create(gbk_ctx* ctx, const gbk_sweep_desc* desc, gbk_sweep** out_plan);
 gbk_status gbk_sweep_destroy(gbk_sweep* plan);

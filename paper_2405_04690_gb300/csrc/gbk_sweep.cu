@@ -15,7 +15,8 @@ struct gbk_sweep {
   long long* rsnap;     // residual snapshot [W][2][n_bins][2]
   void* rho;            // opened windows [W][n_bp_max][2][3N], complex of the sweep precision
   void* wcache;         // current waveform of every slot [T][W][B][n_max][2][N]
-  size_t rho_bytes, cache_bytes;
+  void* hsum;           // sum of the present templates of every band on its window [T][W][B][2][3N]
+  size_t rho_bytes, cache_bytes, hsum_bytes;
   cudaEvent_t ev[2][4][2];  // [parity][refresh, open, band, swap][begin, end] when timing
   bool timed, have_ev;
 };
@@ -35,6 +36,7 @@ struct SweepArgs {
   const long long* rsnap; // snapshot taken at the start of the half sweep
   void* rho;
   void* wcache;
+  void* hsum;
   int n_bp_max;
   int32_t n_walkers_r;
   int32_t frac_bits;
@@ -233,6 +235,11 @@ __device__ __forceinline__ typename CT<T>::C* cache_ptr(const SweepArgs& a, int6
   return reinterpret_cast<typename CT<T>::C*>(a.wcache) + slot * 2 * a.d.band_bins;
 }
 template <typename T>
+__device__ __forceinline__ typename CT<T>::C* hsum_ptr(const SweepArgs& a, int t, int w, int b) {
+  return reinterpret_cast<typename CT<T>::C*>(a.hsum) +
+         (((int64_t)t * a.d.n_walkers + w) * a.d.n_bands + b) * 2 * 3 * a.d.band_bins;
+}
+template <typename T>
 __device__ __forceinline__ typename CT<T>::C* rho_ptr(const SweepArgs& a, int w, int j) {
   typedef typename CT<T>::C C;
   return reinterpret_cast<C*>(a.rho) + ((int64_t)w * a.n_bp_max + j) * 2 * 3 * a.d.band_bins;
@@ -251,7 +258,7 @@ __device__ __forceinline__ int cached_off(const double* th, int64_t gw, const gb
 // Delta lnL of swapping template r (br, window offset orr) for a (ba, offset oa) against
 // the window residual rw ([2][3N]); either may be absent. Window bin i is grid bin gw + i.
 template <typename T, int N>
-__device__ double window_dll(const SweepArgs& a, const typename CT<T>::C* rw, const typename CT<T>::C* ba, int oa,
+__device__ __noinline__ double window_dll(const SweepArgs& a, const typename CT<T>::C* rw, const typename CT<T>::C* ba, int oa,
                              const typename CT<T>::C* br, int orr, int64_t gw, const PsdWt<T>& pw, int lane) {
   typedef typename CT<T>::C C;
   constexpr int W3 = 3 * N;
@@ -290,7 +297,7 @@ __device__ double window_dll(const SweepArgs& a, const typename CT<T>::C* rw, co
 
 // r' <- r' - a + r over the window; for the cold chain also R <- R - round(a) + round(r).
 template <typename T, int N>
-__device__ void apply_change(const SweepArgs& a, typename CT<T>::C* rw, const typename CT<T>::C* ba, int oa,
+__device__ __noinline__ void apply_change(const SweepArgs& a, typename CT<T>::C* rw, const typename CT<T>::C* ba, int oa,
                              const typename CT<T>::C* br, int orr, bool cold, long long* rglob, int64_t gw, T gs,
                              int lane) {
   constexpr int W3 = 3 * N;
@@ -333,6 +340,54 @@ __device__ void apply_change(const SweepArgs& a, typename CT<T>::C* rw, const ty
 template <typename C>
 __device__ __forceinline__ void copy_band(C* dst, const C* src, int n2, int lane) {
   for (int i = lane; i < n2; i += 32) dst[i] = src[i];
+}
+
+// H(t, w, b) <- sum of the band's present cached templates on its window, summed in slot
+// order (deterministic), written to global memory.
+template <typename T, int N>
+__device__ __noinline__ void write_hsum(const SweepArgs& a, int t, int w, int b, int lane) {
+  typedef typename CT<T>::C C;
+  constexpr int W3 = 3 * N;
+  const gbk_sweep_desc& d = a.d;
+  C* H = hsum_ptr<T>(a, t, w, b);
+  const int64_t gw = d.band_k0 + (int64_t)(b - 1) * N - a.c.grid.k0;
+  const int64_t base = slot_index(d, t, w, b);
+  // lane-parallel offsets of the present slots (slot lane and slot lane + 32)
+  int off0 = -1, off1 = -1;
+  if (lane < d.n_max && a.exists[base + lane]) off0 = cached_off<N>(a.params + (base + lane) * 8, gw, a.c);
+  if (lane + 32 < d.n_max && a.exists[base + lane + 32]) off1 = cached_off<N>(a.params + (base + lane + 32) * 8, gw, a.c);
+  const unsigned p0 = __ballot_sync(0xffffffffu, off0 >= 0);
+  const unsigned p1 = __ballot_sync(0xffffffffu, off1 >= 0);
+  for (int i = lane; i < W3; i += 32) {
+    C xa = mkc((T)0, (T)0), xe = xa;
+    for (int half = 0; half < 2; ++half) {
+      for (unsigned m = half ? p1 : p0; m; m &= m - 1) {
+        const int sl = __ffs(m) - 1;
+        const int o = __shfl_sync(0xffffffffu, half ? off1 : off0, sl);
+        const int j = i - o;
+        if (j >= 0 && j < N) {
+          const C* h = cache_ptr<T>(a, base + sl + 32 * half);
+          xa = cadd(xa, h[j]);
+          xe = cadd(xe, h[N + j]);
+        }
+      }
+    }
+    H[i] = xa;
+    H[W3 + i] = xe;
+  }
+  __syncwarp();
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kSwWarps * 32) k_hsum(const SweepArgs a) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const gbk_sweep_desc& d = a.d;
+  const int64_t ntask = (int64_t)d.n_temps * d.n_walkers * d.n_bands;
+  for (int64_t x = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; x < ntask; x += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+    const int t = (int)(x / ((int64_t)d.n_walkers * d.n_bands));
+    const int rem = (int)(x % ((int64_t)d.n_walkers * d.n_bands));
+    write_hsum<T, N>(a, t, rem / d.n_bands, rem % d.n_bands, lane);
+  }
 }
 
 // -------------------------------------------------------------- cache refresh
@@ -392,17 +447,8 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_open(const SweepArgs a) {
         rho[ch * W3 + i] = mkc(i2t(v.x, T()) * rs, i2t(v.y, T()) * rs);
       }
     __syncwarp();
-    const int64_t base = slot_index(d, 0, w, b);
-    for (int s = 0; s < d.n_max; ++s) {
-      if (!a.exists[base + s]) continue;
-      const C* h = cache_ptr<T>(a, base + s);
-      const int o = cached_off<N>(a.params + (base + s) * 8, gw, a.c);
-      for (int i = lane; i < N; i += 32) {
-        rho[o + i] = cadd(rho[o + i], h[i]);
-        rho[W3 + o + i] = cadd(rho[W3 + o + i], h[N + i]);
-      }
-      __syncwarp();
-    }
+    const C* H = hsum_ptr<T>(a, 0, w, b);
+    for (int i = lane; i < 2 * W3; i += 32) rho[i] = cadd(rho[i], H[i]);
   }
 }
 
@@ -420,12 +466,14 @@ struct BandSmem {
 };
 
 // Set up proposal j (lane-parallel): words, source, perturbation, support, prior, constants.
+// __noinline__ and not unrolled over blocks: this set-up runs on a few lanes between
+// waveform generations, and its code must not crowd the instruction cache.
 template <typename T, int N>
-__device__ void prep_inmodel(const SweepArgs& a, const PriorK& pk, BandSmem<T, N>& S, int l, int jp, uint32_t tid,
-                             int g, const double* P, int b) {
+__device__ __noinline__ void prep_inmodel(const SweepArgs& a, const PriorK& pk, BandSmem<T, N>& S, int l, int jp,
+                                          uint32_t tid, int g, const double* P, int b) {
   const gbk_sweep_desc& d = a.d;
   uint32_t w[48];
-#pragma unroll
+#pragma unroll 1
   for (int m = 0; m < 12; ++m) {
     const U4 v = philox4x32_10(12u * jp + m, tid, 0u | ((uint32_t)a.parity << 4), a.sweep, a.k0, a.k1);
     w[4 * m] = v.x; w[4 * m + 1] = v.y; w[4 * m + 2] = v.z; w[4 * m + 3] = v.w;
@@ -443,6 +491,27 @@ __device__ void prep_inmodel(const SweepArgs& a, const PriorK& pk, BandSmem<T, N
   for (int c = 0; c < 8; ++c) S.th[l][c] = nw[c];
   if (ok) {
     S.lpn[l] = dlog_prior(nw, th, T());
+    S.src[l] = make_src<T>(nw, 1, 0, a.c.grid.tobs, N);
+  }
+}
+
+template <typename T, int N>
+__device__ __noinline__ void prep_rj(const SweepArgs& a, BandSmem<T, N>& S, int l, int jp, uint32_t tid,
+                                     const uint8_t* E, int b) {
+  const int s = S.list[jp];
+  uint32_t wv[16];
+#pragma unroll 1
+  for (int m = 0; m < 4; ++m) {
+    const U4 v = philox4x32_10(4u * jp + m, tid, 2u | ((uint32_t)a.parity << 4), a.sweep, a.k0, a.k1);
+    wv[4 * m] = v.x; wv[4 * m + 1] = v.y; wv[4 * m + 2] = v.z; wv[4 * m + 3] = v.w;
+  }
+  S.lu[l] = log_u(u53(wv[8], wv[9]), T());
+  S.k[l] = s;
+  if (!E[s]) {
+    double nw[8];
+    draw_birth(a.d, a.c.grid.tobs, b, wv, nw);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) S.th[l][c] = nw[c];
     S.src[l] = make_src<T>(nw, 1, 0, a.c.grid.tobs, N);
   }
 }
@@ -492,18 +561,9 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
       __syncwarp();
     } else {
       const C* rho = rho_ptr<T>(a, w, j);
-      for (int i = lane; i < 2 * W3; i += 32) S.rw[i] = rho[i];
+      const C* H = hsum_ptr<T>(a, t, w, b);
+      for (int i = lane; i < 2 * W3; i += 32) S.rw[i] = csub(rho[i], H[i]);
       __syncwarp();
-      for (int s = 0; s < d.n_max; ++s) {
-        if (!E[s]) continue;
-        const C* h = cache_ptr<T>(a, base + s);
-        const int o = cached_off<N>(P + s * 8, gw, a.c);
-        for (int i = lane; i < N; i += 32) {
-          S.rw[o + i] = csub(S.rw[o + i], h[i]);
-          S.rw[W3 + o + i] = csub(S.rw[W3 + o + i], h[N + i]);
-        }
-        __syncwarp();
-      }
     }
     // ---- in-model proposals (Alg. 1)
     if (flags & GBK_SWEEP_INMODEL) {
@@ -568,25 +628,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
       for (int j0 = 0; j0 < d.n_max; j0 += 32) {
         const int cnt = min(32, d.n_max - j0);
         // lane-parallel set-up: uniform for the decision and, for empty slots, the prior draw
-        if (lane < cnt) {
-          const int jp = j0 + lane;
-          const int s = S.list[jp];
-          uint32_t wv[16];
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            const U4 v = philox4x32_10(4u * jp + m, tid, 2u | ((uint32_t)a.parity << 4), a.sweep, a.k0, a.k1);
-            wv[4 * m] = v.x; wv[4 * m + 1] = v.y; wv[4 * m + 2] = v.z; wv[4 * m + 3] = v.w;
-          }
-          S.lu[lane] = log_u(u53(wv[8], wv[9]), T());
-          S.k[lane] = s;
-          if (!E[s]) {
-            double nw[8];
-            draw_birth(d, tobs, b, wv, nw);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) S.th[lane][c] = nw[c];
-            S.src[lane] = make_src<T>(nw, 1, 0, tobs, N);
-          }
-        }
+        if (lane < cnt) prep_rj<T, N>(a, S, lane, j0 + lane, tid, E, b);
         __syncwarp();
         for (int q = 0; q < cnt; ++q) {
           const int jp = j0 + q;
@@ -623,39 +665,24 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
       }
     }
     __syncwarp();
+    write_hsum<T, N>(a, t, w, b, lane);   // the band's template sum for openings and swaps
   }
   if (lane == 0) ws.flush(a.stats);
 }
 
 // -------------------------------------------------------------- tempering (Alg. 2)
-// H <- sum of the band's present (cached) templates on the window.
-template <typename T, int N>
-__device__ void set_sum(const SweepArgs& a, int64_t base, typename CT<T>::C* H, int64_t gw, int lane) {
-  typedef typename CT<T>::C C;
-  constexpr int W3 = 3 * N;
-  for (int i = lane; i < 2 * W3; i += 32) H[i] = mkc((T)0, (T)0);
-  __syncwarp();
-  for (int s = 0; s < a.d.n_max; ++s) {
-    if (!a.exists[base + s]) continue;
-    const C* h = cache_ptr<T>(a, base + s);
-    const int o = cached_off<N>(a.params + (base + s) * 8, gw, a.c);
-    for (int i = lane; i < N; i += 32) {
-      H[o + i] = cadd(H[o + i], h[i]);
-      H[W3 + o + i] = cadd(H[W3 + o + i], h[N + i]);
-    }
-    __syncwarp();
-  }
-}
-
 // <rho - Hx|rho - Hx> - <rho - Hy|rho - Hy> = cw sum_k w_k Re[(Hy - Hx) conj(2 rho - Hx - Hy)],
 // formed bin by bin so the large common parts cancel before summation.
 template <typename T, int N>
-__device__ double set_diff(const SweepArgs& a, const typename CT<T>::C* rho, const typename CT<T>::C* hx,
-                           const typename CT<T>::C* hy, int64_t gw, const PsdWt<T>& pw, int lane) {
+__device__ __noinline__ double set_diff(const SweepArgs& a, const typename CT<T>::C* __restrict__ rho,
+                                        const typename CT<T>::C* __restrict__ hx,
+                                        const typename CT<T>::C* __restrict__ hy, int64_t gw, const PsdWt<T>& pw,
+                                        int lane) {
   typedef typename CT<T>::C C;
   constexpr int W3 = 3 * N;
   typename SAcc<T>::S acc;
   acc.init();
+#pragma unroll 4
   for (int i = lane; i < W3; i += 32) {
     const int64_t k = gw + i;
     const T wt = iqv(a.c, k, T()) * recip((T)1 + pw.aw * rhov(a.c, k, T()));
@@ -675,7 +702,7 @@ __device__ double set_diff(const SweepArgs& a, const typename CT<T>::C* rho, con
 // Move the cached templates of one band into (sign +1: R -= h) or out of (sign -1:
 // R += h) the cold-chain residual, each rounded to the fixed-point grid.
 template <typename T, int N>
-__device__ void cold_update(const SweepArgs& a, int64_t base, int sign, long long* Rw, int lane) {
+__device__ __noinline__ void cold_update(const SweepArgs& a, int64_t base, int sign, long long* Rw, int lane) {
   typedef typename CT<T>::C C;
   const int64_t nb = a.c.grid.n_bins;
   const T gs = (T)ldexp(1.0, a.frac_bits - kStrainExp);
@@ -693,19 +720,21 @@ __device__ void cold_update(const SweepArgs& a, int64_t base, int sign, long lon
         atomicAdd(dst, (unsigned long long)hx);
         atomicAdd(dst + 1, (unsigned long long)hy);
       }
-    __syncwarp();
   }
+  __syncwarp();
 }
 
 template <typename T, int N>
 __host__ __device__ constexpr size_t swap_warp_bytes(int nt, int nw) {
-  return (4 * 3 * N * sizeof(typename CT<T>::C) + (size_t)nt * nw * sizeof(short) + 15) / 16 * 16;
+  return ((size_t)nt * nw * sizeof(short) + 15) / 16 * 16;
 }
 template <typename T, int N>
 __host__ __device__ constexpr size_t refresh_warp_bytes() {
   return 4 * N * sizeof(typename CT<T>::C) + 32 * sizeof(Src<T>) + 128;
 }
 
+// One warp per (band, chain): walkers permuted per temperature, swaps from the top
+// temperature down; the band's template sums come from the set-sum cache.
 template <typename T, int N>
 __global__ void __launch_bounds__(kSwWarps * 32) k_swap(const SweepArgs a) {
   typedef typename CT<T>::C C;
@@ -714,10 +743,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_swap(const SweepArgs a) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const gbk_sweep_desc& d = a.d;
   const int T_ = d.n_temps, W = d.n_walkers;
-  const size_t per_warp = swap_warp_bytes<T, N>(T_, W);
-  C* HA = reinterpret_cast<C*>(smem_raw + (size_t)wid * per_warp);
-  C* HB = HA + 2 * W3;
-  short* perm = reinterpret_cast<short*>(HB + 2 * W3);   // [T][W]
+  short* perm = reinterpret_cast<short*>(smem_raw + (size_t)wid * swap_warp_bytes<T, N>(T_, W));   // [T][W]
   const int nbp = (d.n_bands - a.parity + 1) / 2;
   const int64_t ntask = (int64_t)nbp * W;
   const int nslotc = 2 * N;
@@ -745,23 +771,19 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_swap(const SweepArgs a) {
       }
     }
     __syncwarp();
-    int wt = perm[(T_ - 1) * W + c];
-    C* cur = HA;
-    C* oth = HB;
-    set_sum<T, N>(a, slot_index(d, T_ - 1, wt, b), cur, gw, lane);
     for (int t = T_ - 1; t > 0; --t) {
-      wt = perm[t * W + c];
+      const int wt = perm[t * W + c];
       const int wm = perm[(t - 1) * W + c];
       const int64_t bt = slot_index(d, t, wt, b), bm = slot_index(d, t - 1, wm, b);
-      set_sum<T, N>(a, bm, oth, gw, lane);
+      C* Ht = hsum_ptr<T>(a, t, wt, b);
+      C* Hm = hsum_ptr<T>(a, t - 1, wm, b);
       const PsdWt<T> pt_ = walker_psd<T>(a, wt), pm_ = walker_psd<T>(a, wm);
       // l_t(m) - l_t(t) = -1/2 D1, l_m(t) - l_m(m) = -1/2 D2 (band-local likelihoods)
-      const double D1 = set_diff<T, N>(a, rho_ptr<T>(a, wt, j), oth, cur, gw, pt_, lane);
-      const double D2 = set_diff<T, N>(a, rho_ptr<T>(a, wm, j), cur, oth, gw, pm_, lane);
+      const double D1 = set_diff<T, N>(a, rho_ptr<T>(a, wt, j), Hm, Ht, gw, pt_, lane);
+      const double D2 = set_diff<T, N>(a, rho_ptr<T>(a, wm, j), Ht, Hm, gw, pm_, lane);
       const double la = a.betas[(int64_t)b * T_ + t] * (-0.5 * D1) + a.betas[(int64_t)b * T_ + t - 1] * (-0.5 * D2);
       const U4 v = philox4x32_10((uint32_t)t, (uint32_t)(b * W + c), 4u | ((uint32_t)a.parity << 4), a.sweep, a.k0, a.k1);
-      const double u = u53(v.x, v.y);
-      const double lu = u > 0.0 ? log(u) : -INFINITY;
+      const double lu = log_u(u53(v.x, v.y), T());
       const bool acc = __shfl_sync(0xffffffffu, (int)(lu < la), 0) != 0;
       if (acc) {
         double* Pt = a.params + bt * 8;
@@ -777,15 +799,15 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_swap(const SweepArgs a) {
         for (int i = lane; i < d.n_max * nslotc; i += 32) {
           const C q = ct[i]; ct[i] = cm[i]; cm[i] = q;
         }
+        for (int i = lane; i < 2 * W3; i += 32) {
+          const C q = Ht[i]; Ht[i] = Hm[i]; Hm[i] = q;
+        }
         __syncwarp();
         if (t == 1) {
           long long* Rw = a.resid + (int64_t)wm * 2 * a.c.grid.n_bins * 2;
           cold_update<T, N>(a, bt, -1, Rw, lane);   // old cold set leaves the model
           cold_update<T, N>(a, bm, +1, Rw, lane);   // new cold set enters
         }
-        // the set now at t-1 is `cur`; `oth` is free
-      } else {
-        C* q = cur; cur = oth; oth = q;
       }
       if (lane == 0) record(a, ws, 3, t, wt, b, c, t, acc, la, la, nullptr, 0, 0);
       __syncwarp();
@@ -843,6 +865,10 @@ static gbk_status run_refresh(SweepArgs& a, cudaStream_t st) {
   if ((s = prep(k_refresh<T, N>, refresh_warp_bytes<T, N>(), (nslot + 31) / 32, &grid, &thr, &sm))) return s;
   ev_rec(1, 0, 0, st);
   k_refresh<T, N><<<grid, thr, sm, st>>>(a);
+  if ((s = check_launch("gb_sweep(refresh)"))) return s;
+  const int64_t ntask = (int64_t)a.d.n_temps * a.d.n_walkers * a.d.n_bands;
+  if ((s = prep(k_hsum<T, N>, 0, ntask, &grid, &thr, &sm))) return s;
+  k_hsum<T, N><<<grid, kSwWarps * 32, 0, st>>>(a);
   ev_rec(1, 0, 1, st);
   return check_launch("gb_sweep(refresh)");
 }
@@ -935,13 +961,16 @@ extern "C" gbk_status gbk_sweep_create(gbk_ctx* ctx, const gbk_sweep_desc* desc,
   const size_t rbytes = (size_t)d.n_walkers * 2 * ctx->grid.n_bins * 2 * sizeof(long long);
   p->rho_bytes = (size_t)d.n_walkers * p->n_bp_max * 2 * 3 * d.band_bins * csz;
   p->cache_bytes = (size_t)d.n_temps * d.n_walkers * d.n_bands * (d.n_max > 0 ? d.n_max : 1) * 2 * d.band_bins * csz;
+  p->hsum_bytes = (size_t)d.n_temps * d.n_walkers * d.n_bands * 2 * 3 * d.band_bins * csz;
   cudaError_t e = cudaMalloc((void**)&p->rsnap, rbytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->rho, p->rho_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->wcache, p->cache_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&p->hsum, p->hsum_bytes);
   if (e != cudaSuccess) {
     cudaFree(p->rsnap);
     cudaFree(p->rho);
     cudaFree(p->wcache);
+    cudaFree(p->hsum);
     free(p);
     cudaGetLastError();
     return set_error(e == cudaErrorMemoryAllocation ? GBK_ENOMEM : GBK_ECUDA, "gbk_sweep_create: %s",
@@ -957,6 +986,7 @@ extern "C" gbk_status gbk_sweep_destroy(gbk_sweep* plan) {
   cudaFree(plan->rsnap);
   cudaFree(plan->rho);
   cudaFree(plan->wcache);
+  cudaFree(plan->hsum);
   if (plan->have_ev)
     for (int p = 0; p < 2; ++p)
       for (int k = 0; k < 4; ++k)
@@ -1003,6 +1033,7 @@ extern "C" gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists,
   a.rsnap = plan->rsnap;
   a.rho = plan->rho;
   a.wcache = plan->wcache;
+  a.hsum = plan->hsum;
   a.n_bp_max = plan->n_bp_max;
   a.n_walkers_r = residual->n_walkers;
   a.frac_bits = residual->frac_bits;

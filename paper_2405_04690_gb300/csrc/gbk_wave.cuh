@@ -182,22 +182,24 @@ __device__ __noinline__ Src<T> make_src(const double* __restrict__ prm, int64_t 
     ph -= rint(ph);
     split<T>(ph, s.phh, s.phl);
   }
-  // Sky angles in the arithmetic type: a relative error e in the Doppler amplitude is a
-  // phase error of ~e f0 AU/c cycles, which moves <a|a> not at all and <d-H|a> by
-  // ~SNR e f0 AU/c (far below 1e-2 for e ~ 1e-7); products with f0 are formed in float64.
-  const T sb = (T)sinb;
-  const T cb = sqrt((T)1 - sb * sb);
-  T sl, cl;
-  sincos_((T)lam, &sl, &cl);
+  const double cbd = sqrt(1.0 - sinb * sinb);
+  double sld, cld;
+  sincos(lam, &sld, &cld);
   const double aoc = kAU / kC;
-  split<T>(-(double)cb * (double)cl * f0 * aoc, s.dxh, s.dxl);
-  split<T>(-(double)cb * (double)sl * f0 * aoc, s.dyh, s.dyl);
-  s.fkx = (T)(-(double)cb * (double)cl * fdot * aoc);
-  s.fky = (T)(-(double)cb * (double)sl * fdot * aoc);
+  split<T>(-cbd * cld * f0 * aoc, s.dxh, s.dxl);
+  split<T>(-cbd * sld * f0 * aoc, s.dyh, s.dyl);
+  s.fkx = (T)(-cbd * cld * fdot * aoc);
+  s.fky = (T)(-cbd * sld * fdot * aoc);
   s.f0 = (T)f0;
   s.fdot = (T)fdot;
-  T s2, c2;
-  sincos_((T)(2.0 * psi), &s2, &c2);
+  const T sb = (T)sinb;
+  const T cb = (T)cbd;
+  const T sl = (T)sld, cl = (T)cld;
+  // sky position in float64: its rounding would move the antenna pattern (an amplitude
+  // error, which <a|a> feels directly) by ~1e-7, too much for Delta lnL ~ 1e4 to 1e-2
+  double s2d, c2d;
+  sincos(2.0 * psi, &s2d, &c2d);
+  const T s2 = (T)s2d, c2 = (T)c2d;
   s.kx = -cb * cl; s.ky = -cb * sl; s.kz = -sb;
   s.ux = sb * cl; s.uy = sb * sl; s.uz = -cb;
   s.vx = sl; s.vy = -cl; s.vz = (T)0;
