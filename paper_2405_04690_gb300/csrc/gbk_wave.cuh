@@ -28,7 +28,13 @@
 
 #include "gbk_internal.cuh"
 
+#ifndef GBK_SAMPLE_UNROLL
+#define GBK_SAMPLE_UNROLL 1
+#endif
+
 namespace gbk {
+
+constexpr int kSampleUnroll = GBK_SAMPLE_UNROLL;
 
 template <typename T> struct CT;
 template <> struct CT<float> { typedef float2 C; };
@@ -270,8 +276,11 @@ __device__ __noinline__ void gen_band(const Src<T>* __restrict__ srcp, const T* 
   const T lc = (T)kLc;
   const T dtp = (T)(tobs / N);
   const T inv_n = (T)1 / (T)N;
+  // The per-sample body is long; unrolling the sample loop multiplies the code that
+  // every warp must fetch (GBK_SAMPLE_UNROLL, chosen by measurement).
   const T rs2 = (T)0.70710678118654752440;
   const T rs6 = (T)0.40824829046386301637;
+#pragma unroll (kSampleUnroll)
   for (int p = lane; p < N; p += 32) {
     const T* o = orb + p;
     const T cah = o[0 * N], sah = o[1 * N], cal = o[20 * N], sal = o[21 * N];
