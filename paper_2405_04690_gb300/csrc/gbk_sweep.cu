@@ -16,6 +16,7 @@ struct gbk_sweep {
   void* rho;            // opened windows [W][n_bp_max][2][3N], complex of the sweep precision
   void* wcache;         // current waveform of every slot [T][W][B][n_max][2][N]
   void* hsum;           // sum of the present templates of every band on its window [T][W][B][2][3N]
+  int32_t* setid;       // cache block of band (t, w, b) [T][W][B]; tempering swaps exchange ids
   size_t rho_bytes, cache_bytes, hsum_bytes;
   cudaEvent_t ev[2][4][2];  // [parity][refresh, open, band, swap][begin, end] when timing
   bool timed, have_ev;
@@ -37,6 +38,7 @@ struct SweepArgs {
   void* rho;
   void* wcache;
   void* hsum;
+  int32_t* setid;
   int n_bp_max;
   int32_t n_walkers_r;
   int32_t frac_bits;
@@ -230,14 +232,19 @@ __device__ __forceinline__ PsdWt<T> walker_psd(const SweepArgs& a, int w) {
 __device__ __forceinline__ int64_t slot_index(const gbk_sweep_desc& d, int t, int w, int b) {
   return (((int64_t)t * d.n_walkers + w) * d.n_bands + b) * d.n_max;
 }
+// The waveform and set-sum caches of band (t, w, b) live in block setid[t][w][b]; a
+// tempering swap exchanges the two blocks' ids instead of copying their contents.
+__device__ __forceinline__ int64_t cache_base(const SweepArgs& a, int t, int w, int b) {
+  return (int64_t)a.setid[((int64_t)t * a.d.n_walkers + w) * a.d.n_bands + b] * a.d.n_max;
+}
 template <typename T>
-__device__ __forceinline__ typename CT<T>::C* cache_ptr(const SweepArgs& a, int64_t slot) {
-  return reinterpret_cast<typename CT<T>::C*>(a.wcache) + slot * 2 * a.d.band_bins;
+__device__ __forceinline__ typename CT<T>::C* cache_ptr(const SweepArgs& a, int64_t cslot) {
+  return reinterpret_cast<typename CT<T>::C*>(a.wcache) + cslot * 2 * a.d.band_bins;
 }
 template <typename T>
 __device__ __forceinline__ typename CT<T>::C* hsum_ptr(const SweepArgs& a, int t, int w, int b) {
   return reinterpret_cast<typename CT<T>::C*>(a.hsum) +
-         (((int64_t)t * a.d.n_walkers + w) * a.d.n_bands + b) * 2 * 3 * a.d.band_bins;
+         (int64_t)a.setid[((int64_t)t * a.d.n_walkers + w) * a.d.n_bands + b] * 2 * 3 * a.d.band_bins;
 }
 template <typename T>
 __device__ __forceinline__ typename CT<T>::C* rho_ptr(const SweepArgs& a, int w, int j) {
@@ -352,6 +359,7 @@ __device__ __noinline__ void write_hsum(const SweepArgs& a, int t, int w, int b,
   C* H = hsum_ptr<T>(a, t, w, b);
   const int64_t gw = d.band_k0 + (int64_t)(b - 1) * N - a.c.grid.k0;
   const int64_t base = slot_index(d, t, w, b);
+  const int64_t cb = cache_base(a, t, w, b);
   // lane-parallel offsets of the present slots (slot lane and slot lane + 32)
   int off0 = -1, off1 = -1;
   if (lane < d.n_max && a.exists[base + lane]) off0 = cached_off<N>(a.params + (base + lane) * 8, gw, a.c);
@@ -366,7 +374,7 @@ __device__ __noinline__ void write_hsum(const SweepArgs& a, int t, int w, int b,
         const int o = __shfl_sync(0xffffffffu, half ? off1 : off0, sl);
         const int j = i - o;
         if (j >= 0 && j < N) {
-          const C* h = cache_ptr<T>(a, base + sl + 32 * half);
+          const C* h = cache_ptr<T>(a, cb + sl + 32 * half);
           xa = cadd(xa, h[j]);
           xe = cadd(xe, h[N + j]);
         }
@@ -392,6 +400,11 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_hsum(const SweepArgs a) {
 
 // -------------------------------------------------------------- cache refresh
 // Regenerate the cached waveform of every present slot (32 slots per warp batch).
+__global__ void k_identity_ids(int32_t* ids, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    ids[i] = (int32_t)i;
+}
+
 template <typename T, int N>
 __global__ void __launch_bounds__(kSwWarps * 32) k_refresh(const SweepArgs a) {
   typedef typename CT<T>::C C;
@@ -542,6 +555,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
     const int b = a.parity + 2 * j;
     const int64_t gw = d.band_k0 + (int64_t)(b - 1) * N - a.c.grid.k0;
     const int64_t base = slot_index(d, t, w, b);
+    const int64_t cb = cache_base(a, t, w, b);
     double* P = a.params + base * 8;
     uint8_t* E = a.exists + base;
     const double beta = a.betas[(int64_t)b * d.n_temps + t];
@@ -588,7 +602,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
             continue;
           }
           gen_band<T, N>(&S.src[q], orb, tw, tobs, S.ba, S.bs, lane);
-          const C* hr = cache_ptr<T>(a, base + k);
+          const C* hr = cache_ptr<T>(a, cb + k);
           const int oa = band_off<N>(S.src[q].q, gw, a.c);
           const int orr = cached_off<N>(P + k * 8, gw, a.c);
           const double dll = window_dll<T, N>(a, S.rw, S.ba, oa, hr, orr, gw, pw, lane);
@@ -598,7 +612,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
           if (acc) {
             apply_change<T, N>(a, S.rw, S.ba, oa, hr, orr, cold, Rw, gw, gs, lane);
             __syncwarp();
-            copy_band(cache_ptr<T>(a, base + k), S.ba, 2 * N, lane);
+            copy_band(cache_ptr<T>(a, cb + k), S.ba, 2 * N, lane);
             if (lane < 8) P[k * 8 + lane] = S.th[q][lane];
             __syncwarp();
             // later proposals of this batch that move the same source start from the new state
@@ -634,7 +648,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
           const int jp = j0 + q;
           const int s = S.k[q];
           if (E[s]) {
-            const C* hr = cache_ptr<T>(a, base + s);
+            const C* hr = cache_ptr<T>(a, cb + s);
             const int orr = cached_off<N>(P + s * 8, gw, a.c);
             const double dll = window_dll<T, N>(a, S.rw, (const C*)nullptr, 0, hr, orr, gw, pw, lane);
             const double la = beta * dll - d.log_occ_odds;
@@ -654,7 +668,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
             if (lane == 0) record(a, ws, 1, t, w, b, s, jp, acc, dll, la, S.th[q], 1, 1);
             if (acc) {
               apply_change<T, N>(a, S.rw, S.ba, oa, (const C*)nullptr, 0, cold, Rw, gw, gs, lane);
-              copy_band(cache_ptr<T>(a, base + s), S.ba, 2 * N, lane);
+              copy_band(cache_ptr<T>(a, cb + s), S.ba, 2 * N, lane);
               if (lane < 8) P[s * 8 + lane] = S.th[q][lane];
               __syncwarp();
               if (lane == 0) E[s] = 1;
@@ -702,14 +716,15 @@ __device__ __noinline__ double set_diff(const SweepArgs& a, const typename CT<T>
 // Move the cached templates of one band into (sign +1: R -= h) or out of (sign -1:
 // R += h) the cold-chain residual, each rounded to the fixed-point grid.
 template <typename T, int N>
-__device__ __noinline__ void cold_update(const SweepArgs& a, int64_t base, int sign, long long* Rw, int lane) {
+__device__ __noinline__ void cold_update(const SweepArgs& a, int64_t base, int64_t cb, int sign, long long* Rw,
+                                         int lane) {
   typedef typename CT<T>::C C;
   const int64_t nb = a.c.grid.n_bins;
   const T gs = (T)ldexp(1.0, a.frac_bits - kStrainExp);
   unsigned long long* R = reinterpret_cast<unsigned long long*>(Rw);
   for (int s = 0; s < a.d.n_max; ++s) {
     if (!a.exists[base + s]) continue;
-    const C* h = cache_ptr<T>(a, base + s);
+    const C* h = cache_ptr<T>(a, cb + s);
     const int64_t o = (long long)floor(a.params[(base + s) * 8 + 1] * a.c.grid.tobs) - N / 2 - a.c.grid.k0;
     for (int i = lane; i < N; i += 32)
       for (int ch = 0; ch < 2; ++ch) {
@@ -794,19 +809,16 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_swap(const SweepArgs a) {
         for (int i = lane; i < d.n_max; i += 32) {
           const uint8_t q = a.exists[bt + i]; a.exists[bt + i] = a.exists[bm + i]; a.exists[bm + i] = q;
         }
-        C* ct = cache_ptr<T>(a, bt);
-        C* cm = cache_ptr<T>(a, bm);
-        for (int i = lane; i < d.n_max * nslotc; i += 32) {
-          const C q = ct[i]; ct[i] = cm[i]; cm[i] = q;
-        }
-        for (int i = lane; i < 2 * W3; i += 32) {
-          const C q = Ht[i]; Ht[i] = Hm[i]; Hm[i] = q;
+        if (lane == 0) {
+          int32_t* it = a.setid + ((int64_t)t * W + wt) * d.n_bands + b;
+          int32_t* im = a.setid + ((int64_t)(t - 1) * W + wm) * d.n_bands + b;
+          const int32_t q = *it; *it = *im; *im = q;
         }
         __syncwarp();
         if (t == 1) {
           long long* Rw = a.resid + (int64_t)wm * 2 * a.c.grid.n_bins * 2;
-          cold_update<T, N>(a, bt, -1, Rw, lane);   // old cold set leaves the model
-          cold_update<T, N>(a, bm, +1, Rw, lane);   // new cold set enters
+          cold_update<T, N>(a, bt, cache_base(a, t, wt, b), -1, Rw, lane);       // old cold set leaves the model
+          cold_update<T, N>(a, bm, cache_base(a, t - 1, wm, b), +1, Rw, lane);   // new cold set enters
         }
       }
       if (lane == 0) record(a, ws, 3, t, wt, b, c, t, acc, la, la, nullptr, 0, 0);
@@ -864,6 +876,8 @@ static gbk_status run_refresh(SweepArgs& a, cudaStream_t st) {
   gbk_status s;
   if ((s = prep(k_refresh<T, N>, refresh_warp_bytes<T, N>(), (nslot + 31) / 32, &grid, &thr, &sm))) return s;
   ev_rec(1, 0, 0, st);
+  const int64_t nsets = (int64_t)a.d.n_temps * a.d.n_walkers * a.d.n_bands;
+  k_identity_ids<<<(int)((nsets + 255) / 256 < 4096 ? (nsets + 255) / 256 : 4096), 256, 0, st>>>(a.setid, nsets);
   k_refresh<T, N><<<grid, thr, sm, st>>>(a);
   if ((s = check_launch("gb_sweep(refresh)"))) return s;
   const int64_t ntask = (int64_t)a.d.n_temps * a.d.n_walkers * a.d.n_bands;
@@ -966,11 +980,13 @@ extern "C" gbk_status gbk_sweep_create(gbk_ctx* ctx, const gbk_sweep_desc* desc,
   if (e == cudaSuccess) e = cudaMalloc(&p->rho, p->rho_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->wcache, p->cache_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->hsum, p->hsum_bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->setid, (size_t)d.n_temps * d.n_walkers * d.n_bands * sizeof(int32_t));
   if (e != cudaSuccess) {
     cudaFree(p->rsnap);
     cudaFree(p->rho);
     cudaFree(p->wcache);
     cudaFree(p->hsum);
+    cudaFree(p->setid);
     free(p);
     cudaGetLastError();
     return set_error(e == cudaErrorMemoryAllocation ? GBK_ENOMEM : GBK_ECUDA, "gbk_sweep_create: %s",
@@ -987,6 +1003,7 @@ extern "C" gbk_status gbk_sweep_destroy(gbk_sweep* plan) {
   cudaFree(plan->rho);
   cudaFree(plan->wcache);
   cudaFree(plan->hsum);
+  cudaFree(plan->setid);
   if (plan->have_ev)
     for (int p = 0; p < 2; ++p)
       for (int k = 0; k < 4; ++k)
@@ -1034,6 +1051,7 @@ extern "C" gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists,
   a.rho = plan->rho;
   a.wcache = plan->wcache;
   a.hsum = plan->hsum;
+  a.setid = plan->setid;
   a.n_bp_max = plan->n_bp_max;
   a.n_walkers_r = residual->n_walkers;
   a.frac_bits = residual->frac_bits;
