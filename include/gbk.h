@@ -264,6 +264,31 @@ gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists, const doub
  * tempering swaps, each summed over both parities. Synchronises with those events. */
 gbk_status gbk_sweep_kernel_ms(gbk_sweep* plan, double* ms_out);
 
+/* ------------------------------------------------------------------ no-allocation variant
+ * total_loglike_noalloc -- the same result as total_loglike (Eq. like for W walkers, both
+ * channels), for callers that cannot allocate device memory: code that runs inside
+ * another framework's allocator or memory budget, or that must not grow the device
+ * footprint after start-up. It needs no gbk_ctx (whose creation allocates): the grid is
+ * passed directly and the PSD shape is computed in the kernel. (The paper has no
+ * counterpart: this is a deployment variant of the total-likelihood pass.)
+ *   tobs, k0, n_bins  the window, as in gbk_grid; (k0 + n_bins) / tobs < c / (2L)
+ *   residual          [W][2][n_bins][2] float32, 8-byte aligned
+ *   psd_params        [W][2] float64;  logl [W] float64 out
+ * Its scratch (cross-block partial sums) is a fixed array of
+ * total_loglike_noalloc_capacity() doubles (8 MiB) in the library's device memory, held
+ * on every device that loads the library until the process exits. A call needs
+ * ceil(n_bins / 4096) * (2 W + 1) doubles; larger requests return GBK_ERANGE. Every call
+ * overwrites all the partial sums it reads, so earlier contents do not matter; but all
+ * calls share the one array, so calls that overlap on the GPU (different streams, or
+ * host threads without ordering) race and give wrong results: order them on one stream.
+ * The first call on each device looks up the array's device address; make that first
+ * call before any stream capture. Allocates nothing (no cudaMalloc, no library calls that
+ * allocate).
+ */
+int64_t total_loglike_noalloc_capacity(void);
+gbk_status total_loglike_noalloc(double tobs, int64_t k0, int64_t n_bins, const float* residual,
+                                 const double* psd_params, int32_t n_walkers, double* logl, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

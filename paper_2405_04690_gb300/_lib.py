@@ -81,6 +81,8 @@ SIGNATURES = {
     "gbk_sweep_create": (ctypes.c_int, [_vp, ctypes.POINTER(GbkSweepDesc), ctypes.POINTER(_vp)]),
     "gbk_sweep_destroy": (ctypes.c_int, [_vp]),
     "gbk_sweep_kernel_ms": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
+    "total_loglike_noalloc_capacity": (ctypes.c_int64, []),
+    "total_loglike_noalloc": (ctypes.c_int, [ctypes.c_double, _i64, _i64, _vp, _vp, _i32, _vp, _vp]),
     "gb_sweep": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(GbkResidual), ctypes.POINTER(GbkPsd),
                                 ctypes.c_uint64, ctypes.c_uint32, _i32, ctypes.POINTER(GbkTrace), _vp, _vp]),
 }
@@ -270,3 +272,11 @@ def gbk_sweep_kernel_ms(plan):
     out = (ctypes.c_double * 4)()
     _check(lib().gbk_sweep_kernel_ms(plan.handle, out), "gbk_sweep_kernel_ms")
     return list(out)
+
+
+def total_loglike_noalloc(tobs, k0, n_bins, residual, psd_params, logl, stream=None):
+    """Eq. like for W walkers without a context and without allocating (fixed scratch)."""
+    w = psd_params.shape[0]
+    _check(lib().total_loglike_noalloc(float(tobs), int(k0), int(n_bins), _dev(residual, torch.float32, "residual"),
+                                       _dev(psd_params, torch.float64, "psd_params"), w,
+                                       _dev(logl, torch.float64, "logl"), _stream(stream)), "total_loglike_noalloc")

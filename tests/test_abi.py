@@ -13,7 +13,7 @@ LIB = os.path.join(ROOT, "paper_2405_04690_gb300", "libgbk.so")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:gbk_status|const char\*|int)\s+(\w+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:gbk_status|const char\*|int|int64_t)\s+(\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 
