@@ -54,6 +54,31 @@ def flops_per_evaluation(n=N_BAND):
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
+def measured_hbm_gbs():
+    """Measured copy bandwidth of the GB300s, else the profiling fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def autocorr_time(x, c=5.0):
+    """Integrated autocorrelation time of series x [n_chains][n_steps] (mean ACF over
+    chains, Sokal's adaptive window: smallest M with M >= c tau(M))."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.shape[1]
+    xc = x - x.mean(axis=1, keepdims=True)
+    f = np.fft.rfft(xc, n=2 * n, axis=1)
+    acf = np.fft.irfft(f * np.conj(f), axis=1)[:, :n]
+    acf = acf / np.maximum(acf[:, :1], 1e-300)
+    rho = acf.mean(axis=0)
+    taus = 2.0 * np.cumsum(rho) - 1.0
+    for m in range(1, n):
+        if m >= c * taus[m]:
+            return float(taus[m])
+    return float(taus[-1])
+
+
 # ------------------------------------------------------------------ CPU oracle timing
 def _oracle_worker(args):
     seed, n_bands = args
@@ -335,6 +360,71 @@ def run_ours(args):
     h2d = S["P"].numel() * 8 + S["E"].numel()
     d2h = h2d + 80
 
+    # total log-likelihood pass of 512 walkers x 2 channels x 2^20 bins (float32 residual,
+    # per-walker PSD; HBM bound): psd_eval for the noise draw, total_loglike timed
+    c3 = {}
+    if not args.no_c3:
+        from paper_2405_04690_gb300 import synth
+        g3 = synth.rng(3 + 1000 * rank)
+        n3, w3, k03 = 1 << 20, args.c3_walkers, 3146
+        ctx3 = L.Context(TOBS, DT, k03, n3)
+        pp3 = torch.from_numpy(synth.draw_psd_params(g3, w3)).to(dev)
+        r3 = torch.empty((w3, 2, n3, 2), dtype=torch.float32, device=dev)
+        s3 = torch.empty((1, n3), dtype=torch.float64, device=dev)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(3 + 1000 * rank)
+        for w in range(w3):
+            L.psd_eval(ctx3, pp3[w:w + 1].contiguous(), s3)
+            sd = torch.sqrt(s3[0] * (TOBS / 4.0)).to(torch.float32)
+            r3[w].normal_(generator=gen)
+            r3[w].mul_(sd[None, :, None])
+        out3 = torch.empty(w3, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            L.total_loglike(ctx3, r3, pp3, out3, stream)
+        torch.cuda.synchronize()
+        evs3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for a0, a1 in evs3:
+            a0.record(stream)
+            L.total_loglike(ctx3, r3, pp3, out3, stream)
+            a1.record(stream)
+        torch.cuda.synchronize()
+        ms3 = float(np.mean([a0.elapsed_time(a1) for a0, a1 in evs3]))
+        bytes3 = w3 * 2 * n3 * 8
+        peak, kind = measured_hbm_gbs()
+        c3 = {"workload": "total logL: %d walkers x 2 ch x 2^20 bins float32, per-walker PSD (Eq. like)" % w3,
+              "ms": ms3, "GB/s": bytes3 / (ms3 * 1e-3) / 1e9, "algorithmic_bytes": bytes3,
+              "peak_GB/s": peak, "peak_kind": kind, "frac": bytes3 / (ms3 * 1e-3) / 1e9 / peak,
+              "walker_logl_per_s": w3 / (ms3 * 1e-3)}
+        del r3, s3
+        ctx3.close()
+
+    # effective samples: integrated autocorrelation time of every cold walker's total
+    # log-likelihood (Eq. like on its residual) over a run of sweeps
+    ess = {}
+    if args.ess_sweeps > 0:
+        nb = ens["n_bins"]
+        lnl = torch.empty(N_W, dtype=torch.float64, device=dev)
+        rf = torch.empty((N_W, 2, nb, 2), dtype=torch.float32, device=dev)
+        series = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_sweeps = 0.0
+        for k in range(args.ess_sweeps):
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_sweeps += e0.elapsed_time(e1) * 1e-3
+            rf.copy_((S["resid"].to(torch.float64) * 2.0 ** -FRAC_BITS).to(torch.float32))
+            L.total_loglike(S["ctx"], rf, S["psdp"].expand(N_W, 2).contiguous(), lnl, stream)
+            series.append(lnl.cpu().numpy().copy())
+        x = np.array(series).T[:, args.ess_sweeps // 4:]
+        tau = autocorr_time(x)
+        n_eff = x.shape[0] * x.shape[1] / max(tau, 1.0)
+        ess = {"ess_per_s": n_eff / (t_sweeps * x.shape[1] / args.ess_sweeps), "tau_sweeps": tau,
+               "sweeps": args.ess_sweeps, "burn_in": args.ess_sweeps // 4,
+               "scalar": "cold-chain total lnL of each of the 32 walkers (Eq. like on its residual)"}
+        del rf
+
     # the plain float64 path on the same GPU: (a) the same sweep in float64, one step;
     # (b) per-source launches of the float64 Delta lnL (one proposal per launch)
     fp64 = {}
@@ -400,6 +490,10 @@ def run_ours(args):
         "wall_s_timed_region": wall,
     }
     line["config"].update(fp64)
+    if c3:
+        line["total_loglike"] = c3
+    if ess:
+        line["ess"] = ess
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -437,6 +531,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison runs")
+    ap.add_argument("--no-c3", action="store_true", help="skip the total log-likelihood (HBM) measurement")
+    ap.add_argument("--ess-sweeps", type=int, default=120, help="sweeps for the ESS/s measurement (0: skip)")
+    ap.add_argument("--c3-walkers", type=int, default=512, help="walkers of the total log-likelihood measurement")
     ap.add_argument("--n-temps", type=int, default=N_T, help="smaller ensemble for profiling captures")
     args = ap.parse_args()
     if args.impl == "reference":
