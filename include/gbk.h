@@ -63,7 +63,7 @@ typedef struct gbk_grid {
   double tobs;     /* observation time T [s]; df = 1 / T (Eq. inner's Delta f) */
   double dt;       /* sampling cadence [s]; T / dt must be a multiple of 1024 */
   int64_t k0;      /* first absolute frequency bin of the residual window, >= 1 */
-  int64_t n_bins;  /* bins in the window, >= 1 */
+  int64_t n_bins;  /* bins in the window, >= 1; (k0 + n_bins) / tobs < c / (2L) */
 } gbk_grid;
 
 /* Residual d - H of every walker as int64 fixed point: value = integer * 2^-frac_bits.

@@ -127,8 +127,11 @@ extern "C" gbk_status gbk_create(gbk_ctx** out_ctx, const gbk_grid* grid) {
   const double nt = grid->tobs / grid->dt;
   if (fabs(nt - rint(nt)) > 1e-9 * nt || fmod(rint(nt), 1024.0) != 0.0)
     return set_error(GBK_EINVAL, "gbk_create: tobs/dt = %g is not a multiple of 1024", nt);
-  if ((double)(grid->k0 + grid->n_bins) > 0.5 * nt)
-    return set_error(GBK_EINVAL, "gbk_create: window passes the Nyquist bin");
+  // Eq. psd vanishes at x = pi (f = c / 2L); windows must stay below it. A window may pass
+  // the Nyquist bin N_t/2 (a synthetic total-likelihood pass over 2^20 bins from 0.1 mHz
+  // does), where only the PSD model, not the waveform, is evaluated.
+  if ((double)(grid->k0 + grid->n_bins) / grid->tobs >= 0.5 / kLc)
+    return set_error(GBK_EINVAL, "gbk_create: window reaches f = c/(2L), where the PSD vanishes");
   gbk_ctx* c = (gbk_ctx*)calloc(1, sizeof(gbk_ctx));
   if (!c) return set_error(GBK_ENOMEM, "gbk_create: host allocation failed");
   c->grid = *grid;
