@@ -260,6 +260,77 @@ def build_device_state(torch, L, dev, ens, precision, seed):
             "psdp": psdp, "betas": betas}
 
 
+def band_for(f0):
+    """Band length by octave: 128 below 1 mHz, doubling per octave up to 1024."""
+    return np.where(f0 < 1e-3, 128, np.where(f0 < 2e-3, 256, np.where(f0 < 4e-3, 512, 1024))).astype(np.int32)
+
+
+def run_uneven(torch, L, dev, stream, seed, n_prop=200000, reps=10):
+    from paper_2405_04690_gb300 import synth
+    g = synth.rng(seed)
+    p = synth.draw_sources(g, n_prop, 3e-4, 2e-2, log_f=True)
+    new = synth.perturb(g, p, synth.proposal_widths(p))
+    nb = band_for(p[1])
+    k0, nbins = synth.window_for(2.5e-4, 2.05e-2, 1100)
+    ctx = L.Context(TOBS, DT, k0, nbins)
+    psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
+    s = torch.empty((1, nbins), dtype=torch.float64, device=dev)
+    L.psd_eval(ctx, psdp, s)
+    z = torch.from_numpy(synth.unit_complex_normal(g, (2, nbins))).to(dev)
+    noise = z * torch.sqrt(s[0] * (TOBS / 4.0))
+    scale = float(2.0 ** FRAC_BITS)
+    resid = torch.stack([torch.round(noise.real * scale), torch.round(noise.imag * scale)],
+                        dim=-1).to(torch.int64).unsqueeze(0).contiguous()
+    R = L.residual_struct(resid, FRAC_BITS)
+    P = L.psd_struct(psdp)
+    groups = {}
+    for n in (128, 256, 512, 1024):
+        idx = np.nonzero(nb == n)[0]
+        if len(idx) == 0:
+            continue
+        m = len(idx)
+        groups[n] = {"new": torch.from_numpy(np.ascontiguousarray(new[:, idx])).to(dev),
+                     "old": torch.from_numpy(np.ascontiguousarray(p[:, idx])).to(dev),
+                     "nb": torch.full((m,), n, dtype=torch.int32, device=dev),
+                     "w": torch.zeros(m, dtype=torch.int32, device=dev),
+                     "out": torch.empty(m, dtype=torch.float64, device=dev), "m": m}
+    per_n = {}
+    for n, G in groups.items():
+        best = L.gbk_autotune_dlogl(ctx, G["new"], G["old"], G["nb"], n, G["w"], R, P, G["out"], L.GBK_MIXED, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            L.gb_delta_loglike_batch(ctx, G["new"], G["old"], G["nb"], n, G["w"], R, P, G["out"], L.GBK_MIXED, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        per_n[str(n)] = {"proposals": G["m"], "proposals_per_s": G["m"] / (ms * 1e-3),
+                         "waveforms_per_s": 2 * G["m"] / (ms * 1e-3), "tuned_warps_per_cta": best[0],
+                         "tuned_ctas_per_sm": best[1] or "max"}
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(graph, stream=cap):
+            for n, G in groups.items():
+                L.gb_delta_loglike_batch(ctx, G["new"], G["old"], G["nb"], n, G["w"], R, P, G["out"], L.GBK_MIXED)
+    torch.cuda.current_stream().wait_stream(cap)
+    graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    L.gbk_sync_status(ctx)
+    ctx.close()
+    return {"workload": "200,000 proposals, f0 log-uniform 0.3-20 mHz, N = 128/256/512/1024 by octave; binned by N, "
+                        "autotuned launch shape per N, one CUDA graph of the 4 launches",
+            "proposals_per_s": n_prop / (ms * 1e-3), "ms_per_batch": ms, "per_N": per_n}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -398,6 +469,13 @@ def run_ours(args):
         del r3, s3
         ctx3.close()
 
+    # uneven band lengths in one batch (200,000 proposals, f0 log-uniform in 0.3-20 mHz, N by
+    # octave): binned by N, launch shape autotuned per N, the four launches captured in one
+    # CUDA graph and replayed
+    uneven = {}
+    if not args.no_uneven:
+        uneven = run_uneven(torch, L, dev, stream, seed=2 + 1000 * rank)
+
     # effective samples: integrated autocorrelation time of every cold walker's total
     # log-likelihood (Eq. like on its residual) over a run of sweeps
     ess = {}
@@ -492,6 +570,8 @@ def run_ours(args):
     line["config"].update(fp64)
     if c3:
         line["total_loglike"] = c3
+    if uneven:
+        line["uneven_n"] = uneven
     if ess:
         line["ess"] = ess
     if cpu is not None:
@@ -534,6 +614,7 @@ def main():
     ap.add_argument("--no-c3", action="store_true", help="skip the total log-likelihood (HBM) measurement")
     ap.add_argument("--ess-sweeps", type=int, default=120, help="sweeps for the ESS/s measurement (0: skip)")
     ap.add_argument("--c3-walkers", type=int, default=512, help="walkers of the total log-likelihood measurement")
+    ap.add_argument("--no-uneven", action="store_true", help="skip the uneven band-length measurement")
     ap.add_argument("--n-temps", type=int, default=N_T, help="smaller ensemble for profiling captures")
     args = ap.parse_args()
     if args.impl == "reference":

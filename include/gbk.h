@@ -141,6 +141,19 @@ gbk_status gb_delta_loglike_batch(gbk_ctx* ctx, const double* params_new,
                                   double* dlogl, gbk_precision precision, void* stream);
 
 /*
+ * gbk_autotune_dlogl -- pick the launch shape of gb_delta_loglike_batch for one band
+ * length and precision by timing the caller's sample batch (same arguments as that call)
+ * with every candidate (warps per CTA in {1, 2, 4, 8}, CTAs per SM in {1, 2, 4, as many as
+ * fit}); the fastest is kept in the context and used by later calls with the same
+ * n_band_max and precision. Synchronises `stream`. best_out (host, 2 ints, or NULL)
+ * receives (warps per CTA, CTAs per SM; 0 = as many as fit). dlogl is overwritten.
+ */
+gbk_status gbk_autotune_dlogl(gbk_ctx* ctx, const double* params_new, const double* params_old,
+                              const int32_t* n_band, int32_t n_band_max, const int32_t* walker, int64_t n,
+                              const gbk_residual* residual, const gbk_psd* psd, double* dlogl,
+                              gbk_precision precision, int32_t* best_out, void* stream);
+
+/*
  * residual_add_sub -- move n templates into or out of the model (Alg. 1 write-back).
  * sign = +1: the templates enter the model, R <- R - h; sign = -1: they leave, R <- R + h.
  * Each template value is rounded to the fixed-point grid before the integer update, so

@@ -74,6 +74,8 @@ SIGNATURES = {
     "gb_waveform_batch": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i64, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "gb_delta_loglike_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _vp, _i64, ctypes.POINTER(GbkResidual),
                                               ctypes.POINTER(GbkPsd), _vp, ctypes.c_int, _vp]),
+    "gbk_autotune_dlogl": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _vp, _i64, ctypes.POINTER(GbkResidual),
+                                          ctypes.POINTER(GbkPsd), _vp, ctypes.c_int, ctypes.POINTER(_i32), _vp]),
     "residual_add_sub": (ctypes.c_int, [_vp, ctypes.POINTER(GbkResidual), _vp, _vp, _i32, _vp, _i64, _i32,
                                         ctypes.c_int, _vp]),
     "psd_eval": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
@@ -280,3 +282,16 @@ def total_loglike_noalloc(tobs, k0, n_bins, residual, psd_params, logl, stream=N
     _check(lib().total_loglike_noalloc(float(tobs), int(k0), int(n_bins), _dev(residual, torch.float32, "residual"),
                                        _dev(psd_params, torch.float64, "psd_params"), w,
                                        _dev(logl, torch.float64, "logl"), _stream(stream)), "total_loglike_noalloc")
+
+
+def gbk_autotune_dlogl(ctx, params_new, params_old, n_band, n_band_max, walker, residual, psd, dlogl, precision,
+                       stream=None):
+    """Autotune the Delta lnL launch shape for one band length; returns (warps/CTA, CTAs/SM)."""
+    n = params_new.shape[1]
+    best = (_i32 * 2)()
+    _check(lib().gbk_autotune_dlogl(ctx.handle, _dev(params_new, torch.float64, "params_new"),
+                                    _dev(params_old, torch.float64, "params_old"), _dev(n_band, torch.int32, "n_band"),
+                                    int(n_band_max), _dev(walker, torch.int32, "walker"), n, ctypes.byref(residual),
+                                    ctypes.byref(psd), _dev(dlogl, torch.float64, "dlogl"), int(precision), best,
+                                    _stream(stream)), "gbk_autotune_dlogl")
+    return int(best[0]), int(best[1])

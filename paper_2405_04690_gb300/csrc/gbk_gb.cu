@@ -8,7 +8,8 @@
 
 namespace gbk {
 
-constexpr int kWarpsPerCta = 4;
+constexpr int kWarpsPerCta = 4;      // default warps per CTA
+constexpr int kMaxWarpsPerCta = 8;   // largest shape the autotuner may pick
 
 template <typename T>
 __device__ __forceinline__ const T* orb_table(const gbk_ctx& c, int bi);
@@ -47,7 +48,7 @@ __host__ __device__ constexpr size_t warp_bytes(int nmax, int nbuf, int nsrc) {
 
 // ---------------------------------------------------------------- gb_waveform_batch
 template <typename T, int NMAX>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+__global__ void __launch_bounds__(kMaxWarpsPerCta * 32)
 k_waveform(const gbk_ctx c, const double* __restrict__ params, const int32_t* __restrict__ nb,
            int64_t n, int64_t* __restrict__ k_start, typename CT<T>::C* __restrict__ ha,
            typename CT<T>::C* __restrict__ he, const int64_t* __restrict__ off) {
@@ -140,7 +141,7 @@ __device__ __forceinline__ void acc_bin(const gbk_ctx& c, const long long* __res
 
 // Batch of 16 proposals per warp: lanes 0-15 set up the new templates, 16-31 the old.
 template <typename T, int NMAX>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+__global__ void __launch_bounds__(kMaxWarpsPerCta * 32)
 k_dlogl(const gbk_ctx c, const double* __restrict__ pnew, const double* __restrict__ pold,
         const int32_t* __restrict__ nb, const int32_t* __restrict__ walker, int64_t n,
         const long long* __restrict__ resid, int32_t n_walkers, int32_t frac_bits,
@@ -238,7 +239,7 @@ __device__ __forceinline__ long long to_grid(float v, float s) { return __float2
 __device__ __forceinline__ long long to_grid(double v, double s) { return __double2ll_rn(v * s); }
 
 template <typename T, int NMAX>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+__global__ void __launch_bounds__(kMaxWarpsPerCta * 32)
 k_addsub(const gbk_ctx c, const double* __restrict__ params, const int32_t* __restrict__ nb,
          const int32_t* __restrict__ walker, int64_t n, long long* __restrict__ resid,
          int32_t n_walkers, int32_t frac_bits, int sign) {
@@ -309,8 +310,9 @@ static int warps_for(size_t per_warp) {
 
 template <typename K>
 static gbk_status launch_cfg(K kernel, size_t per_warp, int64_t items, int* grid_out, int* threads_out,
-                             size_t* smem_out) {
-  const int wpc = warps_for(per_warp);
+                             size_t* smem_out, int want_wpc = 0, int want_bps = 0) {
+  int wpc = warps_for(per_warp);
+  if (want_wpc > 0 && (size_t)want_wpc * per_warp <= 220 * 1024) wpc = want_wpc;
   const size_t smem = per_warp * wpc;
   if (smem > 48 * 1024) {
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
@@ -325,8 +327,9 @@ static gbk_status launch_cfg(K kernel, size_t per_warp, int64_t items, int* grid
     cudaGetLastError();
     return set_error(GBK_ECUDA, "kernel does not fit on an SM (smem=%zu)", smem);
   }
+  if (want_bps > 0 && want_bps < per_sm) per_sm = want_bps;
   int64_t need = (items + wpc - 1) / wpc;
-  int64_t cap = (int64_t)sms * per_sm;
+  int64_t cap = (int64_t)sms * per_sm;   // a multiple of the SM count: one persistent wave
   *grid_out = (int)(need < cap ? (need > 0 ? need : 1) : cap);
   *threads_out = wpc * 32;
   *smem_out = smem;
@@ -359,12 +362,14 @@ static gbk_status dlogl_t(gbk_ctx* ctx, const double* pn, const double* po, cons
                           const int32_t* walker, int64_t n, const gbk_residual* R, const gbk_psd* psd,
                           double* out, cudaStream_t st) {
   const size_t pw = warp_bytes<T>(nmax, 3, 32);
+  const int pi = sizeof(T) == sizeof(float) ? GBK_MIXED : GBK_FP64;
   int grid = 0, thr = 0;
   size_t smem = 0;
   gbk_status s = GBK_OK;
 #define GBK_DL(NM)                                                                                      \
   case NM:                                                                                              \
-    s = launch_cfg(k_dlogl<T, NM>, pw, (n + 15) / 16, &grid, &thr, &smem);                                          \
+    s = launch_cfg(k_dlogl<T, NM>, pw, (n + 15) / 16, &grid, &thr, &smem, ctx->tune_wpc[pi][band_index(NM)],     \
+                   ctx->tune_bps[pi][band_index(NM)]);                                          \
     if (s) return s;                                                                                    \
     k_dlogl<T, NM><<<grid, thr, smem, st>>>(*ctx, pn, po, nb, walker, n,                                \
                                                           (const long long*)R->data, R->n_walkers,      \
@@ -449,4 +454,53 @@ extern "C" gbk_status residual_add_sub(gbk_ctx* ctx, const gbk_residual* residua
   if (precision == GBK_MIXED) return addsub_t<float>(ctx, residual, params, n_band, n_band_max, walker, n, sign, st);
   if (precision == GBK_FP64) return addsub_t<double>(ctx, residual, params, n_band, n_band_max, walker, n, sign, st);
   return set_error(GBK_EINVAL, "residual_add_sub: bad precision %d", (int)precision);
+}
+
+// Time gb_delta_loglike_batch on the caller's sample batch for every launch shape (warps per
+// CTA 1, 2, 4, 8 that fit; CTAs per SM 1, 2, 4 or as many as fit) and keep the fastest for
+// this precision and band length in the context.
+extern "C" gbk_status gbk_autotune_dlogl(gbk_ctx* ctx, const double* params_new, const double* params_old,
+                                         const int32_t* n_band, int32_t n_band_max, const int32_t* walker, int64_t n,
+                                         const gbk_residual* residual, const gbk_psd* psd, double* dlogl,
+                                         gbk_precision precision, int32_t* best_out, void* stream) {
+  if (!ctx) return set_error(GBK_EINVAL, "gbk_autotune_dlogl: null context");
+  if (!valid_nmax(n_band_max) || (precision != GBK_MIXED && precision != GBK_FP64) || n < 1)
+    return set_error(GBK_EINVAL, "gbk_autotune_dlogl: bad arguments");
+  const int bi = band_index(n_band_max);
+  const int pi = (int)precision;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(GBK_ECUDA, "gbk_autotune_dlogl: cudaEventCreate failed");
+  }
+  float best = 1e30f;
+  int bw = 0, bb = 0;
+  const int wpcs[4] = {1, 2, 4, 8};
+  const int bpss[4] = {1, 2, 4, 0};
+  gbk_status s = GBK_OK;
+  for (int i = 0; i < 4 && !s; ++i)
+    for (int j = 0; j < 4 && !s; ++j) {
+      ctx->tune_wpc[pi][bi] = wpcs[i];
+      ctx->tune_bps[pi][bi] = bpss[j];
+      s = gb_delta_loglike_batch(ctx, params_new, params_old, n_band, n_band_max, walker, n, residual, psd, dlogl,
+                                 precision, stream);
+      if (s) break;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 3 && !s; ++r)
+        s = gb_delta_loglike_batch(ctx, params_new, params_old, n_band, n_band_max, walker, n, residual, psd, dlogl,
+                                   precision, stream);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (!s && ms < best) { best = ms; bw = wpcs[i]; bb = bpss[j]; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->tune_wpc[pi][bi] = bw;
+  ctx->tune_bps[pi][bi] = bb;
+  if (s) return s;
+  if (best_out) { best_out[0] = bw; best_out[1] = bb; }
+  return GBK_OK;
 }

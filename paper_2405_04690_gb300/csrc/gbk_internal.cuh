@@ -61,6 +61,10 @@ struct gbk_ctx {
   // scratch for cross-block partial sums of total_loglike
   double* scratch;
   size_t scratch_bytes;
+  // launch shapes chosen by gbk_autotune_dlogl: [precision][band index] warps per CTA
+  // and CTAs per SM (0 = library default)
+  int tune_wpc[2][4];
+  int tune_bps[2][4];
 };
 
 namespace gbk {

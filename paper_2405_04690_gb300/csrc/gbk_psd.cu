@@ -8,7 +8,7 @@ namespace gbk {
 
 constexpr int kTlThreads = 256;
 constexpr int kTlChunk = 4096;      // bins per block
-constexpr int kTlWalkers = 8;       // walkers per block
+constexpr int kTlWalkers = 4;       // walkers per block
 constexpr int kTlMaxW = 4096;       // walkers per launch pair (scratch sizing)
 
 size_t total_loglike_scratch_bytes(int64_t n_bins) {
@@ -30,25 +30,29 @@ __global__ void k_psd_eval(const double* __restrict__ q, const double* __restric
 // Per bin k and walker w (u = 1 + a_w rho_k, iq_k = 2^-128 / Q_k):
 //   q-term (|R_A|^2 + |R_E|^2) 2^128 iq_k / u,   l-term ln u.
 // Writes compensated block sums to part[(chunk * nwl + wl) * 2 + {0, 1}].
-__global__ void __launch_bounds__(kTlThreads)
+__global__ void __launch_bounds__(kTlThreads, 3)
 k_total_loglike_part(const float* __restrict__ R, const float* __restrict__ iq, const float* __restrict__ rho,
                      const double* __restrict__ pp, int32_t w0, int32_t nwl, int64_t nb, double* __restrict__ part) {
   const int chunk = blockIdx.x;
   const int wg = blockIdx.y * kTlWalkers;  // local walker offset within this launch
   const int64_t kbeg = (int64_t)chunk * kTlChunk;
   const int64_t kend = min(kbeg + (int64_t)kTlChunk, nb);
+  __shared__ float s_aw[kTlWalkers];
+  if (threadIdx.x < kTlWalkers) {     // per-walker S_acc / S_oms, once per block
+    const int wl = wg + threadIdx.x;
+    const int w = w0 + (wl < nwl ? wl : 0);
+    const double so = pp[2 * w] * pp[2 * w], sa = pp[2 * w + 1] * pp[2 * w + 1];
+    s_aw[threadIdx.x] = (float)(sa / so);
+  }
+  __syncthreads();
   float aw[kTlWalkers];
-  const float* rw[kTlWalkers];
   bool act[kTlWalkers];
 #pragma unroll
   for (int j = 0; j < kTlWalkers; ++j) {
-    const int wl = wg + j;
-    act[j] = wl < nwl;
-    const int w = w0 + (act[j] ? wl : 0);
-    const double so = pp[2 * w] * pp[2 * w], sa = pp[2 * w + 1] * pp[2 * w + 1];
-    aw[j] = (float)(sa / so);
-    rw[j] = R + (int64_t)w * 2 * nb * 2;
+    act[j] = wg + j < nwl;
+    aw[j] = s_aw[j];
   }
+  const float* rbase = R + (int64_t)(w0 + wg) * 2 * nb * 2;
   CompF sq[kTlWalkers], sl[kTlWalkers];
 #pragma unroll
   for (int j = 0; j < kTlWalkers; ++j) { sq[j].init(); sl[j].init(); }
@@ -62,8 +66,9 @@ k_total_loglike_part(const float* __restrict__ R, const float* __restrict__ iq, 
 #pragma unroll
       for (int j = 0; j < kTlWalkers; ++j) {
         if (act[j]) {
-          a[j] = __ldcs(reinterpret_cast<const float4*>(rw[j] + 2 * k));
-          e[j] = __ldcs(reinterpret_cast<const float4*>(rw[j] + 2 * (nb + k)));
+          const float* rw = rbase + (int64_t)j * 2 * nb * 2;
+          a[j] = __ldcs(reinterpret_cast<const float4*>(rw + 2 * k));
+          e[j] = __ldcs(reinterpret_cast<const float4*>(rw + 2 * (nb + k)));
         }
       }
 #pragma unroll
@@ -85,8 +90,9 @@ k_total_loglike_part(const float* __restrict__ R, const float* __restrict__ iq, 
 #pragma unroll
         for (int j = 0; j < kTlWalkers; ++j) {
           if (!act[j]) continue;
-          const float2 a = *reinterpret_cast<const float2*>(rw[j] + 2 * kk);
-          const float2 e = *reinterpret_cast<const float2*>(rw[j] + 2 * (nb + kk));
+          const float* rw = rbase + (int64_t)j * 2 * nb * 2;
+          const float2 a = *reinterpret_cast<const float2*>(rw + 2 * kk);
+          const float2 e = *reinterpret_cast<const float2*>(rw + 2 * (nb + kk));
           const float u = fmaf(aw[j], rhk, 1.0f);
           const float ax = a.x * up, ay = a.y * up, ex = e.x * up, ey = e.y * up;
           sq[j].add((ax * ax + ay * ay + ex * ex + ey * ey) * iqk * __frcp_rn(u));
