@@ -1,0 +1,120 @@
+"""Pins of the oracle's mixture-density proposal: gradients against finite differences,
+exact normalisation of the truncated mixture, sampling against the density, the unit-box
+coordinate map, and Adam's first step."""
+import math
+
+import numpy as np
+from scipy import integrate, stats
+from scipy.special import ndtr
+
+from oracle import mdn as MD
+
+from _sweep_setup import small_ensemble
+
+
+def _small_theta(g):
+    return MD.init_params(g, scale=0.5)
+
+
+def _sigma_logits(k):
+    return np.arange(k * 17 + 9, k * 17 + 17)
+
+
+def _broad_raw(g, rows, shift=2.0):
+    raw = g.normal(0, 1, (rows, MD.N_OUT))
+    for k in range(MD.N_COMP):
+        raw[:, _sigma_logits(k)] += shift        # sigma ~ 0.1-0.5: smooth enough for the checks
+    return raw
+
+
+def test_grad_raw_matches_finite_differences():
+    # fourth-order central differences of -ln q
+    g = np.random.default_rng(1)
+    raw = _broad_raw(g, 3, shift=1.0)
+    u = g.uniform(0.05, 0.95, (3, MD.N_DIM))
+    an = MD.grad_raw(raw, u)
+    h = 1e-4
+    for j in g.choice(MD.N_OUT, 80, replace=False):
+        f = []
+        for step in (h, -h, 2 * h, -2 * h):
+            r = raw.copy()
+            r[:, j] += step
+            f.append(-MD.log_q(r, u))
+        fd = (8 * (f[0] - f[1]) - (f[2] - f[3])) / (12 * h)
+        np.testing.assert_allclose(an[:, j], fd, rtol=1e-7, atol=1e-9)
+
+
+def test_backward_matches_finite_differences():
+    g = np.random.default_rng(2)
+    theta = _small_theta(g)
+    x = g.normal(0, 1, (4, MD.N_IN))
+    u = g.uniform(0.05, 0.95, (4, MD.N_DIM))
+    grad = MD.backward(theta, x, u)
+    assert grad.shape == (MD.n_params(),)
+    # parameters spread over every layer's weights and biases
+    offs, k = [], 0
+    for o, i in MD.LAYERS:
+        offs.append((k, o * i))
+        k += o * i
+        offs.append((k, o))
+        k += o
+    eps = 1e-6
+    for start, size in offs:
+        for j in g.choice(size, 4, replace=False):
+            idx = start + j
+            tp, tm = theta.copy(), theta.copy()
+            tp[idx] += eps
+            tm[idx] -= eps
+            fd = (MD.nll(tp, x, u) - MD.nll(tm, x, u)) / (2 * eps)
+            assert abs(grad[idx] - fd) <= 1e-5 * max(1e-3, abs(fd)), (idx, grad[idx], fd)
+
+
+def test_truncated_normal_integrates_to_one_on_the_box():
+    for mu, ls in ((0.02, -3.0), (0.5, 0.0), (0.97, -1.0), (0.3, -8.0)):
+        f = lambda x: math.exp(MD.log_trunc_normal(np.array(x), np.array(mu), np.array(ls)))
+        val, _ = integrate.quad(f, 0.0, 1.0, points=[mu], limit=200)
+        assert abs(val - 1.0) < 1e-7, (mu, ls, val)
+
+
+def test_mixture_density_integrates_to_one():
+    # broad random mixture; Monte Carlo over the unit box
+    g = np.random.default_rng(3)
+    raw = _broad_raw(g, 1, shift=3.0)
+    u = g.uniform(0, 1, (400000, MD.N_DIM))
+    q = np.exp(MD.log_q(np.repeat(raw, len(u), axis=0), u))
+    est = q.mean()
+    err = q.std() / math.sqrt(len(u))
+    assert abs(est - 1.0) < 5 * err + 1e-3, (est, err)
+
+
+def test_sampling_follows_the_density():
+    g = np.random.default_rng(4)
+    raw = g.normal(0, 1, (1, MD.N_OUT))
+    lpi, mu, ls = MD.mixture(raw)
+    draws = MD.sample(np.repeat(raw, 20000, axis=0), g)
+    # marginal CDF of dimension 2 under the mixture, by its closed form
+    d = 2
+
+    def cdf(x):
+        s = np.exp(ls[0, :, d])
+        m = mu[0, :, d]
+        lo, hi = ndtr(-m / s), ndtr((1 - m) / s)
+        return float(np.sum(np.exp(lpi[0]) * (ndtr((x - m) / s) - lo) / (hi - lo)))
+
+    assert stats.kstest(draws[:, d], np.vectorize(cdf)).pvalue > 1e-3
+
+
+def test_unit_coordinates_round_trip():
+    cfg, state, _, _ = small_ensemble(seed=12)
+    g = np.random.default_rng(5)
+    for _ in range(20):
+        u = g.uniform(0, 1, MD.N_DIM)
+        th = MD.from_unit(cfg, 1, u)
+        np.testing.assert_allclose(MD.to_unit(cfg, 1, th), u, rtol=1e-10, atol=1e-12)
+
+
+def test_adam_first_step_moves_by_lr_times_sign():
+    theta = np.array([1.0, -2.0, 0.5])
+    grad = np.array([3.0, -0.2, 1e-3])
+    t, m, v = MD.adam(theta, np.zeros(3), np.zeros(3), grad, 1, 0.01)
+    np.testing.assert_allclose(t, theta - 0.01 * np.sign(grad), rtol=0, atol=1e-6)
