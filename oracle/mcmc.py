@@ -24,6 +24,7 @@ import math
 import numpy as np
 
 from . import likelihood as LK
+from . import mdn as MD
 from . import philox as PX
 from . import residual as RS
 from . import waveform as WF
@@ -70,7 +71,15 @@ class SweepConfig:
       which is multiplied by exp(sigma_A z) (a symmetric move in ln A, whose Hastings
       factor cancels the 1/A prior);
     * n_prop = round(props_per_source * g) in-model proposals per band task, g the
-      number of sources in the band at the start of the task.
+      number of sources in the band at the start of the task;
+    * learned proposal (optional): ``mdn_raw`` gives the mixture-density outputs [272] of
+      every (walker, band), as an array [n_walkers][n_bands][272] or a function
+      (w, b, rho) -> [272] of the opened window. Births then draw from the defensive
+      mixture eps + (1 - eps) q_MDN in the band's unit coordinates (``oracle.mdn``), and a
+      fraction ``mdn_inmodel`` of the in-model moves are independence proposals from it.
+      rho does not change during the band's pass (it holds the cold chain's sources
+      outside band b and all of b's own), so q is one fixed density for every move of the
+      pass and Eq. rj-acceptance uses it as it stands.
     """
 
     def __init__(self, **kw):
@@ -97,6 +106,9 @@ class SweepConfig:
         self.f_min = kw.get("f_min", 1e-3)
         self.f_max = kw.get("f_max", 4e-3)
         self.df = 1.0 / self.tobs
+        self.mdn_raw = kw.get("mdn_raw", None)
+        self.mdn_eps = kw.get("mdn_eps", 0.1)
+        self.mdn_inmodel = kw.get("mdn_inmodel", 0.0)
 
     def band_bins(self, b):
         lo = self.band_k0 + b * self.nb
@@ -191,6 +203,26 @@ def draw_birth(cfg, b, words):
             TWO_PI * u[7]]
 
 
+def _mdn_row(cfg, w, b, rho):
+    if cfg.mdn_raw is None:
+        return None
+    if callable(cfg.mdn_raw):
+        return np.asarray(cfg.mdn_raw(w, b, rho), dtype=np.float64)
+    return np.asarray(cfg.mdn_raw[w][b], dtype=np.float64)
+
+
+def mdn_draw(cfg, raw, b, w_def, w_comp, w_dims):
+    """Draw from eps prior + (1 - eps) MDN: the prior branch is ``draw_birth`` on the same 8 words."""
+    if PX.u32(w_def) < cfg.mdn_eps:
+        return draw_birth(cfg, b, w_dims)
+    return MD.from_unit(cfg, b, MD.draw_unit(raw, w_comp, w_dims))
+
+
+def mdn_log_q(cfg, raw, b, th):
+    """ln q of source th of band b under the defensive mixture (unit coordinates, prior density 1)."""
+    return MD.log_q_defensive(raw, MD.to_unit(cfg, b, th), cfg.mdn_eps)
+
+
 def _rec(kind, t, w, b, slot, seq, acc, parity, dll, la, th, lu):
     """One trace record (the fields of the GPU trace plus ln u)."""
     return {"kind": kind, "t": t, "w": w, "b": b, "slot": slot, "seq": seq, "accepted": bool(acc),
@@ -254,6 +286,7 @@ def band_task(cfg, state, r_snap, rho, t, w, b, parity, sweep, trace):
             if th_new is not None:
                 R[w] = RS.add_sub(R[w], cfg.k0, WF.fastslow_band(th_new, cfg.nb, cfg.tobs), +1, cfg.frac_bits)
 
+    raw = _mdn_row(cfg, w, b, rho)
     existing = [s for s in range(cfg.n_max) if E[t, w, b, s]]
     g = len(existing)
     n_prop = int(round(cfg.props_per_source * g))
@@ -261,13 +294,20 @@ def band_task(cfg, state, r_snap, rho, t, w, b, parity, sweep, trace):
         words = _block_words(cfg.key, 12 * j, tid, 0 | (parity << 4), sweep, 12)
         k = existing[PX.ranged(words[0], g)]
         th = list(P[t, w, b, k])
-        new = propose_in_model(cfg, th, words)
+        indep = raw is not None and PX.u32(words[35]) < cfg.mdn_inmodel
+        if indep:   # independence proposal from the learned mixture
+            new = mdn_draw(cfg, raw, b, words[36], words[37], words[38:46])
+        else:
+            new = propose_in_model(cfg, th, words)
         lu = math.log(PX.u53(words[33], words[34])) if PX.u53(words[33], words[34]) > 0 else -math.inf
         if not in_support(cfg, new, b):
             trace.append(_rec(0, t, w, b, k, j, False, parity, float("nan"), -math.inf, new, lu))
             continue
         dll = _swap_dll(cfg, rp, psd_w, b, new, th)
-        la = beta * dll + dlog_prior(new, th)
+        if indep:   # unit coordinates: prior density 1, q(theta) / q(theta') is the Hastings factor
+            la = beta * dll + mdn_log_q(cfg, raw, b, th) - mdn_log_q(cfg, raw, b, new)
+        else:
+            la = beta * dll + dlog_prior(new, th)
         acc = lu < la
         trace.append(_rec(0, t, w, b, k, j, acc, parity, dll, la, new, lu))
         if acc:
@@ -289,15 +329,25 @@ def band_task(cfg, state, r_snap, rho, t, w, b, parity, sweep, trace):
             th = list(P[t, w, b, s])
             dll = _swap_dll(cfg, rp, psd_w, b, None, th)
             la = beta * dll - cfg.log_occ_odds
+            if raw is not None:
+                la += mdn_log_q(cfg, raw, b, th)
             acc = lu < la
             trace.append(_rec(2, t, w, b, s, j, acc, parity, dll, la, th, lu))
             if acc:
                 E[t, w, b, s] = False
                 apply(None, th)
         else:
-            new = draw_birth(cfg, b, words)
+            if raw is None:
+                new = draw_birth(cfg, b, words)
+            else:
+                new = mdn_draw(cfg, raw, b, words[10], words[11], words[0:8])
+                if not in_support(cfg, new, b):
+                    trace.append(_rec(1, t, w, b, s, j, False, parity, float("nan"), -math.inf, new, lu))
+                    continue
             dll = _swap_dll(cfg, rp, psd_w, b, new, None)
             la = beta * dll + cfg.log_occ_odds
+            if raw is not None:
+                la -= mdn_log_q(cfg, raw, b, new)
             acc = lu < la
             trace.append(_rec(1, t, w, b, s, j, acc, parity, dll, la, new, lu))
             if acc:

@@ -13,6 +13,10 @@ in the coordinates where the band's prior is uniform:
 (lo_b, hi_b the band's f0 allowance). In these coordinates the prior density is 1, so a
 birth's Eq. rj-acceptance ratio is L^beta / q(u).
 
+The proposal the sampler uses is the defensive mixture q(u) = eps + (1 - eps) q_MDN(u) (a
+fraction eps of the draws come from the prior), so that no region of the prior is left
+without proposals however the network was trained.
+
 Network: 1024 whitened inputs -> 512 -> 512 -> 512 (ReLU) -> 272 = 16 x (1 logit + 8 mu
 logits + 8 log-sigma logits); mu = sigmoid, ln sigma = S_MIN + (S_MAX - S_MIN) sigmoid,
 mixture weights softmax. Weights are [out][in] matrices.
@@ -22,7 +26,10 @@ import math
 import numpy as np
 from scipy.special import ndtr, ndtri
 
-from .mcmc import GM_SUN_C3, K_CHIRP
+from . import philox as PX
+from .constants import GM_SUN_C3
+
+K_CHIRP = 96.0 / 5.0 * math.pi ** (8.0 / 3.0)
 
 N_IN, N_HID, N_COMP, N_DIM = 1024, 512, 16, 8
 N_OUT = N_COMP * (1 + 2 * N_DIM)
@@ -183,3 +190,57 @@ def init_params(g, scale=1.0):
         out.append((g.standard_normal((o, i)) * scale * math.sqrt(2.0 / i)).ravel())
         out.append(np.zeros(o))
     return np.concatenate(out)
+
+
+# ---------------------------------------------------------------- inputs
+def to_bf16(x):
+    """Round float64 values to the nearest bfloat16 (ties to even), via float32."""
+    f = np.asarray(x, dtype=np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def features(rho, psd_w, df, nb=256):
+    """Whitened residual of a band's own sub-band: x[ch 512 + 2 i + {0: Re, 1: Im}] =
+    rho[ch][nb + i] sqrt(4 df / S_n), i < nb, rho the band window [2][3 nb] (sub-bands b-1, b,
+    b+1) with the band's own sources added back, psd_w the PSD on the window. Noise-only bins
+    are standard normal in each of Re and Im (Eq. inner's weight 4 df / S_n)."""
+    c = rho[:, nb:2 * nb] * np.sqrt(4.0 * df / psd_w[nb:2 * nb])[None, :]
+    x = np.empty(4 * nb)
+    for ch in range(2):
+        x[ch * 2 * nb:(ch + 1) * 2 * nb:2] = c[ch].real
+        x[ch * 2 * nb + 1:(ch + 1) * 2 * nb:2] = c[ch].imag
+    return x
+
+
+# ---------------------------------------------------------------- proposal used by the sampler
+def log_q_defensive(raw_row, u, eps):
+    """ln[eps + (1 - eps) q_MDN(u)] for one mixture (raw_row [272]) at one point u [8]."""
+    lq = float(log_q(np.asarray(raw_row)[None, :], np.asarray(u)[None, :])[0])
+    if eps >= 1.0:
+        return 0.0
+    if eps <= 0.0:
+        return lq
+    return float(np.logaddexp(math.log(eps), math.log1p(-eps) + lq))
+
+
+def draw_unit(raw_row, w_comp, w_dims):
+    """u from the truncated mixture: component = first k whose cumulative weight exceeds
+    u32(w_comp) (the last if rounding leaves none); per dimension the inverse CDF
+    u_d = mu + s Phi^-1(Phi(-mu/s) + [Phi((1-mu)/s) - Phi(-mu/s)] u32(w_d)), clamped to [0, 1]."""
+    lpi, mu, ls = mixture(np.asarray(raw_row)[None, :])
+    pi = np.exp(lpi[0])
+    v = PX.u32(w_comp)
+    k, c = N_COMP - 1, 0.0
+    for j in range(N_COMP):
+        c += pi[j]
+        if v < c:
+            k = j
+            break
+    u = np.empty(N_DIM)
+    for d in range(N_DIM):
+        m, s = mu[0, k, d], math.exp(ls[0, k, d])
+        lo, hi = ndtr(-m / s), ndtr((1.0 - m) / s)
+        u[d] = min(max(m + s * ndtri(lo + (hi - lo) * PX.u32(w_dims[d])), 0.0), 1.0)
+    return u

@@ -84,3 +84,57 @@ def test_prior_only_sweeps_reproduce_occupancy_and_f0_prior():
     n = len(occ) * cfg.n_bands * cfg.n_max
     assert abs(np.mean(occ) - pi) < 4 * math.sqrt(pi * (1 - pi) / n)
     assert stats.kstest(np.asarray(frel), "uniform").pvalue > 1e-3
+
+
+def _table(cfg, g, peaked=True):
+    from test_oracle_mdn import raw_from
+    from oracle import mdn as MD
+    t = np.empty((cfg.n_walkers, cfg.n_bands, MD.N_OUT))
+    for w in range(cfg.n_walkers):
+        for b in range(cfg.n_bands):
+            pi = g.dirichlet(np.ones(MD.N_COMP))
+            mu = g.uniform(0.25, 0.45, (MD.N_COMP, MD.N_DIM))
+            s = g.uniform(0.03, 0.08, (MD.N_COMP, MD.N_DIM)) if peaked else np.full((MD.N_COMP, MD.N_DIM), 0.3)
+            t[w, b] = raw_from(pi, mu, s)
+    return t
+
+
+def test_learned_proposal_with_eps_one_is_the_prior_sweep():
+    # eps = 1 draws every birth from the prior branch (the same words as the prior draw)
+    # and q = 1: the trace must equal the plain sweep's, decision by decision.
+    cfg, state, _, _ = small_ensemble(seed=4, n_temps=2, n_walkers=1, n_bands=2, n_max=3, n_per_band=1,
+                                      betas=(1.0, 0.5))
+    t_plain = OM.sweep(cfg, copy_state(state), 0)
+    cfg.mdn_raw, cfg.mdn_eps = _table(cfg, np.random.default_rng(5)), 1.0
+    t_mdn = OM.sweep(cfg, copy_state(state), 0)
+    assert len(t_plain) == len(t_mdn)
+    for a, b in zip(t_plain, t_mdn):
+        assert a["accepted"] == b["accepted"] and a["params"] == b["params"]
+        assert a["log_alpha"] == b["log_alpha"] or (math.isinf(a["log_alpha"]) and math.isinf(b["log_alpha"]))
+
+
+def test_prior_only_sweeps_with_learned_proposal_keep_the_prior():
+    # With beta = 0 the target is the prior. A peaked proposal (components near u = 0.35,
+    # widths 0.03-0.08) used for births, deaths and half the in-model moves must leave
+    # the occupancy and the unit-box marginals unchanged; a wrong sign or a missing q
+    # factor piles the sources up where q is large.
+    pi = 0.4
+    cfg, state, _, _ = small_ensemble(seed=10, n_temps=1, n_walkers=1, n_bands=2, n_max=6, n_per_band=1,
+                                      betas=(0.0,), log_occ_odds=math.log(pi / (1 - pi)))
+    from oracle import mdn as MD
+    cfg.mdn_raw, cfg.mdn_eps, cfg.mdn_inmodel = _table(cfg, np.random.default_rng(6)), 0.2, 0.5
+    st = copy_state(state)
+    occ, u = [], []
+    for k in range(60):
+        OM.sweep(cfg, st, k, do_swap=False)
+        if k >= 4:
+            occ.append(st["exists"].mean())
+            for b in range(cfg.n_bands):
+                for s in range(cfg.n_max):
+                    if st["exists"][0, 0, b, s]:
+                        u.append(MD.to_unit(cfg, b, st["params"][0, 0, b, s]))
+    u = np.asarray(u)
+    n = len(occ) * cfg.n_bands * cfg.n_max
+    assert abs(np.mean(occ) - pi) < 4 * math.sqrt(pi * (1 - pi) / n) * 2   # x2: correlated sweeps
+    for d in (0, 1, 2, 7):
+        assert stats.kstest(u[:, d], "uniform").pvalue > 1e-3, d

@@ -118,3 +118,66 @@ def test_adam_first_step_moves_by_lr_times_sign():
     grad = np.array([3.0, -0.2, 1e-3])
     t, m, v = MD.adam(theta, np.zeros(3), np.zeros(3), grad, 1, 0.01)
     np.testing.assert_allclose(t, theta - 0.01 * np.sign(grad), rtol=0, atol=1e-6)
+
+
+def raw_from(pi, mu, s):
+    """Raw network outputs [272] for given weights pi [16], means mu [16][8] and widths s [16][8]."""
+    raw = np.empty((MD.N_COMP, 1 + 2 * MD.N_DIM))
+    raw[:, 0] = np.log(pi)
+    raw[:, 1:1 + MD.N_DIM] = np.log(mu / (1 - mu))
+    sg = (np.log(s) - MD.S_MIN) / (MD.S_MAX - MD.S_MIN)
+    raw[:, 1 + MD.N_DIM:] = np.log(sg / (1 - sg))
+    return raw.ravel()
+
+
+def _peaked_raw(g):
+    pi = g.dirichlet(np.ones(MD.N_COMP))
+    mu = g.uniform(0.2, 0.8, (MD.N_COMP, MD.N_DIM))
+    s = g.uniform(0.03, 0.15, (MD.N_COMP, MD.N_DIM))
+    return raw_from(pi, mu, s)
+
+
+def test_raw_from_inverts_the_output_maps():
+    g = np.random.default_rng(11)
+    pi = g.dirichlet(np.ones(MD.N_COMP))
+    mu = g.uniform(0.1, 0.9, (MD.N_COMP, MD.N_DIM))
+    s = g.uniform(0.01, 0.5, (MD.N_COMP, MD.N_DIM))
+    lpi, m2, ls = MD.mixture(raw_from(pi, mu, s)[None, :])
+    assert np.allclose(np.exp(lpi[0]), pi, rtol=1e-12)
+    assert np.allclose(m2[0], mu, rtol=1e-12)
+    assert np.allclose(np.exp(ls[0]), s, rtol=1e-12)
+
+
+def test_draw_unit_follows_the_mixture_marginals():
+    # Draws from fixed words: each coordinate's empirical CDF against the mixture's
+    # closed-form marginal CDF sum_k pi_k [Phi((x-mu)/s) - Phi(-mu/s)] / Z_k.
+    g = np.random.default_rng(12)
+    raw = _peaked_raw(g)
+    lpi, mu, ls = MD.mixture(raw[None, :])
+    pi, mu, s = np.exp(lpi[0]), mu[0], np.exp(ls[0])
+    n = 4000
+    words = g.integers(0, 2 ** 32, (n, 9), dtype=np.uint64)
+    u = np.array([MD.draw_unit(raw, int(wd[0]), [int(x) for x in wd[1:]]) for wd in words])
+    for d in (0, 3, 7):
+        def cdf(x, d=d):
+            x = np.atleast_1d(x)[:, None]
+            lo, hi = ndtr(-mu[:, d] / s[:, d]), ndtr((1 - mu[:, d]) / s[:, d])
+            return np.sum(pi * (ndtr((x - mu[:, d]) / s[:, d]) - lo) / (hi - lo), axis=1)
+        assert stats.kstest(u[:, d], cdf).pvalue > 1e-3
+
+
+def test_defensive_density_integrates_to_one_and_reduces_to_prior():
+    g = np.random.default_rng(13)
+    raw = _peaked_raw(g)
+    # the integral of q over the box is 1: E_uniform[q] for a mixture broad enough that
+    # uniform draws sample it well
+    pi = g.dirichlet(np.ones(MD.N_COMP))
+    broad = raw_from(pi, g.uniform(0.2, 0.8, (MD.N_COMP, MD.N_DIM)), g.uniform(0.25, 0.6, (MD.N_COMP, MD.N_DIM)))
+    x = g.uniform(0, 1, (20000, MD.N_DIM))
+    q = np.exp(MD.log_q(np.tile(broad, (len(x), 1)), x))
+    assert abs(q.mean() - 1.0) < 5 * q.std() / math.sqrt(len(x)), (q.mean(), q.std())
+    # eps = 1 is the prior (density 1 everywhere); eps mixes linearly
+    x = g.uniform(0, 1, MD.N_DIM)
+    assert MD.log_q_defensive(raw, x, 1.0) == 0.0
+    q = math.exp(MD.log_q(raw[None, :], x[None, :])[0])
+    assert abs(math.exp(MD.log_q_defensive(raw, x, 0.25)) - (0.25 + 0.75 * q)) < 1e-12 * (1 + q)
