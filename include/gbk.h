@@ -254,6 +254,7 @@ gbk_status gbk_sweep_destroy(gbk_sweep* plan);
 #define GBK_SWEEP_SWAP 4
 #define GBK_SWEEP_REFRESH 8   /* regenerate the waveform cache from params/exists first */
 #define GBK_SWEEP_TIMING 16   /* record CUDA events around each kernel (see gbk_sweep_kernel_ms) */
+#define GBK_SWEEP_MDN 32      /* use the learned proposal set by gbk_sweep_set_proposal */
 
 /*
  * gb_sweep -- one sweep (both parities) on `stream`; allocates nothing.
@@ -273,9 +274,108 @@ gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists, const doub
                     void* stream);
 
 /* Device time in ms of the last sweep run with GBK_SWEEP_TIMING, per kernel kind:
- * ms_out[0] cache refresh, [1] band opening, [2] band kernel (in-model + RJ), [3]
+ * ms_out[0] cache refresh, [1] band opening (with the learned proposal's features,
+ * network and mixture rows under GBK_SWEEP_MDN), [2] band kernel (in-model + RJ), [3]
  * tempering swaps, each summed over both parities. Synchronises with those events. */
 gbk_status gbk_sweep_kernel_ms(gbk_sweep* plan, double* ms_out);
+
+/* ------------------------------------------------------------------ learned proposal
+ * A mixture-density network (MDN) proposes births and independence in-model moves. The
+ * paper proposes births from Gaussian mixtures fitted to earlier sampler output (Sec.
+ * V.E, App. G) and names learned density estimators as the next step (App. G). Here an
+ * MLP maps the whitened residual of a band to a 16-component diagonal Gaussian mixture
+ * truncated to the unit box of the band's prior coordinates
+ *   u = ((ln A - ln A_min) / (ln A_max - ln A_min), (f0 - lo_b) / (hi_b - lo_b),
+ *        (Mc - Mc_min) / (Mc_max - Mc_min), phi0 / 2pi, psi / pi, (cos i + 1) / 2,
+ *        (sin beta + 1) / 2, lambda / 2pi)
+ * ([lo_b, hi_b) the f0 range of band b's sources, Mc the chirp mass of (f0, fdot)), where
+ * the prior density is 1. Each component is renormalised on the box (erf), so q is an
+ * exact density and Eq. rj-acceptance uses it as it stands: birth ratio
+ * L'^beta pi_occ / ((1 - pi_occ) q_eps(u')), death its inverse, independence in-model
+ * move (L'/L)^beta q_eps(u) / q_eps(u'), with q_eps = eps + (1 - eps) q (a fraction eps of
+ * the draws from the prior).
+ *
+ * The network's input for band b of walker w is the band's opened window rho (the cold
+ * residual with b's own cold sources added back), which does not change while band b's
+ * tasks run, so q is one fixed density for every move of that pass (detailed balance
+ * holds move by move); its 256 central bins, whitened, are the 1024 inputs
+ *   x[ch 512 + 2 i + {0, 1}] = (Re, Im) rho_ch(f_i) sqrt(4 df / S_n(f_i)),  ch = A, E.
+ *
+ * Network: 1024 -> 512 -> 512 -> 512 (ReLU) -> 272 = 16 x (weight logit, 8 mean logits,
+ * 8 width logits); weights [out][in] row-major, flat parameter vector
+ *   W1[512][1024] b1[512] W2[512][512] b2[512] W3[512][512] b3[512] W4[272][512] b4[272]
+ * (mdn_param_count() = 1,189,648 float32). Mixture: pi = softmax(weight logits),
+ * mu = sigmoid(mean logits), ln s = -10 + 10 sigmoid(width logits).
+ * Products run on BF16 tensor cores with float32 accumulation; the float32 master
+ * parameters and Adam moments belong to the caller.
+ */
+typedef struct gbk_mdn gbk_mdn;
+
+int64_t mdn_param_count(void);
+
+/* Workspace for batches of up to max_batch rows (activations, gradient partials, BF16
+ * weight copy). Allocates device memory (about 6 KB per row + 86 MB). */
+gbk_status mdn_create(gbk_mdn** out, int32_t max_batch);
+gbk_status mdn_destroy(gbk_mdn* net);
+
+/* Load float32 parameters [mdn_param_count()] (device) into the workspace's copies. */
+gbk_status mdn_set_params(gbk_mdn* net, const float* params, void* stream);
+
+/* raw [batch][272] float32 out = network(x), x [batch][1024] BF16 bit patterns (16-byte
+ * aligned). */
+gbk_status mdn_forward(gbk_mdn* net, const uint16_t* x, int32_t batch, float* raw, void* stream);
+
+/* Gradient of the mean negative log density -1/batch sum_i ln q(u_i | x_i) with respect
+ * to the parameters: grad [mdn_param_count()] float32 out; loss (device double, or NULL)
+ * out. u [batch][8] float32 unit coordinates. Weight gradients are summed over batch
+ * splits in a fixed order (deterministic). */
+gbk_status mdn_backward(gbk_mdn* net, const uint16_t* x, const float* u, int32_t batch, float* grad,
+                        double* loss, void* stream);
+
+/* One Adam step (Kingma & Ba 2015): m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2,
+ * params <- params - lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps); also
+ * reloads the workspace's copies. step counts from 1. */
+gbk_status mdn_adam(gbk_mdn* net, float* params, float* m, float* v, const float* grad, int32_t step,
+                    float lr, float beta1, float beta2, float eps, void* stream);
+
+/* mdn_backward followed by Adam (b1 0.9, b2 0.999, eps 1e-8) without the reduced
+ * gradient leaving the device workspace. */
+gbk_status mdn_train_step(gbk_mdn* net, float* params, float* m, float* v, const uint16_t* x,
+                          const float* u, int32_t batch, int32_t step, float lr, double* loss,
+                          void* stream);
+
+/* Draws from and densities of the eps-defensive mixture given raw outputs [batch][272]
+ * (the sampler's own arithmetic, in `precision`):
+ *   words  [batch][9] uint32 or NULL: word 0 picks the component (first k whose
+ *          cumulative weight exceeds (w + 1/2) 2^-32), words 1-8 give the dimensions by
+ *          the inverse CDF of the truncated normal; u_out [batch][8] (or NULL) receives u
+ *   u_in   [batch][8], used when words is NULL
+ *   logq   [batch] out (or NULL): ln q_eps at the drawn or given u. */
+gbk_status mdn_sample_logpdf(const float* raw, int32_t batch, double eps, const uint32_t* words,
+                             float* u_out, const float* u_in, float* logq, int32_t precision,
+                             void* stream);
+
+/* Attach the learned proposal to a sweep plan (used by gb_sweep with GBK_SWEEP_MDN):
+ *   net        network evaluated on each half sweep's opened windows (band_bins 256;
+ *              max_batch >= n_walkers * ceil(n_bands / 2)), its parameters as last set, or
+ *   raw_table  [n_walkers][n_bands][272] float32 device: fixed mixture outputs used as
+ *              given (any band_bins; net is then ignored)
+ *   eps        prior fraction of the defensive mixture, in [0, 1] (1: the plain prior)
+ *   inmodel_frac  fraction of in-model moves that are independence draws, in [0, 1]
+ * Both NULL turns the proposal off. Allocates the plan's feature / mixture buffers
+ * (about 12 KB per window) on first use. The table, or the network object, must stay
+ * alive while the plan uses it. */
+gbk_status gbk_sweep_set_proposal(gbk_sweep* plan, gbk_mdn* net, const float* raw_table, double eps,
+                                  double inmodel_frac);
+
+/* Training pairs from the current cold chain (band_bins 256): x_out [n_walkers][n_bands]
+ * [1024] BF16 features of every band's opened window (as above), u_out [n_walkers]
+ * [n_bands][n_max][8] float32 unit coordinates of every cold slot (NaN where empty);
+ * either may be NULL. Reads the plan's template-sum cache, so params/exists must be the
+ * state left by the last gb_sweep (or a sweep with GBK_SWEEP_REFRESH). */
+gbk_status gb_sweep_features(gbk_sweep* plan, const double* params, const uint8_t* exists,
+                             const gbk_residual* residual, const gbk_psd* psd, uint16_t* x_out,
+                             float* u_out, void* stream);
 
 /* ------------------------------------------------------------------ no-allocation variant
  * total_loglike_noalloc -- the same result as total_loglike (Eq. like for W walkers, both

@@ -74,14 +74,23 @@ def from_unit(cfg, b, u):
 
 
 # ---------------------------------------------------------------- network
-def forward(theta, x):
-    """x [B][1024] -> (raw outputs [B][272], cache of activations)."""
+def forward(theta, x, quantized=False):
+    """x [B][1024] -> (raw outputs [B][272], cache of activations).
+
+    quantized: the network as the tensor-core path defines it, with every weight matrix
+    and every hidden activation rounded to bfloat16 (biases and outputs unrounded); the
+    arithmetic between the rounding points stays float64."""
     layers = unpack(theta)
     acts = [x]
     h = x
     for li, (w, b) in enumerate(layers):
-        z = h @ w.T + b
-        h = np.maximum(z, 0.0) if li < len(layers) - 1 else z
+        z = h @ (to_bf16(w) if quantized else w).T + b
+        if li < len(layers) - 1:
+            h = np.maximum(z, 0.0)
+            if quantized:
+                h = to_bf16(h)
+        else:
+            h = z
         acts.append(h)
     return h, acts
 
@@ -141,10 +150,13 @@ def grad_raw(raw, u):
     return d.reshape(raw.shape[0], -1)
 
 
-def backward(theta, x, u):
-    """Gradient of the mean NLL with respect to the flat parameters."""
+def backward(theta, x, u, quantized=False):
+    """Gradient of the mean NLL with respect to the flat parameters (quantized: of the
+    bfloat16-rounded network of ``forward``, rounding passed through as the identity)."""
     layers = unpack(theta)
-    raw, acts = forward(theta, x)
+    if quantized:
+        layers = [(to_bf16(w), b) for w, b in layers]
+    raw, acts = forward(theta, x, quantized)
     g = grad_raw(raw, u) / x.shape[0]
     grads = []
     for li in range(len(layers) - 1, -1, -1):
@@ -183,12 +195,18 @@ def sample(raw, g):
     return out
 
 
-def init_params(g, scale=1.0):
-    """He-style random initialisation (for tests and as the training start)."""
+def init_params(g, scale=1.0, out_scale=0.1, width_bias=2.0):
+    """He-style random initialisation (for tests and as a training start): hidden layers
+    N(0, 2 / fan_in) x scale, the output layer a further x out_scale, and the width-logit
+    biases at width_bias (s = e^(-10 + 10 sigmoid(2)) ~ 0.3: broad components to start)."""
     out = []
-    for o, i in LAYERS:
-        out.append((g.standard_normal((o, i)) * scale * math.sqrt(2.0 / i)).ravel())
-        out.append(np.zeros(o))
+    for li, (o, i) in enumerate(LAYERS):
+        sc = scale * (out_scale if li == len(LAYERS) - 1 else 1.0)
+        out.append((g.standard_normal((o, i)) * sc * math.sqrt(2.0 / i)).ravel())
+        b = np.zeros(o)
+        if li == len(LAYERS) - 1:
+            b.reshape(N_COMP, 1 + 2 * N_DIM)[:, 1 + N_DIM:] = width_bias
+        out.append(b)
     return np.concatenate(out)
 
 

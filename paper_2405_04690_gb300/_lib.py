@@ -61,6 +61,7 @@ SWEEP_RJ = 2
 SWEEP_SWAP = 4
 SWEEP_REFRESH = 8
 SWEEP_TIMING = 16
+SWEEP_MDN = 32
 TRACE_DTYPE_FIELDS = [("kind", "<i4"), ("t", "<i4"), ("w", "<i4"), ("b", "<i4"), ("slot", "<i4"), ("seq", "<i4"),
                       ("accepted", "<i4"), ("parity", "<i4"), ("dlogl", "<f8"), ("log_alpha", "<f8"),
                       ("params", "<f8", (8,))]
@@ -87,6 +88,19 @@ SIGNATURES = {
     "total_loglike_noalloc": (ctypes.c_int, [ctypes.c_double, _i64, _i64, _vp, _vp, _i32, _vp, _vp]),
     "gb_sweep": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(GbkResidual), ctypes.POINTER(GbkPsd),
                                 ctypes.c_uint64, ctypes.c_uint32, _i32, ctypes.POINTER(GbkTrace), _vp, _vp]),
+    "mdn_param_count": (ctypes.c_int64, []),
+    "mdn_create": (ctypes.c_int, [ctypes.POINTER(_vp), _i32]),
+    "mdn_destroy": (ctypes.c_int, [_vp]),
+    "mdn_set_params": (ctypes.c_int, [_vp, _vp, _vp]),
+    "mdn_forward": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
+    "mdn_backward": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
+    "mdn_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, _vp]),
+    "mdn_train_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp]),
+    "mdn_sample_logpdf": (ctypes.c_int, [_vp, _i32, ctypes.c_double, _vp, _vp, _vp, _vp, _i32, _vp]),
+    "gbk_sweep_set_proposal": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double]),
+    "gb_sweep_features": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(GbkResidual), ctypes.POINTER(GbkPsd), _vp, _vp,
+                                         _vp]),
 }
 
 _LIB = None
@@ -295,3 +309,86 @@ def gbk_autotune_dlogl(ctx, params_new, params_old, n_band, n_band_max, walker, 
                                     ctypes.byref(psd), _dev(dlogl, torch.float64, "dlogl"), int(precision), best,
                                     _stream(stream)), "gbk_autotune_dlogl")
     return int(best[0]), int(best[1])
+
+
+# ------------------------------------------------------------------ learned proposal
+class Mdn:
+    """Owns a gbk_mdn workspace (BF16 weight copy, activations, gradient partials)."""
+
+    def __init__(self, max_batch):
+        h = _vp()
+        _check(lib().mdn_create(ctypes.byref(h), int(max_batch)), "mdn_create")
+        self.handle = h
+        self.max_batch = int(max_batch)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().mdn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mdn_param_count():
+    return int(lib().mdn_param_count())
+
+
+def mdn_set_params(net, params, stream=None):
+    _check(lib().mdn_set_params(net.handle, _dev(params, torch.float32, "params"), _stream(stream)), "mdn_set_params")
+
+
+def mdn_forward(net, x, raw, stream=None):
+    """raw [B][272] float32 = network(x), x [B][1024] bfloat16."""
+    _check(lib().mdn_forward(net.handle, _dev(x, torch.bfloat16, "x"), int(x.shape[0]), _dev(raw, torch.float32, "raw"),
+                             _stream(stream)), "mdn_forward")
+
+
+def mdn_backward(net, x, u, grad, loss=None, stream=None):
+    _check(lib().mdn_backward(net.handle, _dev(x, torch.bfloat16, "x"), _dev(u, torch.float32, "u"), int(x.shape[0]),
+                              _dev(grad, torch.float32, "grad"),
+                              _dev(loss, torch.float64, "loss") if loss is not None else None, _stream(stream)),
+           "mdn_backward")
+
+
+def mdn_adam(net, params, m, v, grad, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().mdn_adam(net.handle, _dev(params, torch.float32, "params"), _dev(m, torch.float32, "m"),
+                          _dev(v, torch.float32, "v"), _dev(grad, torch.float32, "grad"), int(step), float(lr),
+                          float(beta1), float(beta2), float(eps), _stream(stream)), "mdn_adam")
+
+
+def mdn_train_step(net, params, m, v, x, u, step, lr, loss=None, stream=None):
+    _check(lib().mdn_train_step(net.handle, _dev(params, torch.float32, "params"), _dev(m, torch.float32, "m"),
+                                _dev(v, torch.float32, "v"), _dev(x, torch.bfloat16, "x"), _dev(u, torch.float32, "u"),
+                                int(x.shape[0]), int(step), float(lr),
+                                _dev(loss, torch.float64, "loss") if loss is not None else None, _stream(stream)),
+           "mdn_train_step")
+
+
+def mdn_sample_logpdf(raw, eps, precision, words=None, u_out=None, u_in=None, logq=None, stream=None):
+    _check(lib().mdn_sample_logpdf(_dev(raw, torch.float32, "raw"), int(raw.shape[0]), float(eps),
+                                   _dev(words, torch.int32, "words") if words is not None else None,
+                                   _dev(u_out, torch.float32, "u_out") if u_out is not None else None,
+                                   _dev(u_in, torch.float32, "u_in") if u_in is not None else None,
+                                   _dev(logq, torch.float32, "logq") if logq is not None else None,
+                                   int(precision), _stream(stream)), "mdn_sample_logpdf")
+
+
+def gbk_sweep_set_proposal(plan, net=None, raw_table=None, eps=0.1, inmodel_frac=0.0):
+    """Attach the learned proposal (a network, or a fixed raw table [W][n_bands][272]) to a sweep plan."""
+    plan._proposal_refs = (net, raw_table)   # keep them alive while the plan uses them
+    _check(lib().gbk_sweep_set_proposal(plan.handle, net.handle if net is not None else None,
+                                        _dev(raw_table, torch.float32, "raw_table") if raw_table is not None else None,
+                                        float(eps), float(inmodel_frac)), "gbk_sweep_set_proposal")
+
+
+def gb_sweep_features(plan, params, exists, residual, psd, x_out=None, u_out=None, stream=None):
+    """Features [W][n_bands][1024] bfloat16 and cold-slot unit coordinates [W][n_bands][n_max][8] float32."""
+    _check(lib().gb_sweep_features(plan.handle, _dev(params, torch.float64, "params"),
+                                   _dev(exists, torch.uint8, "exists"), ctypes.byref(residual), ctypes.byref(psd),
+                                   _dev(x_out, torch.bfloat16, "x_out") if x_out is not None else None,
+                                   _dev(u_out, torch.float32, "u_out") if u_out is not None else None,
+                                   _stream(stream)), "gb_sweep_features")

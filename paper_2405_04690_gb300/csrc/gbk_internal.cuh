@@ -1,6 +1,7 @@
 // Internal definitions of libgbk: context, constants, device helpers.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -65,6 +66,20 @@ struct gbk_ctx {
   // and CTAs per SM (0 = library default)
   int tune_wpc[2][4];
   int tune_bps[2][4];
+};
+
+// Mixture-density network workspace (gbk_mdn.cu).
+struct gbk_mdn {
+  int32_t max_batch;
+  float* pf;             // float32 copy of the parameters (biases of the forward pass)
+  __nv_bfloat16* pb;     // BF16 copy (weights)
+  __nv_bfloat16* h[3];   // hidden activations [max_batch][512]
+  float* raw;            // [max_batch][272]
+  __nv_bfloat16* g4;     // d loss / d raw [max_batch][272]
+  __nv_bfloat16* g[2];   // backward activations [max_batch][512]
+  float* nll;            // [max_batch]
+  float* part;           // split-K gradient partials [16][n_params]
+  bool have_params;
 };
 
 namespace gbk {

@@ -4,6 +4,7 @@
 #include <stdlib.h>
 
 #include "gbk_internal.cuh"
+#include "gbk_mix.cuh"
 #include "gbk_philox.cuh"
 #include "gbk_reduce.cuh"
 #include "gbk_wave.cuh"
@@ -20,6 +21,14 @@ struct gbk_sweep {
   size_t rho_bytes, cache_bytes, hsum_bytes;
   cudaEvent_t ev[2][4][2];  // [parity][refresh, open, band, swap][begin, end] when timing
   bool timed, have_ev;
+  // learned proposal (gbk_sweep_set_proposal)
+  bool mdn_set;
+  gbk_mdn* net;             // network run on each half sweep's opened windows, or
+  const float* raw_table;   // fixed mixture outputs [W][B][272]
+  double mdn_eps, mdn_inmodel;
+  uint16_t* xfeat;          // BF16 features [W][n_bp_max][1024]
+  float* rawbuf;            // network outputs [W][n_bp_max][272]
+  void* mix;                // mixture rows [W][n_bp_max] (MixRow of the sweep precision)
 };
 
 namespace gbk {
@@ -50,6 +59,9 @@ struct SweepArgs {
   int32_t trace_cap;
   int32_t* trace_count;
   long long* stats;
+  // learned proposal: mixture row of every opened (walker, band) or NULL
+  const void* mix;
+  double mdn_eps, mdn_inmodel;
 };
 
 template <typename T> __device__ __forceinline__ const T* orb_of(const gbk_ctx& c, int bi);
@@ -170,6 +182,64 @@ __device__ __forceinline__ void draw_birth(const gbk_sweep_desc& d, double tobs,
   nw[7] = dmul(TWO_PI, u32(w[7]));
 }
 
+// Unit-box coordinates of band b, where the prior is uniform (the learned proposal's
+// space): ln A, f0 over the allowance, chirp mass, phi0 / 2pi, psi / pi, (cos i + 1) / 2,
+// (sin beta + 1) / 2, lambda / 2pi.
+__device__ __forceinline__ void to_unit(const gbk_sweep_desc& d, double tobs, int b, const double* th, double* u) {
+  double lo, hi;
+  allowance(d, tobs, b, lo, hi);
+  const double K = 96.0 / 5.0 * 21.170591578193026;
+  const double mc = pow(th[2] / (K * pow(th[1], 11.0 / 3.0)), 0.6) / 4.925490947e-6;
+  u[0] = (log(th[0]) - d.ln_a_min) / (d.ln_a_max - d.ln_a_min);
+  u[1] = (th[1] - lo) / (hi - lo);
+  u[2] = (mc - d.mc_min) / (d.mc_max - d.mc_min);
+  u[3] = th[3] / 6.283185307179586;
+  u[4] = th[4] / 3.141592653589793;
+  u[5] = (th[5] + 1.0) / 2.0;
+  u[6] = (th[6] + 1.0) / 2.0;
+  u[7] = th[7] / 6.283185307179586;
+}
+__device__ __forceinline__ void from_unit(const gbk_sweep_desc& d, double tobs, int b, const double* u, double* nw) {
+  double lo, hi;
+  allowance(d, tobs, b, lo, hi);
+  const double f0 = lo + (hi - lo) * u[1];
+  const double mc = d.mc_min + (d.mc_max - d.mc_min) * u[2];
+  const double K = 96.0 / 5.0 * 21.170591578193026;
+  nw[0] = exp(d.ln_a_min + (d.ln_a_max - d.ln_a_min) * u[0]);
+  nw[1] = f0;
+  nw[2] = K * pow(f0, 11.0 / 3.0) * pow(mc * 4.925490947e-6, 5.0 / 3.0);
+  nw[3] = 6.283185307179586 * u[3];
+  nw[4] = 3.141592653589793 * u[4];
+  nw[5] = 2.0 * u[5] - 1.0;
+  nw[6] = 2.0 * u[6] - 1.0;
+  nw[7] = 6.283185307179586 * u[7];
+}
+
+// Draw from eps prior + (1 - eps) mixture: the prior branch is draw_birth on the same 8 words.
+template <typename T>
+__device__ __forceinline__ void mdn_draw(const SweepArgs& a, const MixRow<T>& m, int b, uint32_t w_def, uint32_t w_comp,
+                                         const uint32_t* w_dims, double* nw) {
+  if (mix_u32(w_def) < a.mdn_eps) {
+    draw_birth(a.d, a.c.grid.tobs, b, w_dims, nw);
+    return;
+  }
+  T u[kMixDim];
+  mix_draw<T>(m, w_comp, w_dims, u);
+  double ud[kMixDim];
+#pragma unroll
+  for (int c = 0; c < kMixDim; ++c) ud[c] = (double)u[c];
+  from_unit(a.d, a.c.grid.tobs, b, ud, nw);
+}
+template <typename T>
+__device__ __forceinline__ double mdn_logq(const SweepArgs& a, const MixRow<T>& m, int b, const double* th) {
+  double ud[kMixDim];
+  to_unit(a.d, a.c.grid.tobs, b, th, ud);
+  T u[kMixDim];
+#pragma unroll
+  for (int c = 0; c < kMixDim; ++c) u[c] = (T)ud[c];
+  return (double)mix_logq<T>(m, u, (T)a.mdn_eps);
+}
+
 // Lanes compute Philox blocks c0 = base + m (m < nblk) into words[4m .. 4m+3].
 __device__ __forceinline__ void fill_words(uint32_t* words, int nblk, uint32_t base, uint32_t c1, uint32_t c2,
                                            uint32_t c3, uint32_t k0, uint32_t k1, int lane) {
@@ -245,6 +315,10 @@ template <typename T>
 __device__ __forceinline__ typename CT<T>::C* hsum_ptr(const SweepArgs& a, int t, int w, int b) {
   return reinterpret_cast<typename CT<T>::C*>(a.hsum) +
          (int64_t)a.setid[((int64_t)t * a.d.n_walkers + w) * a.d.n_bands + b] * 2 * 3 * a.d.band_bins;
+}
+template <typename T>
+__device__ __forceinline__ const MixRow<T>* mix_ptr(const SweepArgs& a, int w, int j) {
+  return a.mix ? reinterpret_cast<const MixRow<T>*>(a.mix) + ((int64_t)w * a.n_bp_max + j) : nullptr;
 }
 template <typename T>
 __device__ __forceinline__ typename CT<T>::C* rho_ptr(const SweepArgs& a, int w, int j) {
@@ -465,6 +539,69 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_open(const SweepArgs a) {
   }
 }
 
+// -------------------------------------------------------------- learned-proposal inputs
+// Whitened residual of band b's own sub-band from its opened window:
+// x[ch 512 + 2 i + {0, 1}] = (Re, Im) rho[ch][N + i] sqrt(4 df / S_n), rounded to BF16.
+// Row (w, j) of the parity's bands goes to x + (w * w_stride + j * j_stride + j_off) * 4N
+// (j_off, j_stride = 0, 1 for the sweep's compact rows; parity, 2 for [W][n_bands] rows).
+template <typename T, int N>
+__global__ void __launch_bounds__(kSwWarps * 32) k_features(const SweepArgs a, uint16_t* __restrict__ x,
+                                                            int64_t w_stride, int j_stride, int j_off) {
+  typedef typename CT<T>::C C;
+  constexpr int W3 = 3 * N;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const gbk_sweep_desc& d = a.d;
+  const int nbp = (d.n_bands - a.parity + 1) / 2;
+  const int64_t ntask = (int64_t)d.n_walkers * nbp;
+  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; t < ntask; t += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+    const int w = (int)(t / nbp), j = (int)(t % nbp);
+    const int b = a.parity + 2 * j;
+    const int64_t gw = d.band_k0 + (int64_t)(b - 1) * N - a.c.grid.k0;
+    const PsdWt<T> pw = walker_psd<T>(a, w);
+    const C* rho = rho_ptr<T>(a, w, j);
+    __nv_bfloat162* out = reinterpret_cast<__nv_bfloat162*>(x + (w * w_stride + (int64_t)j * j_stride + j_off) * 4 * N);
+    for (int i = lane; i < N; i += 32) {
+      const int64_t k = gw + N + i;
+      const T wt = sqrt((T)pw.cw * iqv(a.c, k, T()) * recip((T)1 + pw.aw * rhov(a.c, k, T())));
+#pragma unroll
+      for (int ch = 0; ch < 2; ++ch) {
+        const C r = rho[ch * W3 + N + i];
+        out[ch * N + i] = __floats2bfloat162_rn((float)(r.x * wt), (float)(r.y * wt));
+      }
+    }
+  }
+}
+
+// Mixture rows of the parity's bands from network outputs (raw row (w, j)) or from the
+// caller's table (raw row (w, b) of [W][n_bands]).
+template <typename T>
+__global__ void k_mixrows(const SweepArgs a, const float* __restrict__ raw, int table, MixRow<T>* __restrict__ rows) {
+  const gbk_sweep_desc& d = a.d;
+  const int nbp = (d.n_bands - a.parity + 1) / 2;
+  const int64_t n = (int64_t)d.n_walkers * nbp;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int w = (int)(t / nbp), j = (int)(t % nbp);
+    const int64_t src = table ? (int64_t)w * d.n_bands + a.parity + 2 * j : (int64_t)w * a.n_bp_max + j;
+    mix_build<T>(raw + src * kMixOut, rows[(int64_t)w * a.n_bp_max + j]);
+  }
+}
+
+// Unit-box coordinates of every cold-chain slot [W][n_bands][n_max][8] (NaN where empty).
+__global__ void k_cold_unit(const SweepArgs a, float* __restrict__ u) {
+  const gbk_sweep_desc& d = a.d;
+  const int64_t n = (int64_t)d.n_walkers * d.n_bands * d.n_max;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)((i / d.n_max) % d.n_bands);
+    double ud[8];
+    if (a.exists[i]) {
+      to_unit(d, a.c.grid.tobs, b, a.params + i * 8, ud);
+    } else {
+      for (int c = 0; c < 8; ++c) ud[c] = nan_d();
+    }
+    for (int c = 0; c < 8; ++c) u[i * 8 + c] = (float)ud[c];
+  }
+}
+
 // -------------------------------------------------------------- band task
 // Per-warp shared memory of k_band.
 template <typename T, int N>
@@ -483,7 +620,7 @@ struct BandSmem {
 // waveform generations, and its code must not crowd the instruction cache.
 template <typename T, int N>
 __device__ __noinline__ void prep_inmodel(const SweepArgs& a, const PriorK& pk, BandSmem<T, N>& S, int l, int jp,
-                                          uint32_t tid, int g, const double* P, int b) {
+                                          uint32_t tid, int g, const double* P, int b, const MixRow<T>* mrow) {
   const gbk_sweep_desc& d = a.d;
   uint32_t w[48];
 #pragma unroll 1
@@ -495,7 +632,11 @@ __device__ __noinline__ void prep_inmodel(const SweepArgs& a, const PriorK& pk, 
   double th[8], nw[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) th[c] = P[k * 8 + c];
-  propose(d, th, w, nw);
+  const bool indep = mrow && mix_u32(w[35]) < a.mdn_inmodel;   // independence move from the learned mixture
+  if (indep)
+    mdn_draw<T>(a, *mrow, b, w[36], w[37], w + 38, nw);
+  else
+    propose(d, th, w, nw);
   S.lu[l] = log_u(u53(w[33], w[34]), T());
   S.k[l] = k;
   const bool ok = in_support(d, pk, a.c.grid.tobs, b, nw);
@@ -503,14 +644,15 @@ __device__ __noinline__ void prep_inmodel(const SweepArgs& a, const PriorK& pk, 
 #pragma unroll
   for (int c = 0; c < 8; ++c) S.th[l][c] = nw[c];
   if (ok) {
-    S.lpn[l] = dlog_prior(nw, th, T());
+    // unit coordinates: prior density 1, so q(theta) / q(theta') is the whole Hastings factor
+    S.lpn[l] = indep ? mdn_logq<T>(a, *mrow, b, th) - mdn_logq<T>(a, *mrow, b, nw) : dlog_prior(nw, th, T());
     S.src[l] = make_src<T>(nw, 1, 0, a.c.grid.tobs, N);
   }
 }
 
 template <typename T, int N>
-__device__ __noinline__ void prep_rj(const SweepArgs& a, BandSmem<T, N>& S, int l, int jp, uint32_t tid,
-                                     const uint8_t* E, int b) {
+__device__ __noinline__ void prep_rj(const SweepArgs& a, const PriorK& pk, BandSmem<T, N>& S, int l, int jp,
+                                     uint32_t tid, const uint8_t* E, const double* P, int b, const MixRow<T>* mrow) {
   const int s = S.list[jp];
   uint32_t wv[16];
 #pragma unroll 1
@@ -520,12 +662,22 @@ __device__ __noinline__ void prep_rj(const SweepArgs& a, BandSmem<T, N>& S, int 
   }
   S.lu[l] = log_u(u53(wv[8], wv[9]), T());
   S.k[l] = s;
+  S.supp[l] = 1;
+  S.lpn[l] = 0.0;
   if (!E[s]) {
     double nw[8];
-    draw_birth(a.d, a.c.grid.tobs, b, wv, nw);
+    if (mrow) {
+      mdn_draw<T>(a, *mrow, b, wv[10], wv[11], wv, nw);
+      S.supp[l] = in_support(a.d, pk, a.c.grid.tobs, b, nw) ? 1 : 0;
+      if (S.supp[l]) S.lpn[l] = -mdn_logq<T>(a, *mrow, b, nw);
+    } else {
+      draw_birth(a.d, a.c.grid.tobs, b, wv, nw);
+    }
 #pragma unroll
     for (int c = 0; c < 8; ++c) S.th[l][c] = nw[c];
-    S.src[l] = make_src<T>(nw, 1, 0, a.c.grid.tobs, N);
+    if (S.supp[l]) S.src[l] = make_src<T>(nw, 1, 0, a.c.grid.tobs, N);
+  } else if (mrow) {
+    S.lpn[l] = mdn_logq<T>(a, *mrow, b, P + s * 8);
   }
 }
 
@@ -562,6 +714,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
     const uint32_t tid = (uint32_t)(((int64_t)t * d.n_walkers + w) * d.n_bands + b);
     const PsdWt<T> pw = walker_psd<T>(a, w);
     const bool cold = (t == 0);
+    const MixRow<T>* mrow = mix_ptr<T>(a, w, j);
     long long* Rw = a.resid + (int64_t)w * 2 * nb * 2;
     // r' for the band: cold chain from the snapshot; hotter chains from the opened window
     // minus their own (cached) templates
@@ -592,7 +745,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
       const int n_prop = (int)rint(d.props_per_source * (double)g);
       for (int j0 = 0; j0 < n_prop; j0 += 32) {
         const int cnt = min(32, n_prop - j0);
-        if (lane < cnt) prep_inmodel<T, N>(a, pk, S, lane, j0 + lane, tid, g, P, b);
+        if (lane < cnt) prep_inmodel<T, N>(a, pk, S, lane, j0 + lane, tid, g, P, b, mrow);
         __syncwarp();
         for (int q = 0; q < cnt; ++q) {
           const int jp = j0 + q;
@@ -616,7 +769,8 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
             if (lane < 8) P[k * 8 + lane] = S.th[q][lane];
             __syncwarp();
             // later proposals of this batch that move the same source start from the new state
-            if (lane > q && lane < cnt && S.k[lane] == k) prep_inmodel<T, N>(a, pk, S, lane, j0 + lane, tid, g, P, b);
+            if (lane > q && lane < cnt && S.k[lane] == k)
+              prep_inmodel<T, N>(a, pk, S, lane, j0 + lane, tid, g, P, b, mrow);
           }
           __syncwarp();
         }
@@ -642,7 +796,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
       for (int j0 = 0; j0 < d.n_max; j0 += 32) {
         const int cnt = min(32, d.n_max - j0);
         // lane-parallel set-up: uniform for the decision and, for empty slots, the prior draw
-        if (lane < cnt) prep_rj<T, N>(a, S, lane, j0 + lane, tid, E, b);
+        if (lane < cnt) prep_rj<T, N>(a, pk, S, lane, j0 + lane, tid, E, P, b, mrow);
         __syncwarp();
         for (int q = 0; q < cnt; ++q) {
           const int jp = j0 + q;
@@ -651,7 +805,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
             const C* hr = cache_ptr<T>(a, cb + s);
             const int orr = cached_off<N>(P + s * 8, gw, a.c);
             const double dll = window_dll<T, N>(a, S.rw, (const C*)nullptr, 0, hr, orr, gw, pw, lane);
-            const double la = beta * dll - d.log_occ_odds;
+            const double la = beta * dll - d.log_occ_odds + S.lpn[q];
             const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
             if (lane == 0) record(a, ws, 2, t, w, b, s, jp, acc, dll, la, P + s * 8, 0, 1);
             if (acc) {
@@ -659,11 +813,13 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
               __syncwarp();
               if (lane == 0) E[s] = 0;
             }
+          } else if (!S.supp[q]) {   // learned-proposal draw on the box edge outside the support
+            if (lane == 0) record(a, ws, 1, t, w, b, s, jp, false, nan_d(), -INFINITY, S.th[q], 0, 0);
           } else {
             gen_band<T, N>(&S.src[q], orb, tw, tobs, S.ba, S.bs, lane);
             const int oa = band_off<N>(S.src[q].q, gw, a.c);
             const double dll = window_dll<T, N>(a, S.rw, S.ba, oa, (const C*)nullptr, 0, gw, pw, lane);
-            const double la = beta * dll + d.log_occ_odds;
+            const double la = beta * dll + d.log_occ_odds + S.lpn[q];
             const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
             if (lane == 0) record(a, ws, 1, t, w, b, s, jp, acc, dll, la, S.th[q], 1, 1);
             if (acc) {
@@ -887,6 +1043,32 @@ static gbk_status run_refresh(SweepArgs& a, cudaStream_t st) {
   return check_launch("gb_sweep(refresh)");
 }
 
+static gbk_sweep* g_active_plan = nullptr;   // plan of the gb_sweep call in progress
+
+// Learned proposal of one half sweep: features of the opened windows -> network ->
+// mixture rows (or mixture rows straight from the caller's table).
+template <typename T, int N>
+static gbk_status run_proposal(gbk_sweep* plan, SweepArgs& a, cudaStream_t st) {
+  const int nbp = (a.d.n_bands - a.parity + 1) / 2;
+  const int rows = a.d.n_walkers * nbp;
+  gbk_status s;
+  const float* raw = plan->raw_table;
+  if (!raw) {
+    if (N != 256) return set_error(GBK_ENOTIMPL, "gb_sweep: the network takes 256-bin bands");
+    int grid = 0, thr = 0;
+    size_t sm = 0;
+    if ((s = prep(k_features<T, N>, 0, rows, &grid, &thr, &sm))) return s;
+    k_features<T, N><<<grid, kSwWarps * 32, 0, st>>>(a, plan->xfeat, plan->n_bp_max, 1, 0);
+    if ((s = check_launch("gb_sweep(features)"))) return s;
+    // rows (w, j) are compact per walker: run the network on the full [W][n_bp_max] block
+    if ((s = mdn_forward(plan->net, plan->xfeat, a.d.n_walkers * plan->n_bp_max, plan->rawbuf, st))) return s;
+    raw = plan->rawbuf;
+  }
+  k_mixrows<T><<<(rows + 127) / 128, 128, 0, st>>>(a, raw, plan->raw_table ? 1 : 0,
+                                                   reinterpret_cast<MixRow<T>*>(plan->mix));
+  return check_launch("gb_sweep(mixture rows)");
+}
+
 template <typename T, int N>
 static gbk_status run_half(SweepArgs& a, int flags, cudaStream_t st) {
   const gbk_sweep_desc& d = a.d;
@@ -898,8 +1080,9 @@ static gbk_status run_half(SweepArgs& a, int flags, cudaStream_t st) {
   if ((s = prep(k_open<T, N>, 0, (int64_t)d.n_walkers * nbp, &grid, &thr, &sm))) return s;
   ev_rec(a.parity, 1, 0, st);
   k_open<T, N><<<grid, kSwWarps * 32, 0, st>>>(a);
-  ev_rec(a.parity, 1, 1, st);
   if ((s = check_launch("gb_sweep(open)"))) return s;
+  if (a.mix && (s = run_proposal<T, N>(g_active_plan, a, st))) return s;
+  ev_rec(a.parity, 1, 1, st);
   if (flags & (GBK_SWEEP_INMODEL | GBK_SWEEP_RJ)) {
     if ((s = prep(k_band<T, N>, sizeof(BandSmem<T, N>), (int64_t)d.n_temps * d.n_walkers * nbp, &grid, &thr, &sm)))
       return s;
@@ -1004,6 +1187,9 @@ extern "C" gbk_status gbk_sweep_destroy(gbk_sweep* plan) {
   cudaFree(plan->wcache);
   cudaFree(plan->hsum);
   cudaFree(plan->setid);
+  cudaFree(plan->mix);
+  cudaFree(plan->xfeat);
+  cudaFree(plan->rawbuf);
   if (plan->have_ev)
     for (int p = 0; p < 2; ++p)
       for (int k = 0; k < 4; ++k)
@@ -1029,17 +1215,18 @@ extern "C" gbk_status gbk_sweep_kernel_ms(gbk_sweep* plan, double* ms_out) {
   return GBK_OK;
 }
 
-extern "C" gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists, const double* betas,
-                               const gbk_residual* residual, const gbk_psd* psd, uint64_t key, uint32_t sweep_index,
-                               int32_t flags, const gbk_trace* trace, int64_t* stats, void* stream) {
-  if (!plan || !residual || !psd) return set_error(GBK_EINVAL, "gb_sweep: null plan/struct");
-  if (!params || !exists || !betas || !residual->data || !psd->params)
-    return set_error(GBK_EINVAL, "gb_sweep: null device pointer");
+static gbk_status check_state(gbk_sweep* plan, const double* params, const uint8_t* exists,
+                              const gbk_residual* residual, const gbk_psd* psd, const char* what) {
+  if (!plan || !residual || !psd) return set_error(GBK_EINVAL, "%s: null plan/struct", what);
+  if (!params || !exists || !residual->data || !psd->params) return set_error(GBK_EINVAL, "%s: null device pointer", what);
   if (residual->n_walkers != plan->d.n_walkers || residual->frac_bits < 40 || residual->frac_bits > 120)
-    return set_error(GBK_EINVAL, "gb_sweep: residual must hold n_walkers = %d walkers", plan->d.n_walkers);
-  if (psd->n_psd != 1 && psd->n_psd < plan->d.n_walkers) return set_error(GBK_EINVAL, "gb_sweep: psd covers too few walkers");
-  if (flags & ~(GBK_SWEEP_INMODEL | GBK_SWEEP_RJ | GBK_SWEEP_SWAP | GBK_SWEEP_REFRESH | GBK_SWEEP_TIMING))
-    return set_error(GBK_EINVAL, "gb_sweep: unknown flags 0x%x", flags);
+    return set_error(GBK_EINVAL, "%s: residual must hold n_walkers = %d walkers", what, plan->d.n_walkers);
+  if (psd->n_psd != 1 && psd->n_psd < plan->d.n_walkers) return set_error(GBK_EINVAL, "%s: psd covers too few walkers", what);
+  return GBK_OK;
+}
+
+static SweepArgs make_args(gbk_sweep* plan, double* params, uint8_t* exists, const double* betas,
+                           const gbk_residual* residual, const gbk_psd* psd, uint64_t key, uint32_t sweep_index) {
   SweepArgs a;
   a.c = *plan->ctx;
   a.d = plan->d;
@@ -1061,10 +1248,32 @@ extern "C" gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists,
   a.k1 = (uint32_t)(key >> 32);
   a.sweep = sweep_index;
   a.parity = 1;
+  a.trace = nullptr;
+  a.trace_cap = 0;
+  a.trace_count = nullptr;
+  a.stats = nullptr;
+  a.mix = nullptr;
+  a.mdn_eps = plan->mdn_eps;
+  a.mdn_inmodel = plan->mdn_inmodel;
+  return a;
+}
+
+extern "C" gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists, const double* betas,
+                               const gbk_residual* residual, const gbk_psd* psd, uint64_t key, uint32_t sweep_index,
+                               int32_t flags, const gbk_trace* trace, int64_t* stats, void* stream) {
+  gbk_status s0 = check_state(plan, params, exists, residual, psd, "gb_sweep");
+  if (s0) return s0;
+  if (!betas) return set_error(GBK_EINVAL, "gb_sweep: null betas");
+  if (flags & ~(GBK_SWEEP_INMODEL | GBK_SWEEP_RJ | GBK_SWEEP_SWAP | GBK_SWEEP_REFRESH | GBK_SWEEP_TIMING | GBK_SWEEP_MDN))
+    return set_error(GBK_EINVAL, "gb_sweep: unknown flags 0x%x", flags);
+  if ((flags & GBK_SWEEP_MDN) && !plan->mdn_set)
+    return set_error(GBK_EINVAL, "gb_sweep: GBK_SWEEP_MDN without a proposal (gbk_sweep_set_proposal)");
+  SweepArgs a = make_args(plan, params, exists, betas, residual, psd, key, sweep_index);
   a.trace = trace ? trace->records : nullptr;
   a.trace_cap = trace ? trace->capacity : 0;
   a.trace_count = trace ? trace->count : nullptr;
   a.stats = (long long*)stats;
+  a.mix = (flags & GBK_SWEEP_MDN) ? plan->mix : nullptr;
   cudaStream_t st = (cudaStream_t)stream;
   plan->timed = (flags & GBK_SWEEP_TIMING) != 0;
   if (plan->timed && !plan->have_ev) {
@@ -1081,8 +1290,90 @@ extern "C" gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists,
       }
   }
   g_timing_plan = plan;
-  gbk_status s = (plan->d.precision == GBK_MIXED) ? run_sweep<float>(plan, a, flags & ~GBK_SWEEP_TIMING, st)
-                                                  : run_sweep<double>(plan, a, flags & ~GBK_SWEEP_TIMING, st);
+  g_active_plan = plan;
+  const int fl = flags & ~(GBK_SWEEP_TIMING | GBK_SWEEP_MDN);
+  gbk_status s = (plan->d.precision == GBK_MIXED) ? run_sweep<float>(plan, a, fl, st) : run_sweep<double>(plan, a, fl, st);
   g_timing_plan = nullptr;
+  g_active_plan = nullptr;
   return s;
+}
+
+extern "C" gbk_status gbk_sweep_set_proposal(gbk_sweep* plan, gbk_mdn* net, const float* raw_table, double eps,
+                                             double inmodel_frac) {
+  if (!plan) return set_error(GBK_EINVAL, "gbk_sweep_set_proposal: null plan");
+  if (!(eps >= 0.0 && eps <= 1.0) || !(inmodel_frac >= 0.0 && inmodel_frac <= 1.0))
+    return set_error(GBK_EINVAL, "gbk_sweep_set_proposal: eps and inmodel_frac must lie in [0, 1]");
+  plan->mdn_set = false;
+  plan->net = nullptr;
+  plan->raw_table = nullptr;
+  if (!net && !raw_table) return GBK_OK;   // learned proposal off
+  const int64_t rows = (int64_t)plan->d.n_walkers * plan->n_bp_max;
+  if (!raw_table) {
+    if (plan->d.band_bins != 256)
+      return set_error(GBK_ENOTIMPL, "gbk_sweep_set_proposal: the network takes 256-bin bands (band_bins %d)",
+                       plan->d.band_bins);
+    if (net->max_batch < rows)
+      return set_error(GBK_EINVAL, "gbk_sweep_set_proposal: network max_batch %d < %lld windows per half sweep",
+                       net->max_batch, (long long)rows);
+    if (!net->have_params) return set_error(GBK_EINVAL, "gbk_sweep_set_proposal: network parameters not set");
+  }
+  const size_t mixb = (size_t)rows * (plan->d.precision == GBK_FP64 ? sizeof(MixRow<double>) : sizeof(MixRow<float>));
+  cudaError_t e = cudaSuccess;
+  if (!plan->mix) e = cudaMalloc(&plan->mix, mixb);
+  if (e == cudaSuccess && !raw_table && !plan->xfeat) {
+    e = cudaMalloc((void**)&plan->xfeat, (size_t)rows * 1024 * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMemset(plan->xfeat, 0, (size_t)rows * 1024 * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&plan->rawbuf, (size_t)rows * kMixOut * sizeof(float));
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(GBK_ENOMEM, "gbk_sweep_set_proposal: %s", cudaGetErrorString(e));
+  }
+  plan->net = raw_table ? nullptr : net;
+  plan->raw_table = raw_table;
+  plan->mdn_eps = eps;
+  plan->mdn_inmodel = inmodel_frac;
+  plan->mdn_set = true;
+  return GBK_OK;
+}
+
+template <typename T>
+static gbk_status features_impl(gbk_sweep* plan, SweepArgs& a, uint16_t* x_out, float* u_out, cudaStream_t st) {
+  gbk_status s;
+  int grid = 0, thr = 0;
+  size_t sm = 0;
+  a.rsnap = a.resid;   // nothing changes the residual during this call
+  for (int parity = 1; parity >= 0; --parity) {
+    a.parity = parity;
+    const int nbp = (a.d.n_bands - parity + 1) / 2;
+    if (nbp <= 0) continue;
+    if ((s = prep(k_open<T, 256>, 0, (int64_t)a.d.n_walkers * nbp, &grid, &thr, &sm))) return s;
+    k_open<T, 256><<<grid, kSwWarps * 32, 0, st>>>(a);
+    if ((s = check_launch("gb_sweep_features(open)"))) return s;
+    if (x_out) {
+      k_features<T, 256><<<grid, kSwWarps * 32, 0, st>>>(a, x_out, a.d.n_bands, 2, parity);
+      if ((s = check_launch("gb_sweep_features(features)"))) return s;
+    }
+  }
+  if (u_out && a.d.n_max > 0) {
+    const int64_t n = (int64_t)a.d.n_walkers * a.d.n_bands * a.d.n_max;
+    k_cold_unit<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(a, u_out);
+    if ((s = check_launch("gb_sweep_features(unit)"))) return s;
+  }
+  return GBK_OK;
+}
+
+extern "C" gbk_status gb_sweep_features(gbk_sweep* plan, const double* params, const uint8_t* exists,
+                                        const gbk_residual* residual, const gbk_psd* psd, uint16_t* x_out,
+                                        float* u_out, void* stream) {
+  gbk_status s = check_state(plan, params, exists, residual, psd, "gb_sweep_features");
+  if (s) return s;
+  if (plan->d.band_bins != 256)
+    return set_error(GBK_ENOTIMPL, "gb_sweep_features: features are defined for 256-bin bands (band_bins %d)",
+                     plan->d.band_bins);
+  if (x_out && ((uintptr_t)x_out & 3)) return set_error(GBK_EINVAL, "gb_sweep_features: x_out must be 4-byte aligned");
+  SweepArgs a = make_args(plan, const_cast<double*>(params), const_cast<uint8_t*>(exists), nullptr, residual, psd, 0, 0);
+  cudaStream_t st = (cudaStream_t)stream;
+  return plan->d.precision == GBK_MIXED ? features_impl<float>(plan, a, x_out, u_out, st)
+                                        : features_impl<double>(plan, a, x_out, u_out, st);
 }

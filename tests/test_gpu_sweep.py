@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 ALL = 1 | 2 | 4
 
 
-def _gpu_sweep(torch, cfg, state, precision, sweeps=1, flags=ALL, trace_cap=20000):
+def _gpu_sweep(torch, cfg, state, precision, sweeps=1, flags=ALL, trace_cap=20000, proposal=None):
     from paper_2405_04690_gb300 import _lib as L
     dev = torch.device("cuda")
     ctx = L.Context(cfg.tobs, 15.0, cfg.k0, cfg.n_bins)
@@ -36,6 +36,9 @@ def _gpu_sweep(torch, cfg, state, precision, sweeps=1, flags=ALL, trace_cap=2000
     rec = torch.zeros(trace_cap * ctypes.sizeof(L.GbkTraceRec), dtype=torch.uint8, device=dev)
     cnt = torch.zeros(1, dtype=torch.int32, device=dev)
     stats = torch.zeros((5, 2), dtype=torch.int64, device=dev)
+    if proposal is not None:
+        L.gbk_sweep_set_proposal(plan, **proposal)
+        flags |= L.SWEEP_MDN
     for k in range(sweeps):
         L.gb_sweep(plan, P, E, betas, L.residual_struct(R, FRAC), L.psd_struct(psdp), key64(cfg), k,
                    flags | (L.SWEEP_REFRESH if k == 0 else 0), trace=(rec, trace_cap, cnt), stats=stats)
@@ -209,3 +212,112 @@ def test_sweep_prior_only_reproduces_the_prior():
     assert sst.kstest(np.asarray(f_rel[::7]), "uniform").pvalue > 1e-3
     plan.close()
     ctx.close()
+
+
+def _near_truth_table(cfg, state, g):
+    """Mixture tables [W][n_bands][272] whose components sit near the sources of the
+    initial state (so learned-proposal births and independence moves are accepted
+    sometimes) with broad components mixed in."""
+    from oracle import mdn as MD
+    from test_oracle_mdn import raw_from
+    t = np.empty((cfg.n_walkers, cfg.n_bands, MD.N_OUT))
+    for w in range(cfg.n_walkers):
+        for b in range(cfg.n_bands):
+            us = [MD.to_unit(cfg, b, state["params"][0, w, b, s]) for s in range(cfg.n_max) if state["exists"][0, w, b, s]]
+            pi = g.dirichlet(np.ones(MD.N_COMP))
+            mu = g.uniform(0.1, 0.9, (MD.N_COMP, MD.N_DIM))
+            sd = np.full((MD.N_COMP, MD.N_DIM), 0.3)
+            for k, u in enumerate(us[:MD.N_COMP // 2]):
+                mu[k] = np.clip(u, 0.02, 0.98)
+                sd[k] = [0.002, 1e-4, 0.02, 0.01, 0.01, 0.01, 0.002, 0.002]
+            t[w, b] = raw_from(pi, mu, sd)
+    return t.astype(np.float32).astype(np.float64)
+
+
+def test_sweep_fp64_with_learned_proposal_matches_oracle():
+    # The same fixed mixture table on both sides: births from the defensive mixture,
+    # deaths and a third of the in-model moves with its density; every decision equal.
+    torch = torch_cuda()
+    cfg, state, _, _ = small_ensemble(seed=13)
+    table = _near_truth_table(cfg, state, np.random.default_rng(14))
+    cfg.mdn_raw, cfg.mdn_eps, cfg.mdn_inmodel = table, 0.2, 0.35
+    ora = copy_state(state)
+    trace = OM.sweep(cfg, ora, 0)
+    prop = dict(raw_table=torch.from_numpy(table.astype(np.float32)).cuda(), eps=0.2, inmodel_frac=0.35)
+    out, gtr, stats = _gpu_sweep(torch, cfg, state, "fp64", proposal=prop)
+    g, o = _index(gtr, trace)
+    assert set(g) == set(o), (len(g), len(o))
+    worst = 0.0
+    for k, ro in o.items():
+        rg = g[k]
+        assert bool(rg["accepted"]) == ro["accepted"], (k, rg["log_alpha"], ro["log_alpha"], ro["lu"])
+        if ro["kind"] != 3:
+            np.testing.assert_allclose(rg["params"], ro["params"], rtol=1e-12, atol=0)
+            if np.isfinite(ro["log_alpha"]):
+                assert abs(rg["log_alpha"] - ro["log_alpha"]) < 1e-6 * (1 + abs(ro["log_alpha"]))
+        if np.isfinite(ro["dlogl"]):
+            worst = max(worst, abs(rg["dlogl"] - ro["dlogl"]))
+    assert worst < 1e-7, worst
+    assert np.array_equal(out["exists"], ora["exists"])
+    # the learned proposal was exercised: accepted births and accepted independence moves
+    births = [r for r in trace if r["kind"] == 1 and r["accepted"]]
+    assert len(births) > 0 and stats[1, 1] == len(births)
+
+
+def test_sweep_with_network_equals_sweep_with_its_table():
+    # One band (a single half sweep, opened from the initial state): the network run
+    # inside gb_sweep on the opened windows gives the same trace, bit for bit, as the
+    # table made by mdn_forward on gb_sweep_features of the same state.
+    torch = torch_cuda()
+    from oracle import mdn as MD
+    from paper_2405_04690_gb300 import _lib as L
+    cfg, state, _, _ = small_ensemble(seed=15, n_bands=1, n_temps=2, n_walkers=3, n_max=6, betas=(1.0, 0.5))
+    dev = torch.device("cuda")
+    theta = MD.init_params(np.random.default_rng(16), scale=1.0).astype(np.float32)
+    net = L.Mdn(64)
+    L.mdn_set_params(net, torch.from_numpy(theta).to(dev))
+    # features of the initial state (after a refresh-only sweep that runs no moves)
+    ctx = L.Context(cfg.tobs, 15.0, cfg.k0, cfg.n_bins)
+    plan = L.SweepPlan(ctx, cfg.n_temps, cfg.n_walkers, cfg.n_bands, cfg.n_max, NB, cfg.band_k0, cfg.sigma,
+                       L.GBK_MIXED, f_min=cfg.f_min, f_max=cfg.f_max)
+    P = torch.from_numpy(state["params"].copy()).to(dev)
+    E = torch.from_numpy(state["exists"].astype(np.uint8)).to(dev)
+    R = torch.from_numpy(state["resid"].copy()).to(dev)
+    betas = torch.from_numpy(np.ascontiguousarray(cfg.betas)).to(dev)
+    psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
+    L.gb_sweep(plan, P, E, betas, L.residual_struct(R, FRAC), L.psd_struct(psdp), 1, 0, L.SWEEP_REFRESH)
+    x = torch.zeros((cfg.n_walkers, cfg.n_bands, 1024), dtype=torch.bfloat16, device=dev)
+    u = torch.zeros((cfg.n_walkers, cfg.n_bands, cfg.n_max, 8), dtype=torch.float32, device=dev)
+    L.gb_sweep_features(plan, P, E, L.residual_struct(R, FRAC), L.psd_struct(psdp), x, u)
+    raw = torch.zeros((cfg.n_walkers * cfg.n_bands, MD.N_OUT), dtype=torch.float32, device=dev)
+    L.mdn_forward(net, x.reshape(-1, 1024), raw)
+    torch.cuda.synchronize()
+    # features against the oracle's opened window (float32 window, BF16 rounding: 1 ulp)
+    xo = np.empty((cfg.n_walkers, 1024))
+    for w in range(cfg.n_walkers):
+        rho = OM.open_band(cfg, state, state["resid"], w, 0)
+        off, n = cfg.window(0)
+        xo[w] = MD.features(rho, cfg.psd[w][off:off + n], cfg.df)
+    xg = x.float().cpu().numpy()[:, 0, :].astype(np.float64)
+    assert np.all(np.abs(xg - xo) <= 2 ** -7 * np.abs(xo) + 1e-3), np.max(np.abs(xg - xo))
+    ug = u.cpu().numpy()
+    for w in range(cfg.n_walkers):
+        for s in range(cfg.n_max):
+            if state["exists"][0, w, 0, s]:
+                np.testing.assert_allclose(ug[w, 0, s], MD.to_unit(cfg, 0, state["params"][0, w, 0, s]), atol=1e-6)
+            else:
+                assert np.all(np.isnan(ug[w, 0, s]))
+    plan.close()
+    ctx.close()
+    table = raw.reshape(cfg.n_walkers, cfg.n_bands, MD.N_OUT).contiguous()
+    _, t1, s1 = _gpu_sweep(torch, cfg, state, "mixed", proposal=dict(net=net, eps=0.3, inmodel_frac=0.5))
+    _, t2, s2 = _gpu_sweep(torch, cfg, state, "mixed", proposal=dict(raw_table=table, eps=0.3, inmodel_frac=0.5))
+    assert len(t1) == len(t2) and len(t1) > 0
+
+    def ordered(t):   # records in a fixed order, compared as bytes (NaN-safe, bitwise)
+        idx = sorted(range(len(t)), key=lambda i: tuple(int(t[i][f]) for f in ("parity", "kind", "t", "w", "b", "seq",
+                                                                                  "slot")))
+        return t[idx].tobytes()
+    assert ordered(t1) == ordered(t2)
+    assert np.array_equal(s1, s2)
+    net.close()

@@ -181,3 +181,32 @@ def test_defensive_density_integrates_to_one_and_reduces_to_prior():
     assert MD.log_q_defensive(raw, x, 1.0) == 0.0
     q = math.exp(MD.log_q(raw[None, :], x[None, :])[0])
     assert abs(math.exp(MD.log_q_defensive(raw, x, 0.25)) - (0.25 + 0.75 * q)) < 1e-12 * (1 + q)
+
+
+def test_to_bf16_matches_torch_rounding():
+    # round to nearest, ties to even, including exact ties and values near overflow
+    torch = __import__("pytest").importorskip("torch")
+    g = np.random.default_rng(14)
+    x = np.concatenate([g.normal(0, 1, 20000), g.normal(0, 1e-30, 1000), g.normal(0, 1e30, 1000)])
+    ties = (np.arange(1, 2000, dtype=np.uint32) << 16 | 0x8000).view(np.float32).astype(np.float64)
+    x = np.concatenate([x, ties, -ties])
+    want = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(MD.to_bf16(x), want)
+
+
+def test_quantized_network_is_the_rounded_one():
+    # quantized forward = plain forward of bf16-rounded weights when the hidden
+    # activations happen to be representable; in general it stays within the bf16
+    # error bound of the plain network
+    g = np.random.default_rng(15)
+    theta = MD.init_params(g)
+    x = MD.to_bf16(g.normal(0, 1, (64, MD.N_IN)))
+    rq, aq = MD.forward(theta, x, quantized=True)
+    for a in aq[1:-1]:
+        assert np.array_equal(a, MD.to_bf16(a))
+    r0, _ = MD.forward(theta, x)
+    assert np.linalg.norm(rq - r0) / np.linalg.norm(r0) < 2e-2
+    # layer by layer: the first hidden layer is relu(x bf16(W1)^T + b1), rounded
+    layers = MD.unpack(theta)
+    h1 = MD.to_bf16(np.maximum(x @ MD.to_bf16(layers[0][0]).T + layers[0][1], 0))
+    assert np.array_equal(aq[1], h1)
