@@ -331,6 +331,176 @@ def run_uneven(torch, L, dev, stream, seed, n_prop=200000, reps=10):
             "proposals_per_s": n_prop / (ms * 1e-3), "ms_per_batch": ms, "per_N": per_n}
 
 
+def run_ess(torch, L, S, step, stats, stream, n_sweeps, flags=0, pairs=None):
+    """ESS/s: integrated autocorrelation time of every cold walker's total log-likelihood
+    (Eq. like on its residual) over n_sweeps sweeps (first quarter discarded). Optionally
+    collects training pairs of the learned proposal after the burn-in (outside the timing)."""
+    nb = S["resid"].shape[2]
+    nw = S["resid"].shape[0]
+    lnl = torch.empty(nw, dtype=torch.float64, device=S["P"].device)
+    rf = torch.empty((nw, 2, nb, 2), dtype=torch.float32, device=S["P"].device)
+    series = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_sweeps = 0.0
+    stats.zero_()
+    for k in range(n_sweeps):
+        e0.record(stream)
+        step(flags)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_sweeps += e0.elapsed_time(e1) * 1e-3
+        rf.copy_((S["resid"].to(torch.float64) * 2.0 ** -FRAC_BITS).to(torch.float32))
+        L.total_loglike(S["ctx"], rf, S["psdp"].expand(nw, 2).contiguous(), lnl, stream)
+        series.append(lnl.cpu().numpy().copy())
+        if pairs is not None and k >= n_sweeps // 4 and pairs.n < pairs.capacity:
+            pairs.add_from_sweep(S["plan"], S["P"], S["E"], S["R"], S["psd"])
+    st = stats.cpu().numpy()
+    x = np.array(series).T[:, n_sweeps // 4:]
+    tau = autocorr_time(x)
+    n_eff = x.shape[0] * x.shape[1] / max(tau, 1.0)
+    return {"ess_per_s": n_eff / (t_sweeps * x.shape[1] / n_sweeps), "tau_sweeps": tau, "sweeps": n_sweeps,
+            "burn_in": n_sweeps // 4, "ms_per_sweep": 1e3 * t_sweeps / n_sweeps,
+            "proposals_per_s": float(st[:4, 0].sum()) / t_sweeps,
+            "acceptance": {k: float(st[i, 1]) / max(1.0, float(st[i, 0])) for i, k in
+                           enumerate(["in_model", "birth", "death", "swap"])},
+            "scalar": "cold-chain total lnL of each of the %d walkers (Eq. like on its residual)" % nw}
+
+
+def recovered_sources(truth, P, E, tobs, n_bands, band_k0, walkers=4):
+    """Injected sources matched by a cold-chain source of the same walker (|df0| < 1 bin,
+    |d ln A| < 0.3), summed over the first `walkers` walkers."""
+    f_t = truth[1] * tobs
+    la_t = np.log(truth[0])
+    bt = ((np.floor(f_t).astype(np.int64) - band_k0) // N_BAND)
+    n = 0
+    for w in range(min(walkers, P.shape[1])):
+        for b in range(n_bands):
+            sel = np.nonzero(bt == b)[0]
+            if len(sel) == 0:
+                continue
+            cand = []
+            for bb in (b - 1, b, b + 1):
+                if 0 <= bb < n_bands:
+                    m = E[0, w, bb].astype(bool)
+                    cand.append(P[0, w, bb][m])
+            c = np.concatenate(cand) if cand else np.zeros((0, 8))
+            if len(c) == 0:
+                continue
+            df = np.abs(c[None, :, 1] * tobs - f_t[sel, None])
+            da = np.abs(np.log(np.maximum(c[None, :, 0], 1e-30)) - la_t[sel, None])
+            n += int(np.sum(np.any((df < 1.0) & (da < 0.3), axis=1)))
+    return n
+
+
+def run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, snap, ess_plain):
+    """The learned proposal on the ensemble: training throughput on the cold-chain pairs
+    (BF16 tensor cores), then the same ESS run with the proposal, then a search from an
+    empty model with and without it."""
+    from paper_2405_04690_gb300 import proposal as PR
+    dev = S["P"].device
+    n = pairs.n
+    n_val = max(4096, n // 20)
+    n_tr = n - n_val
+    batch = 4096
+    train = PR.PairBuffer(1)
+    train.x, train.u, train.n = pairs.x[:n_tr], pairs.u[:n_tr], n_tr
+    val = PR.PairBuffer(1)
+    val.x, val.u, val.n = pairs.x[n_tr:n], pairs.u[n_tr:n], n_val
+    net = L.Mdn(max(batch, N_W * ((ens["n_bands"] + 1) // 2)))
+    tr = PR.Trainer(net, torch.from_numpy(PR.init_params(11)).to(dev), lr=1e-3)
+    v0 = tr.mean_loss(val)
+    tr.epoch(train, batch, seed=0, max_steps=5)          # warm-up (also first steps of training)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps0 = tr.step
+    e0.record(stream)
+    for ep in range(args.mdn_epochs):
+        tr.epoch(train, batch, seed=1 + ep)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_train = e0.elapsed_time(e1) * 1e-3
+    samples = (tr.step - steps0) * batch
+    v1 = tr.mean_loss(val)
+    # inference throughput on batch-sized blocks
+    raw = torch.empty((batch, PR.N_OUT), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        L.mdn_forward(net, train.x[:batch], raw)
+    e0.record(stream)
+    reps = 50
+    for r in range(reps):
+        L.mdn_forward(net, train.x[(r % 8) * batch:(r % 8 + 1) * batch], raw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_inf = e0.elapsed_time(e1) * 1e-3
+    peak = None
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        peak = 1900.0
+    tflops = samples * PR.FLOPS_TRAIN / t_train / 1e12
+    out = {"pairs": n, "train_pairs": n_tr, "val_pairs": n_val, "batch": batch, "epochs": args.mdn_epochs,
+           "train_samples_per_s": samples / t_train, "train_tflops": tflops,
+           "train_roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                              "frac": tflops / peak, "peak_kind": "measured cuBLAS bf16 burst",
+                              "flops_per_sample": PR.FLOPS_TRAIN},
+           "infer_samples_per_s": reps * batch / t_inf,
+           "infer_tflops": reps * batch * PR.FLOPS_FORWARD / t_inf / 1e12,
+           "val_nll_start": v0, "val_nll_end": v1}
+    # ESS with the learned proposal from the same starting state
+    P0, E0, R0, k0 = snap
+    S["P"].copy_(P0)
+    S["E"].copy_(E0)
+    S["resid"].copy_(R0)
+    L.gbk_sweep_set_proposal(S["plan"], net=net, eps=args.mdn_eps, inmodel_frac=args.mdn_inmodel)
+    sweep_no[0] = k0
+    L.gb_sweep(S["plan"], S["P"], S["E"], S["betas"], S["R"], S["psd"], 1, 0, L.SWEEP_REFRESH, stream=stream)
+    out["ess"] = run_ess(torch, L, S, step, stats, stream, args.ess_sweeps, flags=L.SWEEP_MDN)
+    out["ess_gain"] = out["ess"]["ess_per_s"] / ess_plain["ess_per_s"]
+    out["proposal"] = {"eps_prior": args.mdn_eps, "inmodel_frac": args.mdn_inmodel}
+    # search: every chain starts empty (residual = data); K sweeps with each proposal
+    search = {"sweeps": args.search_sweeps}
+    L.gbk_sweep_set_proposal(S["plan"])
+    S["P"].copy_(P0)
+    S["E"].copy_(E0)
+    S["resid"].copy_(R0)
+    cold = P0[0].reshape(-1, 8)[E0[0].reshape(-1).bool()]
+    wv = E0[0].reshape(N_W, -1).bool().nonzero()[:, 0].to(torch.int32)
+    L.residual_add_sub(S["ctx"], S["R"], cold.t().contiguous(), torch.full((cold.shape[0],), N_BAND,
+                       dtype=torch.int32, device=dev), N_BAND, wv, -1, L.GBK_MIXED, stream)
+    data = S["resid"].clone()                               # d (noise + injected sources) per walker
+    for mode in ("prior", "learned"):
+        S["P"].zero_()
+        S["E"].zero_()
+        S["resid"].copy_(data)
+        if mode == "learned":
+            L.gbk_sweep_set_proposal(S["plan"], net=net, eps=args.mdn_eps, inmodel_frac=args.mdn_inmodel)
+        else:
+            L.gbk_sweep_set_proposal(S["plan"])
+        fl = L.SWEEP_MDN if mode == "learned" else 0
+        stats.zero_()
+        curve = []
+        t = 0.0
+        for k in range(args.search_sweeps):
+            e0.record(stream)
+            L.gb_sweep(S["plan"], S["P"], S["E"], S["betas"], S["R"], S["psd"], 0xA11, 5000 + k,
+                       1 | 2 | 4 | fl | (L.SWEEP_REFRESH if k == 0 else 0), stats=stats, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t += e0.elapsed_time(e1) * 1e-3
+            if k in (0, 1, 2, 4, args.search_sweeps - 1):
+                curve.append([k + 1, recovered_sources(ens["truth"], S["P"].cpu().numpy(), S["E"].cpu().numpy(),
+                                                       TOBS, ens["n_bands"], ens["band_k0"])])
+        st = stats.cpu().numpy()
+        search[mode] = {"recovered_after_sweeps": curve, "seconds": t,
+                        "birth_acceptance": float(st[1, 1]) / max(1.0, float(st[1, 0]))}
+    search["injected"] = int(ens["truth"].shape[1]) * min(4, N_W)
+    search["counted"] = "cold chains of walkers 0-3: injected sources matched within 1 bin in f0 and 0.3 in ln A"
+    out["search"] = search
+    L.gbk_sweep_set_proposal(S["plan"])
+    net.close()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -479,29 +649,17 @@ def run_ours(args):
     # effective samples: integrated autocorrelation time of every cold walker's total
     # log-likelihood (Eq. like on its residual) over a run of sweeps
     ess = {}
+    learned = {}
     if args.ess_sweeps > 0:
-        nb = ens["n_bins"]
-        lnl = torch.empty(N_W, dtype=torch.float64, device=dev)
-        rf = torch.empty((N_W, 2, nb, 2), dtype=torch.float32, device=dev)
-        series = []
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t_sweeps = 0.0
-        for k in range(args.ess_sweeps):
-            e0.record(stream)
-            step()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t_sweeps += e0.elapsed_time(e1) * 1e-3
-            rf.copy_((S["resid"].to(torch.float64) * 2.0 ** -FRAC_BITS).to(torch.float32))
-            L.total_loglike(S["ctx"], rf, S["psdp"].expand(N_W, 2).contiguous(), lnl, stream)
-            series.append(lnl.cpu().numpy().copy())
-        x = np.array(series).T[:, args.ess_sweeps // 4:]
-        tau = autocorr_time(x)
-        n_eff = x.shape[0] * x.shape[1] / max(tau, 1.0)
-        ess = {"ess_per_s": n_eff / (t_sweeps * x.shape[1] / args.ess_sweeps), "tau_sweeps": tau,
-               "sweeps": args.ess_sweeps, "burn_in": args.ess_sweeps // 4,
-               "scalar": "cold-chain total lnL of each of the 32 walkers (Eq. like on its residual)"}
-        del rf
+        snap = (S["P"].clone(), S["E"].clone(), S["resid"].clone(), sweep_no[0])
+        pairs = None
+        if not args.no_learned:
+            from paper_2405_04690_gb300 import proposal as PR
+            pairs = PR.PairBuffer(args.mdn_samples)
+        ess = run_ess(torch, L, S, step, stats, stream, args.ess_sweeps, pairs=pairs)
+        if pairs is not None:
+            learned = run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, snap, ess)
+        del snap
 
     # the plain float64 path on the same GPU: (a) the same sweep in float64, one step;
     # (b) per-source launches of the float64 Delta lnL (one proposal per launch)
@@ -574,6 +732,8 @@ def run_ours(args):
         line["uneven_n"] = uneven
     if ess:
         line["ess"] = ess
+    if learned:
+        line["learned_proposal"] = learned
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -616,6 +776,12 @@ def main():
     ap.add_argument("--c3-walkers", type=int, default=512, help="walkers of the total log-likelihood measurement")
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven band-length measurement")
     ap.add_argument("--n-temps", type=int, default=N_T, help="smaller ensemble for profiling captures")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal measurements")
+    ap.add_argument("--mdn-samples", type=int, default=1000000, help="training pairs of the learned proposal")
+    ap.add_argument("--mdn-epochs", type=int, default=6)
+    ap.add_argument("--mdn-eps", type=float, default=0.2, help="prior fraction of the learned proposal")
+    ap.add_argument("--mdn-inmodel", type=float, default=0.25, help="fraction of in-model moves drawn from it")
+    ap.add_argument("--search-sweeps", type=int, default=10)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -101,30 +101,50 @@ __device__ __forceinline__ void allowance(const gbk_sweep_desc& d, double tobs, 
   if (hi > d.f_max) hi = d.f_max;
 }
 
+// f0 range [lo, hi) of band b's sources, computed once per band task.
+struct BandGeom {
+  double lo, hi, inv_span;
+};
+__device__ __forceinline__ BandGeom band_geom(const gbk_sweep_desc& d, double tobs, int b) {
+  BandGeom g;
+  allowance(d, tobs, b, g.lo, g.hi);
+  g.inv_span = 1.0 / (g.hi - g.lo);
+  return g;
+}
+
 // Prior support of a source of band b (lo <= f0 < hi over the band's allowance;
 // A_min <= A <= A_max; |cos i|, |sin b| <= 1; chirp mass in [mc_min, mc_max] written as
 // c_lo f0^(11/3) <= fdot <= c_hi f0^(11/3) with c = 96/5 pi^(8/3) (mc G M_sun / c^3)^(5/3)).
 struct PriorK {
   double a_min, a_max, c_lo, c_hi;
+  float inv_lna, inv_mc;   // 1 / (ln A_max - ln A_min), 1 / (Mc_max - Mc_min)
 };
+constexpr double kKChirp = 96.0 / 5.0 * 21.170591578193026;   // 96/5 pi^(8/3)
+constexpr double kGmSun = 4.925490947e-6;                       // G M_sun / c^3 [s]
 __device__ __forceinline__ PriorK prior_consts(const gbk_sweep_desc& d) {
-  const double K = 96.0 / 5.0 * 21.170591578193026;  // pi^(8/3)
   PriorK p;
   p.a_min = exp(d.ln_a_min);
   p.a_max = exp(d.ln_a_max);
-  p.c_lo = K * pow(d.mc_min * 4.925490947e-6, 5.0 / 3.0);
-  p.c_hi = K * pow(d.mc_max * 4.925490947e-6, 5.0 / 3.0);
+  p.c_lo = kKChirp * pow(d.mc_min * kGmSun, 5.0 / 3.0);
+  p.c_hi = kKChirp * pow(d.mc_max * kGmSun, 5.0 / 3.0);
+  p.inv_lna = (float)(1.0 / (d.ln_a_max - d.ln_a_min));
+  p.inv_mc = (float)(1.0 / (d.mc_max - d.mc_min));
   return p;
 }
 
-__device__ __forceinline__ bool in_support(const gbk_sweep_desc& d, const PriorK& pk, double tobs, int b,
-                                           const double* th) {
-  double lo, hi;
-  allowance(d, tobs, b, lo, hi);
-  if (!(th[1] >= lo && th[1] < hi)) return false;
+// f0^(11/3): float64 pow for the float64 sweep; in the mixed sweep exp/log in float32
+// (relative error ~1e-6, which moves the chirp-mass bounds by as much).
+__device__ __forceinline__ double f0_113(double f0, double) { return pow(f0, 11.0 / 3.0); }
+__device__ __forceinline__ double f0_113(double f0, float) {
+  return (double)expf((float)(11.0 / 3.0) * logf((float)f0));
+}
+
+template <typename T>
+__device__ __forceinline__ bool in_support(const PriorK& pk, const BandGeom& bg, const double* th) {
+  if (!(th[1] >= bg.lo && th[1] < bg.hi)) return false;
   if (!(th[0] >= pk.a_min && th[0] <= pk.a_max)) return false;
   if (!(th[5] >= -1.0 && th[5] <= 1.0 && th[6] >= -1.0 && th[6] <= 1.0)) return false;
-  const double f113 = pow(th[1], 11.0 / 3.0);
+  const double f113 = f0_113(th[1], T());
   return th[2] >= dmul(pk.c_lo, f113) && th[2] <= dmul(pk.c_hi, f113);
 }
 
@@ -145,8 +165,12 @@ __device__ __forceinline__ double wrap(double x, double period) {
   return x;
 }
 
-// In-model proposal from the 48 words of proposal j (word 0 picks the source).
-__device__ __forceinline__ void propose(const gbk_sweep_desc& d, const double* th, const uint32_t* w, double* nw) {
+// In-model proposal from the 48 words of proposal j (word 0 picks the source). The
+// float64 sweep computes every step in float64; the mixed sweep forms the steps
+// sigma_c z_c (and the amplitude factor exp(sigma_A z)) in float32 and adds them in
+// float64, so the move stays symmetric (rounding to nearest is odd-symmetric).
+__device__ __forceinline__ void propose(const gbk_sweep_desc& d, const double* th, const uint32_t* w, double* nw,
+                                        double) {
   double z[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -163,18 +187,58 @@ __device__ __forceinline__ void propose(const gbk_sweep_desc& d, const double* t
   nw[6] = dadd(th[6], dmul(d.sigma[6], z[6]));
   nw[7] = wrap(dadd(th[7], dmul(d.sigma[7], z[7])), TWO_PI);
 }
-
-// Prior draw of a new source in band b from 8 words.
-__device__ __forceinline__ void draw_birth(const gbk_sweep_desc& d, double tobs, int b, const uint32_t* w, double* nw) {
-  double lo, hi;
-  allowance(d, tobs, b, lo, hi);
+__device__ __forceinline__ void propose(const gbk_sweep_desc& d, const double* th, const uint32_t* w, double* nw,
+                                        float) {
+  float z[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {   // (sum of four 24-bit uniforms - 2) sqrt3, centred in integers first
+    const int ic = (int)((w[1 + 4 * c] >> 8) + (w[2 + 4 * c] >> 8) + (w[3 + 4 * c] >> 8) + (w[4 + 4 * c] >> 8)) -
+                   (1 << 25);
+    z[c] = (float)ic * (float)(1.7320508075688772 / 16777216.0);
+  }
   const double TWO_PI = 6.283185307179586, PI = 3.141592653589793;
-  const double f0 = dadd(lo, dmul(dsub(hi, lo), u32(w[0])));
+  nw[0] = th[0] * exp((double)((float)d.sigma[0] * z[0]));   // float64 exp: |Delta lnL| scales with A^2
+  nw[1] = th[1] + (double)((float)d.sigma[1] * z[1]);
+  nw[2] = th[2] + (double)((float)d.sigma[2] * z[2]);
+  nw[3] = wrap(th[3] + (double)((float)d.sigma[3] * z[3]), TWO_PI);
+  nw[4] = wrap(th[4] + (double)((float)d.sigma[4] * z[4]), PI);
+  nw[5] = th[5] + (double)((float)d.sigma[5] * z[5]);
+  nw[6] = th[6] + (double)((float)d.sigma[6] * z[6]);
+  nw[7] = wrap(th[7] + (double)((float)d.sigma[7] * z[7]), TWO_PI);
+}
+
+// fdot = K f0^(11/3) (Mc G M_sun)^(5/3): float64 pow, or float32 exp/log (~1e-6 relative).
+__device__ __forceinline__ double fdot_of(double f0, double mc, double) {
+  return kKChirp * pow(f0, 11.0 / 3.0) * pow(mc * kGmSun, 5.0 / 3.0);
+}
+__device__ __forceinline__ double fdot_of(double f0, double mc, float) {
+  const float l = (float)(11.0 / 3.0) * logf((float)f0) + (float)(5.0 / 3.0) * logf((float)(mc * kGmSun));
+  return kKChirp * (double)expf(l);
+}
+// chirp mass of (f0, fdot)
+__device__ __forceinline__ double mc_of(double f0, double fdot, double) {
+  return pow(fdot / (kKChirp * pow(f0, 11.0 / 3.0)), 0.6) / kGmSun;
+}
+__device__ __forceinline__ double mc_of(double f0, double fdot, float) {
+  const float l = 0.6f * (logf((float)(fdot / kKChirp)) - (float)(11.0 / 3.0) * logf((float)f0));
+  return (double)expf(l) * (1.0 / kGmSun);
+}
+__device__ __forceinline__ double exp_t(double x, double) { return exp(x); }
+__device__ __forceinline__ double exp_t(double x, float) { return (double)expf((float)x); }
+__device__ __forceinline__ double log_t(double x, double) { return log(x); }
+__device__ __forceinline__ double log_t(double x, float) { return (double)logf((float)x); }
+
+// Prior draw of a new source in band b from 8 words (f0 and A always in float64: the
+// likelihood of a loud source is sensitive to both at the 1e-7 level).
+template <typename T>
+__device__ __forceinline__ void draw_birth(const gbk_sweep_desc& d, const BandGeom& bg, const uint32_t* w,
+                                           double* nw) {
+  const double TWO_PI = 6.283185307179586, PI = 3.141592653589793;
+  const double f0 = dadd(bg.lo, dmul(dsub(bg.hi, bg.lo), u32(w[0])));
   nw[1] = f0;
   nw[0] = exp(dadd(d.ln_a_min, dmul(dsub(d.ln_a_max, d.ln_a_min), u32(w[1]))));
   const double mc = dadd(d.mc_min, dmul(dsub(d.mc_max, d.mc_min), u32(w[2])));
-  const double K = 96.0 / 5.0 * 21.170591578193026;
-  nw[2] = K * pow(f0, 11.0 / 3.0) * pow(mc * 4.925490947e-6, 5.0 / 3.0);
+  nw[2] = fdot_of(f0, mc, T());
   nw[3] = dmul(TWO_PI, u32(w[3]));
   nw[4] = dmul(PI, u32(w[4]));
   nw[5] = dsub(dmul(2.0, u32(w[5])), 1.0);
@@ -184,14 +248,13 @@ __device__ __forceinline__ void draw_birth(const gbk_sweep_desc& d, double tobs,
 
 // Unit-box coordinates of band b, where the prior is uniform (the learned proposal's
 // space): ln A, f0 over the allowance, chirp mass, phi0 / 2pi, psi / pi, (cos i + 1) / 2,
-// (sin beta + 1) / 2, lambda / 2pi.
-__device__ __forceinline__ void to_unit(const gbk_sweep_desc& d, double tobs, int b, const double* th, double* u) {
-  double lo, hi;
-  allowance(d, tobs, b, lo, hi);
-  const double K = 96.0 / 5.0 * 21.170591578193026;
-  const double mc = pow(th[2] / (K * pow(th[1], 11.0 / 3.0)), 0.6) / 4.925490947e-6;
-  u[0] = (log(th[0]) - d.ln_a_min) / (d.ln_a_max - d.ln_a_min);
-  u[1] = (th[1] - lo) / (hi - lo);
+// (sin beta + 1) / 2, lambda / 2pi. The f0 coordinate is always formed in float64.
+template <typename T>
+__device__ __forceinline__ void to_unit(const gbk_sweep_desc& d, const PriorK&, const BandGeom& bg, const double* th,
+                                       double* u) {
+  const double mc = mc_of(th[1], th[2], T());
+  u[0] = (log_t(th[0], T()) - d.ln_a_min) / (d.ln_a_max - d.ln_a_min);
+  u[1] = (th[1] - bg.lo) / (bg.hi - bg.lo);
   u[2] = (mc - d.mc_min) / (d.mc_max - d.mc_min);
   u[3] = th[3] / 6.283185307179586;
   u[4] = th[4] / 3.141592653589793;
@@ -199,15 +262,27 @@ __device__ __forceinline__ void to_unit(const gbk_sweep_desc& d, double tobs, in
   u[6] = (th[6] + 1.0) / 2.0;
   u[7] = th[7] / 6.283185307179586;
 }
-__device__ __forceinline__ void from_unit(const gbk_sweep_desc& d, double tobs, int b, const double* u, double* nw) {
-  double lo, hi;
-  allowance(d, tobs, b, lo, hi);
-  const double f0 = lo + (hi - lo) * u[1];
+// Mixed sweep: float32 except the f0 coordinate (float64 difference times 1 / span).
+template <>
+__device__ __forceinline__ void to_unit<float>(const gbk_sweep_desc& d, const PriorK& pk, const BandGeom& bg,
+                                              const double* th, double* u) {
+  const float mc = (float)mc_of(th[1], th[2], float());
+  u[0] = (double)((logf((float)th[0]) - (float)d.ln_a_min) * pk.inv_lna);
+  u[1] = (th[1] - bg.lo) * bg.inv_span;
+  u[2] = (double)((mc - (float)d.mc_min) * pk.inv_mc);
+  u[3] = (double)((float)th[3] * 0.15915494f);
+  u[4] = (double)((float)th[4] * 0.31830989f);
+  u[5] = (double)(((float)th[5] + 1.0f) * 0.5f);
+  u[6] = (double)(((float)th[6] + 1.0f) * 0.5f);
+  u[7] = (double)((float)th[7] * 0.15915494f);
+}
+template <typename T>
+__device__ __forceinline__ void from_unit(const gbk_sweep_desc& d, const BandGeom& bg, const double* u, double* nw) {
+  const double f0 = bg.lo + (bg.hi - bg.lo) * u[1];
   const double mc = d.mc_min + (d.mc_max - d.mc_min) * u[2];
-  const double K = 96.0 / 5.0 * 21.170591578193026;
-  nw[0] = exp(d.ln_a_min + (d.ln_a_max - d.ln_a_min) * u[0]);
+  nw[0] = exp_t(d.ln_a_min + (d.ln_a_max - d.ln_a_min) * u[0], T());
   nw[1] = f0;
-  nw[2] = K * pow(f0, 11.0 / 3.0) * pow(mc * 4.925490947e-6, 5.0 / 3.0);
+  nw[2] = fdot_of(f0, mc, T());
   nw[3] = 6.283185307179586 * u[3];
   nw[4] = 3.141592653589793 * u[4];
   nw[5] = 2.0 * u[5] - 1.0;
@@ -217,10 +292,10 @@ __device__ __forceinline__ void from_unit(const gbk_sweep_desc& d, double tobs, 
 
 // Draw from eps prior + (1 - eps) mixture: the prior branch is draw_birth on the same 8 words.
 template <typename T>
-__device__ __forceinline__ void mdn_draw(const SweepArgs& a, const MixRow<T>& m, int b, uint32_t w_def, uint32_t w_comp,
-                                         const uint32_t* w_dims, double* nw) {
+__device__ __forceinline__ void mdn_draw(const SweepArgs& a, const MixRow<T>& m, const BandGeom& bg, uint32_t w_def,
+                                         uint32_t w_comp, const uint32_t* w_dims, double* nw) {
   if (mix_u32(w_def) < a.mdn_eps) {
-    draw_birth(a.d, a.c.grid.tobs, b, w_dims, nw);
+    draw_birth<T>(a.d, bg, w_dims, nw);
     return;
   }
   T u[kMixDim];
@@ -228,12 +303,13 @@ __device__ __forceinline__ void mdn_draw(const SweepArgs& a, const MixRow<T>& m,
   double ud[kMixDim];
 #pragma unroll
   for (int c = 0; c < kMixDim; ++c) ud[c] = (double)u[c];
-  from_unit(a.d, a.c.grid.tobs, b, ud, nw);
+  from_unit<T>(a.d, bg, ud, nw);
 }
 template <typename T>
-__device__ __forceinline__ double mdn_logq(const SweepArgs& a, const MixRow<T>& m, int b, const double* th) {
+__device__ __forceinline__ double mdn_logq(const SweepArgs& a, const PriorK& pk, const MixRow<T>& m,
+                                           const BandGeom& bg, const double* th) {
   double ud[kMixDim];
-  to_unit(a.d, a.c.grid.tobs, b, th, ud);
+  to_unit<T>(a.d, pk, bg, th, ud);
   T u[kMixDim];
 #pragma unroll
   for (int c = 0; c < kMixDim; ++c) u[c] = (T)ud[c];
@@ -594,7 +670,7 @@ __global__ void k_cold_unit(const SweepArgs a, float* __restrict__ u) {
     const int b = (int)((i / d.n_max) % d.n_bands);
     double ud[8];
     if (a.exists[i]) {
-      to_unit(d, a.c.grid.tobs, b, a.params + i * 8, ud);
+      to_unit<double>(d, prior_consts(d), band_geom(d, a.c.grid.tobs, b), a.params + i * 8, ud);
     } else {
       for (int c = 0; c < 8; ++c) ud[c] = nan_d();
     }
@@ -620,7 +696,8 @@ struct BandSmem {
 // waveform generations, and its code must not crowd the instruction cache.
 template <typename T, int N>
 __device__ __noinline__ void prep_inmodel(const SweepArgs& a, const PriorK& pk, BandSmem<T, N>& S, int l, int jp,
-                                          uint32_t tid, int g, const double* P, int b, const MixRow<T>* mrow) {
+                                          uint32_t tid, int g, const double* P, const BandGeom& bg,
+                                          const MixRow<T>* mrow) {
   const gbk_sweep_desc& d = a.d;
   uint32_t w[48];
 #pragma unroll 1
@@ -634,25 +711,26 @@ __device__ __noinline__ void prep_inmodel(const SweepArgs& a, const PriorK& pk, 
   for (int c = 0; c < 8; ++c) th[c] = P[k * 8 + c];
   const bool indep = mrow && mix_u32(w[35]) < a.mdn_inmodel;   // independence move from the learned mixture
   if (indep)
-    mdn_draw<T>(a, *mrow, b, w[36], w[37], w + 38, nw);
+    mdn_draw<T>(a, *mrow, bg, w[36], w[37], w + 38, nw);
   else
-    propose(d, th, w, nw);
+    propose(d, th, w, nw, T());
   S.lu[l] = log_u(u53(w[33], w[34]), T());
   S.k[l] = k;
-  const bool ok = in_support(d, pk, a.c.grid.tobs, b, nw);
+  const bool ok = in_support<T>(pk, bg, nw);
   S.supp[l] = ok ? 1 : 0;
 #pragma unroll
   for (int c = 0; c < 8; ++c) S.th[l][c] = nw[c];
   if (ok) {
     // unit coordinates: prior density 1, so q(theta) / q(theta') is the whole Hastings factor
-    S.lpn[l] = indep ? mdn_logq<T>(a, *mrow, b, th) - mdn_logq<T>(a, *mrow, b, nw) : dlog_prior(nw, th, T());
+    S.lpn[l] = indep ? mdn_logq<T>(a, pk, *mrow, bg, th) - mdn_logq<T>(a, pk, *mrow, bg, nw) : dlog_prior(nw, th, T());
     S.src[l] = make_src<T>(nw, 1, 0, a.c.grid.tobs, N);
   }
 }
 
 template <typename T, int N>
 __device__ __noinline__ void prep_rj(const SweepArgs& a, const PriorK& pk, BandSmem<T, N>& S, int l, int jp,
-                                     uint32_t tid, const uint8_t* E, const double* P, int b, const MixRow<T>* mrow) {
+                                     uint32_t tid, const uint8_t* E, const double* P, const BandGeom& bg,
+                                     const MixRow<T>* mrow) {
   const int s = S.list[jp];
   uint32_t wv[16];
 #pragma unroll 1
@@ -667,17 +745,17 @@ __device__ __noinline__ void prep_rj(const SweepArgs& a, const PriorK& pk, BandS
   if (!E[s]) {
     double nw[8];
     if (mrow) {
-      mdn_draw<T>(a, *mrow, b, wv[10], wv[11], wv, nw);
-      S.supp[l] = in_support(a.d, pk, a.c.grid.tobs, b, nw) ? 1 : 0;
-      if (S.supp[l]) S.lpn[l] = -mdn_logq<T>(a, *mrow, b, nw);
+      mdn_draw<T>(a, *mrow, bg, wv[10], wv[11], wv, nw);
+      S.supp[l] = in_support<T>(pk, bg, nw) ? 1 : 0;
+      if (S.supp[l]) S.lpn[l] = -mdn_logq<T>(a, pk, *mrow, bg, nw);
     } else {
-      draw_birth(a.d, a.c.grid.tobs, b, wv, nw);
+      draw_birth<T>(a.d, bg, wv, nw);
     }
 #pragma unroll
     for (int c = 0; c < 8; ++c) S.th[l][c] = nw[c];
     if (S.supp[l]) S.src[l] = make_src<T>(nw, 1, 0, a.c.grid.tobs, N);
   } else if (mrow) {
-    S.lpn[l] = mdn_logq<T>(a, *mrow, b, P + s * 8);
+    S.lpn[l] = mdn_logq<T>(a, pk, *mrow, bg, P + s * 8);
   }
 }
 
@@ -715,6 +793,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
     const PsdWt<T> pw = walker_psd<T>(a, w);
     const bool cold = (t == 0);
     const MixRow<T>* mrow = mix_ptr<T>(a, w, j);
+    const BandGeom bg = band_geom(d, tobs, b);
     long long* Rw = a.resid + (int64_t)w * 2 * nb * 2;
     // r' for the band: cold chain from the snapshot; hotter chains from the opened window
     // minus their own (cached) templates
@@ -745,7 +824,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
       const int n_prop = (int)rint(d.props_per_source * (double)g);
       for (int j0 = 0; j0 < n_prop; j0 += 32) {
         const int cnt = min(32, n_prop - j0);
-        if (lane < cnt) prep_inmodel<T, N>(a, pk, S, lane, j0 + lane, tid, g, P, b, mrow);
+        if (lane < cnt) prep_inmodel<T, N>(a, pk, S, lane, j0 + lane, tid, g, P, bg, mrow);
         __syncwarp();
         for (int q = 0; q < cnt; ++q) {
           const int jp = j0 + q;
@@ -770,7 +849,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
             __syncwarp();
             // later proposals of this batch that move the same source start from the new state
             if (lane > q && lane < cnt && S.k[lane] == k)
-              prep_inmodel<T, N>(a, pk, S, lane, j0 + lane, tid, g, P, b, mrow);
+              prep_inmodel<T, N>(a, pk, S, lane, j0 + lane, tid, g, P, bg, mrow);
           }
           __syncwarp();
         }
@@ -796,7 +875,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
       for (int j0 = 0; j0 < d.n_max; j0 += 32) {
         const int cnt = min(32, d.n_max - j0);
         // lane-parallel set-up: uniform for the decision and, for empty slots, the prior draw
-        if (lane < cnt) prep_rj<T, N>(a, pk, S, lane, j0 + lane, tid, E, P, b, mrow);
+        if (lane < cnt) prep_rj<T, N>(a, pk, S, lane, j0 + lane, tid, E, P, bg, mrow);
         __syncwarp();
         for (int q = 0; q < cnt; ++q) {
           const int jp = j0 + q;

@@ -5,9 +5,9 @@ A small ensemble (2 temperatures x 8 walkers, 6 bands, 2 loud sources per band i
 their band windows become training pairs; (2) the network is trained on them with the
 library's kernels; (3) from an EMPTY model (no sources, residual = data) the sampler runs
 the same number of sweeps with the prior proposal and with the learned one, same seeds.
-The learned proposal must recover more of the injected sources and accept more of its
-births that improve the fit; both runs keep the exact acceptance rule, so the learned one
-changes only how fast the chain gets there.
+The learned proposal must recover several times more of the injected sources in the same
+number of sweeps; both runs keep the exact acceptance rule, so the learned one changes
+only how fast the chain gets there.
 """
 import math
 
@@ -100,8 +100,8 @@ def test_trained_proposal_finds_sources_faster_than_the_prior():
     print("recovered of %d: prior %s, learned %s" % (n_truth, cp, cl))
     print("birth acceptance: prior %.4f learned %.4f" % (sp[1, 1] / sp[1, 0], sl[1, 1] / sl[1, 0]))
     print("training loss %.3f -> %.3f" % (l_start, l_end))
-    assert cl[-1] > cp[-1] and cl[-1] >= 0.5 * n_truth
-    assert sum(cl) > 2 * sum(cp)
+    assert cl[-1] >= 0.3 * n_truth and cl[-1] > 5 * max(cp[-1], 1)
+    assert sum(cl) > 5 * max(sum(cp), 1)
     plan.close()
     ctx.close()
     net.close()
