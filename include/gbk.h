@@ -306,23 +306,31 @@ gbk_status gbk_sweep_kernel_ms(gbk_sweep* plan, double* ms_out);
  *   W1[512][1024] b1[512] W2[512][512] b2[512] W3[512][512] b3[512] W4[272][512] b4[272]
  * (mdn_param_count() = 1,189,648 float32). Mixture: pi = softmax(weight logits),
  * mu = sigmoid(mean logits), ln s = -10 + 10 sigmoid(width logits).
- * Products run on BF16 tensor cores with float32 accumulation; the float32 master
- * parameters and Adam moments belong to the caller.
+ * Products run on the BF16 tensor cores (tcgen05, TMA, accumulators in tensor memory) with
+ * float32 accumulation; weights and hidden activations are rounded to BF16 (that rounded
+ * network is the model). The float32 master parameters and Adam moments belong to the
+ * caller. Every wait inside the tensor-core kernels is bounded; one that gives up skips the
+ * rest of its tile and is reported by mdn_status.
  */
 typedef struct gbk_mdn gbk_mdn;
 
 int64_t mdn_param_count(void);
 
 /* Workspace for batches of up to max_batch rows (activations, gradient partials, BF16
- * weight copy). Allocates device memory (about 6 KB per row + 86 MB). */
+ * weight copies, transposed operand copies). Allocates device memory (about 12 KB per row
+ * + 45 MB). */
 gbk_status mdn_create(gbk_mdn** out, int32_t max_batch);
 gbk_status mdn_destroy(gbk_mdn* net);
+
+/* Synchronise `stream`, then read and clear the workspace's device error word: GBK_ETIMEOUT
+ * if a tensor-core product gave up a bounded wait since the last call, else GBK_OK. */
+gbk_status mdn_status(gbk_mdn* net, void* stream);
 
 /* Load float32 parameters [mdn_param_count()] (device) into the workspace's copies. */
 gbk_status mdn_set_params(gbk_mdn* net, const float* params, void* stream);
 
-/* raw [batch][272] float32 out = network(x), x [batch][1024] BF16 bit patterns (16-byte
- * aligned). */
+/* raw [batch][272] float32 out = network(x), x [batch][1024] BF16 bit patterns; both
+ * 16-byte aligned. */
 gbk_status mdn_forward(gbk_mdn* net, const uint16_t* x, int32_t batch, float* raw, void* stream);
 
 /* Gradient of the mean negative log density -1/batch sum_i ln q(u_i | x_i) with respect
@@ -343,6 +351,15 @@ gbk_status mdn_adam(gbk_mdn* net, float* params, float* m, float* v, const float
 gbk_status mdn_train_step(gbk_mdn* net, float* params, float* m, float* v, const uint16_t* x,
                           const float* u, int32_t batch, int32_t step, float lr, double* loss,
                           void* stream);
+
+/* n_steps Adam steps (as mdn_train_step) over minibatches gathered on the device:
+ * step k trains on rows order[k batch .. (k+1) batch) of x [n_rows][1024] (BF16) and
+ * u [n_rows][8]; Adam step numbers step0 + 1 .. step0 + n_steps; loss (device double, or
+ * NULL) receives the last minibatch's mean -ln q. An index outside [0, n_rows) trains on a
+ * zero row and is reported by mdn_status. */
+gbk_status mdn_train_epoch(gbk_mdn* net, float* params, float* m, float* v, const uint16_t* x,
+                           const float* u, int64_t n_rows, const int32_t* order, int32_t batch,
+                           int32_t n_steps, int32_t step0, float lr, double* loss, void* stream);
 
 /* Draws from and densities of the eps-defensive mixture given raw outputs [batch][272]
  * (the sampler's own arithmetic, in `precision`):

@@ -91,6 +91,7 @@ SIGNATURES = {
     "mdn_param_count": (ctypes.c_int64, []),
     "mdn_create": (ctypes.c_int, [ctypes.POINTER(_vp), _i32]),
     "mdn_destroy": (ctypes.c_int, [_vp]),
+    "mdn_status": (ctypes.c_int, [_vp, _vp]),
     "mdn_set_params": (ctypes.c_int, [_vp, _vp, _vp]),
     "mdn_forward": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
     "mdn_backward": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
@@ -98,6 +99,8 @@ SIGNATURES = {
                                 ctypes.c_float, _vp]),
     "mdn_train_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp]),
     "mdn_sample_logpdf": (ctypes.c_int, [_vp, _i32, ctypes.c_double, _vp, _vp, _vp, _vp, _i32, _vp]),
+    "mdn_train_epoch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, ctypes.c_float, _vp,
+                                       _vp]),
     "gbk_sweep_set_proposal": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double]),
     "gb_sweep_features": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(GbkResidual), ctypes.POINTER(GbkPsd), _vp, _vp,
                                          _vp]),
@@ -333,6 +336,10 @@ class Mdn:
             pass
 
 
+def mdn_status(net, stream=None):
+    _check(lib().mdn_status(net.handle, _stream(stream)), "mdn_status")
+
+
 def mdn_param_count():
     return int(lib().mdn_param_count())
 
@@ -366,6 +373,17 @@ def mdn_train_step(net, params, m, v, x, u, step, lr, loss=None, stream=None):
                                 int(x.shape[0]), int(step), float(lr),
                                 _dev(loss, torch.float64, "loss") if loss is not None else None, _stream(stream)),
            "mdn_train_step")
+
+
+def mdn_train_epoch(net, params, m, v, x, u, order, batch, step0, lr, loss=None, stream=None):
+    """len(order) // batch Adam steps over rows of x [n][1024] bf16 / u [n][8] picked by order (int32, device)."""
+    n_steps = int(order.numel()) // int(batch)
+    _check(lib().mdn_train_epoch(net.handle, _dev(params, torch.float32, "params"), _dev(m, torch.float32, "m"),
+                                 _dev(v, torch.float32, "v"), _dev(x, torch.bfloat16, "x"), _dev(u, torch.float32, "u"),
+                                 int(x.shape[0]), _dev(order, torch.int32, "order"), int(batch), n_steps, int(step0),
+                                 float(lr), _dev(loss, torch.float64, "loss") if loss is not None else None,
+                                 _stream(stream)), "mdn_train_epoch")
+    return n_steps
 
 
 def mdn_sample_logpdf(raw, eps, precision, words=None, u_out=None, u_in=None, logq=None, stream=None):

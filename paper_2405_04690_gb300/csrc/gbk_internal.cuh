@@ -71,15 +71,33 @@ struct gbk_ctx {
 // Mixture-density network workspace (gbk_mdn.cu).
 struct gbk_mdn {
   int32_t max_batch;
+  int64_t ldt;           // row length of the transposed copies (max_batch rounded up to 8)
   float* pf;             // float32 copy of the parameters (biases of the forward pass)
-  __nv_bfloat16* pb;     // BF16 copy (weights)
+  __nv_bfloat16* pb;     // BF16 copy (weights, [out][in])
+  __nv_bfloat16* pbT;    // BF16 W^T [in][out] of layers 2-4
   __nv_bfloat16* h[3];   // hidden activations [max_batch][512]
+  __nv_bfloat16* hT[3];  // and transposed [512][ldt]
   float* raw;            // [max_batch][272]
   __nv_bfloat16* g4;     // d loss / d raw [max_batch][272]
-  __nv_bfloat16* g[2];   // backward activations [max_batch][512]
+  __nv_bfloat16* g4T;    // and transposed [272][ldt]
+  __nv_bfloat16* g[2];   // back-propagated signals [max_batch][512]
+  __nv_bfloat16* gT[2];  // and transposed [512][ldt]
+  __nv_bfloat16* xT;     // input features transposed [1024][ldt]
   float* nll;            // [max_batch]
-  float* part;           // split-K gradient partials [16][n_params]
+  float* part;           // split-K gradient partials [8][n_params]
+  int* err;              // device error word (bounded waits of the tensor-core products)
+  __nv_bfloat16* xb;     // gathered training rows [max_batch][1024]
+  float* ub;             // and their targets [max_batch][8]
   bool have_params;
+  // encoded TMA maps of the operands seen so far (pointers and shapes repeat every step)
+  struct MapEntry {
+    const void* p;
+    int64_t rows, k, ld;
+    int box;
+    alignas(64) unsigned char map[128];
+  };
+  MapEntry maps[48];
+  int n_maps, next_map;
 };
 
 namespace gbk {

@@ -6,18 +6,24 @@
 // Here a small MLP maps a band's whitened residual (1024 values) to a 16-component
 // truncated diagonal mixture over the band's unit-box coordinates (gbk_mix.cuh):
 //   1024 -> 512 -> 512 -> 512 (ReLU) -> 272,  weights [out][in], float32 master copy.
-// Every matrix product is one launch of k_gemm: mma.sync m16n8k16 BF16 x BF16 -> FP32,
-// 3-stage cp.async pipeline through shared memory, operands of either orientation read
-// with ldmatrix (.trans where the contraction index is the strided one), a fused
-// epilogue (bias + ReLU -> BF16, bias -> FP32, ReLU-mask -> BF16, or split-K partials).
-// Weight gradients are split over the batch into fixed partial slots and summed in a
-// fixed order by the Adam / reduce kernel, so training is deterministic.
+// Every matrix product is one launch of the tcgen05 kernel of gbk_umma.cuh (TMA tiles,
+// 128 x 128 accumulator in tensor memory, fused epilogue). Both of its operands are
+// K-contiguous, so the backward products read transposed copies that the producing kernels
+// write alongside: hidden activations h^T and back-propagated signals g^T (by the GEMM
+// epilogues and the loss kernel), W^T of layers 2-4 (by the parameter update), x^T (by a
+// transpose kernel). Weight gradients are split over the batch into fixed partial slots
+// and summed in a fixed order by the Adam / reduce kernel, so training is deterministic.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
 
+#include <string.h>
+
+#include <mutex>
+
 #include "gbk_internal.cuh"
 #include "gbk_mix.cuh"
+#include "gbk_umma.cuh"
 
 namespace gbk {
 
@@ -28,226 +34,138 @@ constexpr int64_t kOffW2 = kOffB1 + kHid, kOffB2 = kOffW2 + (int64_t)kHid * kHid
 constexpr int64_t kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + (int64_t)kHid * kHid;
 constexpr int64_t kOffW4 = kOffB3 + kHid, kOffB4 = kOffW4 + (int64_t)kOut * kHid;
 constexpr int64_t kNParams = kOffB4 + kOut;
-constexpr int kMaxSplit = 16;
+constexpr int kMaxSplit = 8;
 
 typedef __nv_bfloat16 bf16;
 
-// -------------------------------------------------------------- GEMM
-enum { EPI_BIAS_RELU_BF16 = 0, EPI_BIAS_F32 = 1, EPI_MASK_BF16 = 2, EPI_PART_F32 = 3 };
+// transposed weight copies W^T [in][out] of layers 2-4 (the input-gradient products' B)
+constexpr int64_t kOffT2 = 0, kOffT3 = (int64_t)kHid * kHid, kOffT4 = 2 * (int64_t)kHid * kHid;
+constexpr int64_t kNT = kOffT4 + (int64_t)kHid * kOut;
 
-struct GemmArgs {
-  const bf16* A; int64_t lda;      // A(m, k) = AK ? A[m lda + k] : A[k lda + m]
-  const bf16* B; int64_t ldb;      // B(k, n) = BK ? B[n ldb + k] : B[k ldb + n]
-  int M, N, K, kps;                // kps: K range of one split (multiple of 32)
-  const float* bias;               // [N]
-  const bf16* mask; int64_t ldm;   // EPI_MASK: keep (m, n) where mask[m ldm + n] > 0
-  void* C; int64_t ldc;            // C(m, n) = C[m ldc + n]
-  int64_t split_stride;            // EPI_PART: split z writes C + z split_stride
-};
+// -------------------------------------------------------------- tensor-core products
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-constexpr int kBN = 128, kBK = 32, kStages = 3, kGemmThreads = 256;
-constexpr int kPitchK = kBK + 8;       // [rows][k] tiles: 80-byte rows
-constexpr int kPitchMN = 128 + 8;      // [k][rows] tiles: 272-byte rows
-
-template <int BM, bool AK, bool BK>
-struct GemmSmem {
-  static constexpr int a_elems = AK ? BM * kPitchK : kBK * (BM + 8);
-  static constexpr int b_elems = BK ? kBN * kPitchK : kBK * kPitchMN;
-  static constexpr int stage_elems = a_elems + b_elems;
-  static constexpr size_t bytes = (size_t)kStages * stage_elems * sizeof(bf16);
-};
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool ok) {
-  const int n = ok ? 16 : 0;   // src-size 0: fill the 16 bytes with zeros, read nothing
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(n));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t* r, const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+static EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
 }
 
-// Copy k-tile [k0, k0 + 32) of A and B into one pipeline stage (zero outside the matrix
-// or the split's K range; every 16-byte chunk lies wholly inside or outside, since
-// the contiguous extents are multiples of 8 elements).
-template <int BM, bool AK, bool BK>
-__device__ __forceinline__ void gemm_load(const GemmArgs& g, bf16* sa, bf16* sb, int m0, int n0, int k0, int kend) {
-  const int tid = threadIdx.x;
-  if (AK) {   // [BM][32]: BM x 4 chunks
-    for (int c = tid; c < BM * 4; c += kGemmThreads) {
-      const int r = c >> 2, kc = (c & 3) * 8;
-      const int m = m0 + r, k = k0 + kc;
-      const bool ok = m < g.M && k < kend;
-      cp_async16(sa + r * kPitchK + kc, ok ? g.A + (int64_t)m * g.lda + k : g.A, ok);
-    }
-  } else {    // [32][BM]: 32 x BM/8 chunks
-    constexpr int cpr = BM / 8;
-    for (int c = tid; c < kBK * cpr; c += kGemmThreads) {
-      const int r = c / cpr, mc = (c % cpr) * 8;
-      const int k = k0 + r, m = m0 + mc;
-      const bool ok = k < kend && m < g.M;
-      cp_async16(sa + r * (BM + 8) + mc, ok ? g.A + (int64_t)k * g.lda + m : g.A, ok);
+// TMA map of a row-major BF16 matrix [rows][ld] read as [rows][K] tiles of box_rows x 64,
+// from the workspace's cache when the same operand was seen before.
+static gbk_status tmap(gbk_mdn* net, CUtensorMap* m, const bf16* p, int64_t rows, int64_t K, int64_t ld,
+                       int box_rows) {
+  for (int i = 0; i < net->n_maps; ++i) {
+    const gbk_mdn::MapEntry& e = net->maps[i];
+    if (e.p == p && e.rows == rows && e.k == K && e.ld == ld && e.box == box_rows) {
+      memcpy(m, e.map, sizeof(CUtensorMap));
+      return GBK_OK;
     }
   }
-  if (BK) {   // [128][32]
-    for (int c = tid; c < kBN * 4; c += kGemmThreads) {
-      const int r = c >> 2, kc = (c & 3) * 8;
-      const int n = n0 + r, k = k0 + kc;
-      const bool ok = n < g.N && k < kend;
-      cp_async16(sb + r * kPitchK + kc, ok ? g.B + (int64_t)n * g.ldb + k : g.B, ok);
-    }
-  } else {    // [32][128]
-    for (int c = tid; c < kBK * 16; c += kGemmThreads) {
-      const int r = c >> 4, nc = (c & 15) * 8;
-      const int k = k0 + r, n = n0 + nc;
-      const bool ok = k < kend && n < g.N;
-      cp_async16(sb + r * kPitchMN + nc, ok ? g.B + (int64_t)k * g.ldb + n : g.B, ok);
-    }
-  }
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return set_error(GBK_ECUDA, "mdn: cuTensorMapEncodeTiled unavailable");
+  if (((uintptr_t)p & 15) || ((ld * 2) & 15)) return set_error(GBK_EINVAL, "mdn: operand not 16-byte aligned");
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)umma::kBK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(p), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(GBK_ECUDA, "mdn: tensor map encoding failed (%d)", (int)r);
+  const int slot = net->n_maps < 48 ? net->n_maps++ : (net->next_map++ % 48);
+  gbk_mdn::MapEntry& e = net->maps[slot];
+  e.p = p; e.rows = rows; e.k = K; e.ld = ld; e.box = box_rows;
+  memcpy(e.map, m, sizeof(CUtensorMap));
+  return GBK_OK;
 }
 
-// C tile [BM][128] per CTA; 8 warps as 2 (m) x 4 (n), each (BM/2) x 32.
-template <int BM, bool AK, bool BK, int EPI>
-__global__ void __launch_bounds__(kGemmThreads) k_gemm(const GemmArgs g) {
-  constexpr int MI = BM / 32;   // m16 tiles per warp
-  typedef GemmSmem<BM, AK, BK> SM;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  bf16* smem = reinterpret_cast<bf16*>(smem_raw);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int wm = wid >> 2, wn = wid & 3;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * kBN;
-  const int kbeg = blockIdx.z * g.kps;
-  const int kend = min(g.K, kbeg + g.kps);
-  const int nk = kend > kbeg ? (kend - kbeg + kBK - 1) / kBK : 0;
+constexpr int kBN = 128;
 
-  float acc[MI][4][4];
-#pragma unroll
-  for (int i = 0; i < MI; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-
-#pragma unroll
-  for (int s = 0; s < kStages - 1; ++s) {
-    if (s < nk) gemm_load<BM, AK, BK>(g, smem + s * SM::stage_elems, smem + s * SM::stage_elems + SM::a_elems, m0, n0,
-                                      kbeg + s * kBK, kend);
-    cp_commit();
-  }
-  const int r8 = lane & 7, mat = lane >> 3;
-  for (int kt = 0; kt < nk; ++kt) {
-    cp_wait<kStages - 2>();
-    __syncthreads();
-    {   // refill the stage consumed in the previous iteration
-      const int nt = kt + kStages - 1;
-      if (nt < nk) {
-        const int st = nt % kStages;
-        gemm_load<BM, AK, BK>(g, smem + st * SM::stage_elems, smem + st * SM::stage_elems + SM::a_elems, m0, n0,
-                              kbeg + nt * kBK, kend);
-      }
-      cp_commit();
-    }
-    const bf16* sa = smem + (kt % kStages) * SM::stage_elems;
-    const bf16* sb = sa + SM::a_elems;
-#pragma unroll
-    for (int kk = 0; kk < kBK; kk += 16) {
-      uint32_t af[MI][4], bfr[4][2];
-#pragma unroll
-      for (int i = 0; i < MI; ++i) {
-        const int mb = wm * (BM / 2) + i * 16;
-        if (AK) {   // matrix j: rows mb + (j & 1) 8, k kk + (j >> 1) 8
-          ldsm_x4(af[i], sa + (mb + (mat & 1) * 8 + r8) * kPitchK + kk + (mat >> 1) * 8);
-        } else {    // stored [k][m]: rows k = kk + (j >> 1) 8 + r, cols m = mb + (j & 1) 8
-          ldsm_x4_t(af[i], sa + (kk + (mat >> 1) * 8 + r8) * (BM + 8) + mb + (mat & 1) * 8);
-        }
-      }
-#pragma unroll
-      for (int jp = 0; jp < 2; ++jp) {   // two n16 pairs -> four n8 tiles
-        const int nb = wn * 32 + jp * 16;
-        uint32_t r[4];
-        if (BK) {   // stored [n][k]: matrix j: n = nb + (j >> 1) 8 + r, k = kk + (j & 1) 8
-          ldsm_x4(r, sb + (nb + (mat >> 1) * 8 + r8) * kPitchK + kk + (mat & 1) * 8);
-        } else {    // stored [k][n]: rows k = kk + (j & 1) 8 + r, cols n = nb + (j >> 1) 8
-          ldsm_x4_t(r, sb + (kk + (mat & 1) * 8 + r8) * kPitchMN + nb + (mat >> 1) * 8);
-        }
-        bfr[2 * jp][0] = r[0]; bfr[2 * jp][1] = r[1];
-        bfr[2 * jp + 1][0] = r[2]; bfr[2 * jp + 1][1] = r[3];
-      }
-#pragma unroll
-      for (int i = 0; i < MI; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
-    }
-  }
-  cp_wait<0>();
-
-  // epilogue: acc[i][j] = rows m (e 0, 1) and m + 8 (e 2, 3), columns n, n + 1
-  const int gq = lane >> 2, tq = lane & 3;
-#pragma unroll
-  for (int i = 0; i < MI; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n = n0 + wn * 32 + j * 8 + 2 * tq;
-      if (n >= g.N) continue;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int m = m0 + wm * (BM / 2) + i * 16 + gq + 8 * h;
-        if (m >= g.M) continue;
-        float v0 = acc[i][j][2 * h], v1 = acc[i][j][2 * h + 1];
-        if (EPI == EPI_BIAS_RELU_BF16) {
-          v0 = fmaxf(v0 + g.bias[n], 0.f);
-          v1 = fmaxf(v1 + g.bias[n + 1], 0.f);
-          *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<bf16*>(g.C) + (int64_t)m * g.ldc + n) =
-              __floats2bfloat162_rn(v0, v1);
-        } else if (EPI == EPI_BIAS_F32) {
-          *reinterpret_cast<float2*>(reinterpret_cast<float*>(g.C) + (int64_t)m * g.ldc + n) =
-              make_float2(v0 + g.bias[n], v1 + g.bias[n + 1]);
-        } else if (EPI == EPI_MASK_BF16) {
-          const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(g.mask + (int64_t)m * g.ldm + n);
-          if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
-          if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
-          *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<bf16*>(g.C) + (int64_t)m * g.ldc + n) =
-              __floats2bfloat162_rn(v0, v1);
-        } else {
-          *reinterpret_cast<float2*>(reinterpret_cast<float*>(g.C) + blockIdx.z * g.split_stride +
-                                     (int64_t)m * g.ldc + n) = make_float2(v0, v1);
-        }
-      }
-    }
-}
-
-template <int BM, bool AK, bool BK, int EPI>
-static gbk_status gemm(const GemmArgs& g, int splits, cudaStream_t st) {
-  typedef GemmSmem<BM, AK, BK> SM;
-  static bool attr = false;   // per instantiation; same value on every device
+// C[M][N] = A[M][K] . B[N][K]^T (+ epilogue); A, B row-major BF16 with leading dimensions.
+template <int EPI>
+static gbk_status mm(gbk_mdn* net, const bf16* A, int64_t lda, const bf16* B, int64_t ldb, int M, int N, int K,
+                     umma::Args g, int splits, cudaStream_t st) {
+  typedef umma::Smem<kBN> SM;
+  static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(k_gemm<BM, AK, BK, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes) !=
+    if (cudaFuncSetAttribute(umma::k_umma<kBN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes) !=
         cudaSuccess) {
       cudaGetLastError();
-      return set_error(GBK_ECUDA, "mdn: cannot set GEMM shared memory size");
+      return set_error(GBK_ECUDA, "mdn: cannot set the tensor-core kernel's shared memory size");
     }
     attr = true;
   }
-  dim3 grid((g.N + kBN - 1) / kBN, (g.M + BM - 1) / BM, splits);
-  k_gemm<BM, AK, BK, EPI><<<grid, kGemmThreads, SM::bytes, st>>>(g);
-  return check_launch("mdn gemm");
+  CUtensorMap ma, mb;
+  gbk_status s;
+  if ((s = tmap(net, &ma, A, M, K, lda, umma::kBM))) return s;
+  if ((s = tmap(net, &mb, B, N, K, ldb, kBN))) return s;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  if (splits <= 1) g.kps = K;
+  dim3 grid((N + kBN - 1) / kBN, (M + umma::kBM - 1) / umma::kBM, splits > 1 ? splits : 1);
+  umma::k_umma<kBN, EPI><<<grid, umma::kThreads, SM::bytes, st>>>(ma, mb, g);
+  return check_launch("mdn tensor-core product");
+}
+
+static umma::Args margs(gbk_mdn* net, void* C, int64_t ldc) {
+  umma::Args g;
+  g.M = g.N = g.K = g.kps = 0;
+  g.bias = nullptr;
+  g.mask = nullptr;
+  g.ldm = 0;
+  g.C = C;
+  g.ldc = ldc;
+  g.split_stride = 0;
+  g.CT = nullptr;
+  g.ldct = 0;
+  g.err = net->err;
+  return g;
+}
+
+// x [B][1024] -> x^T [1024][ldt] (32 x 32 tiles through shared memory)
+__global__ void k_transpose(const bf16* __restrict__ x, int B, int cols, bf16* __restrict__ xt, int64_t ldt) {
+  __shared__ bf16 t[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < B && c < cols) t[i][threadIdx.x] = x[(int64_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < B && c < cols) xt[(int64_t)c * ldt + r] = t[threadIdx.x][i];
+  }
+}
+
+// Training rows of one minibatch: x[order[i]] -> xb[i] (16-byte chunks), u[order[i]] -> ub[i].
+__global__ void k_gather(const bf16* __restrict__ x, const float* __restrict__ u, const int32_t* __restrict__ order,
+                         int B, int64_t n_rows, bf16* __restrict__ xb, float* __restrict__ ub, int* err) {
+  const int64_t total = (int64_t)B * (kIn / 8);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / (kIn / 8)), c = (int)(i % (kIn / 8));
+    const int32_t src = order[r];
+    if (src < 0 || src >= n_rows) {   // bad index: zero row, error bit, nothing read
+      if (c == 0) atomicOr(err, 4);
+      reinterpret_cast<uint4*>(xb + (int64_t)r * kIn)[c] = make_uint4(0, 0, 0, 0);
+      if (c < kMixDim) ub[(int64_t)r * kMixDim + c] = 0.5f;
+      continue;
+    }
+    reinterpret_cast<uint4*>(xb + (int64_t)r * kIn)[c] = reinterpret_cast<const uint4*>(x + (int64_t)src * kIn)[c];
+    if (c < kMixDim) ub[(int64_t)r * kMixDim + c] = u[(int64_t)src * kMixDim + c];
+  }
 }
 
 // -------------------------------------------------------------- loss and its gradient
@@ -322,15 +240,23 @@ __global__ void k_mean(const float* __restrict__ x, int n, double* __restrict__ 
 }
 
 // Bias gradients: column sums of g [B][N] over split z's rows, into part + z stride + off.
+// Block (32 columns) x (8 row phases); the 8 phase sums are added in a fixed order.
 __global__ void k_colsum(const bf16* __restrict__ g, int B, int N, int kps, float* __restrict__ part,
                          int64_t stride, int64_t off) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
+  __shared__ float red[8][33];
+  const int n = blockIdx.x * 32 + threadIdx.x;
   const int z = blockIdx.y;
   const int r1 = min(B, (z + 1) * kps);
   float s = 0.f;
-  for (int r = z * kps; r < r1; ++r) s += __bfloat162float(g[(int64_t)r * N + n]);
-  part[(int64_t)z * stride + off + n] = s;
+  if (n < N)
+    for (int r = z * kps + threadIdx.y; r < r1; r += 8) s += __bfloat162float(g[(int64_t)r * N + n]);
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && n < N) {
+    float t = 0.f;
+    for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
+    part[(int64_t)z * stride + off + n] = t;
+  }
 }
 
 // grad = sum over splits (fixed order).
@@ -345,9 +271,26 @@ __global__ void k_reduce(const float* __restrict__ part, int S, int64_t n, float
 // Adam (Kingma & Ba 2015) on the float32 master parameters, gradient summed from the
 // split partials (S > 0) or read directly (S == 0); refreshes the network's float32 and
 // BF16 copies. c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t).
+// Store parameter i into the network's copies: float32, BF16 and, for the weights of
+// layers 2-4, the transposed BF16 copy W^T [in][out].
+__device__ __forceinline__ void store_param(int64_t i, float v, float* pf, bf16* pb, bf16* pbt) {
+  pf[i] = v;
+  const bf16 b = __float2bfloat16_rn(v);
+  pb[i] = b;
+  int64_t off, tof;
+  int nout;
+  if (i >= kOffW2 && i < kOffB2) { off = kOffW2; tof = kOffT2; nout = kHid; }
+  else if (i >= kOffW3 && i < kOffB3) { off = kOffW3; tof = kOffT3; nout = kHid; }
+  else if (i >= kOffW4 && i < kOffB4) { off = kOffW4; tof = kOffT4; nout = kOut; }
+  else return;
+  const int64_t r = i - off;              // W[o][ii], o = r / 512, ii = r % 512
+  pbt[tof + (r % kHid) * nout + r / kHid] = b;
+}
+
 __global__ void k_adam(const float* __restrict__ part, int S, const float* __restrict__ grad, int64_t n,
                        float* __restrict__ p, float* __restrict__ m, float* __restrict__ v, float lr, float b1,
-                       float b2, float eps, float c1, float c2, float* __restrict__ pf, bf16* __restrict__ pb) {
+                       float b2, float eps, float c1, float c2, float* __restrict__ pf, bf16* __restrict__ pb,
+                       bf16* __restrict__ pbt) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float gi;
     if (S > 0) {
@@ -362,16 +305,14 @@ __global__ void k_adam(const float* __restrict__ part, int S, const float* __res
     v[i] = vi;
     const float pi = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
     p[i] = pi;
-    pf[i] = pi;
-    pb[i] = __float2bfloat16_rn(pi);
+    store_param(i, pi, pf, pb, pbt);
   }
 }
 
-__global__ void k_copy_params(const float* __restrict__ p, int64_t n, float* __restrict__ pf, bf16* __restrict__ pb) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    pf[i] = p[i];
-    pb[i] = __float2bfloat16_rn(p[i]);
-  }
+__global__ void k_copy_params(const float* __restrict__ p, int64_t n, float* __restrict__ pf, bf16* __restrict__ pb,
+                              bf16* __restrict__ pbt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    store_param(i, p[i], pf, pb, pbt);
 }
 
 // Mixture rows, log densities and draws for the mdn_sample_logpdf entry point.
@@ -401,77 +342,83 @@ using namespace gbk;
 namespace {
 
 int splits_for(int B, int* kps) {
-  int S = (B + 255) / 256;
+  int S = (B + 511) / 512;
   if (S < 1) S = 1;
   if (S > kMaxSplit) S = kMaxSplit;
   int per = (B + S - 1) / S;
-  per = (per + kBK - 1) / kBK * kBK;
+  per = (per + umma::kBK - 1) / umma::kBK * umma::kBK;   // whole 64-wide k tiles per split
+  S = (B + per - 1) / per;
   *kps = per;
   return S;
 }
 
-GemmArgs ga(const bf16* A, int64_t lda, const bf16* B, int64_t ldb, int M, int N, int K, void* C, int64_t ldc) {
-  GemmArgs g;
-  g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.M = M; g.N = N; g.K = K; g.kps = K;
-  g.bias = nullptr; g.mask = nullptr; g.ldm = 0; g.C = C; g.ldc = ldc; g.split_stride = 0;
-  return g;
-}
-
-// Forward through the four layers; raw outputs to out (float32 [B][272]).
-gbk_status forward(gbk_mdn* net, const bf16* x, int B, float* out, cudaStream_t st) {
+// Forward through the four layers; raw outputs to out (float32 [B][272]). With
+// transposed = true the hidden activations are also written as h^T [512][ldt].
+gbk_status forward(gbk_mdn* net, const bf16* x, int B, float* out, bool transposed, cudaStream_t st) {
   const int64_t offw[4] = {kOffW1, kOffW2, kOffW3, kOffW4}, offb[4] = {kOffB1, kOffB2, kOffB3, kOffB4};
   const bf16* in = x;
   int64_t ldin = kIn;
   gbk_status s;
   for (int l = 0; l < 3; ++l) {
-    GemmArgs g = ga(in, ldin, net->pb + offw[l], ldin, B, kHid, (int)ldin, net->h[l], kHid);
+    umma::Args g = margs(net, net->h[l], kHid);
     g.bias = net->pf + offb[l];
-    if ((s = (B >= 4096 ? gemm<128, true, true, EPI_BIAS_RELU_BF16>(g, 1, st)
-                        : gemm<64, true, true, EPI_BIAS_RELU_BF16>(g, 1, st))))
-      return s;
+    if (transposed) {
+      g.CT = net->hT[l];
+      g.ldct = net->ldt;
+    }
+    if ((s = mm<umma::EPI_BIAS_RELU_BF16>(net, in, ldin, net->pb + offw[l], ldin, B, kHid, (int)ldin, g, 1, st))) return s;
     in = net->h[l];
     ldin = kHid;
   }
-  GemmArgs g = ga(in, kHid, net->pb + kOffW4, kHid, B, kOut, kHid, out, kOut);
+  umma::Args g = margs(net, out, kOut);
   g.bias = net->pf + kOffB4;
-  return gemm<64, true, true, EPI_BIAS_F32>(g, 1, st);
+  return mm<umma::EPI_BIAS_F32>(net, in, kHid, net->pb + kOffW4, kHid, B, kOut, kHid, g, 1, st);
 }
 
 // Loss, gradient and backward pass; weight / bias gradient partials to net->part.
 gbk_status backward(gbk_mdn* net, const bf16* x, const float* u, int B, double* loss, int* S_out, cudaStream_t st) {
   gbk_status s;
-  if ((s = forward(net, x, B, net->raw, st))) return s;
+  if ((s = forward(net, x, B, net->raw, true, st))) return s;
   k_mdn_loss<<<(B + 7) / 8, 256, 0, st>>>(net->raw, u, B, 1.0f / (float)B, net->g4, net->nll);
   if ((s = check_launch("mdn loss"))) return s;
+  k_transpose<<<dim3((kOut + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(net->g4, B, kOut, net->g4T, net->ldt);
   if (loss) {
     k_mean<<<1, 256, 0, st>>>(net->nll, B, loss);
     if ((s = check_launch("mdn loss mean"))) return s;
   }
+  k_transpose<<<dim3(kIn / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(x, B, kIn, net->xT, net->ldt);
+  if ((s = check_launch("mdn input transpose"))) return s;
   int kps;
   const int S = splits_for(B, &kps);
   *S_out = S;
   const int64_t offw[4] = {kOffW1, kOffW2, kOffW3, kOffW4}, offb[4] = {kOffB1, kOffB2, kOffB3, kOffB4};
+  const int64_t offt[4] = {0, kOffT2, kOffT3, kOffT4};
   const int nout[4] = {kHid, kHid, kHid, kOut}, nin[4] = {kIn, kHid, kHid, kHid};
   const bf16* gcur = net->g4;
+  const bf16* gcurT = net->g4T;
   for (int l = 3; l >= 0; --l) {
-    const bf16* hin = l == 0 ? x : net->h[l - 1];
-    // dW_l[o][i] = sum_m g[m][o] hin[m][i]: A = g^T (M = out, contiguous in M), B = hin (contiguous in N)
-    GemmArgs gw = ga(gcur, nout[l], hin, nin[l], nout[l], nin[l], B, net->part + offw[l], nin[l]);
+    const bf16* hinT = l == 0 ? net->xT : net->hT[l - 1];
+    // dW_l[o][i] = sum_m g[m][o] hin[m][i] = (g^T) . (hin^T)^T over the batch, split over it
+    umma::Args gw = margs(net, net->part + offw[l], nin[l]);
     gw.kps = kps;
     gw.split_stride = kNParams;
-    if ((s = gemm<128, false, false, EPI_PART_F32>(gw, S, st))) return s;
-    k_colsum<<<dim3((nout[l] + 255) / 256, S), 256, 0, st>>>(gcur, B, nout[l], kps, net->part, kNParams, offb[l]);
+    if ((s = mm<umma::EPI_PART_F32>(net, gcurT, net->ldt, hinT, net->ldt, nout[l], nin[l], B, gw, S, st))) return s;
+    k_colsum<<<dim3((nout[l] + 31) / 32, S), dim3(32, 8), 0, st>>>(gcur, B, nout[l], kps, net->part, kNParams,
+                                                                    offb[l]);
     if ((s = check_launch("mdn bias gradient"))) return s;
     if (l == 0) break;
-    // g_prev[m][i] = sum_o g[m][o] W[o][i], kept where the forward activation was positive
+    // g_prev[m][i] = sum_o g[m][o] W[o][i] = g . (W^T)^T, kept where the forward activation was positive
     bf16* gn = net->g[l & 1];
-    GemmArgs gx = ga(gcur, nout[l], net->pb + offw[l], nin[l], B, nin[l], nout[l], gn, nin[l]);
+    bf16* gnT = net->gT[l & 1];
+    umma::Args gx = margs(net, gn, nin[l]);
     gx.mask = net->h[l - 1];
     gx.ldm = kHid;
-    if ((s = (B >= 4096 ? gemm<128, true, false, EPI_MASK_BF16>(gx, 1, st)
-                        : gemm<64, true, false, EPI_MASK_BF16>(gx, 1, st))))
+    gx.CT = gnT;
+    gx.ldct = net->ldt;
+    if ((s = mm<umma::EPI_MASK_BF16>(net, gcur, nout[l], net->pbT + offt[l], nout[l], B, nin[l], nout[l], gx, 1, st)))
       return s;
     gcur = gn;
+    gcurT = gnT;
   }
   return GBK_OK;
 }
@@ -498,15 +445,27 @@ extern "C" gbk_status mdn_create(gbk_mdn** out, int32_t max_batch) {
   if (max_batch < 1 || max_batch > (1 << 22)) return set_error(GBK_EINVAL, "mdn_create: max_batch out of range");
   gbk_mdn* n = new gbk_mdn();
   n->max_batch = max_batch;
-  const size_t B = (size_t)max_batch;
+  n->ldt = (max_batch + 7) / 8 * 8;   // transposed copies: rows 16-byte aligned
+  const size_t B = (size_t)max_batch, T = (size_t)n->ldt;
   bool ok = cudaMalloc(&n->pf, kNParams * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&n->pb, kNParams * sizeof(bf16)) == cudaSuccess &&
+            cudaMalloc(&n->pbT, kNT * sizeof(bf16)) == cudaSuccess &&
             cudaMalloc(&n->raw, B * kOut * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&n->g4, B * kOut * sizeof(bf16)) == cudaSuccess &&
+            cudaMalloc(&n->g4T, T * kOut * sizeof(bf16)) == cudaSuccess &&
+            cudaMalloc(&n->xT, T * kIn * sizeof(bf16)) == cudaSuccess &&
             cudaMalloc(&n->nll, B * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&n->err, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&n->xb, B * kIn * sizeof(bf16)) == cudaSuccess &&
+            cudaMalloc(&n->ub, B * kMixDim * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&n->part, (size_t)kMaxSplit * kNParams * sizeof(float)) == cudaSuccess;
-  for (int i = 0; i < 3 && ok; ++i) ok = cudaMalloc(&n->h[i], B * kHid * sizeof(bf16)) == cudaSuccess;
-  for (int i = 0; i < 2 && ok; ++i) ok = cudaMalloc(&n->g[i], B * kHid * sizeof(bf16)) == cudaSuccess;
+  for (int i = 0; i < 3 && ok; ++i)
+    ok = cudaMalloc(&n->h[i], B * kHid * sizeof(bf16)) == cudaSuccess &&
+         cudaMalloc(&n->hT[i], T * kHid * sizeof(bf16)) == cudaSuccess;
+  for (int i = 0; i < 2 && ok; ++i)
+    ok = cudaMalloc(&n->g[i], B * kHid * sizeof(bf16)) == cudaSuccess &&
+         cudaMalloc(&n->gT[i], T * kHid * sizeof(bf16)) == cudaSuccess;
+  if (ok) ok = cudaMemset(n->err, 0, sizeof(int)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     mdn_destroy(n);
@@ -518,16 +477,31 @@ extern "C" gbk_status mdn_create(gbk_mdn** out, int32_t max_batch) {
 
 extern "C" gbk_status mdn_destroy(gbk_mdn* n) {
   if (!n) return GBK_OK;
-  cudaFree(n->pf); cudaFree(n->pb); cudaFree(n->raw); cudaFree(n->g4); cudaFree(n->nll); cudaFree(n->part);
-  for (int i = 0; i < 3; ++i) cudaFree(n->h[i]);
-  for (int i = 0; i < 2; ++i) cudaFree(n->g[i]);
+  cudaFree(n->pf); cudaFree(n->pb); cudaFree(n->pbT); cudaFree(n->raw); cudaFree(n->g4); cudaFree(n->g4T);
+  cudaFree(n->xT); cudaFree(n->nll); cudaFree(n->err); cudaFree(n->part); cudaFree(n->xb); cudaFree(n->ub);
+  for (int i = 0; i < 3; ++i) { cudaFree(n->h[i]); cudaFree(n->hT[i]); }
+  for (int i = 0; i < 2; ++i) { cudaFree(n->g[i]); cudaFree(n->gT[i]); }
   delete n;
+  return GBK_OK;
+}
+
+extern "C" gbk_status mdn_status(gbk_mdn* net, void* stream) {
+  if (!net) return set_error(GBK_EINVAL, "mdn_status: null network");
+  int h = 0;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess ||
+      cudaMemcpy(&h, net->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(net->err, 0, sizeof(int)) != cudaSuccess) {
+    const cudaError_t e = cudaGetLastError();
+    return set_error(GBK_ECUDA, "mdn_status: %s", cudaGetErrorString(e));
+  }
+  if (h & kErrTimeout) return set_error(GBK_ETIMEOUT, "mdn: a tensor-core product gave up waiting (bounded wait)");
+  if (h & kErrWalker) return set_error(GBK_ERANGE, "mdn: a training-row index was out of range");
   return GBK_OK;
 }
 
 extern "C" gbk_status mdn_set_params(gbk_mdn* net, const float* params, void* stream) {
   if (!net || !params) return set_error(GBK_EINVAL, "mdn_set_params: null argument");
-  k_copy_params<<<blocks_for(kNParams), 256, 0, (cudaStream_t)stream>>>(params, kNParams, net->pf, net->pb);
+  k_copy_params<<<blocks_for(kNParams), 256, 0, (cudaStream_t)stream>>>(params, kNParams, net->pf, net->pb, net->pbT);
   net->have_params = true;
   return check_launch("mdn_set_params");
 }
@@ -536,8 +510,8 @@ extern "C" gbk_status mdn_forward(gbk_mdn* net, const uint16_t* x, int32_t batch
   gbk_status s = check_batch(net, batch, "mdn_forward");
   if (s) return s;
   if (!x || !raw) return set_error(GBK_EINVAL, "mdn_forward: null device pointer");
-  if (((uintptr_t)x & 15) || ((uintptr_t)raw & 7)) return set_error(GBK_EINVAL, "mdn_forward: misaligned buffer");
-  return forward(net, reinterpret_cast<const bf16*>(x), batch, raw, (cudaStream_t)stream);
+  if (((uintptr_t)x & 15) || ((uintptr_t)raw & 15)) return set_error(GBK_EINVAL, "mdn_forward: misaligned buffer");
+  return forward(net, reinterpret_cast<const bf16*>(x), batch, raw, false, (cudaStream_t)stream);
 }
 
 extern "C" gbk_status mdn_backward(gbk_mdn* net, const uint16_t* x, const float* u, int32_t batch, float* grad,
@@ -560,7 +534,7 @@ extern "C" gbk_status mdn_adam(gbk_mdn* net, float* params, float* m, float* v, 
   const float c1 = (float)(1.0 / (1.0 - pow((double)beta1, step)));
   const float c2 = (float)(1.0 / (1.0 - pow((double)beta2, step)));
   k_adam<<<blocks_for(kNParams), 256, 0, (cudaStream_t)stream>>>(nullptr, 0, grad, kNParams, params, m, v, lr, beta1,
-                                                                  beta2, eps, c1, c2, net->pf, net->pb);
+                                                                  beta2, eps, c1, c2, net->pf, net->pb, net->pbT);
   net->have_params = true;
   return check_launch("mdn_adam");
 }
@@ -579,7 +553,7 @@ extern "C" gbk_status mdn_train_step(gbk_mdn* net, float* params, float* m, floa
   const double b1 = 0.9, b2 = 0.999;
   const float c1 = (float)(1.0 / (1.0 - pow(b1, step))), c2 = (float)(1.0 / (1.0 - pow(b2, step)));
   k_adam<<<blocks_for(kNParams), 256, 0, st>>>(net->part, S, nullptr, kNParams, params, m, v, lr, (float)b1, (float)b2,
-                                              1e-8f, c1, c2, net->pf, net->pb);
+                                              1e-8f, c1, c2, net->pf, net->pb, net->pbT);
   return check_launch("mdn_train_step");
 }
 
@@ -598,4 +572,30 @@ extern "C" gbk_status mdn_sample_logpdf(const float* raw, int32_t batch, double 
   else
     return set_error(GBK_EINVAL, "mdn_sample_logpdf: bad precision");
   return check_launch("mdn_sample_logpdf");
+}
+
+extern "C" gbk_status mdn_train_epoch(gbk_mdn* net, float* params, float* m, float* v, const uint16_t* x,
+                                      const float* u, int64_t n_rows, const int32_t* order, int32_t batch,
+                                      int32_t n_steps, int32_t step0, float lr, double* loss, void* stream) {
+  gbk_status s = check_batch(net, batch, "mdn_train_epoch");
+  if (s) return s;
+  if (!params || !m || !v || !x || !u || !order) return set_error(GBK_EINVAL, "mdn_train_epoch: null device pointer");
+  if ((uintptr_t)x & 15) return set_error(GBK_EINVAL, "mdn_train_epoch: x must be 16-byte aligned");
+  if (n_steps < 0 || step0 < 0 || n_rows < 1) return set_error(GBK_EINVAL, "mdn_train_epoch: bad counts");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double b1 = 0.9, b2 = 0.999;
+  const int gblocks = blocks_for((int64_t)batch * (kIn / 8));
+  for (int32_t k = 0; k < n_steps; ++k) {
+    k_gather<<<gblocks, 256, 0, st>>>(reinterpret_cast<const bf16*>(x), u, order + (int64_t)k * batch, batch, n_rows,
+                                      net->xb, net->ub, net->err);
+    if ((s = check_launch("mdn_train_epoch(gather)"))) return s;
+    int S = 0;
+    if ((s = backward(net, net->xb, net->ub, batch, k == n_steps - 1 ? loss : nullptr, &S, st))) return s;
+    const int step = step0 + k + 1;
+    const float c1 = (float)(1.0 / (1.0 - pow(b1, step))), c2 = (float)(1.0 / (1.0 - pow(b2, step)));
+    k_adam<<<blocks_for(kNParams), 256, 0, st>>>(net->part, S, nullptr, kNParams, params, m, v, lr, (float)b1,
+                                                (float)b2, 1e-8f, c1, c2, net->pf, net->pb, net->pbT);
+    if ((s = check_launch("mdn_train_epoch(adam)"))) return s;
+  }
+  return GBK_OK;
 }

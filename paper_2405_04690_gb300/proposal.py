@@ -7,8 +7,9 @@ opened window (its cold residual with the band's own cold sources added back, wh
 u the unit-box coordinates of one of those sources. A network trained on such pairs
 proposes new sources where the cold chain has put them for similar residuals: the
 amortised version of the paper's mixture fits to earlier sampler output (Sec. V.E,
-App. G). Every arithmetic step runs in libgbk; this module only allocates device
-buffers, gathers training rows and loops.
+App. G). Every arithmetic step, and the per-minibatch gather of training rows, runs in
+libgbk; this module allocates device buffers, assembles the pair buffer and draws the
+minibatch order.
 """
 import math
 
@@ -74,7 +75,7 @@ class PairBuffer:
 
 
 class Trainer:
-    """Adam training of the network on a PairBuffer (mdn_train_step per minibatch)."""
+    """Adam training of the network on a PairBuffer (one mdn_train_epoch call per epoch)."""
 
     def __init__(self, net, params, lr=1e-3):
         self.net = net
@@ -87,17 +88,14 @@ class Trainer:
         L.mdn_set_params(net, params)
 
     def epoch(self, buf, batch, seed, max_steps=None):
-        """One pass over the buffer in a seeded random order; returns the last minibatch loss."""
+        """One pass over the buffer in a seeded random order (the gathers and Adam steps run
+        in one library call); returns the last minibatch loss."""
         g = np.random.Generator(np.random.PCG64(seed))
-        n = buf.n - buf.n % batch
-        order = torch.from_numpy(g.permutation(buf.n)[:n].astype(np.int64)).to(buf.x.device)
-        steps = n // batch if max_steps is None else min(n // batch, max_steps)
-        for s in range(steps):
-            idx = order[s * batch:(s + 1) * batch]
-            x = buf.x.index_select(0, idx)
-            u = buf.u.index_select(0, idx)
-            self.step += 1
-            L.mdn_train_step(self.net, self.p, self.m, self.v, x, u, self.step, self.lr, self.loss)
+        steps = buf.n // batch if max_steps is None else min(buf.n // batch, max_steps)
+        order = torch.from_numpy(g.permutation(buf.n)[:steps * batch].astype(np.int32)).to(buf.x.device)
+        L.mdn_train_epoch(self.net, self.p, self.m, self.v, buf.x[:buf.n], buf.u[:buf.n], order, batch, self.step,
+                          self.lr, self.loss)
+        self.step += steps
         return float(self.loss.item())
 
     def mean_loss(self, buf, batch=4096, limit=None):
