@@ -52,6 +52,7 @@ def flops_per_evaluation(n=N_BAND):
 
 
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+K_BAND_TRAFFIC = 8 * (915.158528e6 + 562.060288e6)  # DRAM bytes per band-kernel launch (ncu, scaled)
 
 
 def measured_hbm_gbs():
@@ -715,7 +716,10 @@ def run_ours(args):
                    "kernel_ms_per_step": {"open": kms[1] / args.steps, "band": band_ms, "swap": kms[3] / args.steps},
                    "parallelism": "replica per GPU"},
         "roofline": {"bound": "alu", "achieved": ach, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                     "frac": ach / PEAK_FP32_TFLOPS, "traffic": None,
+                     "frac": ach / PEAK_FP32_TFLOPS, "traffic": K_BAND_TRAFFIC,
+                     "traffic_note": "bytes per launch: ncu dram read + write of one k_band launch on the "
+                                     "2-temperature ensemble (1.477 GB) x 8 for the 16-temperature launch "
+                                     "(traffic scales with the band tasks)",
                      "kernel": "k_band<float,256> (in-model + flip-all RJ)",
                      "peak_note": "FP32 ALU: 152 SMs x 128 lanes x 2 (FMA) x 2.07 GHz (derived, not measured)",
                      "flops_per_waveform": flops_per_waveform(), "flops_per_evaluation": flops_per_evaluation()},
@@ -780,7 +784,7 @@ def main():
     ap.add_argument("--mdn-samples", type=int, default=1000000, help="training pairs of the learned proposal")
     ap.add_argument("--mdn-epochs", type=int, default=6)
     ap.add_argument("--mdn-eps", type=float, default=0.2, help="prior fraction of the learned proposal")
-    ap.add_argument("--mdn-inmodel", type=float, default=0.25, help="fraction of in-model moves drawn from it")
+    ap.add_argument("--mdn-inmodel", type=float, default=0.1, help="fraction of in-model moves drawn from it")
     ap.add_argument("--search-sweeps", type=int, default=10)
     args = ap.parse_args()
     if args.impl == "reference":
