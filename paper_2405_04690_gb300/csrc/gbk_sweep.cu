@@ -18,6 +18,8 @@ struct gbk_sweep {
   void* wcache;         // current waveform of every slot [T][W][B][n_max][2][N]
   void* hsum;           // sum of the present templates of every band on its window [T][W][B][2][3N]
   int32_t* setid;       // cache block of band (t, w, b) [T][W][B]; tempering swaps exchange ids
+  void* rwbuf;          // band windows of the band kernel's warps [SMs x 64][2][3N]
+  size_t rwbuf_bytes;
   size_t rho_bytes, cache_bytes, hsum_bytes;
   cudaEvent_t ev[2][4][2];  // [parity][refresh, open, band, swap][begin, end] when timing
   bool timed, have_ev;
@@ -34,6 +36,9 @@ struct gbk_sweep {
 namespace gbk {
 
 constexpr int kSwWarps = 4;
+// band kernel: 4 warps per CTA, 3 CTAs per SM (15 KB of shared memory per warp, 168
+// registers per thread). Capping registers for 14 warps per SM spilled and ran 6 % slower.
+constexpr int kBandWarps = 4, kBandMinCtas = 3;
 constexpr int kMaxSlots = 64;
 
 struct SweepArgs {
@@ -59,6 +64,8 @@ struct SweepArgs {
   int32_t trace_cap;
   int32_t* trace_count;
   long long* stats;
+  // band windows r' of the band kernel's warps (global, L1-cached): [warps][2][3N]
+  void* rwbuf;
   // learned proposal: mixture row of every opened (walker, band) or NULL
   const void* mix;
   double mdn_eps, mdn_inmodel;
@@ -682,7 +689,6 @@ __global__ void k_cold_unit(const SweepArgs a, float* __restrict__ u) {
 // Per-warp shared memory of k_band.
 template <typename T, int N>
 struct BandSmem {
-  typename CT<T>::C rw[2 * 3 * N];     // r' on the window
   typename CT<T>::C ba[2 * N], bs[2 * N];
   Src<T> src[32];                      // constants of the batch's new templates
   double th[32][8];                    // proposed parameters
@@ -760,12 +766,15 @@ __device__ __noinline__ void prep_rj(const SweepArgs& a, const PriorK& pk, BandS
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int flags) {
+__global__ void __launch_bounds__(kBandWarps * 32, kBandMinCtas) k_band(const SweepArgs a, int flags) {
   typedef typename CT<T>::C C;
   constexpr int W3 = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   BandSmem<T, N>& S = reinterpret_cast<BandSmem<T, N>*>(smem_raw)[wid];
+  // the band window lives in a per-warp global slot: cached in L1 (which takes the shared
+  // memory it would have used), so more warps fit per SM
+  C* const rw = reinterpret_cast<C*>(a.rwbuf) + ((size_t)blockIdx.x * (blockDim.x >> 5) + wid) * 2 * W3;
   const gbk_sweep_desc& d = a.d;
   const int nbp = (d.n_bands - a.parity + 1) / 2;
   const int64_t ntask = (int64_t)d.n_temps * d.n_walkers * nbp;
@@ -802,13 +811,13 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
       for (int i = lane; i < W3; i += 32)
         for (int ch = 0; ch < 2; ++ch) {
           const longlong2 v = *reinterpret_cast<const longlong2*>(rs_w + 2 * (ch * nb + gw + i));
-          S.rw[ch * W3 + i] = mkc(i2t(v.x, T()) * rs, i2t(v.y, T()) * rs);
+          rw[ch * W3 + i] = mkc(i2t(v.x, T()) * rs, i2t(v.y, T()) * rs);
         }
       __syncwarp();
     } else {
       const C* rho = rho_ptr<T>(a, w, j);
       const C* H = hsum_ptr<T>(a, t, w, b);
-      for (int i = lane; i < 2 * W3; i += 32) S.rw[i] = csub(rho[i], H[i]);
+      for (int i = lane; i < 2 * W3; i += 32) rw[i] = csub(rho[i], H[i]);
       __syncwarp();
     }
     // ---- in-model proposals (Alg. 1)
@@ -837,12 +846,12 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
           const C* hr = cache_ptr<T>(a, cb + k);
           const int oa = band_off<N>(S.src[q].q, gw, a.c);
           const int orr = cached_off<N>(P + k * 8, gw, a.c);
-          const double dll = window_dll<T, N>(a, S.rw, S.ba, oa, hr, orr, gw, pw, lane);
+          const double dll = window_dll<T, N>(a, rw, S.ba, oa, hr, orr, gw, pw, lane);
           const double la = beta * dll + S.lpn[q];
           const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
           if (lane == 0) record(a, ws, 0, t, w, b, k, jp, acc, dll, la, S.th[q], 1, 1);
           if (acc) {
-            apply_change<T, N>(a, S.rw, S.ba, oa, hr, orr, cold, Rw, gw, gs, lane);
+            apply_change<T, N>(a, rw, S.ba, oa, hr, orr, cold, Rw, gw, gs, lane);
             __syncwarp();
             copy_band(cache_ptr<T>(a, cb + k), S.ba, 2 * N, lane);
             if (lane < 8) P[k * 8 + lane] = S.th[q][lane];
@@ -883,12 +892,12 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
           if (E[s]) {
             const C* hr = cache_ptr<T>(a, cb + s);
             const int orr = cached_off<N>(P + s * 8, gw, a.c);
-            const double dll = window_dll<T, N>(a, S.rw, (const C*)nullptr, 0, hr, orr, gw, pw, lane);
+            const double dll = window_dll<T, N>(a, rw, (const C*)nullptr, 0, hr, orr, gw, pw, lane);
             const double la = beta * dll - d.log_occ_odds + S.lpn[q];
             const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
             if (lane == 0) record(a, ws, 2, t, w, b, s, jp, acc, dll, la, P + s * 8, 0, 1);
             if (acc) {
-              apply_change<T, N>(a, S.rw, (const C*)nullptr, 0, hr, orr, cold, Rw, gw, gs, lane);
+              apply_change<T, N>(a, rw, (const C*)nullptr, 0, hr, orr, cold, Rw, gw, gs, lane);
               __syncwarp();
               if (lane == 0) E[s] = 0;
             }
@@ -897,12 +906,12 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_band(const SweepArgs a, int f
           } else {
             gen_band<T, N>(&S.src[q], orb, tw, tobs, S.ba, S.bs, lane);
             const int oa = band_off<N>(S.src[q].q, gw, a.c);
-            const double dll = window_dll<T, N>(a, S.rw, S.ba, oa, (const C*)nullptr, 0, gw, pw, lane);
+            const double dll = window_dll<T, N>(a, rw, S.ba, oa, (const C*)nullptr, 0, gw, pw, lane);
             const double la = beta * dll + d.log_occ_odds + S.lpn[q];
             const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
             if (lane == 0) record(a, ws, 1, t, w, b, s, jp, acc, dll, la, S.th[q], 1, 1);
             if (acc) {
-              apply_change<T, N>(a, S.rw, S.ba, oa, (const C*)nullptr, 0, cold, Rw, gw, gs, lane);
+              apply_change<T, N>(a, rw, S.ba, oa, (const C*)nullptr, 0, cold, Rw, gw, gs, lane);
               copy_band(cache_ptr<T>(a, cb + s), S.ba, 2 * N, lane);
               if (lane < 8) P[s * 8 + lane] = S.th[q][lane];
               __syncwarp();
@@ -1072,14 +1081,15 @@ static int sms_of_device() {
 }
 
 // Warps per CTA (<= kSwWarps) so that the CTA's shared memory fits the SM.
-static int sweep_warps(size_t per_warp) {
+static int sweep_warps(size_t per_warp, int max_warps) {
   int w = (int)((220 * 1024) / (per_warp > 0 ? per_warp : 1));
-  return w < 1 ? 1 : (w > kSwWarps ? kSwWarps : w);
+  return w < 1 ? 1 : (w > max_warps ? max_warps : w);
 }
 
 template <typename K>
-static gbk_status prep(K kernel, size_t per_warp, int64_t items, int* grid, int* threads, size_t* smem) {
-  const int wpc = sweep_warps(per_warp);
+static gbk_status prep(K kernel, size_t per_warp, int64_t items, int* grid, int* threads, size_t* smem,
+                       int max_warps = kSwWarps) {
+  const int wpc = sweep_warps(per_warp, max_warps);
   *threads = wpc * 32;
   *smem = per_warp * wpc;
   if (*smem > 48 * 1024 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem) != cudaSuccess) {
@@ -1163,7 +1173,8 @@ static gbk_status run_half(SweepArgs& a, int flags, cudaStream_t st) {
   if (a.mix && (s = run_proposal<T, N>(g_active_plan, a, st))) return s;
   ev_rec(a.parity, 1, 1, st);
   if (flags & (GBK_SWEEP_INMODEL | GBK_SWEEP_RJ)) {
-    if ((s = prep(k_band<T, N>, sizeof(BandSmem<T, N>), (int64_t)d.n_temps * d.n_walkers * nbp, &grid, &thr, &sm)))
+    if ((s = prep(k_band<T, N>, sizeof(BandSmem<T, N>), (int64_t)d.n_temps * d.n_walkers * nbp, &grid, &thr, &sm,
+                  kBandWarps)))
       return s;
     ev_rec(a.parity, 2, 0, st);
     k_band<T, N><<<grid, thr, sm, st>>>(a, flags);
@@ -1243,12 +1254,15 @@ extern "C" gbk_status gbk_sweep_create(gbk_ctx* ctx, const gbk_sweep_desc* desc,
   if (e == cudaSuccess) e = cudaMalloc(&p->wcache, p->cache_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->hsum, p->hsum_bytes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->setid, (size_t)d.n_temps * d.n_walkers * d.n_bands * sizeof(int32_t));
+  p->rwbuf_bytes = (size_t)sms_of_device() * 64 * 2 * 3 * d.band_bins * csz;   // every warp an SM can hold
+  if (e == cudaSuccess) e = cudaMalloc(&p->rwbuf, p->rwbuf_bytes);
   if (e != cudaSuccess) {
     cudaFree(p->rsnap);
     cudaFree(p->rho);
     cudaFree(p->wcache);
     cudaFree(p->hsum);
     cudaFree(p->setid);
+    cudaFree(p->rwbuf);
     free(p);
     cudaGetLastError();
     return set_error(e == cudaErrorMemoryAllocation ? GBK_ENOMEM : GBK_ECUDA, "gbk_sweep_create: %s",
@@ -1266,6 +1280,7 @@ extern "C" gbk_status gbk_sweep_destroy(gbk_sweep* plan) {
   cudaFree(plan->wcache);
   cudaFree(plan->hsum);
   cudaFree(plan->setid);
+  cudaFree(plan->rwbuf);
   cudaFree(plan->mix);
   cudaFree(plan->xfeat);
   cudaFree(plan->rawbuf);
@@ -1318,6 +1333,7 @@ static SweepArgs make_args(gbk_sweep* plan, double* params, uint8_t* exists, con
   a.wcache = plan->wcache;
   a.hsum = plan->hsum;
   a.setid = plan->setid;
+  a.rwbuf = plan->rwbuf;
   a.n_bp_max = plan->n_bp_max;
   a.n_walkers_r = residual->n_walkers;
   a.frac_bits = residual->frac_bits;
