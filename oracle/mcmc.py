@@ -79,7 +79,13 @@ class SweepConfig:
       fraction ``mdn_inmodel`` of the in-model moves are independence proposals from it.
       rho does not change during the band's pass (it holds the cold chain's sources
       outside band b and all of b's own), so q is one fixed density for every move of the
-      pass and Eq. rj-acceptance uses it as it stands.
+      pass and Eq. rj-acceptance uses it as it stands;
+    * group stretch (optional, the paper's in-model move): ``group`` from ``build_group`` is
+      the stationary group (the cold chain's sources of bands b-1, b, b+1 of every walker,
+      sorted by f0); a fraction ``group_frac`` of the in-model moves are stretch moves
+      Y = X_j + z (X_k - X_j) (Eq. stretch) with X_j drawn uniformly from the
+      ``n_friends`` group members nearest in f0 to X_k, z from g(z) ~ 1/sqrt(z) on
+      [1/a, a]; see ``group_stretch``.
     """
 
     def __init__(self, **kw):
@@ -109,6 +115,10 @@ class SweepConfig:
         self.mdn_raw = kw.get("mdn_raw", None)
         self.mdn_eps = kw.get("mdn_eps", 0.1)
         self.mdn_inmodel = kw.get("mdn_inmodel", 0.0)
+        self.group = kw.get("group", None)
+        self.group_frac = kw.get("group_frac", 0.0)
+        self.n_friends = kw.get("n_friends", 32)
+        self.stretch_a = kw.get("stretch_a", 2.0)
 
     def band_bins(self, b):
         lo = self.band_k0 + b * self.nb
@@ -223,6 +233,88 @@ def mdn_log_q(cfg, raw, b, th):
     return MD.log_q_defensive(raw, MD.to_unit(cfg, b, th), cfg.mdn_eps)
 
 
+# ---------------------------------------------------------------- group stretch
+STRETCH_PERIODS = (None, None, None, TWO_PI, math.pi, None, None, TWO_PI)
+
+
+def build_group(cfg, state):
+    """Stationary group of every band: the cold chain's sources of bands b-1, b, b+1 of all
+    walkers, sorted by f0; list of (f0 array, params array [G][8])."""
+    P, E = state["params"], state["exists"]
+    out = []
+    for b in range(cfg.n_bands):
+        rows = []
+        for bb in (b - 1, b, b + 1):
+            if 0 <= bb < cfg.n_bands:
+                for w in range(cfg.n_walkers):
+                    for s in range(cfg.n_max):
+                        if E[0, w, bb, s]:
+                            rows.append(P[0, w, bb, s])
+        gp = np.array(rows, dtype=np.float64).reshape(-1, 8)
+        order = np.argsort(gp[:, 1], kind="stable")
+        gp = gp[order]
+        out.append((gp[:, 1].copy(), gp))
+    return out
+
+
+def friends_start(fs, f, nf):
+    """Start of the window of the nf group members nearest in f0 to f (fs sorted; nf <= len)."""
+    G = len(fs)
+    lo = int(np.searchsorted(fs, f, side="left")) - 1
+    hi = lo + 1
+    for _ in range(nf):
+        if hi >= G or (lo >= 0 and f - fs[lo] <= fs[hi] - f):
+            lo -= 1
+        else:
+            hi += 1
+    return lo + 1
+
+
+def _wrap_sym(d, period):
+    if d >= 0.5 * period:
+        return d - period
+    if d < -0.5 * period:
+        return d + period
+    return d
+
+
+def group_stretch(cfg, group_b, th, w_j, w_z):
+    """Group stretch (Eq. stretch with a stationary group). Coordinates (ln A, f0, fdot, phi0,
+    psi, cos i, sin b, lambda); periodic differences taken in [-P/2, P/2). Returns
+    (new parameters, ln z) or (new, None) when the move is not reversible as drawn: the
+    auxiliary point X_j is not among the nearest friends of the proposed point, or a
+    stretched periodic difference leaves [-P/2, P/2). The proposal probability of j,
+    1/n_friends both ways, then cancels, and the acceptance is
+    z^(d-1) L'^beta p' / (L^beta p) with d = 8."""
+    fs, gp = group_b
+    G = len(fs)
+    nf = min(cfg.n_friends, G)
+    s0 = friends_start(fs, th[1], nf)
+    j = s0 + PX.ranged(w_j, nf)
+    xj = gp[j]
+    a = cfg.stretch_a
+    z = ((a - 1.0) * PX.u32(w_z) + 1.0) ** 2 / a
+    x = [math.log(th[0])] + list(th[1:])
+    y0 = [math.log(xj[0])] + list(xj[1:])
+    y = []
+    ok = True
+    for c in range(8):
+        per = STRETCH_PERIODS[c]
+        if per is None:
+            y.append(y0[c] + z * (x[c] - y0[c]))
+        else:
+            d = z * _wrap_sym(x[c] - y0[c], per)
+            if not (-0.5 * per <= d < 0.5 * per):
+                ok = False
+            v = y0[c] + d
+            y.append(_wrap(v, per))
+    new = [math.exp(y[0])] + y[1:]
+    if ok:
+        s1 = friends_start(fs, new[1], nf)
+        ok = s1 <= j < s1 + nf
+    return new, (math.log(z) if ok else None)
+
+
 def _rec(kind, t, w, b, slot, seq, acc, parity, dll, la, th, lu):
     """One trace record (the fields of the GPU trace plus ln u)."""
     return {"kind": kind, "t": t, "w": w, "b": b, "slot": slot, "seq": seq, "accepted": bool(acc),
@@ -295,17 +387,24 @@ def band_task(cfg, state, r_snap, rho, t, w, b, parity, sweep, trace):
         k = existing[PX.ranged(words[0], g)]
         th = list(P[t, w, b, k])
         indep = raw is not None and PX.u32(words[35]) < cfg.mdn_inmodel
+        grp = (not indep and cfg.group is not None and len(cfg.group[b][0]) > 0
+               and PX.u32(words[46]) < cfg.group_frac)
+        lnz = 0.0
         if indep:   # independence proposal from the learned mixture
             new = mdn_draw(cfg, raw, b, words[36], words[37], words[38:46])
+        elif grp:   # group stretch: words 1 (friend) and 2 (stretch factor)
+            new, lnz = group_stretch(cfg, cfg.group[b], th, words[1], words[2])
         else:
             new = propose_in_model(cfg, th, words)
         lu = math.log(PX.u53(words[33], words[34])) if PX.u53(words[33], words[34]) > 0 else -math.inf
-        if not in_support(cfg, new, b):
+        if (grp and lnz is None) or not in_support(cfg, new, b):
             trace.append(_rec(0, t, w, b, k, j, False, parity, float("nan"), -math.inf, new, lu))
             continue
         dll = _swap_dll(cfg, rp, psd_w, b, new, th)
         if indep:   # unit coordinates: prior density 1, q(theta) / q(theta') is the Hastings factor
             la = beta * dll + mdn_log_q(cfg, raw, b, th) - mdn_log_q(cfg, raw, b, new)
+        elif grp:   # stretch Jacobian z^(d-1), d = 8 (ln A, f0, fdot and five more)
+            la = beta * dll + dlog_prior(new, th) + 7.0 * lnz
         else:
             la = beta * dll + dlog_prior(new, th)
         acc = lu < la

@@ -138,3 +138,162 @@ def test_prior_only_sweeps_with_learned_proposal_keep_the_prior():
     assert abs(np.mean(occ) - pi) < 4 * math.sqrt(pi * (1 - pi) / n) * 2   # x2: correlated sweeps
     for d in (0, 1, 2, 7):
         assert stats.kstest(u[:, d], "uniform").pvalue > 1e-3, d
+
+
+def test_friends_window_holds_the_nearest_members():
+    g = np.random.default_rng(30)
+    for _ in range(200):
+        G = int(g.integers(1, 60))
+        fs = np.sort(g.uniform(0, 1, G))
+        nf = int(g.integers(1, G + 1))
+        f = float(g.uniform(-0.2, 1.2))
+        s = OM.friends_start(fs, f, nf)
+        assert 0 <= s and s + nf <= G
+        win = set(range(s, s + nf))
+        far_in = max(abs(fs[i] - f) for i in win)
+        near_out = min([abs(fs[i] - f) for i in range(G) if i not in win], default=np.inf)
+        assert far_in <= near_out
+
+
+def test_group_stretch_is_reversible_with_the_same_friend_and_inverse_z():
+    # Y from (X, j, z); then from Y with the same j and 1/z the map returns X (periodic
+    # coordinates included), whenever the move was accepted as reversible.
+    cfg, state, _, _ = small_ensemble(seed=31, n_temps=1, n_walkers=4, n_bands=2, n_max=4, n_per_band=2,
+                                      betas=(1.0,))
+    grp = OM.build_group(cfg, state)
+    g = np.random.default_rng(32)
+    fs, gp = grp[0]
+    n_rev = 0
+    for _ in range(300):
+        th = list(gp[int(g.integers(len(fs)))] + np.array([0, 0.3 * OM.PX.u32(1) * 0, 0, 0.1, 0.1, 0, 0, 0.1]))
+        th[3] %= 2 * math.pi
+        th[4] %= math.pi
+        th[7] %= 2 * math.pi
+        wj, wz = int(g.integers(2 ** 32)), int(g.integers(2 ** 32))
+        new, lnz = OM.group_stretch(cfg, grp[0], th, wj, wz)
+        if lnz is None:
+            continue
+        n_rev += 1
+        nf = min(cfg.n_friends, len(fs))
+        j = OM.friends_start(fs, th[1], nf) + OM.PX.ranged(wj, nf)
+        z = math.exp(lnz)
+        y = [math.log(new[0])] + list(new[1:])
+        xj = [math.log(gp[j][0])] + list(gp[j][1:])
+        back = []
+        for c in range(8):
+            per = OM.STRETCH_PERIODS[c]
+            if per is None:
+                back.append(xj[c] + (y[c] - xj[c]) / z)
+            else:
+                back.append((xj[c] + OM._wrap_sym(y[c] - xj[c], per) / z) % per)
+        back[0] = math.exp(back[0])
+        np.testing.assert_allclose(back, th, rtol=1e-9, atol=1e-12)
+    assert n_rev > 100
+
+
+def test_group_stretch_keeps_a_known_target_stationary():
+    # The move on its own: chains started from exact draws of a known target (independent
+    # normals in the stretch coordinates ln A, f0, fdot, cos i, sin b; uniform phases) take
+    # 8 MH steps each with group-stretch proposals (a fixed group of 40 target draws, 8
+    # friends); the final states must still follow the target. A kernel that does not
+    # leave the target invariant shifts them: dropping or doubling the z^(d-1) factor, or
+    # the reverse-friend condition, planted in the oracle on the CPU, fails this.
+    class C:
+        n_friends, stretch_a = 8, 2.0
+    g = np.random.default_rng(34)
+    mu = np.array([math.log(2e-22), 2.5e-3, 1e-17, 0.0, 0.0, 0.1, -0.2, 0.0])
+    sd = np.array([0.3, 3e-8, 2e-19, 0.0, 0.0, 0.15, 0.1, 0.0])
+    per = OM.STRETCH_PERIODS
+
+    def draw(n):
+        x = g.normal(mu, np.where(sd > 0, sd, 1.0), (n, 8))
+        for c in range(8):
+            if per[c] is not None:
+                x[:, c] = g.uniform(0, per[c], n)
+        return x
+
+    def logp(u):
+        return -0.5 * float(np.sum(((u - mu) / np.where(sd > 0, sd, 1.0)) ** 2 * (sd > 0)))
+
+    gu = draw(40)
+    gu = gu[np.argsort(gu[:, 1])]
+    gp = gu.copy()
+    gp[:, 0] = np.exp(gu[:, 0])
+    group = (gp[:, 1].copy(), gp)
+    starts = draw(3000)
+    final = np.empty_like(starts)
+    moved = 0
+    for i, x in enumerate(starts):
+        th = list(x)
+        th[0] = math.exp(x[0])
+        for _ in range(8):
+            new, lnz = OM.group_stretch(C, group, th, int(g.integers(2 ** 32)), int(g.integers(2 ** 32)))
+            if lnz is None:
+                continue
+            un = np.array([math.log(new[0])] + list(new[1:]))
+            uo = np.array([math.log(th[0])] + list(th[1:]))
+            if math.log(g.uniform()) < logp(un) - logp(uo) + 7.0 * lnz:
+                th = new
+                moved += 1
+        final[i] = [math.log(th[0])] + list(th[1:])
+    assert moved > 3000 * 8 * 0.15
+    for c in (0, 1, 2, 5, 6):
+        assert stats.kstest((final[:, c] - mu[c]) / sd[c], "norm").pvalue > 1e-3, c
+    for c in (3, 4, 7):
+        assert stats.kstest(final[:, c] / per[c], "uniform").pvalue > 1e-3, c
+
+
+def test_nearest_friend_selection_needs_the_reverse_condition():
+    # The friend rule on its own, in one dimension (N(0, 1) target, group of 40 draws, 8
+    # nearest friends, 20 steps from 20000 exact draws): with the reverse condition (the
+    # auxiliary point must also be among the proposed point's friends) the spread stays 1;
+    # without it the spread shrinks (to ~0.97, six standard errors). This pins the
+    # acceptance rule that group_stretch applies.
+    g = np.random.default_rng(1)
+    grp = np.sort(g.normal(0, 1, 40))
+
+    def run(cond):
+        xs = g.normal(0, 1, 20000)
+        for i in range(len(xs)):
+            x = xs[i]
+            for _ in range(20):
+                j = OM.friends_start(grp, x, 8) + int(g.integers(8))
+                z = (g.uniform() + 1.0) ** 2 / 2.0
+                y = grp[j] + z * (x - grp[j])
+                ok = True
+                if cond:
+                    s1 = OM.friends_start(grp, y, 8)
+                    ok = s1 <= j < s1 + 8
+                if ok and math.log(g.uniform()) < 0.5 * (x * x - y * y):
+                    x = y
+            xs[i] = x
+        return xs
+
+    se = 1.0 / math.sqrt(2 * 20000)
+    assert abs(run(True).std() - 1.0) < 3 * se
+    assert run(False).std() < 1.0 - 3 * se
+
+
+def test_prior_only_sweeps_with_group_stretch_keep_the_prior():
+    # beta = 0: the target is the prior. Group stretch moves (70 % of the in-model moves,
+    # 6 friends, a fixed group) must keep the unit-box marginals uniform; dropping the
+    # z^(d-1) factor (planted in the oracle, on the CPU) fails this.
+    from oracle import mdn as MD
+    pi = 0.5
+    cfg, state, _, _ = small_ensemble(seed=33, n_temps=1, n_walkers=2, n_bands=2, n_max=4, n_per_band=2,
+                                      betas=(0.0,), log_occ_odds=math.log(pi / (1 - pi)))
+    cfg.group, cfg.group_frac, cfg.n_friends = OM.build_group(cfg, state), 0.7, 6
+    cfg.props_per_source = 3.0
+    st = copy_state(state)
+    u = []
+    for k in range(50):
+        OM.sweep(cfg, st, k, do_swap=False)
+        if k >= 5:
+            for w in range(cfg.n_walkers):
+                for b in range(cfg.n_bands):
+                    for s in range(cfg.n_max):
+                        if st["exists"][0, w, b, s]:
+                            u.append(MD.to_unit(cfg, b, st["params"][0, w, b, s]))
+    u = np.asarray(u)
+    for d in (0, 2, 3, 5):
+        assert stats.kstest(u[::3, d], "uniform").pvalue > 1e-3, d
