@@ -332,7 +332,7 @@ def run_uneven(torch, L, dev, stream, seed, n_prop=200000, reps=10):
             "proposals_per_s": n_prop / (ms * 1e-3), "ms_per_batch": ms, "per_N": per_n}
 
 
-def run_ess(torch, L, S, step, stats, stream, n_sweeps, flags=0, pairs=None):
+def run_ess(torch, L, S, step, stats, stream, n_sweeps, flags=0, pairs=None, group=None):
     """ESS/s: integrated autocorrelation time of every cold walker's total log-likelihood
     (Eq. like on its residual) over n_sweeps sweeps (first quarter discarded). Optionally
     collects training pairs of the learned proposal after the burn-in (outside the timing)."""
@@ -346,6 +346,8 @@ def run_ess(torch, L, S, step, stats, stream, n_sweeps, flags=0, pairs=None):
     stats.zero_()
     for k in range(n_sweeps):
         e0.record(stream)
+        if group is not None and k % group[2] == 0:   # (fraction, friends, sweeps between rebuilds)
+            L.gbk_sweep_update_group(S["plan"], S["P"], S["E"], group[0], group[1], stream)
         step(flags)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -658,6 +660,17 @@ def run_ours(args):
             from paper_2405_04690_gb300 import proposal as PR
             pairs = PR.PairBuffer(args.mdn_samples)
         ess = run_ess(torch, L, S, step, stats, stream, args.ess_sweeps, pairs=pairs)
+        if args.group_frac > 0:   # the paper's in-model move: group stretch, group rebuilt every 30 sweeps
+            S["P"].copy_(snap[0])
+            S["E"].copy_(snap[1])
+            S["resid"].copy_(snap[2])
+            L.gb_sweep(S["plan"], S["P"], S["E"], S["betas"], S["R"], S["psd"], 1, 0, L.SWEEP_REFRESH, stream=stream)
+            eg = run_ess(torch, L, S, step, stats, stream, args.ess_sweeps,
+                         group=(args.group_frac, args.n_friends, 30))
+            L.gbk_sweep_update_group(S["plan"], S["P"], S["E"], 0.0, 1, stream)
+            eg["group"] = {"frac": args.group_frac, "n_friends": args.n_friends, "rebuild_every_sweeps": 30}
+            eg["ess_gain"] = eg["ess_per_s"] / ess["ess_per_s"]
+            ess["group_stretch"] = eg
         if pairs is not None:
             learned = run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, snap, ess)
         del snap
@@ -786,6 +799,9 @@ def main():
     ap.add_argument("--mdn-eps", type=float, default=0.2, help="prior fraction of the learned proposal")
     ap.add_argument("--mdn-inmodel", type=float, default=0.1, help="fraction of in-model moves drawn from it")
     ap.add_argument("--search-sweeps", type=int, default=10)
+    ap.add_argument("--group-frac", type=float, default=0.5, help="fraction of in-model moves that are group stretches "
+                                                                   "in the group-stretch ESS run (0: skip it)")
+    ap.add_argument("--n-friends", type=int, default=32)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -385,6 +385,21 @@ gbk_status mdn_sample_logpdf(const float* raw, int32_t batch, double eps, const 
 gbk_status gbk_sweep_set_proposal(gbk_sweep* plan, gbk_mdn* net, const float* raw_table, double eps,
                                   double inmodel_frac);
 
+/* Group stretch in-model moves (the paper's in-model proposal, Eq. stretch with a stationary
+ * group): builds every band's stationary group from the current cold chain -- the sources of
+ * bands b-1, b, b+1 of all walkers, sorted by f0 -- and makes a fraction `frac` of the
+ * in-model moves of later gb_sweep calls stretch moves Y = X_j + z (X_k - X_j) in the
+ * coordinates (ln A, f0, fdot, phi0, psi, cos iota, sin beta, lambda), X_j drawn uniformly
+ * from the n_friends group members nearest in f0 to X_k, z from g(z) ~ 1/sqrt(z) on
+ * [1/2, 2], acceptance z^7 (L'/L)^beta p'/p. A draw whose X_j is not also among the
+ * n_friends nearest members of Y (or whose stretched phase difference leaves half a period)
+ * is rejected without a likelihood: the friend choice is then symmetric and the move exact.
+ * The group stays fixed until the next call (the paper rebuilds it every ~30 sweeps).
+ * frac = 0 turns the moves off. Allocates the group on first use (B x 3 W n_max x 72 bytes).
+ *   params, exists  the sweep state (device), as for gb_sweep */
+gbk_status gbk_sweep_update_group(gbk_sweep* plan, const double* params, const uint8_t* exists, double frac,
+                                  int32_t n_friends, void* stream);
+
 /* Training pairs from the current cold chain (band_bins 256): x_out [n_walkers][n_bands]
  * [1024] BF16 features of every band's opened window (as above), u_out [n_walkers]
  * [n_bands][n_max][8] float32 unit coordinates of every cold slot (NaN where empty);

@@ -102,6 +102,7 @@ SIGNATURES = {
     "mdn_train_epoch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, ctypes.c_float, _vp,
                                        _vp]),
     "gbk_sweep_set_proposal": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double]),
+    "gbk_sweep_update_group": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _i32, _vp]),
     "gb_sweep_features": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(GbkResidual), ctypes.POINTER(GbkPsd), _vp, _vp,
                                          _vp]),
 }
@@ -401,6 +402,13 @@ def gbk_sweep_set_proposal(plan, net=None, raw_table=None, eps=0.1, inmodel_frac
     _check(lib().gbk_sweep_set_proposal(plan.handle, net.handle if net is not None else None,
                                         _dev(raw_table, torch.float32, "raw_table") if raw_table is not None else None,
                                         float(eps), float(inmodel_frac)), "gbk_sweep_set_proposal")
+
+
+def gbk_sweep_update_group(plan, params, exists, frac, n_friends=32, stream=None):
+    """Rebuild every band's stationary group from the cold chain; frac of in-model moves become group stretches."""
+    _check(lib().gbk_sweep_update_group(plan.handle, _dev(params, torch.float64, "params"),
+                                        _dev(exists, torch.uint8, "exists"), float(frac), int(n_friends),
+                                        _stream(stream)), "gbk_sweep_update_group")
 
 
 def gb_sweep_features(plan, params, exists, residual, psd, x_out=None, u_out=None, stream=None):

@@ -31,6 +31,13 @@ struct gbk_sweep {
   uint16_t* xfeat;          // BF16 features [W][n_bp_max][1024]
   float* rawbuf;            // network outputs [W][n_bp_max][272]
   void* mix;                // mixture rows [W][n_bp_max] (MixRow of the sweep precision)
+  // group stretch (gbk_sweep_update_group): stationary group of every band, sorted by f0
+  double* grp_f0;           // [B][gmax]
+  double* grp_par;          // [B][gmax][8]
+  int32_t* grp_n;           // [B]
+  int gmax;
+  double grp_frac;
+  int n_friends;
 };
 
 namespace gbk {
@@ -69,6 +76,12 @@ struct SweepArgs {
   // learned proposal: mixture row of every opened (walker, band) or NULL
   const void* mix;
   double mdn_eps, mdn_inmodel;
+  // group stretch: stationary group (NULL when off)
+  const double* grp_f0;
+  const double* grp_par;
+  const int32_t* grp_n;
+  int gmax, n_friends;
+  double grp_frac;
 };
 
 template <typename T> __device__ __forceinline__ const T* orb_of(const gbk_ctx& c, int bi);
@@ -321,6 +334,66 @@ __device__ __forceinline__ double mdn_logq(const SweepArgs& a, const PriorK& pk,
 #pragma unroll
   for (int c = 0; c < kMixDim; ++c) u[c] = (T)ud[c];
   return (double)mix_logq<T>(m, u, (T)a.mdn_eps);
+}
+
+// -------------------------------------------------------------- group stretch
+// Start of the window of the nf stationary-group members nearest in f0 to f (fs sorted, G
+// members, nf <= G): lower bound, then nf steps taking the nearer side (ties to the lower).
+__device__ __forceinline__ int friends_start(const double* fs, int G, double f, int nf) {
+  int lo = 0, hi = G;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (fs[mid] < f) lo = mid + 1; else hi = mid;
+  }
+  int l = lo - 1, h = lo;
+  for (int i = 0; i < nf; ++i) {
+    if (h >= G || (l >= 0 && f - fs[l] <= fs[h] - f)) --l; else ++h;
+  }
+  return l + 1;
+}
+__device__ __forceinline__ double wrap_sym(double d, double period) {
+  if (d >= 0.5 * period) return d - period;
+  if (d < -0.5 * period) return d + period;
+  return d;
+}
+// Stretch move Y = X_j + z (X - X_j) (Eq. stretch) with X_j one of the nf nearest members of
+// band b's stationary group, in the coordinates (ln A, f0, fdot, phi0, psi, cos i, sin b,
+// lambda), periodic differences in [-P/2, P/2). Returns ln z, or NaN when the move is not
+// reversible as drawn (a stretched periodic difference leaves [-P/2, P/2), or X_j is not
+// among the nf nearest members of Y).
+__device__ __noinline__ double group_stretch(const SweepArgs& a, int b, const double* th, uint32_t w_j, uint32_t w_z,
+                                             double* nw) {
+  const double* fs = a.grp_f0 + (int64_t)b * a.gmax;
+  const double* gp = a.grp_par + (int64_t)b * a.gmax * 8;
+  const int G = a.grp_n[b];
+  const int nf = a.n_friends < G ? a.n_friends : G;
+  const int j = friends_start(fs, G, th[1], nf) + (int)ranged(w_j, (uint32_t)nf);
+  const double* xj = gp + (int64_t)j * 8;
+  const double sa = 2.0;   // stretch scale a
+  const double zz = (sa - 1.0) * u32(w_z) + 1.0;
+  const double z = zz * zz / sa;
+  const double TWO_PI = 6.283185307179586, PI = 3.141592653589793;
+  bool ok = true;
+  const double lx = log(th[0]), lj = log(xj[0]);
+  nw[0] = exp(lj + z * (lx - lj));
+  nw[1] = xj[1] + z * (th[1] - xj[1]);
+  nw[2] = xj[2] + z * (th[2] - xj[2]);
+  nw[5] = xj[5] + z * (th[5] - xj[5]);
+  nw[6] = xj[6] + z * (th[6] - xj[6]);
+  const int pc[3] = {3, 4, 7};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int c = pc[q];
+    const double per = c == 4 ? PI : TWO_PI;
+    const double dlt = z * wrap_sym(th[c] - xj[c], per);
+    if (!(dlt >= -0.5 * per && dlt < 0.5 * per)) ok = false;
+    nw[c] = wrap(xj[c] + dlt, per);
+  }
+  if (ok) {
+    const int s1 = friends_start(fs, G, nw[1], nf);
+    ok = s1 <= j && j < s1 + nf;
+  }
+  return ok ? log(z) : nan_d();
 }
 
 // Lanes compute Philox blocks c0 = base + m (m < nblk) into words[4m .. 4m+3].
@@ -685,6 +758,61 @@ __global__ void k_cold_unit(const SweepArgs a, float* __restrict__ u) {
   }
 }
 
+// -------------------------------------------------------------- stationary group
+// Band b's group: every cold-chain source of bands b-1, b, b+1 of all walkers, sorted by
+// (f0, slot index) with a bitonic sort in shared memory (p2 = power of two >= members).
+__global__ void k_group_build(const double* __restrict__ params, const uint8_t* __restrict__ exists,
+                              gbk_sweep_desc d, int gmax, int p2, double* __restrict__ gf0, double* __restrict__ gpar,
+                              int32_t* __restrict__ gn) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* key = reinterpret_cast<double*>(smem_raw);
+  int32_t* idx = reinterpret_cast<int32_t*>(key + p2);
+  __shared__ int count;
+  const int b = blockIdx.x;
+  if (threadIdx.x == 0) count = 0;
+  __syncthreads();
+  const int per_band = d.n_walkers * d.n_max;
+  for (int c = threadIdx.x; c < 3 * per_band; c += blockDim.x) {
+    const int bb = b - 1 + c / per_band;
+    if (bb < 0 || bb >= d.n_bands) continue;
+    const int w = (c % per_band) / d.n_max, s = c % d.n_max;
+    const int64_t slot = ((int64_t)w * d.n_bands + bb) * d.n_max + s;   // cold chain: t = 0
+    if (!exists[slot]) continue;
+    const int i = atomicAdd(&count, 1);
+    if (i < gmax) {
+      key[i] = params[slot * 8 + 1];
+      idx[i] = (int32_t)slot;
+    }
+  }
+  __syncthreads();
+  const int n = count < gmax ? count : gmax;
+  for (int i = n + threadIdx.x; i < p2; i += blockDim.x) {
+    key[i] = INFINITY;
+    idx[i] = 0x7fffffff;
+  }
+  __syncthreads();
+  for (int k = 2; k <= p2; k <<= 1)
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+        const int l = i ^ jj;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const bool gt = key[i] > key[l] || (key[i] == key[l] && idx[i] > idx[l]);
+          if (gt == up) {
+            const double tk = key[i]; key[i] = key[l]; key[l] = tk;
+            const int32_t ti = idx[i]; idx[i] = idx[l]; idx[l] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    gf0[(int64_t)b * gmax + i] = key[i];
+    for (int c = 0; c < 8; ++c) gpar[((int64_t)b * gmax + i) * 8 + c] = params[(int64_t)idx[i] * 8 + c];
+  }
+  if (threadIdx.x == 0) gn[b] = n;
+}
+
 // -------------------------------------------------------------- band task
 // Per-warp shared memory of k_band.
 template <typename T, int N>
@@ -702,7 +830,7 @@ struct BandSmem {
 // waveform generations, and its code must not crowd the instruction cache.
 template <typename T, int N>
 __device__ __noinline__ void prep_inmodel(const SweepArgs& a, const PriorK& pk, BandSmem<T, N>& S, int l, int jp,
-                                          uint32_t tid, int g, const double* P, const BandGeom& bg,
+                                          uint32_t tid, int g, const double* P, int b, const BandGeom& bg,
                                           const MixRow<T>* mrow) {
   const gbk_sweep_desc& d = a.d;
   uint32_t w[48];
@@ -716,19 +844,25 @@ __device__ __noinline__ void prep_inmodel(const SweepArgs& a, const PriorK& pk, 
 #pragma unroll
   for (int c = 0; c < 8; ++c) th[c] = P[k * 8 + c];
   const bool indep = mrow && mix_u32(w[35]) < a.mdn_inmodel;   // independence move from the learned mixture
+  const bool grp = !indep && a.grp_f0 && a.grp_n[b] > 0 && mix_u32(w[46]) < a.grp_frac;   // group stretch
+  double lnz = 0.0;
   if (indep)
     mdn_draw<T>(a, *mrow, bg, w[36], w[37], w + 38, nw);
+  else if (grp)
+    lnz = group_stretch(a, b, th, w[1], w[2], nw);
   else
     propose(d, th, w, nw, T());
   S.lu[l] = log_u(u53(w[33], w[34]), T());
   S.k[l] = k;
-  const bool ok = in_support<T>(pk, bg, nw);
+  const bool ok = !(lnz != lnz) && in_support<T>(pk, bg, nw);   // NaN ln z: not reversible as drawn
   S.supp[l] = ok ? 1 : 0;
 #pragma unroll
   for (int c = 0; c < 8; ++c) S.th[l][c] = nw[c];
   if (ok) {
-    // unit coordinates: prior density 1, so q(theta) / q(theta') is the whole Hastings factor
-    S.lpn[l] = indep ? mdn_logq<T>(a, pk, *mrow, bg, th) - mdn_logq<T>(a, pk, *mrow, bg, nw) : dlog_prior(nw, th, T());
+    // unit coordinates: prior density 1, so q(theta) / q(theta') is the whole Hastings factor;
+    // the stretch adds its Jacobian z^(d-1), d = 8
+    S.lpn[l] = indep ? mdn_logq<T>(a, pk, *mrow, bg, th) - mdn_logq<T>(a, pk, *mrow, bg, nw)
+                     : dlog_prior(nw, th, T()) + (grp ? 7.0 * lnz : 0.0);
     S.src[l] = make_src<T>(nw, 1, 0, a.c.grid.tobs, N);
   }
 }
@@ -833,7 +967,7 @@ __global__ void __launch_bounds__(kBandWarps * 32, kBandMinCtas) k_band(const Sw
       const int n_prop = (int)rint(d.props_per_source * (double)g);
       for (int j0 = 0; j0 < n_prop; j0 += 32) {
         const int cnt = min(32, n_prop - j0);
-        if (lane < cnt) prep_inmodel<T, N>(a, pk, S, lane, j0 + lane, tid, g, P, bg, mrow);
+        if (lane < cnt) prep_inmodel<T, N>(a, pk, S, lane, j0 + lane, tid, g, P, b, bg, mrow);
         __syncwarp();
         for (int q = 0; q < cnt; ++q) {
           const int jp = j0 + q;
@@ -858,7 +992,7 @@ __global__ void __launch_bounds__(kBandWarps * 32, kBandMinCtas) k_band(const Sw
             __syncwarp();
             // later proposals of this batch that move the same source start from the new state
             if (lane > q && lane < cnt && S.k[lane] == k)
-              prep_inmodel<T, N>(a, pk, S, lane, j0 + lane, tid, g, P, bg, mrow);
+              prep_inmodel<T, N>(a, pk, S, lane, j0 + lane, tid, g, P, b, bg, mrow);
           }
           __syncwarp();
         }
@@ -1282,6 +1416,9 @@ extern "C" gbk_status gbk_sweep_destroy(gbk_sweep* plan) {
   cudaFree(plan->setid);
   cudaFree(plan->rwbuf);
   cudaFree(plan->mix);
+  cudaFree(plan->grp_f0);
+  cudaFree(plan->grp_par);
+  cudaFree(plan->grp_n);
   cudaFree(plan->xfeat);
   cudaFree(plan->rawbuf);
   if (plan->have_ev)
@@ -1350,6 +1487,13 @@ static SweepArgs make_args(gbk_sweep* plan, double* params, uint8_t* exists, con
   a.mix = nullptr;
   a.mdn_eps = plan->mdn_eps;
   a.mdn_inmodel = plan->mdn_inmodel;
+  const bool grp = plan->grp_f0 && plan->grp_frac > 0.0;
+  a.grp_f0 = grp ? plan->grp_f0 : nullptr;
+  a.grp_par = grp ? plan->grp_par : nullptr;
+  a.grp_n = grp ? plan->grp_n : nullptr;
+  a.gmax = plan->gmax;
+  a.n_friends = plan->n_friends;
+  a.grp_frac = plan->grp_frac;
   return a;
 }
 
@@ -1471,4 +1615,40 @@ extern "C" gbk_status gb_sweep_features(gbk_sweep* plan, const double* params, c
   cudaStream_t st = (cudaStream_t)stream;
   return plan->d.precision == GBK_MIXED ? features_impl<float>(plan, a, x_out, u_out, st)
                                         : features_impl<double>(plan, a, x_out, u_out, st);
+}
+
+extern "C" gbk_status gbk_sweep_update_group(gbk_sweep* plan, const double* params, const uint8_t* exists,
+                                             double frac, int32_t n_friends, void* stream) {
+  if (!plan) return set_error(GBK_EINVAL, "gbk_sweep_update_group: null plan");
+  if (!(frac >= 0.0 && frac <= 1.0) || n_friends < 1)
+    return set_error(GBK_EINVAL, "gbk_sweep_update_group: frac must lie in [0, 1] and n_friends >= 1");
+  plan->grp_frac = frac;
+  plan->n_friends = n_friends;
+  if (frac == 0.0) return GBK_OK;
+  if (!params || !exists) return set_error(GBK_EINVAL, "gbk_sweep_update_group: null device pointer");
+  const gbk_sweep_desc& d = plan->d;
+  const int gmax = 3 * d.n_walkers * (d.n_max > 0 ? d.n_max : 1);
+  int p2 = 1;
+  while (p2 < gmax) p2 <<= 1;
+  const size_t smem = (size_t)p2 * (sizeof(double) + sizeof(int32_t));
+  if (smem > 200 * 1024)
+    return set_error(GBK_ENOTIMPL, "gbk_sweep_update_group: group of %d members exceeds the sort's shared memory", gmax);
+  if (!plan->grp_f0) {
+    cudaError_t e = cudaMalloc((void**)&plan->grp_f0, (size_t)d.n_bands * gmax * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&plan->grp_par, (size_t)d.n_bands * gmax * 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&plan->grp_n, (size_t)d.n_bands * sizeof(int32_t));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(GBK_ENOMEM, "gbk_sweep_update_group: %s", cudaGetErrorString(e));
+    }
+    plan->gmax = gmax;
+  }
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_group_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(GBK_ECUDA, "gbk_sweep_update_group: cannot set shared memory size");
+  }
+  k_group_build<<<d.n_bands, 256, smem, (cudaStream_t)stream>>>(params, exists, d, gmax, p2, plan->grp_f0,
+                                                                plan->grp_par, plan->grp_n);
+  return check_launch("gbk_sweep_update_group");
 }

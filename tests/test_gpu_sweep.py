@@ -22,12 +22,13 @@ pytestmark = pytest.mark.gpu
 ALL = 1 | 2 | 4
 
 
-def _gpu_sweep(torch, cfg, state, precision, sweeps=1, flags=ALL, trace_cap=20000, proposal=None):
+def _gpu_sweep(torch, cfg, state, precision, sweeps=1, flags=ALL, trace_cap=20000, proposal=None, group=None):
     from paper_2405_04690_gb300 import _lib as L
     dev = torch.device("cuda")
     ctx = L.Context(cfg.tobs, 15.0, cfg.k0, cfg.n_bins)
     plan = L.SweepPlan(ctx, cfg.n_temps, cfg.n_walkers, cfg.n_bands, cfg.n_max, NB, cfg.band_k0, cfg.sigma,
-                       L.PRECISION[precision], log_occ_odds=cfg.log_occ_odds, f_min=cfg.f_min, f_max=cfg.f_max)
+                       L.PRECISION[precision], log_occ_odds=cfg.log_occ_odds, f_min=cfg.f_min, f_max=cfg.f_max,
+                       props_per_source=cfg.props_per_source)
     P = torch.from_numpy(state["params"].copy()).to(dev)
     E = torch.from_numpy(state["exists"].astype(np.uint8)).to(dev)
     R = torch.from_numpy(state["resid"].copy()).to(dev)
@@ -39,6 +40,8 @@ def _gpu_sweep(torch, cfg, state, precision, sweeps=1, flags=ALL, trace_cap=2000
     if proposal is not None:
         L.gbk_sweep_set_proposal(plan, **proposal)
         flags |= L.SWEEP_MDN
+    if group is not None:   # (fraction, friends): stationary group from the initial state
+        L.gbk_sweep_update_group(plan, P, E, group[0], group[1])
     for k in range(sweeps):
         L.gb_sweep(plan, P, E, betas, L.residual_struct(R, FRAC), L.psd_struct(psdp), key64(cfg), k,
                    flags | (L.SWEEP_REFRESH if k == 0 else 0), trace=(rec, trace_cap, cnt), stats=stats)
@@ -321,3 +324,32 @@ def test_sweep_with_network_equals_sweep_with_its_table():
     assert ordered(t1) == ordered(t2)
     assert np.array_equal(s1, s2)
     net.close()
+
+
+def test_sweep_fp64_with_group_stretch_matches_oracle():
+    # Both sides build the stationary group from the initial state; 60 % of the in-model
+    # moves are group stretches with 4 friends; every decision identical.
+    torch = torch_cuda()
+    cfg, state, _, _ = small_ensemble(seed=17)
+    cfg.group, cfg.group_frac, cfg.n_friends = OM.build_group(cfg, state), 0.6, 4
+    cfg.props_per_source = 3.0
+    ora = copy_state(state)
+    trace = OM.sweep(cfg, ora, 0)
+    out, gtr, stats = _gpu_sweep(torch, cfg, state, "fp64", group=(0.6, 4))
+    g, o = _index(gtr, trace)
+    assert set(g) == set(o), (len(g), len(o))
+    worst = 0.0
+    for k, ro in o.items():
+        rg = g[k]
+        assert bool(rg["accepted"]) == ro["accepted"], (k, rg["log_alpha"], ro["log_alpha"], ro["lu"])
+        if ro["kind"] != 3:
+            np.testing.assert_allclose(rg["params"], ro["params"], rtol=1e-12, atol=1e-300)
+            if np.isfinite(ro["log_alpha"]):
+                assert abs(rg["log_alpha"] - ro["log_alpha"]) < 1e-6 * (1 + abs(ro["log_alpha"]))
+        if np.isfinite(ro["dlogl"]):
+            worst = max(worst, abs(rg["dlogl"] - ro["dlogl"]))
+    assert worst < 1e-7, worst
+    assert np.array_equal(out["exists"], ora["exists"])
+    # group moves happened and some were accepted
+    moved = [r for r in trace if r["kind"] == 0 and r["accepted"]]
+    assert len(moved) > 0
