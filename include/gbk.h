@@ -187,6 +187,51 @@ gbk_status total_loglike(gbk_ctx* ctx, const float* residual, const double* psd_
                          int32_t n_walkers, double* logl, void* stream);
 
 
+/* ------------------------------------------------------------------ noise PSD and foreground
+ * Per-channel instrument noise plus the Galactic foreground (Sec. III, Eq. psd; Sec. III.A) and
+ * the PSD module's sampler (Sec. V.B). A PSD walker has 9 float64 parameters:
+ *   sqrt(S_oms,A), sqrt(S_acc,A), sqrt(S_oms,E), sqrt(S_acc,E), A_fg, alpha, f_k [Hz], s1, s2
+ * and channel ch has S_ch = S_n(sqrt(S_oms,ch), sqrt(S_acc,ch)) + S_fg with
+ *   S_fg = 6 x^2 sin^2 x (A_fg / 2) f^(-7/3) exp(-s1 f^alpha) [1 + tanh(-s2 (f - f_k))],
+ * shared by both channels (the paper's parametrisation).
+ */
+
+/* Per-channel PSD values s_out [W][2][n_bins] float64 (or NULL) for psd_params [W][9]. */
+gbk_status psd_eval_fg(gbk_ctx* ctx, const double* psd_params, int32_t n_walkers, double* s_out, void* stream);
+
+/* Eq. like with the per-channel PSD of psd_params [n][9] for n entries: entry i uses residual
+ * resid_index[i] of residual [n_resid][2][n_bins][2] float32 (resid_index NULL: entry i uses
+ * residual i). Entries that share a residual and sit next to each other (groups of 4) read it
+ * once. Per-bin terms in float32 (the foreground exponent with the accurate expf), sums as
+ * in total_loglike. Uses the context scratch (order concurrent calls on one stream). */
+gbk_status total_loglike_fg(gbk_ctx* ctx, const float* residual, int32_t n_resid, const double* psd_params,
+                            const int32_t* resid_index, int32_t n, double* logl, void* stream);
+
+/* PSD sampler: n_temps x n_walkers PSD walkers; walker w at every temperature uses residual w.
+ * Sampled coordinates v = (ln of the 4 noise amplitudes, ln A_fg, alpha, f_k, s1, s2) with a
+ * uniform prior on the box [lo, hi]. */
+typedef struct gbk_psd_desc {
+  int32_t n_temps, n_walkers;  /* n_walkers even */
+  double lo[9], hi[9];         /* prior box in v */
+  double stretch_a;            /* stretch scale a > 1 (2 in the paper's sampler library) */
+} gbk_psd_desc;
+
+typedef struct gbk_psd_plan gbk_psd_plan;
+gbk_status gbk_psd_plan_create(gbk_ctx* ctx, const gbk_psd_desc* desc, gbk_psd_plan** out_plan);
+gbk_status gbk_psd_plan_destroy(gbk_psd_plan* plan);
+
+/* One sweep: stretch moves (Eq. stretch) of walkers [0, W/2) then [W/2, W) at every
+ * temperature, the partner drawn from the other half, z ~ 1/sqrt(z) on [1/a, a], acceptance
+ * z^8 (L_Y / L_X)^beta (box prior); then swaps between temperatures t and t-1 of the same
+ * walker from the top down (Eq. temp-orig: the residual is shared). Philox4x32-10 counters:
+ * stretch of walker k at temperature t in half h: (t W + k, h, 5, sweep_index), words 0
+ * partner, 1 z, 2-3 ln u; swap (t, w, 6, sweep_index), words 0-1 ln u.
+ *   params [T][W][9], logl [T][W] (the current ln L of each walker, kept up to date) in/out;
+ *   residual [W][2][n_bins][2] float32; betas [T]; stats [2][2] int64 added to (stretch,
+ *   swap) x (proposed, accepted), or NULL. Allocates nothing. */
+gbk_status gb_psd_sweep(gbk_psd_plan* plan, double* params, double* logl, const float* residual,
+                        const double* betas, uint64_t key, uint32_t sweep_index, int64_t* stats, void* stream);
+
 /* ------------------------------------------------------------------ ensemble sweep
  * One sweep of the GB sampler over an ensemble of n_temps x n_walkers chains whose
  * sources are grouped by sub-band (Sec. V.D): odd sub-bands first, then even ones;

@@ -46,6 +46,11 @@ class GbkSweepDesc(ctypes.Structure):
                 ("f_max", ctypes.c_double), ("precision", _i32)]
 
 
+class GbkPsdDesc(ctypes.Structure):
+    _fields_ = [("n_temps", _i32), ("n_walkers", _i32), ("lo", ctypes.c_double * 9), ("hi", ctypes.c_double * 9),
+                ("stretch_a", ctypes.c_double)]
+
+
 class GbkTraceRec(ctypes.Structure):
     _fields_ = [("kind", _i32), ("t", _i32), ("w", _i32), ("b", _i32), ("slot", _i32), ("seq", _i32),
                 ("accepted", _i32), ("parity", _i32), ("dlogl", ctypes.c_double), ("log_alpha", ctypes.c_double),
@@ -102,6 +107,11 @@ SIGNATURES = {
     "mdn_train_epoch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, ctypes.c_float, _vp,
                                        _vp]),
     "gbk_sweep_set_proposal": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double]),
+    "psd_eval_fg": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
+    "total_loglike_fg": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp]),
+    "gbk_psd_plan_create": (ctypes.c_int, [_vp, ctypes.POINTER(GbkPsdDesc), ctypes.POINTER(_vp)]),
+    "gbk_psd_plan_destroy": (ctypes.c_int, [_vp]),
+    "gb_psd_sweep": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp]),
     "gbk_sweep_update_group": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _i32, _vp]),
     "gb_sweep_features": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(GbkResidual), ctypes.POINTER(GbkPsd), _vp, _vp,
                                          _vp]),
@@ -418,3 +428,54 @@ def gb_sweep_features(plan, params, exists, residual, psd, x_out=None, u_out=Non
                                    _dev(x_out, torch.bfloat16, "x_out") if x_out is not None else None,
                                    _dev(u_out, torch.float32, "u_out") if u_out is not None else None,
                                    _stream(stream)), "gb_sweep_features")
+
+
+# ------------------------------------------------------------------ noise PSD and foreground
+def psd_eval_fg(ctx, psd_params, s_out, stream=None):
+    """Per-channel PSD [W][2][n_bins] float64 of the 9-parameter model."""
+    _check(lib().psd_eval_fg(ctx.handle, _dev(psd_params, torch.float64, "psd_params"), int(psd_params.shape[0]),
+                             _dev(s_out, torch.float64, "s_out") if s_out is not None else None, _stream(stream)),
+           "psd_eval_fg")
+
+
+def total_loglike_fg(ctx, residual, psd_params, logl, resid_index=None, stream=None):
+    """Eq. like for entries psd_params [n][9] against residual [n_resid][2][n_bins][2] float32."""
+    _check(lib().total_loglike_fg(ctx.handle, _dev(residual, torch.float32, "residual"), int(residual.shape[0]),
+                                  _dev(psd_params, torch.float64, "psd_params"),
+                                  _dev(resid_index, torch.int32, "resid_index") if resid_index is not None else None,
+                                  int(psd_params.shape[0]), _dev(logl, torch.float64, "logl"), _stream(stream)),
+           "total_loglike_fg")
+
+
+class PsdPlan:
+    """Owns a gbk_psd_plan (proposal buffers and partial sums of the PSD sampler)."""
+
+    def __init__(self, ctx, n_temps, n_walkers, lo, hi, stretch_a=2.0):
+        d = GbkPsdDesc()
+        d.n_temps, d.n_walkers = int(n_temps), int(n_walkers)
+        for i in range(9):
+            d.lo[i], d.hi[i] = float(lo[i]), float(hi[i])
+        d.stretch_a = float(stretch_a)
+        self.desc = d
+        h = _vp()
+        _check(lib().gbk_psd_plan_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)), "gbk_psd_plan_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().gbk_psd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gb_psd_sweep(plan, params, logl, residual, betas, key, sweep_index, stats=None, stream=None):
+    _check(lib().gb_psd_sweep(plan.handle, _dev(params, torch.float64, "params"), _dev(logl, torch.float64, "logl"),
+                              _dev(residual, torch.float32, "residual"), _dev(betas, torch.float64, "betas"),
+                              ctypes.c_uint64(int(key)), ctypes.c_uint32(int(sweep_index)),
+                              _dev(stats, torch.int64, "stats") if stats is not None else None, _stream(stream)),
+           "gb_psd_sweep")

@@ -112,6 +112,9 @@ extern "C" gbk_status gbk_destroy(gbk_ctx* ctx) {
   cudaFree(ctx->rho_f);
   cudaFree(ctx->iq_d);
   cudaFree(ctx->rho_d);
+  cudaFree(ctx->fg_lnf);
+  cudaFree(ctx->fg_f);
+  cudaFree(ctx->fg_c);
   cudaFree(ctx->err);
   cudaFree(ctx->scratch);
   free(ctx);
@@ -159,7 +162,7 @@ extern "C" gbk_status gbk_create(gbk_ctx** out_ctx, const gbk_grid* grid) {
   }
   const int64_t nb = grid->n_bins;
   std::vector<double> q(nb), pa(nb), iq(nb), rho(nb);
-  std::vector<float> iqf(nb), rhof(nb);
+  std::vector<float> iqf(nb), rhof(nb), lnff(nb), ff(nb), fgc(nb);
   double s = 0.0, comp = 0.0;  // compensated sum of ln Q
   for (int64_t i = 0; i < nb; ++i) {
     const double f = (double)(grid->k0 + i) / grid->tobs;
@@ -168,6 +171,10 @@ extern "C" gbk_status gbk_create(gbk_ctx** out_ctx, const gbk_grid* grid) {
     iq[i] = ldexp(1.0 / q[i], -2 * kStrainExp);
     iqf[i] = (float)iq[i];
     rhof[i] = (float)rho[i];
+    const double x = 2.0 * M_PI * f * kLc, sx = sin(x);
+    lnff[i] = (float)log(f);
+    ff[i] = (float)f;
+    fgc[i] = (float)(log(6.0 * x * x * sx * sx) - log(q[i]) - (7.0 / 3.0) * log(f));
     const double y = log(q[i]) - comp;
     const double t = s + y;
     comp = (t - s) - y;
@@ -180,6 +187,9 @@ extern "C" gbk_status gbk_create(gbk_ctx** out_ctx, const gbk_grid* grid) {
   if (e == cudaSuccess) e = upload(&c->rho_d, rho.data(), nb * sizeof(double));
   if (e == cudaSuccess) e = upload(&c->iq_f, iqf.data(), nb * sizeof(float));
   if (e == cudaSuccess) e = upload(&c->rho_f, rhof.data(), nb * sizeof(float));
+  if (e == cudaSuccess) e = upload(&c->fg_lnf, lnff.data(), nb * sizeof(float));
+  if (e == cudaSuccess) e = upload(&c->fg_f, ff.data(), nb * sizeof(float));
+  if (e == cudaSuccess) e = upload(&c->fg_c, fgc.data(), nb * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(int));
   if (e == cudaSuccess) {

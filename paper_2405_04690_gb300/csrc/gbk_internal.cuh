@@ -58,6 +58,11 @@ struct gbk_ctx {
   double* iq_d;
   double* rho_d;
   double sum_lnq;      // sum_k ln Q_k over the window, float64
+  // Galactic-foreground shape over the window (Sec. III.A): ln f, the float32 frequency and
+  // fgc = ln(6 x^2 sin^2 x / Q) - (7/3) ln f, so S_fg / Q = A_fg exp(fgc - s1 f^alpha - softplus(2 s2 (f - f_k)))
+  float* fg_lnf;
+  float* fg_f;
+  float* fg_c;
   int* err;            // device error word
   // scratch for cross-block partial sums of total_loglike
   double* scratch;

@@ -1,0 +1,409 @@
+// Per-channel instrument noise plus the Galactic foreground (Sec. III, Eq. psd; Sec. III.A),
+// its full log-likelihood pass (Eq. like), and the PSD module's sampler (Sec. V.B): regular
+// stretch moves over walkers (Eq. stretch), swaps between neighbouring temperatures of the
+// same walker index, which share one residual (Eq. temp-orig).
+//
+// Parameters of one PSD walker (float64 [9]): sqrt(S_oms,A), sqrt(S_acc,A), sqrt(S_oms,E),
+// sqrt(S_acc,E), A_fg, alpha, f_k, s1, s2. Per bin and channel
+//   S_ch = S_oms,ch Q (1 + (S_acc,ch / S_oms,ch) rho + g / S_oms,ch),
+//   g = S_fg / Q = A_fg exp(fgc - s1 f^alpha - softplus(2 s2 (f - f_k))),
+// with the context's tables Q, rho = P/Q and fgc = ln(6 x^2 sin^2 x / Q) - (7/3) ln f
+// (since (1 + tanh(-y)) = 2 / (1 + e^(2y)) and (A_fg / 2) 2 = A_fg).
+#include <math.h>
+
+#include "gbk_internal.cuh"
+#include "gbk_philox.cuh"
+#include "gbk_reduce.cuh"
+
+namespace gbk {
+
+constexpr int kFgThreads = 256;
+constexpr int kFgChunk = 4096;
+constexpr int kFgEntries = 4;   // PSD walkers per block (share one residual load when they share a residual)
+constexpr int kPsdDim = 9;
+
+size_t total_loglike_scratch_bytes(int64_t n_bins);
+
+struct FgEntry {
+  float aw_a, aw_e;     // S_acc / S_oms per channel
+  float k_a, k_e;       // A_fg / S_oms per channel (x 2^0: g and S_oms share the 2^128 scale of Q)
+  float alpha, s1, s2x2, fk;
+};
+
+__device__ __forceinline__ FgEntry fg_entry(const double* p) {
+  FgEntry e;
+  const double so_a = p[0] * p[0], sa_a = p[1] * p[1], so_e = p[2] * p[2], sa_e = p[3] * p[3];
+  e.aw_a = (float)(sa_a / so_a);
+  e.aw_e = (float)(sa_e / so_e);
+  e.k_a = (float)(p[4] / so_a);
+  e.k_e = (float)(p[4] / so_e);
+  e.alpha = (float)p[5];
+  e.fk = (float)p[6];
+  e.s1 = (float)p[7];
+  e.s2x2 = (float)(2.0 * p[8]);
+  return e;
+}
+
+// softplus(x) = ln(1 + e^x), without overflow
+__device__ __forceinline__ float softplus(float x) { return fmaxf(x, 0.f) + log1pf(expf(-fabsf(x))); }
+
+// One block: bins [chunk * kFgChunk, +kFgChunk) of entries [eg, eg + kFgEntries).
+// part[(chunk * nel + e) * 3 + {0, 1, 2}] = sum |R_A|^2 2^128 iq / u_A, the same for E,
+// sum (ln u_A + ln u_E); compensated float32 per thread, float64 across the block.
+__global__ void __launch_bounds__(kFgThreads, 3)
+k_fg_part(const float* __restrict__ R, const float* __restrict__ iq, const float* __restrict__ rho,
+          const float* __restrict__ lnf, const float* __restrict__ ff, const float* __restrict__ fgc,
+          const double* __restrict__ pp, const int32_t* __restrict__ ridx, int32_t n_resid, int32_t e0, int32_t nel,
+          int64_t nb, double* __restrict__ part, int* err) {
+  const int chunk = blockIdx.x;
+  const int eg = blockIdx.y * kFgEntries;
+  const int64_t kbeg = (int64_t)chunk * kFgChunk;
+  const int64_t kend = min(kbeg + (int64_t)kFgChunk, nb);
+  __shared__ FgEntry s_e[kFgEntries];
+  __shared__ int s_r[kFgEntries];
+  if (threadIdx.x < kFgEntries) {
+    const int el = eg + threadIdx.x;
+    const int e = e0 + (el < nel ? el : 0);
+    s_e[threadIdx.x] = fg_entry(pp + (int64_t)e * kPsdDim);
+    int r = ridx ? ridx[e] : e;
+    if (r < 0 || r >= n_resid) {   // bad residual index: error bit, read residual 0 instead
+      atomicOr(err, kErrWalker);
+      r = 0;
+    }
+    s_r[threadIdx.x] = r;
+  }
+  __syncthreads();
+  FgEntry ent[kFgEntries];
+  const float* rw[kFgEntries];
+  bool act[kFgEntries], same[kFgEntries];
+#pragma unroll
+  for (int j = 0; j < kFgEntries; ++j) {
+    ent[j] = s_e[j];
+    act[j] = eg + j < nel;
+    rw[j] = R + (int64_t)s_r[j] * 2 * nb * 2;
+    same[j] = j > 0 && s_r[j] == s_r[j - 1];   // entries of one residual read it once
+  }
+  CompF sqa[kFgEntries], sqe[kFgEntries], sl[kFgEntries];
+#pragma unroll
+  for (int j = 0; j < kFgEntries; ++j) { sqa[j].init(); sqe[j].init(); sl[j].init(); }
+  const float up = 18446744073709551616.0f;  // 2^64
+  for (int64_t k = kbeg + threadIdx.x; k < kend; k += kFgThreads) {
+    const float iqk = __ldg(iq + k), rhk = __ldg(rho + k), lf = __ldg(lnf + k), fk = __ldg(ff + k), c = __ldg(fgc + k);
+    float2 a = make_float2(0.f, 0.f), e = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < kFgEntries; ++j) {
+      if (!act[j]) continue;
+      if (!same[j]) {
+        a = __ldcs(reinterpret_cast<const float2*>(rw[j] + 2 * k));
+        e = __ldcs(reinterpret_cast<const float2*>(rw[j] + 2 * (nb + k)));
+      }
+      // accurate expf: the exponent reaches ~50, where the fast approximation's error would
+      // show in S_fg
+      const float g = expf(c - ent[j].s1 * expf(ent[j].alpha * lf) - softplus(ent[j].s2x2 * (fk - ent[j].fk)));
+      const float ua = fmaf(ent[j].aw_a, rhk, 1.0f) + g * ent[j].k_a;
+      const float ue = fmaf(ent[j].aw_e, rhk, 1.0f) + g * ent[j].k_e;
+      const float ax = a.x * up, ay = a.y * up, ex = e.x * up, ey = e.y * up;
+      sqa[j].add((ax * ax + ay * ay) * iqk * __frcp_rn(ua));
+      sqe[j].add((ex * ex + ey * ey) * iqk * __frcp_rn(ue));
+      sl[j].add(logf(ua) + logf(ue));
+    }
+  }
+  __shared__ double red[kFgThreads / 32][kFgEntries][3];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < kFgEntries; ++j) {
+    const double x0 = sqa[j].warp_total(), x1 = sqe[j].warp_total(), x2 = sl[j].warp_total();
+    if (lane == 0) { red[wid][j][0] = x0; red[wid][j][1] = x1; red[wid][j][2] = x2; }
+  }
+  __syncthreads();
+  if (threadIdx.x < kFgEntries * 3) {
+    const int j = threadIdx.x / 3, which = threadIdx.x % 3;
+    if (eg + j < nel) {
+      double s = 0.0;
+      for (int w = 0; w < kFgThreads / 32; ++w) s += red[w][j][which];
+      part[((int64_t)chunk * nel + eg + j) * 3 + which] = s;
+    }
+  }
+}
+
+// Eq. like per entry from the chunk partials (fixed order).
+__global__ void k_fg_final(const double* __restrict__ part, int nchunks, const double* __restrict__ pp, int32_t e0,
+                           int32_t nel, int64_t nb, double df, double sum_lnq, double* __restrict__ logl) {
+  const int el = blockIdx.x * blockDim.x + threadIdx.x;
+  if (el >= nel) return;
+  const int e = e0 + el;
+  double qa = 0.0, qe = 0.0, l = 0.0;
+  for (int c = 0; c < nchunks; ++c) {
+    qa += part[((int64_t)c * nel + el) * 3];
+    qe += part[((int64_t)c * nel + el) * 3 + 1];
+    l += part[((int64_t)c * nel + el) * 3 + 2];
+  }
+  const double* p = pp + (int64_t)e * kPsdDim;
+  const double so_a = p[0] * p[0], so_e = p[2] * p[2];
+  logl[e] = -0.5 * 4.0 * df * (qa / so_a + qe / so_e) -
+            ((double)nb * (log(so_a) + log(so_e)) + 2.0 * sum_lnq + l);
+}
+
+static gbk_status fg_loglike(gbk_ctx* ctx, const float* residual, int32_t n_resid, const double* pp,
+                             const int32_t* ridx, int32_t n, double* logl, double* scratch, int64_t max_entries,
+                             cudaStream_t st) {
+  const int64_t nb = ctx->grid.n_bins;
+  const int nchunks = (int)((nb + kFgChunk - 1) / kFgChunk);
+  for (int32_t e0 = 0; e0 < n; e0 += (int32_t)max_entries) {
+    const int32_t nel = (int32_t)(n - e0 < max_entries ? n - e0 : max_entries);
+    dim3 grid(nchunks, (nel + kFgEntries - 1) / kFgEntries);
+    k_fg_part<<<grid, kFgThreads, 0, st>>>(residual, ctx->iq_f, ctx->rho_f, ctx->fg_lnf, ctx->fg_f, ctx->fg_c, pp, ridx,
+                                           n_resid, e0, nel, nb, scratch, ctx->err);
+    k_fg_final<<<(nel + 127) / 128, 128, 0, st>>>(scratch, nchunks, pp, e0, nel, nb, 1.0 / ctx->grid.tobs,
+                                                 ctx->sum_lnq, logl);
+  }
+  return check_launch("total_loglike_fg");
+}
+
+// Per-channel PSD values [W][2][n] (float64) of the 9-parameter model.
+__global__ void k_psd_eval_fg(const double* __restrict__ q, const double* __restrict__ p, const double* __restrict__ pp,
+                              int32_t nw, int64_t k0, int64_t nb, double tobs, double* __restrict__ out) {
+  const int64_t total = (int64_t)nw * nb;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = i / nb, k = i - w * nb;
+    const double* t = pp + w * kPsdDim;
+    const double f = (double)(k0 + k) / tobs;
+    const double x = 2.0 * 3.141592653589793 * f * kLc, sx = sin(x);
+    const double hfg = 0.5 * t[4] * pow(f, -7.0 / 3.0) * exp(-t[7] * pow(f, t[5])) * (1.0 + tanh(-t[8] * (f - t[6])));
+    const double sfg = 6.0 * x * x * sx * sx * hfg;
+    out[(w * 2 + 0) * nb + k] = t[0] * t[0] * q[k] + t[1] * t[1] * p[k] + sfg;
+    out[(w * 2 + 1) * nb + k] = t[2] * t[2] * q[k] + t[3] * t[3] * p[k] + sfg;
+  }
+}
+
+// -------------------------------------------------------------- PSD sampler
+struct PsdArgs {
+  gbk_psd_desc d;
+  double* params;        // [T][W][9]
+  double* logl;          // [T][W]
+  double* prop;          // [T * W/2][9] proposals of one half, entry e = k_local * T + t
+  double* prop_logl;     // [T * W/2]
+  double* lnz;           // [T * W/2]: ln z, or NaN when outside the prior box
+  int32_t* ridx;         // [T * W/2] residual index of each entry
+  const double* betas;   // [T]
+  uint32_t k0, k1, sweep;
+  long long* stats;      // [2][2]: stretch, swap (proposed, accepted)
+};
+
+__device__ __forceinline__ void to_v(const double* p, double* v) {
+  for (int c = 0; c < 5; ++c) v[c] = log(p[c]);
+  for (int c = 5; c < kPsdDim; ++c) v[c] = p[c];
+}
+__device__ __forceinline__ void from_v(const double* v, double* p) {
+  for (int c = 0; c < 5; ++c) p[c] = exp(v[c]);
+  for (int c = 5; c < kPsdDim; ++c) p[c] = v[c];
+}
+
+// Stretch proposals of half h: Y = X_j + z (X_k - X_j), partner j from the other half.
+__global__ void k_psd_propose(PsdArgs a, int h) {
+  const int T = a.d.n_temps, W = a.d.n_walkers, half = W / 2;
+  const int n = T * half;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int kl = e / T, t = e % T;
+  const int k = h * half + kl;
+  const U4 wv = philox4x32_10((uint32_t)(t * W + k), (uint32_t)h, 5u, a.sweep, a.k0, a.k1);
+  const int j = (1 - h) * half + (int)ranged(wv.x, (uint32_t)half);
+  const double zz = (a.d.stretch_a - 1.0) * u32(wv.y) + 1.0;
+  const double z = zz * zz / a.d.stretch_a;
+  double xk[kPsdDim], xj[kPsdDim], y[kPsdDim];
+  to_v(a.params + ((int64_t)t * W + k) * kPsdDim, xk);
+  to_v(a.params + ((int64_t)t * W + j) * kPsdDim, xj);
+  bool in = true;
+  for (int c = 0; c < kPsdDim; ++c) {
+    y[c] = xj[c] + z * (xk[c] - xj[c]);
+    if (!(y[c] >= a.d.lo[c] && y[c] <= a.d.hi[c])) in = false;
+  }
+  double* pr = a.prop + (int64_t)e * kPsdDim;
+  if (in) {
+    from_v(y, pr);
+  } else {   // evaluate the current point instead (finite); the move is rejected
+    for (int c = 0; c < kPsdDim; ++c) pr[c] = a.params[((int64_t)t * W + k) * kPsdDim + c];
+  }
+  a.lnz[e] = in ? log(z) : __longlong_as_double(0x7ff8000000000000LL);
+  a.ridx[e] = k;
+}
+
+// Accept or reject every proposal of half h: ln u < beta_t (lnL_Y - lnL_X) + (d - 1) ln z.
+__global__ void k_psd_accept(PsdArgs a, int h) {
+  const int T = a.d.n_temps, W = a.d.n_walkers, half = W / 2;
+  const int n = T * half;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int kl = e / T, t = e % T;
+  const int k = h * half + kl;
+  const U4 wv = philox4x32_10((uint32_t)(t * W + k), (uint32_t)h, 5u, a.sweep, a.k0, a.k1);
+  const double ul = u53(wv.z, wv.w);
+  const double lu = ul > 0.0 ? log(ul) : -INFINITY;
+  const double lz = a.lnz[e];
+  bool acc = false;
+  if (lz == lz) {
+    const int64_t i = (int64_t)t * W + k;
+    const double la = a.betas[t] * (a.prop_logl[e] - a.logl[i]) + (double)(kPsdDim - 1) * lz;
+    acc = lu < la;
+    if (acc) {
+      for (int c = 0; c < kPsdDim; ++c) a.params[i * kPsdDim + c] = a.prop[(int64_t)e * kPsdDim + c];
+      a.logl[i] = a.prop_logl[e];
+    }
+  }
+  if (a.stats) {
+    atomicAdd((unsigned long long*)&a.stats[0], 1ull);
+    if (acc) atomicAdd((unsigned long long*)&a.stats[1], 1ull);
+  }
+}
+
+// Swaps between temperatures t and t-1 of walker w (one thread per walker, top down).
+__global__ void k_psd_swap(PsdArgs a) {
+  const int T = a.d.n_temps, W = a.d.n_walkers;
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  unsigned long long prop = 0, accd = 0;
+  for (int t = T - 1; t > 0; --t) {
+    const U4 wv = philox4x32_10((uint32_t)t, (uint32_t)w, 6u, a.sweep, a.k0, a.k1);
+    const double ul = u53(wv.x, wv.y);
+    const double lu = ul > 0.0 ? log(ul) : -INFINITY;
+    const int64_t it = (int64_t)t * W + w, im = (int64_t)(t - 1) * W + w;
+    const double la = (a.betas[t - 1] - a.betas[t]) * (a.logl[it] - a.logl[im]);
+    ++prop;
+    if (lu < la) {
+      ++accd;
+      for (int c = 0; c < kPsdDim; ++c) {
+        const double q = a.params[it * kPsdDim + c];
+        a.params[it * kPsdDim + c] = a.params[im * kPsdDim + c];
+        a.params[im * kPsdDim + c] = q;
+      }
+      const double q = a.logl[it];
+      a.logl[it] = a.logl[im];
+      a.logl[im] = q;
+    }
+  }
+  if (a.stats) {
+    atomicAdd((unsigned long long*)&a.stats[2], prop);
+    atomicAdd((unsigned long long*)&a.stats[3], accd);
+  }
+}
+
+}  // namespace gbk
+
+using namespace gbk;
+
+struct gbk_psd_plan {
+  gbk_ctx* ctx;
+  gbk_psd_desc d;
+  double* prop;
+  double* prop_logl;
+  double* lnz;
+  int32_t* ridx;
+  double* scratch;
+  int64_t max_entries;
+};
+
+extern "C" gbk_status total_loglike_fg(gbk_ctx* ctx, const float* residual, int32_t n_resid, const double* psd_params,
+                                       const int32_t* resid_index, int32_t n, double* logl, void* stream) {
+  if (!ctx) return set_error(GBK_EINVAL, "total_loglike_fg: null context");
+  if (n < 0 || n_resid < 1) return set_error(GBK_EINVAL, "total_loglike_fg: bad counts");
+  if (n == 0) return GBK_OK;
+  if (!residual || !psd_params || !logl) return set_error(GBK_EINVAL, "total_loglike_fg: null device pointer");
+  if (((uintptr_t)residual & 7) != 0) return set_error(GBK_EINVAL, "total_loglike_fg: residual must be 8-byte aligned");
+  if (!resid_index && n > n_resid) return set_error(GBK_EINVAL, "total_loglike_fg: more entries than residuals");
+  // the context scratch holds chunks x 4096 walkers x 2 doubles: 3 doubles per entry here
+  const int64_t max_entries = 4096 * 2 / 3;
+  return fg_loglike(ctx, residual, n_resid, psd_params, resid_index, n, logl, ctx->scratch, max_entries,
+                    (cudaStream_t)stream);
+}
+
+extern "C" gbk_status psd_eval_fg(gbk_ctx* ctx, const double* psd_params, int32_t n_walkers, double* s_out,
+                                  void* stream) {
+  if (!ctx) return set_error(GBK_EINVAL, "psd_eval_fg: null context");
+  if (n_walkers < 0) return set_error(GBK_EINVAL, "psd_eval_fg: n_walkers < 0");
+  if (n_walkers == 0 || !s_out) return GBK_OK;
+  if (!psd_params) return set_error(GBK_EINVAL, "psd_eval_fg: null psd_params");
+  const int64_t total = (int64_t)n_walkers * ctx->grid.n_bins;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_psd_eval_fg<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(ctx->psd_q, ctx->psd_p, psd_params, n_walkers,
+                                                               ctx->grid.k0, ctx->grid.n_bins, ctx->grid.tobs, s_out);
+  return check_launch("psd_eval_fg");
+}
+
+extern "C" gbk_status gbk_psd_plan_create(gbk_ctx* ctx, const gbk_psd_desc* desc, gbk_psd_plan** out) {
+  if (!ctx || !desc || !out) return set_error(GBK_EINVAL, "gbk_psd_plan_create: null argument");
+  *out = nullptr;
+  const gbk_psd_desc& d = *desc;
+  if (d.n_temps < 1 || d.n_walkers < 2 || (d.n_walkers & 1) || d.n_temps * (int64_t)d.n_walkers > (1 << 20))
+    return set_error(GBK_EINVAL, "gbk_psd_plan_create: need n_temps >= 1 and an even n_walkers >= 2");
+  if (!(d.stretch_a > 1.0)) return set_error(GBK_EINVAL, "gbk_psd_plan_create: stretch scale a must exceed 1");
+  for (int c = 0; c < kPsdDim; ++c)
+    if (!(d.lo[c] < d.hi[c])) return set_error(GBK_EINVAL, "gbk_psd_plan_create: empty prior box in coordinate %d", c);
+  gbk_psd_plan* p = new gbk_psd_plan();
+  p->ctx = ctx;
+  p->d = d;
+  const int64_t n = (int64_t)d.n_temps * (d.n_walkers / 2);
+  const int64_t nchunks = (ctx->grid.n_bins + kFgChunk - 1) / kFgChunk;
+  p->max_entries = n;
+  cudaError_t e = cudaMalloc((void**)&p->prop, n * kPsdDim * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->prop_logl, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->lnz, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->ridx, n * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->scratch, nchunks * n * 3 * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    gbk_psd_plan_destroy(p);
+    return set_error(GBK_ENOMEM, "gbk_psd_plan_create: %s", cudaGetErrorString(e));
+  }
+  *out = p;
+  return GBK_OK;
+}
+
+extern "C" gbk_status gbk_psd_plan_destroy(gbk_psd_plan* p) {
+  if (!p) return GBK_OK;
+  cudaFree(p->prop);
+  cudaFree(p->prop_logl);
+  cudaFree(p->lnz);
+  cudaFree(p->ridx);
+  cudaFree(p->scratch);
+  delete p;
+  return GBK_OK;
+}
+
+extern "C" gbk_status gb_psd_sweep(gbk_psd_plan* plan, double* params, double* logl, const float* residual,
+                                   const double* betas, uint64_t key, uint32_t sweep_index, int64_t* stats,
+                                   void* stream) {
+  if (!plan) return set_error(GBK_EINVAL, "gb_psd_sweep: null plan");
+  if (!params || !logl || !residual || !betas) return set_error(GBK_EINVAL, "gb_psd_sweep: null device pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  PsdArgs a;
+  a.d = plan->d;
+  a.params = params;
+  a.logl = logl;
+  a.prop = plan->prop;
+  a.prop_logl = plan->prop_logl;
+  a.lnz = plan->lnz;
+  a.ridx = plan->ridx;
+  a.betas = betas;
+  a.k0 = (uint32_t)(key & 0xffffffffu);
+  a.k1 = (uint32_t)(key >> 32);
+  a.sweep = sweep_index;
+  a.stats = (long long*)stats;
+  const int n = plan->d.n_temps * (plan->d.n_walkers / 2);
+  gbk_status s;
+  for (int h = 0; h < 2; ++h) {
+    k_psd_propose<<<(n + 127) / 128, 128, 0, st>>>(a, h);
+    if ((s = check_launch("gb_psd_sweep(propose)"))) return s;
+    if ((s = fg_loglike(plan->ctx, residual, plan->d.n_walkers, plan->prop, plan->ridx, n, plan->prop_logl,
+                        plan->scratch, plan->max_entries, st)))
+      return s;
+    k_psd_accept<<<(n + 127) / 128, 128, 0, st>>>(a, h);
+    if ((s = check_launch("gb_psd_sweep(accept)"))) return s;
+  }
+  if (plan->d.n_temps > 1) {
+    k_psd_swap<<<(plan->d.n_walkers + 127) / 128, 128, 0, st>>>(a);
+    if ((s = check_launch("gb_psd_sweep(swap)"))) return s;
+  }
+  return GBK_OK;
+}

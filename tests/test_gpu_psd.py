@@ -1,0 +1,139 @@
+"""Per-channel noise PSD with the Galactic foreground and the PSD module's sampler on the GPU,
+against the float64 oracle (oracle/psdmcmc.py).
+
+total_loglike_fg: float32 per-bin terms; the foreground exponent (~50) is formed from a
+float32 table and float32 walker constants, a relative error of a few 1e-6 in S_fg per bin,
+pseudo-random across bins; held, like total_loglike, to 3 n 2^-22. gb_psd_sweep: the stretch
+arithmetic is float64 on both sides and the likelihood differences agree to ~1e-4, so every
+decision matches unless ln u falls within that of ln alpha (not met with these seeds).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import constants as OC
+from oracle import psdmcmc as PM
+from paper_2405_04690_gb300 import synth
+
+from _common import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+TRUTH = np.array([15e-12, 3e-15, 12e-12, 4e-15, 3.3e-44, 1.2, 2.8e-3, 1763.3, 1686.3])
+
+
+def _params(g, n):
+    p = np.tile(TRUTH, (n, 1))
+    p[:, :4] *= np.exp(g.uniform(-0.3, 0.3, (n, 4)))
+    p[:, 4] *= np.exp(g.uniform(-1, 1, n))
+    p[:, 5] += g.uniform(-0.1, 0.1, n)
+    p[:, 6] *= np.exp(g.uniform(-0.2, 0.2, n))
+    p[:, 7:] *= np.exp(g.uniform(-0.2, 0.2, (n, 2)))
+    return p
+
+
+def _residuals(g, f, p):
+    out = np.empty((len(p), 2, len(f)), complex)
+    for w in range(len(p)):
+        sa, se = PM.channel_psd(f, p[w])
+        out[w, 0] = synth.unit_complex_normal(g, len(f)) * np.sqrt(sa / (4 * OC.DF))
+        out[w, 1] = synth.unit_complex_normal(g, len(f)) * np.sqrt(se / (4 * OC.DF))
+    return out.astype(np.complex64)
+
+
+def _dev_resid(torch, r):
+    return torch.from_numpy(r.view(np.float32).reshape(r.shape[0], 2, r.shape[2], 2).copy()).cuda()
+
+
+def test_psd_eval_fg_matches_oracle():
+    torch = torch_cuda()
+    from paper_2405_04690_gb300 import _lib as L
+    g = np.random.default_rng(1)
+    k0, n = 3146, 30001
+    f = (k0 + np.arange(n)) * OC.DF
+    p = _params(g, 3)
+    ctx = L.Context(OC.TOBS, OC.DT, k0, n)
+    out = torch.empty((3, 2, n), dtype=torch.float64, device="cuda")
+    L.psd_eval_fg(ctx, torch.from_numpy(p).cuda(), out)
+    got = out.cpu().numpy()
+    for w in range(3):
+        sa, se = PM.channel_psd(f, p[w])
+        np.testing.assert_allclose(got[w, 0], sa, rtol=1e-11)
+        np.testing.assert_allclose(got[w, 1], se, rtol=1e-11)
+    ctx.close()
+
+
+def test_total_loglike_fg_matches_oracle_and_shares_residual_reads():
+    torch = torch_cuda()
+    from paper_2405_04690_gb300 import _lib as L
+    g = np.random.default_rng(2)
+    k0, n = 3146, 50001                      # ragged last chunk
+    f = (k0 + np.arange(n)) * OC.DF
+    p = _params(g, 6)
+    r = _residuals(g, f, p)
+    ctx = L.Context(OC.TOBS, OC.DT, k0, n)
+    rt = _dev_resid(torch, r)
+    pt = torch.from_numpy(p).cuda()
+    out = torch.full((6,), float("nan"), dtype=torch.float64, device="cuda")
+    L.total_loglike_fg(ctx, rt, pt, out)
+    L.gbk_sync_status(ctx)
+    want = np.array([PM.loglike(r[w].astype(complex), f, OC.DF, p[w]) for w in range(6)])
+    tol = 3 * n * 2.0 ** -22
+    err = np.max(np.abs(out.cpu().numpy() - want))
+    assert err < tol, (err, tol)
+    # entries sharing residuals (pairs, as consecutive temperatures of one walker), indexed
+    idx = torch.tensor([0, 0, 3, 3, 5, 5, 1], dtype=torch.int32, device="cuda")
+    pp = torch.from_numpy(p[[0, 1, 2, 3, 4, 5, 0]]).cuda()
+    out2 = torch.empty(7, dtype=torch.float64, device="cuda")
+    L.total_loglike_fg(ctx, rt, pp, out2, resid_index=idx)
+    L.gbk_sync_status(ctx)
+    pairs = list(zip([0, 0, 3, 3, 5, 5, 1], [0, 1, 2, 3, 4, 5, 0]))
+    want2 = np.array([PM.loglike(r[i].astype(complex), f, OC.DF, p[j]) for i, j in pairs])
+    # a residual under another walker's PSD has larger per-bin terms |R|^2 / S: the float32
+    # errors scale with them, so the bound scales with <R|R> / (4 n) (4 n: its expectation
+    # under the matching PSD)
+    from oracle import likelihood as LK
+    scale = np.array([max(1.0, LK.inner(r[i].astype(complex), r[i].astype(complex), np.stack(PM.channel_psd(f, p[j])),
+                                        OC.DF) / (4 * n)) for i, j in pairs])
+    assert np.all(np.abs(out2.cpu().numpy() - want2) < tol * scale), (np.abs(out2.cpu().numpy() - want2), tol * scale)
+    ctx.close()
+
+
+def test_psd_sweep_matches_oracle():
+    torch = torch_cuda()
+    from paper_2405_04690_gb300 import _lib as L
+    g = np.random.default_rng(3)
+    k0, n = 3146, 2048 * 16
+    f = (k0 + np.arange(n)) * OC.DF
+    T, W = 2, 8
+    lo = np.array([math.log(5e-12), math.log(1e-15), math.log(5e-12), math.log(1e-15), math.log(1e-45), 0.8, 1e-3,
+                   500.0, 500.0])
+    hi = np.array([math.log(45e-12), math.log(9e-15), math.log(45e-12), math.log(9e-15), math.log(1e-42), 1.6, 4e-3,
+                   3000.0, 3000.0])
+    r = _residuals(g, f, np.tile(TRUTH, (W, 1)))
+    params = np.stack([_params(g, W) for _ in range(T)])
+    betas = np.array([1.0, 0.5])
+    cfg = PM.PsdConfig(T, W, lo, hi, betas, key=(11, 12))
+    logl = np.array([[PM.loglike(r[w].astype(complex), f, OC.DF, params[t, w]) for w in range(W)] for t in range(T)])
+    ctx = L.Context(OC.TOBS, OC.DT, k0, n)
+    plan = L.PsdPlan(ctx, T, W, lo, hi)
+    pt = torch.from_numpy(params.copy()).cuda()
+    rt = _dev_resid(torch, r)
+    lt = torch.empty((T, W), dtype=torch.float64, device="cuda")
+    L.total_loglike_fg(ctx, rt, pt.reshape(T * W, 9), lt.reshape(-1),
+                       resid_index=torch.arange(W, dtype=torch.int32, device="cuda").repeat(T))
+    bt = torch.from_numpy(betas).cuda()
+    stats = torch.zeros((2, 2), dtype=torch.int64, device="cuda")
+    key = 11 | (12 << 32)
+    rc = r.astype(complex)
+    for s in range(3):
+        PM.sweep(cfg, params, logl, rc, f, OC.DF, s)
+        L.gb_psd_sweep(plan, pt, lt, rt, bt, key, s, stats)
+        L.gbk_sync_status(ctx)
+        np.testing.assert_allclose(pt.cpu().numpy(), params, rtol=1e-10)
+        assert np.max(np.abs(lt.cpu().numpy() - logl)) < 3 * n * 2.0 ** -22
+    st = stats.cpu().numpy()
+    assert st[0, 0] == 3 * T * W and st[0, 1] > 0 and st[1, 0] == 3 * W * (T - 1)
+    plan.close()
+    ctx.close()
