@@ -639,6 +639,62 @@ def run_ours(args):
               "ms": ms3, "GB/s": bytes3 / (ms3 * 1e-3) / 1e9, "algorithmic_bytes": bytes3,
               "peak_GB/s": peak, "peak_kind": kind, "frac": bytes3 / (ms3 * 1e-3) / 1e9 / peak,
               "walker_logl_per_s": w3 / (ms3 * 1e-3)}
+        # the PSD module (Sec. V.B): per-channel noise + Galactic foreground (9 parameters per
+        # walker) over the same residuals; (a) one likelihood pass of all walkers, (b) sweeps of
+        # the stretch/tempering sampler with 4 temperatures x 128 walkers (walker w's four
+        # temperatures share residual w and read it once)
+        g9 = synth.rng(9 + 1000 * rank)
+        p9 = np.tile(np.array([15e-12, 3e-15, 15e-12, 3e-15, 3.3e-44, 1.2, 2.8e-3, 1763.3, 1686.3]), (w3, 1))
+        p9[:, :4] *= np.exp(g9.uniform(-0.2, 0.2, (w3, 4)))
+        pt9 = torch.from_numpy(p9).to(dev)
+        out9 = torch.empty(w3, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            L.total_loglike_fg(ctx3, r3, pt9, out9, stream=stream)
+        torch.cuda.synchronize()
+        for a0, a1 in evs3:
+            a0.record(stream)
+            L.total_loglike_fg(ctx3, r3, pt9, out9, stream=stream)
+            a1.record(stream)
+        torch.cuda.synchronize()
+        ms9 = float(np.mean([a0.elapsed_time(a1) for a0, a1 in evs3]))
+        c3["foreground"] = {"workload": "Eq. like with per-channel noise + Galactic foreground (9 parameters per "
+                                        "walker), %d walkers x 2 ch x 2^20 bins" % w3,
+                            "ms": ms9, "GB/s": bytes3 / (ms9 * 1e-3) / 1e9, "frac": bytes3 / (ms9 * 1e-3) / 1e9 / peak}
+        T9, W9 = 4, min(128, w3)
+        lo9 = np.array([math.log(5e-12), math.log(1e-15), math.log(5e-12), math.log(1e-15), math.log(1e-45), 0.8,
+                        1e-3, 500.0, 500.0])
+        hi9 = np.array([math.log(45e-12), math.log(9e-15), math.log(45e-12), math.log(9e-15), math.log(1e-42), 1.6,
+                        4e-3, 3000.0, 3000.0])
+        plan9 = L.PsdPlan(ctx3, T9, W9, lo9, hi9)
+        ps9 = torch.from_numpy(np.stack([p9[:W9]] * T9)).to(dev).contiguous()
+        ls9 = torch.empty((T9, W9), dtype=torch.float64, device=dev)
+        rs9 = r3[:W9]
+        L.total_loglike_fg(ctx3, rs9, ps9.reshape(T9 * W9, 9), ls9.reshape(-1),
+                           resid_index=torch.arange(W9, dtype=torch.int32, device=dev).repeat(T9), stream=stream)
+        bt9 = torch.from_numpy(np.array([1.2 ** -t for t in range(T9)])).to(dev)
+        st9 = torch.zeros((2, 2), dtype=torch.int64, device=dev)
+        for k in range(3):
+            L.gb_psd_sweep(plan9, ps9, ls9, rs9, bt9, 0x9D, k, st9, stream)
+        torch.cuda.synchronize()
+        st9.zero_()
+        n9 = 10
+        a0, a1 = evs3[0]
+        a0.record(stream)
+        for k in range(n9):
+            L.gb_psd_sweep(plan9, ps9, ls9, rs9, bt9, 0x9D, 3 + k, st9, stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms_sw = a0.elapsed_time(a1) / n9
+        s9 = st9.cpu().numpy()
+        sweep_bytes = 2 * W9 // 2 * 2 * (1 << 20) * 8   # each half reads its W/2 residuals once
+        c3["psd_sweep"] = {"workload": "PSD sampler sweep: %d temperatures x %d walkers, 2^20 bins, stretch moves of "
+                                       "both halves + tempering swaps" % (T9, W9),
+                           "ms_per_sweep": ms_sw, "walker_updates_per_s": T9 * W9 / (ms_sw * 1e-3),
+                           "GB/s": sweep_bytes / (ms_sw * 1e-3) / 1e9,
+                           "frac": sweep_bytes / (ms_sw * 1e-3) / 1e9 / peak,
+                           "stretch_acceptance": float(s9[0, 1]) / max(1.0, float(s9[0, 0])),
+                           "swap_acceptance": float(s9[1, 1]) / max(1.0, float(s9[1, 0]))}
+        plan9.close()
         del r3, s3
         ctx3.close()
 

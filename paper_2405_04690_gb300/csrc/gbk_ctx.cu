@@ -172,9 +172,9 @@ extern "C" gbk_status gbk_create(gbk_ctx** out_ctx, const gbk_grid* grid) {
     iqf[i] = (float)iq[i];
     rhof[i] = (float)rho[i];
     const double x = 2.0 * M_PI * f * kLc, sx = sin(x);
-    lnff[i] = (float)log(f);
+    lnff[i] = (float)log2(f);
     ff[i] = (float)f;
-    fgc[i] = (float)(log(6.0 * x * x * sx * sx) - log(q[i]) - (7.0 / 3.0) * log(f));
+    fgc[i] = (float)((log(6.0 * x * x * sx * sx) - log(q[i]) - (7.0 / 3.0) * log(f)) * 1.4426950408889634);
     const double y = log(q[i]) - comp;
     const double t = s + y;
     comp = (t - s) - y;

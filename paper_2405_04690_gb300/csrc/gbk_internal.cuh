@@ -58,8 +58,9 @@ struct gbk_ctx {
   double* iq_d;
   double* rho_d;
   double sum_lnq;      // sum_k ln Q_k over the window, float64
-  // Galactic-foreground shape over the window (Sec. III.A): ln f, the float32 frequency and
-  // fgc = ln(6 x^2 sin^2 x / Q) - (7/3) ln f, so S_fg / Q = A_fg exp(fgc - s1 f^alpha - softplus(2 s2 (f - f_k)))
+  // Galactic-foreground shape over the window (Sec. III.A), in base-2 logarithms: log2 f, the
+  // float32 frequency and fgc = log2(6 x^2 sin^2 x / Q) - (7/3) log2 f, so that
+  // S_fg / Q = A_fg 2^(fgc - log2(e) [s1 f^alpha + softplus(2 s2 (f - f_k))])
   float* fg_lnf;
   float* fg_f;
   float* fg_c;

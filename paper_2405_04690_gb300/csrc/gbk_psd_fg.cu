@@ -6,9 +6,11 @@
 // Parameters of one PSD walker (float64 [9]): sqrt(S_oms,A), sqrt(S_acc,A), sqrt(S_oms,E),
 // sqrt(S_acc,E), A_fg, alpha, f_k, s1, s2. Per bin and channel
 //   S_ch = S_oms,ch Q (1 + (S_acc,ch / S_oms,ch) rho + g / S_oms,ch),
-//   g = S_fg / Q = A_fg exp(fgc - s1 f^alpha - softplus(2 s2 (f - f_k))),
-// with the context's tables Q, rho = P/Q and fgc = ln(6 x^2 sin^2 x / Q) - (7/3) ln f
-// (since (1 + tanh(-y)) = 2 / (1 + e^(2y)) and (A_fg / 2) 2 = A_fg).
+//   g = S_fg / Q = A_fg exp(ln(6 x^2 sin^2 x / Q) - (7/3) ln f - s1 f^alpha - softplus(2 s2 (f - f_k)))
+// (since (1 + tanh(-y)) = 2 / (1 + e^(2y)) and (A_fg / 2) 2 = A_fg), evaluated in base 2 on the
+// special-function unit: the context holds log2 f and the bin's constant part in log2 units.
+// The exponent (~70 in log2 units) carries the float32 rounding of its table entry, ~4e-6,
+// i.e. a relative error of ~3e-6 in S_fg, pseudo-random from bin to bin.
 #include <math.h>
 
 #include "gbk_internal.cuh"
@@ -27,8 +29,21 @@ size_t total_loglike_scratch_bytes(int64_t n_bins);
 struct FgEntry {
   float aw_a, aw_e;     // S_acc / S_oms per channel
   float k_a, k_e;       // A_fg / S_oms per channel (x 2^0: g and S_oms share the 2^128 scale of Q)
-  float alpha, s1, s2x2, fk;
+  float alpha, s1l, s2l, fk;   // alpha, s1 log2(e), 2 s2 log2(e), f_k
 };
+
+__device__ __forceinline__ float ex2a(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2a(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// log2(1 + 2^x) without overflow
+__device__ __forceinline__ float softplus2(float x) { return fmaxf(x, 0.f) + lg2a(1.0f + ex2a(-fabsf(x))); }
 
 __device__ __forceinline__ FgEntry fg_entry(const double* p) {
   FgEntry e;
@@ -39,13 +54,10 @@ __device__ __forceinline__ FgEntry fg_entry(const double* p) {
   e.k_e = (float)(p[4] / so_e);
   e.alpha = (float)p[5];
   e.fk = (float)p[6];
-  e.s1 = (float)p[7];
-  e.s2x2 = (float)(2.0 * p[8]);
+  e.s1l = (float)(p[7] * 1.4426950408889634);
+  e.s2l = (float)(2.0 * p[8] * 1.4426950408889634);
   return e;
 }
-
-// softplus(x) = ln(1 + e^x), without overflow
-__device__ __forceinline__ float softplus(float x) { return fmaxf(x, 0.f) + log1pf(expf(-fabsf(x))); }
 
 // One block: bins [chunk * kFgChunk, +kFgChunk) of entries [eg, eg + kFgEntries).
 // part[(chunk * nel + e) * 3 + {0, 1, 2}] = sum |R_A|^2 2^128 iq / u_A, the same for E,
@@ -97,15 +109,17 @@ k_fg_part(const float* __restrict__ R, const float* __restrict__ iq, const float
         a = __ldcs(reinterpret_cast<const float2*>(rw[j] + 2 * k));
         e = __ldcs(reinterpret_cast<const float2*>(rw[j] + 2 * (nb + k)));
       }
-      // accurate expf: the exponent reaches ~50, where the fast approximation's error would
-      // show in S_fg
-      const float g = expf(c - ent[j].s1 * expf(ent[j].alpha * lf) - softplus(ent[j].s2x2 * (fk - ent[j].fk)));
+      // g = 2^(c - log2(e) [s1 f^alpha + softplus(2 s2 (f - f_k))]), f^alpha = 2^(alpha log2 f);
+      // far above the knee (softplus > c + 30) g A_fg / S_oms < 2^-30 relative to 1: skipped
+      const float y = ent[j].s2l * (fk - ent[j].fk);
+      float g = 0.f;
+      if (y < c + 30.f) g = ex2a(c - ent[j].s1l * ex2a(ent[j].alpha * lf) - softplus2(y));
       const float ua = fmaf(ent[j].aw_a, rhk, 1.0f) + g * ent[j].k_a;
       const float ue = fmaf(ent[j].aw_e, rhk, 1.0f) + g * ent[j].k_e;
       const float ax = a.x * up, ay = a.y * up, ex = e.x * up, ey = e.y * up;
       sqa[j].add((ax * ax + ay * ay) * iqk * __frcp_rn(ua));
       sqe[j].add((ex * ex + ey * ey) * iqk * __frcp_rn(ue));
-      sl[j].add(logf(ua) + logf(ue));
+      sl[j].add(0.6931471805599453f * lg2a(ua * ue));
     }
   }
   __shared__ double red[kFgThreads / 32][kFgEntries][3];
