@@ -27,6 +27,7 @@ constexpr int kPsdDim = 9;
 size_t total_loglike_scratch_bytes(int64_t n_bins);
 
 struct FgEntry {
+  float iso_a, iso_e;   // 2^-64 / S_oms per channel (keeps the q-terms of both channels in one sum)
   float aw_a, aw_e;     // S_acc / S_oms per channel
   float k_a, k_e;       // A_fg / S_oms per channel (x 2^0: g and S_oms share the 2^128 scale of Q)
   float alpha, s1l, s2l, fk;   // alpha, s1 log2(e), 2 s2 log2(e), f_k
@@ -35,6 +36,11 @@ struct FgEntry {
 __device__ __forceinline__ float ex2a(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcpa(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 __device__ __forceinline__ float lg2a(float x) {
@@ -48,6 +54,8 @@ __device__ __forceinline__ float softplus2(float x) { return fmaxf(x, 0.f) + lg2
 __device__ __forceinline__ FgEntry fg_entry(const double* p) {
   FgEntry e;
   const double so_a = p[0] * p[0], sa_a = p[1] * p[1], so_e = p[2] * p[2], sa_e = p[3] * p[3];
+  e.iso_a = (float)(ldexp(1.0, -64) / so_a);
+  e.iso_e = (float)(ldexp(1.0, -64) / so_e);
   e.aw_a = (float)(sa_a / so_a);
   e.aw_e = (float)(sa_e / so_e);
   e.k_a = (float)(p[4] / so_a);
@@ -60,9 +68,9 @@ __device__ __forceinline__ FgEntry fg_entry(const double* p) {
 }
 
 // One block: bins [chunk * kFgChunk, +kFgChunk) of entries [eg, eg + kFgEntries).
-// part[(chunk * nel + e) * 3 + {0, 1, 2}] = sum |R_A|^2 2^128 iq / u_A, the same for E,
+// part[(chunk * nel + e) * 2 + {0, 1}] = sum_ch |R_ch|^2 2^64 iq / (u_ch S_oms,ch) and
 // sum (ln u_A + ln u_E); compensated float32 per thread, float64 across the block.
-__global__ void __launch_bounds__(kFgThreads, 3)
+__global__ void __launch_bounds__(kFgThreads, 2)
 k_fg_part(const float* __restrict__ R, const float* __restrict__ iq, const float* __restrict__ rho,
           const float* __restrict__ lnf, const float* __restrict__ ff, const float* __restrict__ fgc,
           const double* __restrict__ pp, const int32_t* __restrict__ ridx, int32_t n_resid, int32_t e0, int32_t nel,
@@ -95,47 +103,76 @@ k_fg_part(const float* __restrict__ R, const float* __restrict__ iq, const float
     rw[j] = R + (int64_t)s_r[j] * 2 * nb * 2;
     same[j] = j > 0 && s_r[j] == s_r[j - 1];   // entries of one residual read it once
   }
-  CompF sqa[kFgEntries], sqe[kFgEntries], sl[kFgEntries];
+  CompF sq[kFgEntries], sl[kFgEntries];
 #pragma unroll
-  for (int j = 0; j < kFgEntries; ++j) { sqa[j].init(); sqe[j].init(); sl[j].init(); }
+  for (int j = 0; j < kFgEntries; ++j) { sq[j].init(); sl[j].init(); }
   const float up = 18446744073709551616.0f;  // 2^64
-  for (int64_t k = kbeg + threadIdx.x; k < kend; k += kFgThreads) {
-    const float iqk = __ldg(iq + k), rhk = __ldg(rho + k), lf = __ldg(lnf + k), fk = __ldg(ff + k), c = __ldg(fgc + k);
-    float2 a = make_float2(0.f, 0.f), e = make_float2(0.f, 0.f);
+  // per-bin, per-entry terms; residual values of both channels at bin k given
+  auto bin = [&](int j, float iqk, float rhk, float lf, float fk, float c, float ar, float ai, float er, float ei) {
+    // g = 2^(c - log2(e) [s1 f^alpha + softplus(2 s2 (f - f_k))]), f^alpha = 2^(alpha log2 f);
+    // far above the knee (softplus > c + 30) g A_fg / S_oms < 2^-30 relative to 1: skipped
+    const float y = ent[j].s2l * (fk - ent[j].fk);
+    float g = 0.f;
+    if (y < c + 30.f) g = ex2a(c - ent[j].s1l * ex2a(ent[j].alpha * lf) - softplus2(y));
+    const float ua = fmaf(ent[j].aw_a, rhk, 1.0f) + g * ent[j].k_a;
+    const float ue = fmaf(ent[j].aw_e, rhk, 1.0f) + g * ent[j].k_e;
+    const float ax = ar * up, ay = ai * up, ex = er * up, ey = ei * up;
+    sq[j].add(iqk * ((ax * ax + ay * ay) * ent[j].iso_a * rcpa(ua) + (ex * ex + ey * ey) * ent[j].iso_e * rcpa(ue)));
+    sl[j].add(0.6931471805599453f * lg2a(ua * ue));
+  };
+  const bool even = (nb & 1) == 0;
+  for (int64_t k = kbeg + 2 * threadIdx.x; k < kend; k += 2 * kFgThreads) {
+    if (even && k + 1 < kend) {   // two bins per thread: all entries' residual loads issued first
+      const float2 iq2 = __ldg(reinterpret_cast<const float2*>(iq + k));
+      const float2 rh2 = __ldg(reinterpret_cast<const float2*>(rho + k));
+      const float2 lf2 = __ldg(reinterpret_cast<const float2*>(lnf + k));
+      const float2 ff2 = __ldg(reinterpret_cast<const float2*>(ff + k));
+      const float2 c2 = __ldg(reinterpret_cast<const float2*>(fgc + k));
+      float4 av[kFgEntries], ev[kFgEntries];
 #pragma unroll
-    for (int j = 0; j < kFgEntries; ++j) {
-      if (!act[j]) continue;
-      if (!same[j]) {
-        a = __ldcs(reinterpret_cast<const float2*>(rw[j] + 2 * k));
-        e = __ldcs(reinterpret_cast<const float2*>(rw[j] + 2 * (nb + k)));
+      for (int j = 0; j < kFgEntries; ++j) {
+        if (act[j] && !same[j]) {
+          av[j] = __ldcs(reinterpret_cast<const float4*>(rw[j] + 2 * k));
+          ev[j] = __ldcs(reinterpret_cast<const float4*>(rw[j] + 2 * (nb + k)));
+        }
       }
-      // g = 2^(c - log2(e) [s1 f^alpha + softplus(2 s2 (f - f_k))]), f^alpha = 2^(alpha log2 f);
-      // far above the knee (softplus > c + 30) g A_fg / S_oms < 2^-30 relative to 1: skipped
-      const float y = ent[j].s2l * (fk - ent[j].fk);
-      float g = 0.f;
-      if (y < c + 30.f) g = ex2a(c - ent[j].s1l * ex2a(ent[j].alpha * lf) - softplus2(y));
-      const float ua = fmaf(ent[j].aw_a, rhk, 1.0f) + g * ent[j].k_a;
-      const float ue = fmaf(ent[j].aw_e, rhk, 1.0f) + g * ent[j].k_e;
-      const float ax = a.x * up, ay = a.y * up, ex = e.x * up, ey = e.y * up;
-      sqa[j].add((ax * ax + ay * ay) * iqk * __frcp_rn(ua));
-      sqe[j].add((ex * ex + ey * ey) * iqk * __frcp_rn(ue));
-      sl[j].add(0.6931471805599453f * lg2a(ua * ue));
+#pragma unroll
+      for (int j = 1; j < kFgEntries; ++j)
+        if (same[j]) { av[j] = av[j - 1]; ev[j] = ev[j - 1]; }
+#pragma unroll
+      for (int j = 0; j < kFgEntries; ++j) {
+        if (!act[j]) continue;
+        bin(j, iq2.x, rh2.x, lf2.x, ff2.x, c2.x, av[j].x, av[j].y, ev[j].x, ev[j].y);
+        bin(j, iq2.y, rh2.y, lf2.y, ff2.y, c2.y, av[j].z, av[j].w, ev[j].z, ev[j].w);
+      }
+    } else {
+      for (int64_t kk = k; kk < min(k + 2, kend); ++kk) {
+        const float iqk = __ldg(iq + kk), rhk = __ldg(rho + kk), lf = __ldg(lnf + kk), fk = __ldg(ff + kk),
+                    c = __ldg(fgc + kk);
+#pragma unroll
+        for (int j = 0; j < kFgEntries; ++j) {
+          if (!act[j]) continue;
+          const float2 a = *reinterpret_cast<const float2*>(rw[j] + 2 * kk);
+          const float2 e = *reinterpret_cast<const float2*>(rw[j] + 2 * (nb + kk));
+          bin(j, iqk, rhk, lf, fk, c, a.x, a.y, e.x, e.y);
+        }
+      }
     }
   }
-  __shared__ double red[kFgThreads / 32][kFgEntries][3];
+  __shared__ double red[kFgThreads / 32][kFgEntries][2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < kFgEntries; ++j) {
-    const double x0 = sqa[j].warp_total(), x1 = sqe[j].warp_total(), x2 = sl[j].warp_total();
-    if (lane == 0) { red[wid][j][0] = x0; red[wid][j][1] = x1; red[wid][j][2] = x2; }
+    const double x0 = sq[j].warp_total(), x1 = sl[j].warp_total();
+    if (lane == 0) { red[wid][j][0] = x0; red[wid][j][1] = x1; }
   }
   __syncthreads();
-  if (threadIdx.x < kFgEntries * 3) {
-    const int j = threadIdx.x / 3, which = threadIdx.x % 3;
+  if (threadIdx.x < kFgEntries * 2) {
+    const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
     if (eg + j < nel) {
       double s = 0.0;
       for (int w = 0; w < kFgThreads / 32; ++w) s += red[w][j][which];
-      part[((int64_t)chunk * nel + eg + j) * 3 + which] = s;
+      part[((int64_t)chunk * nel + eg + j) * 2 + which] = s;
     }
   }
 }
@@ -146,16 +183,15 @@ __global__ void k_fg_final(const double* __restrict__ part, int nchunks, const d
   const int el = blockIdx.x * blockDim.x + threadIdx.x;
   if (el >= nel) return;
   const int e = e0 + el;
-  double qa = 0.0, qe = 0.0, l = 0.0;
+  double q = 0.0, l = 0.0;
   for (int c = 0; c < nchunks; ++c) {
-    qa += part[((int64_t)c * nel + el) * 3];
-    qe += part[((int64_t)c * nel + el) * 3 + 1];
-    l += part[((int64_t)c * nel + el) * 3 + 2];
+    q += part[((int64_t)c * nel + el) * 2];
+    l += part[((int64_t)c * nel + el) * 2 + 1];
   }
   const double* p = pp + (int64_t)e * kPsdDim;
   const double so_a = p[0] * p[0], so_e = p[2] * p[2];
-  logl[e] = -0.5 * 4.0 * df * (qa / so_a + qe / so_e) -
-            ((double)nb * (log(so_a) + log(so_e)) + 2.0 * sum_lnq + l);
+  // q carries |R|^2 2^128 iq / (u S_oms) x 2^-64: restore the 2^64
+  logl[e] = -0.5 * 4.0 * df * ldexp(q, 64) - ((double)nb * (log(so_a) + log(so_e)) + 2.0 * sum_lnq + l);
 }
 
 static gbk_status fg_loglike(gbk_ctx* ctx, const float* residual, int32_t n_resid, const double* pp,
@@ -323,10 +359,10 @@ extern "C" gbk_status total_loglike_fg(gbk_ctx* ctx, const float* residual, int3
   if (n < 0 || n_resid < 1) return set_error(GBK_EINVAL, "total_loglike_fg: bad counts");
   if (n == 0) return GBK_OK;
   if (!residual || !psd_params || !logl) return set_error(GBK_EINVAL, "total_loglike_fg: null device pointer");
-  if (((uintptr_t)residual & 7) != 0) return set_error(GBK_EINVAL, "total_loglike_fg: residual must be 8-byte aligned");
+  if (((uintptr_t)residual & 15) != 0) return set_error(GBK_EINVAL, "total_loglike_fg: residual must be 16-byte aligned");
   if (!resid_index && n > n_resid) return set_error(GBK_EINVAL, "total_loglike_fg: more entries than residuals");
-  // the context scratch holds chunks x 4096 walkers x 2 doubles: 3 doubles per entry here
-  const int64_t max_entries = 4096 * 2 / 3;
+  // the context scratch holds chunks x 4096 walkers x 2 doubles
+  const int64_t max_entries = 4096;
   return fg_loglike(ctx, residual, n_resid, psd_params, resid_index, n, logl, ctx->scratch, max_entries,
                     (cudaStream_t)stream);
 }
@@ -364,7 +400,7 @@ extern "C" gbk_status gbk_psd_plan_create(gbk_ctx* ctx, const gbk_psd_desc* desc
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->prop_logl, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->lnz, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->ridx, n * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&p->scratch, nchunks * n * 3 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->scratch, nchunks * n * 2 * sizeof(double));
   if (e != cudaSuccess) {
     cudaGetLastError();
     gbk_psd_plan_destroy(p);
