@@ -430,6 +430,15 @@ gbk_status mdn_sample_logpdf(const float* raw, int32_t batch, double eps, const 
 gbk_status gbk_sweep_set_proposal(gbk_sweep* plan, gbk_mdn* net, const float* raw_table, double eps,
                                   double inmodel_frac);
 
+/* Temperature-ladder adaptation (Vousden, Farr & Mandel 2016; the paper adapts every ladder,
+ * App. D): for every band independently, with T_0 = 1 and S_i = ln(T_i - T_{i-1}),
+ * S_i += kappa (A_i - A_{i+1}), kappa = t0 / (nu (iteration + t0)), where A_i is the fraction
+ * of walkers whose swap between rungs i-1 and i was accepted in the last gb_sweep (counted on
+ * the device); T_i = T_{i-1} + e^{S_i}. An infinite top rung (beta = 0) stays; a finite one
+ * adapts with A_N = 0. betas [n_bands][n_temps] (device) is updated in place. */
+gbk_status gbk_sweep_adapt_temps(gbk_sweep* plan, double* betas, int32_t iteration, double nu, double t0,
+                                 void* stream);
+
 /* Group stretch in-model moves (the paper's in-model proposal, Eq. stretch with a stationary
  * group): builds every band's stationary group from the current cold chain -- the sources of
  * bands b-1, b, b+1 of all walkers, sorted by f0 -- and makes a fraction `frac` of the

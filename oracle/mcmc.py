@@ -233,6 +233,43 @@ def mdn_log_q(cfg, raw, b, th):
     return MD.log_q_defensive(raw, MD.to_unit(cfg, b, th), cfg.mdn_eps)
 
 
+# ---------------------------------------------------------------- temperature adaptation
+def adapt_ladder(betas, acc, iteration, nu=100.0, t0=1000.0):
+    """Vousden, Farr & Mandel (2016) ladder update (the paper adapts every ladder this way,
+    App. D): with T_0 = 1 and S_i = ln(T_i - T_{i-1}), S_i += kappa (A_i - A_{i+1}) for the
+    finite rungs i = 1 .. N-2 (and N-1 when the top rung is finite, with A_N = 0), where A_i
+    is the swap acceptance between rungs i-1 and i and kappa = t0 / (nu (t + t0)); then
+    T_i = T_{i-1} + e^{S_i}. An infinite top rung (beta = 0) stays."""
+    betas = np.asarray(betas, dtype=np.float64)
+    n = len(betas)
+    if n < 2:
+        return betas.copy()
+    top_inf = betas[-1] == 0.0
+    last = n - 2 if top_inf else n - 1
+    if last < 1:
+        return betas.copy()
+    temps = 1.0 / betas[:last + 1]
+    a = list(acc) + [0.0]
+    kappa = t0 / (nu * (iteration + t0))
+    out = betas.copy()
+    t_prev = 1.0
+    for i in range(1, last + 1):
+        s = math.log(temps[i] - temps[i - 1]) + kappa * (a[i] - a[i + 1])
+        t_prev = t_prev + math.exp(s)
+        out[i] = 1.0 / t_prev
+    return out
+
+
+def swap_acceptance(cfg, trace):
+    """Per band and rung i, the fraction of walkers whose swap between rungs i-1 and i was
+    accepted in a sweep's trace: array [n_bands][n_temps] (column 0 unused)."""
+    acc = np.zeros((cfg.n_bands, cfg.n_temps))
+    for r in trace:
+        if r["kind"] == 3 and r["accepted"]:
+            acc[r["b"], r["t"]] += 1.0
+    return acc / cfg.n_walkers
+
+
 # ---------------------------------------------------------------- group stretch
 STRETCH_PERIODS = (None, None, None, TWO_PI, math.pi, None, None, TWO_PI)
 

@@ -112,6 +112,7 @@ SIGNATURES = {
     "gbk_psd_plan_create": (ctypes.c_int, [_vp, ctypes.POINTER(GbkPsdDesc), ctypes.POINTER(_vp)]),
     "gbk_psd_plan_destroy": (ctypes.c_int, [_vp]),
     "gb_psd_sweep": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp]),
+    "gbk_sweep_adapt_temps": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_double, ctypes.c_double, _vp]),
     "gbk_sweep_update_group": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _i32, _vp]),
     "gb_sweep_features": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(GbkResidual), ctypes.POINTER(GbkPsd), _vp, _vp,
                                          _vp]),
@@ -412,6 +413,12 @@ def gbk_sweep_set_proposal(plan, net=None, raw_table=None, eps=0.1, inmodel_frac
     _check(lib().gbk_sweep_set_proposal(plan.handle, net.handle if net is not None else None,
                                         _dev(raw_table, torch.float32, "raw_table") if raw_table is not None else None,
                                         float(eps), float(inmodel_frac)), "gbk_sweep_set_proposal")
+
+
+def gbk_sweep_adapt_temps(plan, betas, iteration, nu=100.0, t0=1000.0, stream=None):
+    """Adapt every band's ladder from the last sweep's swap acceptance (in place)."""
+    _check(lib().gbk_sweep_adapt_temps(plan.handle, _dev(betas, torch.float64, "betas"), int(iteration), float(nu),
+                                       float(t0), _stream(stream)), "gbk_sweep_adapt_temps")
 
 
 def gbk_sweep_update_group(plan, params, exists, frac, n_friends=32, stream=None):

@@ -38,6 +38,7 @@ struct gbk_sweep {
   int gmax;
   double grp_frac;
   int n_friends;
+  int32_t* swap_acc;        // accepted swaps of the last sweep per band and rung [B][T]
 };
 
 namespace gbk {
@@ -82,6 +83,7 @@ struct SweepArgs {
   const int32_t* grp_n;
   int gmax, n_friends;
   double grp_frac;
+  int32_t* swap_acc;      // [B][T] accepted swaps between rungs t-1 and t
 };
 
 template <typename T> __device__ __forceinline__ const T* orb_of(const gbk_ctx& c, int bi);
@@ -1199,7 +1201,10 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_swap(const SweepArgs a) {
           cold_update<T, N>(a, bm, cache_base(a, t - 1, wm, b), +1, Rw, lane);   // new cold set enters
         }
       }
-      if (lane == 0) record(a, ws, 3, t, wt, b, c, t, acc, la, la, nullptr, 0, 0);
+      if (lane == 0) {
+        record(a, ws, 3, t, wt, b, c, t, acc, la, la, nullptr, 0, 0);
+        if (acc) atomicAdd(&a.swap_acc[(int64_t)b * T_ + t], 1);
+      }
       __syncwarp();
     }
   }
@@ -1390,6 +1395,8 @@ extern "C" gbk_status gbk_sweep_create(gbk_ctx* ctx, const gbk_sweep_desc* desc,
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->setid, (size_t)d.n_temps * d.n_walkers * d.n_bands * sizeof(int32_t));
   p->rwbuf_bytes = (size_t)sms_of_device() * 64 * 2 * 3 * d.band_bins * csz;   // every warp an SM can hold
   if (e == cudaSuccess) e = cudaMalloc(&p->rwbuf, p->rwbuf_bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->swap_acc, (size_t)d.n_bands * d.n_temps * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(p->swap_acc, 0, (size_t)d.n_bands * d.n_temps * sizeof(int32_t));
   if (e != cudaSuccess) {
     cudaFree(p->rsnap);
     cudaFree(p->rho);
@@ -1397,6 +1404,7 @@ extern "C" gbk_status gbk_sweep_create(gbk_ctx* ctx, const gbk_sweep_desc* desc,
     cudaFree(p->hsum);
     cudaFree(p->setid);
     cudaFree(p->rwbuf);
+    cudaFree(p->swap_acc);
     free(p);
     cudaGetLastError();
     return set_error(e == cudaErrorMemoryAllocation ? GBK_ENOMEM : GBK_ECUDA, "gbk_sweep_create: %s",
@@ -1415,6 +1423,7 @@ extern "C" gbk_status gbk_sweep_destroy(gbk_sweep* plan) {
   cudaFree(plan->hsum);
   cudaFree(plan->setid);
   cudaFree(plan->rwbuf);
+  cudaFree(plan->swap_acc);
   cudaFree(plan->mix);
   cudaFree(plan->grp_f0);
   cudaFree(plan->grp_par);
@@ -1494,6 +1503,7 @@ static SweepArgs make_args(gbk_sweep* plan, double* params, uint8_t* exists, con
   a.gmax = plan->gmax;
   a.n_friends = plan->n_friends;
   a.grp_frac = plan->grp_frac;
+  a.swap_acc = plan->swap_acc;
   return a;
 }
 
@@ -1528,6 +1538,9 @@ extern "C" gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists,
         cudaEventRecord(plan->ev[p][k][1], st);
       }
   }
+  if ((flags & GBK_SWEEP_SWAP) &&
+      cudaMemsetAsync(plan->swap_acc, 0, (size_t)plan->d.n_bands * plan->d.n_temps * sizeof(int32_t), st) != cudaSuccess)
+    return set_error(GBK_ECUDA, "gb_sweep: cannot clear the swap counters");
   g_timing_plan = plan;
   g_active_plan = plan;
   const int fl = flags & ~(GBK_SWEEP_TIMING | GBK_SWEEP_MDN);
@@ -1651,4 +1664,37 @@ extern "C" gbk_status gbk_sweep_update_group(gbk_sweep* plan, const double* para
   k_group_build<<<d.n_bands, 256, smem, (cudaStream_t)stream>>>(params, exists, d, gmax, p2, plan->grp_f0,
                                                                 plan->grp_par, plan->grp_n);
   return check_launch("gbk_sweep_update_group");
+}
+
+// Ladder of band b (one thread): Vousden, Farr & Mandel (2016) update from the last sweep's
+// swap acceptance A_i = accepted(i-1 <-> i) / W.
+__global__ void k_adapt_ladder(double* __restrict__ betas, const int32_t* __restrict__ acc, int nb, int nt, int nw,
+                               double kappa) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double* bt = betas + (int64_t)b * nt;
+  const bool top_inf = bt[nt - 1] == 0.0;
+  const int last = top_inf ? nt - 2 : nt - 1;
+  if (last < 1) return;
+  double t_prev = 1.0, t_old_prev = 1.0;
+  for (int i = 1; i <= last; ++i) {
+    const double t_old = 1.0 / bt[i];
+    const double ai = (double)acc[(int64_t)b * nt + i] / nw;
+    const double an = i + 1 < nt ? (double)acc[(int64_t)b * nt + i + 1] / nw : 0.0;
+    const double s = log(t_old - t_old_prev) + kappa * (ai - an);
+    t_old_prev = t_old;
+    t_prev = t_prev + exp(s);
+    bt[i] = 1.0 / t_prev;
+  }
+}
+
+extern "C" gbk_status gbk_sweep_adapt_temps(gbk_sweep* plan, double* betas, int32_t iteration, double nu, double t0,
+                                            void* stream) {
+  if (!plan || !betas) return set_error(GBK_EINVAL, "gbk_sweep_adapt_temps: null argument");
+  if (!(nu > 0.0) || !(t0 > 0.0) || iteration < 0) return set_error(GBK_EINVAL, "gbk_sweep_adapt_temps: bad schedule");
+  const double kappa = t0 / (nu * ((double)iteration + t0));
+  const int nb = plan->d.n_bands;
+  k_adapt_ladder<<<(nb + 127) / 128, 128, 0, (cudaStream_t)stream>>>(betas, plan->swap_acc, nb, plan->d.n_temps,
+                                                                     plan->d.n_walkers, kappa);
+  return check_launch("gbk_sweep_adapt_temps");
 }

@@ -353,3 +353,33 @@ def test_sweep_fp64_with_group_stretch_matches_oracle():
     # group moves happened and some were accepted
     moved = [r for r in trace if r["kind"] == 0 and r["accepted"]]
     assert len(moved) > 0
+
+
+def test_ladder_adaptation_matches_oracle():
+    # one FP64 sweep (decisions identical on both sides), then every band's ladder adapted
+    # from that sweep's swap acceptance: the oracle's update and the GPU's agree to 1e-12
+    torch = torch_cuda()
+    from paper_2405_04690_gb300 import _lib as L
+    cfg, state, _, _ = small_ensemble(seed=18, n_temps=4, n_walkers=3, betas=(1.0, 0.6, 0.3, 0.0))
+    ora = copy_state(state)
+    trace = OM.sweep(cfg, ora, 0)
+    acc = OM.swap_acceptance(cfg, trace)
+    want = np.array([OM.adapt_ladder(cfg.betas[b], acc[b], 7) for b in range(cfg.n_bands)])
+    dev = torch.device("cuda")
+    ctx = L.Context(cfg.tobs, 15.0, cfg.k0, cfg.n_bins)
+    plan = L.SweepPlan(ctx, cfg.n_temps, cfg.n_walkers, cfg.n_bands, cfg.n_max, NB, cfg.band_k0, cfg.sigma,
+                       L.GBK_FP64, f_min=cfg.f_min, f_max=cfg.f_max)
+    P = torch.from_numpy(state["params"].copy()).to(dev)
+    E = torch.from_numpy(state["exists"].astype(np.uint8)).to(dev)
+    R = torch.from_numpy(state["resid"].copy()).to(dev)
+    betas = torch.from_numpy(np.ascontiguousarray(cfg.betas)).to(dev)
+    psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
+    L.gb_sweep(plan, P, E, betas, L.residual_struct(R, FRAC), L.psd_struct(psdp), key64(cfg), 0, ALL | L.SWEEP_REFRESH)
+    L.gbk_sweep_adapt_temps(plan, betas, 7)
+    L.gbk_sync_status(ctx)
+    assert np.array_equal(E.cpu().numpy().astype(bool), ora["exists"])
+    got = betas.cpu().numpy()
+    assert acc[:, 1:].sum() > 0
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
+    plan.close()
+    ctx.close()

@@ -297,3 +297,28 @@ def test_prior_only_sweeps_with_group_stretch_keep_the_prior():
     u = np.asarray(u)
     for d in (0, 2, 3, 5):
         assert stats.kstest(u[::3, d], "uniform").pvalue > 1e-3, d
+
+
+def test_ladder_adaptation_balances_the_swap_rates():
+    b = np.array([1.0, 1 / 1.2, 1 / 1.44, 1 / 1.728, 0.0])
+    # equal acceptances: the ladder does not move
+    np.testing.assert_allclose(OM.adapt_ladder(b, [0, 0.4, 0.4, 0.4, 0.4], 0), b, rtol=1e-14)
+    # a rung pair that swaps more often than the next one widens its gap
+    out = OM.adapt_ladder(b, [0, 0.9, 0.2, 0.4, 0.4], 0)
+    assert 1 / out[1] - 1 > 1 / b[1] - 1
+    assert out[0] == 1.0 and out[-1] == 0.0 and np.all(np.diff(out) < 0)
+    # one step by hand: S_1 = ln(0.2) + (t0/(nu t0)) (0.9 - 0.2)
+    assert abs(1 / out[1] - (1 + math.exp(math.log(0.2) + 0.01 * 0.7))) < 1e-13
+    # the step size decays as t0 / (t + t0)
+    late = OM.adapt_ladder(b, [0, 0.9, 0.2, 0.4, 0.4], 99000)
+    assert abs(1 / late[1] - 1.2) < 0.02 * abs(1 / out[1] - 1.2)
+    # iterated with rates that fall with the gap, the rates equalise
+    g = np.random.default_rng(0)
+    lad = b.copy()
+    for it in range(3000):
+        temps = 1 / lad[:-1]
+        rates = [0.0] + [math.exp(-2.0 * (temps[i] - temps[i - 1])) for i in range(1, len(temps))] + [0.3]
+        lad = OM.adapt_ladder(lad, rates, it, nu=10.0, t0=100.0)
+    temps = 1 / lad[:-1]
+    r = [math.exp(-2.0 * (temps[i] - temps[i - 1])) for i in range(1, len(temps))] + [0.3]
+    assert max(r) - min(r) < 0.05, r
