@@ -332,6 +332,18 @@ def run_uneven(torch, L, dev, stream, seed, n_prop=200000, reps=10):
             "proposals_per_s": n_prop / (ms * 1e-3), "ms_per_batch": ms, "per_N": per_n}
 
 
+def reduce_over_ranks(torch, dist, world, device, ms, work):
+    """Weak scaling (one replica of the workload per rank): the slowest rank's time and the
+    sum of every rank's work. Single process: the values themselves."""
+    if world <= 1:
+        return float(ms), float(work)
+    tm = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    tw = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tw, op=dist.ReduceOp.SUM)
+    return float(tm.item()), float(tw.item())
+
+
 def run_ess(torch, L, S, step, stats, stream, n_sweeps, flags=0, pairs=None, group=None):
     """ESS/s: integrated autocorrelation time of every cold walker's total log-likelihood
     (Eq. like on its residual) over n_sweeps sweeps (first quarter discarded). Optionally
@@ -557,16 +569,9 @@ def run_ours(args):
     L.gbk_sync_status(S["ctx"])
     st = stats.cpu().numpy()
     ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    ms_step = float(np.sum(ms)) / args.steps
-    t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_step = float(t.item())
-    props_step = float(st[:4, 0].sum()) / args.steps
-    total = torch.tensor([props_step], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(total, op=dist.ReduceOp.SUM)
-    value = float(total.item()) / (ms_step * 1e-3)
+    ms_step, total_props = reduce_over_ranks(torch, dist, world, dev, float(np.sum(ms)) / args.steps,
+                                             float(st[:4, 0].sum()) / args.steps)
+    value = total_props / (ms_step * 1e-3)
     # roofline of the band kernel (in-model + RJ): algorithmic flops / its device time
     wf, ev = float(st[4, 0]), float(st[4, 1])
     band_ms = kms[2] / args.steps
@@ -595,12 +600,8 @@ def run_ours(args):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    e2e_props = float(stats[:4, 0].sum().item()) / args.steps
-    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(e2e_t.item())
+    e2e_ms, e2e_props = reduce_over_ranks(torch, dist, world, dev, e0.elapsed_time(e1) / args.steps,
+                                          float(stats[:4, 0].sum().item()) / args.steps)
     h2d = S["P"].numel() * 8 + S["E"].numel()
     d2h = h2d + 80
 
@@ -792,7 +793,7 @@ def run_ours(args):
                      "kernel": "k_band<float,256> (in-model + flip-all RJ)",
                      "peak_note": "FP32 ALU: 152 SMs x 128 lanes x 2 (FMA) x 2.07 GHz (derived, not measured)",
                      "flops_per_waveform": flops_per_waveform(), "flops_per_evaluation": flops_per_evaluation()},
-        "e2e": {"value": e2e_props * world / (e2e_ms * 1e-3), "unit": "proposals/s",
+        "e2e": {"value": e2e_props / (e2e_ms * 1e-3), "unit": "proposals/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": 6 * args.steps,
         "clocks": clk,
