@@ -1246,7 +1246,7 @@ static gbk_status prep(K kernel, size_t per_warp, int64_t items, int* grid, int*
   return GBK_OK;
 }
 
-static gbk_sweep* g_timing_plan = nullptr;  // plan whose kernels are being timed (set per call)
+static thread_local gbk_sweep* g_timing_plan = nullptr;  // plan whose kernels are being timed (per host thread)
 static void ev_rec(int parity, int which, int edge, cudaStream_t st) {
   if (g_timing_plan && g_timing_plan->timed) cudaEventRecord(g_timing_plan->ev[parity][which][edge], st);
 }
@@ -1271,7 +1271,7 @@ static gbk_status run_refresh(SweepArgs& a, cudaStream_t st) {
   return check_launch("gb_sweep(refresh)");
 }
 
-static gbk_sweep* g_active_plan = nullptr;   // plan of the gb_sweep call in progress
+static thread_local gbk_sweep* g_active_plan = nullptr;   // plan of the gb_sweep call in progress (per host thread)
 
 // Learned proposal of one half sweep: features of the opened windows -> network ->
 // mixture rows (or mixture rows straight from the caller's table).
