@@ -77,18 +77,18 @@ struct gbk_ctx {
 // Mixture-density network workspace (gbk_mdn.cu).
 struct gbk_mdn {
   int32_t max_batch;
-  int64_t ldt;           // row length of the transposed copies (max_batch rounded up to 8)
+  int64_t ldt;           // row length of the transposed copies (2 x max_batch rounded up to 8)
   float* pf;             // float32 copy of the parameters (biases of the forward pass)
   __nv_bfloat16* pb;     // BF16 copy (weights, [out][in])
-  __nv_bfloat16* pbT;    // BF16 W^T [in][out] of layers 2-4
+  __nv_bfloat16* pbT;    // BF16 [W^T | W^T] [in][2 out] of layers 2-4
   __nv_bfloat16* h[3];   // hidden activations [max_batch][512]
-  __nv_bfloat16* hT[3];  // and transposed [512][ldt]
+  __nv_bfloat16* hT[3];  // and transposed twice, [h^T | h^T] [512][ldt]
   float* raw;            // [max_batch][272]
-  __nv_bfloat16* g4;     // d loss / d raw [max_batch][272]
-  __nv_bfloat16* g4T;    // and transposed [272][ldt]
-  __nv_bfloat16* g[2];   // back-propagated signals [max_batch][512]
-  __nv_bfloat16* gT[2];  // and transposed [512][ldt]
-  __nv_bfloat16* xT;     // input features transposed [1024][ldt]
+  __nv_bfloat16* g4;     // d loss / d raw as BF16 pairs [max_batch][hi 272 | lo 272]
+  __nv_bfloat16* g4T;    // and transposed [272][hi B | lo B] (pitch ldt)
+  __nv_bfloat16* g[2];   // back-propagated signals [max_batch][hi 512 | lo 512]
+  __nv_bfloat16* gT[2];  // and transposed [512][hi B | lo B] (pitch ldt)
+  __nv_bfloat16* xT;     // input features transposed twice, [x^T | x^T] [1024][ldt]
   float* nll;            // [max_batch]
   float* part;           // split-K gradient partials [8][n_params]
   int* err;              // device error word (bounded waits of the tensor-core products)

@@ -11,7 +11,10 @@
 // K-contiguous, so the backward products read transposed copies that the producing kernels
 // write alongside: hidden activations h^T and back-propagated signals g^T (by the GEMM
 // epilogues and the loss kernel), W^T of layers 2-4 (by the parameter update), x^T (by a
-// transpose kernel). Weight gradients are split over the batch into fixed partial slots
+// transpose kernel). The back-propagated signal is kept as a BF16 pair g = hi + lo (about 16
+// significant bits): every backward product contracts over [hi | lo] against a doubled copy
+// of its other operand ([W^T | W^T], [h^T | h^T]), so it sums hi and lo terms in one
+// accumulator. Weight gradients are split over the batch into fixed partial slots
 // and summed in a fixed order by the Adam / reduce kernel, so training is deterministic.
 #include <cuda_bf16.h>
 #include <math.h>
@@ -39,8 +42,9 @@ constexpr int kMaxSplit = 8;
 typedef __nv_bfloat16 bf16;
 
 // transposed weight copies W^T [in][out] of layers 2-4 (the input-gradient products' B)
-constexpr int64_t kOffT2 = 0, kOffT3 = (int64_t)kHid * kHid, kOffT4 = 2 * (int64_t)kHid * kHid;
-constexpr int64_t kNT = kOffT4 + (int64_t)kHid * kOut;
+// (each row doubled: [in][2 out] = [W^T | W^T])
+constexpr int64_t kOffT2 = 0, kOffT3 = 2 * (int64_t)kHid * kHid, kOffT4 = 4 * (int64_t)kHid * kHid;
+constexpr int64_t kNT = kOffT4 + 2 * (int64_t)kHid * kOut;
 
 // -------------------------------------------------------------- tensor-core products
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -131,22 +135,32 @@ static umma::Args margs(gbk_mdn* net, void* C, int64_t ldc) {
   g.split_stride = 0;
   g.CT = nullptr;
   g.ldct = 0;
+  g.ct_dup = 0;
   g.err = net->err;
   return g;
 }
 
-// x [B][1024] -> x^T [1024][ldt] (32 x 32 tiles through shared memory)
-__global__ void k_transpose(const bf16* __restrict__ x, int B, int cols, bf16* __restrict__ xt, int64_t ldt) {
-  __shared__ bf16 t[32][33];
+// Transposes through 32 x 32 shared-memory tiles. split = 0: x [B][cols] -> xt[c][r] and the
+// copy xt[c][B + r]; split = 1: x [B][2 cols] = [hi | lo] -> xt[c][r] = hi, xt[c][B + r] = lo.
+__global__ void k_transpose(const bf16* __restrict__ x, int B, int cols, int split, bf16* __restrict__ xt,
+                            int64_t ldt) {
+  __shared__ bf16 t[2][32][33];
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int64_t ldx = split ? 2 * (int64_t)cols : cols;
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int r = r0 + i, c = c0 + threadIdx.x;
-    if (r < B && c < cols) t[i][threadIdx.x] = x[(int64_t)r * cols + c];
+    if (r < B && c < cols) {
+      t[0][i][threadIdx.x] = x[(int64_t)r * ldx + c];
+      t[1][i][threadIdx.x] = split ? x[(int64_t)r * ldx + cols + c] : t[0][i][threadIdx.x];
+    }
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int c = c0 + i, r = r0 + threadIdx.x;
-    if (r < B && c < cols) xt[(int64_t)c * ldt + r] = t[threadIdx.x][i];
+    if (r < B && c < cols) {
+      xt[(int64_t)c * ldt + r] = t[0][threadIdx.x][i];
+      xt[(int64_t)c * ldt + B + r] = t[1][threadIdx.x][i];
+    }
   }
 }
 
@@ -211,16 +225,21 @@ __global__ void k_mdn_loss(const float* __restrict__ raw, const float* __restric
   for (int o = 8; o > 0; o >>= 1) ce += __shfl_xor_sync(0xffffffffu, ce, o);
   const float lq = cm + logf(ce);
   const float resp = expf(comp - lq);
-  bf16* gr = graw + (int64_t)m * kOut + k * 17;
-  if (h == 0) gr[0] = __float2bfloat16_rn((expf(lpi) - resp) * inv_b);
+  bf16* gr = graw + (int64_t)m * 2 * kOut + k * 17;   // [hi | lo] pairs, row of 2 x 272
+  auto put = [&](int j, float v) {
+    const bf16 hi = __float2bfloat16_rn(v);
+    gr[j] = hi;
+    gr[kOut + j] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  };
+  if (h == 0) put(0, (expf(lpi) - resp) * inv_b);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int d = 4 * h + i;
     const float dx = uu[i] - mu[i];
     const float dmu = dx / (s[i] * s[i]) - (pb[i] - pa[i]) / (s[i] * z[i]);
     const float dls = (dx / s[i]) * (dx / s[i]) - 1.f - (-a[i] * pa[i] + bb[i] * pb[i]) / z[i];
-    gr[1 + d] = __float2bfloat16_rn(-resp * dmu * mu[i] * (1.f - mu[i]) * inv_b);
-    gr[9 + d] = __float2bfloat16_rn(-resp * dls * (float)(kMixSMax - kMixSMin) * sg[i] * (1.f - sg[i]) * inv_b);
+    put(1 + d, -resp * dmu * mu[i] * (1.f - mu[i]) * inv_b);
+    put(9 + d, -resp * dls * (float)(kMixSMax - kMixSMin) * sg[i] * (1.f - sg[i]) * inv_b);
   }
   if (lane == 0) nll[m] = -lq;
 }
@@ -239,7 +258,8 @@ __global__ void k_mean(const float* __restrict__ x, int n, double* __restrict__ 
   if (threadIdx.x == 0) *out = red[0] / (double)n;
 }
 
-// Bias gradients: column sums of g [B][N] over split z's rows, into part + z stride + off.
+// Bias gradients: column sums of g = hi + lo ([B][2N]: [hi | lo]) over split z's rows, into
+// part + z stride + off.
 // Block (32 columns) x (8 row phases); the 8 phase sums are added in a fixed order.
 __global__ void k_colsum(const bf16* __restrict__ g, int B, int N, int kps, float* __restrict__ part,
                          int64_t stride, int64_t off) {
@@ -249,7 +269,8 @@ __global__ void k_colsum(const bf16* __restrict__ g, int B, int N, int kps, floa
   const int r1 = min(B, (z + 1) * kps);
   float s = 0.f;
   if (n < N)
-    for (int r = z * kps + threadIdx.y; r < r1; r += 8) s += __bfloat162float(g[(int64_t)r * N + n]);
+    for (int r = z * kps + threadIdx.y; r < r1; r += 8)
+      s += __bfloat162float(g[(int64_t)r * 2 * N + n]) + __bfloat162float(g[(int64_t)r * 2 * N + N + n]);
   red[threadIdx.y][threadIdx.x] = s;
   __syncthreads();
   if (threadIdx.y == 0 && n < N) {
@@ -284,7 +305,9 @@ __device__ __forceinline__ void store_param(int64_t i, float v, float* pf, bf16*
   else if (i >= kOffW4 && i < kOffB4) { off = kOffW4; tof = kOffT4; nout = kOut; }
   else return;
   const int64_t r = i - off;              // W[o][ii], o = r / 512, ii = r % 512
-  pbt[tof + (r % kHid) * nout + r / kHid] = b;
+  bf16* row = pbt + tof + (r % kHid) * 2 * nout;
+  row[r / kHid] = b;
+  row[nout + r / kHid] = b;
 }
 
 __global__ void k_adam(const float* __restrict__ part, int S, const float* __restrict__ grad, int64_t n,
@@ -353,7 +376,7 @@ int splits_for(int B, int* kps) {
 }
 
 // Forward through the four layers; raw outputs to out (float32 [B][272]). With
-// transposed = true the hidden activations are also written as h^T [512][ldt].
+// transposed = true the hidden activations are also written as [h^T | h^T] [512][ldt].
 gbk_status forward(gbk_mdn* net, const bf16* x, int B, float* out, bool transposed, cudaStream_t st) {
   const int64_t offw[4] = {kOffW1, kOffW2, kOffW3, kOffW4}, offb[4] = {kOffB1, kOffB2, kOffB3, kOffB4};
   const bf16* in = x;
@@ -365,6 +388,7 @@ gbk_status forward(gbk_mdn* net, const bf16* x, int B, float* out, bool transpos
     if (transposed) {
       g.CT = net->hT[l];
       g.ldct = net->ldt;
+      g.ct_dup = 1;
     }
     if ((s = mm<umma::EPI_BIAS_RELU_BF16>(net, in, ldin, net->pb + offw[l], ldin, B, kHid, (int)ldin, g, 1, st))) return s;
     in = net->h[l];
@@ -381,15 +405,15 @@ gbk_status backward(gbk_mdn* net, const bf16* x, const float* u, int B, double* 
   if ((s = forward(net, x, B, net->raw, true, st))) return s;
   k_mdn_loss<<<(B + 7) / 8, 256, 0, st>>>(net->raw, u, B, 1.0f / (float)B, net->g4, net->nll);
   if ((s = check_launch("mdn loss"))) return s;
-  k_transpose<<<dim3((kOut + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(net->g4, B, kOut, net->g4T, net->ldt);
+  k_transpose<<<dim3((kOut + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(net->g4, B, kOut, 1, net->g4T, net->ldt);
   if (loss) {
     k_mean<<<1, 256, 0, st>>>(net->nll, B, loss);
     if ((s = check_launch("mdn loss mean"))) return s;
   }
-  k_transpose<<<dim3(kIn / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(x, B, kIn, net->xT, net->ldt);
+  k_transpose<<<dim3(kIn / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(x, B, kIn, 0, net->xT, net->ldt);
   if ((s = check_launch("mdn input transpose"))) return s;
   int kps;
-  const int S = splits_for(B, &kps);
+  const int S = splits_for(2 * B, &kps);   // the weight-gradient contraction runs over [hi | lo]: 2 B
   *S_out = S;
   const int64_t offw[4] = {kOffW1, kOffW2, kOffW3, kOffW4}, offb[4] = {kOffB1, kOffB2, kOffB3, kOffB4};
   const int64_t offt[4] = {0, kOffT2, kOffT3, kOffT4};
@@ -402,20 +426,23 @@ gbk_status backward(gbk_mdn* net, const bf16* x, const float* u, int B, double* 
     umma::Args gw = margs(net, net->part + offw[l], nin[l]);
     gw.kps = kps;
     gw.split_stride = kNParams;
-    if ((s = mm<umma::EPI_PART_F32>(net, gcurT, net->ldt, hinT, net->ldt, nout[l], nin[l], B, gw, S, st))) return s;
+    if ((s = mm<umma::EPI_PART_F32>(net, gcurT, net->ldt, hinT, net->ldt, nout[l], nin[l], 2 * B, gw, S, st)))
+      return s;
     k_colsum<<<dim3((nout[l] + 31) / 32, S), dim3(32, 8), 0, st>>>(gcur, B, nout[l], kps, net->part, kNParams,
                                                                     offb[l]);
     if ((s = check_launch("mdn bias gradient"))) return s;
     if (l == 0) break;
-    // g_prev[m][i] = sum_o g[m][o] W[o][i] = g . (W^T)^T, kept where the forward activation was positive
+    // g_prev[m][i] = sum_o g[m][o] W[o][i] = [hi | lo] . [W^T | W^T]^T (contraction over 2 nout),
+    // kept where the forward activation was positive and stored again as a hi / lo pair
     bf16* gn = net->g[l & 1];
     bf16* gnT = net->gT[l & 1];
-    umma::Args gx = margs(net, gn, nin[l]);
+    umma::Args gx = margs(net, gn, 2 * nin[l]);
     gx.mask = net->h[l - 1];
     gx.ldm = kHid;
     gx.CT = gnT;
     gx.ldct = net->ldt;
-    if ((s = mm<umma::EPI_MASK_BF16>(net, gcur, nout[l], net->pbT + offt[l], nout[l], B, nin[l], nout[l], gx, 1, st)))
+    if ((s = mm<umma::EPI_MASK_SPLIT>(net, gcur, 2 * nout[l], net->pbT + offt[l], 2 * nout[l], B, nin[l],
+                                       2 * nout[l], gx, 1, st)))
       return s;
     gcur = gn;
     gcurT = gnT;
@@ -445,13 +472,13 @@ extern "C" gbk_status mdn_create(gbk_mdn** out, int32_t max_batch) {
   if (max_batch < 1 || max_batch > (1 << 22)) return set_error(GBK_EINVAL, "mdn_create: max_batch out of range");
   gbk_mdn* n = new gbk_mdn();
   n->max_batch = max_batch;
-  n->ldt = (max_batch + 7) / 8 * 8;   // transposed copies: rows 16-byte aligned
+  n->ldt = 2 * ((max_batch + 7) / 8 * 8);   // transposed [hi | lo] / doubled copies: rows 16-byte aligned
   const size_t B = (size_t)max_batch, T = (size_t)n->ldt;
   bool ok = cudaMalloc(&n->pf, kNParams * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&n->pb, kNParams * sizeof(bf16)) == cudaSuccess &&
             cudaMalloc(&n->pbT, kNT * sizeof(bf16)) == cudaSuccess &&
             cudaMalloc(&n->raw, B * kOut * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&n->g4, B * kOut * sizeof(bf16)) == cudaSuccess &&
+            cudaMalloc(&n->g4, B * 2 * kOut * sizeof(bf16)) == cudaSuccess &&
             cudaMalloc(&n->g4T, T * kOut * sizeof(bf16)) == cudaSuccess &&
             cudaMalloc(&n->xT, T * kIn * sizeof(bf16)) == cudaSuccess &&
             cudaMalloc(&n->nll, B * sizeof(float)) == cudaSuccess &&
@@ -463,7 +490,7 @@ extern "C" gbk_status mdn_create(gbk_mdn** out, int32_t max_batch) {
     ok = cudaMalloc(&n->h[i], B * kHid * sizeof(bf16)) == cudaSuccess &&
          cudaMalloc(&n->hT[i], T * kHid * sizeof(bf16)) == cudaSuccess;
   for (int i = 0; i < 2 && ok; ++i)
-    ok = cudaMalloc(&n->g[i], B * kHid * sizeof(bf16)) == cudaSuccess &&
+    ok = cudaMalloc(&n->g[i], B * 2 * kHid * sizeof(bf16)) == cudaSuccess &&
          cudaMalloc(&n->gT[i], T * kHid * sizeof(bf16)) == cudaSuccess;
   if (ok) ok = cudaMemset(n->err, 0, sizeof(int)) == cudaSuccess;
   if (!ok) {

@@ -25,7 +25,12 @@ namespace umma {
 constexpr int kBM = 128, kBK = 64, kStages = 4, kThreads = 128;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
-enum { EPI_BIAS_RELU_BF16 = 0, EPI_BIAS_F32 = 1, EPI_MASK_BF16 = 2, EPI_PART_F32 = 3 };
+// EPI_BIAS_RELU_BF16: relu(acc + bias) -> BF16 C (and CT; with ct_dup also CT[n ldct + M + m]);
+// EPI_BIAS_F32: acc + bias -> float32 C; EPI_PART_F32: acc -> float32 partial slot z;
+// EPI_MASK_SPLIT: v = acc where mask > 0, else 0, stored as the BF16 pair hi = bf16(v),
+// lo = bf16(v - hi): C[m ldc + n] = hi, C[m ldc + N + n] = lo, CT[n ldct + m] = hi,
+// CT[n ldct + M + m] = lo (about 16 significant bits for the back-propagated signal).
+enum { EPI_BIAS_RELU_BF16 = 0, EPI_BIAS_F32 = 1, EPI_MASK_SPLIT = 2, EPI_PART_F32 = 3 };
 
 struct Args {
   int M, N, K, kps;                    // kps: k range per split (multiple of 64)
@@ -36,6 +41,7 @@ struct Args {
   int64_t ldc, split_stride;
   __nv_bfloat16* CT;                   // optional transposed BF16 copy: CT[n ldct + m]
   int64_t ldct;
+  int ct_dup;                          // EPI_BIAS_RELU_BF16: also CT[n ldct + M + m] (a second copy)
   int* err;                            // device error word
 };
 
@@ -223,15 +229,16 @@ k_umma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
       if (row >= g.M || n0 + c0 >= g.N) continue;
       const int nv = min(32, g.N - (n0 + c0));   // N is a multiple of 8
       const int nb = n0 + c0;
-      if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_MASK_BF16) {
+      if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_MASK_SPLIT) {
         __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(g.C) + (int64_t)row * g.ldc + nb;
-        const __nv_bfloat16* mk = EPI == EPI_MASK_BF16 ? g.mask + (int64_t)row * g.ldm + nb : nullptr;
+        const __nv_bfloat16* mk = EPI == EPI_MASK_SPLIT ? g.mask + (int64_t)row * g.ldm + nb : nullptr;
 #pragma unroll
         for (int q = 0; q < 32; q += 8) {
           if (q >= nv) break;
           __align__(16) __nv_bfloat16 o[8];
+          __align__(16) __nv_bfloat16 lo[8];
           uint4 mv;
-          if (EPI == EPI_MASK_BF16) mv = *reinterpret_cast<const uint4*>(mk + q);
+          if (EPI == EPI_MASK_SPLIT) mv = *reinterpret_cast<const uint4*>(mk + q);
           const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mv);
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
@@ -239,11 +246,19 @@ k_umma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
             if (EPI == EPI_BIAS_RELU_BF16) x = fmaxf(x + g.bias[nb + q + e], 0.f);
             else if (!(__bfloat162float(mb[e]) > 0.f)) x = 0.f;
             o[e] = __float2bfloat16_rn(x);
+            if (EPI == EPI_MASK_SPLIT) lo[e] = __float2bfloat16_rn(x - __bfloat162float(o[e]));
           }
           *reinterpret_cast<uint4*>(C + q) = *reinterpret_cast<const uint4*>(o);
-          if (g.CT)
+          if (EPI == EPI_MASK_SPLIT) *reinterpret_cast<uint4*>(C + g.N + q) = *reinterpret_cast<const uint4*>(lo);
+          if (g.CT) {
 #pragma unroll
-            for (int e = 0; e < 8; ++e) g.CT[(int64_t)(nb + q + e) * g.ldct + row] = o[e];
+            for (int e = 0; e < 8; ++e) {
+              __nv_bfloat16* ct = g.CT + (int64_t)(nb + q + e) * g.ldct + row;
+              ct[0] = o[e];
+              if (EPI == EPI_MASK_SPLIT) ct[g.M] = lo[e];
+              else if (g.ct_dup) ct[g.M] = o[e];
+            }
+          }
         }
       } else {
         float* C = reinterpret_cast<float*>(g.C) + (EPI == EPI_PART_F32 ? (int64_t)blockIdx.z * g.split_stride : 0) +

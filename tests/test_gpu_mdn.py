@@ -10,9 +10,14 @@ network rounds every weight matrix and hidden activation to BF16; the oracle's
 ``quantized`` network applies the same roundings and computes everything else in float64,
 so the forward outputs agree to float32 accumulation error (held to 1e-4), and against the
 unrounded float64 network to a few u over four layers (held to 1e-2). The backward pass
-also rounds the back-propagated signal to BF16 at each layer; through the sums over the
-batch (whose terms partly cancel) that gives ~3e-3 on the first layer's weights, held to
-1e-2 against the gradient of the quantized network. The loss, a batch mean, to 1e-3.
+keeps the back-propagated signal as a BF16 pair hi + lo (~16 bits) and accumulates in
+float32, so on its own it adds ~1e-4; what remains on a random batch comes from the forward
+pass: float32 and float64 accumulation put a pre-activation within ~1e-4 of zero on
+opposite sides of the ReLU kink now and then, and each such flip moves one whole term of a
+batch sum whose terms largely cancel (~1e-2 at 1000 rows, growing with the batch). Hence
+two gradient tests: every row of a random batch against 1e-2, and the rows whose
+pre-activations all keep 1e-3 of their RMS away from zero (chosen from the oracle's forward
+pass) against 1e-3. The loss, a batch mean, to 1e-3.
 The gradient of the quantized network differs from the unrounded network's by up to ~7%
 on the first layer: the two are gradients of different functions, and the trained
 function is the quantized one.
@@ -65,30 +70,58 @@ def test_forward_matches_oracle(B):
     net.close()
 
 
-def test_backward_matches_oracle_layer_by_layer():
-    torch = torch_cuda()
+def _backward_errors(torch, theta, x, u):
+    """Per-layer relative errors (W1, b1, ..., W4, b4) of the library's gradient against the
+    quantized oracle network's, and the loss against the oracle's."""
     from paper_2405_04690_gb300 import _lib as L
-    g = np.random.default_rng(7)
-    B = 1000
-    theta, x, pt, xt = _setup(torch, g, B)
-    u = g.uniform(0.02, 0.98, (B, MD.N_DIM)).astype(np.float32).astype(np.float64)
+    B = x.shape[0]
     net = L.Mdn(B)
-    L.mdn_set_params(net, pt)
+    L.mdn_set_params(net, torch.from_numpy(theta.astype(np.float32)).cuda())
     grad = torch.zeros(MD.n_params(), dtype=torch.float32, device="cuda")
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    xt = torch.from_numpy(x.astype(np.float32)).cuda().to(torch.bfloat16)
     L.mdn_backward(net, xt, torch.from_numpy(u.astype(np.float32)).cuda(), grad, loss)
     L.mdn_status(net)
+    net.close()
     got = grad.cpu().numpy().astype(np.float64)
     want = MD.backward(theta, x, u, quantized=True)
     nll = MD.nll(theta, x, u)
     assert abs(loss.item() - nll) < 1e-3 * abs(nll), (loss.item(), nll)
-    k = 0
-    for li, (o, i) in enumerate(MD.LAYERS):
-        for name, n in (("W", o * i), ("b", o)):
-            e = rel_l2(got[k:k + n], want[k:k + n])
-            assert e < 1e-2, (li, name, e)
+    errs, k = [], 0
+    for o, i in MD.LAYERS:
+        for n in (o * i, o):
+            errs.append(rel_l2(got[k:k + n], want[k:k + n]))
             k += n
-    net.close()
+    return errs
+
+
+def test_backward_matches_oracle_layer_by_layer():
+    torch = torch_cuda()
+    g = np.random.default_rng(7)
+    B = 1000
+    theta, x, _, _ = _setup(torch, g, B)
+    u = g.uniform(0.02, 0.98, (B, MD.N_DIM)).astype(np.float32).astype(np.float64)
+    errs = _backward_errors(torch, theta, x, u)
+    assert max(errs) < 1e-2, errs
+
+
+def test_backward_to_1e3_away_from_relu_kinks():
+    """Rows whose oracle pre-activations all keep 1e-3 of their RMS away from zero: both
+    sides then take the same ReLU branches, and the gradient is held to 1e-3 (a few hundred
+    rows: three 128-row tiles, two k-splits of the weight-gradient products)."""
+    torch = torch_cuda()
+    g = np.random.default_rng(7)
+    B = 1000
+    theta, x, _, _ = _setup(torch, g, B)
+    u = g.uniform(0.02, 0.98, (B, MD.N_DIM)).astype(np.float32).astype(np.float64)
+    _, acts = MD.forward(theta, x, quantized=True)
+    keep = np.ones(B, bool)
+    for li, (w, b) in enumerate(MD.unpack(theta)[:3]):
+        z = acts[li] @ MD.to_bf16(w).T + b
+        keep &= (np.abs(z) / np.sqrt(np.mean(z * z))).min(axis=1) > 1e-3
+    assert 257 <= keep.sum() < B, keep.sum()
+    errs = _backward_errors(torch, theta, x[keep], u[keep])
+    assert max(errs) < 1e-3, errs
 
 
 def test_adam_matches_oracle_update():
