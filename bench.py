@@ -538,9 +538,14 @@ def run_ours(args):
     key = 0x5EED0000 + rank
     sweep_no = [0]
 
+    xfer = torch.zeros(2, dtype=torch.int32, device=dev)   # ownership transfers: moved, blocked
+
     def step(flags_extra=0):
+        # one sweep (in-model + flip-all RJ + swaps over both parities), then the band-edge
+        # ownership transfer of the cold chain (Sec. V.D)
         L.gb_sweep(S["plan"], S["P"], S["E"], S["betas"], S["R"], S["psd"], key, sweep_no[0],
                    1 | 2 | 4 | flags_extra, stats=stats, stream=stream)
+        L.gbk_sweep_transfer(S["plan"], S["P"], S["E"], xfer, stream)
         sweep_no[0] += 1
 
     step(L.SWEEP_REFRESH)                  # fills the waveform cache
@@ -548,6 +553,7 @@ def run_ours(args):
         step()
     L.gbk_sync_status(S["ctx"])
     stats.zero_()
+    xfer.zero_()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kms = np.zeros(4)
     clocks = ClockSampler()
@@ -568,6 +574,7 @@ def run_ours(args):
     clk = clocks.stop(local)
     L.gbk_sync_status(S["ctx"])
     st = stats.cpu().numpy()
+    xf = xfer.cpu().numpy()
     ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     ms_step, total_props = reduce_over_ranks(torch, dist, world, dev, float(np.sum(ms)) / args.steps,
                                              float(st[:4, 0].sum()) / args.steps)
@@ -783,6 +790,8 @@ def run_ours(args):
                    "acceptance": {k: (float(st[i, 1]) / max(1.0, float(st[i, 0]))) for i, k in
                                   enumerate(["in_model", "birth", "death", "swap"])},
                    "waveforms_per_step": wf / args.steps,
+                   "ownership_transfers_per_step": {"moved": float(xf[0]) / args.steps,
+                                                    "blocked": float(xf[1]) / args.steps},
                    "kernel_ms_per_step": {"open": kms[1] / args.steps, "band": band_ms, "swap": kms[3] / args.steps},
                    "parallelism": "replica per GPU"},
         "roofline": {"bound": "alu", "achieved": ach, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
@@ -795,7 +804,7 @@ def run_ours(args):
                      "flops_per_waveform": flops_per_waveform(), "flops_per_evaluation": flops_per_evaluation()},
         "e2e": {"value": e2e_props / (e2e_ms * 1e-3), "unit": "proposals/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 9 * args.steps,   # per step: open, band, swap per parity; transfer assign, apply, sums
         "clocks": clk,
         "wall_s_timed_region": wall,
     }

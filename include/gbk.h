@@ -439,6 +439,21 @@ gbk_status gbk_sweep_set_proposal(gbk_sweep* plan, gbk_mdn* net, const float* ra
 gbk_status gbk_sweep_adapt_temps(gbk_sweep* plan, double* betas, int32_t iteration, double nu, double t0,
                                  void* stream);
 
+/* Band-edge ownership transfer (Sec. V.D): sources may wander half a band into each
+ * neighbour while their band is sampled; afterwards a cold-chain source of band b whose f0
+ * lies in the own bins of a neighbour b' = b -+ 1 (floor((f0 Tobs - band_k0) / band_bins)
+ * = b') moves to a free slot of b'. Decided on the state at the call, every move at once:
+ * band b' takes candidates from b' - 1, then from b' + 1, each in ascending slot order, into
+ * its free slots in ascending order; candidates beyond its free slots stay (blocked), as do
+ * sources whose owner is outside [0, n_bands) and all hotter chains. The model does not
+ * change (the residual is untouched): only which band's slots hold a source. The plan's
+ * template caches move with the sources, so params/exists must be the state left by the
+ * last gb_sweep (caches current), and the next gb_sweep needs no refresh.
+ *   params, exists  the sweep state (device), updated in place
+ *   counts          optional device int32[2]: moved and blocked sources are ADDED (NULL: none)
+ * Three small kernels plus the cold chain's template sums (n_walkers x n_bands warps). */
+gbk_status gbk_sweep_transfer(gbk_sweep* plan, double* params, uint8_t* exists, int32_t* counts, void* stream);
+
 /* Group stretch in-model moves (the paper's in-model proposal, Eq. stretch with a stationary
  * group): builds every band's stationary group from the current cold chain -- the sources of
  * bands b-1, b, b+1 of all walkers, sorted by f0 -- and makes a fraction `frac` of the

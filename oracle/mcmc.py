@@ -553,6 +553,43 @@ def swap_band(cfg, state, rhos, b, parity, sweep, trace):
                                                cfg.frac_bits)
 
 
+def owner_band(cfg, f0):
+    """Sub-band whose own bins hold f0 (Sec. V.D): floor((f0 T - band_k0) / nb)."""
+    return math.floor((f0 * cfg.tobs - cfg.band_k0) / cfg.nb)
+
+
+def transfer_ownership(cfg, state):
+    """Band-edge ownership transfer of the cold chain (Sec. V.D): a cold-chain source of band b
+    whose f0 now lies in the own bins of a neighbour b' = b -+ 1 moves to a free slot of b'.
+
+    Readings: decided on the state at the call (every move at once); band b' takes its
+    candidates from b' - 1 first, then from b' + 1, each in ascending slot order, into its
+    free slots in ascending order, and a candidate beyond b''s free slots stays where it is
+    ("blocked"). Sources whose owner lies outside [0, n_bands), and the hotter chains, stay.
+    The model (the set of sources, the residual) does not change: only which band's slots
+    hold a source. Returns (moved, blocked); state is updated in place."""
+    P0 = state["params"][0].copy()
+    E0 = state["exists"][0].copy()
+    moved = blocked = 0
+    for w in range(cfg.n_walkers):
+        for b in range(cfg.n_bands):
+            free = [s for s in range(cfg.n_max) if not E0[w, b, s]]
+            cands = []
+            for nb_ in (b - 1, b + 1):
+                if 0 <= nb_ < cfg.n_bands:
+                    cands += [(nb_, s) for s in range(cfg.n_max)
+                              if E0[w, nb_, s] and owner_band(cfg, P0[w, nb_, s, 1]) == b]
+            for k, (src_b, s) in enumerate(cands):
+                if k < len(free):
+                    state["params"][0, w, b, free[k]] = P0[w, src_b, s]
+                    state["exists"][0, w, b, free[k]] = True
+                    state["exists"][0, w, src_b, s] = False
+                    moved += 1
+                else:
+                    blocked += 1
+    return moved, blocked
+
+
 def sweep(cfg, state, sweep_index, trace=None, do_swap=True):
     """One sweep: odd bands, then even bands; each half: open, band tasks (Alg. 1 + RJ), swaps (Alg. 2)."""
     if trace is None:

@@ -113,6 +113,7 @@ SIGNATURES = {
     "gbk_psd_plan_destroy": (ctypes.c_int, [_vp]),
     "gb_psd_sweep": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp]),
     "gbk_sweep_adapt_temps": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_double, ctypes.c_double, _vp]),
+    "gbk_sweep_transfer": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "gbk_sweep_update_group": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _i32, _vp]),
     "gb_sweep_features": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(GbkResidual), ctypes.POINTER(GbkPsd), _vp, _vp,
                                          _vp]),
@@ -419,6 +420,15 @@ def gbk_sweep_adapt_temps(plan, betas, iteration, nu=100.0, t0=1000.0, stream=No
     """Adapt every band's ladder from the last sweep's swap acceptance (in place)."""
     _check(lib().gbk_sweep_adapt_temps(plan.handle, _dev(betas, torch.float64, "betas"), int(iteration), float(nu),
                                        float(t0), _stream(stream)), "gbk_sweep_adapt_temps")
+
+
+def gbk_sweep_transfer(plan, params, exists, counts=None, stream=None):
+    """Band-edge ownership transfer of the cold chain (in place); counts: optional int32[2]
+    device tensor to which (moved, blocked) are added."""
+    _check(lib().gbk_sweep_transfer(plan.handle, _dev(params, torch.float64, "params"),
+                                    _dev(exists, torch.uint8, "exists"),
+                                    None if counts is None else _dev(counts, torch.int32, "counts"),
+                                    _stream(stream)), "gbk_sweep_transfer")
 
 
 def gbk_sweep_update_group(plan, params, exists, frac, n_friends=32, stream=None):

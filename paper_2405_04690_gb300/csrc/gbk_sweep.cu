@@ -2,6 +2,7 @@
 // (Alg. 1, App. C), ensemble-permuted tempering swaps (Alg. 2, Eq. temp-final).
 #include <math.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include "gbk_internal.cuh"
 #include "gbk_mix.cuh"
@@ -39,6 +40,7 @@ struct gbk_sweep {
   double grp_frac;
   int n_friends;
   int32_t* swap_acc;        // accepted swaps of the last sweep per band and rung [B][T]
+  int32_t* xfer_dest;       // ownership transfer: destination (band n_max + slot) of every cold slot, or -1
 };
 
 namespace gbk {
@@ -618,11 +620,12 @@ __device__ __noinline__ void write_hsum(const SweepArgs& a, int t, int w, int b,
   __syncwarp();
 }
 
+// (temperatures [0, n_t): all of them after a refresh, the cold chain after a transfer)
 template <typename T, int N>
-__global__ void __launch_bounds__(kSwWarps * 32) k_hsum(const SweepArgs a) {
+__global__ void __launch_bounds__(kSwWarps * 32) k_hsum(const SweepArgs a, int n_t) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const gbk_sweep_desc& d = a.d;
-  const int64_t ntask = (int64_t)d.n_temps * d.n_walkers * d.n_bands;
+  const int64_t ntask = (int64_t)n_t * d.n_walkers * d.n_bands;
   for (int64_t x = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; x < ntask; x += (int64_t)gridDim.x * (blockDim.x >> 5)) {
     const int t = (int)(x / ((int64_t)d.n_walkers * d.n_bands));
     const int rem = (int)(x % ((int64_t)d.n_walkers * d.n_bands));
@@ -1266,9 +1269,113 @@ static gbk_status run_refresh(SweepArgs& a, cudaStream_t st) {
   if ((s = check_launch("gb_sweep(refresh)"))) return s;
   const int64_t ntask = (int64_t)a.d.n_temps * a.d.n_walkers * a.d.n_bands;
   if ((s = prep(k_hsum<T, N>, 0, ntask, &grid, &thr, &sm))) return s;
-  k_hsum<T, N><<<grid, kSwWarps * 32, 0, st>>>(a);
+  k_hsum<T, N><<<grid, kSwWarps * 32, 0, st>>>(a, a.d.n_temps);
   ev_rec(1, 0, 1, st);
   return check_launch("gb_sweep(refresh)");
+}
+
+// -------------------------------------------------------------- band-edge ownership transfer
+// Sec. V.D: a cold-chain source of band b whose f0 lies in the own bins of a neighbour moves
+// there. Decided on the state at the call: destination band b' (one thread per (w, b'))
+// takes its candidates from b' - 1, then b' + 1, in slot order, into its free slots in slot
+// order; candidates beyond its free slots stay. Every cold slot has at most one destination
+// (its owner), so each entry of dest is written by one thread at most.
+__device__ __forceinline__ long long owner_of(double f0, double tobs, const gbk_sweep_desc& d) {
+  return (long long)floor(__ddiv_rn(dsub(dmul(f0, tobs), (double)d.band_k0), (double)d.band_bins));
+}
+
+__global__ void k_xfer_assign(const double* __restrict__ params, const uint8_t* __restrict__ exists,
+                              const gbk_sweep_desc d, double tobs, int32_t* __restrict__ dest,
+                              int32_t* __restrict__ counts) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= d.n_walkers * d.n_bands) return;
+  const int w = x / d.n_bands, b = x % d.n_bands;
+  const int64_t base = ((int64_t)w * d.n_bands + b) * d.n_max;   // temperature 0
+  int free_s[kMaxSlots];
+  int nfree = 0;
+  for (int s = 0; s < d.n_max; ++s)
+    if (!exists[base + s]) free_s[nfree++] = s;
+  int k = 0, moved = 0, blocked = 0;
+  for (int side = 0; side < 2; ++side) {
+    const int sb = side == 0 ? b - 1 : b + 1;
+    if (sb < 0 || sb >= d.n_bands) continue;
+    const int64_t sbase = ((int64_t)w * d.n_bands + sb) * d.n_max;
+    for (int s = 0; s < d.n_max; ++s) {
+      if (!exists[sbase + s] || owner_of(params[(sbase + s) * 8 + 1], tobs, d) != b) continue;
+      if (k < nfree) {
+        dest[sbase + s] = b * d.n_max + free_s[k];
+        ++moved;
+      } else {
+        ++blocked;
+      }
+      ++k;
+    }
+  }
+  if (counts && (moved | blocked)) {
+    atomicAdd(&counts[0], moved);
+    atomicAdd(&counts[1], blocked);
+  }
+}
+
+// One warp per cold slot with a destination: parameters, occupancy and the cached template
+// (tmpl16 16-byte words) move; reads only dest and the moving slot, writes only the moving
+// slot and its (free) destination.
+__global__ void k_xfer_apply(const SweepArgs a, const int32_t* __restrict__ dest, int tmpl16) {
+  const int lane = threadIdx.x & 31;
+  const gbk_sweep_desc& d = a.d;
+  const int64_t nslot = (int64_t)d.n_walkers * d.n_bands * d.n_max;
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < nslot;
+       x += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t to = dest[x];
+    if (to < 0) continue;
+    const int w = (int)(x / ((int64_t)d.n_bands * d.n_max));
+    const int b = (int)((x / d.n_max) % d.n_bands), s = (int)(x % d.n_max);
+    const int db = to / d.n_max, ds = to % d.n_max;
+    const int64_t y = ((int64_t)w * d.n_bands + db) * d.n_max + ds;
+    if (lane < 8) a.params[y * 8 + lane] = a.params[x * 8 + lane];
+    const int64_t cs = (int64_t)a.setid[(int64_t)w * d.n_bands + b] * d.n_max + s;
+    const int64_t cd = (int64_t)a.setid[(int64_t)w * d.n_bands + db] * d.n_max + ds;
+    const uint4* src = reinterpret_cast<const uint4*>(a.wcache) + cs * tmpl16;
+    uint4* dst = reinterpret_cast<uint4*>(a.wcache) + cd * tmpl16;
+    for (int i = lane; i < tmpl16; i += 32) dst[i] = src[i];
+    if (lane == 0) {
+      a.exists[y] = 1;
+      a.exists[x] = 0;
+    }
+  }
+}
+
+template <typename T, int N>
+static gbk_status run_transfer(gbk_sweep* plan, SweepArgs& a, int32_t* counts, cudaStream_t st) {
+  const gbk_sweep_desc& d = a.d;
+  const int64_t nslot = (int64_t)d.n_walkers * d.n_bands * d.n_max;
+  if (nslot == 0) return GBK_OK;
+  if (cudaMemsetAsync(plan->xfer_dest, 0xff, nslot * sizeof(int32_t), st) != cudaSuccess)
+    return set_error(GBK_ECUDA, "gbk_sweep_transfer: cannot clear the destinations");
+  const int wb = d.n_walkers * d.n_bands;
+  k_xfer_assign<<<(wb + 127) / 128, 128, 0, st>>>(a.params, a.exists, d, a.c.grid.tobs, plan->xfer_dest, counts);
+  gbk_status s;
+  if ((s = check_launch("gbk_sweep_transfer(assign)"))) return s;
+  const int tmpl16 = (int)(2 * N * sizeof(typename CT<T>::C) / 16);
+  const int64_t blocks = (nslot + 7) / 8;
+  k_xfer_apply<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(a, plan->xfer_dest, tmpl16);
+  if ((s = check_launch("gbk_sweep_transfer(apply)"))) return s;
+  int grid = 0, thr = 0;
+  size_t sm = 0;
+  if ((s = prep(k_hsum<T, N>, 0, wb, &grid, &thr, &sm))) return s;
+  k_hsum<T, N><<<grid, kSwWarps * 32, 0, st>>>(a, 1);   // the cold chain's template sums
+  return check_launch("gbk_sweep_transfer(template sums)");
+}
+
+template <typename T>
+static gbk_status transfer_n(gbk_sweep* plan, SweepArgs& a, int32_t* counts, cudaStream_t st) {
+  switch (a.d.band_bins) {
+    case 128: return run_transfer<T, 128>(plan, a, counts, st);
+    case 256: return run_transfer<T, 256>(plan, a, counts, st);
+    case 512: return run_transfer<T, 512>(plan, a, counts, st);
+    case 1024: return run_transfer<T, 1024>(plan, a, counts, st);
+    default: return set_error(GBK_EINVAL, "gbk_sweep_transfer: band_bins %d", a.d.band_bins);
+  }
 }
 
 static thread_local gbk_sweep* g_active_plan = nullptr;   // plan of the gb_sweep call in progress (per host thread)
@@ -1397,6 +1504,8 @@ extern "C" gbk_status gbk_sweep_create(gbk_ctx* ctx, const gbk_sweep_desc* desc,
   if (e == cudaSuccess) e = cudaMalloc(&p->rwbuf, p->rwbuf_bytes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->swap_acc, (size_t)d.n_bands * d.n_temps * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(p->swap_acc, 0, (size_t)d.n_bands * d.n_temps * sizeof(int32_t));
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&p->xfer_dest, (size_t)d.n_walkers * d.n_bands * (d.n_max > 0 ? d.n_max : 1) * sizeof(int32_t));
   if (e != cudaSuccess) {
     cudaFree(p->rsnap);
     cudaFree(p->rho);
@@ -1405,6 +1514,7 @@ extern "C" gbk_status gbk_sweep_create(gbk_ctx* ctx, const gbk_sweep_desc* desc,
     cudaFree(p->setid);
     cudaFree(p->rwbuf);
     cudaFree(p->swap_acc);
+    cudaFree(p->xfer_dest);
     free(p);
     cudaGetLastError();
     return set_error(e == cudaErrorMemoryAllocation ? GBK_ENOMEM : GBK_ECUDA, "gbk_sweep_create: %s",
@@ -1424,6 +1534,7 @@ extern "C" gbk_status gbk_sweep_destroy(gbk_sweep* plan) {
   cudaFree(plan->setid);
   cudaFree(plan->rwbuf);
   cudaFree(plan->swap_acc);
+  cudaFree(plan->xfer_dest);
   cudaFree(plan->mix);
   cudaFree(plan->grp_f0);
   cudaFree(plan->grp_par);
@@ -1697,4 +1808,22 @@ extern "C" gbk_status gbk_sweep_adapt_temps(gbk_sweep* plan, double* betas, int3
   k_adapt_ladder<<<(nb + 127) / 128, 128, 0, (cudaStream_t)stream>>>(betas, plan->swap_acc, nb, plan->d.n_temps,
                                                                      plan->d.n_walkers, kappa);
   return check_launch("gbk_sweep_adapt_temps");
+}
+
+extern "C" gbk_status gbk_sweep_transfer(gbk_sweep* plan, double* params, uint8_t* exists, int32_t* counts,
+                                         void* stream) {
+  if (!plan) return set_error(GBK_EINVAL, "gbk_sweep_transfer: null plan");
+  if (!params || !exists) return set_error(GBK_EINVAL, "gbk_sweep_transfer: null device pointer");
+  SweepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.c = *plan->ctx;
+  a.d = plan->d;
+  a.params = params;
+  a.exists = exists;
+  a.wcache = plan->wcache;
+  a.hsum = plan->hsum;
+  a.setid = plan->setid;
+  a.n_bp_max = plan->n_bp_max;
+  cudaStream_t st = (cudaStream_t)stream;
+  return plan->d.precision == GBK_MIXED ? transfer_n<float>(plan, a, counts, st) : transfer_n<double>(plan, a, counts, st);
 }

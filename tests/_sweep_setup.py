@@ -57,17 +57,22 @@ def small_ensemble(seed=0, n_temps=3, n_walkers=2, n_bands=4, n_max=4, n_per_ban
                     th[7] %= 2 * math.pi
                     params[t, w, b, i] = th
                     exists[t, w, b, i] = True
-    resid = np.empty((n_walkers, 2, n_bins, 2), dtype=np.int64)
     dfix = OR.to_fixed(data, FRAC)
-    for w in range(n_walkers):
-        r = dfix.copy()
-        for b in range(n_bands):
-            for i in range(n_max):
-                if exists[0, w, b, i]:
-                    r = OR.add_sub(r, k0, OW.fastslow_band(params[0, w, b, i], NB), +1, FRAC)
-        resid[w] = r
-    state = {"params": params, "exists": exists, "resid": resid}
+    state = {"params": params, "exists": exists, "resid": cold_residual(cfg, dfix, params, exists)}
     return cfg, state, dfix, s
+
+
+def cold_residual(cfg, dfix, params, exists):
+    """Fixed-point residual of every walker: data minus its cold-chain sources."""
+    resid = np.empty((cfg.n_walkers, 2, cfg.n_bins, 2), dtype=np.int64)
+    for w in range(cfg.n_walkers):
+        r = dfix.copy()
+        for b in range(cfg.n_bands):
+            for i in range(cfg.n_max):
+                if exists[0, w, b, i]:
+                    r = OR.add_sub(r, cfg.k0, OW.fastslow_band(params[0, w, b, i], NB), +1, FRAC)
+        resid[w] = r
+    return resid
 
 
 def _place(cfg, th):

@@ -15,7 +15,7 @@ from oracle import mcmc as OM
 from paper_2405_04690_gb300 import synth
 
 from _common import torch_cuda
-from _sweep_setup import FRAC, NB, copy_state, key64, small_ensemble
+from _sweep_setup import FRAC, NB, cold_residual, copy_state, key64, small_ensemble
 
 pytestmark = pytest.mark.gpu
 
@@ -381,5 +381,84 @@ def test_ladder_adaptation_matches_oracle():
     got = betas.cpu().numpy()
     assert acc[:, 1:].sum() > 0
     np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
+    plan.close()
+    ctx.close()
+
+
+def _edge_state(seed):
+    """Small ensemble with cold sources placed in a neighbour's own bins (inside their own
+    band's allowance): band 1 -> 2 and band 2 -> 1 of walker 0, band 1 -> 2 of walker 1 into
+    a full band 2 (blocked), band 0 below the first band (owner outside: stays), and a hot
+    chain's source in a neighbour (hot chains stay)."""
+    cfg, state, dfix, _ = small_ensemble(seed=seed, n_temps=3, n_walkers=2, n_bands=4, n_max=4, n_per_band=2)
+    P, E = state["params"], state["exists"]
+
+    def at(x):
+        return (cfg.band_k0 + x) / cfg.tobs
+
+    P[0, 0, 1, 0, 1] = at(2 * NB + 30)
+    P[0, 0, 2, 1, 1] = at(2 * NB - 40)
+    P[0, 0, 0, 1, 1] = at(-50)
+    P[1, 0, 1, 1, 1] = at(2 * NB + 60)
+    for s in (2, 3):                       # walker 1: band 2 full, then band 1 -> 2 is blocked
+        P[0, 1, 2, s] = P[0, 1, 2, s - 2]
+        P[0, 1, 2, s, 1] = at(2 * NB + 60 + 50 * s)
+        P[0, 1, 2, s, 0] *= 0.5
+        E[0, 1, 2, s] = True
+    P[0, 1, 1, 1, 1] = at(2 * NB + 20)
+    state["resid"] = cold_residual(cfg, dfix, P, E)
+    return cfg, state
+
+
+def test_ownership_transfer_matches_oracle_and_keeps_the_caches():
+    # FP64: transfer, sweep, transfer, sweep on both sides (the library's caches built first by
+    # a refresh-only call). The transfers move the same sources (counts, occupancy and
+    # parameters bitwise), and the sweeps after them take identical decisions: the moved
+    # templates and the cold template sums the library keeps are those of the new ownership.
+    torch = torch_cuda()
+    from paper_2405_04690_gb300 import _lib as L
+    cfg, state = _edge_state(21)
+    ora = copy_state(state)
+    ora_tr, ora_counts = [], []
+    for k in range(2):
+        ora_counts.append(OM.transfer_ownership(cfg, ora))
+        ora_tr.append(OM.sweep(cfg, ora, k))
+    dev = torch.device("cuda")
+    ctx = L.Context(cfg.tobs, 15.0, cfg.k0, cfg.n_bins)
+    plan = L.SweepPlan(ctx, cfg.n_temps, cfg.n_walkers, cfg.n_bands, cfg.n_max, NB, cfg.band_k0, cfg.sigma,
+                       L.GBK_FP64, f_min=cfg.f_min, f_max=cfg.f_max)
+    P = torch.from_numpy(state["params"].copy()).to(dev)
+    E = torch.from_numpy(state["exists"].astype(np.uint8)).to(dev)
+    R = torch.from_numpy(state["resid"].copy()).to(dev)
+    betas = torch.from_numpy(np.ascontiguousarray(cfg.betas)).to(dev)
+    psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
+    cap = 20000
+    rec = torch.zeros(cap * ctypes.sizeof(L.GbkTraceRec), dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    counts = torch.zeros(2, dtype=torch.int32, device=dev)
+    gpu_counts, bounds = [], [0]
+    L.gb_sweep(plan, P, E, betas, L.residual_struct(R, FRAC), L.psd_struct(psdp), key64(cfg), 0, L.SWEEP_REFRESH)
+    for k in range(2):
+        counts.zero_()
+        L.gbk_sweep_transfer(plan, P, E, counts)
+        gpu_counts.append(tuple(int(v) for v in counts.cpu().numpy()))
+        L.gb_sweep(plan, P, E, betas, L.residual_struct(R, FRAC), L.psd_struct(psdp), key64(cfg), k, ALL,
+                   trace=(rec, cap, cnt))
+        bounds.append(int(cnt.item()))
+    L.gbk_sync_status(ctx)
+    assert bounds[-1] <= cap
+    tr = np.frombuffer(rec.cpu().numpy().tobytes(), dtype=np.dtype(L.TRACE_DTYPE_FIELDS))[:bounds[-1]]
+    assert gpu_counts == ora_counts, (gpu_counts, ora_counts)
+    assert ora_counts[0] == (2, 1)
+    for k in range(2):
+        g, o = _index(tr[bounds[k]:bounds[k + 1]], ora_tr[k])
+        assert set(g) == set(o), (k, len(g), len(o))
+        for key, ro in o.items():
+            assert bool(g[key]["accepted"]) == ro["accepted"], (k, key)
+            if np.isfinite(ro["dlogl"]):
+                assert abs(g[key]["dlogl"] - ro["dlogl"]) < 1e-7, (k, key)
+    assert np.array_equal(E.cpu().numpy().astype(bool), ora["exists"])
+    got = P.cpu().numpy()
+    np.testing.assert_allclose(got[ora["exists"]], ora["params"][ora["exists"]], rtol=1e-13, atol=0)
     plan.close()
     ctx.close()

@@ -322,3 +322,82 @@ def test_ladder_adaptation_balances_the_swap_rates():
     temps = 1 / lad[:-1]
     r = [math.exp(-2.0 * (temps[i] - temps[i - 1])) for i in range(1, len(temps))] + [0.3]
     assert max(r) - min(r) < 0.05, r
+
+
+def _xfer_cfg(n_bands, n_max, n_temps=2, n_walkers=1):
+    tobs, band_k0 = 31457280.0, 65536
+    n_bins = (n_bands + 4) * 256
+    return OM.SweepConfig(tobs=tobs, k0=band_k0 - 512, n_bins=n_bins, band_k0=band_k0, nb=256, n_bands=n_bands,
+                          n_temps=n_temps, n_walkers=n_walkers, n_max=n_max, betas=np.ones((n_bands, n_temps)),
+                          psd=np.ones((n_walkers, n_bins)), sigma=np.ones(8), f_min=1e-4, f_max=1e-2)
+
+
+def _at(cfg, x):
+    """Parameters of a source x bins above band_k0 (only f0 matters to the transfer)."""
+    th = np.zeros(8)
+    th[0] = 1e-22
+    th[1] = (cfg.band_k0 + x) / cfg.tobs
+    return th
+
+
+def test_ownership_transfer_worked_example():
+    # Sec. V.D: a cold source that ended in a neighbour's own bins moves to that band.
+    # Bands of 256 bins: band 0 owns x in [0, 256), band 1 [256, 512), band 2 [512, 768).
+    cfg = _xfer_cfg(3, 3)
+    st = {"params": np.zeros((2, 1, 3, 3, 8)), "exists": np.zeros((2, 1, 3, 3), bool)}
+    layout = {(0, 0): 100, (0, 1): 300, (0, 2): -50,     # band 0: own, band 1's, below band 0 (stays)
+              (1, 0): 400, (1, 1): 450,                  # band 1: two own, slot 2 free
+              (2, 0): 600, (2, 1): 500, (2, 2): 800}     # band 2: own, band 1's (blocked), beyond band 2
+    for (b, s), x in layout.items():
+        for t in range(2):
+            st["params"][t, 0, b, s] = _at(cfg, x)
+            st["exists"][t, 0, b, s] = True
+    hot = (st["params"][1].copy(), st["exists"][1].copy())
+    moved, blocked = OM.transfer_ownership(cfg, st)
+    assert (moved, blocked) == (1, 1)
+    E = st["exists"][0, 0]
+    assert E.tolist() == [[True, False, True], [True, True, True], [True, True, True]]
+    assert np.array_equal(st["params"][0, 0, 1, 2], _at(cfg, 300))
+    assert np.array_equal(st["params"][0, 0, 2, 1], _at(cfg, 500))
+    assert np.array_equal(st["params"][1], hot[0]) and np.array_equal(st["exists"][1], hot[1])
+    # band 1 takes band 0's candidate before band 2's: with room for both, both move
+    st["exists"][0, 0, 1, :2] = False
+    st["exists"][0, 0, 0, 1] = True
+    st["params"][0, 0, 0, 1] = _at(cfg, 260)
+    assert OM.transfer_ownership(cfg, st) == (2, 0)
+    assert np.array_equal(st["params"][0, 0, 1, 0], _at(cfg, 260))
+    assert np.array_equal(st["params"][0, 0, 1, 1], _at(cfg, 500))
+    assert st["exists"][0, 0].tolist() == [[True, False, True], [True, True, True], [True, False, True]]
+
+
+def test_ownership_transfer_keeps_the_model_and_fills_owners():
+    # Random cold states (sources anywhere in their band's allowance): the transfer keeps the
+    # multiset of sources, never overfills a band, moves a source only into its owner; repeated
+    # until nothing moves, every source sits in its owner band unless that band is full or
+    # outside the range.
+    g = np.random.default_rng(5)
+    for trial in range(20):
+        n_bands, n_max, W = 6, 4, 3
+        cfg = _xfer_cfg(n_bands, n_max, n_temps=1, n_walkers=W)
+        st = {"params": np.zeros((1, W, n_bands, n_max, 8)), "exists": g.uniform(size=(1, W, n_bands, n_max)) < 0.6}
+        for w in range(W):
+            for b in range(n_bands):
+                for s in range(n_max):
+                    st["params"][0, w, b, s] = _at(cfg, 256 * b + g.uniform(-128, 384))
+        before = sorted(tuple(st["params"][0, w, b, s]) + (w,) for w, b, s in zip(*np.nonzero(st["exists"][0])))
+        total = 0
+        for _ in range(10):
+            prev = st["exists"][0].copy(), st["params"][0].copy()
+            moved, _ = OM.transfer_ownership(cfg, st)
+            total += moved
+            for w, b, s in zip(*np.nonzero(st["exists"][0] & ~prev[0])):    # arrivals sit in their owner
+                assert OM.owner_band(cfg, st["params"][0, w, b, s, 1]) == b
+            if moved == 0:
+                break
+        after = sorted(tuple(st["params"][0, w, b, s]) + (w,) for w, b, s in zip(*np.nonzero(st["exists"][0])))
+        assert before == after
+        assert total > 0 or trial > 0
+        for w, b, s in zip(*np.nonzero(st["exists"][0])):
+            o = OM.owner_band(cfg, st["params"][0, w, b, s, 1])
+            assert abs(o - b) <= 1
+            assert o == b or not 0 <= o < n_bands or st["exists"][0, w, o].all()
