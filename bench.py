@@ -344,10 +344,12 @@ def reduce_over_ranks(torch, dist, world, device, ms, work):
     return float(tm.item()), float(tw.item())
 
 
-def run_ess(torch, L, S, step, stats, stream, n_sweeps, flags=0, pairs=None, group=None):
+def run_ess(torch, L, S, step, stats, stream, n_sweeps, flags=0, pairs=None, group=None, units=None, keep=10):
     """ESS/s: integrated autocorrelation time of every cold walker's total log-likelihood
     (Eq. like on its residual) over n_sweeps sweeps (first quarter discarded). Optionally
-    collects training pairs of the learned proposal after the burn-in (outside the timing)."""
+    collects training pairs of the learned proposal after the burn-in and the cold slots' unit
+    coordinates of the last `keep` sweeps (for the mixture refit) into `units` (outside the
+    timing)."""
     nb = S["resid"].shape[2]
     nw = S["resid"].shape[0]
     lnl = torch.empty(nw, dtype=torch.float64, device=S["P"].device)
@@ -369,6 +371,11 @@ def run_ess(torch, L, S, step, stats, stream, n_sweeps, flags=0, pairs=None, gro
         series.append(lnl.cpu().numpy().copy())
         if pairs is not None and k >= n_sweeps // 4 and pairs.n < pairs.capacity:
             pairs.add_from_sweep(S["plan"], S["P"], S["E"], S["R"], S["psd"])
+        if units is not None and k >= n_sweeps - keep:
+            d = S["plan"].desc
+            u = torch.empty((d.n_walkers, d.n_bands, d.n_max, 8), dtype=torch.float32, device=S["P"].device)
+            L.gb_sweep_features(S["plan"], S["P"], S["E"], S["R"], S["psd"], None, u, stream)
+            units.append(u)
     st = stats.cpu().numpy()
     x = np.array(series).T[:, n_sweeps // 4:]
     tau = autocorr_time(x)
@@ -407,7 +414,34 @@ def recovered_sources(truth, P, E, tobs, n_bands, band_k0, walkers=4):
     return n
 
 
-def run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, snap, ess_plain):
+def run_gmm_fit(torch, L, units, n_walkers, args, stream):
+    """Refit-RJ mixtures (Sec. V.E, App. G): one EM fit per band on the GPU to the cold-chain
+    sources of the last sweeps, written as a sweep table [W][n_bands][272]; timed."""
+    u = torch.stack(units)                                        # [keep][W][B][n_max][8]
+    nb = u.shape[2]
+    x = u.permute(2, 0, 1, 3, 4).reshape(nb, -1, 8).contiguous()  # [B][keep W n_max][8]
+    raw = torch.empty((n_walkers, nb, 272), dtype=torch.float32, device=x.device)
+    ll = torch.empty(nb, dtype=torch.float64, device=x.device)
+    for _ in range(2):
+        L.gmm_fit(x, raw, n_iter=args.gmm_iters, precision=L.GBK_MIXED, loglike=ll, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        L.gmm_fit(x, raw, n_iter=args.gmm_iters, precision=L.GBK_MIXED, loglike=ll, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    present = int((~torch.isnan(x).any(dim=2)).sum().item())
+    used = int(torch.minimum((~torch.isnan(x).any(dim=2)).sum(dim=1),
+                             torch.tensor(L.gmm_max_points(), device=x.device)).sum().item())
+    return raw, {"bands": nb, "rows_per_band": int(x.shape[1]), "present_points": present, "fitted_points": used,
+                 "components": 16, "em_iterations": args.gmm_iters, "sweeps_kept": len(units), "fit_ms": ms,
+                 "point_iterations_per_s": used * (args.gmm_iters + 1) / (ms * 1e-3),
+                 "precision": "mixed (float32 E-step, float64 M-step)"}
+
+
+def run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, snap, ess_plain, units=None):
     """The learned proposal on the ensemble: training throughput on the cold-chain pairs
     (BF16 tensor cores), then the same ESS run with the proposal, then a search from an
     empty model with and without it."""
@@ -472,6 +506,20 @@ def run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, sn
     out["ess"] = run_ess(torch, L, S, step, stats, stream, args.ess_sweeps, flags=L.SWEEP_MDN)
     out["ess_gain"] = out["ess"]["ess_per_s"] / ess_plain["ess_per_s"]
     out["proposal"] = {"eps_prior": args.mdn_eps, "inmodel_frac": args.mdn_inmodel}
+    # the paper's refit-RJ Gaussian mixtures as the comparison proposal: fitted on the GPU to
+    # the last sweeps of the plain run, then the same ESS run with them
+    gmm_raw = None
+    if units:
+        gmm_raw, gfit = run_gmm_fit(torch, L, units, N_W, args, stream)
+        S["P"].copy_(P0)
+        S["E"].copy_(E0)
+        S["resid"].copy_(R0)
+        L.gbk_sweep_set_proposal(S["plan"], raw_table=gmm_raw, eps=args.mdn_eps, inmodel_frac=args.mdn_inmodel)
+        sweep_no[0] = k0
+        L.gb_sweep(S["plan"], S["P"], S["E"], S["betas"], S["R"], S["psd"], 1, 0, L.SWEEP_REFRESH, stream=stream)
+        gfit["ess"] = run_ess(torch, L, S, step, stats, stream, args.ess_sweeps, flags=L.SWEEP_MDN)
+        gfit["ess_gain"] = gfit["ess"]["ess_per_s"] / ess_plain["ess_per_s"]
+        out["gmm_refit"] = gfit
     # search: every chain starts empty (residual = data); K sweeps with each proposal
     search = {"sweeps": args.search_sweeps}
     L.gbk_sweep_set_proposal(S["plan"])
@@ -483,15 +531,19 @@ def run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, sn
     L.residual_add_sub(S["ctx"], S["R"], cold.t().contiguous(), torch.full((cold.shape[0],), N_BAND,
                        dtype=torch.int32, device=dev), N_BAND, wv, -1, L.GBK_MIXED, stream)
     data = S["resid"].clone()                               # d (noise + injected sources) per walker
-    for mode in ("prior", "learned"):
+    for mode in ("prior", "learned", "gmm_refit"):
+        if mode == "gmm_refit" and gmm_raw is None:
+            continue
         S["P"].zero_()
         S["E"].zero_()
         S["resid"].copy_(data)
         if mode == "learned":
             L.gbk_sweep_set_proposal(S["plan"], net=net, eps=args.mdn_eps, inmodel_frac=args.mdn_inmodel)
+        elif mode == "gmm_refit":
+            L.gbk_sweep_set_proposal(S["plan"], raw_table=gmm_raw, eps=args.mdn_eps, inmodel_frac=args.mdn_inmodel)
         else:
             L.gbk_sweep_set_proposal(S["plan"])
-        fl = L.SWEEP_MDN if mode == "learned" else 0
+        fl = 0 if mode == "prior" else L.SWEEP_MDN
         stats.zero_()
         curve = []
         t = 0.0
@@ -720,10 +772,13 @@ def run_ours(args):
     if args.ess_sweeps > 0:
         snap = (S["P"].clone(), S["E"].clone(), S["resid"].clone(), sweep_no[0])
         pairs = None
+        units = None
         if not args.no_learned:
             from paper_2405_04690_gb300 import proposal as PR
             pairs = PR.PairBuffer(args.mdn_samples)
-        ess = run_ess(torch, L, S, step, stats, stream, args.ess_sweeps, pairs=pairs)
+            units = []
+        ess = run_ess(torch, L, S, step, stats, stream, args.ess_sweeps, pairs=pairs, units=units,
+                      keep=args.gmm_keep)
         if args.group_frac > 0:   # the paper's in-model move: group stretch, group rebuilt every 30 sweeps
             S["P"].copy_(snap[0])
             S["E"].copy_(snap[1])
@@ -736,7 +791,7 @@ def run_ours(args):
             eg["ess_gain"] = eg["ess_per_s"] / ess["ess_per_s"]
             ess["group_stretch"] = eg
         if pairs is not None:
-            learned = run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, snap, ess)
+            learned = run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, snap, ess, units)
         del snap
 
     # the plain float64 path on the same GPU: (a) the same sweep in float64, one step;
@@ -865,6 +920,8 @@ def main():
     ap.add_argument("--mdn-eps", type=float, default=0.2, help="prior fraction of the learned proposal")
     ap.add_argument("--mdn-inmodel", type=float, default=0.1, help="fraction of in-model moves drawn from it")
     ap.add_argument("--search-sweeps", type=int, default=10)
+    ap.add_argument("--gmm-keep", type=int, default=10, help="sweeps of cold-chain sources for the mixture refit")
+    ap.add_argument("--gmm-iters", type=int, default=50, help="EM iterations of the mixture refit")
     ap.add_argument("--group-frac", type=float, default=0.5, help="fraction of in-model moves that are group stretches "
                                                                    "in the group-stretch ESS run (0: skip it)")
     ap.add_argument("--n-friends", type=int, default=32)

@@ -417,6 +417,38 @@ gbk_status mdn_sample_logpdf(const float* raw, int32_t batch, double eps, const 
                              float* u_out, const float* u_in, float* logq, int32_t precision,
                              void* stream);
 
+/* ------------------------------------------------------------------ Gaussian-mixture refit
+ * gmm_fit -- the paper's GMM-based reversible-jump proposals (Sec. V.E, App. G) fit Gaussian
+ * mixtures to sampler output (scikit-learn on CPUs in the paper, which names batched GPU
+ * fitting as the desirable form). One CTA per group fits a diagonal-covariance mixture of
+ * K = min(n_comp, n) components to the group's n present points by EM (Dempster, Laird &
+ * Rubin 1977): start from the points sorted by the second coordinate (f0; ties by
+ * position), means at ranks floor((k + 1/2) n / K), every variance the group's
+ * per-dimension variance + reg, weights 1/K; then n_iter (E, M) iterations with
+ * N_k = sum_i r_ik + 10 DBL_EPSILON, w_k = N_k / sum_j N_j, mu_k = sum_i r_ik x_i / N_k,
+ * var_k = sum_i r_ik (x_i - mu_k)^2 / N_k + reg. The result is written as the sampler's
+ * 272 mixture outputs (the learned-proposal raw layout: 16 x (weight logit, 8 logit(mu),
+ * 8 logit((ln sigma + 10) / 10)), logits clamped to p in [1e-9, 1 - 1e-9]): components
+ * with w_k >= min_weight share equal probability (the paper weights each fitted group
+ * equally), the others get weight logit -30, missing components (K < 16) are broad
+ * (mu 0.5, sigma 1), and an empty group is 16 broad components of equal weight. Feed it to
+ * gbk_sweep_set_proposal as raw_table for RJ births (and in-model independence moves).
+ *   x          [n_groups][n_points][8] float32 (device): points in the unit coordinates of the
+ *              learned proposal; a row with a NaN is absent; the first gmm_max_points()
+ *              present rows of a group are used
+ *   n_comp     1..16;  n_iter >= 0;  reg > 0 (1e-6 typical);  min_weight in [0, 1]
+ *   precision  GBK_MIXED: float32 E-step and per-lane sums (centred on the current means),
+ *              float64 combination and M-step; GBK_FP64: float64 throughout
+ *   raw_out    [n_copies][n_groups][272] float32 (device): the same rows n_copies times
+ *              (n_copies = n_walkers gives a sweep table [W][n_bands][272])
+ *   fit_out    optional [n_groups][16][17] float64: w, mu[8], var[8] (zero beyond K)
+ *   loglike    optional [n_groups] float64: sum_i ln sum_k w_k N(x_i) of the result
+ * One launch, ~98 KB of shared memory per CTA; no allocation. */
+int32_t gmm_max_points(void);
+gbk_status gmm_fit(const float* x, int32_t n_groups, int32_t n_points, int32_t n_comp, int32_t n_iter, double reg,
+                   double min_weight, int32_t precision, int32_t n_copies, float* raw_out, double* fit_out,
+                   double* loglike, void* stream);
+
 /* Attach the learned proposal to a sweep plan (used by gb_sweep with GBK_SWEEP_MDN):
  *   net        network evaluated on each half sweep's opened windows (band_bins 256;
  *              max_batch >= n_walkers * ceil(n_bands / 2)), its parameters as last set, or

@@ -104,6 +104,9 @@ SIGNATURES = {
                                 ctypes.c_float, _vp]),
     "mdn_train_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp]),
     "mdn_sample_logpdf": (ctypes.c_int, [_vp, _i32, ctypes.c_double, _vp, _vp, _vp, _vp, _i32, _vp]),
+    "gmm_max_points": (_i32, []),
+    "gmm_fit": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, ctypes.c_double, ctypes.c_double, _i32, _i32, _vp, _vp,
+                               _vp, _vp]),
     "mdn_train_epoch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, ctypes.c_float, _vp,
                                        _vp]),
     "gbk_sweep_set_proposal": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double]),
@@ -406,6 +409,21 @@ def mdn_sample_logpdf(raw, eps, precision, words=None, u_out=None, u_in=None, lo
                                    _dev(u_in, torch.float32, "u_in") if u_in is not None else None,
                                    _dev(logq, torch.float32, "logq") if logq is not None else None,
                                    int(precision), _stream(stream)), "mdn_sample_logpdf")
+
+
+def gmm_max_points():
+    return int(lib().gmm_max_points())
+
+
+def gmm_fit(x, raw_out, n_comp=16, n_iter=50, reg=1e-6, min_weight=0.01, precision=GBK_MIXED, fit_out=None,
+            loglike=None, stream=None):
+    """Batched EM fit of x [G][P][8] (float32, NaN rows absent); raw_out [C][G][272] float32."""
+    if x.dim() != 3 or x.shape[2] != 8 or raw_out.dim() != 3 or raw_out.shape[1:] != (x.shape[0], 272):
+        raise ValueError("gmm_fit: x must be [G][P][8] and raw_out [C][G][272]")
+    _check(lib().gmm_fit(_dev(x, torch.float32, "x"), int(x.shape[0]), int(x.shape[1]), int(n_comp), int(n_iter),
+                         float(reg), float(min_weight), int(precision), int(raw_out.shape[0]),
+                         _dev(raw_out, torch.float32, "raw_out"), _dev(fit_out, torch.float64, "fit_out"),
+                         _dev(loglike, torch.float64, "loglike"), _stream(stream)), "gmm_fit")
 
 
 def gbk_sweep_set_proposal(plan, net=None, raw_table=None, eps=0.1, inmodel_frac=0.0):

@@ -12,7 +12,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbk.so")
 
-SOURCES = ["gbk_ctx.cu", "gbk_gb.cu", "gbk_psd.cu", "gbk_sweep.cu", "gbk_static.cu", "gbk_mdn.cu", "gbk_psd_fg.cu"]
+SOURCES = ["gbk_ctx.cu", "gbk_gb.cu", "gbk_psd.cu", "gbk_sweep.cu", "gbk_static.cu", "gbk_mdn.cu", "gbk_psd_fg.cu",
+           "gbk_gmm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
