@@ -130,6 +130,7 @@ def cpu_baseline(n_bands=12, cores=None):
     done = sum(c for _, c in res)
     busy = max(t for t, _ in res)
     return {"value": done / busy, "unit": "proposals/s", "cores": cores, "kind": "oracle",
+            "value_per_core": float(np.mean([c / t for t, c in res])),
             "sample": "%d proposals: %d processes each run one FP64 oracle sweep of 2 temps x 1 walker x %d sub-bands "
                       "(5 GBs/band, 8 slots) near 2 mHz; %.1f s wall incl. pool start" % (done, cores, n_bands, wall)}
 

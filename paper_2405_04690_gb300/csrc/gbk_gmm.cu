@@ -18,8 +18,10 @@ constexpr double kLog2Pi = 1.8378770664093454836;
 constexpr double kWOff = -30.0;     // weight logit of a component left out of the proposal
 constexpr double kClamp = 1e-9;
 
+template <typename T>
 struct GmmSmem {
   float pts[kGmmCap][kMixDim];
+  T em[kMixComp][kMixDim], eiv[kMixComp][kMixDim], ec[kMixComp];   // E-step constants
   unsigned long long keys[kGmmCap];
   double acc[kGmmWarps][kMixComp][kAcc];
   double llw[kGmmWarps];
@@ -48,8 +50,8 @@ __device__ __forceinline__ double logit_c(double p) {
 
 // Per-dimension sum over the n points of f(x_d) (double, fixed order: thread-strided, then
 // a shuffle tree per warp, then the warps in order); result in S.mean.
-template <typename F>
-__device__ void dim_sums(GmmSmem& S, int n, F f) {
+template <typename T, typename F>
+__device__ void dim_sums(GmmSmem<T>& S, int n, F f) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   double s[kMixDim];
 #pragma unroll
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(kGmmThreads) k_gmm_fit(const float* __restrict
                                                          int n_copies, float* __restrict__ raw_out,
                                                          double* __restrict__ fit_out, double* __restrict__ loglike) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  GmmSmem& S = *reinterpret_cast<GmmSmem*>(smem_raw);
+  GmmSmem<T>& S = *reinterpret_cast<GmmSmem<T>*>(smem_raw);
   const int g = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const float* xg = x + (int64_t)g * n_points * kMixDim;
@@ -156,16 +158,28 @@ __global__ void __launch_bounds__(kGmmThreads) k_gmm_fit(const float* __restrict
   // ---- EM: n_iter (E, M) passes, then one E pass for the log-likelihood of the result
   const int h = lane >> 4, k = lane & 15;
   for (int it = 0; it <= n_iter && n > 0; ++it) {
+    // E-step constants, once per CTA, one thread per (component, dimension) in warps 0-3:
+    // (T) mu, (T) 1/var and ln w - 1/2 sum_d (ln var + ln 2 pi) (sum over the 8 lanes of k)
+    if (tid < kMixComp * kMixDim) {
+      const int kk = tid / kMixDim, d = tid % kMixDim;
+      double lv = 0.0;
+      if (kk < K) {
+        S.em[kk][d] = (T)S.mu[kk][d];
+        S.eiv[kk][d] = (T)(1.0 / S.var[kk][d]);
+        lv = log(S.var[kk][d]) + kLog2Pi;
+      }
+      for (int o = 4; o; o >>= 1) lv += __shfl_xor_sync(0xffffffffu, lv, o, kMixDim);
+      if (kk < K && d == 0) S.ec[kk] = (T)(log(S.w[kk]) - 0.5 * lv);
+    }
+    __syncthreads();
     T m_k[kMixDim], iv_k[kMixDim], c_k = (T)0;
     if (k < K) {
-      double c = log(S.w[k]);
 #pragma unroll
       for (int d = 0; d < kMixDim; ++d) {
-        m_k[d] = (T)S.mu[k][d];
-        iv_k[d] = (T)(1.0 / S.var[k][d]);
-        c -= 0.5 * (log(S.var[k][d]) + kLog2Pi);
+        m_k[d] = S.em[k][d];
+        iv_k[d] = S.eiv[k][d];
       }
-      c_k = (T)c;
+      c_k = S.ec[k];
     } else {
 #pragma unroll
       for (int d = 0; d < kMixDim; ++d) m_k[d] = iv_k[d] = (T)0;
@@ -173,7 +187,7 @@ __global__ void __launch_bounds__(kGmmThreads) k_gmm_fit(const float* __restrict
     T a[kAcc];
 #pragma unroll
     for (int f = 0; f < kAcc; ++f) a[f] = (T)0;
-    double ll = 0.0;
+    T ll = (T)0;   // per-point log-likelihoods (lanes 0 and 16); float64 only across lanes and warps
     for (int base = 2 * wid; base < n; base += 2 * kGmmWarps) {
       const int p = base + h;
       const bool pv = p < n;
@@ -204,7 +218,7 @@ __global__ void __launch_bounds__(kGmmThreads) k_gmm_fit(const float* __restrict
             a[1 + kMixDim + d] += r * z * z;
           }
         }
-        if (k == 0) ll += (double)mx + (double)g_log(sum);
+        if (k == 0) ll += mx + g_log(sum);
       }
     }
     // halves -> lanes 0..15 (double), warps -> shared memory
@@ -214,8 +228,8 @@ __global__ void __launch_bounds__(kGmmThreads) k_gmm_fit(const float* __restrict
       const double u = __shfl_down_sync(0xffffffffu, v, 16);
       if (lane < 16 && k < K) S.acc[wid][k][f] = v + u;
     }
-    ll += __shfl_down_sync(0xffffffffu, ll, 16);
-    if (lane == 0) S.llw[wid] = ll;
+    const double lld = (double)ll + (double)__shfl_down_sync(0xffffffffu, ll, 16);
+    if (lane == 0) S.llw[wid] = lld;
     __syncthreads();
     if (it == n_iter) break;
     // M-step (fixed warp order): N_k = S0 + 10 eps, mu += S1 / N, var = S2 / N - (S1 / N)^2 + reg
@@ -294,7 +308,7 @@ extern "C" gbk_status gmm_fit(const float* x, int32_t n_groups, int32_t n_points
   if (!(reg > 0.0) || !(min_weight >= 0.0 && min_weight <= 1.0))
     return set_error(GBK_EINVAL, "gmm_fit: reg must be > 0 and min_weight in [0, 1]");
   if (precision != GBK_MIXED && precision != GBK_FP64) return set_error(GBK_EINVAL, "gmm_fit: bad precision");
-  const size_t smem = sizeof(GmmSmem);
+  const size_t smem = precision == GBK_MIXED ? sizeof(GmmSmem<float>) : sizeof(GmmSmem<double>);
   cudaStream_t st = (cudaStream_t)stream;
   if (precision == GBK_MIXED) {
     if (cudaFuncSetAttribute(k_gmm_fit<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {

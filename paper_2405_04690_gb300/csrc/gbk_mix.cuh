@@ -25,7 +25,7 @@ constexpr double kMixSMin = -10.0, kMixSMax = 0.0;
 constexpr double kLogSqrt2Pi = 0.91893853320467274178;
 
 template <typename T>
-struct MixRow {
+struct __align__(16) MixRow {   // 16-byte aligned: rows are read with vector loads
   T lw[kMixComp];              // ln pi_k - sum_d (ln s_kd + ln Z_kd) - 8 ln sqrt(2 pi)
   T cw[kMixComp];              // cumulative weights pi_0 + ... + pi_k
   T mu[kMixComp][kMixDim];
@@ -78,23 +78,47 @@ __device__ void mix_build(const float* __restrict__ raw, MixRow<T>& m) {
   }
 }
 
-// ln q_eps(u).
+// 8 (16) contiguous values of a row in vector loads (rows are 16-byte aligned), so that the
+// loads of a component are in flight together.
+__device__ __forceinline__ void ld8(const float* p, float* o) {
+  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+__device__ __forceinline__ void ld8(const double* p, double* o) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double2 a = *reinterpret_cast<const double2*>(p + 2 * i);
+    o[2 * i] = a.x;
+    o[2 * i + 1] = a.y;
+  }
+}
+
+// ln q_eps(u): log-sum-exp over the components in one pass (running maximum).
 template <typename T>
 __device__ T mix_logq(const MixRow<T>& m, const T* u, T eps) {
   if (eps >= (T)1) return (T)0;
-  T c[kMixComp];
-  T mx = -(T)INFINITY;
+  T uu[kMixDim];
+#pragma unroll
+  for (int d = 0; d < kMixDim; ++d) uu[d] = u[d];
+  T mx = -(T)INFINITY, se = (T)0;
+#pragma unroll 2
   for (int k = 0; k < kMixComp; ++k) {
+    T mu[kMixDim], is[kMixDim];
+    ld8(m.mu[k], mu);
+    ld8(m.is[k], is);
     T acc = m.lw[k];
+#pragma unroll
     for (int d = 0; d < kMixDim; ++d) {
-      const T z = (u[d] - m.mu[k][d]) * m.is[k][d];
+      const T z = (uu[d] - mu[d]) * is[d];
       acc -= (T)0.5 * z * z;
     }
-    c[k] = acc;
-    mx = fmax(mx, acc);
+    if (acc > mx) {
+      se = se * m_exp(mx - acc) + (T)1;
+      mx = acc;
+    } else {
+      se += m_exp(acc - mx);
+    }
   }
-  T se = 0;
-  for (int k = 0; k < kMixComp; ++k) se += m_exp(c[k] - mx);
   const T lq = mx + m_log(se);
   if (eps <= (T)0) return lq;
   // ln[eps + (1 - eps) e^lq] = logaddexp(ln eps, ln(1 - eps) + lq)
@@ -111,12 +135,22 @@ __device__ __forceinline__ double mix_u32(uint32_t w) { return ((double)w + 0.5)
 template <typename T>
 __device__ void mix_draw(const MixRow<T>& m, uint32_t w_comp, const uint32_t* w_dims, T* u) {
   const T v = (T)mix_u32(w_comp);
+  T cw[kMixComp];
+  ld8(m.cw, cw);
+  ld8(m.cw + 8, cw + 8);
   int k = kMixComp - 1;
-  for (int j = 0; j < kMixComp; ++j)
-    if (v < m.cw[j]) { k = j; break; }
+#pragma unroll
+  for (int j = kMixComp - 1; j >= 0; --j)
+    if (v < cw[j]) k = j;
+  T pl[kMixDim], pw[kMixDim], mu[kMixDim], sg[kMixDim];
+  ld8(m.plo[k], pl);
+  ld8(m.pw[k], pw);
+  ld8(m.mu[k], mu);
+  ld8(m.s[k], sg);
+#pragma unroll
   for (int d = 0; d < kMixDim; ++d) {
-    const T p = m.plo[k][d] + m.pw[k][d] * (T)mix_u32(w_dims[d]);
-    T x = m.mu[k][d] + m.s[k][d] * m_icdf(p);
+    const T p = pl[d] + pw[d] * (T)mix_u32(w_dims[d]);
+    T x = mu[d] + sg[d] * m_icdf(p);
     x = x < (T)0 ? (T)0 : x;        // also maps a NaN-free -inf to 0
     x = x > (T)1 ? (T)1 : x;
     u[d] = x;
