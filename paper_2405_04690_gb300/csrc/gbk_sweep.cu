@@ -98,6 +98,10 @@ __device__ __forceinline__ float iqv(const gbk_ctx& c, int64_t k, float) { retur
 __device__ __forceinline__ double iqv(const gbk_ctx& c, int64_t k, double) { return __ldg(&c.iq_d[k]); }
 __device__ __forceinline__ float rhov(const gbk_ctx& c, int64_t k, float) { return __ldg(&c.rho_f[k]); }
 __device__ __forceinline__ double rhov(const gbk_ctx& c, int64_t k, double) { return __ldg(&c.rho_d[k]); }
+__device__ __forceinline__ const float* tab_iq(const gbk_ctx& c, float) { return c.iq_f; }
+__device__ __forceinline__ const double* tab_iq(const gbk_ctx& c, double) { return c.iq_d; }
+__device__ __forceinline__ const float* tab_rho(const gbk_ctx& c, float) { return c.rho_f; }
+__device__ __forceinline__ const double* tab_rho(const gbk_ctx& c, double) { return c.rho_d; }
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 __device__ __forceinline__ float i2t(long long v, float) { return __ll2float_rn(v); }
@@ -498,6 +502,8 @@ __device__ __forceinline__ int cached_off(const double* th, int64_t gw, const gb
 
 // Delta lnL of swapping template r (br, window offset orr) for a (ba, offset oa) against
 // the window residual rw ([2][3N]); either may be absent. Window bin i is grid bin gw + i.
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 template <typename T, int N>
 __device__ __noinline__ double window_dll(const SweepArgs& a, const typename CT<T>::C* rw, const typename CT<T>::C* ba, int oa,
                              const typename CT<T>::C* br, int orr, int64_t gw, const PsdWt<T>& pw, int lane) {
@@ -506,6 +512,32 @@ __device__ __noinline__ double window_dll(const SweepArgs& a, const typename CT<
   typename SAcc<T>::S sdd, srd;
   sdd.init();
   srd.init();
+  {   // the lines this evaluation reads (window, old template, PSD tables) towards L1: their
+      // loads then meet L1 instead of L2 in the latency-bound loops below
+    const int o0 = ba ? oa : orr;
+    constexpr int kPer = 128 / (int)sizeof(C);          // complex bins per 128-byte line
+    const int nl = (N + kPer - 1) / kPer + 1;           // lines of N bins (unaligned start)
+    for (int i = lane; i < 2 * nl; i += 32) {
+      const int ch = i / nl, li = i % nl;
+      const int idx = (o0 & ~(kPer - 1)) + li * kPer;      // stays inside this warp's window
+      if (idx < W3) prefetch_l1(rw + ch * W3 + idx);
+    }
+    constexpr int nt = N / kPer;                          // lines of one channel of a template
+    if (br)
+      for (int i = lane; i < 2 * nt; i += 32) prefetch_l1(br + i * kPer);
+    {   // PSD-table lines of the evaluated bins
+      constexpr int kT = 128 / (int)sizeof(T);           // table entries per line
+      const int64_t k0 = (gw + o0) & ~(int64_t)(kT - 1);
+      constexpr int nq = N / kT + 1;
+      const int64_t kend = a.c.grid.n_bins;
+      const T* iq = tab_iq(a.c, T());
+      const T* rh = tab_rho(a.c, T());
+      for (int i = lane; i < 2 * nq; i += 32) {
+        const int64_t k = k0 + (int64_t)kT * (i % nq);
+        if (k < kend) prefetch_l1(i < nq ? iq + k : rh + k);
+      }
+    }
+  }
   auto bin = [&](int i, C da, C de) {
     const int64_t k = gw + i;
     const T wt = iqv(a.c, k, T()) * recip((T)1 + pw.aw * rhov(a.c, k, T()));
