@@ -1,0 +1,107 @@
+"""Pins of the oracle's per-band search sampler (oracle/search.py): a known tempered target
+stays stationary under the stretch moves and swaps, the prior (beta = 0) is uniform on the
+unit box, the likelihood is Eq. addsource (+1/2 SNR^2 at an injected source on noise-free
+data), and the best-point bookkeeping on a worked example."""
+import math
+
+import numpy as np
+
+from oracle import constants as OC
+from oracle import likelihood as LK
+from oracle import psd as OP
+from oracle import residual as RS
+from oracle import search as SR
+from oracle import waveform as WF
+
+
+def _cfg(n_bands=1, n_temps=2, n_walkers=16, betas=(1.0, 0.25), key=(7, 9)):
+    band_k0 = int(math.floor(2.0e-3 * OC.TOBS))
+    k0 = band_k0 - 2 * 256
+    n_bins = (n_bands + 4) * 256
+    f = (k0 + np.arange(n_bins)) * OC.DF
+    return SR.SearchConfig(tobs=OC.TOBS, k0=k0, n_bins=n_bins, band_k0=band_k0, n_bands=n_bands, n_temps=n_temps,
+                           n_walkers=n_walkers, betas=np.tile(np.asarray(betas[:n_temps]), (n_bands, 1)),
+                           psd=OP.psd_ae(f, OC.SQRT_S_OMS, OC.SQRT_S_ACC), key=key)
+
+
+def test_tempered_gaussian_target_stays_stationary():
+    # target at temperature t: N(0.5, s^2 / beta_t) per coordinate (far from the box edges);
+    # ensembles started from exact draws keep that law after 15 sweeps (60 independent
+    # ensembles): a wrong Jacobian power, z law or swap rule moves the moments
+    s = 0.04
+    mu = 0.5
+
+    def fn(b, x):
+        return -0.5 * float(np.sum((x - mu) ** 2)) / s ** 2
+
+    g = np.random.default_rng(1)
+    finals = {0: [], 1: []}
+    for e in range(60):
+        cfg = _cfg(key=(11, e))
+        u = np.empty((1, 2, 16, 8))
+        for t in range(2):
+            u[0, t] = mu + s / math.sqrt(cfg.betas[0, t]) * g.standard_normal((16, 8))
+        ell = SR.evaluate(cfg, None, u, fn)
+        for k in range(15):
+            SR.sweep(cfg, None, u, ell, k, fn)
+        for t in range(2):
+            finals[t].append(u[0, t].copy())
+    for t, beta in ((0, 1.0), (1, 0.25)):
+        x = np.concatenate(finals[t]).ravel()
+        sd = s / math.sqrt(beta)
+        assert abs(x.mean() - mu) < 4 * sd / math.sqrt(x.size / 16), (t, x.mean())
+        assert abs(x.var() / sd ** 2 - 1) < 0.08, (t, x.var() / sd ** 2)
+
+
+def test_prior_only_search_is_uniform_on_the_box():
+    # beta = 0: every walker's law stays uniform on [0, 1]^8 (final states of 40 independent
+    # ensembles started from the prior, 40 sweeps each)
+    xs = []
+    for e in range(40):
+        cfg = _cfg(n_temps=1, n_walkers=16, betas=(0.0,), key=(5, e))
+        u = SR.init(cfg, 3)
+        ell = np.zeros((1, 1, 16))
+        for k in range(40):
+            SR.sweep(cfg, None, u, ell, k, lambda b, x: 0.0)
+        xs.append(u[0, 0].copy())
+    x = np.concatenate(xs)
+    assert ((x >= 0) & (x <= 1)).all()
+    assert np.abs(x.mean(axis=0) - 0.5).max() < 0.05
+    assert np.abs(x.var(axis=0) * 12 - 1).max() < 0.15
+
+
+def test_search_likelihood_is_eq_addsource():
+    # noise-free residual = one source of band 0: at its own coordinates l = +1/2 <h|h>;
+    # elsewhere l = <h|h'> - 1/2 <h'|h'>
+    cfg = _cfg(n_temps=1)
+    u0 = np.array([0.8, 0.37, 0.5, 0.2, 0.3, 0.6, 0.4, 0.7])
+    th = SR.from_unit(cfg, 0, u0)
+    off, n = cfg.window(0)
+    h = LK.place(WF.fastslow_band(th, 256, cfg.tobs), cfg.k0 + off, n)
+    R = np.zeros((2, cfg.n_bins), complex)
+    R[:, off:off + n] = h
+    rw = SR.windows(cfg, RS.to_fixed(R, 98), 98)
+    psd = cfg.psd[off:off + n]
+    hh = LK.inner(h, h, psd, cfg.df)
+    assert hh > 100.0
+    assert abs(SR.loglike(cfg, rw[0], 0, u0) - 0.5 * hh) < 1e-8 * hh
+    u1 = u0.copy()
+    u1[1] += 0.01
+    h1 = LK.place(WF.fastslow_band(SR.from_unit(cfg, 0, u1), 256, cfg.tobs), cfg.k0 + off, n)
+    want = LK.inner(h, h1, psd, cfg.df) - 0.5 * LK.inner(h1, h1, psd, cfg.df)
+    assert abs(SR.loglike(cfg, rw[0], 0, u1) - want) < 1e-8 * hh
+    # the own-bin prior box: u1 = 0 and 1 are the band's first and last own bins
+    lo, hi = cfg.core(0)
+    assert abs(SR.from_unit(cfg, 0, np.zeros(8))[1] * cfg.tobs - cfg.band_k0) < 1e-6
+    assert abs((hi - lo) * cfg.tobs - 256) < 1e-6
+
+
+def test_best_point_bookkeeping():
+    u = np.arange(2 * 1 * 3 * 8, dtype=float).reshape(2, 1, 3, 8)
+    ell = np.array([[[1.0, 5.0, 5.0]], [[-1.0, -2.0, -3.0]]])
+    best = np.array([-np.inf, 0.0])
+    bu = np.zeros((2, 8))
+    stall = np.array([4, 4])
+    SR.best_update(u, ell, best, bu, stall)
+    assert best.tolist() == [5.0, 0.0] and stall.tolist() == [0, 5]
+    assert np.array_equal(bu[0], u[0, 0, 1]) and np.array_equal(bu[1], np.zeros(8))
