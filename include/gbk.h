@@ -486,6 +486,56 @@ gbk_status gbk_sweep_adapt_temps(gbk_sweep* plan, double* betas, int32_t iterati
  * Three small kernels plus the cold chain's template sums (n_walkers x n_bands warps). */
 gbk_status gbk_sweep_transfer(gbk_sweep* plan, double* params, uint8_t* exists, int32_t* counts, void* stream);
 
+/* ------------------------------------------------------------------ per-band search sampler
+ * The search-RJ proposal's sampler (Sec. V.E, App. G): for every sub-band b an independent,
+ * parallel-tempered ensemble (n_temps x n_walkers single sources) with stretch moves,
+ * looking for the highest-likelihood source still in one walker's residual R. A walker is a
+ * point u of the unit box of band b's prior with f0 narrowed to the band's own bins:
+ *   u0 = (ln A - ln_a_min) / (ln_a_max - ln_a_min), u1 = (f0 T - band_k0 - b N) / N,
+ *   u2 = (Mc - mc_min) / (mc_max - mc_min), u3 = phi0 / 2 pi, u4 = psi / pi,
+ *   u5 = (cos iota + 1) / 2, u6 = (sin beta + 1) / 2, u7 = lambda / 2 pi,
+ * and its likelihood is l(u) = <R|h> - 1/2 <h|h> on the band's window b-1..b+1 (the birth
+ * Delta lnL, Eq. addsource). A sweep: stretch moves of walker half 0, then half 1, at every
+ * temperature (partner from the other half, z ~ 1/sqrt(z) on [1/a, a], Y = X_j + z (X_k -
+ * X_j); a Y outside [0, 1]^8 is rejected; acceptance ln u < beta (l_Y - l_X) + 7 ln z), then
+ * tempering swaps of each walker index from the top temperature down (Eq. temp-orig), then
+ * (optionally) the best point of every band: the largest cold l, kept if it improves
+ * (stall = 0) else stall += 1. Random numbers: Philox4x32-10 with the 64-bit key; start of
+ * chain c = (b T + t) W + k from counters (c, m, 9, seed), m = 0, 1; stretch of chain c in
+ * half h of sweep s from (c, h, 7, s) (words: partner, z, ln u); swap of (b, w) between t and
+ * t - 1 from (b W + w, t, 8, s). SNR of a band's best point: sqrt(2 l_best). */
+typedef struct gbk_search_desc {
+  int32_t n_bands, band_bins, n_temps, n_walkers;  /* n_walkers even, >= 4 */
+  int64_t band_k0;        /* absolute first bin of band 0; windows [band_k0 + (b-1) N, +3N) in the grid */
+  double ln_a_min, ln_a_max, mc_min, mc_max;        /* prior bounds (chirp mass in M_sun) */
+  double stretch_a;       /* stretch scale a > 1 (2 in the paper's sampler) */
+  int32_t precision;      /* GBK_MIXED or GBK_FP64 (waveforms and inner products) */
+} gbk_search_desc;
+
+typedef struct gbk_search gbk_search;
+
+/* Plan: validates the description against the context grid; allocates the residual windows
+ * ([n_bands][2][3N] complex of the precision). */
+gbk_status gbk_search_create(gbk_ctx* ctx, const gbk_search_desc* desc, gbk_search** out);
+gbk_status gbk_search_destroy(gbk_search* plan);
+/* u [n_bands][n_temps][n_walkers][8] float64 (device) drawn from the prior (uniform box). */
+gbk_status gb_search_init(gbk_search* plan, double* u, uint64_t key, uint32_t seed, void* stream);
+/* Copies walker `walker`'s fixed-point residual (gbk_residual, device) onto every band's window;
+ * the windows stay until the next call. */
+gbk_status gb_search_windows(gbk_search* plan, const gbk_residual* residual, int32_t walker, void* stream);
+/* ell [n_bands][n_temps][n_walkers] float64 (device) = l(u) of every walker, with the PSD of
+ * psd_walker (the residual's walker; index 0 of a one-row PSD). */
+gbk_status gb_search_eval(gbk_search* plan, const double* u, double* ell, const gbk_psd* psd, int32_t psd_walker,
+                          void* stream);
+/* One sweep; u and ell (consistent, e.g. from gb_search_eval) are updated in place.
+ *   betas     [n_bands][n_temps] float64 (device)
+ *   best_ell  [n_bands] float64, best_u [n_bands][8], stall [n_bands] int32 (device, in/out;
+ *             start best_ell at -inf); all three or none
+ *   stats     optional int64[2][2] (device): stretch proposals, accepted; swaps, accepted (added) */
+gbk_status gb_search_sweep(gbk_search* plan, double* u, double* ell, const double* betas, const gbk_psd* psd,
+                           int32_t psd_walker, uint64_t key, uint32_t sweep_index, double* best_ell, double* best_u,
+                           int32_t* stall, int64_t* stats, void* stream);
+
 /* Group stretch in-model moves (the paper's in-model proposal, Eq. stretch with a stationary
  * group): builds every band's stationary group from the current cold chain -- the sources of
  * bands b-1, b, b+1 of all walkers, sorted by f0 -- and makes a fraction `frac` of the

@@ -6,6 +6,7 @@ kernels. A missing library or a non-CUDA tensor raises immediately: there is no 
 fallback.
 """
 import ctypes
+import math
 import os
 
 import torch
@@ -49,6 +50,13 @@ class GbkSweepDesc(ctypes.Structure):
 class GbkPsdDesc(ctypes.Structure):
     _fields_ = [("n_temps", _i32), ("n_walkers", _i32), ("lo", ctypes.c_double * 9), ("hi", ctypes.c_double * 9),
                 ("stretch_a", ctypes.c_double)]
+
+
+class GbkSearchDesc(ctypes.Structure):
+    _fields_ = [("n_bands", _i32), ("band_bins", _i32), ("n_temps", _i32), ("n_walkers", _i32),
+                ("band_k0", ctypes.c_int64), ("ln_a_min", ctypes.c_double), ("ln_a_max", ctypes.c_double),
+                ("mc_min", ctypes.c_double), ("mc_max", ctypes.c_double), ("stretch_a", ctypes.c_double),
+                ("precision", _i32)]
 
 
 class GbkTraceRec(ctypes.Structure):
@@ -115,6 +123,13 @@ SIGNATURES = {
     "gbk_psd_plan_create": (ctypes.c_int, [_vp, ctypes.POINTER(GbkPsdDesc), ctypes.POINTER(_vp)]),
     "gbk_psd_plan_destroy": (ctypes.c_int, [_vp]),
     "gb_psd_sweep": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp]),
+    "gbk_search_create": (ctypes.c_int, [_vp, ctypes.POINTER(GbkSearchDesc), ctypes.POINTER(_vp)]),
+    "gbk_search_destroy": (ctypes.c_int, [_vp]),
+    "gb_search_init": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64, ctypes.c_uint32, _vp]),
+    "gb_search_windows": (ctypes.c_int, [_vp, ctypes.POINTER(GbkResidual), _i32, _vp]),
+    "gb_search_eval": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(GbkPsd), _i32, _vp]),
+    "gb_search_sweep": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(GbkPsd), _i32, ctypes.c_uint64,
+                                       ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp]),
     "gbk_sweep_adapt_temps": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_double, ctypes.c_double, _vp]),
     "gbk_sweep_transfer": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "gbk_sweep_update_group": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _i32, _vp]),
@@ -514,3 +529,57 @@ def gb_psd_sweep(plan, params, logl, residual, betas, key, sweep_index, stats=No
                               ctypes.c_uint64(int(key)), ctypes.c_uint32(int(sweep_index)),
                               _dev(stats, torch.int64, "stats") if stats is not None else None, _stream(stream)),
            "gb_psd_sweep")
+
+
+class SearchPlan:
+    """Owns a gbk_search plan (per-band search sampler of the search-RJ proposal)."""
+
+    def __init__(self, ctx, n_bands, band_bins, band_k0, n_temps, n_walkers, precision=GBK_MIXED,
+                 ln_a_min=math.log(1e-23), ln_a_max=math.log(10 ** -21.5), mc_min=0.3, mc_max=0.8, stretch_a=2.0):
+        d = GbkSearchDesc()
+        d.n_bands, d.band_bins, d.n_temps, d.n_walkers = int(n_bands), int(band_bins), int(n_temps), int(n_walkers)
+        d.band_k0 = int(band_k0)
+        d.ln_a_min, d.ln_a_max, d.mc_min, d.mc_max = float(ln_a_min), float(ln_a_max), float(mc_min), float(mc_max)
+        d.stretch_a = float(stretch_a)
+        d.precision = int(precision)
+        self.desc = d
+        h = _vp()
+        _check(lib().gbk_search_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)), "gbk_search_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().gbk_search_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gb_search_init(plan, u, key, seed, stream=None):
+    _check(lib().gb_search_init(plan.handle, _dev(u, torch.float64, "u"), ctypes.c_uint64(int(key)),
+                                ctypes.c_uint32(int(seed)), _stream(stream)), "gb_search_init")
+
+
+def gb_search_windows(plan, residual, walker, stream=None):
+    _check(lib().gb_search_windows(plan.handle, ctypes.byref(residual), int(walker), _stream(stream)),
+           "gb_search_windows")
+
+
+def gb_search_eval(plan, u, ell, psd, psd_walker=0, stream=None):
+    _check(lib().gb_search_eval(plan.handle, _dev(u, torch.float64, "u"), _dev(ell, torch.float64, "ell"),
+                                ctypes.byref(psd), int(psd_walker), _stream(stream)), "gb_search_eval")
+
+
+def gb_search_sweep(plan, u, ell, betas, psd, key, sweep_index, psd_walker=0, best=None, stats=None, stream=None):
+    """best: (best_ell [B] float64, best_u [B][8] float64, stall [B] int32) or None."""
+    be, bu, st = best if best is not None else (None, None, None)
+    _check(lib().gb_search_sweep(plan.handle, _dev(u, torch.float64, "u"), _dev(ell, torch.float64, "ell"),
+                                 _dev(betas, torch.float64, "betas"), ctypes.byref(psd), int(psd_walker),
+                                 ctypes.c_uint64(int(key)), ctypes.c_uint32(int(sweep_index)),
+                                 _dev(be, torch.float64, "best_ell"), _dev(bu, torch.float64, "best_u"),
+                                 _dev(st, torch.int32, "stall"), _dev(stats, torch.int64, "stats"), _stream(stream)),
+           "gb_search_sweep")

@@ -1859,3 +1859,394 @@ extern "C" gbk_status gbk_sweep_transfer(gbk_sweep* plan, double* params, uint8_
   cudaStream_t st = (cudaStream_t)stream;
   return plan->d.precision == GBK_MIXED ? transfer_n<float>(plan, a, counts, st) : transfer_n<double>(plan, a, counts, st);
 }
+
+// ==================================================================== per-band search sampler
+// The search-RJ proposal's sampler (Sec. V.E, App. G): for every sub-band an independent,
+// parallel-tempered ensemble of single sources with stretch moves in the band's own-bin prior
+// box, looking for the highest-likelihood source left in one walker's residual.
+struct gbk_search {
+  gbk_ctx* ctx;
+  gbk_search_desc d;
+  void* rw;            // residual windows [B][2][3N] of the sampler's precision
+  bool have_windows;
+};
+
+namespace gbk {
+
+constexpr int kSearchWarps = 4;
+
+struct SearchArgs {
+  SweepArgs sa;        // context, PSD and the residual windows (sa.rho) for the shared helpers
+  gbk_search_desc d;
+  double* u;           // [B][T][W][8]
+  double* ell;         // [B][T][W]
+  const double* betas; // [B][T]
+  int psd_walker;
+  long long* stats;    // [2][2]: stretch proposals, accepted; swaps, accepted
+};
+
+template <typename T, int N>
+struct SearchSmem {
+  typename CT<T>::C ba[2 * N], bs[2 * N];
+  Src<T> src;
+  double y[8];
+  double lz;
+  int inb;
+};
+
+// Source parameters of unit coordinates u in band b's own-bin box (f0 over [lo_b, hi_b)),
+// rounded step by step as written (no contraction).
+__device__ __forceinline__ void search_from_unit(const gbk_search_desc& d, double tobs, int b, const double* u,
+                                                 double* th) {
+  const long long lob = d.band_k0 + (long long)b * d.band_bins;
+  const double lo = __ddiv_rn((double)lob, tobs), hi = __ddiv_rn((double)(lob + d.band_bins), tobs);
+  const double f0 = dadd(lo, dmul(dsub(hi, lo), u[1]));
+  const double mc = dadd(d.mc_min, dmul(dsub(d.mc_max, d.mc_min), u[2]));
+  th[0] = exp(dadd(d.ln_a_min, dmul(dsub(d.ln_a_max, d.ln_a_min), u[0])));
+  th[1] = f0;
+  th[2] = fdot_of(f0, mc, double());
+  th[3] = dmul(6.283185307179586, u[3]);
+  th[4] = dmul(3.141592653589793, u[4]);
+  th[5] = dsub(dmul(2.0, u[5]), 1.0);
+  th[6] = dsub(dmul(2.0, u[6]), 1.0);
+  th[7] = dmul(6.283185307179586, u[7]);
+}
+
+template <typename T, int N>
+__device__ __forceinline__ const typename CT<T>::C* search_window(const SearchArgs& a, int b) {
+  return reinterpret_cast<const typename CT<T>::C*>(a.sa.rho) + (int64_t)b * 2 * 3 * N;
+}
+
+// l(u) = <R|h> - 1/2 <h|h> on band b's window (the birth Delta lnL, Eq. addsource); whole warp.
+template <typename T, int N>
+__device__ double search_ell(const SearchArgs& a, SearchSmem<T, N>& S, int b, const double* u, int lane) {
+  if (lane == 0) {
+    double th[8];
+    search_from_unit(a.d, a.sa.c.grid.tobs, b, u, th);
+    S.src = make_src<T>(th, 1, 0, a.sa.c.grid.tobs, N);
+  }
+  __syncwarp();
+  gen_band<T, N>(&S.src, orb_of<T>(a.sa.c, band_index(N)), tw_of<T>(a.sa.c, band_index(N)), a.sa.c.grid.tobs, S.ba,
+                 S.bs, lane);
+  const int64_t gw = a.d.band_k0 + (int64_t)(b - 1) * N - a.sa.c.grid.k0;
+  const int oa = band_off<N>(S.src.q, gw, a.sa.c);
+  const PsdWt<T> pw = walker_psd<T>(a.sa, a.psd_walker);
+  const double l = window_dll<T, N>(a.sa, search_window<T, N>(a, b), S.ba, oa, (const typename CT<T>::C*)nullptr, 0,
+                                    gw, pw, lane);
+  __syncwarp();
+  return l;
+}
+
+// residual windows: R of one walker on every band's three sub-bands
+template <typename T, int N>
+__global__ void __launch_bounds__(kSearchWarps * 32) k_search_windows(const SearchArgs a, const long long* resid,
+                                                                      int64_t n_bins, int walker, int frac_bits) {
+  typedef typename CT<T>::C C;
+  constexpr int W3 = 3 * N;
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x * kSearchWarps + (threadIdx.x >> 5);
+  if (b >= a.d.n_bands) return;
+  const T rs = (T)ldexp(1.0, kStrainExp - frac_bits);
+  const int64_t gw = a.d.band_k0 + (int64_t)(b - 1) * N - a.sa.c.grid.k0;
+  const long long* rw = resid + (int64_t)walker * 2 * n_bins * 2;
+  C* out = reinterpret_cast<C*>(a.sa.rho) + (int64_t)b * 2 * W3;
+  for (int i = lane; i < W3; i += 32)
+    for (int ch = 0; ch < 2; ++ch) {
+      const longlong2 v = *reinterpret_cast<const longlong2*>(rw + 2 * (ch * n_bins + gw + i));
+      out[ch * W3 + i] = mkc(i2t(v.x, T()) * rs, i2t(v.y, T()) * rs);
+    }
+}
+
+// walkers from the prior: u = u32 of 8 Philox words at (chain, m, 9, seed), m = 0, 1
+__global__ void k_search_init(double* u, int n, uint32_t seed, uint32_t k0, uint32_t k1) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  for (int m = 0; m < 2; ++m) {
+    const U4 v = philox4x32_10((uint32_t)c, (uint32_t)m, 9u, seed, k0, k1);
+    u[(int64_t)c * 8 + 4 * m] = u32(v.x);
+    u[(int64_t)c * 8 + 4 * m + 1] = u32(v.y);
+    u[(int64_t)c * 8 + 4 * m + 2] = u32(v.z);
+    u[(int64_t)c * 8 + 4 * m + 3] = u32(v.w);
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kSearchWarps * 32) k_search_eval(const SearchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  SearchSmem<T, N>& S = reinterpret_cast<SearchSmem<T, N>*>(smem_raw)[wid];
+  const int n = a.d.n_bands * a.d.n_temps * a.d.n_walkers;
+  for (int c = blockIdx.x * kSearchWarps + wid; c < n; c += gridDim.x * kSearchWarps) {
+    const int b = c / (a.d.n_temps * a.d.n_walkers);
+    const double l = search_ell<T, N>(a, S, b, a.u + (int64_t)c * 8, lane);
+    if (lane == 0) a.ell[c] = l;
+  }
+}
+
+// Stretch moves of half h (one warp per chain of the half): partner from the other half, z
+// from g(z) ~ 1/sqrt(z) on [1/a, a], Y = X_j + z (X_k - X_j) in the unit box, acceptance
+// ln u < beta (l_Y - l_X) + 7 ln z; a Y outside [0, 1]^8 is rejected without a likelihood.
+template <typename T, int N>
+__global__ void __launch_bounds__(kSearchWarps * 32) k_search_half(const SearchArgs a, int h, uint32_t sweep,
+                                                                   uint32_t k0, uint32_t k1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  SearchSmem<T, N>& S = reinterpret_cast<SearchSmem<T, N>*>(smem_raw)[wid];
+  const int T_ = a.d.n_temps, W = a.d.n_walkers, half = W / 2;
+  const int n = a.d.n_bands * T_ * half;
+  for (int e = blockIdx.x * kSearchWarps + wid; e < n; e += gridDim.x * kSearchWarps) {
+    const int b = e / (T_ * half), r = e % (T_ * half);
+    const int t = r / half, k = h * half + r % half;
+    const int64_t ck = ((int64_t)b * T_ + t) * W + k;
+    const U4 wv = philox4x32_10((uint32_t)ck, (uint32_t)h, 7u, sweep, k0, k1);
+    if (lane == 0) {
+      const int j = (1 - h) * half + (int)ranged(wv.x, (uint32_t)half);
+      const double zz = dadd(dmul(dsub(a.d.stretch_a, 1.0), u32(wv.y)), 1.0);
+      const double z = __ddiv_rn(dmul(zz, zz), a.d.stretch_a);
+      const double* xk = a.u + ck * 8;
+      const double* xj = a.u + (ck - k + j) * 8;
+      int inb = 1;
+      for (int c = 0; c < 8; ++c) {
+        const double y = dadd(xj[c], dmul(z, dsub(xk[c], xj[c])));
+        S.y[c] = y;
+        if (!(y >= 0.0 && y <= 1.0)) inb = 0;
+      }
+      S.inb = inb;
+      S.lz = log(z);
+    }
+    __syncwarp();
+    bool acc = false;
+    if (S.inb) {
+      const double ly = search_ell<T, N>(a, S, b, S.y, lane);
+      const double ul = u53(wv.z, wv.w);
+      const double lu = ul > 0.0 ? log(ul) : -INFINITY;
+      const double la = a.betas[(int64_t)b * T_ + t] * (ly - a.ell[ck]) + 7.0 * S.lz;
+      acc = __shfl_sync(0xffffffffu, (int)(lu < la), 0) != 0;
+      if (acc && lane == 0) a.ell[ck] = ly;
+      if (acc && lane < 8) a.u[ck * 8 + lane] = S.y[lane];
+    }
+    if (lane == 0 && a.stats) {
+      atomicAdd((unsigned long long*)&a.stats[0], 1ull);
+      if (acc) atomicAdd((unsigned long long*)&a.stats[1], 1ull);
+    }
+    __syncwarp();
+  }
+}
+
+// Tempering swaps of walker index w between t and t-1, from the top down (one thread per (b, w)).
+__global__ void k_search_swap(const SearchArgs a, uint32_t sweep, uint32_t k0, uint32_t k1) {
+  const int T_ = a.d.n_temps, W = a.d.n_walkers;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= a.d.n_bands * W) return;
+  const int b = x / W, w = x % W;
+  int n = 0, na = 0;
+  for (int t = T_ - 1; t > 0; --t) {
+    const U4 wv = philox4x32_10((uint32_t)x, (uint32_t)t, 8u, sweep, k0, k1);
+    const double ul = u53(wv.x, wv.y);
+    const double lu = ul > 0.0 ? log(ul) : -INFINITY;
+    const int64_t i1 = ((int64_t)b * T_ + t) * W + w, i0 = i1 - W;
+    const double la = (a.betas[(int64_t)b * T_ + t - 1] - a.betas[(int64_t)b * T_ + t]) * (a.ell[i1] - a.ell[i0]);
+    ++n;
+    if (lu < la) {
+      ++na;
+      const double tl = a.ell[i1];
+      a.ell[i1] = a.ell[i0];
+      a.ell[i0] = tl;
+      for (int c = 0; c < 8; ++c) {
+        const double tu = a.u[i1 * 8 + c];
+        a.u[i1 * 8 + c] = a.u[i0 * 8 + c];
+        a.u[i0 * 8 + c] = tu;
+      }
+    }
+  }
+  if (a.stats && n) {
+    atomicAdd((unsigned long long*)&a.stats[2], (unsigned long long)n);
+    atomicAdd((unsigned long long*)&a.stats[3], (unsigned long long)na);
+  }
+}
+
+// best point of every band: the largest cold-chain l (first walker on ties) if it improves
+__global__ void k_search_best(const SearchArgs a, double* best_ell, double* best_u, int32_t* stall) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.d.n_bands) return;
+  const int W = a.d.n_walkers;
+  const double* l = a.ell + (int64_t)b * a.d.n_temps * W;
+  int k = 0;
+  for (int i = 1; i < W; ++i)
+    if (l[i] > l[k]) k = i;
+  if (l[k] > best_ell[b]) {
+    best_ell[b] = l[k];
+    for (int c = 0; c < 8; ++c) best_u[(int64_t)b * 8 + c] = a.u[((int64_t)b * a.d.n_temps * W + k) * 8 + c];
+    stall[b] = 0;
+  } else {
+    stall[b] += 1;
+  }
+}
+
+template <typename T, int N>
+static gbk_status search_launch(SearchArgs& a, int what, uint32_t sweep, uint32_t k0, uint32_t k1, cudaStream_t st) {
+  const size_t sm = kSearchWarps * sizeof(SearchSmem<T, N>);
+  const int per_sm = 6;
+  if (what == 0) {
+    if (cudaFuncSetAttribute(k_search_eval<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(GBK_ECUDA, "gb_search_eval: shared memory size");
+    }
+    const int n = a.d.n_bands * a.d.n_temps * a.d.n_walkers;
+    const int cap = sms_of_device() * per_sm;
+    const int grid = (n + kSearchWarps - 1) / kSearchWarps < cap ? (n + kSearchWarps - 1) / kSearchWarps : cap;
+    k_search_eval<T, N><<<grid, kSearchWarps * 32, sm, st>>>(a);
+    return check_launch("gb_search_eval");
+  }
+  if (cudaFuncSetAttribute(k_search_half<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(GBK_ECUDA, "gb_search_sweep: shared memory size");
+  }
+  const int n = a.d.n_bands * a.d.n_temps * (a.d.n_walkers / 2);
+  const int cap = sms_of_device() * per_sm;
+  const int grid = (n + kSearchWarps - 1) / kSearchWarps < cap ? (n + kSearchWarps - 1) / kSearchWarps : cap;
+  for (int h = 0; h < 2; ++h) {
+    k_search_half<T, N><<<grid, kSearchWarps * 32, sm, st>>>(a, h, sweep, k0, k1);
+    gbk_status s;
+    if ((s = check_launch("gb_search_sweep(stretch)"))) return s;
+  }
+  return GBK_OK;
+}
+
+template <typename T>
+static gbk_status search_dispatch(SearchArgs& a, int what, uint32_t sweep, uint32_t k0, uint32_t k1, cudaStream_t st) {
+  switch (a.d.band_bins) {
+    case 128: return search_launch<T, 128>(a, what, sweep, k0, k1, st);
+    case 256: return search_launch<T, 256>(a, what, sweep, k0, k1, st);
+    case 512: return search_launch<T, 512>(a, what, sweep, k0, k1, st);
+    case 1024: return search_launch<T, 1024>(a, what, sweep, k0, k1, st);
+    default: return set_error(GBK_EINVAL, "gb_search: band_bins %d", a.d.band_bins);
+  }
+}
+
+static SearchArgs search_args(gbk_search* p, double* u, double* ell, const double* betas, const gbk_psd* psd,
+                              int psd_walker) {
+  SearchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.sa.c = *p->ctx;
+  a.sa.rho = p->rw;
+  if (psd) {
+    a.sa.psdp = psd->params;
+    a.sa.npsd = psd->n_psd;
+  }
+  a.d = p->d;
+  a.u = u;
+  a.ell = ell;
+  a.betas = betas;
+  a.psd_walker = psd_walker;
+  return a;
+}
+
+}  // namespace gbk
+
+extern "C" gbk_status gbk_search_create(gbk_ctx* ctx, const gbk_search_desc* desc, gbk_search** out) {
+  if (!ctx || !desc || !out) return set_error(GBK_EINVAL, "gbk_search_create: null argument");
+  *out = nullptr;
+  const gbk_search_desc& d = *desc;
+  if (d.n_bands < 1 || d.n_temps < 1 || d.n_walkers < 4 || (d.n_walkers & 1) || band_index(d.band_bins) < 0 ||
+      (int64_t)d.n_bands * d.n_temps * d.n_walkers > (1 << 26))
+    return set_error(GBK_EINVAL, "gbk_search_create: bad sizes (B=%d T=%d W=%d N=%d; W even, >= 4)", d.n_bands,
+                     d.n_temps, d.n_walkers, d.band_bins);
+  if (d.precision != GBK_MIXED && d.precision != GBK_FP64) return set_error(GBK_EINVAL, "gbk_search_create: bad precision");
+  if (!(d.stretch_a > 1.0) || !(d.ln_a_min < d.ln_a_max) || !(d.mc_min < d.mc_max) || !(d.mc_min > 0.0))
+    return set_error(GBK_EINVAL, "gbk_search_create: bad prior bounds or stretch scale");
+  const int64_t lo = d.band_k0 - d.band_bins - ctx->grid.k0;
+  const int64_t hi = d.band_k0 + (int64_t)(d.n_bands + 1) * d.band_bins - ctx->grid.k0;
+  if (lo < 0 || hi > ctx->grid.n_bins)
+    return set_error(GBK_ERANGE, "gbk_search_create: band windows [%lld, %lld) leave the grid", (long long)lo,
+                     (long long)hi);
+  gbk_search* p = (gbk_search*)calloc(1, sizeof(gbk_search));
+  if (!p) return set_error(GBK_ENOMEM, "gbk_search_create: host allocation");
+  p->ctx = ctx;
+  p->d = d;
+  const size_t csz = d.precision == GBK_MIXED ? sizeof(float2) : sizeof(double2);
+  if (cudaMalloc(&p->rw, (size_t)d.n_bands * 2 * 3 * d.band_bins * csz) != cudaSuccess) {
+    cudaGetLastError();
+    free(p);
+    return set_error(GBK_ENOMEM, "gbk_search_create: device allocation");
+  }
+  *out = p;
+  return GBK_OK;
+}
+
+extern "C" gbk_status gbk_search_destroy(gbk_search* p) {
+  if (!p) return set_error(GBK_EINVAL, "gbk_search_destroy: null plan");
+  cudaDeviceSynchronize();
+  cudaFree(p->rw);
+  free(p);
+  return GBK_OK;
+}
+
+extern "C" gbk_status gb_search_init(gbk_search* p, double* u, uint64_t key, uint32_t seed, void* stream) {
+  if (!p || !u) return set_error(GBK_EINVAL, "gb_search_init: null argument");
+  const int n = p->d.n_bands * p->d.n_temps * p->d.n_walkers;
+  k_search_init<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(u, n, seed, (uint32_t)(key & 0xffffffffu),
+                                                                   (uint32_t)(key >> 32));
+  return check_launch("gb_search_init");
+}
+
+extern "C" gbk_status gb_search_windows(gbk_search* p, const gbk_residual* residual, int32_t walker, void* stream) {
+  if (!p || !residual || !residual->data) return set_error(GBK_EINVAL, "gb_search_windows: null argument");
+  if (walker < 0 || walker >= residual->n_walkers || residual->frac_bits < 40 || residual->frac_bits > 120)
+    return set_error(GBK_EINVAL, "gb_search_windows: walker %d outside the residual's %d", walker, residual->n_walkers);
+  SearchArgs a = search_args(p, nullptr, nullptr, nullptr, nullptr, 0);
+  const int grid = (p->d.n_bands + kSearchWarps - 1) / kSearchWarps;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long* r = (const long long*)residual->data;
+  const int64_t nb = p->ctx->grid.n_bins;
+#define GBK_SW(TT, NN) k_search_windows<TT, NN><<<grid, kSearchWarps * 32, 0, st>>>(a, r, nb, walker, residual->frac_bits)
+  const bool mixed = p->d.precision == GBK_MIXED;
+  switch (p->d.band_bins) {
+    case 128: if (mixed) GBK_SW(float, 128); else GBK_SW(double, 128); break;
+    case 256: if (mixed) GBK_SW(float, 256); else GBK_SW(double, 256); break;
+    case 512: if (mixed) GBK_SW(float, 512); else GBK_SW(double, 512); break;
+    default: if (mixed) GBK_SW(float, 1024); else GBK_SW(double, 1024); break;
+  }
+#undef GBK_SW
+  p->have_windows = true;
+  return check_launch("gb_search_windows");
+}
+
+extern "C" gbk_status gb_search_eval(gbk_search* p, const double* u, double* ell, const gbk_psd* psd, int32_t psd_walker,
+                                     void* stream) {
+  if (!p || !u || !ell || !psd || !psd->params) return set_error(GBK_EINVAL, "gb_search_eval: null argument");
+  if (!p->have_windows) return set_error(GBK_EINVAL, "gb_search_eval: no residual windows (gb_search_windows)");
+  if (psd_walker < 0 || (psd->n_psd != 1 && psd_walker >= psd->n_psd))
+    return set_error(GBK_EINVAL, "gb_search_eval: psd_walker %d outside the PSD's %d", psd_walker, psd->n_psd);
+  SearchArgs a = search_args(p, const_cast<double*>(u), ell, nullptr, psd, psd_walker);
+  cudaStream_t st = (cudaStream_t)stream;
+  return p->d.precision == GBK_MIXED ? search_dispatch<float>(a, 0, 0, 0, 0, st) : search_dispatch<double>(a, 0, 0, 0, 0, st);
+}
+
+extern "C" gbk_status gb_search_sweep(gbk_search* p, double* u, double* ell, const double* betas, const gbk_psd* psd,
+                                      int32_t psd_walker, uint64_t key, uint32_t sweep_index, double* best_ell,
+                                      double* best_u, int32_t* stall, int64_t* stats, void* stream) {
+  if (!p || !u || !ell || !betas || !psd || !psd->params) return set_error(GBK_EINVAL, "gb_search_sweep: null argument");
+  if (!p->have_windows) return set_error(GBK_EINVAL, "gb_search_sweep: no residual windows (gb_search_windows)");
+  if (psd_walker < 0 || (psd->n_psd != 1 && psd_walker >= psd->n_psd))
+    return set_error(GBK_EINVAL, "gb_search_sweep: psd_walker %d outside the PSD's %d", psd_walker, psd->n_psd);
+  if ((best_ell || best_u || stall) && !(best_ell && best_u && stall))
+    return set_error(GBK_EINVAL, "gb_search_sweep: best_ell, best_u and stall go together");
+  SearchArgs a = search_args(p, u, ell, betas, psd, psd_walker);
+  a.stats = (long long*)stats;
+  const uint32_t k0 = (uint32_t)(key & 0xffffffffu), k1 = (uint32_t)(key >> 32);
+  cudaStream_t st = (cudaStream_t)stream;
+  gbk_status s = p->d.precision == GBK_MIXED ? search_dispatch<float>(a, 1, sweep_index, k0, k1, st)
+                                             : search_dispatch<double>(a, 1, sweep_index, k0, k1, st);
+  if (s) return s;
+  if (p->d.n_temps > 1) {
+    const int n = p->d.n_bands * p->d.n_walkers;
+    k_search_swap<<<(n + 127) / 128, 128, 0, st>>>(a, sweep_index, k0, k1);
+    if ((s = check_launch("gb_search_sweep(swap)"))) return s;
+  }
+  if (best_ell) {
+    k_search_best<<<(p->d.n_bands + 127) / 128, 128, 0, st>>>(a, best_ell, best_u, stall);
+    if ((s = check_launch("gb_search_sweep(best)"))) return s;
+  }
+  return GBK_OK;
+}

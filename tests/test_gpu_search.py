@@ -1,0 +1,101 @@
+"""Per-band search sampler (gb_search_*) against the float64 oracle (oracle/search.py).
+
+Seeded residual (noise + two injected sources per band) of one walker, 3 bands x 2
+temperatures x 8 walkers. FP64: the prior draws bit for bit, every walker's likelihood to
+1e-8 (relative to the band's loudest), and three sweeps with identical decisions: the final
+walkers bit for bit (the stretch arithmetic is the oracle's, step by step), likelihoods to
+1e-8, the same numbers of accepted moves and swaps, the same best points. Mixed: likelihoods
+of the same walkers within 1e-2 + 1e-6 |l| (float32 waveforms and products, as the sweep's
+Delta lnL).
+"""
+import numpy as np
+import pytest
+
+from oracle import search as SR
+
+from _common import torch_cuda
+from _sweep_setup import FRAC, NB, small_ensemble
+
+pytestmark = pytest.mark.gpu
+
+KEY = (0x51, 0x7E)
+SEED = 4
+
+
+def _setup():
+    cfg, state, dfix, s = small_ensemble(seed=30, n_temps=1, n_walkers=1, n_bands=3, n_max=2, n_per_band=2,
+                                         betas=(1.0,))
+    scfg = SR.SearchConfig(tobs=cfg.tobs, k0=cfg.k0, n_bins=cfg.n_bins, band_k0=cfg.band_k0, nb=NB, n_bands=3,
+                           n_temps=2, n_walkers=8, betas=np.tile([1.0, 0.3], (3, 1)), psd=s, key=KEY)
+    return scfg, dfix
+
+
+def _gpu(torch, scfg, dfix, precision, n_sweeps):
+    from paper_2405_04690_gb300 import _lib as L
+    from paper_2405_04690_gb300 import synth
+    dev = torch.device("cuda")
+    ctx = L.Context(scfg.tobs, 15.0, scfg.k0, scfg.n_bins)
+    plan = L.SearchPlan(ctx, scfg.n_bands, NB, scfg.band_k0, scfg.n_temps, scfg.n_walkers, precision)
+    R = torch.from_numpy(dfix[None].copy()).to(dev).contiguous()
+    psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
+    PS = L.psd_struct(psdp)
+    u = torch.empty((scfg.n_bands, scfg.n_temps, scfg.n_walkers, 8), dtype=torch.float64, device=dev)
+    ell = torch.empty((scfg.n_bands, scfg.n_temps, scfg.n_walkers), dtype=torch.float64, device=dev)
+    key = KEY[0] | (KEY[1] << 32)
+    L.gb_search_init(plan, u, key, SEED)
+    L.gb_search_windows(plan, L.residual_struct(R, FRAC), 0)
+    L.gb_search_eval(plan, u, ell, PS)
+    u0, l0 = u.cpu().numpy(), ell.cpu().numpy()
+    betas = torch.from_numpy(np.ascontiguousarray(scfg.betas)).to(dev)
+    be = torch.full((scfg.n_bands,), -np.inf, dtype=torch.float64, device=dev)
+    bu = torch.zeros((scfg.n_bands, 8), dtype=torch.float64, device=dev)
+    stall = torch.zeros(scfg.n_bands, dtype=torch.int32, device=dev)
+    stats = torch.zeros((2, 2), dtype=torch.int64, device=dev)
+    for k in range(n_sweeps):
+        L.gb_search_sweep(plan, u, ell, betas, PS, key, k, best=(be, bu, stall), stats=stats)
+    L.gbk_sync_status(ctx)
+    out = (u0, l0, u.cpu().numpy(), ell.cpu().numpy(), be.cpu().numpy(), bu.cpu().numpy(), stall.cpu().numpy(),
+           stats.cpu().numpy())
+    plan.close()
+    ctx.close()
+    return out
+
+
+def test_search_fp64_matches_oracle():
+    torch = torch_cuda()
+    from paper_2405_04690_gb300 import _lib as L
+    scfg, dfix = _setup()
+    rw = SR.windows(scfg, dfix, FRAC)
+    u = SR.init(scfg, SEED)
+    u_init = u.copy()
+    ell = SR.evaluate(scfg, rw, u)
+    l_init = ell.copy()
+    best, bu, stall = np.full(3, -np.inf), np.zeros((3, 8)), np.zeros(3, dtype=np.int64)
+    trace = []
+    for k in range(3):
+        SR.sweep(scfg, rw, u, ell, k, trace=trace)
+        SR.best_update(u, ell, best, bu, stall)
+    u0, l0, ug, lg, bg, bug, sg, st = _gpu(torch, scfg, dfix, L.GBK_FP64, 3)
+    assert np.array_equal(u0, u_init)
+    scale = np.abs(l_init).max(axis=(1, 2))[:, None, None]
+    assert (np.abs(l0 - l_init) <= 1e-8 * scale).all(), np.abs(l0 - l_init).max()
+    assert np.array_equal(ug, u)
+    assert (np.abs(lg - ell) <= 1e-8 * scale).all()
+    n_str = sum(1 for r in trace if r["kind"] == 7)
+    n_str_acc = sum(1 for r in trace if r["kind"] == 7 and r["accepted"])
+    n_sw = sum(1 for r in trace if r["kind"] == 8)
+    n_sw_acc = sum(1 for r in trace if r["kind"] == 8 and r["accepted"])
+    assert st.tolist() == [[n_str, n_str_acc], [n_sw, n_sw_acc]]
+    assert n_str_acc > 0 and n_sw_acc > 0
+    assert np.array_equal(bug, bu) and np.array_equal(sg, stall)
+    assert (np.abs(bg - best) <= 1e-8 * scale[:, 0, 0]).all()
+
+
+def test_search_mixed_likelihoods():
+    torch = torch_cuda()
+    from paper_2405_04690_gb300 import _lib as L
+    scfg, dfix = _setup()
+    rw = SR.windows(scfg, dfix, FRAC)
+    u0, l0, *_ = _gpu(torch, scfg, dfix, L.GBK_MIXED, 0)
+    want = SR.evaluate(scfg, rw, u0)
+    assert (np.abs(l0 - want) <= 1e-2 + 1e-6 * np.abs(want)).all(), np.abs(l0 - want).max()
