@@ -442,6 +442,57 @@ def run_gmm_fit(torch, L, units, n_walkers, args, stream):
                  "precision": "mixed (float32 E-step, float64 M-step)"}
 
 
+def run_search_rj(torch, L, S, ens, data, args, stream):
+    """Search-RJ mixtures (Sec. V.E, App. G): every band's search sampler (4 temperatures x 32
+    walkers, own-bin f0 prior) runs on walker 0's residual; bands whose best point reaches
+    SNR 7 give their cold walkers of the last sweeps to one EM fit per band; returns the
+    sweep table [W][n_bands][272] and the timings."""
+    dev = data.device
+    nb, T_s, W_s = ens["n_bands"], 4, 32
+    plan = L.SearchPlan(S["ctx"], nb, N_BAND, ens["band_k0"], T_s, W_s, L.GBK_MIXED)
+    u = torch.empty((nb, T_s, W_s, 8), dtype=torch.float64, device=dev)
+    ell = torch.empty((nb, T_s, W_s), dtype=torch.float64, device=dev)
+    betas = torch.tensor([[0.5 ** t for t in range(T_s)]] * nb, dtype=torch.float64, device=dev)
+    be = torch.full((nb,), -np.inf, dtype=torch.float64, device=dev)
+    bu = torch.zeros((nb, 8), dtype=torch.float64, device=dev)
+    stall = torch.zeros(nb, dtype=torch.int32, device=dev)
+    st = torch.zeros((2, 2), dtype=torch.int64, device=dev)
+    n_run, n_keep = args.search_rj_sweeps, 20
+    x = torch.empty((nb, n_keep * W_s, 8), dtype=torch.float32, device=dev)
+    key = 0x5EA2C4
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    L.gb_search_init(plan, u, key, 1, stream)
+    L.gb_search_windows(plan, L.residual_struct(data, FRAC_BITS), 0, stream)
+    L.gb_search_eval(plan, u, ell, S["psd"], 0, stream)
+    for k in range(n_run):
+        L.gb_search_sweep(plan, u, ell, betas, S["psd"], key, k, best=(be, bu, stall), stats=st, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_run = e0.elapsed_time(e1)
+    for k in range(n_keep):
+        L.gb_search_sweep(plan, u, ell, betas, S["psd"], key, n_run + k, best=(be, bu, stall), stream=stream)
+        L.gb_search_samples(plan, u, be, 7.0, F_LO, F_HI, x, k * W_s, stream)
+    raw = torch.empty((N_W, nb, 272), dtype=torch.float32, device=dev)
+    e0.record(stream)
+    L.gmm_fit(x, raw, n_iter=args.gmm_iters, precision=L.GBK_MIXED, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    snr = torch.sqrt(2.0 * torch.clamp(be, min=0.0)).cpu().numpy()
+    s = st.cpu().numpy()
+    plan.close()
+    out = {"bands": nb, "temps": T_s, "walkers": W_s, "sweeps": n_run, "sample_sweeps": n_keep,
+           "ms_per_sweep": ms_run / n_run,
+           "proposals_per_s": float(s[0, 0]) / (ms_run * 1e-3),
+           "stretch_acceptance": float(s[0, 1]) / max(1.0, float(s[0, 0])),
+           "swap_acceptance": float(s[1, 1]) / max(1.0, float(s[1, 0])),
+           "bands_snr_ge_7": int((snr >= 7.0).sum()), "best_snr_median": float(np.median(snr)),
+           "bands_still_improving_last_50": int((stall.cpu().numpy() < 50).sum()),
+           "fit_ms": e0.elapsed_time(e1), "snr_min": 7.0}
+    return raw, out
+
+
 def run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, snap, ess_plain, units=None):
     """The learned proposal on the ensemble: training throughput on the cold-chain pairs
     (BF16 tensor cores), then the same ESS run with the proposal, then a search from an
@@ -532,7 +583,10 @@ def run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, sn
     L.residual_add_sub(S["ctx"], S["R"], cold.t().contiguous(), torch.full((cold.shape[0],), N_BAND,
                        dtype=torch.int32, device=dev), N_BAND, wv, -1, L.GBK_MIXED, stream)
     data = S["resid"].clone()                               # d (noise + injected sources) per walker
-    for mode in ("prior", "learned", "gmm_refit"):
+    # the paper's search-RJ proposal: per-band search samplers on walker 0's data residual, then
+    # mixtures fitted to their cold walkers around the best points of bands with SNR >= 7
+    srj_raw, search["search_rj_sampler"] = run_search_rj(torch, L, S, ens, data, args, stream)
+    for mode in ("prior", "learned", "gmm_refit", "search_rj"):
         if mode == "gmm_refit" and gmm_raw is None:
             continue
         S["P"].zero_()
@@ -542,6 +596,8 @@ def run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, sn
             L.gbk_sweep_set_proposal(S["plan"], net=net, eps=args.mdn_eps, inmodel_frac=args.mdn_inmodel)
         elif mode == "gmm_refit":
             L.gbk_sweep_set_proposal(S["plan"], raw_table=gmm_raw, eps=args.mdn_eps, inmodel_frac=args.mdn_inmodel)
+        elif mode == "search_rj":
+            L.gbk_sweep_set_proposal(S["plan"], raw_table=srj_raw, eps=args.mdn_eps, inmodel_frac=args.mdn_inmodel)
         else:
             L.gbk_sweep_set_proposal(S["plan"])
         fl = 0 if mode == "prior" else L.SWEEP_MDN
@@ -922,6 +978,7 @@ def main():
     ap.add_argument("--mdn-inmodel", type=float, default=0.1, help="fraction of in-model moves drawn from it")
     ap.add_argument("--search-sweeps", type=int, default=10)
     ap.add_argument("--gmm-keep", type=int, default=10, help="sweeps of cold-chain sources for the mixture refit")
+    ap.add_argument("--search-rj-sweeps", type=int, default=300, help="search-sampler sweeps before sampling")
     ap.add_argument("--gmm-iters", type=int, default=50, help="EM iterations of the mixture refit")
     ap.add_argument("--group-frac", type=float, default=0.5, help="fraction of in-model moves that are group stretches "
                                                                    "in the group-stretch ESS run (0: skip it)")

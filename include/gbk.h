@@ -535,6 +535,14 @@ gbk_status gb_search_eval(gbk_search* plan, const double* u, double* ell, const 
 gbk_status gb_search_sweep(gbk_search* plan, double* u, double* ell, const double* betas, const gbk_psd* psd,
                            int32_t psd_walker, uint64_t key, uint32_t sweep_index, double* best_ell, double* best_u,
                            int32_t* stall, int64_t* stats, void* stream);
+/* Training points of the search-RJ mixtures from the current state: for every band b the cold
+ * walkers' u in the sweep's unit coordinates (the learned proposal's: f0 over the band's
+ * allowance, own bins +- half a band clipped to [f_min, f_max]; the other coordinates
+ * unchanged) into x[b][row0 + k][8] (float32, device, [n_bands][n_rows][8]), k < n_walkers;
+ * rows of a band whose best point has sqrt(2 best_ell) < snr_min are NaN. Fit them with
+ * gmm_fit (one group per band) for the sweep's mixture table. */
+gbk_status gb_search_samples(gbk_search* plan, const double* u, const double* best_ell, double snr_min, double f_min,
+                             double f_max, float* x, int32_t n_rows, int32_t row0, void* stream);
 
 /* Group stretch in-model moves (the paper's in-model proposal, Eq. stretch with a stationary
  * group): builds every band's stationary group from the current cold chain -- the sources of

@@ -172,3 +172,29 @@ def best_update(u, ell, best_ell, best_u, stall):
             stall[b] = 0
         else:
             stall[b] += 1
+
+
+def to_sweep_unit(cfg, b, u, f_min, f_max):
+    """A search point of band b in the sampler's unit coordinates (``oracle.mdn.to_unit``), whose
+    f0 coordinate spans the band's allowance (own bins +- half a band, clipped to [f_min,
+    f_max]) instead of its own bins; the other coordinates are the same."""
+    lo, hi = cfg.core(b)
+    f0 = lo + (hi - lo) * u[1]
+    lob = cfg.band_k0 + b * cfg.nb
+    alo = max(f_min, (lob - cfg.nb / 2) / cfg.tobs)
+    ahi = min(f_max, (lob + cfg.nb + cfg.nb / 2) / cfg.tobs)
+    out = np.array(u, dtype=np.float64)
+    out[1] = (f0 - alo) / (ahi - alo)
+    return out
+
+
+def samples(cfg, u, best_ell, snr_min, f_min, f_max):
+    """Training points of the search-RJ mixtures from one sweep: the cold walkers of every band
+    in the sampler's unit coordinates, [B][W][8]; rows of a band whose best point has
+    sqrt(2 l_best) < snr_min are NaN (the band gets no fitted component)."""
+    out = np.full((cfg.n_bands, cfg.n_walkers, D), np.nan)
+    for b in range(cfg.n_bands):
+        if best_ell[b] > 0 and math.sqrt(2.0 * best_ell[b]) >= snr_min:
+            for k in range(cfg.n_walkers):
+                out[b, k] = to_sweep_unit(cfg, b, u[b, 0, k], f_min, f_max)
+    return out

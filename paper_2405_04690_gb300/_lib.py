@@ -130,6 +130,8 @@ SIGNATURES = {
     "gb_search_eval": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(GbkPsd), _i32, _vp]),
     "gb_search_sweep": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(GbkPsd), _i32, ctypes.c_uint64,
                                        ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp]),
+    "gb_search_samples": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp, _i32,
+                                         _i32, _vp]),
     "gbk_sweep_adapt_temps": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_double, ctypes.c_double, _vp]),
     "gbk_sweep_transfer": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "gbk_sweep_update_group": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _i32, _vp]),
@@ -583,3 +585,10 @@ def gb_search_sweep(plan, u, ell, betas, psd, key, sweep_index, psd_walker=0, be
                                  _dev(be, torch.float64, "best_ell"), _dev(bu, torch.float64, "best_u"),
                                  _dev(st, torch.int32, "stall"), _dev(stats, torch.int64, "stats"), _stream(stream)),
            "gb_search_sweep")
+
+
+def gb_search_samples(plan, u, best_ell, snr_min, f_min, f_max, x, row0, stream=None):
+    """Cold walkers of every band into x [n_bands][n_rows][8] (float32) at rows row0 .. row0 + W."""
+    _check(lib().gb_search_samples(plan.handle, _dev(u, torch.float64, "u"), _dev(best_ell, torch.float64, "best_ell"),
+                                   float(snr_min), float(f_min), float(f_max), _dev(x, torch.float32, "x"),
+                                   int(x.shape[1]), int(row0), _stream(stream)), "gb_search_samples")

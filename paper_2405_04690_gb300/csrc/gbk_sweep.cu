@@ -2083,6 +2083,34 @@ __global__ void k_search_best(const SearchArgs a, double* best_ell, double* best
   }
 }
 
+// Training points of the search-RJ mixtures: the cold walkers of every band in the sampler's
+// unit coordinates (f0 over the band's allowance, clipped to [f_min, f_max]), NaN rows for a
+// band whose best point has sqrt(2 l_best) < snr_min. One thread per (band, walker).
+__global__ void k_search_samples(const SearchArgs a, const double* __restrict__ best_ell, double snr_min,
+                                 double f_min, double f_max, float* __restrict__ x, int n_rows, int row0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int W = a.d.n_walkers;
+  if (i >= a.d.n_bands * W) return;
+  const int b = i / W, k = i % W;
+  float* o = x + ((int64_t)b * n_rows + row0 + k) * 8;
+  const double be = best_ell[b];
+  if (!(be > 0.0 && sqrt(2.0 * be) >= snr_min)) {
+    for (int c = 0; c < 8; ++c) o[c] = __int_as_float(0x7fc00000);
+    return;
+  }
+  const double* u = a.u + ((int64_t)b * a.d.n_temps * W + k) * 8;
+  const double tobs = a.sa.c.grid.tobs;
+  const long long lob = a.d.band_k0 + (long long)b * a.d.band_bins;
+  const double lo = __ddiv_rn((double)lob, tobs), hi = __ddiv_rn((double)(lob + a.d.band_bins), tobs);
+  const double f0 = dadd(lo, dmul(dsub(hi, lo), u[1]));
+  const double half = 0.5 * a.d.band_bins;
+  double alo = __ddiv_rn(dsub((double)lob, half), tobs), ahi = __ddiv_rn(dadd((double)(lob + a.d.band_bins), half), tobs);
+  if (alo < f_min) alo = f_min;
+  if (ahi > f_max) ahi = f_max;
+  for (int c = 0; c < 8; ++c) o[c] = (float)u[c];
+  o[1] = (float)__ddiv_rn(dsub(f0, alo), dsub(ahi, alo));
+}
+
 template <typename T, int N>
 static gbk_status search_launch(SearchArgs& a, int what, uint32_t sweep, uint32_t k0, uint32_t k1, cudaStream_t st) {
   const size_t sm = kSearchWarps * sizeof(SearchSmem<T, N>);
@@ -2249,4 +2277,18 @@ extern "C" gbk_status gb_search_sweep(gbk_search* p, double* u, double* ell, con
     if ((s = check_launch("gb_search_sweep(best)"))) return s;
   }
   return GBK_OK;
+}
+
+extern "C" gbk_status gb_search_samples(gbk_search* p, const double* u, const double* best_ell, double snr_min,
+                                        double f_min, double f_max, float* x, int32_t n_rows, int32_t row0,
+                                        void* stream) {
+  if (!p || !u || !best_ell || !x) return set_error(GBK_EINVAL, "gb_search_samples: null argument");
+  if (row0 < 0 || (int64_t)row0 + p->d.n_walkers > n_rows)
+    return set_error(GBK_EINVAL, "gb_search_samples: rows [%d, %d) outside %d", row0, row0 + p->d.n_walkers, n_rows);
+  if (!(f_min < f_max)) return set_error(GBK_EINVAL, "gb_search_samples: f_min >= f_max");
+  SearchArgs a = search_args(p, const_cast<double*>(u), nullptr, nullptr, nullptr, 0);
+  const int n = p->d.n_bands * p->d.n_walkers;
+  k_search_samples<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(a, best_ell, snr_min, f_min, f_max, x, n_rows,
+                                                                       row0);
+  return check_launch("gb_search_samples");
 }

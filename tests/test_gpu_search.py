@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 KEY = (0x51, 0x7E)
 SEED = 4
+SNR_MIN, F_MIN, F_MAX = 3.0, 1e-3, 4e-3
 
 
 def _setup():
@@ -53,9 +54,11 @@ def _gpu(torch, scfg, dfix, precision, n_sweeps):
     stats = torch.zeros((2, 2), dtype=torch.int64, device=dev)
     for k in range(n_sweeps):
         L.gb_search_sweep(plan, u, ell, betas, PS, key, k, best=(be, bu, stall), stats=stats)
+    x = torch.full((scfg.n_bands, scfg.n_walkers + 3, 8), 7.0, dtype=torch.float32, device=dev)
+    L.gb_search_samples(plan, u, be, SNR_MIN, F_MIN, F_MAX, x, 2)
     L.gbk_sync_status(ctx)
     out = (u0, l0, u.cpu().numpy(), ell.cpu().numpy(), be.cpu().numpy(), bu.cpu().numpy(), stall.cpu().numpy(),
-           stats.cpu().numpy())
+           stats.cpu().numpy(), x.cpu().numpy())
     plan.close()
     ctx.close()
     return out
@@ -75,7 +78,7 @@ def test_search_fp64_matches_oracle():
     for k in range(3):
         SR.sweep(scfg, rw, u, ell, k, trace=trace)
         SR.best_update(u, ell, best, bu, stall)
-    u0, l0, ug, lg, bg, bug, sg, st = _gpu(torch, scfg, dfix, L.GBK_FP64, 3)
+    u0, l0, ug, lg, bg, bug, sg, st, xg = _gpu(torch, scfg, dfix, L.GBK_FP64, 3)
     assert np.array_equal(u0, u_init)
     scale = np.abs(l_init).max(axis=(1, 2))[:, None, None]
     assert (np.abs(l0 - l_init) <= 1e-8 * scale).all(), np.abs(l0 - l_init).max()
@@ -89,6 +92,11 @@ def test_search_fp64_matches_oracle():
     assert n_str_acc > 0 and n_sw_acc > 0
     assert np.array_equal(bug, bu) and np.array_equal(sg, stall)
     assert (np.abs(bg - best) <= 1e-8 * scale[:, 0, 0]).all()
+    # training points for the mixtures: rows 2 .. 2 + W of every band, the rest untouched
+    want = SR.samples(scfg, u, best, SNR_MIN, F_MIN, F_MAX).astype(np.float32)
+    assert np.isfinite(want).any() and np.isnan(want).any()
+    np.testing.assert_allclose(xg[:, 2:2 + scfg.n_walkers], want, rtol=1e-7, atol=0)
+    assert (xg[:, :2] == 7.0).all() and (xg[:, 2 + scfg.n_walkers:] == 7.0).all()
 
 
 def test_search_mixed_likelihoods():

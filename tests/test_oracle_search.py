@@ -105,3 +105,26 @@ def test_best_point_bookkeeping():
     SR.best_update(u, ell, best, bu, stall)
     assert best.tolist() == [5.0, 0.0] and stall.tolist() == [0, 5]
     assert np.array_equal(bu[0], u[0, 0, 1]) and np.array_equal(bu[1], np.zeros(8))
+
+
+def test_search_points_map_to_the_sampler_coordinates():
+    # own-bin u1 = 0, 1/2, 1 -> allowance coordinate 1/4, 1/2, 3/4 for an interior band; the
+    # parameters are unchanged (same source); low-SNR bands give NaN rows
+    from oracle import mdn as MD
+    from oracle import mcmc as OM
+    cfg = _cfg(n_bands=3)
+    g = np.random.default_rng(2)
+    for u1, want in ((0.0, 0.25), (0.5, 0.5), (1.0, 0.75)):
+        u = g.uniform(0.1, 0.9, 8)
+        u[1] = u1
+        v = SR.to_sweep_unit(cfg, 1, u, 1e-4, 1e-2)
+        assert abs(v[1] - want) < 1e-12 and np.array_equal(np.delete(v, 1), np.delete(u, 1))
+    scfg = OM.SweepConfig(tobs=cfg.tobs, k0=cfg.k0, n_bins=cfg.n_bins, band_k0=cfg.band_k0, nb=256, n_bands=3,
+                          n_temps=1, n_walkers=1, n_max=1, betas=np.ones((3, 1)), psd=np.ones((1, cfg.n_bins)),
+                          sigma=np.ones(8), f_min=1e-4, f_max=1e-2)
+    u = g.uniform(0.1, 0.9, 8)
+    th = SR.from_unit(cfg, 1, u)
+    np.testing.assert_allclose(MD.to_unit(scfg, 1, th), SR.to_sweep_unit(cfg, 1, u, 1e-4, 1e-2), rtol=1e-9, atol=1e-12)
+    uu = g.uniform(0, 1, (3, 2, 16, 8))
+    x = SR.samples(cfg, uu, np.array([50.0, 10.0, -1.0]), 7.0, 1e-4, 1e-2)
+    assert np.isfinite(x[0]).all() and np.isnan(x[1]).all() and np.isnan(x[2]).all()
