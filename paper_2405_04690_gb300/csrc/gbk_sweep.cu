@@ -1102,30 +1102,41 @@ __global__ void __launch_bounds__(kBandWarps * 32, kBandMinCtas) k_band(const Sw
 // -------------------------------------------------------------- tempering (Alg. 2)
 // <rho - Hx|rho - Hx> - <rho - Hy|rho - Hy> = cw sum_k w_k Re[(Hy - Hx) conj(2 rho - Hx - Hy)],
 // formed bin by bin so the large common parts cancel before summation.
+// Both set differences of one swap proposal in one pass over the window, the two template
+// sums read once: D1 = diff(rho_t; hx, hy) with walker t's PSD weights and D2 = diff(rho_m;
+// hy, hx) with walker m's, where diff(rho; x, y) = <rho - x|rho - x> - <rho - y|rho - y>.
 template <typename T, int N>
-__device__ __noinline__ double set_diff(const SweepArgs& a, const typename CT<T>::C* __restrict__ rho,
-                                        const typename CT<T>::C* __restrict__ hx,
-                                        const typename CT<T>::C* __restrict__ hy, int64_t gw, const PsdWt<T>& pw,
-                                        int lane) {
+__device__ __noinline__ void set_diff2(const SweepArgs& a, const typename CT<T>::C* __restrict__ rt,
+                                       const typename CT<T>::C* __restrict__ rm, const typename CT<T>::C* __restrict__ hx,
+                                       const typename CT<T>::C* __restrict__ hy, int64_t gw, const PsdWt<T>& pt,
+                                       const PsdWt<T>& pm, int lane, double& d1, double& d2) {
   typedef typename CT<T>::C C;
   constexpr int W3 = 3 * N;
-  typename SAcc<T>::S acc;
-  acc.init();
+  typename SAcc<T>::S a1, a2;
+  a1.init();
+  a2.init();
 #pragma unroll 4
   for (int i = lane; i < W3; i += 32) {
     const int64_t k = gw + i;
-    const T wt = iqv(a.c, k, T()) * recip((T)1 + pw.aw * rhov(a.c, k, T()));
-    T s = (T)0;
+    const T iq = iqv(a.c, k, T()), rh = rhov(a.c, k, T());
+    const T w1 = iq * recip((T)1 + pt.aw * rh);
+    const T w2 = iq * recip((T)1 + pm.aw * rh);
+    T s1 = (T)0, s2 = (T)0;
 #pragma unroll
     for (int ch = 0; ch < 2; ++ch) {
-      const C r = rho[ch * W3 + i], x = hx[ch * W3 + i], y = hy[ch * W3 + i];
-      const C dlt = csub(y, x);
-      const C sm = csub(cscale(r, (T)2), cadd(x, y));
-      s += dlt.x * sm.x + dlt.y * sm.y;
+      const C x = hx[ch * W3 + i], y = hy[ch * W3 + i];
+      const C r1 = rt[ch * W3 + i], r2 = rm[ch * W3 + i];
+      const C dl1 = csub(y, x), dl2 = csub(x, y);
+      const C sm1 = csub(cscale(r1, (T)2), cadd(x, y));
+      const C sm2 = csub(cscale(r2, (T)2), cadd(y, x));
+      s1 += dl1.x * sm1.x + dl1.y * sm1.y;
+      s2 += dl2.x * sm2.x + dl2.y * sm2.y;
     }
-    acc.add(wt * s);
+    a1.add(w1 * s1);
+    a2.add(w2 * s2);
   }
-  return pw.cw * acc.warp_total();
+  d1 = pt.cw * a1.warp_total();
+  d2 = pm.cw * a2.warp_total();
 }
 
 // Move the cached templates of one band into (sign +1: R -= h) or out of (sign -1:
@@ -1209,8 +1220,8 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_swap(const SweepArgs a) {
       C* Hm = hsum_ptr<T>(a, t - 1, wm, b);
       const PsdWt<T> pt_ = walker_psd<T>(a, wt), pm_ = walker_psd<T>(a, wm);
       // l_t(m) - l_t(t) = -1/2 D1, l_m(t) - l_m(m) = -1/2 D2 (band-local likelihoods)
-      const double D1 = set_diff<T, N>(a, rho_ptr<T>(a, wt, j), Hm, Ht, gw, pt_, lane);
-      const double D2 = set_diff<T, N>(a, rho_ptr<T>(a, wm, j), Ht, Hm, gw, pm_, lane);
+      double D1, D2;
+      set_diff2<T, N>(a, rho_ptr<T>(a, wt, j), rho_ptr<T>(a, wm, j), Hm, Ht, gw, pt_, pm_, lane, D1, D2);
       const double la = a.betas[(int64_t)b * T_ + t] * (-0.5 * D1) + a.betas[(int64_t)b * T_ + t - 1] * (-0.5 * D2);
       const U4 v = philox4x32_10((uint32_t)t, (uint32_t)(b * W + c), 4u | ((uint32_t)a.parity << 4), a.sweep, a.k0, a.k1);
       const double lu = log_u(u53(v.x, v.y), T());
