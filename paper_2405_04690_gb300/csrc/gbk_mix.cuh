@@ -101,7 +101,7 @@ __device__ T mix_logq(const MixRow<T>& m, const T* u, T eps) {
 #pragma unroll
   for (int d = 0; d < kMixDim; ++d) uu[d] = u[d];
   T mx = -(T)INFINITY, se = (T)0;
-#pragma unroll 2
+#pragma unroll 4
   for (int k = 0; k < kMixComp; ++k) {
     T mu[kMixDim], is[kMixDim];
     ld8(m.mu[k], mu);
