@@ -52,7 +52,7 @@ def flops_per_evaluation(n=N_BAND):
 
 
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
-K_BAND_TRAFFIC = 8 * (1275.473e6 + 812.201e6)   # DRAM bytes per band-kernel launch (ncu, scaled)
+K_BAND_TRAFFIC = 8 * (1276.079e6 + 812.371e6)   # DRAM bytes per band-kernel launch (ncu, scaled)
 
 
 def measured_hbm_gbs():
