@@ -36,7 +36,7 @@ METRIC = "GB proposals (waveform+DeltalogL) /sec"
 WORKLOAD = ("batched ensemble: 16 temps x 32 walkers x 2000 GBs (1-4 mHz, N=256, 369 sub-bands); one step = one "
             "full sweep (in-model 1/source + flip-all RJ + PT swaps), mixed precision")
 
-# Algorithmic float32 work (derived in the design doc from the operation count of the method):
+# Algorithmic float32 work (counted from the operations of the method):
 # slow-part response 621 flops per coarse sample, band FFT 5 N log2 N per channel,
 # Delta lnL 45 flops per band bin.
 FLOPS_SLOW_PER_SAMPLE = 621

@@ -9,8 +9,8 @@ constants and no tables; each writes its own from the paper.
 Contents (each function cites the passage of arXiv:2405.04690 it follows):
 
 * ``constants``  -- physical constants and the observation grid (Sec. III, Eq. psd).
-* ``orbits``     -- analytic equal-arm constellation (the paper cites it; reading in
-                    DESIGN.md).
+* ``orbits``     -- analytic equal-arm constellation (the paper cites it but gives no
+                    model: first-order-in-eccentricity heliocentric orbits).
 * ``psd``        -- Eq. psd with S_pm/S_op, and the Galactic foreground (Sec. III.A).
 * ``waveform``   -- GB TDI A/E band by the fast/slow decomposition (App. F, Sec. II.A),
                     plus the brute-force time-domain response used to pin it.

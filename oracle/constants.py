@@ -2,7 +2,7 @@
 
 The paper fixes f* = c/L and x = 2 pi f / f* (Sec. III, Eq. psd) but not the
 numerical values of c, L, the astronomical unit or the year; the values below are the
-standard LISA / LDC ones (reading recorded in the design doc).
+standard LISA / LDC ones.
 """
 
 C_LIGHT = 299792458.0          # m / s

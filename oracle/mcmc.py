@@ -16,7 +16,7 @@ Follows arXiv:2405.04690:
   changes the cold chain updates its residual.
 * Sec. V.D: odd bands first, then even bands; three sub-bands per band window.
 
-Readings where the paper is silent (listed in the design doc): see ``SweepConfig``.
+Readings where the paper is silent: see ``SweepConfig``.
 Random numbers come from Philox4x32-10 at fixed counters (``oracle.philox``).
 """
 import math
@@ -55,7 +55,7 @@ def temp_final_log_alpha(ll_i_m, ll_j_n, ll_i_n, ll_j_m, beta_I, beta_II):
 
 # ---------------------------------------------------------------- configuration
 class SweepConfig:
-    """Sampler set-up. Readings of the paper:
+    """Sampler set-up. Readings where the paper is silent:
 
     * bands of ``nb`` bins starting at bin ``band_k0``; band b owns f0 in
       [band_k0 + b nb, band_k0 + (b+1) nb) / T and its sources may move half a band

@@ -1,7 +1,7 @@
 """Analytic LISA orbits for the oracle (test infrastructure).
 
 The paper assumes a rigid constellation with equal, constant arms for TDI 1.5
-(Sec. II, below Eq. swapsource) and names no orbit model. Reading (DESIGN.md): the
+(Sec. II, below Eq. swapsource) and names no orbit model. Reading: the
 standard first-order-in-eccentricity heliocentric orbits, orbital phase and
 constellation orientation both zero at t = 0,
 

@@ -12,7 +12,7 @@ proposal (Eq. stretch) over walkers and tempering between neighbouring temperatu
 same walker index, which share the residual (so Eq. temp-orig applies and no extra
 likelihoods are needed).
 
-Readings: sampled coordinates v = (ln sqrt(S_oms,A), ln sqrt(S_acc,A),
+Readings (the paper gives the structure only): sampled coordinates v = (ln sqrt(S_oms,A), ln sqrt(S_acc,A),
 ln sqrt(S_oms,E), ln sqrt(S_acc,E), ln A_fg, alpha, f_k, s1, s2), uniform prior on a box;
 ensemble halves [0, W/2) and [W/2, W) updated in turn, partner drawn from the other half;
 z ~ 1/sqrt(z) on [1/a, a], a = 2; acceptance z^(d-1) (L_Y / L_X)^beta, d = 9; swaps from the

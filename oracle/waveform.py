@@ -8,7 +8,7 @@ formula for it. The oracle therefore gives the model in two forms:
 * ``bruteforce_tdi`` / ``bruteforce_band`` (W1) -- the same physical model evaluated
   exactly at every fine sample with a direct DFT; W2 is pinned against it.
 
-Model (readings recorded in the design doc):
+Model (readings where the paper is silent):
 
 * 8 parameters A, f0, fdot, phi0, psi, cos(iota), sin(beta), lambda.
 * h_+ = A (1 + cos^2 iota) cos Phi, h_x = -2 A cos iota sin Phi,
