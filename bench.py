@@ -259,7 +259,7 @@ def build_device_state(torch, L, dev, ens, precision, seed):
                        f_min=F_LO, f_max=F_HI)
     L.gbk_sync_status(ctx)
     return {"ctx": ctx, "plan": plan, "P": P, "E": E, "resid": resid, "R": R, "psd": L.psd_struct(psdp),
-            "psdp": psdp, "betas": betas}
+            "psdp": psdp, "betas": betas, "noise": one}
 
 
 def band_for(f0):
