@@ -345,7 +345,8 @@ def reduce_over_ranks(torch, dist, world, device, ms, work):
     return float(tm.item()), float(tw.item())
 
 
-def run_ess(torch, L, S, step, stats, stream, n_sweeps, flags=0, pairs=None, group=None, units=None, keep=10):
+def run_ess(torch, L, S, step, stats, stream, n_sweeps, flags=0, pairs=None, group=None, units=None, keep=10,
+            adapt=False):
     """ESS/s: integrated autocorrelation time of every cold walker's total log-likelihood
     (Eq. like on its residual) over n_sweeps sweeps (first quarter discarded). Optionally
     collects training pairs of the learned proposal after the burn-in and the cold slots' unit
@@ -364,6 +365,8 @@ def run_ess(torch, L, S, step, stats, stream, n_sweeps, flags=0, pairs=None, gro
         if group is not None and k % group[2] == 0:   # (fraction, friends, sweeps between rebuilds)
             L.gbk_sweep_update_group(S["plan"], S["P"], S["E"], group[0], group[1], stream)
         step(flags)
+        if adapt:   # every band's ladder from this sweep's swap acceptance (Vousden et al.)
+            L.gbk_sweep_adapt_temps(S["plan"], S["betas"], k, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
         t_sweeps += e0.elapsed_time(e1) * 1e-3
@@ -847,6 +850,19 @@ def run_ours(args):
             eg["group"] = {"frac": args.group_frac, "n_friends": args.n_friends, "rebuild_every_sweeps": 30}
             eg["ess_gain"] = eg["ess_per_s"] / ess["ess_per_s"]
             ess["group_stretch"] = eg
+        # ladders adapted after every sweep (the paper adapts its temperatures as it runs)
+        betas0 = S["betas"].clone()
+        S["P"].copy_(snap[0])
+        S["E"].copy_(snap[1])
+        S["resid"].copy_(snap[2])
+        L.gb_sweep(S["plan"], S["P"], S["E"], S["betas"], S["R"], S["psd"], 1, 0, L.SWEEP_REFRESH, stream=stream)
+        ea = run_ess(torch, L, S, step, stats, stream, args.ess_sweeps, adapt=True)
+        bt = S["betas"].cpu().numpy()
+        ea["ladder"] = {"beta_rung_1_median": float(np.median(bt[:, 1])), "beta_rung_1_range":
+                        [float(bt[:, 1].min()), float(bt[:, 1].max())], "start_beta_rung_1": float(betas0[0, 1].item())}
+        ea["ess_gain"] = ea["ess_per_s"] / ess["ess_per_s"]
+        ess["adaptive_ladder"] = ea
+        S["betas"].copy_(betas0)
         if pairs is not None:
             learned = run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, snap, ess, units)
         del snap

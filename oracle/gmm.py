@@ -78,10 +78,13 @@ def m_step(x, r, reg=1e-6):
     return nk / nk.sum(), mu, var
 
 
-def fit(x, n_comp=N_COMP, n_iter=50, reg=1e-6):
-    """EM from ``init``: n_iter (E, M) iterations. Returns (w, mu, var, history) with history the
-    log-likelihood before each M-step and, last, that of the returned parameters."""
+def fit(x, n_comp=N_COMP, n_iter=50, reg=1e-6, cap=None):
+    """EM from ``init``: n_iter (E, M) iterations on the present rows (the first ``cap`` of them
+    when given). Returns (w, mu, var, history) with history the log-likelihood before each
+    M-step and, last, that of the returned parameters."""
     x = present(x)
+    if cap is not None:
+        x = x[:cap]
     if x.shape[0] == 0:
         return np.zeros(0), np.zeros((0, N_DIM)), np.zeros((0, N_DIM)), []
     w, mu, var = init(x, n_comp, reg)

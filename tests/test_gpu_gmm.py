@@ -119,3 +119,27 @@ def test_gmm_fit_mixed_likelihood_with_16_components():
         n = int((~np.isnan(x[gi]).any(axis=1)).sum())
         assert abs(ll[gi] - lw) < 1e-3 * n, (gi, ll[gi], lw)
     assert np.isfinite(raw).all()
+
+
+def test_gmm_fit_uses_the_first_present_rows_up_to_the_cap():
+    # 3000 rows (100 absent) of three clusters in one group: the library fits the first
+    # gmm_max_points() present rows, as the oracle does with the same cap (FP64, 1e-9)
+    torch = torch_cuda()
+    from paper_2405_04690_gb300 import _lib as L
+    cap = L.gmm_max_points()
+    g = np.random.default_rng(12)
+    c = g.uniform(0.2, 0.8, (3, 8))
+    x = np.concatenate([c[j] + 0.01 * g.standard_normal((1000, 8)) for j in range(3)])
+    x[g.choice(3000, 100, replace=False)] = np.nan
+    x = x.astype(np.float32)[None]
+    assert (~np.isnan(x[0]).any(axis=1)).sum() > cap
+    w, mu, var, hist = GM.fit(x[0].astype(np.float64), n_iter=20, cap=cap)
+    raw = torch.empty((1, 1, 272), dtype=torch.float32, device="cuda")
+    fit = torch.zeros((1, 16, 17), dtype=torch.float64, device="cuda")
+    ll = torch.zeros(1, dtype=torch.float64, device="cuda")
+    L.gmm_fit(torch.from_numpy(x).cuda(), raw, n_iter=20, precision=L.GBK_FP64, fit_out=fit, loglike=ll)
+    fit = fit.cpu().numpy()[0]
+    np.testing.assert_allclose(fit[:, 0], w, rtol=1e-9, atol=1e-14)
+    np.testing.assert_allclose(fit[:, 1:9], mu, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(fit[:, 9:], var, rtol=1e-9, atol=1e-15)
+    assert abs(ll.item() - hist[-1]) <= 1e-10 * abs(hist[-1])
