@@ -1984,10 +1984,10 @@ __global__ void k_search_init(double* u, int n, uint32_t seed, uint32_t k0, uint
 template <typename T, int N>
 __global__ void __launch_bounds__(kSearchWarps * 32) k_search_eval(const SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   SearchSmem<T, N>& S = reinterpret_cast<SearchSmem<T, N>*>(smem_raw)[wid];
   const int n = a.d.n_bands * a.d.n_temps * a.d.n_walkers;
-  for (int c = blockIdx.x * kSearchWarps + wid; c < n; c += gridDim.x * kSearchWarps) {
+  for (int c = blockIdx.x * wpc + wid; c < n; c += gridDim.x * wpc) {
     const int b = c / (a.d.n_temps * a.d.n_walkers);
     const double l = search_ell<T, N>(a, S, b, a.u + (int64_t)c * 8, lane);
     if (lane == 0) a.ell[c] = l;
@@ -2001,11 +2001,11 @@ template <typename T, int N>
 __global__ void __launch_bounds__(kSearchWarps * 32) k_search_half(const SearchArgs a, int h, uint32_t sweep,
                                                                    uint32_t k0, uint32_t k1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   SearchSmem<T, N>& S = reinterpret_cast<SearchSmem<T, N>*>(smem_raw)[wid];
   const int T_ = a.d.n_temps, W = a.d.n_walkers, half = W / 2;
   const int n = a.d.n_bands * T_ * half;
-  for (int e = blockIdx.x * kSearchWarps + wid; e < n; e += gridDim.x * kSearchWarps) {
+  for (int e = blockIdx.x * wpc + wid; e < n; e += gridDim.x * wpc) {
     const int b = e / (T_ * half), r = e % (T_ * half);
     const int t = r / half, k = h * half + r % half;
     const int64_t ck = ((int64_t)b * T_ + t) * W + k;
@@ -2122,31 +2122,25 @@ __global__ void k_search_samples(const SearchArgs a, const double* __restrict__ 
   o[1] = (float)__ddiv_rn(dsub(f0, alo), dsub(ahi, alo));
 }
 
+// launch shapes from prep(): warps per CTA fitted to the per-warp shared memory (float64 at
+// N = 1024 takes 64 KB per warp), grid capped at the resident CTAs
 template <typename T, int N>
 static gbk_status search_launch(SearchArgs& a, int what, uint32_t sweep, uint32_t k0, uint32_t k1, cudaStream_t st) {
-  const size_t sm = kSearchWarps * sizeof(SearchSmem<T, N>);
-  const int per_sm = 6;
+  int grid = 0, thr = 0;
+  size_t sm = 0;
+  gbk_status s;
   if (what == 0) {
-    if (cudaFuncSetAttribute(k_search_eval<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
-      cudaGetLastError();
-      return set_error(GBK_ECUDA, "gb_search_eval: shared memory size");
-    }
-    const int n = a.d.n_bands * a.d.n_temps * a.d.n_walkers;
-    const int cap = sms_of_device() * per_sm;
-    const int grid = (n + kSearchWarps - 1) / kSearchWarps < cap ? (n + kSearchWarps - 1) / kSearchWarps : cap;
-    k_search_eval<T, N><<<grid, kSearchWarps * 32, sm, st>>>(a);
+    if ((s = prep(k_search_eval<T, N>, sizeof(SearchSmem<T, N>), (int64_t)a.d.n_bands * a.d.n_temps * a.d.n_walkers,
+                  &grid, &thr, &sm, kSearchWarps)))
+      return s;
+    k_search_eval<T, N><<<grid, thr, sm, st>>>(a);
     return check_launch("gb_search_eval");
   }
-  if (cudaFuncSetAttribute(k_search_half<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
-    cudaGetLastError();
-    return set_error(GBK_ECUDA, "gb_search_sweep: shared memory size");
-  }
-  const int n = a.d.n_bands * a.d.n_temps * (a.d.n_walkers / 2);
-  const int cap = sms_of_device() * per_sm;
-  const int grid = (n + kSearchWarps - 1) / kSearchWarps < cap ? (n + kSearchWarps - 1) / kSearchWarps : cap;
+  if ((s = prep(k_search_half<T, N>, sizeof(SearchSmem<T, N>),
+                (int64_t)a.d.n_bands * a.d.n_temps * (a.d.n_walkers / 2), &grid, &thr, &sm, kSearchWarps)))
+    return s;
   for (int h = 0; h < 2; ++h) {
-    k_search_half<T, N><<<grid, kSearchWarps * 32, sm, st>>>(a, h, sweep, k0, k1);
-    gbk_status s;
+    k_search_half<T, N><<<grid, thr, sm, st>>>(a, h, sweep, k0, k1);
     if ((s = check_launch("gb_search_sweep(stretch)"))) return s;
   }
   return GBK_OK;
