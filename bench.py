@@ -994,7 +994,7 @@ def main():
     ap.add_argument("--mdn-inmodel", type=float, default=0.1, help="fraction of in-model moves drawn from it")
     ap.add_argument("--search-sweeps", type=int, default=10)
     ap.add_argument("--gmm-keep", type=int, default=10, help="sweeps of cold-chain sources for the mixture refit")
-    ap.add_argument("--search-rj-sweeps", type=int, default=300, help="search-sampler sweeps before sampling")
+    ap.add_argument("--search-rj-sweeps", type=int, default=1000, help="search-sampler sweeps before sampling")
     ap.add_argument("--gmm-iters", type=int, default=50, help="EM iterations of the mixture refit")
     ap.add_argument("--group-frac", type=float, default=0.5, help="fraction of in-model moves that are group stretches "
                                                                    "in the group-stretch ESS run (0: skip it)")
