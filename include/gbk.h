@@ -289,7 +289,9 @@ typedef struct gbk_sweep gbk_sweep;
  * for 16 x 32 x 369 bands x 20 slots at N = 256) and a cache of every band's template
  * sum on its window ([T][W][B][2][3N] complex, 1.2 GB), so that deaths, band openings
  * and tempering swaps reuse waveforms instead of regenerating them. The caches must be
- * refreshed (GBK_SWEEP_REFRESH) whenever params/exists are changed outside gb_sweep. */
+ * refreshed (GBK_SWEEP_REFRESH) whenever params/exists are changed outside gb_sweep; until
+ * the first successful call with GBK_SWEEP_REFRESH they are empty, and gb_sweep without that
+ * flag, gbk_sweep_transfer and gb_sweep_features return GBK_EINVAL. */
 gbk_status gbk_sweep_create(gbk_ctx* ctx, const gbk_sweep_desc* desc, gbk_sweep** out_plan);
 gbk_status gbk_sweep_destroy(gbk_sweep* plan);
 

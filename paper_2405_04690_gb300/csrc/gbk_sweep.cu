@@ -24,6 +24,7 @@ struct gbk_sweep {
   size_t rho_bytes, cache_bytes, hsum_bytes;
   cudaEvent_t ev[2][4][2];  // [parity][refresh, open, band, swap][begin, end] when timing
   bool timed, have_ev;
+  bool refreshed;           // the caches have been filled (a gb_sweep with GBK_SWEEP_REFRESH ran)
   // learned proposal (gbk_sweep_set_proposal)
   bool mdn_set;
   gbk_mdn* net;             // network run on each half sweep's opened windows, or
@@ -1671,6 +1672,8 @@ extern "C" gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists,
     return set_error(GBK_EINVAL, "gb_sweep: unknown flags 0x%x", flags);
   if ((flags & GBK_SWEEP_MDN) && !plan->mdn_set)
     return set_error(GBK_EINVAL, "gb_sweep: GBK_SWEEP_MDN without a proposal (gbk_sweep_set_proposal)");
+  if (!(flags & GBK_SWEEP_REFRESH) && !plan->refreshed)
+    return set_error(GBK_EINVAL, "gb_sweep: the plan's caches are empty (the first call needs GBK_SWEEP_REFRESH)");
   SweepArgs a = make_args(plan, params, exists, betas, residual, psd, key, sweep_index);
   a.trace = trace ? trace->records : nullptr;
   a.trace_cap = trace ? trace->capacity : 0;
@@ -1699,6 +1702,7 @@ extern "C" gbk_status gb_sweep(gbk_sweep* plan, double* params, uint8_t* exists,
   g_active_plan = plan;
   const int fl = flags & ~(GBK_SWEEP_TIMING | GBK_SWEEP_MDN);
   gbk_status s = (plan->d.precision == GBK_MIXED) ? run_sweep<float>(plan, a, fl, st) : run_sweep<double>(plan, a, fl, st);
+  if (s == GBK_OK && (flags & GBK_SWEEP_REFRESH)) plan->refreshed = true;
   g_timing_plan = nullptr;
   g_active_plan = nullptr;
   return s;
@@ -1778,6 +1782,8 @@ extern "C" gbk_status gb_sweep_features(gbk_sweep* plan, const double* params, c
     return set_error(GBK_ENOTIMPL, "gb_sweep_features: features are defined for 256-bin bands (band_bins %d)",
                      plan->d.band_bins);
   if (x_out && ((uintptr_t)x_out & 3)) return set_error(GBK_EINVAL, "gb_sweep_features: x_out must be 4-byte aligned");
+  if (!plan->refreshed)
+    return set_error(GBK_EINVAL, "gb_sweep_features: the plan's caches are empty (run gb_sweep with GBK_SWEEP_REFRESH)");
   SweepArgs a = make_args(plan, const_cast<double*>(params), const_cast<uint8_t*>(exists), nullptr, residual, psd, 0, 0);
   cudaStream_t st = (cudaStream_t)stream;
   return plan->d.precision == GBK_MIXED ? features_impl<float>(plan, a, x_out, u_out, st)
@@ -1857,6 +1863,8 @@ extern "C" gbk_status gbk_sweep_transfer(gbk_sweep* plan, double* params, uint8_
                                          void* stream) {
   if (!plan) return set_error(GBK_EINVAL, "gbk_sweep_transfer: null plan");
   if (!params || !exists) return set_error(GBK_EINVAL, "gbk_sweep_transfer: null device pointer");
+  if (!plan->refreshed)
+    return set_error(GBK_EINVAL, "gbk_sweep_transfer: the plan's caches are empty (run gb_sweep with GBK_SWEEP_REFRESH)");
   SweepArgs a;
   memset(&a, 0, sizeof(a));
   a.c = *plan->ctx;

@@ -462,3 +462,33 @@ def test_ownership_transfer_matches_oracle_and_keeps_the_caches():
     np.testing.assert_allclose(got[ora["exists"]], ora["params"][ora["exists"]], rtol=1e-13, atol=0)
     plan.close()
     ctx.close()
+
+
+def test_unfilled_plan_is_refused_not_run():
+    # before the first refresh the plan's caches are empty: a sweep without GBK_SWEEP_REFRESH, a
+    # transfer and the feature pass return GBK_EINVAL instead of reading them
+    torch = torch_cuda()
+    from paper_2405_04690_gb300 import _lib as L
+    cfg, state, _, _ = small_ensemble(seed=3)
+    dev = torch.device("cuda")
+    ctx = L.Context(cfg.tobs, 15.0, cfg.k0, cfg.n_bins)
+    plan = L.SweepPlan(ctx, cfg.n_temps, cfg.n_walkers, cfg.n_bands, cfg.n_max, NB, cfg.band_k0, cfg.sigma,
+                       L.GBK_MIXED, f_min=cfg.f_min, f_max=cfg.f_max)
+    P = torch.from_numpy(state["params"].copy()).to(dev)
+    E = torch.from_numpy(state["exists"].astype(np.uint8)).to(dev)
+    R = torch.from_numpy(state["resid"].copy()).to(dev)
+    betas = torch.from_numpy(np.ascontiguousarray(cfg.betas)).to(dev)
+    psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
+    RS, PS = L.residual_struct(R, FRAC), L.psd_struct(psdp)
+    with pytest.raises(RuntimeError, match="caches are empty"):
+        L.gb_sweep(plan, P, E, betas, RS, PS, 1, 0, ALL)
+    with pytest.raises(RuntimeError, match="caches are empty"):
+        L.gbk_sweep_transfer(plan, P, E)
+    u = torch.zeros((cfg.n_walkers, cfg.n_bands, cfg.n_max, 8), dtype=torch.float32, device=dev)
+    with pytest.raises(RuntimeError, match="caches are empty"):
+        L.gb_sweep_features(plan, P, E, RS, PS, None, u)
+    L.gb_sweep(plan, P, E, betas, RS, PS, 1, 0, ALL | L.SWEEP_REFRESH)
+    L.gbk_sweep_transfer(plan, P, E)
+    L.gbk_sync_status(ctx)
+    plan.close()
+    ctx.close()
