@@ -110,22 +110,28 @@ def init(cfg, seed):
     return u
 
 
-def evaluate(cfg, rwins, u, fn=None):
-    """l of every walker: [B][T][W]; fn(b, u) replaces the likelihood (tests)."""
+def evaluate(cfg, rwins, u, fn=None, bands=None):
+    """l of every walker: [B][T][W] (only the listed bands when given, zero elsewhere); fn(b, u)
+    replaces the likelihood (tests)."""
     f = fn or (lambda b, x: loglike(cfg, rwins[b], b, x))
-    return np.array([[[f(b, u[b, t, k]) for k in range(cfg.n_walkers)] for t in range(cfg.n_temps)]
-                     for b in range(cfg.n_bands)])
+    out = np.zeros((cfg.n_bands, cfg.n_temps, cfg.n_walkers))
+    for b in (range(cfg.n_bands) if bands is None else bands):
+        for t in range(cfg.n_temps):
+            for k in range(cfg.n_walkers):
+                out[b, t, k] = f(b, u[b, t, k])
+    return out
 
 
-def sweep(cfg, rwins, u, ell, s, fn=None, trace=None):
-    """One search sweep of every band: stretch moves of half 0 then half 1 at every temperature,
-    then tempering swaps. u [B][T][W][8] and ell [B][T][W] are updated in place."""
+def sweep(cfg, rwins, u, ell, s, fn=None, trace=None, bands=None):
+    """One search sweep of every band (or of the listed bands: the bands are independent):
+    stretch moves of half 0 then half 1 at every temperature, then tempering swaps. u
+    [B][T][W][8] and ell [B][T][W] are updated in place."""
     f = fn or (lambda b, x: loglike(cfg, rwins[b], b, x))
     T, W = cfg.n_temps, cfg.n_walkers
     half = W // 2
     if trace is None:
         trace = []
-    for b in range(cfg.n_bands):
+    for b in (range(cfg.n_bands) if bands is None else bands):
         for h in (0, 1):
             for t in range(T):
                 for k in range(h * half, (h + 1) * half):

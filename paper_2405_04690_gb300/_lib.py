@@ -230,14 +230,21 @@ def gb_waveform_batch(ctx, params, n_band, n_band_max, k_start, h_a, h_e, out_of
 
 
 def residual_struct(resid, frac_bits):
-    """gbk_residual for an int64 tensor [W][2][n_bins][2]."""
+    """gbk_residual for an int64 tensor [W][2][n_bins][2]. The struct keeps a reference to the
+    tensor: it holds the tensor's device address, which must stay allocated while the struct
+    (or work queued with it) is in use."""
     _dev(resid, torch.int64, "residual")
-    return GbkResidual(ctypes.c_void_p(resid.data_ptr()), int(resid.shape[0]), int(frac_bits))
+    s = GbkResidual(ctypes.c_void_p(resid.data_ptr()), int(resid.shape[0]), int(frac_bits))
+    s._tensor = resid
+    return s
 
 
 def psd_struct(psd_params):
+    """gbk_psd for a float64 tensor [n_psd][2] (the struct keeps a reference to the tensor)."""
     _dev(psd_params, torch.float64, "psd_params")
-    return GbkPsd(ctypes.c_void_p(psd_params.data_ptr()), int(psd_params.shape[0]))
+    s = GbkPsd(ctypes.c_void_p(psd_params.data_ptr()), int(psd_params.shape[0]))
+    s._tensor = psd_params
+    return s
 
 
 def gb_delta_loglike_batch(ctx, params_new, params_old, n_band, n_band_max, walker, residual, psd, dlogl,

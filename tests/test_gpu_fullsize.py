@@ -11,6 +11,9 @@ the float64 oracle.
    oracle's templates of the injected sources, gives back the injected noise to the float32
    template error (1e-5 of the summed template norms; the mixed waveform's error is ~4e-7 each).
 3. The move statistics add up: every proposal is counted once, acceptances never exceed them.
+
+The refit EM (369 groups, one launch) and the search samplers (369 bands x 4 x 32, one launch
+per half sweep) at the bench's sizes are checked on sampled groups and bands against the oracle.
 """
 import os
 import sys
@@ -100,3 +103,100 @@ def test_full_size_sweep_bookkeeping_and_sampled_windows():
     assert worst < 1e-5, worst
     S["plan"].close()
     S["ctx"].close()
+
+
+def test_full_size_em_fit_sampled_bands():
+    # the bench's refit: 369 groups of 6400 rows (~1700 present points, clusters of sources that
+    # repeat over sweeps and walkers), 16 components, 50 iterations, one launch; 5 sampled groups
+    # against the oracle's EM (FP64 1e-9; mixed: log-likelihood within 1e-3 nats per point)
+    torch = torch_cuda()
+    from oracle import gmm as GM
+    from paper_2405_04690_gb300 import _lib as L
+    g = np.random.default_rng(21)
+    B, P = 369, 6400
+    x = np.full((B, P, 8), np.nan, dtype=np.float32)
+    for b in range(B):
+        k = int(g.integers(3, 9))
+        c = g.uniform(0.1, 0.9, (k, 8))
+        idx = g.choice(P, int(g.integers(1400, 2000)), replace=False)
+        lab = g.integers(0, k, idx.size)
+        x[b, idx] = (c[lab] + 0.003 * g.standard_normal((idx.size, 8))).astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    sample = [0, 97, 180, 250, 368]
+    want = {b: GM.fit(x[b].astype(np.float64), n_iter=50, cap=L.gmm_max_points()) for b in sample}
+    for prec in ("fp64", "mixed"):
+        raw = torch.empty((1, B, 272), dtype=torch.float32, device="cuda")
+        fit = torch.zeros((B, 16, 17), dtype=torch.float64, device="cuda")
+        ll = torch.zeros(B, dtype=torch.float64, device="cuda")
+        L.gmm_fit(xt, raw, n_iter=50, precision=L.PRECISION[prec], fit_out=fit, loglike=ll)
+        fit, ll = fit.cpu().numpy(), ll.cpu().numpy()
+        assert np.isfinite(raw.cpu().numpy()).all()
+        for b in sample:
+            w, mu, var, hist = want[b]
+            n = min(int((~np.isnan(x[b]).any(axis=1)).sum()), L.gmm_max_points())
+            if prec == "fp64":
+                np.testing.assert_allclose(fit[b, :, 0], w, rtol=1e-9, atol=1e-14)
+                np.testing.assert_allclose(fit[b, :, 1:9], mu, rtol=1e-9, atol=1e-12)
+                np.testing.assert_allclose(fit[b, :, 9:], var, rtol=1e-9, atol=1e-15)
+            assert abs(ll[b] - hist[-1]) < (1e-9 * abs(hist[-1]) if prec == "fp64" else 1e-3 * n), (prec, b)
+
+
+def test_full_size_search_sampled_bands():
+    # the bench's search samplers: 369 bands x 4 temperatures x 32 walkers in one launch per
+    # half sweep; three sampled bands (each with an injected source) follow the oracle's FP64
+    # sampler bit for bit over two sweeps (the bands are independent)
+    torch = torch_cuda()
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench as BN
+    from oracle import constants as OC
+    from oracle import psd as OP
+    from oracle import search as SR
+    from paper_2405_04690_gb300 import _lib as L
+    from paper_2405_04690_gb300 import synth
+    nb_, B, T, W = BN.N_BAND, 369, 4, 32
+    band_k0 = int(np.floor(BN.F_LO * BN.TOBS))
+    k0 = band_k0 - 2 * nb_
+    n_bins = (B + 4) * nb_
+    f = (k0 + np.arange(n_bins)) * OC.DF
+    s = OP.psd_ae(f, OC.SQRT_S_OMS, OC.SQRT_S_ACC)
+    g = synth.rng(33)
+    data = synth.unit_complex_normal(g, (2, n_bins)) * np.sqrt(s / (4 * OC.DF))
+    sample = [5, 200, 363]
+    for b in sample:
+        lo = band_k0 + b * nb_
+        th = synth.draw_sources(g, 1, (lo + 20) / OC.TOBS, (lo + nb_ - 20) / OC.TOBS)[:, 0]
+        th[0] = 2e-22
+        ks, a, e = OW.fastslow_band(th, nb_, OC.TOBS)
+        data[0, ks - k0:ks - k0 + nb_] += a
+        data[1, ks - k0:ks - k0 + nb_] += e
+    rfix = OR.to_fixed(data, BN.FRAC_BITS)
+    betas = np.tile([0.5 ** t for t in range(T)], (B, 1))
+    cfg = SR.SearchConfig(tobs=OC.TOBS, k0=k0, n_bins=n_bins, band_k0=band_k0, nb=nb_, n_bands=B, n_temps=T,
+                          n_walkers=W, betas=betas, psd=s, key=(0x77, 0x12))
+    rw = SR.windows(cfg, rfix, BN.FRAC_BITS)
+    u = SR.init(cfg, 2)
+    ell = SR.evaluate(cfg, rw, u, bands=sample)
+    for k in range(2):
+        SR.sweep(cfg, rw, u, ell, k, bands=sample)
+    dev = torch.device("cuda")
+    ctx = L.Context(OC.TOBS, OC.DT, k0, n_bins)
+    plan = L.SearchPlan(ctx, B, nb_, band_k0, T, W, L.GBK_FP64)
+    ug = torch.empty((B, T, W, 8), dtype=torch.float64, device=dev)
+    lg = torch.empty((B, T, W), dtype=torch.float64, device=dev)
+    key = 0x77 | (0x12 << 32)
+    PS = L.psd_struct(torch.tensor([[OC.SQRT_S_OMS, OC.SQRT_S_ACC]], dtype=torch.float64, device=dev))
+    L.gb_search_init(plan, ug, key, 2)
+    L.gb_search_windows(plan, L.residual_struct(torch.from_numpy(rfix[None].copy()).to(dev), BN.FRAC_BITS), 0)
+    L.gb_search_eval(plan, ug, lg, PS)
+    bt = torch.from_numpy(betas).to(dev)
+    for k in range(2):
+        L.gb_search_sweep(plan, ug, lg, bt, PS, key, k)
+    L.gbk_sync_status(ctx)
+    ug, lg = ug.cpu().numpy(), lg.cpu().numpy()
+    for b in sample:
+        assert np.array_equal(ug[b], u[b]), b
+        scale = np.abs(ell[b]).max()
+        assert (np.abs(lg[b] - ell[b]) <= 1e-8 * scale).all(), b
+    plan.close()
+    ctx.close()
