@@ -447,9 +447,10 @@ def run_gmm_fit(torch, L, units, n_walkers, args, stream):
 
 def run_search_rj(torch, L, S, ens, data, args, stream):
     """Search-RJ mixtures (Sec. V.E, App. G): every band's search sampler (4 temperatures x 32
-    walkers, own-bin f0 prior) runs on walker 0's residual; bands whose best point reaches
-    SNR 7 give their cold walkers of the last sweeps to one EM fit per band; returns the
-    sweep table [W][n_bands][272] and the timings."""
+    walkers, own-bin f0 prior) runs on walker 0's residual, relaunched halfway from a ball around
+    each band's best point; bands whose best point reaches SNR 7 give their cold walkers of the
+    last sweeps to one EM fit per band; returns the sweep table [W][n_bands][272] and the
+    timings."""
     dev = data.device
     nb, T_s, W_s = ens["n_bands"], 4, 32
     plan = L.SearchPlan(S["ctx"], nb, N_BAND, ens["band_k0"], T_s, W_s, L.GBK_MIXED)
@@ -470,6 +471,9 @@ def run_search_rj(torch, L, S, ens, data, args, stream):
     L.gb_search_windows(plan, L.residual_struct(data, FRAC_BITS), 0, stream)
     L.gb_search_eval(plan, u, ell, S["psd"], 0, stream)
     for k in range(n_run):
+        if k == n_run // 2:   # relaunch every band's ensemble from a ball around its best point (App. G)
+            L.gb_search_ball(plan, u, be, bu, 0.002, key, 2, stream)
+            L.gb_search_eval(plan, u, ell, S["psd"], 0, stream)
         L.gb_search_sweep(plan, u, ell, betas, S["psd"], key, k, best=(be, bu, stall), stats=st, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -485,7 +489,8 @@ def run_search_rj(torch, L, S, ens, data, args, stream):
     snr = torch.sqrt(2.0 * torch.clamp(be, min=0.0)).cpu().numpy()
     s = st.cpu().numpy()
     plan.close()
-    out = {"bands": nb, "temps": T_s, "walkers": W_s, "sweeps": n_run, "sample_sweeps": n_keep,
+    out = {"bands": nb, "temps": T_s, "walkers": W_s, "sweeps": n_run, "ball_relaunch_at": n_run // 2,
+           "ball_sigma": 0.002, "sample_sweeps": n_keep,
            "ms_per_sweep": ms_run / n_run,
            "proposals_per_s": float(s[0, 0]) / (ms_run * 1e-3),
            "stretch_acceptance": float(s[0, 1]) / max(1.0, float(s[0, 0])),

@@ -537,6 +537,13 @@ gbk_status gb_search_eval(gbk_search* plan, const double* u, double* ell, const 
 gbk_status gb_search_sweep(gbk_search* plan, double* u, double* ell, const double* betas, const gbk_psd* psd,
                            int32_t psd_walker, uint64_t key, uint32_t sweep_index, double* best_ell, double* best_u,
                            int32_t* stall, int64_t* stats, void* stream);
+/* Relaunch around the best points (App. G: a new ball of points around the maximum-likelihood
+ * point, then the same search again): every chain of a band whose best_ell is finite becomes
+ * clip(best_u + sigma z, 0, 1) with z standard normal (Box-Muller on Philox words at counters
+ * (chain, m, 10, seed), m = 0, 1); other bands keep their walkers. Follow with gb_search_eval.
+ *   u [n_bands][n_temps][n_walkers][8] (device, updated); best_ell [n_bands], best_u [n_bands][8] */
+gbk_status gb_search_ball(gbk_search* plan, double* u, const double* best_ell, const double* best_u, double sigma,
+                          uint64_t key, uint32_t seed, void* stream);
 /* Training points of the search-RJ mixtures from the current state: for every band b the cold
  * walkers' u in the sweep's unit coordinates (the learned proposal's: f0 over the band's
  * allowance, own bins +- half a band clipped to [f_min, f_max]; the other coordinates

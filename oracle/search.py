@@ -110,6 +110,28 @@ def init(cfg, seed):
     return u
 
 
+def ball(cfg, u, best_ell, best_u, sigma, seed):
+    """Relaunch around the best points (App. G: a new ball of points around the maximum-likelihood
+    point, the search then run again): every walker of a band with a best point becomes
+    clip(best + sigma z, 0, 1), z standard normal by Box-Muller on Philox words at counters
+    (chain, m, 10, seed), m = 0, 1: z_{2i}, z_{2i+1} = sqrt(-2 ln u_a) (cos, sin)(2 pi u_b) from
+    the word pair (2i, 2i+1) of the 8 words. Bands without a best point (best_ell = -inf) keep
+    their walkers. u [B][T][W][8] is updated in place."""
+    for b in range(cfg.n_bands):
+        if not np.isfinite(best_ell[b]):
+            continue
+        for t in range(cfg.n_temps):
+            for k in range(cfg.n_walkers):
+                c = _ctr(cfg, b, t, k)
+                w = list(PX.philox4x32_10((c, 0, 10, seed), cfg.key)) + list(PX.philox4x32_10((c, 1, 10, seed), cfg.key))
+                z = np.empty(D)
+                for i in range(D // 2):
+                    r = math.sqrt(-2.0 * math.log(PX.u32(w[2 * i])))
+                    a = 2.0 * math.pi * PX.u32(w[2 * i + 1])
+                    z[2 * i], z[2 * i + 1] = r * math.cos(a), r * math.sin(a)
+                u[b, t, k] = np.clip(best_u[b] + sigma * z, 0.0, 1.0)
+
+
 def evaluate(cfg, rwins, u, fn=None, bands=None):
     """l of every walker: [B][T][W] (only the listed bands when given, zero elsewhere); fn(b, u)
     replaces the likelihood (tests)."""

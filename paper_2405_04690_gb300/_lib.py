@@ -132,6 +132,7 @@ SIGNATURES = {
                                        ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp]),
     "gb_search_samples": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp, _i32,
                                          _i32, _vp]),
+    "gb_search_ball": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32, _vp]),
     "gbk_sweep_adapt_temps": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_double, ctypes.c_double, _vp]),
     "gbk_sweep_transfer": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "gbk_sweep_update_group": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _i32, _vp]),
@@ -599,3 +600,10 @@ def gb_search_samples(plan, u, best_ell, snr_min, f_min, f_max, x, row0, stream=
     _check(lib().gb_search_samples(plan.handle, _dev(u, torch.float64, "u"), _dev(best_ell, torch.float64, "best_ell"),
                                    float(snr_min), float(f_min), float(f_max), _dev(x, torch.float32, "x"),
                                    int(x.shape[1]), int(row0), _stream(stream)), "gb_search_samples")
+
+
+def gb_search_ball(plan, u, best_ell, best_u, sigma, key, seed, stream=None):
+    """Walkers of bands with a best point redrawn around it (clipped normal of width sigma)."""
+    _check(lib().gb_search_ball(plan.handle, _dev(u, torch.float64, "u"), _dev(best_ell, torch.float64, "best_ell"),
+                                _dev(best_u, torch.float64, "best_u"), float(sigma), ctypes.c_uint64(int(key)),
+                                ctypes.c_uint32(int(seed)), _stream(stream)), "gb_search_ball")

@@ -2102,6 +2102,33 @@ __global__ void k_search_best(const SearchArgs a, double* best_ell, double* best
   }
 }
 
+// Relaunch around the best points: every chain of a band with a best point becomes
+// clip(best + sigma z, 0, 1), z standard normal by Box-Muller on the Philox words of counters
+// (chain, m, 10, seed), m = 0, 1 (word pairs (2i, 2i + 1) -> z_2i, z_2i+1). One thread per chain.
+__global__ void k_search_ball(double* __restrict__ u, const double* __restrict__ best_ell,
+                              const double* __restrict__ best_u, int n_bands, int per_band, double sigma,
+                              uint32_t seed, uint32_t k0, uint32_t k1) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_bands * per_band) return;
+  const int b = c / per_band;
+  if (!(best_ell[b] > -INFINITY)) return;
+  uint32_t w[8];
+  for (int m = 0; m < 2; ++m) {
+    const U4 v = philox4x32_10((uint32_t)c, (uint32_t)m, 10u, seed, k0, k1);
+    w[4 * m] = v.x; w[4 * m + 1] = v.y; w[4 * m + 2] = v.z; w[4 * m + 3] = v.w;
+  }
+  for (int i = 0; i < 4; ++i) {
+    const double r = sqrt(-2.0 * log(u32(w[2 * i])));
+    const double an = 2.0 * 3.141592653589793 * u32(w[2 * i + 1]);
+    const double z[2] = {dmul(r, cos(an)), dmul(r, sin(an))};
+    for (int j = 0; j < 2; ++j) {
+      const int d = 2 * i + j;
+      const double x = dadd(best_u[(int64_t)b * 8 + d], dmul(sigma, z[j]));
+      u[(int64_t)c * 8 + d] = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
+    }
+  }
+}
+
 // Training points of the search-RJ mixtures: the cold walkers of every band in the sampler's
 // unit coordinates (f0 over the band's allowance, clipped to [f_min, f_max]), NaN rows for a
 // band whose best point has sqrt(2 l_best) < snr_min. One thread per (band, walker).
@@ -2304,4 +2331,15 @@ extern "C" gbk_status gb_search_samples(gbk_search* p, const double* u, const do
   k_search_samples<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(a, best_ell, snr_min, f_min, f_max, x, n_rows,
                                                                        row0);
   return check_launch("gb_search_samples");
+}
+
+extern "C" gbk_status gb_search_ball(gbk_search* p, double* u, const double* best_ell, const double* best_u,
+                                     double sigma, uint64_t key, uint32_t seed, void* stream) {
+  if (!p || !u || !best_ell || !best_u) return set_error(GBK_EINVAL, "gb_search_ball: null argument");
+  if (!(sigma > 0.0)) return set_error(GBK_EINVAL, "gb_search_ball: sigma must be > 0");
+  const int per = p->d.n_temps * p->d.n_walkers;
+  const int n = p->d.n_bands * per;
+  k_search_ball<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(u, best_ell, best_u, p->d.n_bands, per, sigma, seed,
+                                                                  (uint32_t)(key & 0xffffffffu), (uint32_t)(key >> 32));
+  return check_launch("gb_search_ball");
 }

@@ -107,3 +107,59 @@ def test_search_mixed_likelihoods():
     u0, l0, *_ = _gpu(torch, scfg, dfix, L.GBK_MIXED, 0)
     want = SR.evaluate(scfg, rw, u0)
     assert (np.abs(l0 - want) <= 1e-2 + 1e-6 * np.abs(want)).all(), np.abs(l0 - want).max()
+
+
+def test_search_ball_relaunch_matches_oracle():
+    # three sweeps with best points, a relaunch around them (sigma 0.01), the likelihood pass and
+    # two more sweeps: walkers within 1e-12 of the oracle's (the Box-Muller logs and cosines may
+    # differ in the last bit), likelihoods to 1e-8, the same accepted counts
+    torch = torch_cuda()
+    from paper_2405_04690_gb300 import _lib as L
+    from paper_2405_04690_gb300 import synth
+    scfg, dfix = _setup()
+    rw = SR.windows(scfg, dfix, FRAC)
+    u = SR.init(scfg, SEED)
+    ell = SR.evaluate(scfg, rw, u)
+    best, bu, stall = np.full(3, -np.inf), np.zeros((3, 8)), np.zeros(3, dtype=np.int64)
+    for k in range(3):
+        SR.sweep(scfg, rw, u, ell, k)
+        SR.best_update(u, ell, best, bu, stall)
+    SR.ball(scfg, u, best, bu, 0.01, 5)
+    u_ball = u.copy()
+    ell = SR.evaluate(scfg, rw, u)
+    trace = []
+    for k in range(3, 5):
+        SR.sweep(scfg, rw, u, ell, k, trace=trace)
+    dev = torch.device("cuda")
+    ctx = L.Context(scfg.tobs, 15.0, scfg.k0, scfg.n_bins)
+    plan = L.SearchPlan(ctx, scfg.n_bands, NB, scfg.band_k0, scfg.n_temps, scfg.n_walkers, L.GBK_FP64)
+    R = torch.from_numpy(dfix[None].copy()).to(dev).contiguous()
+    psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
+    PS = L.psd_struct(psdp)
+    ug = torch.empty((scfg.n_bands, scfg.n_temps, scfg.n_walkers, 8), dtype=torch.float64, device=dev)
+    lg = torch.empty((scfg.n_bands, scfg.n_temps, scfg.n_walkers), dtype=torch.float64, device=dev)
+    key = KEY[0] | (KEY[1] << 32)
+    L.gb_search_init(plan, ug, key, SEED)
+    L.gb_search_windows(plan, L.residual_struct(R, FRAC), 0)
+    L.gb_search_eval(plan, ug, lg, PS)
+    betas = torch.from_numpy(np.ascontiguousarray(scfg.betas)).to(dev)
+    be = torch.full((scfg.n_bands,), -np.inf, dtype=torch.float64, device=dev)
+    bg = torch.zeros((scfg.n_bands, 8), dtype=torch.float64, device=dev)
+    sg = torch.zeros(scfg.n_bands, dtype=torch.int32, device=dev)
+    for k in range(3):
+        L.gb_search_sweep(plan, ug, lg, betas, PS, key, k, best=(be, bg, sg))
+    L.gb_search_ball(plan, ug, be, bg, 0.01, key, 5)
+    ub = ug.cpu().numpy()
+    L.gb_search_eval(plan, ug, lg, PS)
+    stats = torch.zeros((2, 2), dtype=torch.int64, device=dev)
+    for k in range(3, 5):
+        L.gb_search_sweep(plan, ug, lg, betas, PS, key, k, stats=stats)
+    L.gbk_sync_status(ctx)
+    assert np.abs(ub - u_ball).max() < 1e-12
+    assert np.abs(ug.cpu().numpy() - u).max() < 1e-12
+    scale = np.abs(ell).max(axis=(1, 2))[:, None, None]
+    assert (np.abs(lg.cpu().numpy() - ell) <= 1e-8 * scale).all()
+    n_acc = sum(1 for r in trace if r["kind"] == 7 and r["accepted"])
+    assert int(stats[0, 1].item()) == n_acc and n_acc > 0
+    plan.close()
+    ctx.close()

@@ -128,3 +128,20 @@ def test_search_points_map_to_the_sampler_coordinates():
     uu = g.uniform(0, 1, (3, 2, 16, 8))
     x = SR.samples(cfg, uu, np.array([50.0, 10.0, -1.0]), 7.0, 1e-4, 1e-2)
     assert np.isfinite(x[0]).all() and np.isnan(x[1]).all() and np.isnan(x[2]).all()
+
+
+def test_ball_relaunch_is_a_clipped_normal_around_the_best_point():
+    # every walker of a band with a best point: best + sigma z, z ~ N(0, 1) per coordinate
+    # (Box-Muller on the Philox words), clipped to the box; bands without one are untouched
+    from scipy import stats
+    cfg = _cfg(n_bands=3, n_temps=4, n_walkers=32)
+    u = SR.init(cfg, 1)
+    keep = u.copy()
+    best = np.array([1.0, -np.inf, 2.0])
+    bu = np.array([[0.5] * 8, [0.1] * 8, [0.02] + [0.5] * 7])
+    SR.ball(cfg, u, best, bu, 0.01, 3)
+    assert np.array_equal(u[1], keep[1])
+    z = (u[0] - 0.5) / 0.01
+    assert stats.kstest(z.ravel(), "norm").pvalue > 1e-3
+    assert abs(z.mean()) < 0.1 and abs(z.std() - 1) < 0.1
+    assert (u[2, ..., 0] >= 0).all() and (u[2, ..., 0] == 0).any()     # clipped at the box edge
