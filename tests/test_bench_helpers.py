@@ -24,3 +24,29 @@ def test_autocorrelation_time_of_ar1_chains():
         want = (1 + phi) / (1 - phi)
         got = BN.autocorr_time(x)
         assert abs(got / want - 1) < 0.1, (phi, got, want)
+
+
+def test_clock_sampler_reads_median_and_throttle_reasons(tmp_path):
+    # nvidia-smi CSV rows (index, sm, max sm, power, active mask, hw, hw thermal, sw thermal,
+    # sw power cap): the median SM clock of GPU 0 and every reason seen active
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench as BN
+
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    p = tmp_path / "clocks.csv"
+    p.write_text("0, 2070, 2070, 900, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                 "1, 1000, 2070, 500, 0x0, Active, Not Active, Not Active, Not Active\n"
+                 "0, 1980, 2070, 1400, 0x4, Not Active, Not Active, Not Active, Active\n"
+                 "0, 2070, 2070, 1300, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    cs = BN.ClockSampler()
+    cs.proc, cs.path = _Proc(), str(p)
+    out = cs.stop(0)
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
