@@ -594,7 +594,7 @@ def run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, sn
     # the paper's search-RJ proposal: per-band search samplers on walker 0's data residual, then
     # mixtures fitted to their cold walkers around the best points of bands with SNR >= 7
     srj_raw, search["search_rj_sampler"] = run_search_rj(torch, L, S, ens, data, args, stream)
-    for mode in ("prior", "learned", "gmm_refit", "search_rj"):
+    for mode in ("prior", "learned", "gmm_refit", "search_rj", "search_rj_rerun"):
         if mode == "gmm_refit" and gmm_raw is None:
             continue
         S["P"].zero_()
@@ -604,7 +604,7 @@ def run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, sn
             L.gbk_sweep_set_proposal(S["plan"], net=net, eps=args.mdn_eps, inmodel_frac=args.mdn_inmodel)
         elif mode == "gmm_refit":
             L.gbk_sweep_set_proposal(S["plan"], raw_table=gmm_raw, eps=args.mdn_eps, inmodel_frac=args.mdn_inmodel)
-        elif mode == "search_rj":
+        elif mode in ("search_rj", "search_rj_rerun"):
             L.gbk_sweep_set_proposal(S["plan"], raw_table=srj_raw, eps=args.mdn_eps, inmodel_frac=args.mdn_inmodel)
         else:
             L.gbk_sweep_set_proposal(S["plan"])
@@ -622,9 +622,17 @@ def run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, sn
             if k in (0, 1, 2, 4, args.search_sweeps - 1):
                 curve.append([k + 1, recovered_sources(ens["truth"], S["P"].cpu().numpy(), S["E"].cpu().numpy(),
                                                        TOBS, ens["n_bands"], ens["band_k0"])])
+            if mode == "search_rj_rerun" and k % 2 == 1 and k + 1 < args.search_sweeps:
+                # the paper's continuous search: rerun on the current best-fit residual (walker 0), so
+                # each band's search moves on to the loudest source not yet in the model
+                srj_raw2, _ = run_search_rj(torch, L, S, ens, S["resid"], args, stream)
+                L.gbk_sweep_set_proposal(S["plan"], raw_table=srj_raw2, eps=args.mdn_eps,
+                                         inmodel_frac=args.mdn_inmodel)
         st = stats.cpu().numpy()
         search[mode] = {"recovered_after_sweeps": curve, "seconds": t,
                         "birth_acceptance": float(st[1, 1]) / max(1.0, float(st[1, 0]))}
+        if mode == "search_rj_rerun":
+            search[mode]["reruns"] = "search rerun on walker 0's residual after every second sweep (not in seconds)"
     search["injected"] = int(ens["truth"].shape[1]) * min(4, N_W)
     search["counted"] = "cold chains of walkers 0-3: injected sources matched within 1 bin in f0 and 0.3 in ln A"
     out["search"] = search
