@@ -1904,13 +1904,14 @@ struct SearchArgs {
   long long* stats;    // [2][2]: stretch proposals, accepted; swaps, accepted
 };
 
+// per warp: the FFT buffers and the set-up of a batch of 32 chains (one lane each)
 template <typename T, int N>
 struct SearchSmem {
   typename CT<T>::C ba[2 * N], bs[2 * N];
-  Src<T> src;
-  double y[8];
-  double lz;
-  int inb;
+  Src<T> src[32];
+  double y[32][8];
+  double lz[32];
+  int inb[32];
 };
 
 // Source parameters of unit coordinates u in band b's own-bin box (f0 over [lo_b, hi_b)),
@@ -1936,19 +1937,22 @@ __device__ __forceinline__ const typename CT<T>::C* search_window(const SearchAr
   return reinterpret_cast<const typename CT<T>::C*>(a.sa.rho) + (int64_t)b * 2 * 3 * N;
 }
 
-// l(u) = <R|h> - 1/2 <h|h> on band b's window (the birth Delta lnL, Eq. addsource); whole warp.
+// Set-up of one source (one lane): parameters of u in band b's box and the waveform constants.
 template <typename T, int N>
-__device__ double search_ell(const SearchArgs& a, SearchSmem<T, N>& S, int b, const double* u, int lane) {
-  if (lane == 0) {
-    double th[8];
-    search_from_unit(a.d, a.sa.c.grid.tobs, b, u, th);
-    S.src = make_src<T>(th, 1, 0, a.sa.c.grid.tobs, N);
-  }
-  __syncwarp();
-  gen_band<T, N>(&S.src, orb_of<T>(a.sa.c, band_index(N)), tw_of<T>(a.sa.c, band_index(N)), a.sa.c.grid.tobs, S.ba,
-                 S.bs, lane);
+__device__ __forceinline__ void search_prep(const SearchArgs& a, SearchSmem<T, N>& S, int q, int b, const double* u) {
+  double th[8];
+  search_from_unit(a.d, a.sa.c.grid.tobs, b, u, th);
+  S.src[q] = make_src<T>(th, 1, 0, a.sa.c.grid.tobs, N);
+}
+
+// l = <R|h> - 1/2 <h|h> on band b's window for the prepared source q (the birth Delta lnL,
+// Eq. addsource); whole warp.
+template <typename T, int N>
+__device__ double search_ell(const SearchArgs& a, SearchSmem<T, N>& S, int q, int b, int lane) {
+  gen_band<T, N>(&S.src[q], orb_of<T>(a.sa.c, band_index(N)), tw_of<T>(a.sa.c, band_index(N)), a.sa.c.grid.tobs,
+                 S.ba, S.bs, lane);
   const int64_t gw = a.d.band_k0 + (int64_t)(b - 1) * N - a.sa.c.grid.k0;
-  const int oa = band_off<N>(S.src.q, gw, a.sa.c);
+  const int oa = band_off<N>(S.src[q].q, gw, a.sa.c);
   const PsdWt<T> pw = walker_psd<T>(a.sa, a.psd_walker);
   const double l = window_dll<T, N>(a.sa, search_window<T, N>(a, b), S.ba, oa, (const typename CT<T>::C*)nullptr, 0,
                                     gw, pw, lane);
@@ -1995,14 +1999,21 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_eval(const SearchA
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   SearchSmem<T, N>& S = reinterpret_cast<SearchSmem<T, N>*>(smem_raw)[wid];
   const int n = a.d.n_bands * a.d.n_temps * a.d.n_walkers;
-  for (int c = blockIdx.x * wpc + wid; c < n; c += gridDim.x * wpc) {
-    const int b = c / (a.d.n_temps * a.d.n_walkers);
-    const double l = search_ell<T, N>(a, S, b, a.u + (int64_t)c * 8, lane);
-    if (lane == 0) a.ell[c] = l;
+  const int per = a.d.n_temps * a.d.n_walkers;
+  // batches of 32 chains per warp: the float64 set-up lane-parallel, then one waveform at a time
+  for (int g0 = (blockIdx.x * wpc + wid) * 32; g0 < n; g0 += gridDim.x * wpc * 32) {
+    const int cnt = min(32, n - g0);
+    if (lane < cnt) search_prep<T, N>(a, S, lane, (g0 + lane) / per, a.u + (int64_t)(g0 + lane) * 8);
+    __syncwarp();
+    for (int q = 0; q < cnt; ++q) {
+      const double l = search_ell<T, N>(a, S, q, (g0 + q) / per, lane);
+      if (lane == 0) a.ell[g0 + q] = l;
+    }
+    __syncwarp();
   }
 }
 
-// Stretch moves of half h (one warp per chain of the half): partner from the other half, z
+// Stretch moves of half h (one warp per batch of 32 chains of the half): partner from the other half, z
 // from g(z) ~ 1/sqrt(z) on [1/a, a], Y = X_j + z (X_k - X_j) in the unit box, acceptance
 // ln u < beta (l_Y - l_X) + 7 ln z; a Y outside [0, 1]^8 is rejected without a likelihood.
 template <typename T, int N>
@@ -2013,12 +2024,16 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_half(const SearchA
   SearchSmem<T, N>& S = reinterpret_cast<SearchSmem<T, N>*>(smem_raw)[wid];
   const int T_ = a.d.n_temps, W = a.d.n_walkers, half = W / 2;
   const int n = a.d.n_bands * T_ * half;
-  for (int e = blockIdx.x * wpc + wid; e < n; e += gridDim.x * wpc) {
-    const int b = e / (T_ * half), r = e % (T_ * half);
-    const int t = r / half, k = h * half + r % half;
-    const int64_t ck = ((int64_t)b * T_ + t) * W + k;
-    const U4 wv = philox4x32_10((uint32_t)ck, (uint32_t)h, 7u, sweep, k0, k1);
-    if (lane == 0) {
+  // batches of 32 chains of the half per warp: words, partner, z, Y, box test and the float64
+  // source set-up lane-parallel, then the waveforms and decisions one chain at a time
+  for (int g0 = (blockIdx.x * wpc + wid) * 32; g0 < n; g0 += gridDim.x * wpc * 32) {
+    const int cnt = min(32, n - g0);
+    if (lane < cnt) {
+      const int e = g0 + lane;
+      const int b = e / (T_ * half), r = e % (T_ * half);
+      const int t = r / half, k = h * half + r % half;
+      const int64_t ck = ((int64_t)b * T_ + t) * W + k;
+      const U4 wv = philox4x32_10((uint32_t)ck, (uint32_t)h, 7u, sweep, k0, k1);
       const int j = (1 - h) * half + (int)ranged(wv.x, (uint32_t)half);
       const double zz = dadd(dmul(dsub(a.d.stretch_a, 1.0), u32(wv.y)), 1.0);
       const double z = __ddiv_rn(dmul(zz, zz), a.d.stretch_a);
@@ -2027,26 +2042,36 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_half(const SearchA
       int inb = 1;
       for (int c = 0; c < 8; ++c) {
         const double y = dadd(xj[c], dmul(z, dsub(xk[c], xj[c])));
-        S.y[c] = y;
+        S.y[lane][c] = y;
         if (!(y >= 0.0 && y <= 1.0)) inb = 0;
       }
-      S.inb = inb;
-      S.lz = log(z);
+      S.inb[lane] = inb;
+      S.lz[lane] = log(z);
+      if (inb) search_prep<T, N>(a, S, lane, b, S.y[lane]);
     }
     __syncwarp();
-    bool acc = false;
-    if (S.inb) {
-      const double ly = search_ell<T, N>(a, S, b, S.y, lane);
+    int n_acc = 0;
+    for (int q = 0; q < cnt; ++q) {
+      const int e = g0 + q;
+      const int b = e / (T_ * half), r = e % (T_ * half);
+      const int t = r / half, k = h * half + r % half;
+      const int64_t ck = ((int64_t)b * T_ + t) * W + k;
+      if (!S.inb[q]) continue;
+      const double ly = search_ell<T, N>(a, S, q, b, lane);
+      const U4 wv = philox4x32_10((uint32_t)ck, (uint32_t)h, 7u, sweep, k0, k1);
       const double ul = u53(wv.z, wv.w);
       const double lu = ul > 0.0 ? log(ul) : -INFINITY;
-      const double la = a.betas[(int64_t)b * T_ + t] * (ly - a.ell[ck]) + 7.0 * S.lz;
-      acc = __shfl_sync(0xffffffffu, (int)(lu < la), 0) != 0;
-      if (acc && lane == 0) a.ell[ck] = ly;
-      if (acc && lane < 8) a.u[ck * 8 + lane] = S.y[lane];
+      const double la = a.betas[(int64_t)b * T_ + t] * (ly - a.ell[ck]) + 7.0 * S.lz[q];
+      const bool acc = __shfl_sync(0xffffffffu, (int)(lu < la), 0) != 0;
+      if (acc) {
+        if (lane == 0) a.ell[ck] = ly;
+        if (lane < 8) a.u[ck * 8 + lane] = S.y[q][lane];
+        ++n_acc;
+      }
     }
     if (lane == 0 && a.stats) {
-      atomicAdd((unsigned long long*)&a.stats[0], 1ull);
-      if (acc) atomicAdd((unsigned long long*)&a.stats[1], 1ull);
+      atomicAdd((unsigned long long*)&a.stats[0], (unsigned long long)cnt);
+      if (n_acc) atomicAdd((unsigned long long*)&a.stats[1], (unsigned long long)n_acc);
     }
     __syncwarp();
   }
@@ -2165,14 +2190,15 @@ static gbk_status search_launch(SearchArgs& a, int what, uint32_t sweep, uint32_
   size_t sm = 0;
   gbk_status s;
   if (what == 0) {
-    if ((s = prep(k_search_eval<T, N>, sizeof(SearchSmem<T, N>), (int64_t)a.d.n_bands * a.d.n_temps * a.d.n_walkers,
-                  &grid, &thr, &sm, kSearchWarps)))
+    // one warp per batch of 32 chains
+    if ((s = prep(k_search_eval<T, N>, sizeof(SearchSmem<T, N>),
+                  ((int64_t)a.d.n_bands * a.d.n_temps * a.d.n_walkers + 31) / 32, &grid, &thr, &sm, kSearchWarps)))
       return s;
     k_search_eval<T, N><<<grid, thr, sm, st>>>(a);
     return check_launch("gb_search_eval");
   }
   if ((s = prep(k_search_half<T, N>, sizeof(SearchSmem<T, N>),
-                (int64_t)a.d.n_bands * a.d.n_temps * (a.d.n_walkers / 2), &grid, &thr, &sm, kSearchWarps)))
+                ((int64_t)a.d.n_bands * a.d.n_temps * (a.d.n_walkers / 2) + 31) / 32, &grid, &thr, &sm, kSearchWarps)))
     return s;
   for (int h = 0; h < 2; ++h) {
     k_search_half<T, N><<<grid, thr, sm, st>>>(a, h, sweep, k0, k1);
