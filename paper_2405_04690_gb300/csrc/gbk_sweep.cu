@@ -1994,15 +1994,15 @@ __global__ void k_search_init(double* u, int n, uint32_t seed, uint32_t k0, uint
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kSearchWarps * 32) k_search_eval(const SearchArgs a) {
+__global__ void __launch_bounds__(kSearchWarps * 32) k_search_eval(const SearchArgs a, int bs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   SearchSmem<T, N>& S = reinterpret_cast<SearchSmem<T, N>*>(smem_raw)[wid];
   const int n = a.d.n_bands * a.d.n_temps * a.d.n_walkers;
   const int per = a.d.n_temps * a.d.n_walkers;
-  // batches of 32 chains per warp: the float64 set-up lane-parallel, then one waveform at a time
-  for (int g0 = (blockIdx.x * wpc + wid) * 32; g0 < n; g0 += gridDim.x * wpc * 32) {
-    const int cnt = min(32, n - g0);
+  // batches of bs <= 32 chains per warp: the float64 set-up lane-parallel, then one waveform at a time
+  for (int g0 = (blockIdx.x * wpc + wid) * bs; g0 < n; g0 += gridDim.x * wpc * bs) {
+    const int cnt = min(bs, n - g0);
     if (lane < cnt) search_prep<T, N>(a, S, lane, (g0 + lane) / per, a.u + (int64_t)(g0 + lane) * 8);
     __syncwarp();
     for (int q = 0; q < cnt; ++q) {
@@ -2018,16 +2018,16 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_eval(const SearchA
 // ln u < beta (l_Y - l_X) + 7 ln z; a Y outside [0, 1]^8 is rejected without a likelihood.
 template <typename T, int N>
 __global__ void __launch_bounds__(kSearchWarps * 32) k_search_half(const SearchArgs a, int h, uint32_t sweep,
-                                                                   uint32_t k0, uint32_t k1) {
+                                                                   uint32_t k0, uint32_t k1, int bs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   SearchSmem<T, N>& S = reinterpret_cast<SearchSmem<T, N>*>(smem_raw)[wid];
   const int T_ = a.d.n_temps, W = a.d.n_walkers, half = W / 2;
   const int n = a.d.n_bands * T_ * half;
-  // batches of 32 chains of the half per warp: words, partner, z, Y, box test and the float64
-  // source set-up lane-parallel, then the waveforms and decisions one chain at a time
-  for (int g0 = (blockIdx.x * wpc + wid) * 32; g0 < n; g0 += gridDim.x * wpc * 32) {
-    const int cnt = min(32, n - g0);
+  // batches of bs <= 32 chains of the half per warp: words, partner, z, Y, box test and the
+  // float64 source set-up lane-parallel, then the waveforms and decisions one chain at a time
+  for (int g0 = (blockIdx.x * wpc + wid) * bs; g0 < n; g0 += gridDim.x * wpc * bs) {
+    const int cnt = min(bs, n - g0);
     if (lane < cnt) {
       const int e = g0 + lane;
       const int b = e / (T_ * half), r = e % (T_ * half);
@@ -2182,6 +2182,12 @@ __global__ void k_search_samples(const SearchArgs a, const double* __restrict__ 
   o[1] = (float)__ddiv_rn(dsub(f0, alo), dsub(ahi, alo));
 }
 
+// chains per warp batch: enough warps for ~12 per SM, at most 32 (one lane each), at least 4
+static int search_batch(int64_t n) {
+  const int64_t per = n / ((int64_t)sms_of_device() * 12);
+  return per < 4 ? 4 : (per > 32 ? 32 : (int)per);
+}
+
 // launch shapes from prep(): warps per CTA fitted to the per-warp shared memory (float64 at
 // N = 1024 takes 64 KB per warp), grid capped at the resident CTAs
 template <typename T, int N>
@@ -2190,18 +2196,19 @@ static gbk_status search_launch(SearchArgs& a, int what, uint32_t sweep, uint32_
   size_t sm = 0;
   gbk_status s;
   if (what == 0) {
-    // one warp per batch of 32 chains
-    if ((s = prep(k_search_eval<T, N>, sizeof(SearchSmem<T, N>),
-                  ((int64_t)a.d.n_bands * a.d.n_temps * a.d.n_walkers + 31) / 32, &grid, &thr, &sm, kSearchWarps)))
+    const int64_t n = (int64_t)a.d.n_bands * a.d.n_temps * a.d.n_walkers;
+    const int bs = search_batch(n);
+    if ((s = prep(k_search_eval<T, N>, sizeof(SearchSmem<T, N>), (n + bs - 1) / bs, &grid, &thr, &sm, kSearchWarps)))
       return s;
-    k_search_eval<T, N><<<grid, thr, sm, st>>>(a);
+    k_search_eval<T, N><<<grid, thr, sm, st>>>(a, bs);
     return check_launch("gb_search_eval");
   }
-  if ((s = prep(k_search_half<T, N>, sizeof(SearchSmem<T, N>),
-                ((int64_t)a.d.n_bands * a.d.n_temps * (a.d.n_walkers / 2) + 31) / 32, &grid, &thr, &sm, kSearchWarps)))
+  const int64_t n = (int64_t)a.d.n_bands * a.d.n_temps * (a.d.n_walkers / 2);
+  const int bs = search_batch(n);
+  if ((s = prep(k_search_half<T, N>, sizeof(SearchSmem<T, N>), (n + bs - 1) / bs, &grid, &thr, &sm, kSearchWarps)))
     return s;
   for (int h = 0; h < 2; ++h) {
-    k_search_half<T, N><<<grid, thr, sm, st>>>(a, h, sweep, k0, k1);
+    k_search_half<T, N><<<grid, thr, sm, st>>>(a, h, sweep, k0, k1, bs);
     if ((s = check_launch("gb_search_sweep(stretch)"))) return s;
   }
   return GBK_OK;
