@@ -13,7 +13,7 @@ LIB = os.path.join(ROOT, "paper_2405_04690_gb300", "libgbk.so")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:gbk_status|const char\*|int|int64_t)\s+(\w+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:gbk_status|const char\*|int|int32_t|int64_t)\s+(\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 
@@ -45,3 +45,15 @@ def test_version_and_error_string_without_gpu():
     h.gbk_last_error.restype = ctypes.c_char_p
     assert h.gbk_version() >= 100
     assert isinstance(h.gbk_last_error(), bytes)
+
+
+def test_binding_refuses_host_tensors():
+    # the product path has no CPU fallback: host tensors are refused before any library call
+    torch = pytest.importorskip("torch")
+    from paper_2405_04690_gb300 import _lib as L
+    x = torch.zeros((2, 16, 8), dtype=torch.float32)
+    raw = torch.zeros((1, 2, 272), dtype=torch.float32)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        L.gmm_fit(x, raw)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        L.psd_struct(torch.zeros((1, 2), dtype=torch.float64))
