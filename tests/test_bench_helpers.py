@@ -1,6 +1,7 @@
 """The benchmark's own statistics on the CPU: the integrated autocorrelation time behind the
 ESS/s figures is checked on AR(1) chains, whose time is known in closed form,
-tau = (1 + phi) / (1 - phi)."""
+tau = (1 + phi) / (1 - phi); the clock sampler's parsing of nvidia-smi rows; the reference arm
+(the oracle on the host cores) prints its one line on rank 0 only."""
 import os
 import sys
 
@@ -50,3 +51,28 @@ def test_clock_sampler_reads_median_and_throttle_reasons(tmp_path):
     out = cs.stop(0)
     assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
     assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_reference_arm_prints_one_line_on_rank_0_only():
+    # the oracle timed on the host cores: one JSON line with the contract's keys on rank 0; any
+    # other rank exits 0 without work or output
+    import json
+    import subprocess
+    env = dict(os.environ, RANK="0")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--gpus", "2"], capture_output=True, text=True, env=env, timeout=600,
+                         cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [x for x in out.stdout.splitlines() if x.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["gpus_used"] == 0 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    env["RANK"] = "1"
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, env=env, timeout=600, cwd=ROOT)
+    assert out.returncode == 0 and out.stdout.strip() == ""
