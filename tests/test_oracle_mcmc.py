@@ -67,6 +67,18 @@ def test_philox_words_are_uniform_and_counter_distinct():
     assert PX.ranged(0xFFFFFFFF, 7) == 6 and PX.ranged(0, 7) == 0
 
 
+def test_philox_known_answers():
+    # the generator's published known-answer vectors (tests/golden/philox4x32_10_kat.json):
+    # a wrong multiplier, Weyl constant, round count or word permutation changes every word
+    import json
+    import os
+    kat = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.json")))
+    for v in kat["vectors"]:
+        ctr = [int(x, 16) for x in v["ctr"]]
+        key = [int(x, 16) for x in v["key"]]
+        assert list(PX.philox4x32_10(ctr, key)) == [int(x, 16) for x in v["out"]]
+
+
 def test_prior_only_sweeps_reproduce_occupancy_and_f0_prior():
     pi = 0.3
     cfg, state, _, _ = small_ensemble(seed=9, n_temps=1, n_walkers=1, n_bands=2, n_max=6, n_per_band=1,
