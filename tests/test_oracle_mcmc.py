@@ -1,6 +1,7 @@
 """Pins of the oracle's sampler pieces: Eq. temp-final vs Eq. temp-orig, the
 reversible-jump ratio, the swap rate of a two-temperature Gaussian toy, the Philox
-generator's uniformity, and a prior-only run of the full sweep."""
+generator's known answers and uniformity, the fdot prior and support induced by a uniform chirp
+mass, and a prior-only run of the full sweep."""
 import math
 
 import numpy as np
@@ -77,6 +78,43 @@ def test_philox_known_answers():
         ctr = [int(x, 16) for x in v["ctr"]]
         key = [int(x, 16) for x in v["key"]]
         assert list(PX.philox4x32_10(ctr, key)) == [int(x, 16) for x in v["out"]]
+
+
+def test_fdot_prior_is_the_one_induced_by_a_uniform_chirp_mass():
+    # Mc ~ U[mc_min, mc_max] at fixed f0 gives p(fdot | f0) = |dMc/dfdot| / (mc_max - mc_min):
+    # the sampler's prior ratio must equal the ratio of that Jacobian, here taken by central
+    # finite differences of the chirp mass (whose formula the input-recipe test holds against
+    # the recipe's own GR chirp); the support is the Mc interval, read back through Mc
+    g = np.random.default_rng(40)
+    cfg, _, _, _ = small_ensemble(seed=1, n_temps=1, n_walkers=1, n_bands=1, n_max=1, n_per_band=1, betas=(1.0,))
+
+    def jac(f0, fd):
+        h = 1e-6 * fd
+        return (OM.chirp_mass(f0, fd + h) - OM.chirp_mass(f0, fd - h)) / (2 * h)
+
+    lo, hi = cfg.allowance(0)
+    for _ in range(200):
+        f0a, f0b = g.uniform(lo, hi, 2)
+        fa = OM.fdot_from_mc(f0a, g.uniform(0.3, 0.8))
+        fb = OM.fdot_from_mc(f0b, g.uniform(0.3, 0.8))
+        th = [1e-22, f0a, fa, 0.1, 0.2, 0.3, 0.4, 0.5]
+        new = [1e-22, f0b, fb, 0.1, 0.2, 0.3, 0.4, 0.5]
+        want = math.log(jac(f0b, fb)) - math.log(jac(f0a, fa))
+        assert abs(OM.dlog_prior(new, th) - want) < 1e-6
+        assert abs(OM.log_prior_shape(new) - OM.log_prior_shape(th) - OM.dlog_prior(new, th)) < 1e-9
+    for _ in range(400):
+        f0 = g.uniform(lo, hi)
+        mc = g.uniform(0.1, 1.0)
+        if min(abs(mc - 0.3), abs(mc - 0.8)) < 1e-9:
+            continue
+        th = [1e-22, f0, OM.fdot_from_mc(f0, mc), 0.1, 0.2, 0.3, 0.4, 0.5]
+        assert OM.in_support(cfg, th, 0) == (0.3 < mc < 0.8), mc
+    th = [1e-22, 0.5 * (lo + hi), OM.fdot_from_mc(0.5 * (lo + hi), 0.5), 0.1, 0.2, 0.3, 0.4, 0.5]
+    assert OM.in_support(cfg, th, 0)
+    for k, v in ((0, 2e-23 * 0.4), (0, 10 ** -21.4), (5, 1.0001), (6, -1.0001), (1, hi), (1, lo - 1e-12)):
+        bad = list(th)
+        bad[k] = v
+        assert not OM.in_support(cfg, bad, 0), (k, v)
 
 
 def test_prior_only_sweeps_reproduce_occupancy_and_f0_prior():
