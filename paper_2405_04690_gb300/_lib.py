@@ -155,7 +155,7 @@ def lib():
     global _LIB
     if _LIB is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libgbk.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+            raise RuntimeError("libgbk.so is not built (%s); run python -m paper_2405_04690_gb300.build" % LIB_PATH)
         h = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(h, name)
