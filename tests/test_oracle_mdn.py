@@ -210,3 +210,30 @@ def test_quantized_network_is_the_rounded_one():
     layers = MD.unpack(theta)
     h1 = MD.to_bf16(np.maximum(x @ MD.to_bf16(layers[0][0]).T + layers[0][1], 0))
     assert np.array_equal(aq[1], h1)
+
+
+def test_features_whiten_the_band_and_interleave_re_im():
+    # noise drawn as z sqrt(S_n / (4 df)) (z unit complex normal) whitens back to z exactly:
+    # x[ch 512 + 2 i] = Re z[ch][nb + i], x[ch 512 + 2 i + 1] = Im z[ch][nb + i] for the band's
+    # own sub-band (the middle third of the window); the neighbours do not enter
+    from oracle import constants as OC
+    from oracle import psd as OP
+    from paper_2405_04690_gb300 import synth
+    nb = 256
+    k0 = int(2.2e-3 * OC.TOBS)
+    f = (k0 + np.arange(3 * nb)) * OC.DF
+    s = OP.psd_ae(f, OC.SQRT_S_OMS, OC.SQRT_S_ACC)
+    z = synth.unit_complex_normal(synth.rng(12), (2, 3 * nb))
+    rho = z * np.sqrt(s / (4 * OC.DF))
+    x = MD.features(rho, s, OC.DF, nb)
+    assert x.shape == (4 * nb,)
+    for ch in range(2):
+        np.testing.assert_allclose(x[ch * 2 * nb:(ch + 1) * 2 * nb:2], z[ch, nb:2 * nb].real, rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(x[ch * 2 * nb + 1:(ch + 1) * 2 * nb:2], z[ch, nb:2 * nb].imag, rtol=1e-13,
+                                   atol=1e-13)
+    rho2 = rho.copy()
+    rho2[:, :nb] *= 7.0
+    rho2[:, 2 * nb:] = 0.0
+    assert np.array_equal(MD.features(rho2, s, OC.DF, nb), x)
+    # on whitened noise the Eq. inner weight gives <n|n> = sum x^2 per channel ~ 2 per bin
+    assert abs(np.sum(x ** 2) / (2 * nb) - 2.0) < 5 * 2.0 / math.sqrt(2 * nb)
