@@ -57,3 +57,46 @@ def test_binding_refuses_host_tensors():
         L.gmm_fit(x, raw)
     with pytest.raises(TypeError, match="CUDA tensor"):
         L.psd_struct(torch.zeros((1, 2), dtype=torch.float64))
+
+
+def test_entry_points_refuse_null_handles_without_a_gpu():
+    # every status-returning call checks its handles and pointers before any CUDA work: with
+    # null handles and zero sizes it returns GBK_EINVAL and names itself in the error string
+    # (destroying a null network or PSD plan, and an empty mixture batch, are no-ops: GBK_OK)
+    if not os.path.exists(LIB):
+        pytest.skip("library not built")
+    from paper_2405_04690_gb300 import _lib as L
+    h = L.lib()
+    no_op = {"mdn_destroy", "gbk_psd_plan_destroy", "mdn_sample_logpdf"}
+    checked = 0
+    for name, (res, args) in L.SIGNATURES.items():
+        if res is not ctypes.c_int or name in ("gbk_version", "gmm_max_points"):
+            continue
+        vals = []
+        for a in args:
+            if a in (ctypes.c_double, ctypes.c_float):
+                vals.append(0.0)
+            elif a in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64):
+                vals.append(0)
+            else:
+                vals.append(None)
+        st = getattr(h, name)(*vals)
+        if name in no_op:
+            assert st == 0, (name, st)
+        else:
+            assert st == 1, (name, st)
+            assert name in h.gbk_last_error().decode(), (name, h.gbk_last_error())
+        checked += 1
+    assert checked >= 40
+
+
+def test_sizes_the_library_reports():
+    # the network's parameter count is the architecture's (1024 -> 3 x 512 -> 272, weights and
+    # biases), the EM point cap and the no-allocation scratch are the documented constants
+    if not os.path.exists(LIB):
+        pytest.skip("library not built")
+    from oracle import mdn as MD
+    from paper_2405_04690_gb300 import _lib as L
+    assert L.lib().mdn_param_count() == MD.n_params() == 1024 * 512 + 512 + 2 * (512 * 512 + 512) + 512 * 272 + 272
+    assert L.lib().gmm_max_points() == 2048
+    assert L.lib().total_loglike_noalloc_capacity() == 1 << 20
