@@ -45,7 +45,8 @@ typedef enum gbk_status {
   GBK_OK = 0,
   GBK_EINVAL = 1,    /* bad argument (null pointer, size, enum value) */
   GBK_ERANGE = 2,    /* a band fell outside the residual window, or an index out of range */
-  GBK_ENOMEM = 3,    /* device allocation failed (only gbk_create / gbk_sweep_create allocate) */
+  GBK_ENOMEM = 3,    /* device allocation failed (only the create calls and the plan set-up
+                        calls gbk_sweep_set_proposal / gbk_sweep_update_group allocate) */
   GBK_ECUDA = 4,     /* a CUDA runtime call or kernel launch failed */
   GBK_ETIMEOUT = 5,  /* a device-side wait gave up after its iteration limit */
   GBK_ENOTIMPL = 6   /* combination not implemented */
@@ -87,8 +88,10 @@ typedef struct gbk_psd {
 typedef struct gbk_ctx gbk_ctx;
 
 /* Create a context on the current CUDA device: orbit tables for every band length,
- * FFT twiddles, PSD shape tables over the window and scratch. Allocates device memory
- * (as does gbk_sweep_create; no other call does). Returns GBK_ENOMEM / GBK_ECUDA on
+ * FFT twiddles, PSD shape tables over the window and scratch. Allocates device memory,
+ * as do the other create calls (gbk_sweep_create, mdn_create, gbk_psd_plan_create,
+ * gbk_search_create) and, on first use, the plan set-up calls gbk_sweep_set_proposal and
+ * gbk_sweep_update_group; no other call allocates. Returns GBK_ENOMEM / GBK_ECUDA on
  * failure. */
 gbk_status gbk_create(gbk_ctx** out_ctx, const gbk_grid* grid);
 
@@ -216,6 +219,8 @@ typedef struct gbk_psd_desc {
   double stretch_a;            /* stretch scale a > 1 (2 in the paper's sampler library) */
 } gbk_psd_desc;
 
+/* PSD-sampler plan: allocates the proposal, likelihood and partial-sum buffers of T x W
+ * walkers (GBK_ENOMEM on failure); destroy frees them (a NULL plan is a no-op). */
 typedef struct gbk_psd_plan gbk_psd_plan;
 gbk_status gbk_psd_plan_create(gbk_ctx* ctx, const gbk_psd_desc* desc, gbk_psd_plan** out_plan);
 gbk_status gbk_psd_plan_destroy(gbk_psd_plan* plan);
