@@ -205,7 +205,8 @@ gbk_status psd_eval_fg(gbk_ctx* ctx, const double* psd_params, int32_t n_walkers
 /* Eq. like with the per-channel PSD of psd_params [n][9] for n entries: entry i uses residual
  * resid_index[i] of residual [n_resid][2][n_bins][2] float32, 16-byte aligned (resid_index
  * NULL: entry i uses residual i). Entries that share a residual and sit next to each other (groups of 4) read it
- * once. Per-bin terms in float32 (the foreground exponent with the accurate expf), sums as
+ * once. Per-bin terms in float32 (the foreground factor as one base-2 exponential on the
+ * special-function unit; bins where it is below 2^-30 of the instrument term skip it), sums as
  * in total_loglike. Uses the context scratch (order concurrent calls on one stream). */
 gbk_status total_loglike_fg(gbk_ctx* ctx, const float* residual, int32_t n_resid, const double* psd_params,
                             const int32_t* resid_index, int32_t n, double* logl, void* stream);
