@@ -1,5 +1,6 @@
 """Pins of the oracle waveform: fast/slow (W2) against the brute-force response (W1),
-invariants (a) and (b), linearity, Parseval, and the long-wavelength limit."""
+invariants (a) and (b), linearity, Parseval, the long-wavelength limit, and the textbook
+sky- and polarisation-averaged antenna pattern (3/20 for 60-degree arms)."""
 import numpy as np
 import pytest
 
@@ -142,3 +143,25 @@ def test_long_wavelength_limit():
         assert w < 4 * u
     # error shrinks in proportion to u
     assert errs[1][1] < 0.2 * errs[0][1]
+
+
+def test_sky_and_polarisation_averaged_response():
+    # Textbook antenna pattern of a two-arm interferometer with opening angle gamma (60 deg here):
+    # averaged over an isotropic sky and the polarisation angle, <F+^2> = <Fx^2> = sin^2(gamma)/5
+    # = 3/20 and <F+ Fx> = 0. In the long-wavelength limit X -> 2 u^2 (n13.H.n13 - n12.H.n12)
+    # = 4 u^2 (A F+ (1 + cos^2 i)/2 + i A Fx cos i) up to a phase, so with cos i = 0,
+    # <|X|^2> / (16 u^4 A^2) = 3/20, and with cos i = 1, <|X|^2> / (64 u^4 A^2) = <F+^2 + Fx^2> = 3/10.
+    # A wrong tensor normalisation, basis or arm geometry moves these averages.
+    g = np.random.default_rng(17)
+    n = 6000
+    f0, amp = 2e-6, 1e-22
+    u = 2 * np.pi * f0 * C.L_ARM / C.C_LIGHT
+    t = np.array([0.0])
+    for cosi, scale, want in ((0.0, 16.0, 0.15), (1.0, 64.0, 0.30)):
+        v = np.empty(n)
+        for i in range(n):
+            p = np.array([amp, f0, 0.0, 0.0, g.uniform(0, np.pi), cosi, g.uniform(-1, 1), g.uniform(0, 2 * np.pi)])
+            X, _, _ = W.slow_tdi(p, t)
+            v[i] = np.abs(X[0]) ** 2 / (scale * u ** 4 * amp ** 2)
+        se = v.std() / np.sqrt(n)
+        assert abs(v.mean() - want) < 5 * se + 2e-3 * want, (cosi, v.mean(), se)
