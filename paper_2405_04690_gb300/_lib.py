@@ -218,10 +218,14 @@ class Context:
 
 
 def gbk_sync_status(ctx, stream=None):
+    """Synchronise the stream and raise GbkError if a kernel set the context's error word."""
     _check(lib().gbk_sync_status(ctx.handle, _stream(stream)), "gbk_sync_status")
 
 
 def gb_waveform_batch(ctx, params, n_band, n_band_max, k_start, h_a, h_e, out_off, precision, stream=None):
+    """TDI A/E bands of n sources (Sec. II.A, App. F): params [8][n] float64, n_band [n] int32,
+    k_start [n] int64 out, h_a / h_e packed complex bands out (complex64 for GBK_MIXED,
+    complex128 for GBK_FP64; source i at element out_off[i], out_off [n] int64)."""
     n = params.shape[1]
     cdt = torch.complex64 if precision == GBK_MIXED else torch.complex128
     _check(lib().gb_waveform_batch(ctx.handle, _dev(params, torch.float64, "params"), _dev(n_band, torch.int32, "n_band"),
@@ -250,6 +254,9 @@ def psd_struct(psd_params):
 
 def gb_delta_loglike_batch(ctx, params_new, params_old, n_band, n_band_max, walker, residual, psd, dlogl,
                            precision, stream=None):
+    """Delta lnL of n independent swaps old -> new (Eq. swapsource; amplitude 0 old: birth, new: death)
+    against walker[i]'s residual: params_* [8][n] float64, n_band / walker [n] int32, residual from
+    residual_struct, psd from psd_struct, dlogl [n] float64 out."""
     n = params_new.shape[1]
     _check(lib().gb_delta_loglike_batch(ctx.handle, _dev(params_new, torch.float64, "params_new"),
                                         _dev(params_old, torch.float64, "params_old"), _dev(n_band, torch.int32, "n_band"),
@@ -259,6 +266,8 @@ def gb_delta_loglike_batch(ctx, params_new, params_old, n_band, n_band_max, walk
 
 
 def residual_add_sub(ctx, residual, params, n_band, n_band_max, walker, sign, precision, stream=None):
+    """sign +1: the sources enter the model (R <- R - h); -1: they leave (R <- R + h); bit-exact inverse
+    pair on the int64 fixed-point residual. params [8][n] float64, n_band / walker [n] int32."""
     n = params.shape[1]
     _check(lib().residual_add_sub(ctx.handle, ctypes.byref(residual), _dev(params, torch.float64, "params"),
                                   _dev(n_band, torch.int32, "n_band"), int(n_band_max), _dev(walker, torch.int32, "walker"),
@@ -266,12 +275,16 @@ def residual_add_sub(ctx, residual, params, n_band, n_band_max, walker, sign, pr
 
 
 def psd_eval(ctx, psd_params, s_out, stream=None):
+    """Eq. psd on the context window: psd_params [W][2] float64 (sqrt S_oms, sqrt S_acc), s_out
+    [W][n_bins] float64 out (or None)."""
     w = psd_params.shape[0]
     _check(lib().psd_eval(ctx.handle, _dev(psd_params, torch.float64, "psd_params"), w,
                           _dev(s_out, torch.float64, "s_out") if s_out is not None else None, _stream(stream)), "psd_eval")
 
 
 def total_loglike(ctx, residual, psd_params, logl, stream=None):
+    """Eq. like per walker: residual [W][2][n_bins][2] float32, psd_params [W][2] float64, logl [W]
+    float64 out."""
     w = psd_params.shape[0]
     _check(lib().total_loglike(ctx.handle, _dev(residual, torch.float32, "residual"),
                                _dev(psd_params, torch.float64, "psd_params"), w, _dev(logl, torch.float64, "logl"),
@@ -284,7 +297,6 @@ class SweepPlan:
     def __init__(self, ctx, n_temps, n_walkers, n_bands, n_max, band_bins, band_k0, sigma, precision,
                  log_occ_odds=0.0, props_per_source=1.0, ln_a_min=None, ln_a_max=None, mc_min=0.3, mc_max=0.8,
                  f_min=1e-3, f_max=4e-3):
-        import math
         d = GbkSweepDesc()
         d.n_temps, d.n_walkers, d.n_bands, d.n_max, d.band_bins = n_temps, n_walkers, n_bands, n_max, band_bins
         d.band_k0 = int(band_k0)
@@ -315,7 +327,10 @@ class SweepPlan:
 
 
 def gb_sweep(plan, params, exists, betas, residual, psd, key, sweep_index, flags, trace=None, stats=None, stream=None):
-    """trace: (records uint8 tensor of capacity*sizeof(GbkTraceRec) bytes, capacity, count int32 tensor) or None."""
+    """One sweep of the ensemble (in-model moves, flip-all RJ, tempering swaps per the flags):
+    params [T][W][B][n_max][8] float64 and exists [T][W][B][n_max] uint8 in/out, betas [B][T]
+    float64, residual / psd structs, stats [5][2] int64 (added to) or None.
+    trace: (records uint8 tensor of capacity*sizeof(GbkTraceRec) bytes, capacity, count int32 tensor) or None."""
     tr = None
     if trace is not None:
         rec, cap, cnt = trace
@@ -378,14 +393,17 @@ class Mdn:
 
 
 def mdn_status(net, stream=None):
+    """Synchronise and raise GbkError if a tensor-core product of the workspace gave up a wait."""
     _check(lib().mdn_status(net.handle, _stream(stream)), "mdn_status")
 
 
 def mdn_param_count():
+    """Length of the flat float32 parameter vector (W1 b1 W2 b2 W3 b3 W4 b4)."""
     return int(lib().mdn_param_count())
 
 
 def mdn_set_params(net, params, stream=None):
+    """Load float32 parameters [mdn_param_count()] into the workspace's BF16 copies."""
     _check(lib().mdn_set_params(net.handle, _dev(params, torch.float32, "params"), _stream(stream)), "mdn_set_params")
 
 
@@ -396,6 +414,8 @@ def mdn_forward(net, x, raw, stream=None):
 
 
 def mdn_backward(net, x, u, grad, loss=None, stream=None):
+    """grad [mdn_param_count()] float32 = d(mean -ln q(u | x))/d(params); x [B][1024] bfloat16,
+    u [B][8] float32 unit coordinates; loss (float64 [1] or None) out."""
     _check(lib().mdn_backward(net.handle, _dev(x, torch.bfloat16, "x"), _dev(u, torch.float32, "u"), int(x.shape[0]),
                               _dev(grad, torch.float32, "grad"),
                               _dev(loss, torch.float64, "loss") if loss is not None else None, _stream(stream)),
@@ -403,12 +423,14 @@ def mdn_backward(net, x, u, grad, loss=None, stream=None):
 
 
 def mdn_adam(net, params, m, v, grad, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """One Adam step on the caller's float32 params / moments (step counts from 1)."""
     _check(lib().mdn_adam(net.handle, _dev(params, torch.float32, "params"), _dev(m, torch.float32, "m"),
                           _dev(v, torch.float32, "v"), _dev(grad, torch.float32, "grad"), int(step), float(lr),
                           float(beta1), float(beta2), float(eps), _stream(stream)), "mdn_adam")
 
 
 def mdn_train_step(net, params, m, v, x, u, step, lr, loss=None, stream=None):
+    """mdn_backward then Adam on one batch, the gradient kept on the device."""
     _check(lib().mdn_train_step(net.handle, _dev(params, torch.float32, "params"), _dev(m, torch.float32, "m"),
                                 _dev(v, torch.float32, "v"), _dev(x, torch.bfloat16, "x"), _dev(u, torch.float32, "u"),
                                 int(x.shape[0]), int(step), float(lr),
@@ -428,6 +450,8 @@ def mdn_train_epoch(net, params, m, v, x, u, order, batch, step0, lr, loss=None,
 
 
 def mdn_sample_logpdf(raw, eps, precision, words=None, u_out=None, u_in=None, logq=None, stream=None):
+    """Draws (words [B][9] int32 bit patterns -> u_out [B][8]) from, or densities (u_in [B][8]) of, the
+    eps-defensive truncated mixture of raw [B][272]; logq [B] float32 out."""
     _check(lib().mdn_sample_logpdf(_dev(raw, torch.float32, "raw"), int(raw.shape[0]), float(eps),
                                    _dev(words, torch.int32, "words") if words is not None else None,
                                    _dev(u_out, torch.float32, "u_out") if u_out is not None else None,
@@ -437,6 +461,7 @@ def mdn_sample_logpdf(raw, eps, precision, words=None, u_out=None, u_in=None, lo
 
 
 def gmm_max_points():
+    """Most present points per group that gmm_fit uses (the first ones)."""
     return int(lib().gmm_max_points())
 
 
