@@ -386,6 +386,21 @@ def open_band(cfg, state, r_snap, w, b):
     return rho
 
 
+def band_residual(cfg, state, r_snap, rho, t, w, b):
+    """r' of Alg. 1 for band (t, w, b) on the band's window: the cold chain reads its residual
+    snapshot (which already lacks its own band-b sources); a hotter chain starts from rho_{w,b}
+    (the cold chain's residual with band b's cold sources added back) and subtracts its own
+    band-b sources (the cold chain's neighbours, Sec. V.D)."""
+    off, n = cfg.window(b)
+    if t == 0:
+        return RS.from_fixed(r_snap[w][:, off:off + n], cfg.frac_bits)
+    rp = rho.copy()
+    for s in range(cfg.n_max):
+        if state["exists"][t, w, b, s]:
+            rp = rp - _band_window(cfg, state["params"][t, w, b, s], b)
+    return rp
+
+
 def band_task(cfg, state, r_snap, rho, t, w, b, parity, sweep, trace):
     """Alg. 1 (in-model) followed by the flip-all RJ pass (App. C) for band (t, w, b)."""
     off, n = cfg.window(b)
@@ -394,13 +409,7 @@ def band_task(cfg, state, r_snap, rho, t, w, b, parity, sweep, trace):
     P = state["params"]
     E = state["exists"]
     R = state["resid"]
-    if t == 0:
-        rp = RS.from_fixed(r_snap[w][:, off:off + n], cfg.frac_bits)
-    else:
-        rp = rho.copy()
-        for s in range(cfg.n_max):
-            if E[t, w, b, s]:
-                rp = rp - _band_window(cfg, P[t, w, b, s], b)
+    rp = band_residual(cfg, state, r_snap, rho, t, w, b)
     tid = task_id(cfg, t, w, b)
 
     def apply(th_new, th_old):
@@ -538,19 +547,27 @@ def swap_band(cfg, state, rhos, b, parity, sweep, trace):
             u = PX.u53(words[0], words[1])
             lu = math.log(u) if u > 0 else -math.inf
             acc = lu < la
-            trace.append(_rec(3, t, wt, b, c, t, acc, parity, la, la, None, lu))
+            rec = _rec(3, t, wt, b, c, t, acc, parity, la, la, None, lu)
+            rec["partner"] = wm   # the walker of rung t - 1 in this swap
+            trace.append(rec)
             if acc:
                 old_cold = [list(P[0, wm, b, s]) for s in range(cfg.n_max) if E[0, wm, b, s]] if t == 1 else None
                 pa, ea = P[t, wt, b].copy(), E[t, wt, b].copy()
                 P[t, wt, b], E[t, wt, b] = P[t - 1, wm, b].copy(), E[t - 1, wm, b].copy()
                 P[t - 1, wm, b], E[t - 1, wm, b] = pa, ea
                 if t == 1:
-                    for th in old_cold:
-                        R[wm] = RS.add_sub(R[wm], cfg.k0, WF.fastslow_band(th, cfg.nb, cfg.tobs), -1, cfg.frac_bits)
-                    for s in range(cfg.n_max):
-                        if E[0, wm, b, s]:
-                            R[wm] = RS.add_sub(R[wm], cfg.k0, WF.fastslow_band(P[0, wm, b, s], cfg.nb, cfg.tobs), +1,
-                                               cfg.frac_bits)
+                    swap_cold_update(cfg, state, wm, b, old_cold)
+
+
+def swap_cold_update(cfg, state, w, b, old_cold):
+    """After a rung-1 swap the cold chain of walker w holds a new band-b source set: its
+    residual d - H gets the old set's templates back and the new set's subtracted."""
+    P, E, R = state["params"], state["exists"], state["resid"]
+    for th in old_cold:
+        R[w] = RS.add_sub(R[w], cfg.k0, WF.fastslow_band(th, cfg.nb, cfg.tobs), -1, cfg.frac_bits)
+    for s in range(cfg.n_max):
+        if E[0, w, b, s]:
+            R[w] = RS.add_sub(R[w], cfg.k0, WF.fastslow_band(P[0, w, b, s], cfg.nb, cfg.tobs), +1, cfg.frac_bits)
 
 
 def owner_band(cfg, f0):
