@@ -584,25 +584,26 @@ gbk_status gb_sweep_features(gbk_sweep* plan, const double* params, const uint8_
                              float* u_out, void* stream);
 
 /* ------------------------------------------------------------------ no-allocation variant
- * total_loglike_noalloc -- the same result as total_loglike (Eq. like for W walkers, both
- * channels), for callers that cannot allocate device memory: code that runs inside
- * another framework's allocator or memory budget, or that must not grow the device
- * footprint after start-up. It needs no gbk_ctx (whose creation allocates): the grid is
- * passed directly and the PSD shape is computed in the kernel. (The paper has no
- * counterpart: this is a deployment variant of the total-likelihood pass.)
+ * total_loglike_noalloc -- the total Gaussian log-likelihood of W walkers over both channels
+ * (what total_loglike returns), for callers that cannot allocate device memory: code that
+ * runs inside another framework's allocator or memory budget, or that must not grow the
+ * device footprint after start-up. It needs no gbk_ctx (whose creation allocates): the grid
+ * is passed directly and the PSD shape is evaluated in float64 by a kernel of the call. The
+ * paper has no counterpart: this is a deployment variant of the total-likelihood pass.
  *   tobs, k0, n_bins  the window, as in gbk_grid; (k0 + n_bins) / tobs < c / (2L)
  *   residual          [W][2][n_bins][2] float32, 8-byte aligned
  *   psd_params        [W][2] float64;  logl [W] float64 out
- * Its scratch (cross-block partial sums) is a fixed array of
- * total_loglike_noalloc_capacity() doubles (8 MiB) in the library's device memory, held
+ * Its scratch (the float32 shape tables and the cross-block partial sums) is a fixed array
+ * of total_loglike_noalloc_capacity() doubles (16 MiB) in the library's device memory, held
  * on every device that loads the library until the process exits. A call needs
- * ceil(n_bins / 4096) * (2 W + 1) doubles; larger requests return GBK_ERANGE. Every call
- * overwrites all the partial sums it reads, so earlier contents do not matter; but all
- * calls share the one array, so calls that overlap on the GPU (different streams, or
- * host threads without ordering) race and give wrong results: order them on one stream.
- * The first call on each device looks up the array's device address; make that first
- * call before any stream capture. Allocates nothing (no cudaMalloc, no library calls that
- * allocate).
+ * n_bins + 2 W ceil(n_bins / 4096) + ceil(n_bins / 256) doubles and W <= 524280; larger
+ * requests return GBK_ERANGE. Every call overwrites all the scratch it reads, so earlier
+ * contents do not matter; but all calls share the one array, so calls that overlap on the
+ * GPU (different streams, or host threads without ordering) race and give wrong results:
+ * order them on one stream. The first call on each device looks up the array's device
+ * address and keeps it for the process; make that first call before any stream capture. A
+ * device reset (cudaDeviceReset) invalidates the kept address: do not call this entry
+ * point after one. Allocates nothing (no cudaMalloc, no library calls that allocate).
  */
 int64_t total_loglike_noalloc_capacity(void);
 gbk_status total_loglike_noalloc(double tobs, int64_t k0, int64_t n_bins, const float* residual,

@@ -350,8 +350,18 @@ def gbk_sweep_kernel_ms(plan):
 
 
 def total_loglike_noalloc(tobs, k0, n_bins, residual, psd_params, logl, stream=None):
-    """Eq. like for W walkers without a context and without allocating (fixed scratch)."""
+    """Total log-likelihood of W walkers without a context and without allocating (fixed scratch).
+
+    residual [W][2][n_bins][2] float32, psd_params [W][2] float64, logl [W] float64 (out);
+    the sizes are checked here, before the library reads any of them."""
+    if psd_params.dim() != 2 or psd_params.shape[1] != 2:
+        raise ValueError("total_loglike_noalloc: psd_params must be [W][2]")
     w = psd_params.shape[0]
+    if residual.numel() < 4 * w * int(n_bins):
+        raise ValueError("total_loglike_noalloc: residual holds %d floats, [W][2][n_bins][2] needs %d"
+                         % (residual.numel(), 4 * w * int(n_bins)))
+    if logl.numel() < w:
+        raise ValueError("total_loglike_noalloc: logl holds %d entries, W = %d" % (logl.numel(), w))
     _check(lib().total_loglike_noalloc(float(tobs), int(k0), int(n_bins), _dev(residual, torch.float32, "residual"),
                                        _dev(psd_params, torch.float64, "psd_params"), w,
                                        _dev(logl, torch.float64, "logl"), _stream(stream)), "total_loglike_noalloc")

@@ -37,12 +37,17 @@ k_total_loglike_part(const float* __restrict__ R, const float* __restrict__ iq, 
   const int wg = blockIdx.y * kTlWalkers;  // local walker offset within this launch
   const int64_t kbeg = (int64_t)chunk * kTlChunk;
   const int64_t kend = min(kbeg + (int64_t)kTlChunk, nb);
-  __shared__ float s_aw[kTlWalkers];
-  if (threadIdx.x < kTlWalkers) {     // per-walker S_acc / S_oms, once per block
+  // per-walker a = S_acc / S_oms as a float pair hi + lo, once per block: u = 1 + a rho is
+  // formed as (1 + hi rho) + lo rho, so the float rounding of a (the same in every bin of the
+  // walker) does not bias the sum of ln u
+  __shared__ float s_aw[kTlWalkers][2];
+  if (threadIdx.x < kTlWalkers) {
     const int wl = wg + threadIdx.x;
     const int w = w0 + (wl < nwl ? wl : 0);
     const double so = pp[2 * w] * pp[2 * w], sa = pp[2 * w + 1] * pp[2 * w + 1];
-    s_aw[threadIdx.x] = (float)(sa / so);
+    const double a = sa / so;
+    s_aw[threadIdx.x][0] = (float)a;
+    s_aw[threadIdx.x][1] = (float)(a - (double)(float)a);
   }
   __syncthreads();
   float aw[kTlWalkers];
@@ -50,8 +55,10 @@ k_total_loglike_part(const float* __restrict__ R, const float* __restrict__ iq, 
 #pragma unroll
   for (int j = 0; j < kTlWalkers; ++j) {
     act[j] = wg + j < nwl;
-    aw[j] = s_aw[j];
+    aw[j] = s_aw[j][0];
   }
+  // the lo parts stay in shared memory (read per use): in registers they would spill
+  volatile const float* awl = &s_aw[0][1];
   const float* rbase = R + (int64_t)(w0 + wg) * 2 * nb * 2;
   CompF sq[kTlWalkers], sl[kTlWalkers];
 #pragma unroll
@@ -74,7 +81,9 @@ k_total_loglike_part(const float* __restrict__ R, const float* __restrict__ iq, 
 #pragma unroll
       for (int j = 0; j < kTlWalkers; ++j) {
         if (!act[j]) continue;
-        const float u0 = fmaf(aw[j], rh2.x, 1.0f), u1 = fmaf(aw[j], rh2.y, 1.0f);
+        const float lo = awl[2 * j];
+        const float u0 = fmaf(lo, rh2.x, fmaf(aw[j], rh2.x, 1.0f));
+        const float u1 = fmaf(lo, rh2.y, fmaf(aw[j], rh2.y, 1.0f));
         const float ax = a[j].x * up, ay = a[j].y * up, az = a[j].z * up, aww = a[j].w * up;
         const float ex = e[j].x * up, ey = e[j].y * up, ez = e[j].z * up, ew = e[j].w * up;
         const float m0 = ax * ax + ay * ay + ex * ex + ey * ey;
@@ -93,7 +102,7 @@ k_total_loglike_part(const float* __restrict__ R, const float* __restrict__ iq, 
           const float* rw = rbase + (int64_t)j * 2 * nb * 2;
           const float2 a = *reinterpret_cast<const float2*>(rw + 2 * kk);
           const float2 e = *reinterpret_cast<const float2*>(rw + 2 * (nb + kk));
-          const float u = fmaf(aw[j], rhk, 1.0f);
+          const float u = fmaf(awl[2 * j], rhk, fmaf(aw[j], rhk, 1.0f));
           const float ax = a.x * up, ay = a.y * up, ex = e.x * up, ey = e.y * up;
           sq[j].add((ax * ax + ay * ay + ex * ex + ey * ey) * iqk * __frcp_rn(u));
           sl[j].add(logf(u));

@@ -5,9 +5,10 @@
 // happen before a latency-critical phase, or a plug-in that is handed device buffers and
 // may not grow the device footprint. They cannot create a gbk_ctx either (gbk_create
 // allocates its tables). This entry point needs neither: the PSD shape is computed in
-// the kernel, and its one piece of scratch, the cross-block partial sums, lives in a
+// a kernel, and its scratch (the shape tables and the cross-block partial sums) lives in a
 // fixed file-scope __device__ array that the module holds for as long as the library is
-// loaded on a device.
+// loaded on a device. The PSD shape is evaluated in float64 once per call into that array
+// (float32 tables, like the context's), and the sum of ln Q is kept in float64.
 #include <math.h>
 #include <mutex>
 
@@ -17,44 +18,63 @@
 namespace gbk {
 
 constexpr int kStThreads = 256;
-constexpr int kStChunk = 4096;                   // bins per block
+constexpr int kStChunk = 4096;                   // bins per block of the likelihood pass
 constexpr int kStWalkers = 8;                    // walkers per block
-constexpr int64_t kStScratchDoubles = 1 << 20;   // 8 MiB of partial sums
+constexpr int kStShapeThreads = 256;             // bins per block of the shape pass
+constexpr int64_t kStScratchDoubles = 1 << 21;   // 16 MiB
 
-// Partial sums [chunk][walker][2] followed by [chunk] sums of ln Q; every call writes all
-// of the entries it later reads, so nothing needs clearing between calls.
+// Scratch layout, in doubles: the float32 shape tables iq [n_bins] and rho [n_bins] (n_bins
+// doubles together), then the likelihood pass's partial sums [chunk][walker][2], then the
+// shape pass's sums of ln Q [shape block]. Every call writes all of the entries it later
+// reads, so nothing needs clearing between calls.
 static __device__ __align__(256) double g_static_scratch[kStScratchDoubles];
 
-// Per-bin PSD shape in float32 (S = S_oms Q (1 + (S_acc/S_oms) rho), Eq. psd):
-// returns iq = 2^-128 / Q and rho = P / Q for frequency f.
-__device__ __forceinline__ void psd_shape_f(double f, float& iq, float& rho, double& q64) {
-  const double x = 2.0 * 3.141592653589793 * f * kLc;
-  const float xf = (float)x, ff = (float)f;
-  float sx, cx;
-  sincosf(xf, &sx, &cx);
-  const float c2x = 2.0f * cx * cx - 1.0f;
-  const float a = 0.4e-3f / ff, bq = ff / 8e-3f, o = 2e-3f / ff;
-  const float tpcf = 6.283185307179586f * 299792458.0f * ff;
-  const float pm_unit = (1.0f / (tpcf * tpcf)) * (1.0f + a * a) * (1.0f + bq * bq * bq * bq);
-  const float tpfc = 6.283185307179586f * ff / 299792458.0f;
-  const float op_unit = tpfc * tpfc * (1.0f + o * o * o * o);
-  const float s2 = 8.0f * sx * sx;
-  const float p = s2 * 2.0f * pm_unit * (3.0f + 2.0f * cx + c2x);
-  const float q = s2 * op_unit * (2.0f + cx);
-  rho = p / q;
-  iq = (1.0f / q) * 2.9387358770557188e-39f;   // 2^-128
-  q64 = (double)q;
+// Eq. psd split by noise power, S_n = S_oms Q(f) + S_acc P(f), in float64 with float64
+// constants (as the context's tables are built): per bin iq = 2^-128 / Q and rho = P / Q
+// rounded once to float32, and the float64 sum of ln Q over the block's bins.
+__global__ void __launch_bounds__(kStShapeThreads)
+k_static_shape(double tobs, int64_t k0, int64_t nb, float* __restrict__ iq, float* __restrict__ rho,
+               double* __restrict__ lnq_part) {
+  const int64_t k = (int64_t)blockIdx.x * kStShapeThreads + threadIdx.x;
+  double lq = 0.0;
+  if (k < nb) {
+    const double f = (double)(k0 + k) / tobs;
+    const double x = 2.0 * 3.141592653589793 * f * kLc;
+    double sx, cx;
+    sincos(x, &sx, &cx);
+    const double c2x = 2.0 * cx * cx - 1.0;
+    const double tpcf = 2.0 * 3.141592653589793 * kC * f;
+    const double a = 0.4e-3 / f, bq = f / 8e-3, o = 2e-3 / f, tpfc = 2.0 * 3.141592653589793 * f / kC;
+    const double pm_unit = (1.0 + a * a) * (1.0 + bq * bq * bq * bq) / (tpcf * tpcf);
+    const double op_unit = tpfc * tpfc * (1.0 + o * o * o * o);
+    const double s2 = 8.0 * sx * sx;
+    const double p = s2 * 2.0 * pm_unit * (3.0 + 2.0 * cx + c2x);
+    const double q = s2 * op_unit * (2.0 + cx);
+    iq[k] = (float)(2.9387358770557188e-39 / q);   // 2^-128 / Q
+    rho[k] = (float)(p / q);
+    lq = log(q);
+  }
+  for (int o = 16; o > 0; o >>= 1) lq += __shfl_xor_sync(0xffffffffu, lq, o);
+  __shared__ double red[kStShapeThreads / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kStShapeThreads / 32; ++w) t += red[w];
+    lnq_part[blockIdx.x] = t;
+  }
 }
 
 __global__ void __launch_bounds__(kStThreads)
-k_static_part(double tobs, int64_t k0, int64_t nb, const float* __restrict__ R, const double* __restrict__ pp,
-              int32_t nwl, double* __restrict__ part) {
+k_static_part(int64_t nb, const float* __restrict__ R, const double* __restrict__ pp, int32_t nwl,
+              const float* __restrict__ iqt, const float* __restrict__ rhot, double* __restrict__ part) {
   const int chunk = blockIdx.x;
   const int wg = blockIdx.y * kStWalkers;
   const int64_t kbeg = (int64_t)chunk * kStChunk;
   const int64_t kend = min(kbeg + (int64_t)kStChunk, nb);
-  const int nchunks = gridDim.x;
-  float aw[kStWalkers];
+  // a = S_acc / S_oms as a float pair hi + lo (u = (1 + hi rho) + lo rho): the rounding of
+  // a, the same in every bin of a walker, would otherwise bias the sum of ln u
+  float aw[kStWalkers], awl[kStWalkers];
   const float* rw[kStWalkers];
   bool act[kStWalkers];
 #pragma unroll
@@ -63,32 +83,29 @@ k_static_part(double tobs, int64_t k0, int64_t nb, const float* __restrict__ R, 
     act[j] = w < nwl;
     const int ww = act[j] ? w : 0;
     const double so = pp[2 * ww] * pp[2 * ww], sa = pp[2 * ww + 1] * pp[2 * ww + 1];
-    aw[j] = (float)(sa / so);
+    const double a = sa / so;
+    aw[j] = (float)a;
+    awl[j] = (float)(a - (double)aw[j]);
     rw[j] = R + (int64_t)ww * 2 * nb * 2;
   }
   CompF sq[kStWalkers], sl[kStWalkers];
 #pragma unroll
   for (int j = 0; j < kStWalkers; ++j) { sq[j].init(); sl[j].init(); }
-  double lnq = 0.0;   // sum of ln Q over this thread's bins (first walker group only)
   const float up = 18446744073709551616.0f;  // 2^64
   for (int64_t k = kbeg + threadIdx.x; k < kend; k += kStThreads) {
-    float iq, rh;
-    double q64;
-    psd_shape_f((double)(k0 + k) / tobs, iq, rh, q64);
-    if (blockIdx.y == 0) lnq += log(q64);
+    const float iq = __ldg(iqt + k), rh = __ldg(rhot + k);
 #pragma unroll
     for (int j = 0; j < kStWalkers; ++j) {
       if (!act[j]) continue;
       const float2 a = *reinterpret_cast<const float2*>(rw[j] + 2 * k);
       const float2 e = *reinterpret_cast<const float2*>(rw[j] + 2 * (nb + k));
-      const float u = fmaf(aw[j], rh, 1.0f);
+      const float u = fmaf(awl[j], rh, fmaf(aw[j], rh, 1.0f));
       const float ax = a.x * up, ay = a.y * up, ex = e.x * up, ey = e.y * up;
       sq[j].add((ax * ax + ay * ay + ex * ex + ey * ey) * iq * __frcp_rn(u));
       sl[j].add(logf(u));
     }
   }
   __shared__ double red[kStThreads / 32][kStWalkers][2];
-  __shared__ double redq[kStThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < kStWalkers; ++j) {
@@ -96,8 +113,6 @@ k_static_part(double tobs, int64_t k0, int64_t nb, const float* __restrict__ R, 
     const double tl = sl[j].warp_total();
     if (lane == 0) { red[wid][j][0] = tq; red[wid][j][1] = tl; }
   }
-  for (int o = 16; o > 0; o >>= 1) lnq += __shfl_xor_sync(0xffffffffu, lnq, o);
-  if (lane == 0) redq[wid] = lnq;
   __syncthreads();
   if (threadIdx.x < kStWalkers * 2) {
     const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
@@ -107,23 +122,19 @@ k_static_part(double tobs, int64_t k0, int64_t nb, const float* __restrict__ R, 
       part[((int64_t)chunk * nwl + wg + j) * 2 + which] = s;
     }
   }
-  if (blockIdx.y == 0 && threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < kStThreads / 32; ++w) s += redq[w];
-    part[(int64_t)nchunks * nwl * 2 + chunk] = s;
-  }
 }
 
-__global__ void k_static_final(const double* __restrict__ part, int nchunks, const double* __restrict__ pp,
-                               int32_t nwl, int64_t nb, double df, double* __restrict__ logl) {
+__global__ void k_static_final(const double* __restrict__ part, int nchunks, const double* __restrict__ lnq_part,
+                               int nshape, const double* __restrict__ pp, int32_t nwl, int64_t nb, double df,
+                               double* __restrict__ logl) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= nwl) return;
   double q = 0.0, l = 0.0, lq = 0.0;
   for (int c = 0; c < nchunks; ++c) {
     q += part[((int64_t)c * nwl + w) * 2];
     l += part[((int64_t)c * nwl + w) * 2 + 1];
-    lq += part[(int64_t)nchunks * nwl * 2 + c];
   }
+  for (int c = 0; c < nshape; ++c) lq += lnq_part[c];
   const double so = pp[2 * w] * pp[2 * w];
   logl[w] = -0.5 * (4.0 * df / so) * q - 2.0 * ((double)nb * log(so) + lq + l);
 }
@@ -169,18 +180,28 @@ extern "C" gbk_status total_loglike_noalloc(double tobs, int64_t k0, int64_t n_b
   if (!residual || !psd_params || !logl) return set_error(GBK_EINVAL, "total_loglike_noalloc: null device pointer");
   if (((uintptr_t)residual & 7) != 0) return set_error(GBK_EINVAL, "total_loglike_noalloc: residual must be 8-byte aligned");
   const int64_t nchunks = (n_bins + kStChunk - 1) / kStChunk;
-  const int64_t need = nchunks * (int64_t)n_walkers * 2 + nchunks;
-  if (need > kStScratchDoubles || nchunks > 65535)
+  const int64_t nshape = (n_bins + kStShapeThreads - 1) / kStShapeThreads;
+  const int64_t ngroups = ((int64_t)n_walkers + kStWalkers - 1) / kStWalkers;
+  if (ngroups > 65535)
+    return set_error(GBK_ERANGE, "total_loglike_noalloc: %lld walkers exceed the %d the launch grid takes",
+                     (long long)n_walkers, 65535 * kStWalkers);
+  const int64_t need = n_bins + nchunks * (int64_t)n_walkers * 2 + nshape;
+  if (need > kStScratchDoubles)
     return set_error(GBK_ERANGE,
                      "total_loglike_noalloc: %lld walkers x %lld bins need %lld scratch doubles, the fixed array holds %lld",
                      (long long)n_walkers, (long long)n_bins, (long long)need, (long long)kStScratchDoubles);
   double* scratch = nullptr;
   gbk_status s = static_scratch(&scratch);
   if (s) return s;
+  float* iq = reinterpret_cast<float*>(scratch);
+  float* rho = iq + n_bins;
+  double* part = scratch + n_bins;
+  double* lnq_part = part + nchunks * (int64_t)n_walkers * 2;
   cudaStream_t st = (cudaStream_t)stream;
-  dim3 grid((unsigned)nchunks, (unsigned)((n_walkers + kStWalkers - 1) / kStWalkers));
-  k_static_part<<<grid, kStThreads, 0, st>>>(tobs, k0, n_bins, residual, psd_params, n_walkers, scratch);
-  k_static_final<<<(n_walkers + 127) / 128, 128, 0, st>>>(scratch, (int)nchunks, psd_params, n_walkers, n_bins,
-                                                          1.0 / tobs, logl);
+  k_static_shape<<<(unsigned)nshape, kStShapeThreads, 0, st>>>(tobs, k0, n_bins, iq, rho, lnq_part);
+  dim3 grid((unsigned)nchunks, (unsigned)ngroups);
+  k_static_part<<<grid, kStThreads, 0, st>>>(n_bins, residual, psd_params, n_walkers, iq, rho, part);
+  k_static_final<<<(n_walkers + 127) / 128, 128, 0, st>>>(part, (int)nchunks, lnq_part, (int)nshape, psd_params,
+                                                          n_walkers, n_bins, 1.0 / tobs, logl);
   return check_launch("total_loglike_noalloc");
 }

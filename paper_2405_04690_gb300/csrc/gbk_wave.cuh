@@ -2,7 +2,9 @@
 // FFT and heterodyne, in float32 (mixed) or float64 (plain) arithmetic.
 //
 // Model (arXiv:2405.04690 Sec. II.A and App. F name FastGB; the response below is the
-// standard equal-arm one, derived in the accompanying design notes):
+// standard equal-arm one: the link response n.H.n / (2 (1 - k.n)) [H(t_emit) - H(t_recv)]
+// with the carrier phase expanded to first order in the light times, Phi(t - tau) =
+// Phi(t) - 2 pi f(t) tau, and the geometry taken at each coarse sample):
 //   H(t) = Re[Hc e^{i Phi(t)}], Hc = A(1+cos^2 i) e+(psi) + 2i A cos i ex(psi),
 //   Phi(t) = phi0 + 2 pi f0 t + pi fdot t^2.
 //   Link i->j (unit vector n from craft i to j, receiver position x_j), slow part:

@@ -99,4 +99,21 @@ def test_sizes_the_library_reports():
     from paper_2405_04690_gb300 import _lib as L
     assert L.lib().mdn_param_count() == MD.n_params() == 1024 * 512 + 512 + 2 * (512 * 512 + 512) + 512 * 272 + 272
     assert L.lib().gmm_max_points() == 2048
-    assert L.lib().total_loglike_noalloc_capacity() == 1 << 20
+    assert L.lib().total_loglike_noalloc_capacity() == 1 << 21
+
+
+def test_noalloc_binding_checks_sizes_before_the_call():
+    # undersized tensors never reach the library (which would read past them): the binding
+    # compares them with W and n_bins first
+    torch = pytest.importorskip("torch")
+    if not os.path.exists(LIB):
+        pytest.skip("library not built")
+    from paper_2405_04690_gb300 import _lib as L
+    pp = torch.ones((4, 2), dtype=torch.float64)
+    out = torch.zeros(4, dtype=torch.float64)
+    with pytest.raises(ValueError, match="residual"):
+        L.total_loglike_noalloc(3.0e7, 3146, 1 << 16, torch.zeros((1, 2, 8, 2), dtype=torch.float32), pp, out)
+    with pytest.raises(ValueError, match="logl"):
+        L.total_loglike_noalloc(3.0e7, 3146, 8, torch.zeros((4, 2, 8, 2), dtype=torch.float32), pp, out[:2])
+    with pytest.raises(ValueError, match="psd_params"):
+        L.total_loglike_noalloc(3.0e7, 3146, 8, torch.zeros((4, 2, 8, 2), dtype=torch.float32), pp[:, :1], out)

@@ -296,6 +296,32 @@ def test_total_loglike_matches_oracle():
     assert np.max(np.abs(got - want)) < tol, (np.max(np.abs(got - want)), tol)
 
 
+def test_total_loglike_full_window_has_no_systematic_error():
+    # The bench's window (2^20 bins from k0 = 3146) with residuals whose noise is off their
+    # walker's PSD by up to 30 %: then an error of the PSD that is the same in every bin (for
+    # example the float32 rounding of S_acc / S_oms) no longer cancels between -1/2 <R|R> and
+    # -sum ln S. The per-bin rounding of the float32 terms is random and sums to ~1e-4 here.
+    torch = torch_cuda()
+    from paper_2405_04690_gb300 import _lib as L
+    g = synth.rng(14)
+    k0, n, nw = 3146, 1 << 20, 4
+    psdp = synth.draw_psd_params(g, nw)
+    R = np.empty((nw, 2, n), np.complex64)
+    want = np.empty(nw)
+    for w, scale in enumerate((0.7, 0.9, 1.1, 1.3)):
+        s = psd_window(k0, n, psdp[w, 0], psdp[w, 1])
+        R[w] = (scale * synth.unit_complex_normal(g, (2, n)) * np.sqrt(s / (4 * OC.DF))).astype(np.complex64)
+        want[w] = OL.loglike(R[w].astype(np.complex128), s, OC.DF)
+    dev = torch.device("cuda")
+    rt = torch.from_numpy(R).view(torch.float32).reshape(nw, 2, n, 2).contiguous().to(dev)
+    out = torch.empty(nw, dtype=torch.float64, device=dev)
+    ctx = _ctx(L, k0, n)
+    L.total_loglike(ctx, rt, torch.from_numpy(psdp).to(dev), out)
+    L.gbk_sync_status(ctx)
+    err = np.abs(out.cpu().numpy() - want)
+    assert np.max(err) < 5e-3, (err, want)
+
+
 def test_errors_are_reported_not_faulted():
     torch = torch_cuda()
     from paper_2405_04690_gb300 import _lib as L

@@ -5,8 +5,9 @@ or memory budget, or that must not grow the device footprint) use
 total_loglike_noalloc, whose only scratch is a fixed array inside the library. This
 test calls it through the C ABI twice in a row, with different sizes, and checks each
 result against total_loglike (which takes its scratch from a context) within the
-tolerance the other likelihood tests use: float32 per-bin terms, |error| <= 3 n 2^-22.
-It lives in a file of its own that pytest collects last.
+tolerance the other likelihood tests use: float32 per-bin terms, |error| <= 3 n 2^-22;
+then against the float64 oracle at 2^20 bins, twice in a row, to 5e-3 nats. It lives in a
+file of its own that pytest collects last.
 """
 import numpy as np
 import pytest
@@ -53,16 +54,53 @@ def test_noalloc_total_loglike_matches_context_path_twice():
         ctx.close()
 
 
+def test_noalloc_total_loglike_matches_oracle_at_a_million_bins():
+    # The full-size window (k0 = 3146, 2^20 bins) against the float64 oracle's Eq. like, with
+    # residuals whose noise level is off their walker's PSD by up to 30 %, so that a
+    # systematic error of the PSD (of ln S or of 1/S) does not cancel between the two terms.
+    torch = torch_cuda()
+    from oracle import likelihood as LK
+    from oracle import psd as OP
+    from paper_2405_04690_gb300 import _lib as L
+    dev = torch.device("cuda")
+    g = synth.rng(32)
+    k0, n, nw = 3146, 1 << 20, 3
+    psdp = synth.draw_psd_params(g, nw)
+    f = (k0 + np.arange(n)) / OC.TOBS
+    r = np.empty((nw, 2, n), np.complex64)
+    want = np.empty(nw)
+    for w, scale in enumerate((0.7, 1.0, 1.3)):
+        s = OP.psd_ae(f, psdp[w, 0], psdp[w, 1])
+        r[w] = (scale * synth.unit_complex_normal(g, (2, n)) * np.sqrt(s / (4 * OC.DF))).astype(np.complex64)
+        want[w] = LK.loglike(r[w].astype(np.complex128), s, OC.DF)
+    rt = torch.from_numpy(r).view(torch.float32).reshape(nw, 2, n, 2).contiguous().to(dev)
+    got = torch.full((nw,), float("nan"), dtype=torch.float64, device=dev)
+    for _ in range(2):   # twice in a row: the shared scratch keeps the first call's contents
+        L.total_loglike_noalloc(OC.TOBS, k0, n, rt, torch.from_numpy(psdp).to(dev), got)
+        torch.cuda.synchronize()
+        err = np.abs(got.cpu().numpy() - want)
+        assert np.max(err) < 5e-3, (err, want)
+
+
 def test_noalloc_rejects_sizes_beyond_its_fixed_scratch():
+    # correctly sized inputs that still exceed what the fixed array or the launch grid takes:
+    # the call must refuse them with GBK_ERANGE before any kernel runs
     torch = torch_cuda()
     from paper_2405_04690_gb300 import _lib as L
     dev = torch.device("cuda")
     cap = L.lib().total_loglike_noalloc_capacity()
-    n = 4096 * 64
-    nw = cap // (64 * 2) + 1            # one walker more than the array holds
-    r = torch.zeros((1, 2, 8, 2), dtype=torch.float32, device=dev)
+    n = cap + 1                                     # the shape tables alone exceed the array
+    tobs = 4 * OC.TOBS                              # keeps 3146 + n bins below f = c / (2L)
+    r = torch.zeros((1, 2, n, 2), dtype=torch.float32, device=dev)
+    pt = torch.ones((1, 2), dtype=torch.float64, device=dev)
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    with pytest.raises(L.GbkError) as ei:
+        L.total_loglike_noalloc(tobs, 3146, n, r, pt, out)
+    assert ei.value.status == 2
+    nw = 65536 * 8                                  # one walker group more than the grid holds
+    r = torch.zeros((nw, 2, 1, 2), dtype=torch.float32, device=dev)
     pt = torch.ones((nw, 2), dtype=torch.float64, device=dev)
     out = torch.zeros(nw, dtype=torch.float64, device=dev)
     with pytest.raises(L.GbkError) as ei:
-        L.total_loglike_noalloc(OC.TOBS, 3146, n, r, pt, out)
+        L.total_loglike_noalloc(OC.TOBS, 3146, 1, r, pt, out)
     assert ei.value.status == 2
