@@ -596,7 +596,7 @@ gbk_status gb_sweep_features(gbk_sweep* plan, const double* params, const uint8_
  * Its scratch (the float32 shape tables and the cross-block partial sums) is a fixed array
  * of total_loglike_noalloc_capacity() doubles (16 MiB) in the library's device memory, held
  * on every device that loads the library until the process exits. A call needs
- * n_bins + 2 W ceil(n_bins / 4096) + ceil(n_bins / 256) doubles and W <= 524280; larger
+ * n_bins + 2 W ceil(n_bins / 4096) + ceil(n_bins / 4096) doubles and W <= 262140; larger
  * requests return GBK_ERANGE. Every call overwrites all the scratch it reads, so earlier
  * contents do not matter; but all calls share the one array, so calls that overlap on the
  * GPU (different streams, or host threads without ordering) race and give wrong results:

@@ -26,20 +26,25 @@ __global__ void k_psd_eval(const double* __restrict__ q, const double* __restric
   }
 }
 
-// One block: bins [chunk * kTlChunk, +kTlChunk) of walkers [w0, w0 + kTlWalkers).
-// Per bin k and walker w (u = 1 + a_w rho_k, iq_k = 2^-128 / Q_k):
-//   q-term (|R_A|^2 + |R_E|^2) 2^128 iq_k / u,   l-term ln u.
-// Writes compensated block sums to part[(chunk * nwl + wl) * 2 + {0, 1}].
+// One block: bins [chunk * kTlChunk, +kTlChunk) of walkers wg .. wg + kTlWalkers - 1 (local to
+// the launch, wg = (g0 + blockIdx.y) kTlWalkers). Per bin k and walker w (u = 1 + a_w rho_k,
+// iq_k = 2^-128 / Q_k): q-term (|R_A|^2 + |R_E|^2) 2^128 iq_k / u, l-term ln u. Writes
+// compensated block sums to part[(chunk * nwl + wl) * 2 + {0, 1}].
+// FULL: all kTlWalkers walkers present and n_bins even, so each thread takes pairs of bins
+// with 16-byte loads, and the two bins of a pair share one reciprocal and one logarithm:
+//   m0 iq0 / u0 + m1 iq1 / u1 = (m0 iq0 u1 + m1 iq1 u0) / (u0 u1),  ln u0 + ln u1 = ln(u0 u1).
+// Otherwise (the last, partial walker group, or odd n_bins) one bin at a time.
+template <bool FULL>
 __global__ void __launch_bounds__(kTlThreads, 3)
 k_total_loglike_part(const float* __restrict__ R, const float* __restrict__ iq, const float* __restrict__ rho,
-                     const double* __restrict__ pp, int32_t w0, int32_t nwl, int64_t nb, double* __restrict__ part) {
+                     const double* __restrict__ pp, int32_t w0, int32_t nwl, int32_t g0, int64_t nb,
+                     double* __restrict__ part) {
   const int chunk = blockIdx.x;
-  const int wg = blockIdx.y * kTlWalkers;  // local walker offset within this launch
+  const int wg = (g0 + blockIdx.y) * kTlWalkers;
   const int64_t kbeg = (int64_t)chunk * kTlChunk;
   const int64_t kend = min(kbeg + (int64_t)kTlChunk, nb);
-  // per-walker a = S_acc / S_oms as a float pair hi + lo, once per block: u = 1 + a rho is
-  // formed as (1 + hi rho) + lo rho, so the float rounding of a (the same in every bin of the
-  // walker) does not bias the sum of ln u
+  const int nact = FULL ? kTlWalkers : min(kTlWalkers, nwl - wg);
+  // per-walker a = S_acc / S_oms as a float pair hi + lo, once per block (see one_plus)
   __shared__ float s_aw[kTlWalkers][2];
   if (threadIdx.x < kTlWalkers) {
     const int wl = wg + threadIdx.x;
@@ -50,63 +55,55 @@ k_total_loglike_part(const float* __restrict__ R, const float* __restrict__ iq, 
     s_aw[threadIdx.x][1] = (float)(a - (double)(float)a);
   }
   __syncthreads();
-  float aw[kTlWalkers];
-  bool act[kTlWalkers];
+  float aw[kTlWalkers], awl[kTlWalkers];
 #pragma unroll
   for (int j = 0; j < kTlWalkers; ++j) {
-    act[j] = wg + j < nwl;
     aw[j] = s_aw[j][0];
+    awl[j] = s_aw[j][1];
   }
-  // the lo parts stay in shared memory (read per use): in registers they would spill
-  volatile const float* awl = &s_aw[0][1];
   const float* rbase = R + (int64_t)(w0 + wg) * 2 * nb * 2;
   CompF sq[kTlWalkers], sl[kTlWalkers];
+  int ecnt[kTlWalkers];   // sums of the binary exponents of u (ln u = e ln 2 + ln m)
 #pragma unroll
-  for (int j = 0; j < kTlWalkers; ++j) { sq[j].init(); sl[j].init(); }
+  for (int j = 0; j < kTlWalkers; ++j) { sq[j].init(); sl[j].init(); ecnt[j] = 0; }
   const float up = 18446744073709551616.0f;  // 2^64
-  const bool even = (nb & 1) == 0;
-  for (int64_t k = kbeg + 2 * threadIdx.x; k < kend; k += 2 * kTlThreads) {
-    if (even && k + 1 < kend) {
+  if (FULL) {
+    for (int64_t k = kbeg + 2 * threadIdx.x; k < kend; k += 2 * kTlThreads) {
       const float2 iq2 = __ldg(reinterpret_cast<const float2*>(iq + k));
       const float2 rh2 = __ldg(reinterpret_cast<const float2*>(rho + k));
       float4 a[kTlWalkers], e[kTlWalkers];
 #pragma unroll
       for (int j = 0; j < kTlWalkers; ++j) {
-        if (act[j]) {
-          const float* rw = rbase + (int64_t)j * 2 * nb * 2;
-          a[j] = __ldcs(reinterpret_cast<const float4*>(rw + 2 * k));
-          e[j] = __ldcs(reinterpret_cast<const float4*>(rw + 2 * (nb + k)));
-        }
+        const float* rw = rbase + (int64_t)j * 2 * nb * 2;
+        a[j] = __ldcs(reinterpret_cast<const float4*>(rw + 2 * k));
+        e[j] = __ldcs(reinterpret_cast<const float4*>(rw + 2 * (nb + k)));
       }
+      // |R|^2 summed unscaled and times 2^64 once, iq times 2^64 once per bin (exact scalings)
+      const float iq0 = iq2.x * up, iq1 = iq2.y * up;
 #pragma unroll
       for (int j = 0; j < kTlWalkers; ++j) {
-        if (!act[j]) continue;
-        const float lo = awl[2 * j];
-        const float u0 = fmaf(lo, rh2.x, fmaf(aw[j], rh2.x, 1.0f));
-        const float u1 = fmaf(lo, rh2.y, fmaf(aw[j], rh2.y, 1.0f));
-        const float ax = a[j].x * up, ay = a[j].y * up, az = a[j].z * up, aww = a[j].w * up;
-        const float ex = e[j].x * up, ey = e[j].y * up, ez = e[j].z * up, ew = e[j].w * up;
-        const float m0 = ax * ax + ay * ay + ex * ex + ey * ey;
-        const float m1 = az * az + aww * aww + ez * ez + ew * ew;
-        sq[j].add(m0 * iq2.x * __frcp_rn(u0));
-        sq[j].add(m1 * iq2.y * __frcp_rn(u1));
-        sl[j].add(logf(u0));
-        sl[j].add(logf(u1));
+        const float u0 = one_plus(aw[j], awl[j], rh2.x);
+        const float u1 = one_plus(aw[j], awl[j], rh2.y);
+        const float4 A = a[j], E = e[j];
+        const float m0 = (A.x * A.x + A.y * A.y + E.x * E.x + E.y * E.y) * up;
+        const float m1 = (A.z * A.z + A.w * A.w + E.z * E.z + E.w * E.w) * up;
+        const float uu = u0 * u1;
+        sq[j].add(fmaf(m0 * iq0, u1, m1 * iq1 * u0) * __frcp_rn(uu));
+        sl[j].add(log_split(uu, ecnt[j]));
       }
-    } else {
-      for (int64_t kk = k; kk < min(k + 2, kend); ++kk) {
-        const float iqk = __ldg(iq + kk), rhk = __ldg(rho + kk);
+    }
+  } else {
+    for (int64_t k = kbeg + threadIdx.x; k < kend; k += kTlThreads) {
+      const float iqk = __ldg(iq + k) * up, rhk = __ldg(rho + k);
 #pragma unroll
-        for (int j = 0; j < kTlWalkers; ++j) {
-          if (!act[j]) continue;
-          const float* rw = rbase + (int64_t)j * 2 * nb * 2;
-          const float2 a = *reinterpret_cast<const float2*>(rw + 2 * kk);
-          const float2 e = *reinterpret_cast<const float2*>(rw + 2 * (nb + kk));
-          const float u = fmaf(awl[2 * j], rhk, fmaf(aw[j], rhk, 1.0f));
-          const float ax = a.x * up, ay = a.y * up, ex = e.x * up, ey = e.y * up;
-          sq[j].add((ax * ax + ay * ay + ex * ex + ey * ey) * iqk * __frcp_rn(u));
-          sl[j].add(logf(u));
-        }
+      for (int j = 0; j < kTlWalkers; ++j) {
+        if (j >= nact) break;
+        const float* rw = rbase + (int64_t)j * 2 * nb * 2;
+        const float2 a = *reinterpret_cast<const float2*>(rw + 2 * k);
+        const float2 e = *reinterpret_cast<const float2*>(rw + 2 * (nb + k));
+        const float u = one_plus(aw[j], awl[j], rhk);
+        sq[j].add((a.x * a.x + a.y * a.y + e.x * e.x + e.y * e.y) * up * iqk * __frcp_rn(u));
+        sl[j].add(log_split(u, ecnt[j]));
       }
     }
   }
@@ -115,18 +112,33 @@ k_total_loglike_part(const float* __restrict__ R, const float* __restrict__ iq, 
 #pragma unroll
   for (int j = 0; j < kTlWalkers; ++j) {
     const double tq = sq[j].warp_total();
-    const double tl = sl[j].warp_total();
+    const double tl = sl[j].warp_total() + kLn2 * (double)__reduce_add_sync(0xffffffffu, ecnt[j]);
     if (lane == 0) { red[wid][j][0] = tq; red[wid][j][1] = tl; }
   }
   __syncthreads();
   if (threadIdx.x < kTlWalkers * 2) {
     const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
-    if (wg + j < nwl) {
+    if (j < nact) {
       double s = 0.0;
       for (int w = 0; w < kTlThreads / 32; ++w) s += red[w][j][which];
       part[((int64_t)chunk * nwl + wg + j) * 2 + which] = s;
     }
   }
+}
+
+// The block passes of nwl walkers (w0 .. w0 + nwl - 1) over n_bins bins into part [chunk][nwl][2]:
+// the full walker groups with the pair loop when n_bins is even, the rest one bin at a time.
+gbk_status total_loglike_parts(const float* R, const float* iq, const float* rho, const double* pp, int32_t w0,
+                               int32_t nwl, int64_t nb, double* part, cudaStream_t st) {
+  const int nchunks = (int)((nb + kTlChunk - 1) / kTlChunk);
+  const int full = (nb & 1) == 0 && ((uintptr_t)R & 15) == 0 ? nwl / kTlWalkers : 0;
+  const int groups = (nwl + kTlWalkers - 1) / kTlWalkers;
+  if (full > 0)
+    k_total_loglike_part<true><<<dim3(nchunks, full), kTlThreads, 0, st>>>(R, iq, rho, pp, w0, nwl, 0, nb, part);
+  if (groups > full)
+    k_total_loglike_part<false><<<dim3(nchunks, groups - full), kTlThreads, 0, st>>>(R, iq, rho, pp, w0, nwl, full,
+                                                                                     nb, part);
+  return check_launch("total_loglike");
 }
 
 // Sum the chunk partials of each walker in chunk order and assemble Eq. like.
@@ -171,15 +183,14 @@ extern "C" gbk_status total_loglike(gbk_ctx* ctx, const float* residual, const d
   if (n_walkers < 0) return set_error(GBK_EINVAL, "total_loglike: n_walkers < 0");
   if (n_walkers == 0) return GBK_OK;
   if (!residual || !psd_params || !logl) return set_error(GBK_EINVAL, "total_loglike: null device pointer");
-  if (((uintptr_t)residual & 15) != 0) return set_error(GBK_EINVAL, "total_loglike: residual must be 16-byte aligned");
+  if (((uintptr_t)residual & 7) != 0) return set_error(GBK_EINVAL, "total_loglike: residual must be 8-byte aligned");
   const int64_t nb = ctx->grid.n_bins;
   const int nchunks = (int)((nb + kTlChunk - 1) / kTlChunk);
   cudaStream_t st = (cudaStream_t)stream;
   for (int32_t w0 = 0; w0 < n_walkers; w0 += kTlMaxW) {
     const int32_t nwl = n_walkers - w0 < kTlMaxW ? n_walkers - w0 : kTlMaxW;
-    dim3 grid(nchunks, (nwl + kTlWalkers - 1) / kTlWalkers);
-    k_total_loglike_part<<<grid, kTlThreads, 0, st>>>(residual, ctx->iq_f, ctx->rho_f, psd_params, w0, nwl, nb,
-                                                       ctx->scratch);
+    gbk_status s = total_loglike_parts(residual, ctx->iq_f, ctx->rho_f, psd_params, w0, nwl, nb, ctx->scratch, st);
+    if (s) return s;
     k_total_loglike_final<<<(nwl + 127) / 128, 128, 0, st>>>(ctx->scratch, nchunks, psd_params, w0, nwl, nb,
                                                             1.0 / ctx->grid.tobs, ctx->sum_lnq, logl);
   }

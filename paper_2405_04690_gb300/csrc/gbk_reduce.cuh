@@ -39,6 +39,22 @@ struct CompF {
   }
 };
 
+// u = 1 + a rho for a PSD ratio a = S_acc / S_oms held as a float pair ah + al: the small term
+// al rho enters before the product a rho is rounded, so the float rounding of a (the same in
+// every bin of a walker) leaves no error common to all bins; what remains is random per bin.
+__device__ __forceinline__ float one_plus(float ah, float al, float rho) { return 1.0f + fmaf(ah, rho, al * rho); }
+
+// ln u for u >= 1, split as e ln 2 + ln m with m in [1, 2): returns ln m and adds the integer e
+// to `e`. ln m < 0.7 keeps the float rounding of the returned part below 6e-8, where ln u itself
+// (up to ~8 at low frequencies) would carry up to 5e-7 per bin, enough to add up to ~1e-2 over
+// 2^20 bins; the caller multiplies the integer sum of e by ln 2 in float64.
+__device__ __forceinline__ float log_split(float u, int& e) {
+  const int bits = __float_as_int(u);
+  e += (bits >> 23) - 127;
+  return logf(__int_as_float((bits & 0x007fffff) | 0x3f800000));
+}
+constexpr double kLn2 = 0.6931471805599453094;
+
 struct PlainD {
   double s;
   __device__ __forceinline__ void init() { s = 0.0; }

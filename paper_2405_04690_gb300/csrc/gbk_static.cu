@@ -17,9 +17,8 @@
 
 namespace gbk {
 
-constexpr int kStThreads = 256;
-constexpr int kStChunk = 4096;                   // bins per block of the likelihood pass
-constexpr int kStWalkers = 8;                    // walkers per block
+constexpr int kStChunk = 4096;                   // bins per block of the likelihood pass (total_loglike_parts)
+constexpr int kStWalkers = 4;                    // walkers per block of that pass
 constexpr int kStShapeThreads = 256;             // bins per block of the shape pass
 constexpr int64_t kStScratchDoubles = 1 << 21;   // 16 MiB
 
@@ -31,28 +30,55 @@ static __device__ __align__(256) double g_static_scratch[kStScratchDoubles];
 
 // Eq. psd split by noise power, S_n = S_oms Q(f) + S_acc P(f), in float64 with float64
 // constants (as the context's tables are built): per bin iq = 2^-128 / Q and rho = P / Q
-// rounded once to float32, and the float64 sum of ln Q over the block's bins.
+// rounded once to float32, and the float64 sum of ln Q over the block's bins. Float64 runs at
+// a small fraction of the float32 rate here, so each thread takes kStRun consecutive bins and
+// spends few float64 operations per bin: (sin x, cos x) advance by a rotation through the bin
+// spacing of x, 1 / f and 1 / Q come from a float32 reciprocal refined by two Newton steps,
+// and ln Q is summed as the log of a product of mantissas plus the sum of binary exponents.
+constexpr int kStRun = 16;
+__device__ __forceinline__ double recip_nr(double v) {
+  double y = (double)__frcp_rn((float)v);
+  y = y * (2.0 - v * y);
+  return y * (2.0 - v * y);
+}
+
 __global__ void __launch_bounds__(kStShapeThreads)
-k_static_shape(double tobs, int64_t k0, int64_t nb, float* __restrict__ iq, float* __restrict__ rho,
-               double* __restrict__ lnq_part) {
-  const int64_t k = (int64_t)blockIdx.x * kStShapeThreads + threadIdx.x;
+k_static_shape(double tobs, int64_t k0, int64_t nb, double ck, double sk, float* __restrict__ iq,
+               float* __restrict__ rho, double* __restrict__ lnq_part) {
+  const int64_t kfirst = ((int64_t)blockIdx.x * kStShapeThreads + threadIdx.x) * kStRun;
   double lq = 0.0;
-  if (k < nb) {
-    const double f = (double)(k0 + k) / tobs;
-    const double x = 2.0 * 3.141592653589793 * f * kLc;
+  if (kfirst < nb) {
+    const double two_pi = 6.283185307179586;
     double sx, cx;
-    sincos(x, &sx, &cx);
-    const double c2x = 2.0 * cx * cx - 1.0;
-    const double tpcf = 2.0 * 3.141592653589793 * kC * f;
-    const double a = 0.4e-3 / f, bq = f / 8e-3, o = 2e-3 / f, tpfc = 2.0 * 3.141592653589793 * f / kC;
-    const double pm_unit = (1.0 + a * a) * (1.0 + bq * bq * bq * bq) / (tpcf * tpcf);
-    const double op_unit = tpfc * tpfc * (1.0 + o * o * o * o);
-    const double s2 = 8.0 * sx * sx;
-    const double p = s2 * 2.0 * pm_unit * (3.0 + 2.0 * cx + c2x);
-    const double q = s2 * op_unit * (2.0 + cx);
-    iq[k] = (float)(2.9387358770557188e-39 / q);   // 2^-128 / Q
-    rho[k] = (float)(p / q);
-    lq = log(q);
+    sincos(two_pi * ((double)(k0 + kfirst) / tobs) * kLc, &sx, &cx);
+    double prod = 1.0;
+    int esum = 0;
+    const int64_t kend = min(kfirst + (int64_t)kStRun, nb);
+    for (int64_t k = kfirst; k < kend; ++k) {
+      const double kk = (double)(k0 + k);
+      const double f = kk / tobs;
+      const double inv_f = tobs * recip_nr(kk);
+      const double c2x = 2.0 * cx * cx - 1.0;
+      const double tpcf = two_pi * kC * f;
+      const double a = 0.4e-3 * inv_f, bq = f * (1.0 / 8e-3), o = 2e-3 * inv_f, tpfc = two_pi * f / kC;
+      const double a2 = a * a, bq2 = bq * bq, o2 = o * o;
+      const double inv_tpcf = recip_nr(tpcf);
+      const double pm_unit = (1.0 + a2) * (1.0 + bq2 * bq2) * (inv_tpcf * inv_tpcf);
+      const double op_unit = tpfc * tpfc * (1.0 + o2 * o2);
+      const double s2 = 8.0 * sx * sx;
+      const double p = s2 * 2.0 * pm_unit * (3.0 + 2.0 * cx + c2x);
+      const double q = s2 * op_unit * (2.0 + cx);
+      const double iqd = recip_nr(q);
+      iq[k] = (float)(2.9387358770557188e-39 * iqd);   // 2^-128 / Q
+      rho[k] = (float)(p * iqd);
+      int e;
+      prod *= frexp(q, &e);
+      esum += e;
+      const double sn = sx * ck + cx * sk;             // x advances by one bin
+      cx = cx * ck - sx * sk;
+      sx = sn;
+    }
+    lq = log(prod) + 0.6931471805599453094 * (double)esum;
   }
   for (int o = 16; o > 0; o >>= 1) lq += __shfl_xor_sync(0xffffffffu, lq, o);
   __shared__ double red[kStShapeThreads / 32];
@@ -62,65 +88,6 @@ k_static_shape(double tobs, int64_t k0, int64_t nb, float* __restrict__ iq, floa
     double t = 0.0;
     for (int w = 0; w < kStShapeThreads / 32; ++w) t += red[w];
     lnq_part[blockIdx.x] = t;
-  }
-}
-
-__global__ void __launch_bounds__(kStThreads)
-k_static_part(int64_t nb, const float* __restrict__ R, const double* __restrict__ pp, int32_t nwl,
-              const float* __restrict__ iqt, const float* __restrict__ rhot, double* __restrict__ part) {
-  const int chunk = blockIdx.x;
-  const int wg = blockIdx.y * kStWalkers;
-  const int64_t kbeg = (int64_t)chunk * kStChunk;
-  const int64_t kend = min(kbeg + (int64_t)kStChunk, nb);
-  // a = S_acc / S_oms as a float pair hi + lo (u = (1 + hi rho) + lo rho): the rounding of
-  // a, the same in every bin of a walker, would otherwise bias the sum of ln u
-  float aw[kStWalkers], awl[kStWalkers];
-  const float* rw[kStWalkers];
-  bool act[kStWalkers];
-#pragma unroll
-  for (int j = 0; j < kStWalkers; ++j) {
-    const int w = wg + j;
-    act[j] = w < nwl;
-    const int ww = act[j] ? w : 0;
-    const double so = pp[2 * ww] * pp[2 * ww], sa = pp[2 * ww + 1] * pp[2 * ww + 1];
-    const double a = sa / so;
-    aw[j] = (float)a;
-    awl[j] = (float)(a - (double)aw[j]);
-    rw[j] = R + (int64_t)ww * 2 * nb * 2;
-  }
-  CompF sq[kStWalkers], sl[kStWalkers];
-#pragma unroll
-  for (int j = 0; j < kStWalkers; ++j) { sq[j].init(); sl[j].init(); }
-  const float up = 18446744073709551616.0f;  // 2^64
-  for (int64_t k = kbeg + threadIdx.x; k < kend; k += kStThreads) {
-    const float iq = __ldg(iqt + k), rh = __ldg(rhot + k);
-#pragma unroll
-    for (int j = 0; j < kStWalkers; ++j) {
-      if (!act[j]) continue;
-      const float2 a = *reinterpret_cast<const float2*>(rw[j] + 2 * k);
-      const float2 e = *reinterpret_cast<const float2*>(rw[j] + 2 * (nb + k));
-      const float u = fmaf(awl[j], rh, fmaf(aw[j], rh, 1.0f));
-      const float ax = a.x * up, ay = a.y * up, ex = e.x * up, ey = e.y * up;
-      sq[j].add((ax * ax + ay * ay + ex * ex + ey * ey) * iq * __frcp_rn(u));
-      sl[j].add(logf(u));
-    }
-  }
-  __shared__ double red[kStThreads / 32][kStWalkers][2];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < kStWalkers; ++j) {
-    const double tq = sq[j].warp_total();
-    const double tl = sl[j].warp_total();
-    if (lane == 0) { red[wid][j][0] = tq; red[wid][j][1] = tl; }
-  }
-  __syncthreads();
-  if (threadIdx.x < kStWalkers * 2) {
-    const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
-    if (wg + j < nwl) {
-      double s = 0.0;
-      for (int w = 0; w < kStThreads / 32; ++w) s += red[w][j][which];
-      part[((int64_t)chunk * nwl + wg + j) * 2 + which] = s;
-    }
   }
 }
 
@@ -180,7 +147,7 @@ extern "C" gbk_status total_loglike_noalloc(double tobs, int64_t k0, int64_t n_b
   if (!residual || !psd_params || !logl) return set_error(GBK_EINVAL, "total_loglike_noalloc: null device pointer");
   if (((uintptr_t)residual & 7) != 0) return set_error(GBK_EINVAL, "total_loglike_noalloc: residual must be 8-byte aligned");
   const int64_t nchunks = (n_bins + kStChunk - 1) / kStChunk;
-  const int64_t nshape = (n_bins + kStShapeThreads - 1) / kStShapeThreads;
+  const int64_t nshape = (n_bins + kStShapeThreads * kStRun - 1) / (kStShapeThreads * kStRun);
   const int64_t ngroups = ((int64_t)n_walkers + kStWalkers - 1) / kStWalkers;
   if (ngroups > 65535)
     return set_error(GBK_ERANGE, "total_loglike_noalloc: %lld walkers exceed the %d the launch grid takes",
@@ -198,9 +165,10 @@ extern "C" gbk_status total_loglike_noalloc(double tobs, int64_t k0, int64_t n_b
   double* part = scratch + n_bins;
   double* lnq_part = part + nchunks * (int64_t)n_walkers * 2;
   cudaStream_t st = (cudaStream_t)stream;
-  k_static_shape<<<(unsigned)nshape, kStShapeThreads, 0, st>>>(tobs, k0, n_bins, iq, rho, lnq_part);
-  dim3 grid((unsigned)nchunks, (unsigned)ngroups);
-  k_static_part<<<grid, kStThreads, 0, st>>>(n_bins, residual, psd_params, n_walkers, iq, rho, part);
+  const double dx = 6.283185307179586 * kLc / tobs;   // x = 2 pi f L / c advances by dx per bin
+  k_static_shape<<<(unsigned)nshape, kStShapeThreads, 0, st>>>(tobs, k0, n_bins, cos(dx), sin(dx), iq, rho, lnq_part);
+  s = total_loglike_parts(residual, iq, rho, psd_params, 0, n_walkers, n_bins, part, st);
+  if (s) return s;
   k_static_final<<<(n_walkers + 127) / 128, 128, 0, st>>>(part, (int)nchunks, lnq_part, (int)nshape, psd_params,
                                                           n_walkers, n_bins, 1.0 / tobs, logl);
   return check_launch("total_loglike_noalloc");

@@ -97,7 +97,7 @@ def test_noalloc_rejects_sizes_beyond_its_fixed_scratch():
     with pytest.raises(L.GbkError) as ei:
         L.total_loglike_noalloc(tobs, 3146, n, r, pt, out)
     assert ei.value.status == 2
-    nw = 65536 * 8                                  # one walker group more than the grid holds
+    nw = 65535 * 4 + 1                              # one walker more than the launch grid holds
     r = torch.zeros((nw, 2, 1, 2), dtype=torch.float32, device=dev)
     pt = torch.ones((nw, 2), dtype=torch.float64, device=dev)
     out = torch.zeros(nw, dtype=torch.float64, device=dev)
