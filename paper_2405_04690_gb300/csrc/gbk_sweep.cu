@@ -42,6 +42,7 @@ struct gbk_sweep {
   int n_friends;
   int32_t* swap_acc;        // accepted swaps of the last sweep per band and rung [B][T]
   int32_t* xfer_dest;       // ownership transfer: destination (band n_max + slot) of every cold slot, or -1
+  unsigned long long* task_ctr;   // next band task of the band kernel, one counter per parity
 };
 
 namespace gbk {
@@ -87,6 +88,7 @@ struct SweepArgs {
   int gmax, n_friends;
   double grp_frac;
   int32_t* swap_acc;      // [B][T] accepted swaps between rungs t-1 and t
+  unsigned long long* task_ctr;   // [2] next band task of the band kernel (zeroed before each launch)
 };
 
 template <typename T> __device__ __forceinline__ const T* orb_of(const gbk_ctx& c, int bi);
@@ -633,22 +635,34 @@ __device__ __noinline__ void write_hsum(const SweepArgs& a, int t, int w, int b,
   if (lane + 32 < d.n_max && a.exists[base + lane + 32]) off1 = cached_off<N>(a.params + (base + lane + 32) * 8, gw, a.c);
   const unsigned p0 = __ballot_sync(0xffffffffu, off0 >= 0);
   const unsigned p1 = __ballot_sync(0xffffffffu, off1 >= 0);
-  for (int i = lane; i < W3; i += 32) {
-    C xa = mkc((T)0, (T)0), xe = xa;
+  // G window bins per lane at a time: for each slot (in slot order) the loads of all G bins
+  // are issued together, then added
+  constexpr int G = 4;
+#pragma unroll 1
+  for (int i0 = lane; i0 < W3; i0 += 32 * G) {
+    C xa[G], xe[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) xa[u] = xe[u] = mkc((T)0, (T)0);
     for (int half = 0; half < 2; ++half) {
       for (unsigned m = half ? p1 : p0; m; m &= m - 1) {
         const int sl = __ffs(m) - 1;
         const int o = __shfl_sync(0xffffffffu, half ? off1 : off0, sl);
-        const int j = i - o;
-        if (j >= 0 && j < N) {
-          const C* h = cache_ptr<T>(a, cb + sl + 32 * half);
-          xa = cadd(xa, h[j]);
-          xe = cadd(xe, h[N + j]);
+        const C* h = cache_ptr<T>(a, cb + sl + 32 * half);
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+          const int j = i0 + 32 * u - o;
+          if (j >= 0 && j < N) {
+            xa[u] = cadd(xa[u], h[j]);
+            xe[u] = cadd(xe[u], h[N + j]);
+          }
         }
       }
     }
-    H[i] = xa;
-    H[W3 + i] = xe;
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      H[i0 + 32 * u] = xa[u];
+      H[W3 + i0 + 32 * u] = xe[u];
+    }
   }
   __syncwarp();
 }
@@ -959,7 +973,13 @@ __global__ void __launch_bounds__(kBandWarps * 32, kBandMinCtas) k_band(const Sw
   WarpStats ws;
   ws.init();
   const PriorK pk = prior_consts(d);
-  for (int64_t x = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; x < ntask; x += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+  // band tasks taken one at a time from a counter: tasks differ in cost (sources, accepted
+  // moves), and a fixed share per warp leaves the launch waiting for its slowest warps
+  for (;;) {
+    int64_t x = 0;
+    if (lane == 0) x = (int64_t)atomicAdd(a.task_ctr + a.parity, 1ull);
+    x = __shfl_sync(0xffffffffu, x, 0);
+    if (x >= ntask) break;
     const int t = (int)(x / ((int64_t)d.n_walkers * nbp));
     const int rem = (int)(x % ((int64_t)d.n_walkers * nbp));
     const int w = rem / nbp, j = rem % nbp;
@@ -980,6 +1000,7 @@ __global__ void __launch_bounds__(kBandWarps * 32, kBandMinCtas) k_band(const Sw
     // minus their own (cached) templates
     if (cold) {
       const long long* rs_w = a.rsnap + (int64_t)w * 2 * nb * 2;
+#pragma unroll 4
       for (int i = lane; i < W3; i += 32)
         for (int ch = 0; ch < 2; ++ch) {
           const longlong2 v = *reinterpret_cast<const longlong2*>(rs_w + 2 * (ch * nb + gw + i));
@@ -989,6 +1010,7 @@ __global__ void __launch_bounds__(kBandWarps * 32, kBandMinCtas) k_band(const Sw
     } else {
       const C* rho = rho_ptr<T>(a, w, j);
       const C* H = hsum_ptr<T>(a, t, w, b);
+#pragma unroll 4
       for (int i = lane; i < 2 * W3; i += 32) rw[i] = csub(rho[i], H[i]);
       __syncwarp();
     }
@@ -1467,6 +1489,8 @@ static gbk_status run_half(SweepArgs& a, int flags, cudaStream_t st) {
                   kBandWarps)))
       return s;
     ev_rec(a.parity, 2, 0, st);
+    if (cudaMemsetAsync(a.task_ctr + a.parity, 0, sizeof(unsigned long long), st) != cudaSuccess)
+      return set_error(GBK_ECUDA, "gb_sweep: task counter reset failed");
     k_band<T, N><<<grid, thr, sm, st>>>(a, flags);
     ev_rec(a.parity, 2, 1, st);
     if ((s = check_launch("gb_sweep(band)"))) return s;
@@ -1550,6 +1574,7 @@ extern "C" gbk_status gbk_sweep_create(gbk_ctx* ctx, const gbk_sweep_desc* desc,
   if (e == cudaSuccess) e = cudaMemset(p->swap_acc, 0, (size_t)d.n_bands * d.n_temps * sizeof(int32_t));
   if (e == cudaSuccess)
     e = cudaMalloc((void**)&p->xfer_dest, (size_t)d.n_walkers * d.n_bands * (d.n_max > 0 ? d.n_max : 1) * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->task_ctr, 2 * sizeof(unsigned long long));
   if (e != cudaSuccess) {
     cudaFree(p->rsnap);
     cudaFree(p->rho);
@@ -1558,6 +1583,7 @@ extern "C" gbk_status gbk_sweep_create(gbk_ctx* ctx, const gbk_sweep_desc* desc,
     cudaFree(p->setid);
     cudaFree(p->rwbuf);
     cudaFree(p->swap_acc);
+    cudaFree(p->xfer_dest);
     cudaFree(p->xfer_dest);
     free(p);
     cudaGetLastError();
@@ -1579,6 +1605,7 @@ extern "C" gbk_status gbk_sweep_destroy(gbk_sweep* plan) {
   cudaFree(plan->rwbuf);
   cudaFree(plan->swap_acc);
   cudaFree(plan->xfer_dest);
+  cudaFree(plan->task_ctr);
   cudaFree(plan->mix);
   cudaFree(plan->grp_f0);
   cudaFree(plan->grp_par);
@@ -1635,6 +1662,7 @@ static SweepArgs make_args(gbk_sweep* plan, double* params, uint8_t* exists, con
   a.hsum = plan->hsum;
   a.setid = plan->setid;
   a.rwbuf = plan->rwbuf;
+  a.task_ctr = plan->task_ctr;
   a.n_bp_max = plan->n_bp_max;
   a.n_walkers_r = residual->n_walkers;
   a.frac_bits = residual->frac_bits;
