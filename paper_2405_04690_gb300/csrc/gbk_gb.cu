@@ -139,6 +139,48 @@ __device__ __forceinline__ void acc_bin(const gbk_ctx& c, const long long* __res
   srd.add(w * (rax * da.x + ray * da.y + rex * de.x + rey * de.y));
 }
 
+// Delta lnL of proposal (a in ba at window offset ka, r in br at kr; either may be absent)
+// against walker w's residual, by the 32 lanes of one warp: lane l sums the bins l, l + 32, ...
+// of each band in order (the same summation in every kernel that calls it).
+template <typename T>
+__device__ __forceinline__ void eval_pair(const gbk_ctx& c, const typename CT<T>::C* ba, const typename CT<T>::C* br,
+                                          bool za, bool zr, int64_t ka, int64_t kr, int nbi, int w,
+                                          const long long* __restrict__ resid, int32_t frac_bits,
+                                          const double* __restrict__ psdp, int32_t npsd, int lane, double* out) {
+  typedef typename CT<T>::C C;
+  const int64_t nbins = c.grid.n_bins;
+  const T rscale = (T)ldexp(1.0, kStrainExp - frac_bits);
+  const PsdW<T> pw = psd_walker<T>(c, psdp, npsd, w);
+  const long long* rw = resid + (int64_t)w * 2 * nbins * 2;
+  typename Acc<T>::S sdd, srd;
+  sdd.init();
+  srd.init();
+  const C zero = mkc((T)0, (T)0);
+  // bins of a's band: D = a - r (r where the bands overlap)
+  if (!za) {
+    for (int j = lane; j < nbi; j += 32) {
+      const int64_t k = ka + j;
+      C ra = zero, re = zero;
+      const int64_t jr = k - kr;
+      if (!zr && jr >= 0 && jr < nbi) { ra = br[jr]; re = br[nbi + jr]; }
+      acc_bin<T>(c, rw, k, csub(ba[j], ra), csub(ba[nbi + j], re), pw.aw, rscale, sdd, srd);
+    }
+  }
+  // bins of r's band outside a's band: D = -r
+  if (!zr) {
+    for (int j = lane; j < nbi; j += 32) {
+      const int64_t k = kr + j;
+      const int64_t ja = k - ka;
+      if (!za && ja >= 0 && ja < nbi) continue;
+      const C ra = br[j], re = br[nbi + j];
+      acc_bin<T>(c, rw, k, mkc(-ra.x, -ra.y), mkc(-re.x, -re.y), pw.aw, rscale, sdd, srd);
+    }
+  }
+  const double dd = sdd.warp_total();
+  const double rd = srd.warp_total();
+  if (lane == 0) *out = pw.cw * (-0.5 * dd + rd);
+}
+
 // Batch of 16 proposals per warp: lanes 0-15 set up the new templates, 16-31 the old.
 template <typename T, int NMAX>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * 32)
@@ -159,7 +201,6 @@ k_dlogl(const gbk_ctx c, const double* __restrict__ pnew, const double* __restri
   const int wpc = blockDim.x >> 5;
   const int64_t stride_w = (int64_t)gridDim.x * wpc * 16;
   const int64_t nbins = c.grid.n_bins;
-  const T rscale = (T)ldexp(1.0, kStrainExp - frac_bits);
   for (int64_t base = ((int64_t)blockIdx.x * wpc + wid) * 16; base < n; base += stride_w) {
     {
       const int l = lane & 15;
@@ -199,38 +240,95 @@ k_dlogl(const gbk_ctx c, const double* __restrict__ pnew, const double* __restri
       }
       if (!za) gen_any<T, NMAX>(c, sa, nbi, ba, bs, lane);
       if (!zr) gen_any<T, NMAX>(c, sr, nbi, br, bs, lane);
-      const PsdW<T> pw = psd_walker<T>(c, psdp, npsd, w);
-      const long long* rw = resid + (int64_t)w * 2 * nbins * 2;
-      typename Acc<T>::S sdd, srd;
-      sdd.init();
-      srd.init();
-      const C zero = mkc((T)0, (T)0);
-      // bins of a's band: D = a - r (r where the bands overlap)
-      if (!za) {
-        for (int j = lane; j < nbi; j += 32) {
-          const int64_t k = ka + j;
-          C ra = zero, re = zero;
-          const int64_t jr = k - kr;
-          if (!zr && jr >= 0 && jr < nbi) { ra = br[jr]; re = br[nbi + jr]; }
-          acc_bin<T>(c, rw, k, csub(ba[j], ra), csub(ba[nbi + j], re), pw.aw, rscale, sdd, srd);
-        }
-      }
-      // bins of r's band outside a's band: D = -r
-      if (!zr) {
-        for (int j = lane; j < nbi; j += 32) {
-          const int64_t k = kr + j;
-          const int64_t ja = k - ka;
-          if (!za && ja >= 0 && ja < nbi) continue;
-          const C ra = br[j], re = br[nbi + j];
-          acc_bin<T>(c, rw, k, mkc(-ra.x, -ra.y), mkc(-re.x, -re.y), pw.aw, rscale, sdd, srd);
-        }
-      }
-      const double dd = sdd.warp_total();
-      const double rd = srd.warp_total();
-      if (lane == 0) dlogl[i] = pw.cw * (-0.5 * dd + rd);
+      eval_pair<T>(c, ba, br, za, zr, ka, kr, nbi, w, resid, frac_bits, psdp, npsd, lane, dlogl + i);
       __syncwarp();
     }
     __syncwarp();
+  }
+}
+
+// Delta lnL for long bands with each waveform generated by a whole block of NT threads: one
+// warp's three band buffers of 1024 bins (48 KB) would leave an SM four warps, the block shares
+// them among NT / 32 warps. Batches of 16 proposals as in k_dlogl: warp 0 sets up the source
+// constants and evaluates the sums with eval_pair, so every result has the same bits as
+// k_dlogl's for the same proposal.
+template <typename T, int NMAX, int NT>
+__device__ __forceinline__ bool gen_any_block(const gbk_ctx& c, const Src<T>* s, int n, typename CT<T>::C* b0,
+                                              typename CT<T>::C* b1, int tid) {
+  const double tobs = c.grid.tobs;
+  switch (n) {
+    case 128: gen_band_block<T, 128, NT>(s, orb_table<T>(c, 0), tw_table<T>(c, 0), tobs, b0, b1, tid); return true;
+    case 256: gen_band_block<T, 256, NT>(s, orb_table<T>(c, 1), tw_table<T>(c, 1), tobs, b0, b1, tid); return true;
+    case 512: gen_band_block<T, 512, NT>(s, orb_table<T>(c, 2), tw_table<T>(c, 2), tobs, b0, b1, tid); return true;
+    case 1024: if (NMAX >= 1024) { gen_band_block<T, 1024, NT>(s, orb_table<T>(c, 3), tw_table<T>(c, 3), tobs, b0, b1, tid); return true; } break;
+    default: break;
+  }
+  return false;
+}
+
+template <typename T, int NMAX>
+constexpr int block_threads() { return NMAX / 8; }   // 8 coarse samples per thread
+
+template <typename T, int NMAX, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT)
+k_dlogl_block(const gbk_ctx c, const double* __restrict__ pnew, const double* __restrict__ pold,
+              const int32_t* __restrict__ nb, const int32_t* __restrict__ walker, int64_t n,
+              const long long* __restrict__ resid, int32_t n_walkers, int32_t frac_bits,
+              const double* __restrict__ psdp, int32_t npsd, double* __restrict__ dlogl) {
+  typedef typename CT<T>::C C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int wid = tid >> 5;
+  C* ba = reinterpret_cast<C*>(smem_raw);
+  C* br = ba + 2 * NMAX;
+  C* bs = br + 2 * NMAX;
+  Src<T>* srcs = reinterpret_cast<Src<T>*>(bs + 2 * NMAX);   // [0,16) new, [16,32) old
+  int* meta = reinterpret_cast<int*>(srcs + 32);            // [0,16) N, [16,32) walker
+  const int64_t nbins = c.grid.n_bins;
+  for (int64_t base = (int64_t)blockIdx.x * 16; base < n; base += (int64_t)gridDim.x * 16) {
+    if (wid == 0) {
+      const int l = lane & 15;
+      const int64_t me = base + l;
+      if (me < n) {
+        const int nbi = nb[me];
+        if (lane < 16) { meta[l] = nbi; meta[16 + l] = walker[me]; }
+        if (nbi <= NMAX && band_index(nbi) >= 0)
+          srcs[lane] = make_src<T>(lane < 16 ? pnew : pold, n, me, c.grid.tobs, nbi);
+      }
+    }
+    __syncthreads();
+    const int cnt = (int)min((int64_t)16, n - base);
+    for (int q = 0; q < cnt; ++q) {
+      const int64_t i = base + q;
+      const int nbi = meta[q];
+      const int w = meta[16 + q];
+      if (nbi > NMAX || band_index(nbi) < 0 || w < 0 || w >= n_walkers || (npsd != 1 && w >= npsd)) {
+        if (tid == 0) {
+          atomicOr(c.err, (w < 0 || w >= n_walkers || (npsd != 1 && w >= npsd)) ? kErrWalker : kErrBand);
+          dlogl[i] = __longlong_as_double(0x7ff8000000000000LL);
+        }
+        continue;
+      }
+      const Src<T>* sa = &srcs[q];
+      const Src<T>* sr = &srcs[16 + q];
+      const bool za = sa->zero, zr = sr->zero;
+      const int64_t ka = sa->q - nbi / 2 - c.grid.k0;
+      const int64_t kr = sr->q - nbi / 2 - c.grid.k0;
+      const bool bad = (!za && (ka < 0 || ka + nbi > nbins)) || (!zr && (kr < 0 || kr + nbi > nbins));
+      if (bad) {
+        if (tid == 0) {
+          atomicOr(c.err, kErrRange);
+          dlogl[i] = __longlong_as_double(0x7ff8000000000000LL);
+        }
+        continue;
+      }
+      if (!za) gen_any_block<T, NMAX, NT>(c, sa, nbi, ba, bs, tid);
+      if (!zr) gen_any_block<T, NMAX, NT>(c, sr, nbi, br, bs, tid);
+      if (wid == 0) eval_pair<T>(c, ba, br, za, zr, ka, kr, nbi, w, resid, frac_bits, psdp, npsd, lane, dlogl + i);
+      __syncthreads();   // the buffers are reused by the next proposal
+    }
+    __syncthreads();     // the batch's constants are rewritten
   }
 }
 
@@ -357,10 +455,43 @@ static gbk_status waveform_t(gbk_ctx* ctx, const double* params, const int32_t* 
   return check_launch("gb_waveform_batch");
 }
 
+// Block shape of k_dlogl_block: its shared memory, and blocks per SM (the autotuned cap, if any).
+template <typename T, int NMAX>
+static gbk_status dlogl_block(gbk_ctx* ctx, const double* pn, const double* po, const int32_t* nb,
+                              const int32_t* walker, int64_t n, const gbk_residual* R, const gbk_psd* psd,
+                              double* out, cudaStream_t st) {
+  constexpr int NT = block_threads<T, NMAX>();
+  const size_t smem = 3 * 2 * NMAX * sizeof(typename CT<T>::C) + 32 * sizeof(Src<T>) + 32 * sizeof(int);
+  auto kernel = k_dlogl_block<T, NMAX, NT>;
+  if (smem > 48 * 1024 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(GBK_ECUDA, "cudaFuncSetAttribute(smem=%zu) failed", smem);
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return set_error(GBK_ECUDA, "k_dlogl_block does not fit on an SM (smem=%zu)", smem);
+  }
+  const int pi = sizeof(T) == sizeof(float) ? GBK_MIXED : GBK_FP64;
+  const int cap_bps = ctx->tune_bps[pi][band_index(NMAX)];
+  if (cap_bps > 0 && cap_bps < per_sm) per_sm = cap_bps;
+  const int64_t need = (n + 15) / 16;
+  const int64_t cap = (int64_t)sms * per_sm;
+  const int grid = (int)(need < cap ? need : cap);
+  kernel<<<grid, NT, smem, st>>>(*ctx, pn, po, nb, walker, n, (const long long*)R->data, R->n_walkers, R->frac_bits,
+                                 psd->params, psd->n_psd, out);
+  return check_launch("gb_delta_loglike_batch");
+}
+
 template <typename T>
 static gbk_status dlogl_t(gbk_ctx* ctx, const double* pn, const double* po, const int32_t* nb, int nmax,
                           const int32_t* walker, int64_t n, const gbk_residual* R, const gbk_psd* psd,
                           double* out, cudaStream_t st) {
+  // long bands: waveforms generated by a block (512: 2 warps, 1024: 4 warps)
+  if (nmax == 512) return dlogl_block<T, 512>(ctx, pn, po, nb, walker, n, R, psd, out, st);
+  if (nmax == 1024) return dlogl_block<T, 1024>(ctx, pn, po, nb, walker, n, R, psd, out, st);
   const size_t pw = warp_bytes<T>(nmax, 3, 32);
   const int pi = sizeof(T) == sizeof(float) ? GBK_MIXED : GBK_FP64;
   int grid = 0, thr = 0;
@@ -479,7 +610,8 @@ extern "C" gbk_status gbk_autotune_dlogl(gbk_ctx* ctx, const double* params_new,
   const int wpcs[4] = {1, 2, 4, 8};
   const int bpss[4] = {1, 2, 4, 0};
   gbk_status s = GBK_OK;
-  for (int i = 0; i < 4 && !s; ++i)
+  const int n_wpc = n_band_max >= 512 ? 1 : 4;   // long bands: fixed block shape, only its count per SM
+  for (int i = 0; i < n_wpc && !s; ++i)
     for (int j = 0; j < 4 && !s; ++j) {
       ctx->tune_wpc[pi][bi] = wpcs[i];
       ctx->tune_bps[pi][bi] = bpss[j];
@@ -501,6 +633,7 @@ extern "C" gbk_status gbk_autotune_dlogl(gbk_ctx* ctx, const double* params_new,
   ctx->tune_wpc[pi][bi] = bw;
   ctx->tune_bps[pi][bi] = bb;
   if (s) return s;
+  if (n_band_max >= 512) bw = n_band_max / 256;   // warps of the block shape
   if (best_out) { best_out[0] = bw; best_out[1] = bb; }
   return GBK_OK;
 }

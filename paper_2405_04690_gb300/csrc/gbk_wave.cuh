@@ -219,15 +219,16 @@ __device__ __noinline__ Src<T> make_src(const double* __restrict__ prm, int64_t 
   return s;
 }
 
-// Radix-4 and radix-2 Stockham stages over both channels of a warp's buffers
-// (layout [2][N]); twiddles tw[m] = exp(-2 pi i m / N).
-template <typename C, int N>
+// Radix-4 and radix-2 Stockham stages over both channels of the buffers (layout [2][N]),
+// shared by NT threads (thread index tid); twiddles tw[m] = exp(-2 pi i m / N). Every
+// butterfly is the same arithmetic whatever NT, so a warp and a block give the same bits.
+template <typename C, int N, int NT>
 __device__ __forceinline__ void stage_r4(const C* __restrict__ in, C* __restrict__ out,
                                          const C* __restrict__ tw, int ns, int lane) {
   constexpr int NB = N / 4;
   const int step = N / (ns * 4);
 #pragma unroll 2
-  for (int b = lane; b < 2 * NB; b += 32) {
+  for (int b = lane; b < 2 * NB; b += NT) {
     const int ch = b / NB;
     const int j = b - ch * NB;
     const C* x = in + ch * N;
@@ -250,11 +251,11 @@ __device__ __forceinline__ void stage_r4(const C* __restrict__ in, C* __restrict
   }
 }
 
-template <typename C, int N>
+template <typename C, int N, int NT>
 __device__ __forceinline__ void stage_r2_first(const C* __restrict__ in, C* __restrict__ out,
                                                int lane) {
   constexpr int NB = N / 2;
-  for (int b = lane; b < 2 * NB; b += 32) {
+  for (int b = lane; b < 2 * NB; b += NT) {
     const int ch = b / NB;
     const int j = b - ch * NB;
     const C* x = in + ch * N;
@@ -264,6 +265,149 @@ __device__ __forceinline__ void stage_r2_first(const C* __restrict__ in, C* __re
     y[2 * j + 1] = csub(v0, v1);
   }
 }
+
+// Slow-part sample p of one source (band FFT input of the A and E channels): the TDI response
+// at the coarse time t_p = p T / N times the heterodyned carrier.
+template <typename T, int N>
+__device__ __forceinline__ void slow_sample(const Src<T>& src, const T* __restrict__ orb, int p, T dtp, T inv_n,
+                                            typename CT<T>::C& outA, typename CT<T>::C& outE) {
+  typedef typename CT<T>::C C;
+  const T lc = (T)kLc;
+  const T rs2 = (T)0.70710678118654752440;
+  const T rs6 = (T)0.40824829046386301637;
+  const T* o = orb + p;
+  const T cah = o[0 * N], sah = o[1 * N], cal = o[20 * N], sal = o[21 * N];
+  T dx[3][3], na[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      dx[c][d] = o[(2 + 3 * c + d) * N];
+      na[c][d] = o[(11 + 3 * c + d) * N];
+    }
+  const T tp = (T)p * dtp;
+  const T f = src.f0 + src.fdot * tp;
+  const T flc = f * lc;
+  const T pif = (T)3.14159265358979323846 * flc;
+  // exponentials with small arguments: E0 = e^{-i pi f L/c}, Ea = e^{i pi f L/c k.n_a},
+  // Ej = e^{-2 pi i f k.dx_j / c}; D = E0^2
+  const C e0 = expi_small(-pif);
+  C ea[3], ej[3];
+  T kn[3];
+  C nhn[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T kd = src.kx * dx[c][0] + src.ky * dx[c][1] + src.kz * dx[c][2];
+    ej[c] = expi_small((T)-6.28318530717958647692 * f * kd);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const T un = src.ux * na[a][0] + src.uy * na[a][1] + src.uz * na[a][2];
+    const T vn = src.vx * na[a][0] + src.vy * na[a][1] + src.vz * na[a][2];
+    kn[a] = src.kx * na[a][0] + src.ky * na[a][1] + src.kz * na[a][2];
+    const T xp = un * un - vn * vn;
+    const T xc = (T)2 * un * vn;
+    nhn[a] = mkc(src.hp * (src.c2p * xp - src.s2p * xc), src.hc * (src.s2p * xp + src.c2p * xc));
+    ea[a] = expi_small(pif * kn[a]);
+  }
+  // link i->j (arm a, direction sign sg, receiver j), common factor E0 removed:
+  //   y_ij = n.Hc.n sinc(pi f L/c (1 - sg k.n_a)) Ea^sg Ej
+  // 12: (0,+,1) 21: (0,-,0) 23: (1,+,2) 32: (1,-,1) 31: (2,+,0) 13: (2,-,2)
+  C y[6];
+  const int arm[6] = {0, 0, 1, 1, 2, 2};
+  const int rcv[6] = {1, 0, 2, 1, 0, 2};
+#pragma unroll
+  for (int l = 0; l < 6; ++l) {
+    const bool plus = (l & 1) == 0;
+    const T sarg = flc * ((T)1 - (plus ? kn[arm[l]] : -kn[arm[l]]));
+    const T sc = sincpi_poly(sarg);
+    const C ph = cmul(plus ? ea[arm[l]] : cconj(ea[arm[l]]), ej[rcv[l]]);
+    y[l] = cmul(mkc(nhn[arm[l]].x * sc, nhn[arm[l]].y * sc), ph);
+  }
+  // y index: 0=12 1=21 2=23 3=32 4=31 5=13
+  const C dd = cmul(e0, e0);
+  const C X = cadd(csub(y[4], y[1]), cmul(dd, csub(y[5], y[0])));
+  const C Y = cadd(csub(y[0], y[3]), cmul(dd, csub(y[1], y[2])));
+  const C Z = cadd(csub(y[2], y[5]), cmul(dd, csub(y[3], y[4])));
+  const C As = cscale(csub(Z, X), rs2);
+  const C Es = cscale(cadd(csub(X, cscale(Y, (T)2)), Z), rs6);
+  // common factor: (-i f)(1 - D^2) E0 e^{2 pi i cyc0} = 2 f sin(2 pi f L/c) e^{2 pi i (cyc0 - 3/2 f L/c)},
+  // cyc0 = phi0/2pi + delta p/N + fdot T^2 (p/N)^2 / 2 - f k.R_gc/c. The guiding-centre
+  // Doppler phase (O(f0 AU/c) cycles) is formed in double-float and reduced exactly.
+  T dop_h, dop_l;
+  {
+    const T p1 = src.dxh * cah, p2 = src.dyh * sah;
+    T e1, e2;
+    fma_err(src.dxh, cah, p1, e1);
+    fma_err(src.dyh, sah, p2, e2);
+    dop_h = p1 + p2;
+    const T bp = dop_h - p1;
+    const T es = (p1 - (dop_h - bp)) + (p2 - bp);
+    dop_l = es + e1 + e2 + (src.dxh * cal + src.dyh * sal) + (src.dxl * cah + src.dyl * sah);
+  }
+  const T pn = (T)p * inv_n;
+  const T pn2 = pn * pn;  // exact: p^2 < 2^24
+  T xd = src.dhi * pn;
+  xd -= rint_(xd);
+  const T q1 = src.fdh * pn2;
+  T q1e;
+  fma_err(src.fdh, pn2, q1, q1e);
+  T big = (src.phh - (dop_h - rint_(dop_h))) + (xd + (q1 - rint_(q1)));
+  big -= rint_(big);
+  const T small = (src.dlo * pn + src.phl) + (q1e + src.fdl * pn2) - dop_l
+                  - tp * (src.fkx * cah + src.fky * sah) - (T)1.5 * flc;
+  const C car = expi_cycles(big + small);
+  const T amp = (T)2 * f * ((T)6.28318530717958647692 * flc) * sincpi_poly((T)2 * flc);
+  const C com = cscale(car, amp);
+  outA = cmul(com, As);
+  outE = cmul(com, Es);
+}
+
+// Band FFT of buf0 ([2][N] slow-part samples) by NT threads, then the rotation by N/2 into
+// band order in buf0; buf1 is scratch. `sync` orders the threads between passes.
+template <typename C, int N, int NT, typename Sync>
+__device__ __forceinline__ void band_fft(C* buf0, C* buf1, const C* __restrict__ tw, int tid, Sync sync) {
+  // Stockham FFT: optional radix-2 first stage, then radix-4 stages.
+  C* in = buf0;
+  C* out = buf1;
+  int ns = 1;
+  if (N == 128 || N == 512) {
+    stage_r2_first<C, N, NT>(in, out, tid);
+    sync();
+    C* t = in; in = out; out = t;
+    ns = 2;
+  }
+  for (; ns < N; ns *= 4) {
+    stage_r4<C, N, NT>(in, out, tw, ns, tid);
+    sync();
+    C* t = in; in = out; out = t;
+  }
+  // result is in `in`; rotate by N/2 into buf0 (band order)
+  if (in == buf0) {
+    for (int i = tid; i < N; i += NT) {   // swap halves, one thread per pair
+      const int ch = i / (N / 2);
+      const int ii = i - ch * (N / 2);
+      C* b = buf0 + ch * N;
+      const C lo = b[ii], hi = b[ii + N / 2];
+      b[ii] = hi;
+      b[ii + N / 2] = lo;
+    }
+  } else {
+    for (int i = tid; i < 2 * N; i += NT) {
+      const int ch = i / N;
+      const int ii = i - ch * N;
+      buf0[i] = in[ch * N + ((ii + N / 2) & (N - 1))];
+    }
+  }
+  sync();
+}
+
+struct WarpSync {
+  __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+struct BlockSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
 
 // Generate the A/E band of one source into buf0 ([2][N], band order: element i is bin
 // q - N/2 + i), in strain units times 2^64. buf1 is scratch of the same size.
@@ -275,136 +419,41 @@ __device__ __noinline__ void gen_band(const Src<T>* __restrict__ srcp, const T* 
                                       int lane) {
   typedef typename CT<T>::C C;
   const Src<T> src = *srcp;
-  const T lc = (T)kLc;
   const T dtp = (T)(tobs / N);
   const T inv_n = (T)1 / (T)N;
   // The per-sample body is long; unrolling the sample loop multiplies the code that
   // every warp must fetch (GBK_SAMPLE_UNROLL, chosen by measurement).
-  const T rs2 = (T)0.70710678118654752440;
-  const T rs6 = (T)0.40824829046386301637;
 #pragma unroll (kSampleUnroll)
   for (int p = lane; p < N; p += 32) {
-    const T* o = orb + p;
-    const T cah = o[0 * N], sah = o[1 * N], cal = o[20 * N], sal = o[21 * N];
-    T dx[3][3], na[3][3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        dx[c][d] = o[(2 + 3 * c + d) * N];
-        na[c][d] = o[(11 + 3 * c + d) * N];
-      }
-    const T tp = (T)p * dtp;
-    const T f = src.f0 + src.fdot * tp;
-    const T flc = f * lc;
-    const T pif = (T)3.14159265358979323846 * flc;
-    // exponentials with small arguments: E0 = e^{-i pi f L/c}, Ea = e^{i pi f L/c k.n_a},
-    // Ej = e^{-2 pi i f k.dx_j / c}; D = E0^2
-    const C e0 = expi_small(-pif);
-    C ea[3], ej[3];
-    T kn[3];
-    C nhn[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const T kd = src.kx * dx[c][0] + src.ky * dx[c][1] + src.kz * dx[c][2];
-      ej[c] = expi_small((T)-6.28318530717958647692 * f * kd);
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const T un = src.ux * na[a][0] + src.uy * na[a][1] + src.uz * na[a][2];
-      const T vn = src.vx * na[a][0] + src.vy * na[a][1] + src.vz * na[a][2];
-      kn[a] = src.kx * na[a][0] + src.ky * na[a][1] + src.kz * na[a][2];
-      const T xp = un * un - vn * vn;
-      const T xc = (T)2 * un * vn;
-      nhn[a] = mkc(src.hp * (src.c2p * xp - src.s2p * xc), src.hc * (src.s2p * xp + src.c2p * xc));
-      ea[a] = expi_small(pif * kn[a]);
-    }
-    // link i->j (arm a, direction sign sg, receiver j), common factor E0 removed:
-    //   y_ij = n.Hc.n sinc(pi f L/c (1 - sg k.n_a)) Ea^sg Ej
-    // 12: (0,+,1) 21: (0,-,0) 23: (1,+,2) 32: (1,-,1) 31: (2,+,0) 13: (2,-,2)
-    C y[6];
-    const int arm[6] = {0, 0, 1, 1, 2, 2};
-    const int rcv[6] = {1, 0, 2, 1, 0, 2};
-#pragma unroll
-    for (int l = 0; l < 6; ++l) {
-      const bool plus = (l & 1) == 0;
-      const T sarg = flc * ((T)1 - (plus ? kn[arm[l]] : -kn[arm[l]]));
-      const T sc = sincpi_poly(sarg);
-      const C ph = cmul(plus ? ea[arm[l]] : cconj(ea[arm[l]]), ej[rcv[l]]);
-      y[l] = cmul(mkc(nhn[arm[l]].x * sc, nhn[arm[l]].y * sc), ph);
-    }
-    // y index: 0=12 1=21 2=23 3=32 4=31 5=13
-    const C dd = cmul(e0, e0);
-    const C X = cadd(csub(y[4], y[1]), cmul(dd, csub(y[5], y[0])));
-    const C Y = cadd(csub(y[0], y[3]), cmul(dd, csub(y[1], y[2])));
-    const C Z = cadd(csub(y[2], y[5]), cmul(dd, csub(y[3], y[4])));
-    const C As = cscale(csub(Z, X), rs2);
-    const C Es = cscale(cadd(csub(X, cscale(Y, (T)2)), Z), rs6);
-    // common factor: (-i f)(1 - D^2) E0 e^{2 pi i cyc0} = 2 f sin(2 pi f L/c) e^{2 pi i (cyc0 - 3/2 f L/c)},
-    // cyc0 = phi0/2pi + delta p/N + fdot T^2 (p/N)^2 / 2 - f k.R_gc/c. The guiding-centre
-    // Doppler phase (O(f0 AU/c) cycles) is formed in double-float and reduced exactly.
-    T dop_h, dop_l;
-    {
-      const T p1 = src.dxh * cah, p2 = src.dyh * sah;
-      T e1, e2;
-      fma_err(src.dxh, cah, p1, e1);
-      fma_err(src.dyh, sah, p2, e2);
-      dop_h = p1 + p2;
-      const T bp = dop_h - p1;
-      const T es = (p1 - (dop_h - bp)) + (p2 - bp);
-      dop_l = es + e1 + e2 + (src.dxh * cal + src.dyh * sal) + (src.dxl * cah + src.dyl * sah);
-    }
-    const T pn = (T)p * inv_n;
-    const T pn2 = pn * pn;  // exact: p^2 < 2^24
-    T xd = src.dhi * pn;
-    xd -= rint_(xd);
-    const T q1 = src.fdh * pn2;
-    T q1e;
-    fma_err(src.fdh, pn2, q1, q1e);
-    T big = (src.phh - (dop_h - rint_(dop_h))) + (xd + (q1 - rint_(q1)));
-    big -= rint_(big);
-    const T small = (src.dlo * pn + src.phl) + (q1e + src.fdl * pn2) - dop_l
-                    - tp * (src.fkx * cah + src.fky * sah) - (T)1.5 * flc;
-    const C car = expi_cycles(big + small);
-    const T amp = (T)2 * f * ((T)6.28318530717958647692 * flc) * sincpi_poly((T)2 * flc);
-    const C com = cscale(car, amp);
-    buf0[p] = cmul(com, As);
-    buf0[N + p] = cmul(com, Es);
+    C sa, se;
+    slow_sample<T, N>(src, orb, p, dtp, inv_n, sa, se);
+    buf0[p] = sa;
+    buf0[N + p] = se;
   }
   __syncwarp();
-  // Stockham FFT: optional radix-2 first stage, then radix-4 stages.
-  C* in = buf0;
-  C* out = buf1;
-  int ns = 1;
-  if (N == 128 || N == 512) {
-    stage_r2_first<C, N>(in, out, lane);
-    __syncwarp();
-    C* t = in; in = out; out = t;
-    ns = 2;
+  band_fft<C, N, 32>(buf0, buf1, tw, lane, WarpSync());
+}
+
+// The same band generated by all NT threads of a block (thread index tid): the samples and
+// butterflies are shared out, each computed exactly as in gen_band (the same bits). Called by
+// every thread of the block; returns with the block synchronised.
+template <typename T, int N, int NT>
+__device__ __noinline__ void gen_band_block(const Src<T>* __restrict__ srcp, const T* __restrict__ orb,
+                                            const typename CT<T>::C* __restrict__ tw, double tobs,
+                                            typename CT<T>::C* buf0, typename CT<T>::C* buf1, int tid) {
+  typedef typename CT<T>::C C;
+  const Src<T> src = *srcp;
+  const T dtp = (T)(tobs / N);
+  const T inv_n = (T)1 / (T)N;
+#pragma unroll (kSampleUnroll)
+  for (int p = tid; p < N; p += NT) {
+    C sa, se;
+    slow_sample<T, N>(src, orb, p, dtp, inv_n, sa, se);
+    buf0[p] = sa;
+    buf0[N + p] = se;
   }
-  for (; ns < N; ns *= 4) {
-    stage_r4<C, N>(in, out, tw, ns, lane);
-    __syncwarp();
-    C* t = in; in = out; out = t;
-  }
-  // result is in `in`; rotate by N/2 into buf0 (band order)
-  if (in == buf0) {
-    for (int i = lane; i < N; i += 32) {   // swap halves, one lane per pair
-      const int ch = i / (N / 2);
-      const int ii = i - ch * (N / 2);
-      C* b = buf0 + ch * N;
-      const C lo = b[ii], hi = b[ii + N / 2];
-      b[ii] = hi;
-      b[ii + N / 2] = lo;
-    }
-  } else {
-    for (int i = lane; i < 2 * N; i += 32) {
-      const int ch = i / N;
-      const int ii = i - ch * N;
-      buf0[i] = in[ch * N + ((ii + N / 2) & (N - 1))];
-    }
-  }
-  __syncwarp();
+  __syncthreads();
+  band_fft<C, N, NT>(buf0, buf1, tw, tid, BlockSync());
 }
 
 }  // namespace gbk

@@ -1,6 +1,9 @@
 """Uneven band lengths (N = 128..1024 by octave over 0.3-20 mHz) in one batch: per-N error
-table against the oracle, and the binned, autotuned launches give bit-identical results to a
-single ragged launch."""
+table against the oracle; the binned, autotuned launches give bit-identical results to a
+single ragged launch (which, for its 1024-bin maximum, generates every waveform with a whole
+block, the binned 128- and 256-bin launches with one warp: the two generators must give the
+same bits); and the binned launches captured in one CUDA graph and replayed give the same bits
+again."""
 import numpy as np
 import pytest
 
@@ -47,6 +50,7 @@ def test_uneven_bands_error_table_and_binned_equals_ragged():
     L.gbk_sync_status(ctx)
     ragged = out.cpu().numpy()
     table = {}
+    bins = {}
     for N in (128, 256, 512, 1024):
         idx = np.nonzero(nb == N)[0]
         if len(idx) == 0:
@@ -64,6 +68,24 @@ def test_uneven_bands_error_table_and_binned_equals_ragged():
         L.gb_delta_loglike_batch(ctx, pn, po, nbt, N, wt, RS, PS, o2, L.GBK_MIXED)
         L.gbk_sync_status(ctx)
         assert np.array_equal(o2.cpu().numpy(), ragged[idx]), N
+        bins[N] = (pn, po, nbt, wt, torch.full_like(o2, float("nan")))
     assert len(table) == 4, table
     print("per-N |Delta lnL error| (count, max):", table)
+    # the four binned launches captured in one CUDA graph, replayed twice
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(graph, stream=cap):
+            for N, (pn, po, nbt, wt, o3) in bins.items():
+                L.gb_delta_loglike_batch(ctx, pn, po, nbt, N, wt, RS, PS, o3, L.GBK_MIXED)
+    torch.cuda.current_stream().wait_stream(cap)
+    for _ in range(2):
+        for o3 in (x[4] for x in bins.values()):
+            o3.fill_(float("nan"))
+        graph.replay()
+        torch.cuda.synchronize()
+        L.gbk_sync_status(ctx)
+        for N, (_, _, _, _, o3) in bins.items():
+            assert np.array_equal(o3.cpu().numpy(), ragged[np.nonzero(nb == N)[0]]), N
     ctx.close()
