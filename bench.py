@@ -880,40 +880,94 @@ def run_ours(args):
             learned = run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, snap, ess, units)
         del snap
 
-    # the plain float64 path on the same GPU: (a) the same sweep in float64, one step;
-    # (b) per-source launches of the float64 Delta lnL (one proposal per launch)
+    # the paper's schedule (Sec. V.D): ~30 in-model proposals per source, then the RJ pass and
+    # the swaps, on the same ensemble (own plan, refreshed from the current state)
+    sched30 = {}
+    if args.pps30_sweeps > 0:
+        plan30 = L.SweepPlan(S["ctx"], ens["params"].shape[0], N_W, ens["n_bands"], ens["n_max"], N_BAND,
+                             ens["band_k0"], sweep_sigma(), L.GBK_MIXED, f_min=F_LO, f_max=F_HI, props_per_source=30.0)
+        S30 = dict(S)
+        S30["plan"] = plan30
+        sw30 = [sweep_no[0]]
+
+        def step30(flags_extra=0):
+            L.gb_sweep(plan30, S30["P"], S30["E"], S30["betas"], S30["R"], S30["psd"], key, sw30[0],
+                       1 | 2 | 4 | flags_extra, stats=stats, stream=stream)
+            L.gbk_sweep_transfer(plan30, S30["P"], S30["E"], xfer, stream)
+            sw30[0] += 1
+
+        step30(L.SWEEP_REFRESH)
+        step30()
+        torch.cuda.synchronize()
+        sched30 = run_ess(torch, L, S30, step30, stats, stream, args.pps30_sweeps)
+        st30 = stats.cpu().numpy()
+        sched30["waveforms_per_s"] = float(st30[4, 0]) / (sched30["ms_per_sweep"] * 1e-3 * args.pps30_sweeps)
+        sched30["schedule"] = "30 in-model proposals per source, then flip-all RJ, then tempering swaps (Sec. V.D)"
+        plan30.close()
+
+    # the plain float64 path on the same GPU: (a) the same sweep in float64, with its ESS/s
+    # measured over a run of sweeps; (b) one float64 Delta lnL launch per source band carrying
+    # that band's in-model proposals (every source moved, new != old), no batching across bands
     fp64 = {}
     if not args.no_fp64:
         S64 = build_device_state(torch, L, dev, ens, L.GBK_FP64, seed=1 + 1000 * rank)
         st64 = torch.zeros((5, 2), dtype=torch.int64, device=dev)
-        L.gb_sweep(S64["plan"], S64["P"], S64["E"], S64["betas"], S64["R"], S64["psd"], key, 0, 1 | 2 | 4 | 8,
-                   stats=st64, stream=stream)
+        sw64 = [0]
+
+        def step64(flags_extra=0):
+            L.gb_sweep(S64["plan"], S64["P"], S64["E"], S64["betas"], S64["R"], S64["psd"], key, sw64[0],
+                       1 | 2 | 4 | flags_extra, stats=st64, stream=stream)
+            L.gbk_sweep_transfer(S64["plan"], S64["P"], S64["E"], xfer, stream)
+            sw64[0] += 1
+
+        step64(L.SWEEP_REFRESH)
         torch.cuda.synchronize()
-        st64.zero_()
+        e64 = run_ess(torch, L, S64, step64, st64, stream, args.fp64_sweeps)
+        s64 = st64.cpu().numpy()
+        fp64["fp64_sweep_proposals_per_s"] = e64["proposals_per_s"]
+        fp64["fp64_sweep"] = {"ess_per_s": e64["ess_per_s"], "tau_sweeps": e64["tau_sweeps"],
+                              "sweeps": e64["sweeps"], "ms_per_sweep": e64["ms_per_sweep"],
+                              "proposals_per_s": e64["proposals_per_s"],
+                              "waveforms_per_s": float(s64[4, 0]) / (e64["ms_per_sweep"] * 1e-3 * e64["sweeps"])}
+        # per-band launches on walker 0's cold chain: bands in order, each band's present sources
+        # moved by the sweep's in-model widths (Gaussian steps; ln A, f0, fdot, angles)
+        g64 = np.random.default_rng(64 + 1000 * rank)
+        sig = np.asarray(sweep_sigma())
+        P0 = S64["P"][0, 0].cpu().numpy()
+        E0 = S64["E"][0, 0].cpu().numpy().astype(bool)
+        launches = []
+        for b in range(ens["n_bands"]):
+            old = P0[b][E0[b]]
+            if len(old) == 0:
+                continue
+            new = old.copy()
+            new[:, 0] = old[:, 0] * np.exp(sig[0] * g64.standard_normal(len(old)))
+            new[:, 1:] = old[:, 1:] + sig[1:] * g64.standard_normal((len(old), 7))
+            new[:, 3] %= 2 * math.pi
+            new[:, 4] %= math.pi
+            new[:, 7] %= 2 * math.pi
+            new[:, 5:7] = np.clip(new[:, 5:7], -1.0, 1.0)
+            launches.append((torch.from_numpy(np.ascontiguousarray(new.T)).to(dev),
+                             torch.from_numpy(np.ascontiguousarray(old.T)).to(dev),
+                             torch.full((len(old),), N_BAND, dtype=torch.int32, device=dev),
+                             torch.zeros(len(old), dtype=torch.int32, device=dev),
+                             torch.empty(len(old), dtype=torch.float64, device=dev)))
+        for pn, po, nbv, wv, ov in launches[:5]:
+            L.gb_delta_loglike_batch(S64["ctx"], pn, po, nbv, N_BAND, wv, S64["R"], S64["psd"], ov, L.GBK_FP64, stream)
+        torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
-        L.gb_sweep(S64["plan"], S64["P"], S64["E"], S64["betas"], S64["R"], S64["psd"], key, 1, 1 | 2 | 4,
-                   stats=st64, stream=stream)
+        for pn, po, nbv, wv, ov in launches:
+            L.gb_delta_loglike_batch(S64["ctx"], pn, po, nbv, N_BAND, wv, S64["R"], S64["psd"], ov, L.GBK_FP64, stream)
         a1.record(stream)
         torch.cuda.synchronize()
-        fp64["fp64_sweep_proposals_per_s"] = float(st64[:4, 0].sum().item()) / (a0.elapsed_time(a1) * 1e-3)
-        # per-source plain path
-        n1 = 200
-        pnew = torch.from_numpy(ens["params"][0, 0].reshape(-1, 8)[ens["exists"][0, 0].reshape(-1).astype(bool)][:n1].T
-                                .copy()).to(dev)
-        one_nb = torch.full((1,), N_BAND, dtype=torch.int32, device=dev)
-        one_w = torch.zeros(1, dtype=torch.int32, device=dev)
-        out1 = torch.empty(1, dtype=torch.float64, device=dev)
-        cols = [pnew[:, i:i + 1].contiguous() for i in range(pnew.shape[1])]
-        for c in cols[:5]:
-            L.gb_delta_loglike_batch(S64["ctx"], c, c, one_nb, N_BAND, one_w, S64["R"], S64["psd"], out1, L.GBK_FP64, stream)
-        torch.cuda.synchronize()
-        a0.record(stream)
-        for c in cols:
-            L.gb_delta_loglike_batch(S64["ctx"], c, c, one_nb, N_BAND, one_w, S64["R"], S64["psd"], out1, L.GBK_FP64, stream)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        fp64["fp64_per_source_proposals_per_s"] = len(cols) / (a0.elapsed_time(a1) * 1e-3)
+        n_prop = sum(int(x[4].numel()) for x in launches)
+        fp64["fp64_per_band_proposals_per_s"] = n_prop / (a0.elapsed_time(a1) * 1e-3)
+        fp64["fp64_per_band"] = {"launches": len(launches), "proposals": n_prop,
+                                 "ms": a0.elapsed_time(a1),
+                                 "path": "gb_delta_loglike_batch in float64, one launch per source band (walker 0, "
+                                         "cold chain), each present source moved (new != old); two waveforms and "
+                                         "one Delta lnL per proposal"}
         S64["plan"].close()
         del S64
     line = {
@@ -943,6 +997,7 @@ def run_ours(args):
                      "kernel": "k_band<float,256> (in-model + flip-all RJ)",
                      "peak_note": "FP32 ALU: 152 SMs x 128 lanes x 2 (FMA) x 2.07 GHz (derived, not measured)",
                      "flops_per_waveform": flops_per_waveform(), "flops_per_evaluation": flops_per_evaluation()},
+        "waveforms_per_s": wf / args.steps / (ms_step * 1e-3),
         "e2e": {"value": e2e_props / (e2e_ms * 1e-3), "unit": "proposals/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": 9 * args.steps,   # per step: open, band, swap per parity; transfer assign, apply, sums
@@ -950,6 +1005,13 @@ def run_ours(args):
         "wall_s_timed_region": wall,
     }
     line["config"].update(fp64)
+    if fp64:
+        line["vs_plain_fp64"] = {
+            "batched_mixed_over_fp64_sweep_proposals": value / fp64["fp64_sweep_proposals_per_s"],
+            "batched_mixed_over_fp64_per_band_proposals": value / fp64["fp64_per_band_proposals_per_s"],
+            "ess_per_s_mixed_over_fp64_sweep": (ess["ess_per_s"] / fp64["fp64_sweep"]["ess_per_s"]) if ess else None}
+    if sched30:
+        line["schedule_30_1_1"] = sched30
     if c3:
         line["total_loglike"] = c3
     if uneven:
@@ -1002,6 +1064,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison runs")
+    ap.add_argument("--fp64-sweeps", type=int, default=24, help="sweeps of the float64 ESS run")
+    ap.add_argument("--pps30-sweeps", type=int, default=40,
+                    help="sweeps of the 30-in-model-proposals-per-source schedule (0: skip)")
     ap.add_argument("--no-c3", action="store_true", help="skip the total log-likelihood (HBM) measurement")
     ap.add_argument("--ess-sweeps", type=int, default=120, help="sweeps for the ESS/s measurement (0: skip)")
     ap.add_argument("--c3-walkers", type=int, default=512, help="walkers of the total log-likelihood measurement")
