@@ -139,14 +139,16 @@ __device__ __forceinline__ void acc_bin(const gbk_ctx& c, const long long* __res
   srd.add(w * (rax * da.x + ray * da.y + rex * de.x + rey * de.y));
 }
 
-// Delta lnL of proposal (a in ba at window offset ka, r in br at kr; either may be absent)
-// against walker w's residual, by the 32 lanes of one warp: lane l sums the bins l, l + 32, ...
-// of each band in order (the same summation in every kernel that calls it).
+// Sums <D|D> and <R|D> of proposal (a in ba at window offset ka, r in br at kr; either may be
+// absent) against walker w's residual over the band bins [jb, je), by the 32 lanes of one warp:
+// lane l sums the bins jb + l, jb + l + 32, ... of each band in order (the same summation in every
+// kernel that calls it). Returns the warp totals in dd, rd.
 template <typename T>
-__device__ __forceinline__ void eval_pair(const gbk_ctx& c, const typename CT<T>::C* ba, const typename CT<T>::C* br,
+__device__ __forceinline__ void eval_sums(const gbk_ctx& c, const typename CT<T>::C* ba, const typename CT<T>::C* br,
                                           bool za, bool zr, int64_t ka, int64_t kr, int nbi, int w,
                                           const long long* __restrict__ resid, int32_t frac_bits,
-                                          const double* __restrict__ psdp, int32_t npsd, int lane, double* out) {
+                                          const double* __restrict__ psdp, int32_t npsd, int lane, int jb, int je,
+                                          double& dd_out, double& rd_out) {
   typedef typename CT<T>::C C;
   const int64_t nbins = c.grid.n_bins;
   const T rscale = (T)ldexp(1.0, kStrainExp - frac_bits);
@@ -158,7 +160,7 @@ __device__ __forceinline__ void eval_pair(const gbk_ctx& c, const typename CT<T>
   const C zero = mkc((T)0, (T)0);
   // bins of a's band: D = a - r (r where the bands overlap)
   if (!za) {
-    for (int j = lane; j < nbi; j += 32) {
+    for (int j = jb + lane; j < je; j += 32) {
       const int64_t k = ka + j;
       C ra = zero, re = zero;
       const int64_t jr = k - kr;
@@ -168,7 +170,7 @@ __device__ __forceinline__ void eval_pair(const gbk_ctx& c, const typename CT<T>
   }
   // bins of r's band outside a's band: D = -r
   if (!zr) {
-    for (int j = lane; j < nbi; j += 32) {
+    for (int j = jb + lane; j < je; j += 32) {
       const int64_t k = kr + j;
       const int64_t ja = k - ka;
       if (!za && ja >= 0 && ja < nbi) continue;
@@ -176,8 +178,19 @@ __device__ __forceinline__ void eval_pair(const gbk_ctx& c, const typename CT<T>
       acc_bin<T>(c, rw, k, mkc(-ra.x, -ra.y), mkc(-re.x, -re.y), pw.aw, rscale, sdd, srd);
     }
   }
-  const double dd = sdd.warp_total();
-  const double rd = srd.warp_total();
+  dd_out = sdd.warp_total();
+  rd_out = srd.warp_total();
+}
+
+// Delta lnL of the proposal over the whole band by one warp.
+template <typename T>
+__device__ __forceinline__ void eval_pair(const gbk_ctx& c, const typename CT<T>::C* ba, const typename CT<T>::C* br,
+                                          bool za, bool zr, int64_t ka, int64_t kr, int nbi, int w,
+                                          const long long* __restrict__ resid, int32_t frac_bits,
+                                          const double* __restrict__ psdp, int32_t npsd, int lane, double* out) {
+  double dd, rd;
+  eval_sums<T>(c, ba, br, za, zr, ka, kr, nbi, w, resid, frac_bits, psdp, npsd, lane, 0, nbi, dd, rd);
+  const PsdW<T> pw = psd_walker<T>(c, psdp, npsd, w);
   if (lane == 0) *out = pw.cw * (-0.5 * dd + rd);
 }
 
@@ -285,6 +298,7 @@ k_dlogl_block(const gbk_ctx c, const double* __restrict__ pnew, const double* __
   C* bs = br + 2 * NMAX;
   Src<T>* srcs = reinterpret_cast<Src<T>*>(bs + 2 * NMAX);   // [0,16) new, [16,32) old
   int* meta = reinterpret_cast<int*>(srcs + 32);            // [0,16) N, [16,32) walker
+  __shared__ double part[NT / 32][2];                        // per-warp sums of one proposal
   const int64_t nbins = c.grid.n_bins;
   for (int64_t base = (int64_t)blockIdx.x * 16; base < n; base += (int64_t)gridDim.x * 16) {
     if (wid == 0) {
@@ -325,7 +339,23 @@ k_dlogl_block(const gbk_ctx c, const double* __restrict__ pnew, const double* __
       }
       if (!za) gen_any_block<T, NMAX, NT>(c, sa, nbi, ba, bs, tid);
       if (!zr) gen_any_block<T, NMAX, NT>(c, sr, nbi, br, bs, tid);
-      if (wid == 0) eval_pair<T>(c, ba, br, za, zr, ka, kr, nbi, w, resid, frac_bits, psdp, npsd, lane, dlogl + i);
+      // the sums over 256-bin quarters of the band by as many warps (a partition fixed by the band
+      // length alone, so any block shape gives the same bits), added in quarter order
+      const int ne = nbi > 256 ? nbi / 256 : 1;
+      if (wid < ne) {
+        const int jb = wid * (nbi / ne);
+        double dd, rd;
+        eval_sums<T>(c, ba, br, za, zr, ka, kr, nbi, w, resid, frac_bits, psdp, npsd, lane, jb, jb + nbi / ne, dd,
+                     rd);
+        if (lane == 0) { part[wid][0] = dd; part[wid][1] = rd; }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double dd = part[0][0], rd = part[0][1];
+        for (int v = 1; v < ne; ++v) { dd += part[v][0]; rd += part[v][1]; }
+        const PsdW<T> pw = psd_walker<T>(c, psdp, npsd, w);
+        dlogl[i] = pw.cw * (-0.5 * dd + rd);
+      }
       __syncthreads();   // the buffers are reused by the next proposal
     }
     __syncthreads();     // the batch's constants are rewritten

@@ -111,9 +111,10 @@ namespace gbk {
 // Record an error message for gbk_last_error() and return the status.
 gbk_status set_error(gbk_status st, const char* fmt, ...);
 gbk_status check_launch(const char* what);
-// Block passes of the total log-likelihood over the float32 shape tables iq, rho: per 4096-bin
-// chunk and walker, the sums of |R|^2 2^128 iq / u and of ln u into part [chunk][nwl][2]
+// Block passes of the total log-likelihood over the float32 shape tables iq, rho: per chunk of
+// kTlChunk bins and walker, the sums of |R|^2 2^128 iq / u and of ln u into part [chunk][nwl][2]
 // (gbk_psd.cu; shared with the no-allocation variant).
+constexpr int kTlChunk = 8192;
 gbk_status total_loglike_parts(const float* R, const float* iq, const float* rho, const double* pp, int32_t w0,
                                int32_t nwl, int64_t nb, double* part, cudaStream_t st);
 

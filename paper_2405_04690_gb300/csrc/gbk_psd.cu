@@ -7,7 +7,6 @@
 namespace gbk {
 
 constexpr int kTlThreads = 256;
-constexpr int kTlChunk = 4096;      // bins per block
 constexpr int kTlWalkers = 4;       // walkers per block
 constexpr int kTlMaxW = 4096;       // walkers per launch pair (scratch sizing)
 
@@ -107,20 +106,29 @@ k_total_loglike_part(const float* __restrict__ R, const float* __restrict__ iq, 
       }
     }
   }
-  __shared__ double red[kTlThreads / 32][kTlWalkers][2];
+  // warp totals stay float pairs (hi, lo) and integer exponent sums: float64 (a small fraction of
+  // the float32 rate) only in the few threads that add up the block
+  __shared__ float2 red[kTlThreads / 32][kTlWalkers][2];
+  __shared__ int rede[kTlThreads / 32][kTlWalkers];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < kTlWalkers; ++j) {
-    const double tq = sq[j].warp_total();
-    const double tl = sl[j].warp_total() + kLn2 * (double)__reduce_add_sync(0xffffffffu, ecnt[j]);
-    if (lane == 0) { red[wid][j][0] = tq; red[wid][j][1] = tl; }
+    const float2 tq = sq[j].warp_pair();
+    const float2 tl = sl[j].warp_pair();
+    const int te = __reduce_add_sync(0xffffffffu, ecnt[j]);
+    if (lane == 0) { red[wid][j][0] = tq; red[wid][j][1] = tl; rede[wid][j] = te; }
   }
   __syncthreads();
   if (threadIdx.x < kTlWalkers * 2) {
     const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
     if (j < nact) {
       double s = 0.0;
-      for (int w = 0; w < kTlThreads / 32; ++w) s += red[w][j][which];
+      int es = 0;
+      for (int w = 0; w < kTlThreads / 32; ++w) {
+        s += (double)red[w][j][which].x + (double)red[w][j][which].y;
+        es += rede[w][j];
+      }
+      if (which) s += kLn2 * (double)es;
       part[((int64_t)chunk * nwl + wg + j) * 2 + which] = s;
     }
   }

@@ -95,30 +95,39 @@ k_fg_part(const float* __restrict__ R, const float* __restrict__ iq, const float
   __syncthreads();
   FgEntry ent[kFgEntries];
   const float* rw[kFgEntries];
-  bool act[kFgEntries], same[kFgEntries];
+  bool act[kFgEntries], same[kFgEntries], gsame[kFgEntries];
 #pragma unroll
   for (int j = 0; j < kFgEntries; ++j) {
     ent[j] = s_e[j];
     act[j] = eg + j < nel;
     rw[j] = R + (int64_t)s_r[j] * 2 * nb * 2;
     same[j] = j > 0 && s_r[j] == s_r[j - 1];   // entries of one residual read it once
+    // entries whose foreground shape (alpha, f_k, s1, s2) equals the previous entry's share its
+    // exponent g (A_fg, which only scales g, may differ)
+    gsame[j] = j > 0 && ent[j].alpha == ent[j - 1].alpha && ent[j].fk == ent[j - 1].fk &&
+               ent[j].s1l == ent[j - 1].s1l && ent[j].s2l == ent[j - 1].s2l;
   }
   CompF sq[kFgEntries], sl[kFgEntries];
 #pragma unroll
   for (int j = 0; j < kFgEntries; ++j) { sq[j].init(); sl[j].init(); }
   const float up = 18446744073709551616.0f;  // 2^64
-  // per-bin, per-entry terms; residual values of both channels at bin k given
-  auto bin = [&](int j, float iqk, float rhk, float lf, float fk, float c, float ar, float ai, float er, float ei) {
-    // g = 2^(c - log2(e) [s1 f^alpha + softplus(2 s2 (f - f_k))]), f^alpha = 2^(alpha log2 f);
-    // far above the knee (softplus > c + 30) g A_fg / S_oms < 2^-30 relative to 1: skipped
+  // g = 2^(c - log2(e) [s1 f^alpha + softplus(2 s2 (f - f_k))]), f^alpha = 2^(alpha log2 f);
+  // far above the knee (softplus > c + 30) g A_fg / S_oms < 2^-30 relative to 1: skipped
+  auto fg_g = [&](int j, float lf, float fk, float c) {
     const float y = ent[j].s2l * (fk - ent[j].fk);
     float g = 0.f;
     if (y < c + 30.f) g = ex2a(c - ent[j].s1l * ex2a(ent[j].alpha * lf) - softplus2(y));
+    return g;
+  };
+  // per-bin, per-entry terms; residual values of both channels at bin k given; the two
+  // channels share one reciprocal: x / ua + y / ue = (x ue + y ua) / (ua ue)
+  auto bin = [&](int j, float g, float iqk, float rhk, float ar, float ai, float er, float ei) {
     const float ua = fmaf(ent[j].aw_a, rhk, 1.0f) + g * ent[j].k_a;
     const float ue = fmaf(ent[j].aw_e, rhk, 1.0f) + g * ent[j].k_e;
     const float ax = ar * up, ay = ai * up, ex = er * up, ey = ei * up;
-    sq[j].add(iqk * ((ax * ax + ay * ay) * ent[j].iso_a * rcpa(ua) + (ex * ex + ey * ey) * ent[j].iso_e * rcpa(ue)));
-    sl[j].add(0.6931471805599453f * lg2a(ua * ue));
+    const float uu = ua * ue;
+    sq[j].add(iqk * fmaf((ax * ax + ay * ay) * ent[j].iso_a, ue, (ex * ex + ey * ey) * ent[j].iso_e * ua) * rcpa(uu));
+    sl[j].add(0.6931471805599453f * lg2a(uu));
   };
   const bool even = (nb & 1) == 0;
   for (int64_t k = kbeg + 2 * threadIdx.x; k < kend; k += 2 * kFgThreads) {
@@ -139,22 +148,29 @@ k_fg_part(const float* __restrict__ R, const float* __restrict__ iq, const float
 #pragma unroll
       for (int j = 1; j < kFgEntries; ++j)
         if (same[j]) { av[j] = av[j - 1]; ev[j] = ev[j - 1]; }
+      float g0 = 0.f, g1 = 0.f;
 #pragma unroll
       for (int j = 0; j < kFgEntries; ++j) {
         if (!act[j]) continue;
-        bin(j, iq2.x, rh2.x, lf2.x, ff2.x, c2.x, av[j].x, av[j].y, ev[j].x, ev[j].y);
-        bin(j, iq2.y, rh2.y, lf2.y, ff2.y, c2.y, av[j].z, av[j].w, ev[j].z, ev[j].w);
+        if (!gsame[j]) {
+          g0 = fg_g(j, lf2.x, ff2.x, c2.x);
+          g1 = fg_g(j, lf2.y, ff2.y, c2.y);
+        }
+        bin(j, g0, iq2.x, rh2.x, av[j].x, av[j].y, ev[j].x, ev[j].y);
+        bin(j, g1, iq2.y, rh2.y, av[j].z, av[j].w, ev[j].z, ev[j].w);
       }
     } else {
       for (int64_t kk = k; kk < min(k + 2, kend); ++kk) {
         const float iqk = __ldg(iq + kk), rhk = __ldg(rho + kk), lf = __ldg(lnf + kk), fk = __ldg(ff + kk),
                     c = __ldg(fgc + kk);
+        float g = 0.f;
 #pragma unroll
         for (int j = 0; j < kFgEntries; ++j) {
           if (!act[j]) continue;
           const float2 a = *reinterpret_cast<const float2*>(rw[j] + 2 * kk);
           const float2 e = *reinterpret_cast<const float2*>(rw[j] + 2 * (nb + kk));
-          bin(j, iqk, rhk, lf, fk, c, a.x, a.y, e.x, e.y);
+          if (!gsame[j]) g = fg_g(j, lf, fk, c);
+          bin(j, g, iqk, rhk, a.x, a.y, e.x, e.y);
         }
       }
     }

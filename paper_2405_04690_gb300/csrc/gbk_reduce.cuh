@@ -24,6 +24,20 @@ struct CompF {
     s = t;
     c = __fadd_rn(c, e);
   }
+  // the warp's total as a float pair (hi, lo), hi + lo the compensated sum
+  __device__ __forceinline__ float2 warp_pair() const {
+    float hi = s, lo = c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+      const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+      float t, e;
+      two_sum(hi, ohi, t, e);
+      hi = t;
+      lo = __fadd_rn(__fadd_rn(lo, olo), e);
+    }
+    return make_float2(hi, lo);
+  }
   __device__ __forceinline__ double warp_total() const {
     float hi = s, lo = c;
 #pragma unroll

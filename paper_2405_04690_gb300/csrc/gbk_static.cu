@@ -17,7 +17,7 @@
 
 namespace gbk {
 
-constexpr int kStChunk = 4096;                   // bins per block of the likelihood pass (total_loglike_parts)
+constexpr int kStChunk = kTlChunk;               // bins per block of the likelihood pass (total_loglike_parts)
 constexpr int kStWalkers = 4;                    // walkers per block of that pass
 constexpr int kStShapeThreads = 256;             // bins per block of the shape pass
 constexpr int64_t kStScratchDoubles = 1 << 21;   // 16 MiB
