@@ -346,7 +346,7 @@ def reduce_over_ranks(torch, dist, world, device, ms, work):
 
 
 def run_ess(torch, L, S, step, stats, stream, n_sweeps, flags=0, pairs=None, group=None, units=None, keep=10,
-            adapt=False):
+            adapt=False, prefix=None):
     """ESS/s: integrated autocorrelation time of every cold walker's total log-likelihood
     (Eq. like on its residual) over n_sweeps sweeps (first quarter discarded). Optionally
     collects training pairs of the learned proposal after the burn-in and the cold slots' unit
@@ -384,7 +384,13 @@ def run_ess(torch, L, S, step, stats, stream, n_sweeps, flags=0, pairs=None, gro
     x = np.array(series).T[:, n_sweeps // 4:]
     tau = autocorr_time(x)
     n_eff = x.shape[0] * x.shape[1] / max(tau, 1.0)
-    return {"ess_per_s": n_eff / (t_sweeps * x.shape[1] / n_sweeps), "tau_sweeps": tau, "sweeps": n_sweeps,
+    extra = {}
+    if prefix is not None and prefix < n_sweeps:   # the same estimate from the first `prefix` sweeps only
+        xp = np.array(series[:prefix]).T[:, prefix // 4:]
+        tp = autocorr_time(xp)
+        extra = {"prefix_sweeps": prefix, "tau_sweeps_prefix": tp,
+                 "ess_per_s_prefix": xp.shape[0] * xp.shape[1] / max(tp, 1.0) / (t_sweeps / n_sweeps * xp.shape[1])}
+    return {**extra, "ess_per_s": n_eff / (t_sweeps * x.shape[1] / n_sweeps), "tau_sweeps": tau, "sweeps": n_sweeps,
             "burn_in": n_sweeps // 4, "ms_per_sweep": 1e3 * t_sweeps / n_sweeps,
             "proposals_per_s": float(st[:4, 0].sum()) / t_sweeps,
             "acceptance": {k: float(st[i, 1]) / max(1.0, float(st[i, 0])) for i, k in
@@ -447,13 +453,15 @@ def run_gmm_fit(torch, L, units, n_walkers, args, stream):
 
 def run_search_rj(torch, L, S, ens, data, args, stream):
     """Search-RJ mixtures (Sec. V.E, App. G): every band's search sampler (4 temperatures x 32
-    walkers, own-bin f0 prior) runs on walker 0's residual, relaunched halfway from a ball around
-    each band's best point; bands whose best point reaches SNR 7 give their cold walkers of the
-    last sweeps to one EM fit per band; returns the sweep table [W][n_bands][272] and the
-    timings."""
+    walkers, own-bin f0 prior) runs on walker 0's residual until its best point has not improved
+    for n_it,max = 500 sweeps (App. G's convergence test; a converged band is left as it is),
+    then every band relaunches from a ball around its best point and searches again until it
+    converges; bands whose best point reaches SNR 7 give their cold walkers of 20 more sweeps to
+    one EM fit per band; returns the sweep table [W][n_bands][272] and the timings."""
     dev = data.device
     nb, T_s, W_s = ens["n_bands"], 4, 32
-    plan = L.SearchPlan(S["ctx"], nb, N_BAND, ens["band_k0"], T_s, W_s, L.GBK_MIXED)
+    n_it_max = args.search_stall
+    plan = L.SearchPlan(S["ctx"], nb, N_BAND, ens["band_k0"], T_s, W_s, L.GBK_MIXED, stall_limit=n_it_max)
     u = torch.empty((nb, T_s, W_s, 8), dtype=torch.float64, device=dev)
     ell = torch.empty((nb, T_s, W_s), dtype=torch.float64, device=dev)
     betas = torch.tensor([[0.5 ** t for t in range(T_s)]] * nb, dtype=torch.float64, device=dev)
@@ -461,25 +469,44 @@ def run_search_rj(torch, L, S, ens, data, args, stream):
     bu = torch.zeros((nb, 8), dtype=torch.float64, device=dev)
     stall = torch.zeros(nb, dtype=torch.int32, device=dev)
     st = torch.zeros((2, 2), dtype=torch.int64, device=dev)
-    n_run, n_keep = args.search_rj_sweeps, 20
+    n_keep = 20
     x = torch.empty((nb, n_keep * W_s, 8), dtype=torch.float32, device=dev)
     key = 0x5EA2C4
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sweep = [0]
+
+    def until_converged(cap):
+        # sweeps until every band has converged (checked every 50 sweeps) or `cap` sweeps
+        n = 0
+        while n < cap:
+            for _ in range(50):
+                L.gb_search_sweep(plan, u, ell, betas, S["psd"], key, sweep[0], best=(be, bu, stall), stats=st,
+                                  stream=stream)
+                sweep[0] += 1
+                n += 1
+            if int(stall.min().item()) >= n_it_max:
+                break
+        return n, int((stall >= n_it_max).sum().item())
+
     torch.cuda.synchronize()
     e0.record(stream)
     L.gb_search_init(plan, u, key, 1, stream)
     L.gb_search_windows(plan, L.residual_struct(data, FRAC_BITS), 0, stream)
     L.gb_search_eval(plan, u, ell, S["psd"], 0, stream)
-    for k in range(n_run):
-        if k == n_run // 2:   # relaunch every band's ensemble from a ball around its best point (App. G)
-            L.gb_search_ball(plan, u, be, bu, 0.002, key, 2, stream)
-            L.gb_search_eval(plan, u, ell, S["psd"], 0, stream)
-        L.gb_search_sweep(plan, u, ell, betas, S["psd"], key, k, best=(be, bu, stall), stats=st, stream=stream)
+    n1, conv1 = until_converged(args.search_rj_sweeps)
+    snr1 = torch.sqrt(2.0 * torch.clamp(be, min=0.0)).cpu().numpy()
+    # relaunch every band's ensemble from a ball around its best point (App. G), search again
+    L.gb_search_ball(plan, u, be, bu, 0.002, key, 2, stream)
+    L.gb_search_eval(plan, u, ell, S["psd"], 0, stream)
+    stall.zero_()
+    n2, conv2 = until_converged(args.search_rj_sweeps)
     e1.record(stream)
     torch.cuda.synchronize()
     ms_run = e0.elapsed_time(e1)
+    stall.zero_()   # samples of every band (converged or not) for the mixtures
     for k in range(n_keep):
-        L.gb_search_sweep(plan, u, ell, betas, S["psd"], key, n_run + k, best=(be, bu, stall), stream=stream)
+        L.gb_search_sweep(plan, u, ell, betas, S["psd"], key, sweep[0], best=(be, bu, stall), stream=stream)
+        sweep[0] += 1
         L.gb_search_samples(plan, u, be, 7.0, F_LO, F_HI, x, k * W_s, stream)
     raw = torch.empty((N_W, nb, 272), dtype=torch.float32, device=dev)
     e0.record(stream)
@@ -489,14 +516,14 @@ def run_search_rj(torch, L, S, ens, data, args, stream):
     snr = torch.sqrt(2.0 * torch.clamp(be, min=0.0)).cpu().numpy()
     s = st.cpu().numpy()
     plan.close()
-    out = {"bands": nb, "temps": T_s, "walkers": W_s, "sweeps": n_run, "ball_relaunch_at": n_run // 2,
-           "ball_sigma": 0.002, "sample_sweeps": n_keep,
-           "ms_per_sweep": ms_run / n_run,
-           "proposals_per_s": float(s[0, 0]) / (ms_run * 1e-3),
+    out = {"bands": nb, "temps": T_s, "walkers": W_s, "n_it_max": n_it_max,
+           "sweeps_to_convergence": n1, "bands_converged": conv1, "bands_snr_ge_7_before_relaunch": int((snr1 >= 7).sum()),
+           "sweeps_after_relaunch": n2, "bands_converged_after_relaunch": conv2, "ball_sigma": 0.002,
+           "sample_sweeps": n_keep, "ms_search": ms_run,
+           "stretch_proposals_per_s": float(s[0, 0]) / (ms_run * 1e-3),
            "stretch_acceptance": float(s[0, 1]) / max(1.0, float(s[0, 0])),
            "swap_acceptance": float(s[1, 1]) / max(1.0, float(s[1, 0])),
            "bands_snr_ge_7": int((snr >= 7.0).sum()), "best_snr_median": float(np.median(snr)),
-           "bands_still_improving_last_50": int((stall.cpu().numpy() < 50).sum()),
            "fit_ms": e0.elapsed_time(e1), "snr_min": 7.0}
     return raw, out
 
@@ -851,7 +878,7 @@ def run_ours(args):
             pairs = PR.PairBuffer(args.mdn_samples)
             units = []
         ess = run_ess(torch, L, S, step, stats, stream, args.ess_sweeps, pairs=pairs, units=units,
-                      keep=args.gmm_keep)
+                      keep=args.gmm_keep, prefix=args.fp64_sweeps)
         if args.group_frac > 0:   # the paper's in-model move: group stretch, group rebuilt every 30 sweeps
             S["P"].copy_(snap[0])
             S["E"].copy_(snap[1])
@@ -1006,10 +1033,13 @@ def run_ours(args):
     }
     line["config"].update(fp64)
     if fp64:
+        # ESS/s ratio on equal footing: the mixed sweep's estimate from its first fp64_sweeps sweeps
+        # (same estimator, same run length as the float64 run)
         line["vs_plain_fp64"] = {
             "batched_mixed_over_fp64_sweep_proposals": value / fp64["fp64_sweep_proposals_per_s"],
             "batched_mixed_over_fp64_per_band_proposals": value / fp64["fp64_per_band_proposals_per_s"],
-            "ess_per_s_mixed_over_fp64_sweep": (ess["ess_per_s"] / fp64["fp64_sweep"]["ess_per_s"]) if ess else None}
+            "ess_per_s_mixed_over_fp64_sweep_same_run_length":
+                (ess["ess_per_s_prefix"] / fp64["fp64_sweep"]["ess_per_s"]) if ess and "ess_per_s_prefix" in ess else None}
     if sched30:
         line["schedule_30_1_1"] = sched30
     if c3:
@@ -1064,7 +1094,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison runs")
-    ap.add_argument("--fp64-sweeps", type=int, default=24, help="sweeps of the float64 ESS run")
+    ap.add_argument("--fp64-sweeps", type=int, default=48, help="sweeps of the float64 ESS run")
     ap.add_argument("--pps30-sweeps", type=int, default=40,
                     help="sweeps of the 30-in-model-proposals-per-source schedule (0: skip)")
     ap.add_argument("--no-c3", action="store_true", help="skip the total log-likelihood (HBM) measurement")
@@ -1079,7 +1109,9 @@ def main():
     ap.add_argument("--mdn-inmodel", type=float, default=0.1, help="fraction of in-model moves drawn from it")
     ap.add_argument("--search-sweeps", type=int, default=10)
     ap.add_argument("--gmm-keep", type=int, default=10, help="sweeps of cold-chain sources for the mixture refit")
-    ap.add_argument("--search-rj-sweeps", type=int, default=1000, help="search-sampler sweeps before sampling")
+    ap.add_argument("--search-rj-sweeps", type=int, default=3000,
+                    help="cap on the search-sampler sweeps of each phase (before and after the relaunch)")
+    ap.add_argument("--search-stall", type=int, default=500, help="n_it,max of the search's convergence test")
     ap.add_argument("--gmm-iters", type=int, default=50, help="EM iterations of the mixture refit")
     ap.add_argument("--group-frac", type=float, default=0.5, help="fraction of in-model moves that are group stretches "
                                                                    "in the group-stretch ESS run (0: skip it)")

@@ -518,6 +518,9 @@ typedef struct gbk_search_desc {
   double ln_a_min, ln_a_max, mc_min, mc_max;        /* prior bounds (chirp mass in M_sun) */
   double stretch_a;       /* stretch scale a > 1 (2 in the paper's sampler) */
   int32_t precision;      /* GBK_MIXED or GBK_FP64 (waveforms and inner products) */
+  int32_t stall_limit;    /* n_it,max: a band whose best point has not improved for this many sweeps
+                             has converged and is frozen (no moves, swaps or best-point updates in
+                             later sweeps until its stall count is reset); 0: never */
 } gbk_search_desc;
 
 typedef struct gbk_search gbk_search;
@@ -538,7 +541,8 @@ gbk_status gb_search_eval(gbk_search* plan, const double* u, double* ell, const 
 /* One sweep; u and ell (consistent, e.g. from gb_search_eval) are updated in place.
  *   betas     [n_bands][n_temps] float64 (device)
  *   best_ell  [n_bands] float64, best_u [n_bands][8], stall [n_bands] int32 (device, in/out;
- *             start best_ell at -inf); all three or none
+ *             start best_ell at -inf); all three or none, and all three with a stall_limit: the
+ *             bands whose stall count has reached it at the start of the sweep are left as they are
  *   stats     optional int64[2][2] (device): stretch proposals, accepted; swaps, accepted (added) */
 gbk_status gb_search_sweep(gbk_search* plan, double* u, double* ell, const double* betas, const gbk_psd* psd,
                            int32_t psd_walker, uint64_t key, uint32_t sweep_index, double* best_ell, double* best_u,
@@ -596,7 +600,7 @@ gbk_status gb_sweep_features(gbk_sweep* plan, const double* params, const uint8_
  * Its scratch (the float32 shape tables and the cross-block partial sums) is a fixed array
  * of total_loglike_noalloc_capacity() doubles (16 MiB) in the library's device memory, held
  * on every device that loads the library until the process exits. A call needs
- * n_bins + 2 W ceil(n_bins / 4096) + ceil(n_bins / 4096) doubles and W <= 262140; larger
+ * n_bins + 2 W ceil(n_bins / 8192) + ceil(n_bins / 4096) doubles and W <= 262140; larger
  * requests return GBK_ERANGE. Every call overwrites all the scratch it reads, so earlier
  * contents do not matter; but all calls share the one array, so calls that overlap on the
  * GPU (different streams, or host threads without ordering) race and give wrong results:

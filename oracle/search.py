@@ -59,6 +59,9 @@ class SearchConfig:
         self.mc_min = kw.get("mc_min", 0.3)
         self.mc_max = kw.get("mc_max", 0.8)
         self.df = 1.0 / self.tobs
+        # n_it,max (App. G): a band whose best point has not improved for this many sweeps has
+        # converged and is left as it is; 0: never
+        self.stall_limit = kw.get("stall_limit", 0)
 
     def core(self, b):
         lo = self.band_k0 + b * self.nb
@@ -189,10 +192,11 @@ def sweep(cfg, rwins, u, ell, s, fn=None, trace=None, bands=None):
     return trace
 
 
-def best_update(u, ell, best_ell, best_u, stall):
-    """After a sweep: the largest cold-chain l of every band (first walker on ties) replaces the
-    band's best point if larger (stall = 0), else stall += 1. Arrays updated in place."""
-    for b in range(ell.shape[0]):
+def best_update(u, ell, best_ell, best_u, stall, bands=None):
+    """After a sweep: the largest cold-chain l of every band (or of the listed bands; first walker
+    on ties) replaces the band's best point if larger (stall = 0), else stall += 1. Arrays updated
+    in place."""
+    for b in (range(ell.shape[0]) if bands is None else bands):
         k = int(np.argmax(ell[b, 0]))
         if ell[b, 0, k] > best_ell[b]:
             best_ell[b] = ell[b, 0, k]
@@ -200,6 +204,22 @@ def best_update(u, ell, best_ell, best_u, stall):
             stall[b] = 0
         else:
             stall[b] += 1
+
+
+def converged(cfg, stall):
+    """Bands whose search has converged (App. G): n_it,max = stall_limit sweeps without a better
+    best point."""
+    return [b for b in range(cfg.n_bands) if cfg.stall_limit > 0 and stall[b] >= cfg.stall_limit]
+
+
+def search_sweep(cfg, rwins, u, ell, s, best_ell, best_u, stall, fn=None, trace=None):
+    """One sweep with the convergence test: the bands that have converged at its start are left as
+    they are, the others sweep and update their best points."""
+    done = set(converged(cfg, stall))
+    active = [b for b in range(cfg.n_bands) if b not in done]
+    trace = sweep(cfg, rwins, u, ell, s, fn=fn, trace=trace, bands=active)
+    best_update(u, ell, best_ell, best_u, stall, bands=active)
+    return trace
 
 
 def to_sweep_unit(cfg, b, u, f_min, f_max):

@@ -56,7 +56,7 @@ class GbkSearchDesc(ctypes.Structure):
     _fields_ = [("n_bands", _i32), ("band_bins", _i32), ("n_temps", _i32), ("n_walkers", _i32),
                 ("band_k0", ctypes.c_int64), ("ln_a_min", ctypes.c_double), ("ln_a_max", ctypes.c_double),
                 ("mc_min", ctypes.c_double), ("mc_max", ctypes.c_double), ("stretch_a", ctypes.c_double),
-                ("precision", _i32)]
+                ("precision", _i32), ("stall_limit", _i32)]
 
 
 class GbkTraceRec(ctypes.Structure):
@@ -580,13 +580,15 @@ class SearchPlan:
     """Owns a gbk_search plan (per-band search sampler of the search-RJ proposal)."""
 
     def __init__(self, ctx, n_bands, band_bins, band_k0, n_temps, n_walkers, precision=GBK_MIXED,
-                 ln_a_min=math.log(1e-23), ln_a_max=math.log(10 ** -21.5), mc_min=0.3, mc_max=0.8, stretch_a=2.0):
+                 ln_a_min=math.log(1e-23), ln_a_max=math.log(10 ** -21.5), mc_min=0.3, mc_max=0.8, stretch_a=2.0,
+                 stall_limit=0):
         d = GbkSearchDesc()
         d.n_bands, d.band_bins, d.n_temps, d.n_walkers = int(n_bands), int(band_bins), int(n_temps), int(n_walkers)
         d.band_k0 = int(band_k0)
         d.ln_a_min, d.ln_a_max, d.mc_min, d.mc_max = float(ln_a_min), float(ln_a_max), float(mc_min), float(mc_max)
         d.stretch_a = float(stretch_a)
         d.precision = int(precision)
+        d.stall_limit = int(stall_limit)
         self.desc = d
         h = _vp()
         _check(lib().gbk_search_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)), "gbk_search_create")

@@ -1930,7 +1930,14 @@ struct SearchArgs {
   const double* betas; // [B][T]
   int psd_walker;
   long long* stats;    // [2][2]: stretch proposals, accepted; swaps, accepted
+  const int32_t* stall;  // [B] sweeps without a better point (NULL: no convergence test)
+  int stall_limit;       // a band with stall >= stall_limit has converged: left as it is
 };
+
+// Has band b's search converged (App. G: n_it,max sweeps without a better point)?
+__device__ __forceinline__ bool search_frozen(const SearchArgs& a, int b) {
+  return a.stall && a.stall_limit > 0 && a.stall[b] >= a.stall_limit;
+}
 
 // per warp: the FFT buffers and the set-up of a batch of 32 chains (one lane each)
 template <typename T, int N>
@@ -2056,11 +2063,13 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_half(const SearchA
   // float64 source set-up lane-parallel, then the waveforms and decisions one chain at a time
   for (int g0 = (blockIdx.x * wpc + wid) * bs; g0 < n; g0 += gridDim.x * wpc * bs) {
     const int cnt = min(bs, n - g0);
+    bool live = false;
     if (lane < cnt) {
       const int e = g0 + lane;
       const int b = e / (T_ * half), r = e % (T_ * half);
       const int t = r / half, k = h * half + r % half;
       const int64_t ck = ((int64_t)b * T_ + t) * W + k;
+      live = !search_frozen(a, b);
       const U4 wv = philox4x32_10((uint32_t)ck, (uint32_t)h, 7u, sweep, k0, k1);
       const int j = (1 - h) * half + (int)ranged(wv.x, (uint32_t)half);
       const double zz = dadd(dmul(dsub(a.d.stretch_a, 1.0), u32(wv.y)), 1.0);
@@ -2073,10 +2082,12 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_half(const SearchA
         S.y[lane][c] = y;
         if (!(y >= 0.0 && y <= 1.0)) inb = 0;
       }
+      if (!live) inb = 0;   // a converged band: no move (and not counted)
       S.inb[lane] = inb;
       S.lz[lane] = log(z);
       if (inb) search_prep<T, N>(a, S, lane, b, S.y[lane]);
     }
+    const int n_live = __popc(__ballot_sync(0xffffffffu, live));
     __syncwarp();
     int n_acc = 0;
     for (int q = 0; q < cnt; ++q) {
@@ -2098,7 +2109,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_half(const SearchA
       }
     }
     if (lane == 0 && a.stats) {
-      atomicAdd((unsigned long long*)&a.stats[0], (unsigned long long)cnt);
+      atomicAdd((unsigned long long*)&a.stats[0], (unsigned long long)n_live);
       if (n_acc) atomicAdd((unsigned long long*)&a.stats[1], (unsigned long long)n_acc);
     }
     __syncwarp();
@@ -2111,6 +2122,7 @@ __global__ void k_search_swap(const SearchArgs a, uint32_t sweep, uint32_t k0, u
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= a.d.n_bands * W) return;
   const int b = x / W, w = x % W;
+  if (search_frozen(a, b)) return;
   int n = 0, na = 0;
   for (int t = T_ - 1; t > 0; --t) {
     const U4 wv = philox4x32_10((uint32_t)x, (uint32_t)t, 8u, sweep, k0, k1);
@@ -2140,7 +2152,7 @@ __global__ void k_search_swap(const SearchArgs a, uint32_t sweep, uint32_t k0, u
 // best point of every band: the largest cold-chain l (first walker on ties) if it improves
 __global__ void k_search_best(const SearchArgs a, double* best_ell, double* best_u, int32_t* stall) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= a.d.n_bands) return;
+  if (b >= a.d.n_bands || search_frozen(a, b)) return;
   const int W = a.d.n_walkers;
   const double* l = a.ell + (int64_t)b * a.d.n_temps * W;
   int k = 0;
@@ -2282,6 +2294,7 @@ extern "C" gbk_status gbk_search_create(gbk_ctx* ctx, const gbk_search_desc* des
     return set_error(GBK_EINVAL, "gbk_search_create: bad sizes (B=%d T=%d W=%d N=%d; W even, >= 4)", d.n_bands,
                      d.n_temps, d.n_walkers, d.band_bins);
   if (d.precision != GBK_MIXED && d.precision != GBK_FP64) return set_error(GBK_EINVAL, "gbk_search_create: bad precision");
+  if (d.stall_limit < 0) return set_error(GBK_EINVAL, "gbk_search_create: stall_limit < 0");
   if (!(d.stretch_a > 1.0) || !(d.ln_a_min < d.ln_a_max) || !(d.mc_min < d.mc_max) || !(d.mc_min > 0.0))
     return set_error(GBK_EINVAL, "gbk_search_create: bad prior bounds or stretch scale");
   const int64_t lo = d.band_k0 - d.band_bins - ctx->grid.k0;
@@ -2361,8 +2374,12 @@ extern "C" gbk_status gb_search_sweep(gbk_search* p, double* u, double* ell, con
     return set_error(GBK_EINVAL, "gb_search_sweep: psd_walker %d outside the PSD's %d", psd_walker, psd->n_psd);
   if ((best_ell || best_u || stall) && !(best_ell && best_u && stall))
     return set_error(GBK_EINVAL, "gb_search_sweep: best_ell, best_u and stall go together");
+  if (p->d.stall_limit > 0 && !stall)
+    return set_error(GBK_EINVAL, "gb_search_sweep: a plan with a stall limit needs best_ell, best_u and stall");
   SearchArgs a = search_args(p, u, ell, betas, psd, psd_walker);
   a.stats = (long long*)stats;
+  a.stall = stall;
+  a.stall_limit = p->d.stall_limit;
   const uint32_t k0 = (uint32_t)(key & 0xffffffffu), k1 = (uint32_t)(key >> 32);
   cudaStream_t st = (cudaStream_t)stream;
   gbk_status s = p->d.precision == GBK_MIXED ? search_dispatch<float>(a, 1, sweep_index, k0, k1, st)

@@ -31,12 +31,13 @@ def _setup():
     return scfg, dfix
 
 
-def _gpu(torch, scfg, dfix, precision, n_sweeps):
+def _gpu(torch, scfg, dfix, precision, n_sweeps, stall_limit=0):
     from paper_2405_04690_gb300 import _lib as L
     from paper_2405_04690_gb300 import synth
     dev = torch.device("cuda")
     ctx = L.Context(scfg.tobs, 15.0, scfg.k0, scfg.n_bins)
-    plan = L.SearchPlan(ctx, scfg.n_bands, NB, scfg.band_k0, scfg.n_temps, scfg.n_walkers, precision)
+    plan = L.SearchPlan(ctx, scfg.n_bands, NB, scfg.band_k0, scfg.n_temps, scfg.n_walkers, precision,
+                        stall_limit=stall_limit)
     R = torch.from_numpy(dfix[None].copy()).to(dev).contiguous()
     psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
     PS = L.psd_struct(psdp)
@@ -163,3 +164,34 @@ def test_search_ball_relaunch_matches_oracle():
     assert int(stats[0, 1].item()) == n_acc and n_acc > 0
     plan.close()
     ctx.close()
+
+
+def test_search_fp64_with_convergence_matches_oracle():
+    # App. G's convergence test (n_it,max = 2 here): bands whose best point has not improved for
+    # two sweeps are left as they are; over 10 sweeps the bands converge at different sweeps, and
+    # walkers, best points, stall counts and move counts equal the oracle's bit for bit
+    torch = torch_cuda()
+    from paper_2405_04690_gb300 import _lib as L
+    scfg, dfix = _setup()
+    scfg.stall_limit = 2
+    rw = SR.windows(scfg, dfix, FRAC)
+    u = SR.init(scfg, SEED)
+    ell = SR.evaluate(scfg, rw, u)
+    scale = np.abs(ell).max(axis=(1, 2))[:, None, None]
+    best, bu, stall = np.full(3, -np.inf), np.zeros((3, 8)), np.zeros(3, dtype=np.int64)
+    trace, frozen_at = [], {}
+    for k in range(10):
+        for b in SR.converged(scfg, stall):
+            frozen_at.setdefault(b, k)
+        SR.search_sweep(scfg, rw, u, ell, k, best, bu, stall, trace=trace)
+    assert len(frozen_at) >= 1, stall
+    _, _, ug, lg, bg, bug, sg, st, _ = _gpu(torch, scfg, dfix, L.GBK_FP64, 10, stall_limit=2)
+    assert np.array_equal(ug, u)
+    assert (np.abs(lg - ell) <= 1e-8 * scale).all()
+    assert np.array_equal(bug, bu) and np.array_equal(sg, stall)
+    assert (np.abs(bg - best) <= 1e-8 * scale[:, 0, 0]).all()
+    n_str = sum(1 for r in trace if r["kind"] == 7)
+    n_str_acc = sum(1 for r in trace if r["kind"] == 7 and r["accepted"])
+    n_sw = sum(1 for r in trace if r["kind"] == 8)
+    n_sw_acc = sum(1 for r in trace if r["kind"] == 8 and r["accepted"])
+    assert st.tolist() == [[n_str, n_str_acc], [n_sw, n_sw_acc]]

@@ -145,3 +145,35 @@ def test_ball_relaunch_is_a_clipped_normal_around_the_best_point():
     assert stats.kstest(z.ravel(), "norm").pvalue > 1e-3
     assert abs(z.mean()) < 0.1 and abs(z.std() - 1) < 0.1
     assert (u[2, ..., 0] >= 0).all() and (u[2, ..., 0] == 0).any()     # clipped at the box edge
+
+
+def test_converged_bands_are_left_as_they_are():
+    # App. G: a band whose best point has not improved for n_it,max sweeps has converged. With a
+    # flat likelihood (bands 0 and 2) the best point is set by the first sweep and never improves,
+    # so those bands converge after stall_limit more sweeps and then stay exactly as they are (no
+    # records, no moves, stall count frozen); band 1 (a peaked target) keeps sweeping while its
+    # best point improves
+    cfg = _cfg(n_bands=3)
+    cfg.stall_limit = 2
+
+    def fn(b, x):
+        return 0.0 if b != 1 else -0.5 * float(np.sum((x - 0.5) ** 2)) / 0.02 ** 2
+
+    u = SR.init(cfg, 5)
+    ell = SR.evaluate(cfg, None, u, fn)
+    best, bu, stall = np.full(3, -np.inf), np.zeros((3, 8)), np.zeros(3, dtype=np.int64)
+    for k in range(8):
+        done = SR.converged(cfg, stall)
+        before = (u.copy(), ell.copy(), best.copy(), stall.copy())
+        trace = SR.search_sweep(cfg, None, u, ell, k, best, bu, stall, fn=fn)
+        for b in done:
+            assert np.array_equal(u[b], before[0][b]) and np.array_equal(ell[b], before[1][b])
+            assert best[b] == before[2][b] and stall[b] == before[3][b]
+            assert not any(r["b"] == b for r in trace)
+        for b in set(range(3)) - set(done):
+            assert any(r["b"] == b for r in trace)
+        if k == 0:
+            assert stall.tolist() == [0, 0, 0]
+    # flat bands: best at sweep 0, stall 1 after sweep 1, 2 after sweep 2: converged from sweep 3
+    assert SR.converged(cfg, stall)[:1] == [0] and 2 in SR.converged(cfg, stall)
+    assert stall[0] == 2 and stall[2] == 2
