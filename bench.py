@@ -1086,8 +1086,51 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kernel_case(args):
+    """One small workload of a single kernel, for profiler captures (no JSON line):
+    total_loglike: three total_loglike calls on 64 walkers x 2 ch x 2^20 bins (1.07 GB of float32
+    residual, larger than L2); dlogl_1024: three Delta lnL batches of 20,000 proposals with
+    1024-bin bands (f0 log-uniform in 4-20 mHz, one walker's zero residual), mixed precision."""
+    import torch
+    from paper_2405_04690_gb300 import _lib as L
+    from paper_2405_04690_gb300 import synth
+    dev = torch.device("cuda")
+    if args.kernel_case == "total_loglike":
+        g = synth.rng(3)
+        n, w, k0 = 1 << 20, 64, 3146
+        ctx = L.Context(TOBS, DT, k0, n)
+        pp = torch.from_numpy(synth.draw_psd_params(g, w)).to(dev)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(3)
+        r = torch.randn((w, 2, n, 2), dtype=torch.float32, device=dev, generator=gen) * 1e-17
+        out = torch.empty(w, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            L.total_loglike(ctx, r, pp, out)
+    else:
+        g = synth.rng(5)
+        m = 20000
+        p = synth.draw_sources(g, m, 4e-3, 2e-2, log_f=True)
+        new = synth.perturb(g, p, synth.proposal_widths(p))
+        k0, nbins = synth.window_for(3.9e-3, 2.05e-2, 1100)
+        ctx = L.Context(TOBS, DT, k0, nbins)
+        psdp = torch.tensor([[synth.SQRT_S_OMS, synth.SQRT_S_ACC]], dtype=torch.float64, device=dev)
+        resid = torch.zeros((1, 2, nbins, 2), dtype=torch.int64, device=dev)
+        pn = torch.from_numpy(np.ascontiguousarray(new)).to(dev)
+        po = torch.from_numpy(np.ascontiguousarray(p)).to(dev)
+        nb = torch.full((m,), 1024, dtype=torch.int32, device=dev)
+        wk = torch.zeros(m, dtype=torch.int32, device=dev)
+        out = torch.empty(m, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            L.gb_delta_loglike_batch(ctx, pn, po, nb, 1024, wk, L.residual_struct(resid, FRAC_BITS), L.psd_struct(psdp),
+                                     out, L.GBK_MIXED)
+    torch.cuda.synchronize()
+    L.gbk_sync_status(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--kernel-case", choices=["total_loglike", "dlogl_1024"], default=None,
+                    help="run one small single-kernel workload for a profiler capture and exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
@@ -1117,7 +1160,9 @@ def main():
                                                                    "in the group-stretch ESS run (0: skip it)")
     ap.add_argument("--n-friends", type=int, default=32)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.kernel_case:
+        run_kernel_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
