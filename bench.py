@@ -1090,7 +1090,10 @@ def run_kernel_case(args):
     """One small workload of a single kernel, for profiler captures (no JSON line):
     total_loglike: three total_loglike calls on 64 walkers x 2 ch x 2^20 bins (1.07 GB of float32
     residual, larger than L2); dlogl_1024: three Delta lnL batches of 20,000 proposals with
-    1024-bin bands (f0 log-uniform in 4-20 mHz, one walker's zero residual), mixed precision."""
+    1024-bin bands (f0 log-uniform in 4-20 mHz, one walker's zero residual), mixed precision;
+    mdn_train: the learned proposal's network on 40,960 random pairs, batch 4096: device times
+    of the forward pass, forward + backward, the Adam step and one step of a training epoch
+    (printed as one JSON line, microseconds)."""
     import torch
     from paper_2405_04690_gb300 import _lib as L
     from paper_2405_04690_gb300 import synth
@@ -1106,6 +1109,47 @@ def run_kernel_case(args):
         out = torch.empty(w, dtype=torch.float64, device=dev)
         for _ in range(3):
             L.total_loglike(ctx, r, pp, out)
+    elif args.kernel_case == "mdn_train":
+        from paper_2405_04690_gb300 import proposal as PR
+        batch, n = 4096, 40960
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(7)
+        buf = PR.PairBuffer(n)
+        buf.x.copy_(torch.randn((n, PR.N_IN), device=dev, generator=gen).to(torch.bfloat16))
+        buf.u.copy_(torch.rand((n, PR.N_DIM), device=dev, generator=gen) * 0.98 + 0.01)
+        buf.n = n
+        net = L.Mdn(batch)
+        tr = PR.Trainer(net, torch.from_numpy(PR.init_params(11)).to(dev), lr=1e-3)
+        tr.epoch(buf, batch, seed=0, max_steps=3)
+        raw = torch.empty((batch, PR.N_OUT), dtype=torch.float32, device=dev)
+        grad = torch.empty_like(tr.p)
+        x, u = buf.x[:batch], buf.u[:batch]
+        st = torch.cuda.current_stream()
+        times = {}
+        for name, fn in (("forward", lambda: L.mdn_forward(net, x, raw)),
+                         ("forward_backward", lambda: L.mdn_backward(net, x, u, grad)),
+                         ("adam", lambda: L.mdn_adam(net, tr.p, tr.m, tr.v, grad, 10, 1e-3)),
+                         ("train_epoch_step", lambda: tr.epoch(buf, batch, seed=1))):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 1 if name == "train_epoch_step" else 20
+            e0.record(st)
+            for _ in range(reps):
+                fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            per = e0.elapsed_time(e1) * 1e3 / reps
+            times[name] = per / (n // batch) if name == "train_epoch_step" else per
+        # host time to enqueue one epoch (the call returns before the device finishes)
+        order = torch.arange(n, dtype=torch.int32, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.mdn_train_epoch(net, tr.p, tr.m, tr.v, buf.x, buf.u, order, batch, 100, 1e-3)
+        t1 = time.perf_counter()
+        torch.cuda.synchronize()
+        times["host_enqueue_per_step"] = (t1 - t0) * 1e6 / (n // batch)
+        print(json.dumps({"mdn_train_us": times, "batch": batch}))
     else:
         g = synth.rng(5)
         m = 20000
@@ -1124,12 +1168,15 @@ def run_kernel_case(args):
             L.gb_delta_loglike_batch(ctx, pn, po, nb, 1024, wk, L.residual_struct(resid, FRAC_BITS), L.psd_struct(psdp),
                                      out, L.GBK_MIXED)
     torch.cuda.synchronize()
-    L.gbk_sync_status(ctx)
+    if args.kernel_case == "mdn_train":
+        L.mdn_status(net)
+    else:
+        L.gbk_sync_status(ctx)
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel-case", choices=["total_loglike", "dlogl_1024"], default=None,
+    ap.add_argument("--kernel-case", choices=["total_loglike", "dlogl_1024", "mdn_train"], default=None,
                     help="run one small single-kernel workload for a profiler capture and exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)

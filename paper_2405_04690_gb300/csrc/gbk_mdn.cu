@@ -46,6 +46,29 @@ typedef __nv_bfloat16 bf16;
 constexpr int64_t kOffT2 = 0, kOffT3 = 2 * (int64_t)kHid * kHid, kOffT4 = 4 * (int64_t)kHid * kHid;
 constexpr int64_t kNT = kOffT4 + 2 * (int64_t)kHid * kOut;
 
+// Launch with programmatic stream serialization (see griddep_wait): every kernel launched this
+// way calls griddep_wait() before it touches global memory.
+template <typename... KArgs, typename... Args>
+static gbk_status launch_pdl(const char* what, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k, args...);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(GBK_ECUDA, "%s: launch failed: %s", what, cudaGetErrorString(e));
+  }
+  return GBK_OK;
+}
+
 // -------------------------------------------------------------- tensor-core products
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -120,8 +143,8 @@ static gbk_status mm(gbk_mdn* net, const bf16* A, int64_t lda, const bf16* B, in
   g.K = K;
   if (splits <= 1) g.kps = K;
   dim3 grid((N + kBN - 1) / kBN, (M + umma::kBM - 1) / umma::kBM, splits > 1 ? splits : 1);
-  umma::k_umma<kBN, EPI><<<grid, umma::kThreads, SM::bytes, st>>>(ma, mb, g);
-  return check_launch("mdn tensor-core product");
+  return launch_pdl("mdn tensor-core product", umma::k_umma<kBN, EPI>, grid, dim3(umma::kThreads), SM::bytes, st, ma,
+                    mb, g);
 }
 
 static umma::Args margs(gbk_mdn* net, void* C, int64_t ldc) {
@@ -140,57 +163,83 @@ static umma::Args margs(gbk_mdn* net, void* C, int64_t ldc) {
   return g;
 }
 
-// Transposes through 32 x 32 shared-memory tiles. split = 0: x [B][cols] -> xt[c][r] and the
-// copy xt[c][B + r]; split = 1: x [B][2 cols] = [hi | lo] -> xt[c][r] = hi, xt[c][B + r] = lo.
-__global__ void k_transpose(const bf16* __restrict__ x, int B, int cols, int split, bf16* __restrict__ xt,
-                            int64_t ldt) {
-  __shared__ bf16 t[2][32][33];
+// Transposes x [B][cols] through 32 x 32 shared-memory tiles into [x^T | x^T]: xt[c][r] and
+// xt[c][B + r].
+__global__ void k_transpose(const bf16* __restrict__ x, int B, int cols, bf16* __restrict__ xt, int64_t ldt) {
+  umma::griddep_wait();
+  umma::griddep_launch();
+  __shared__ bf16 t[32][33];
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  const int64_t ldx = split ? 2 * (int64_t)cols : cols;
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int r = r0 + i, c = c0 + threadIdx.x;
-    if (r < B && c < cols) {
-      t[0][i][threadIdx.x] = x[(int64_t)r * ldx + c];
-      t[1][i][threadIdx.x] = split ? x[(int64_t)r * ldx + cols + c] : t[0][i][threadIdx.x];
-    }
+    if (r < B && c < cols) t[i][threadIdx.x] = x[(int64_t)r * cols + c];
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int c = c0 + i, r = r0 + threadIdx.x;
     if (r < B && c < cols) {
-      xt[(int64_t)c * ldt + r] = t[0][threadIdx.x][i];
-      xt[(int64_t)c * ldt + B + r] = t[1][threadIdx.x][i];
+      xt[(int64_t)c * ldt + r] = t[threadIdx.x][i];
+      xt[(int64_t)c * ldt + B + r] = t[threadIdx.x][i];
     }
   }
 }
 
-// Training rows of one minibatch: x[order[i]] -> xb[i] (16-byte chunks), u[order[i]] -> ub[i].
-__global__ void k_gather(const bf16* __restrict__ x, const float* __restrict__ u, const int32_t* __restrict__ order,
-                         int B, int64_t n_rows, bf16* __restrict__ xb, float* __restrict__ ub, int* err) {
-  const int64_t total = (int64_t)B * (kIn / 8);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(i / (kIn / 8)), c = (int)(i % (kIn / 8));
-    const int32_t src = order[r];
+// Training rows of one minibatch and their transposed copy in one pass: a block takes 64 rows x
+// 64 features, x[order[r]] -> xb[r] (16-byte chunks), and through a shared-memory tile
+// xT[c][r] = xT[c][B + r] = x[order[r]][c] ([x^T | x^T], the weight-gradient product's B
+// operand). u[order[r]] -> ub[r] by the blocks of the first feature column.
+__global__ void __launch_bounds__(256) k_gather_t(const bf16* __restrict__ x, const float* __restrict__ u,
+                                                  const int32_t* __restrict__ order, int B, int64_t n_rows,
+                                                  bf16* __restrict__ xb, float* __restrict__ ub,
+                                                  bf16* __restrict__ xT, int64_t ldt, int* err) {
+  umma::griddep_wait();
+  umma::griddep_launch();
+  __shared__ uint32_t t[64][33];   // 64 rows x 64 BF16 (pairs), odd pitch: column reads hit 32 banks
+  const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
+  for (int idx = threadIdx.x; idx < 64 * 8; idx += 256) {
+    const int r = idx >> 3, c8 = idx & 7;
+    const int row = r0 + r;
+    if (row >= B) continue;
+    const int32_t src = order[row];
+    uint4 q = make_uint4(0, 0, 0, 0);
     if (src < 0 || src >= n_rows) {   // bad index: zero row, error bit, nothing read
-      if (c == 0) atomicOr(err, 4);
-      reinterpret_cast<uint4*>(xb + (int64_t)r * kIn)[c] = make_uint4(0, 0, 0, 0);
-      if (c < kMixDim) ub[(int64_t)r * kMixDim + c] = 0.5f;
-      continue;
+      if (c8 == 0) atomicOr(err, 4);
+      if (blockIdx.x == 0 && c8 == 0)
+        for (int d = 0; d < kMixDim; ++d) ub[(int64_t)row * kMixDim + d] = 0.5f;
+    } else {
+      q = reinterpret_cast<const uint4*>(x + (int64_t)src * kIn + c0)[c8];
+      if (blockIdx.x == 0 && c8 == 0)
+        for (int d = 0; d < kMixDim; ++d) ub[(int64_t)row * kMixDim + d] = u[(int64_t)src * kMixDim + d];
     }
-    reinterpret_cast<uint4*>(xb + (int64_t)r * kIn)[c] = reinterpret_cast<const uint4*>(x + (int64_t)src * kIn)[c];
-    if (c < kMixDim) ub[(int64_t)r * kMixDim + c] = u[(int64_t)src * kMixDim + c];
+    reinterpret_cast<uint4*>(xb + (int64_t)row * kIn + c0)[c8] = q;
+    t[r][4 * c8] = q.x;
+    t[r][4 * c8 + 1] = q.y;
+    t[r][4 * c8 + 2] = q.z;
+    t[r][4 * c8 + 3] = q.w;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = warp; c < 64; c += 8) {
+    bf16* dst = xT + (int64_t)(c0 + c) * ldt;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = lane + 32 * h;
+      if (r0 + r >= B) continue;
+      const uint32_t w = t[r][c >> 1];
+      const unsigned short bits = (c & 1) ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu);
+      const bf16 v = __ushort_as_bfloat16(bits);
+      dst[r0 + r] = v;
+      dst[B + r0 + r] = v;
+    }
   }
 }
 
 // -------------------------------------------------------------- loss and its gradient
-// One warp per sample; lane k + 16 h handles component k, dimensions 4h .. 4h + 3.
-// -ln q and d(-ln q)/d raw (the same formulas as the float64 oracle), gradient scaled
-// by 1/B and stored as BF16 for the backward products; per-sample losses to nll[m].
-__global__ void k_mdn_loss(const float* __restrict__ raw, const float* __restrict__ u, int B, float inv_b,
-                           bf16* __restrict__ graw, float* __restrict__ nll) {
-  const int lane = threadIdx.x & 31;
-  const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (m >= B) return;
+// -ln q of sample m and d(-ln q)/d raw (the same formulas as the float64 oracle), the gradient
+// scaled by 1/B as BF16 pairs into grow = [hi 272 | lo 272]; one warp, lane k + 16 h handles
+// component k, dimensions 4h .. 4h + 3.
+__device__ __forceinline__ void loss_row(const float* __restrict__ raw, const float* __restrict__ u, int m, int lane,
+                                         float inv_b, bf16* grow, float* __restrict__ nll) {
   const int k = lane & 15, h = lane >> 4;
   const float* r = raw + (int64_t)m * kOut + k * 17;
   const float lg = r[0];
@@ -225,7 +274,7 @@ __global__ void k_mdn_loss(const float* __restrict__ raw, const float* __restric
   for (int o = 8; o > 0; o >>= 1) ce += __shfl_xor_sync(0xffffffffu, ce, o);
   const float lq = cm + logf(ce);
   const float resp = expf(comp - lq);
-  bf16* gr = graw + (int64_t)m * 2 * kOut + k * 17;   // [hi | lo] pairs, row of 2 x 272
+  bf16* gr = grow + k * 17;   // [hi | lo] pairs, row of 2 x 272
   auto put = [&](int j, float v) {
     const bf16 hi = __float2bfloat16_rn(v);
     gr[j] = hi;
@@ -244,8 +293,38 @@ __global__ void k_mdn_loss(const float* __restrict__ raw, const float* __restric
   if (lane == 0) nll[m] = -lq;
 }
 
+// A block of 16 warps takes 16 samples, one per warp (loss_row into a shared-memory tile), then
+// writes the gradient rows graw[m] = [hi 272 | lo 272] and their transposed copy gT[j][m] = hi,
+// gT[j][B + m] = lo (the weight-gradient product's A operand); per-sample losses to nll[m].
+constexpr int kLossRows = 16, kLossPitch = 2 * kMixOut + 2;   // odd word pitch: column reads hit distinct banks
+__global__ void __launch_bounds__(kLossRows * 32, 2)
+k_mdn_loss(const float* __restrict__ raw, const float* __restrict__ u, int B, float inv_b, bf16* __restrict__ graw,
+           bf16* __restrict__ gT, int64_t ldt, float* __restrict__ nll) {
+  umma::griddep_wait();
+  umma::griddep_launch();
+  __shared__ __align__(16) bf16 tile[kLossRows][kLossPitch];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int m0 = blockIdx.x * kLossRows;
+  if (m0 + warp < B) loss_row(raw, u, m0 + warp, lane, inv_b, &tile[warp][0], nll);
+  __syncthreads();
+  const int nr = min(kLossRows, B - m0);
+  for (int idx = threadIdx.x; idx < nr * kOut; idx += kLossRows * 32) {   // rows, as 32-bit words
+    const int r = idx / kOut, wd = idx % kOut;
+    reinterpret_cast<uint32_t*>(graw + (int64_t)(m0 + r) * 2 * kOut)[wd] =
+        reinterpret_cast<const uint32_t*>(&tile[r][0])[wd];
+  }
+  const int r = lane & 15;   // a warp writes two columns of 16 samples at a time
+  if (r < nr)
+    for (int j = 2 * warp + (lane >> 4); j < 2 * kOut; j += 2 * kLossRows) {
+      const int jj = j < kOut ? j : j - kOut;
+      gT[(int64_t)jj * ldt + (j < kOut ? 0 : B) + m0 + r] = tile[r][j];
+    }
+}
+
 // Mean of the per-sample losses, one block, fixed order.
 __global__ void k_mean(const float* __restrict__ x, int n, double* __restrict__ out) {
+  umma::griddep_wait();
+  umma::griddep_launch();
   __shared__ double red[256];
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += 256) s += (double)x[i];
@@ -258,30 +337,38 @@ __global__ void k_mean(const float* __restrict__ x, int n, double* __restrict__ 
   if (threadIdx.x == 0) *out = red[0] / (double)n;
 }
 
-// Bias gradients: column sums of g = hi + lo ([B][2N]: [hi | lo]) over split z's rows, into
-// part + z stride + off.
-// Block (32 columns) x (8 row phases); the 8 phase sums are added in a fixed order.
-__global__ void k_colsum(const bf16* __restrict__ g, int B, int N, int kps, float* __restrict__ part,
-                         int64_t stride, int64_t off) {
-  __shared__ float red[8][33];
-  const int n = blockIdx.x * 32 + threadIdx.x;
-  const int z = blockIdx.y;
-  const int r1 = min(B, (z + 1) * kps);
+// Bias gradients: row sums of the transposed signal gT [N][hi B | lo B] (pitch ldt), one warp per
+// row (16-byte loads, lanes in a fixed order, then a fixed shuffle tree), into partial slot 0 at
+// part + off; slots 1 .. S-1 of those entries get 0 (the parameter update sums every slot).
+__global__ void __launch_bounds__(256) k_bias_grad(const bf16* __restrict__ gT, int64_t ldt, int n2, int N,
+                                                   float* __restrict__ part, int S, int64_t stride, int64_t off) {
+  umma::griddep_wait();
+  umma::griddep_launch();
+  const int lane = threadIdx.x & 31;
+  const int n = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (n >= N) return;
+  const bf16* row = gT + (int64_t)n * ldt;
+  const int nv = n2 >> 3;
   float s = 0.f;
-  if (n < N)
-    for (int r = z * kps + threadIdx.y; r < r1; r += 8)
-      s += __bfloat162float(g[(int64_t)r * 2 * N + n]) + __bfloat162float(g[(int64_t)r * 2 * N + N + n]);
-  red[threadIdx.y][threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.y == 0 && n < N) {
-    float t = 0.f;
-    for (int i = 0; i < 8; ++i) t += red[i][threadIdx.x];
-    part[(int64_t)z * stride + off + n] = t;
+#pragma unroll 4
+  for (int j = lane; j < nv; j += 32) {
+    const uint4 q = reinterpret_cast<const uint4*>(row)[j];
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 f = __bfloat1622float2(h[e]);
+      s += f.x + f.y;
+    }
   }
+  for (int j = 8 * nv + lane; j < n2; j += 32) s += __bfloat162float(row[j]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane < S) part[(int64_t)lane * stride + off + n] = lane == 0 ? s : 0.f;
 }
 
 // grad = sum over splits (fixed order).
 __global__ void k_reduce(const float* __restrict__ part, int S, int64_t n, float* __restrict__ grad) {
+  umma::griddep_wait();
+  umma::griddep_launch();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float s = 0.f;
     for (int z = 0; z < S; ++z) s += part[(int64_t)z * n + i];
@@ -310,27 +397,81 @@ __device__ __forceinline__ void store_param(int64_t i, float v, float* pf, bf16*
   row[nout + r / kHid] = b;
 }
 
-__global__ void k_adam(const float* __restrict__ part, int S, const float* __restrict__ grad, int64_t n,
-                       float* __restrict__ p, float* __restrict__ m, float* __restrict__ v, float lr, float b1,
-                       float b2, float eps, float c1, float c2, float* __restrict__ pf, bf16* __restrict__ pb,
-                       bf16* __restrict__ pbt) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float gi;
-    if (S > 0) {
-      gi = 0.f;
-      for (int z = 0; z < S; ++z) gi += part[(int64_t)z * n + i];
-    } else {
-      gi = grad[i];
-    }
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float pi = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
-    p[i] = pi;
-    store_param(i, pi, pf, pb, pbt);
+struct AdamArgs {
+  const float* part;   // split partials [S][n] (S > 0), else grad
+  int S;
+  const float* grad;
+  float *p, *m, *v;
+  float lr, b1, b2, eps, c1, c2;
+  float* pf;
+  bf16 *pb, *pbt;
+};
+
+// Adam update of parameter i: moments, float32 master value and its float32 / BF16 copies;
+// returns the BF16 value.
+__device__ __forceinline__ bf16 adam_one(const AdamArgs& a, int64_t i) {
+  float gi;
+  if (a.S > 0) {
+    gi = 0.f;
+    for (int z = 0; z < a.S; ++z) gi += a.part[(int64_t)z * kNParams + i];
+  } else {
+    gi = a.grad[i];
   }
+  const float mi = a.b1 * a.m[i] + (1.f - a.b1) * gi;
+  const float vi = a.b2 * a.v[i] + (1.f - a.b2) * gi * gi;
+  a.m[i] = mi;
+  a.v[i] = vi;
+  const float pi = a.p[i] - a.lr * (mi * a.c1) / (sqrtf(vi * a.c2) + a.eps);
+  a.p[i] = pi;
+  a.pf[i] = pi;
+  const bf16 b = __float2bfloat16_rn(pi);
+  a.pb[i] = b;
+  return b;
 }
+
+// Blocks [0, kAdamTiles): 32 x 32 tiles of W2, W3, W4 (rows o, columns i), updated along i and
+// written transposed through shared memory into [W^T | W^T]; the remaining blocks: W1 and the
+// biases, one parameter per thread.
+constexpr int kAdamTiles = 2 * (kHid / 32) * (kHid / 32) + ((kOut + 31) / 32) * (kHid / 32);
+constexpr int64_t kAdamFlat = kOffW2 + 2 * kHid + kOut;   // W1, b1 | b2, b3, b4
+__global__ void __launch_bounds__(256) k_adam(const AdamArgs a) {
+  umma::griddep_wait();
+  umma::griddep_launch();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (blockIdx.x < kAdamTiles) {
+    __shared__ bf16 tile[32][34];
+    int t = blockIdx.x, nout = kHid;
+    int64_t off = kOffW2, tof = kOffT2;
+    if (t >= 512) { t -= 512; off = kOffW4; tof = kOffT4; nout = kOut; }
+    else if (t >= 256) { t -= 256; off = kOffW3; tof = kOffT3; }
+    const int o0 = (t / (kHid / 32)) * 32, i0 = (t % (kHid / 32)) * 32;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int o = o0 + ty + 8 * j;
+      if (o < nout) tile[ty + 8 * j][tx] = adam_one(a, off + (int64_t)o * kHid + i0 + tx);
+    }
+    __syncthreads();
+    const int o = o0 + tx;
+    if (o < nout)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        bf16* row = a.pbt + tof + (int64_t)(i0 + ty + 8 * j) * 2 * nout;
+        const bf16 b = tile[tx][ty + 8 * j];
+        row[o] = b;
+        row[nout + o] = b;
+      }
+    return;
+  }
+  const int64_t j = (int64_t)(blockIdx.x - kAdamTiles) * 256 + threadIdx.x;
+  if (j >= kAdamFlat) return;
+  int64_t i = j;
+  if (j >= kOffW2) {
+    const int64_t r = j - kOffW2;
+    i = r < kHid ? kOffB2 + r : r < 2 * kHid ? kOffB3 + (r - kHid) : kOffB4 + (r - 2 * kHid);
+  }
+  adam_one(a, i);
+}
+constexpr int kAdamBlocks = kAdamTiles + (int)((kAdamFlat + 255) / 256);
 
 __global__ void k_copy_params(const float* __restrict__ p, int64_t n, float* __restrict__ pf, bf16* __restrict__ pb,
                               bf16* __restrict__ pbt) {
@@ -363,6 +504,15 @@ using namespace gbk;
 
 
 namespace {
+
+AdamArgs adam_args(gbk_mdn* net, const float* part, int S, const float* grad, float* p, float* m, float* v, float lr,
+                   float b1, float b2, float eps, float c1, float c2) {
+  AdamArgs a;
+  a.part = part; a.S = S; a.grad = grad; a.p = p; a.m = m; a.v = v;
+  a.lr = lr; a.b1 = b1; a.b2 = b2; a.eps = eps; a.c1 = c1; a.c2 = c2;
+  a.pf = net->pf; a.pb = net->pb; a.pbt = net->pbT;
+  return a;
+}
 
 int splits_for(int B, int* kps) {
   int S = (B + 511) / 512;
@@ -400,18 +550,19 @@ gbk_status forward(gbk_mdn* net, const bf16* x, int B, float* out, bool transpos
 }
 
 // Loss, gradient and backward pass; weight / bias gradient partials to net->part.
-gbk_status backward(gbk_mdn* net, const bf16* x, const float* u, int B, double* loss, int* S_out, cudaStream_t st) {
+// x_t_ready: net->xT already holds [x^T | x^T] (written by the training-row gather).
+gbk_status backward(gbk_mdn* net, const bf16* x, const float* u, int B, double* loss, int* S_out, bool x_t_ready,
+                    cudaStream_t st) {
   gbk_status s;
   if ((s = forward(net, x, B, net->raw, true, st))) return s;
-  k_mdn_loss<<<(B + 7) / 8, 256, 0, st>>>(net->raw, u, B, 1.0f / (float)B, net->g4, net->nll);
-  if ((s = check_launch("mdn loss"))) return s;
-  k_transpose<<<dim3((kOut + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(net->g4, B, kOut, 1, net->g4T, net->ldt);
-  if (loss) {
-    k_mean<<<1, 256, 0, st>>>(net->nll, B, loss);
-    if ((s = check_launch("mdn loss mean"))) return s;
-  }
-  k_transpose<<<dim3(kIn / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(x, B, kIn, 0, net->xT, net->ldt);
-  if ((s = check_launch("mdn input transpose"))) return s;
+  if ((s = launch_pdl("mdn loss", k_mdn_loss, dim3((B + kLossRows - 1) / kLossRows), dim3(kLossRows * 32), 0, st,
+                       (const float*)net->raw, u, B, 1.0f / (float)B, net->g4, net->g4T, net->ldt, net->nll)))
+    return s;
+  if (loss && (s = launch_pdl("mdn loss mean", k_mean, dim3(1), dim3(256), 0, st, (const float*)net->nll, B, loss)))
+    return s;
+  if (!x_t_ready && (s = launch_pdl("mdn input transpose", k_transpose, dim3(kIn / 32, (B + 31) / 32), dim3(32, 8), 0,
+                                    st, x, B, kIn, net->xT, net->ldt)))
+    return s;
   int kps;
   const int S = splits_for(2 * B, &kps);   // the weight-gradient contraction runs over [hi | lo]: 2 B
   *S_out = S;
@@ -428,9 +579,9 @@ gbk_status backward(gbk_mdn* net, const bf16* x, const float* u, int B, double* 
     gw.split_stride = kNParams;
     if ((s = mm<umma::EPI_PART_F32>(net, gcurT, net->ldt, hinT, net->ldt, nout[l], nin[l], 2 * B, gw, S, st)))
       return s;
-    k_colsum<<<dim3((nout[l] + 31) / 32, S), dim3(32, 8), 0, st>>>(gcur, B, nout[l], kps, net->part, kNParams,
-                                                                    offb[l]);
-    if ((s = check_launch("mdn bias gradient"))) return s;
+    if ((s = launch_pdl("mdn bias gradient", k_bias_grad, dim3((nout[l] + 7) / 8), dim3(256), 0, st, gcurT, net->ldt,
+                        2 * B, nout[l], net->part, S, kNParams, offb[l])))
+      return s;
     if (l == 0) break;
     // g_prev[m][i] = sum_o g[m][o] W[o][i] = [hi | lo] . [W^T | W^T]^T (contraction over 2 nout),
     // kept where the forward activation was positive and stored again as a hi / lo pair
@@ -549,9 +700,9 @@ extern "C" gbk_status mdn_backward(gbk_mdn* net, const uint16_t* x, const float*
   if ((uintptr_t)x & 15) return set_error(GBK_EINVAL, "mdn_backward: x must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
   int S = 0;
-  if ((s = backward(net, reinterpret_cast<const bf16*>(x), u, batch, loss, &S, st))) return s;
-  k_reduce<<<blocks_for(kNParams), 256, 0, st>>>(net->part, S, kNParams, grad);
-  return check_launch("mdn_backward");
+  if ((s = backward(net, reinterpret_cast<const bf16*>(x), u, batch, loss, &S, false, st))) return s;
+  return launch_pdl("mdn_backward", k_reduce, dim3(blocks_for(kNParams)), dim3(256), 0, st, (const float*)net->part, S,
+                    kNParams, grad);
 }
 
 extern "C" gbk_status mdn_adam(gbk_mdn* net, float* params, float* m, float* v, const float* grad, int32_t step,
@@ -560,10 +711,10 @@ extern "C" gbk_status mdn_adam(gbk_mdn* net, float* params, float* m, float* v, 
   if (step < 1) return set_error(GBK_EINVAL, "mdn_adam: step counts from 1");
   const float c1 = (float)(1.0 / (1.0 - pow((double)beta1, step)));
   const float c2 = (float)(1.0 / (1.0 - pow((double)beta2, step)));
-  k_adam<<<blocks_for(kNParams), 256, 0, (cudaStream_t)stream>>>(nullptr, 0, grad, kNParams, params, m, v, lr, beta1,
-                                                                  beta2, eps, c1, c2, net->pf, net->pb, net->pbT);
-  net->have_params = true;
-  return check_launch("mdn_adam");
+  const gbk_status s = launch_pdl("mdn_adam", k_adam, dim3(kAdamBlocks), dim3(256), 0, (cudaStream_t)stream,
+                                  adam_args(net, nullptr, 0, grad, params, m, v, lr, beta1, beta2, eps, c1, c2));
+  if (!s) net->have_params = true;
+  return s;
 }
 
 extern "C" gbk_status mdn_train_step(gbk_mdn* net, float* params, float* m, float* v, const uint16_t* x,
@@ -576,12 +727,11 @@ extern "C" gbk_status mdn_train_step(gbk_mdn* net, float* params, float* m, floa
   if (step < 1) return set_error(GBK_EINVAL, "mdn_train_step: step counts from 1");
   cudaStream_t st = (cudaStream_t)stream;
   int S = 0;
-  if ((s = backward(net, reinterpret_cast<const bf16*>(x), u, batch, loss, &S, st))) return s;
+  if ((s = backward(net, reinterpret_cast<const bf16*>(x), u, batch, loss, &S, false, st))) return s;
   const double b1 = 0.9, b2 = 0.999;
   const float c1 = (float)(1.0 / (1.0 - pow(b1, step))), c2 = (float)(1.0 / (1.0 - pow(b2, step)));
-  k_adam<<<blocks_for(kNParams), 256, 0, st>>>(net->part, S, nullptr, kNParams, params, m, v, lr, (float)b1, (float)b2,
-                                              1e-8f, c1, c2, net->pf, net->pb, net->pbT);
-  return check_launch("mdn_train_step");
+  return launch_pdl("mdn_train_step", k_adam, dim3(kAdamBlocks), dim3(256), 0, st,
+                    adam_args(net, net->part, S, nullptr, params, m, v, lr, (float)b1, (float)b2, 1e-8f, c1, c2));
 }
 
 extern "C" gbk_status mdn_sample_logpdf(const float* raw, int32_t batch, double eps, const uint32_t* words,
@@ -611,18 +761,18 @@ extern "C" gbk_status mdn_train_epoch(gbk_mdn* net, float* params, float* m, flo
   if (n_steps < 0 || step0 < 0 || n_rows < 1) return set_error(GBK_EINVAL, "mdn_train_epoch: bad counts");
   cudaStream_t st = (cudaStream_t)stream;
   const double b1 = 0.9, b2 = 0.999;
-  const int gblocks = blocks_for((int64_t)batch * (kIn / 8));
   for (int32_t k = 0; k < n_steps; ++k) {
-    k_gather<<<gblocks, 256, 0, st>>>(reinterpret_cast<const bf16*>(x), u, order + (int64_t)k * batch, batch, n_rows,
-                                      net->xb, net->ub, net->err);
-    if ((s = check_launch("mdn_train_epoch(gather)"))) return s;
+    if ((s = launch_pdl("mdn_train_epoch(gather)", k_gather_t, dim3(kIn / 64, (batch + 63) / 64), dim3(256), 0, st,
+                        reinterpret_cast<const bf16*>(x), u, order + (int64_t)k * batch, batch, n_rows, net->xb, net->ub,
+                        net->xT, net->ldt, net->err)))
+      return s;
     int S = 0;
-    if ((s = backward(net, net->xb, net->ub, batch, k == n_steps - 1 ? loss : nullptr, &S, st))) return s;
+    if ((s = backward(net, net->xb, net->ub, batch, k == n_steps - 1 ? loss : nullptr, &S, true, st))) return s;
     const int step = step0 + k + 1;
     const float c1 = (float)(1.0 / (1.0 - pow(b1, step))), c2 = (float)(1.0 / (1.0 - pow(b2, step)));
-    k_adam<<<blocks_for(kNParams), 256, 0, st>>>(net->part, S, nullptr, kNParams, params, m, v, lr, (float)b1,
-                                                (float)b2, 1e-8f, c1, c2, net->pf, net->pb, net->pbT);
-    if ((s = check_launch("mdn_train_epoch(adam)"))) return s;
+    if ((s = launch_pdl("mdn_train_epoch(adam)", k_adam, dim3(kAdamBlocks), dim3(256), 0, st,
+                        adam_args(net, net->part, S, nullptr, params, m, v, lr, (float)b1, (float)b2, 1e-8f, c1, c2))))
+      return s;
   }
   return GBK_OK;
 }

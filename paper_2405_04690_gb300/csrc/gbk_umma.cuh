@@ -9,6 +9,8 @@
 //   all 4 warps        epilogue: tcgen05.ld of their 32 TMEM lanes (= rows), fused bias /
 //                      ReLU / mask, stores (optionally also the transposed BF16 copy the
 //                      backward products read as a K-contiguous operand).
+// Launched as a programmatic dependent launch: barrier set-up and the TMEM allocation overlap the
+// previous kernel, the operands are read only after griddep_wait().
 // Out-of-range rows and k are zero-filled by TMA. Split-K: blockIdx.z takes the k range
 // [z kps, (z + 1) kps), kps a multiple of 64, and writes its own partial slot.
 // Every wait is bounded (2 s by %globaltimer); a wait that gives up sets the abort flag,
@@ -50,10 +52,18 @@ struct Smem {
   static constexpr int a_bytes = kBM * kBK * 2;
   static constexpr int b_bytes = BN * kBK * 2;
   static constexpr int stage_bytes = a_bytes + b_bytes;
-  static constexpr size_t bytes = (size_t)kStages * stage_bytes + 1024 /* alignment */ + 256 /* barriers */;
+  // tiles, barriers (256 bytes), the tile's bias values (BN floats)
+  static constexpr size_t bytes = (size_t)kStages * stage_bytes + 1024 /* alignment */ + 256 + BN * 4;
 };
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start while the previous kernel of the stream still runs; griddep_wait() returns once that
+// kernel has completed and its writes are visible, and no global memory is touched before it.
+// griddep_launch() lets the next such kernel start (once every CTA of this grid has called it
+// or exited).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ uint64_t gtimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -149,6 +159,8 @@ k_umma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
   uint64_t* accum = empty + kStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* first_issued = reinterpret_cast<volatile int*>(tmem_slot + 2);
+  float* sbias = reinterpret_cast<float*>(tiles + kStages * SM::stage_bytes + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
@@ -157,6 +169,8 @@ k_umma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
   const int nk = kend > kbeg ? (kend - kbeg + kBK - 1) / kBK : 0;
 
   if (nk == 0) {   // an empty split writes zeros to its partial slot
+    griddep_wait();
+    griddep_launch();
     if (EPI == EPI_PART_F32) {
       float* C = reinterpret_cast<float*>(g.C) + (int64_t)blockIdx.z * g.split_stride;
       for (int i = threadIdx.x; i < kBM * BN; i += kThreads) {
@@ -173,6 +187,7 @@ k_umma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
     }
     mbar_init(accum, 1);
     *abort_flag = 0;
+    *first_issued = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {   // TMEM: BN float32 columns x 128 lanes
@@ -185,6 +200,23 @@ k_umma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
+  griddep_wait();   // set-up above overlaps the previous kernel; operands are read below
+  // Operands of the epilogue, fetched while the products run (global loads placed among the
+  // epilogue's stores would wait one after another): the tile's bias values into shared memory
+  // by warps 2-3, this thread's row of the mask into registers.
+  if ((EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_BIAS_F32) && warp >= 2)
+    for (int i = threadIdx.x - 64; i < BN; i += kThreads - 64) sbias[i] = n0 + i < g.N ? g.bias[n0 + i] : 0.f;
+  uint4 mrow[EPI == EPI_MASK_SPLIT ? BN / 8 : 1];
+  auto load_mask = [&]() {
+    if (EPI == EPI_MASK_SPLIT) {
+      const int row = m0 + threadIdx.x;
+#pragma unroll
+      for (int j = 0; j < BN / 8; ++j)
+        mrow[j] = row < g.M && n0 + 8 * j < g.N
+                      ? *reinterpret_cast<const uint4*>(g.mask + (int64_t)row * g.ldm + n0 + 8 * j)
+                      : make_uint4(0, 0, 0, 0);
+    }
+  };
 
   if (warp == 0 && lane == 0) {
     int loads = 0;
@@ -195,11 +227,13 @@ k_umma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
       mbar_expect_tx(&full[s], (uint32_t)SM::stage_bytes);
       tma_load(sa, &mapA, kbeg + kb * kBK, m0, &full[s]);
       tma_load(sa + SM::a_bytes, &mapB, kbeg + kb * kBK, n0, &full[s]);
+      if (kb == 0) *first_issued = 1;
       ++loads;
     }
     // the last stages' copies must have landed before the CTA can leave (immediate unless aborted)
     for (int kb = loads > kStages ? loads - kStages : 0; kb < loads; ++kb)
       mbar_drain(&full[kb % kStages], (uint32_t)((kb / kStages) & 1));
+    load_mask();
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t id = idesc<BN>();
     for (int kb = 0; kb < nk; ++kb) {
@@ -214,65 +248,113 @@ k_umma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
       commit(&empty[s]);
     }
     commit(accum);   // arrives when every MMA issued above has completed
+    load_mask();
+  } else if (EPI == EPI_MASK_SPLIT) {
+    // the row's mask is read once the first operand tiles are requested (issued earlier, its
+    // loads would queue ahead of them); the wait is a hint, bounded at 100 us
+    const uint64_t t0 = gtimer();
+    while (!*first_issued && !*abort_flag && gtimer() - t0 < 100000ull) {
+    }
+    load_mask();
   }
   __syncwarp();
-  bool ok = mbar_wait(accum, 0, abort_flag);
+  const bool ok = mbar_wait(accum, 0, abort_flag);
   if (!ok) mbar_drain(accum, 0);   // MMAs already issued finish before TMEM is freed
+  griddep_launch();                // the next kernel's set-up may overlap this epilogue
+  __syncthreads();                 // bias values in shared memory; the abort flag is final
   fence_after();
-  if (ok && !*abort_flag) {
-    const int row = m0 + warp * 32 + lane;
+  if (!*abort_flag) {              // the same for every thread of the CTA
+    const int lr = warp * 32 + lane;   // this thread's TMEM lane = row of the tile
+    const int row = m0 + lr;
+    const int mrows = min(kBM, g.M - m0), ncols = min(BN, g.N - n0);
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
+    // Staging in the operand ring (free once every product has completed), so that the
+    // transposed BF16 copy and the float32 results leave as whole rows of 16-byte stores:
+    // sT [2][BN][kTP] BF16 (column n of the tile as a row of kBM values), sF [kBM][kFP] float32.
+    constexpr int kTP = kBM + 8, kFP = BN + 4;
+    static_assert(2 * BN * kTP * 2 <= kStages * SM::stage_bytes && kBM * kFP * 4 <= kStages * SM::stage_bytes,
+                  "staging area");
+    __nv_bfloat16* sT = reinterpret_cast<__nv_bfloat16*>(tiles);
+    float* sF = reinterpret_cast<float*>(tiles);
+    const bool stage_t = (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_MASK_SPLIT) && g.CT != nullptr;
+#pragma unroll
     for (int c0 = 0; c0 < BN; c0 += 32) {
       float v[32];
       tmem_ld32(trow + (uint32_t)c0, v);
-      if (row >= g.M || n0 + c0 >= g.N) continue;
-      const int nv = min(32, g.N - (n0 + c0));   // N is a multiple of 8
-      const int nb = n0 + c0;
+      if (row >= g.M || c0 >= ncols) continue;
+      const int nv = min(32, ncols - c0);   // N is a multiple of 8
       if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_MASK_SPLIT) {
-        __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(g.C) + (int64_t)row * g.ldc + nb;
-        const __nv_bfloat16* mk = EPI == EPI_MASK_SPLIT ? g.mask + (int64_t)row * g.ldm + nb : nullptr;
+        __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(g.C) + (int64_t)row * g.ldc + n0 + c0;
 #pragma unroll
         for (int q = 0; q < 32; q += 8) {
           if (q >= nv) break;
           __align__(16) __nv_bfloat16 o[8];
           __align__(16) __nv_bfloat16 lo[8];
-          uint4 mv;
-          if (EPI == EPI_MASK_SPLIT) mv = *reinterpret_cast<const uint4*>(mk + q);
+          const uint4 mv = mrow[EPI == EPI_MASK_SPLIT ? (c0 + q) / 8 : 0];
           const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mv);
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             float x = v[q + e];
-            if (EPI == EPI_BIAS_RELU_BF16) x = fmaxf(x + g.bias[nb + q + e], 0.f);
+            if (EPI == EPI_BIAS_RELU_BF16) x = fmaxf(x + sbias[c0 + q + e], 0.f);
             else if (!(__bfloat162float(mb[e]) > 0.f)) x = 0.f;
             o[e] = __float2bfloat16_rn(x);
             if (EPI == EPI_MASK_SPLIT) lo[e] = __float2bfloat16_rn(x - __bfloat162float(o[e]));
           }
           *reinterpret_cast<uint4*>(C + q) = *reinterpret_cast<const uint4*>(o);
           if (EPI == EPI_MASK_SPLIT) *reinterpret_cast<uint4*>(C + g.N + q) = *reinterpret_cast<const uint4*>(lo);
-          if (g.CT) {
+          if (stage_t) {
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-              __nv_bfloat16* ct = g.CT + (int64_t)(nb + q + e) * g.ldct + row;
-              ct[0] = o[e];
-              if (EPI == EPI_MASK_SPLIT) ct[g.M] = lo[e];
-              else if (g.ct_dup) ct[g.M] = o[e];
+              sT[(c0 + q + e) * kTP + lr] = o[e];
+              if (EPI == EPI_MASK_SPLIT) sT[(BN + c0 + q + e) * kTP + lr] = lo[e];
             }
           }
         }
       } else {
-        float* C = reinterpret_cast<float*>(g.C) + (EPI == EPI_PART_F32 ? (int64_t)blockIdx.z * g.split_stride : 0) +
-                   (int64_t)row * g.ldc + nb;
 #pragma unroll
         for (int q = 0; q < 32; q += 4) {
           if (q >= nv) break;
           float4 o;
           o.x = v[q]; o.y = v[q + 1]; o.z = v[q + 2]; o.w = v[q + 3];
           if (EPI == EPI_BIAS_F32) {
-            o.x += g.bias[nb + q]; o.y += g.bias[nb + q + 1]; o.z += g.bias[nb + q + 2]; o.w += g.bias[nb + q + 3];
+            o.x += sbias[c0 + q]; o.y += sbias[c0 + q + 1]; o.z += sbias[c0 + q + 2]; o.w += sbias[c0 + q + 3];
           }
-          *reinterpret_cast<float4*>(C + q) = o;
+          *reinterpret_cast<float4*>(sF + lr * kFP + c0 + q) = o;
         }
+      }
+    }
+    __syncthreads();
+    if (stage_t) {
+      // plane p of CT (columns p M ..): EPI_MASK_SPLIT hi, lo; EPI_BIAS_RELU_BF16 the values, twice with ct_dup
+      const int planes = (EPI == EPI_MASK_SPLIT || g.ct_dup) ? 2 : 1;
+      const bool vec = mrows == kBM && (g.ldct & 7) == 0 && (g.M & 7) == 0 && ((uintptr_t)g.CT & 15) == 0;
+      if (vec) {
+        for (int i = threadIdx.x; i < planes * ncols * (kBM / 8); i += kThreads) {
+          const int p = i / (ncols * (kBM / 8)), rem = i % (ncols * (kBM / 8));
+          const int c = rem / (kBM / 8), j = rem % (kBM / 8);
+          const int sp = EPI == EPI_MASK_SPLIT ? p : 0;
+          *reinterpret_cast<uint4*>(g.CT + (int64_t)(n0 + c) * g.ldct + (int64_t)p * g.M + m0 + 8 * j) =
+              *reinterpret_cast<const uint4*>(sT + (sp * BN + c) * kTP + 8 * j);
+        }
+      } else {
+        for (int i = threadIdx.x; i < planes * ncols * mrows; i += kThreads) {
+          const int p = i / (ncols * mrows), rem = i % (ncols * mrows);
+          const int c = rem / mrows, r = rem % mrows;
+          const int sp = EPI == EPI_MASK_SPLIT ? p : 0;
+          g.CT[(int64_t)(n0 + c) * g.ldct + (int64_t)p * g.M + m0 + r] = sT[(sp * BN + c) * kTP + r];
+        }
+      }
+    }
+    if (EPI == EPI_BIAS_F32 || EPI == EPI_PART_F32) {   // one warp per row
+      float* C = reinterpret_cast<float*>(g.C) + (EPI == EPI_PART_F32 ? (int64_t)blockIdx.z * g.split_stride : 0) +
+                 (int64_t)m0 * g.ldc + n0;
+      const bool vec = (g.ldc & 3) == 0 && ((uintptr_t)C & 15) == 0 && (ncols & 3) == 0;
+      for (int r = warp; r < mrows; r += kThreads / 32) {
+        if (vec)
+          for (int c = 4 * lane; c < ncols; c += 128)
+            *reinterpret_cast<float4*>(C + (int64_t)r * g.ldc + c) = *reinterpret_cast<const float4*>(sF + r * kFP + c);
+        else
+          for (int c = lane; c < ncols; c += 32) C[(int64_t)r * g.ldc + c] = sF[r * kFP + c];
       }
     }
   } else if (threadIdx.x == 0 && g.err) {
