@@ -330,7 +330,8 @@ def group_stretch(cfg, group_b, th, w_j, w_z):
     j = s0 + PX.ranged(w_j, nf)
     xj = gp[j]
     a = cfg.stretch_a
-    z = ((a - 1.0) * PX.u32(w_z) + 1.0) ** 2 / a
+    zz = (a - 1.0) * PX.u32(w_z) + 1.0
+    z = zz * zz / a   # the square as one rounded product (float ** calls pow, not always exact)
     x = [math.log(th[0])] + list(th[1:])
     y0 = [math.log(xj[0])] + list(xj[1:])
     y = []

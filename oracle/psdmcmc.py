@@ -76,7 +76,8 @@ def sweep(cfg, params, logl, resid, f, df, sweep_index, trace=None):
                 words = PX.philox4x32_10((t * W + k, h, 5, sweep_index), cfg.key)
                 j = (1 - h) * half + PX.ranged(words[0], half)
                 u = PX.u32(words[1])
-                z = ((cfg.a - 1.0) * u + 1.0) ** 2 / cfg.a
+                zz = (cfg.a - 1.0) * u + 1.0
+                z = zz * zz / cfg.a   # one rounded product (float ** calls pow, not always exact)
                 xk, xj = to_v(params[t, k]), to_v(params[t, j])
                 y = xj + z * (xk - xj)
                 ul = PX.u53(words[2], words[3])

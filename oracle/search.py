@@ -24,7 +24,10 @@ has SNR = sqrt(2 l_best) >= the limit (at the amplitude that maximises l, <R|h> 
 l = SNR^2 / 2). Random numbers (Philox4x32-10): start of walker (b, t, k) from counters
 (b T W + t W + k, m, 9, seed), m = 0, 1 (8 words); stretch of (b, t, k) in half h of search
 sweep s: (b T W + t W + k, h, 7, s) -> words 0 (partner), 1 (z), 2-3 (ln u); swap of walker w
-between t and t-1: (b W + w, t, 8, s) -> words 0-1.
+between t and t-1: (b W + w, t, 8, s) -> words 0-1. Several searches side by side (the paper
+keeps one per walker, each on that walker's residual and PSD) are independent; search number i
+of them takes band index band0 + b, band0 = i n_bands, in place of b in these counters so that
+their random streams differ.
 """
 import math
 
@@ -62,6 +65,8 @@ class SearchConfig:
         # n_it,max (App. G): a band whose best point has not improved for this many sweeps has
         # converged and is left as it is; 0: never
         self.stall_limit = kw.get("stall_limit", 0)
+        # offset of the band index in the random-number counters (one search among several)
+        self.band0 = kw.get("band0", 0)
 
     def core(self, b):
         lo = self.band_k0 + b * self.nb
@@ -98,7 +103,7 @@ def loglike(cfg, rwin, b, u):
 
 
 def _ctr(cfg, b, t, k):
-    return (b * cfg.n_temps + t) * cfg.n_walkers + k
+    return ((cfg.band0 + b) * cfg.n_temps + t) * cfg.n_walkers + k
 
 
 def init(cfg, seed):
@@ -162,7 +167,8 @@ def sweep(cfg, rwins, u, ell, s, fn=None, trace=None, bands=None):
                 for k in range(h * half, (h + 1) * half):
                     words = PX.philox4x32_10((_ctr(cfg, b, t, k), h, 7, s), cfg.key)
                     j = (1 - h) * half + PX.ranged(words[0], half)
-                    z = ((cfg.a - 1.0) * PX.u32(words[1]) + 1.0) ** 2 / cfg.a
+                    zz = (cfg.a - 1.0) * PX.u32(words[1]) + 1.0
+                    z = zz * zz / cfg.a   # one rounded product (float ** calls pow, not always exact)
                     y = u[b, t, j] + z * (u[b, t, k] - u[b, t, j])
                     ul = PX.u53(words[2], words[3])
                     lu = math.log(ul) if ul > 0 else -math.inf
@@ -179,7 +185,7 @@ def sweep(cfg, rwins, u, ell, s, fn=None, trace=None, bands=None):
                         ell[b, t, k] = ly
         for w in range(W):
             for t in range(T - 1, 0, -1):
-                words = PX.philox4x32_10((b * W + w, t, 8, s), cfg.key)
+                words = PX.philox4x32_10(((cfg.band0 + b) * W + w, t, 8, s), cfg.key)
                 ul = PX.u53(words[0], words[1])
                 lu = math.log(ul) if ul > 0 else -math.inf
                 la = (cfg.betas[b, t - 1] - cfg.betas[b, t]) * (ell[b, t, w] - ell[b, t - 1, w])
