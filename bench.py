@@ -457,7 +457,8 @@ def run_search_rj(torch, L, S, ens, data, args, stream):
     for n_it,max = 500 sweeps (App. G's convergence test; a converged band is left as it is),
     then every band relaunches from a ball around its best point and searches again until it
     converges; bands whose best point reaches SNR 7 give their cold walkers of 20 more sweeps to
-    one EM fit per band; returns the sweep table [W][n_bands][272] and the timings."""
+    one EM fit per band; returns the sweep table [W][n_bands][272], the timings and the final
+    walkers u [n_bands][4][32][8]."""
     dev = data.device
     nb, T_s, W_s = ens["n_bands"], 4, 32
     n_it_max = args.search_stall
@@ -525,7 +526,72 @@ def run_search_rj(torch, L, S, ens, data, args, stream):
            "swap_acceptance": float(s[1, 1]) / max(1.0, float(s[1, 0])),
            "bands_snr_ge_7": int((snr >= 7.0).sum()), "best_snr_median": float(np.median(snr)),
            "fit_ms": e0.elapsed_time(e1), "snr_min": 7.0}
-    return raw, out
+    return raw, out, u
+
+
+class WalkerSearch:
+    """One search per walker, rerun as the fit proceeds (the paper keeps a search sampler per
+    walker on that walker's current residual): a plan of N_W sets (4 temperatures x 32 walkers per
+    band each). A rerun draws every set's walkers from the prior again, moves its windows to its
+    walker's current residual and searches until every band has converged (n_it,max =
+    args.search_rerun_stall sweeps without a better point, a converged band left as it is; at
+    most args.search_rerun_sweeps sweeps), then fits the cold walkers of 20 more sweeps per
+    (walker, band); returns the sweep table [N_W][n_bands][272]."""
+
+    def __init__(self, torch, L, S, ens, args, stream):
+        self.torch, self.L, self.S, self.args, self.stream = torch, L, S, args, stream
+        dev = S["P"].device
+        nb, self.T_s, self.W_s = ens["n_bands"], 4, 32
+        self.nb = nb
+        self.n_it = args.search_rerun_stall
+        self.plan = L.SearchPlan(S["ctx"], nb, N_BAND, ens["band_k0"], self.T_s, self.W_s, L.GBK_MIXED,
+                                 stall_limit=self.n_it, n_sets=N_W)
+        self.u = torch.empty((N_W, nb, self.T_s, self.W_s, 8), dtype=torch.float64, device=dev)
+        self.ell = torch.empty((N_W, nb, self.T_s, self.W_s), dtype=torch.float64, device=dev)
+        self.betas = torch.tensor([[[0.5 ** t for t in range(self.T_s)]] * nb] * N_W, dtype=torch.float64, device=dev)
+        self.be = torch.empty((N_W, nb), dtype=torch.float64, device=dev)
+        self.bu = torch.zeros((N_W, nb, 8), dtype=torch.float64, device=dev)
+        self.stall = torch.zeros((N_W, nb), dtype=torch.int32, device=dev)
+        self.x = torch.empty((N_W * nb, 20 * self.W_s, 8), dtype=torch.float32, device=dev)
+        self.raw = torch.empty((1, N_W * nb, 272), dtype=torch.float32, device=dev)
+        self.sweep = 0
+        self.ms, self.sweeps, self.snr7 = [], [], []
+
+    def rerun(self, resid, n_keep=20):
+        torch, L, st = self.torch, self.L, self.stream
+        key = 0x5EA2C5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        L.gb_search_init(self.plan, self.u, key, 100 + len(self.ms), st)
+        L.gb_search_windows(self.plan, L.residual_struct(resid, FRAC_BITS), 0, st)
+        L.gb_search_eval(self.plan, self.u, self.ell, self.S["psd"], 0, st)
+        self.be.fill_(-np.inf)
+        self.stall.zero_()
+        n = 0
+        while n < self.args.search_rerun_sweeps:
+            for _ in range(50):
+                L.gb_search_sweep(self.plan, self.u, self.ell, self.betas, self.S["psd"], key, self.sweep,
+                                  best=(self.be, self.bu, self.stall), stream=st)
+                self.sweep += 1
+                n += 1
+            if int(self.stall.min().item()) >= self.n_it:
+                break
+        self.stall.zero_()   # samples of every band
+        for k in range(n_keep):
+            L.gb_search_sweep(self.plan, self.u, self.ell, self.betas, self.S["psd"], key, self.sweep,
+                              best=(self.be, self.bu, self.stall), stream=st)
+            self.sweep += 1
+            L.gb_search_samples(self.plan, self.u, self.be, 7.0, F_LO, F_HI, self.x, k * self.W_s, st)
+        L.gmm_fit(self.x, self.raw, n_iter=self.args.gmm_iters, precision=L.GBK_MIXED, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        self.ms.append(e0.elapsed_time(e1))
+        self.sweeps.append(n)
+        self.snr7.append(int((torch.sqrt(2.0 * torch.clamp(self.be, min=0.0)) >= 7.0).sum().item()))
+        return self.raw.view(N_W, self.nb, 272)
+
+    def close(self):
+        self.plan.close()
 
 
 def run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, snap, ess_plain, units=None):
@@ -620,7 +686,8 @@ def run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, sn
     data = S["resid"].clone()                               # d (noise + injected sources) per walker
     # the paper's search-RJ proposal: per-band search samplers on walker 0's data residual, then
     # mixtures fitted to their cold walkers around the best points of bands with SNR >= 7
-    srj_raw, search["search_rj_sampler"] = run_search_rj(torch, L, S, ens, data, args, stream)
+    srj_raw, search["search_rj_sampler"], _ = run_search_rj(torch, L, S, ens, data, args, stream)
+    walker_search = None
     for mode in ("prior", "learned", "gmm_refit", "search_rj", "search_rj_rerun"):
         if mode == "gmm_refit" and gmm_raw is None:
             continue
@@ -650,16 +717,27 @@ def run_learned(torch, L, S, ens, step, stats, stream, sweep_no, args, pairs, sn
                 curve.append([k + 1, recovered_sources(ens["truth"], S["P"].cpu().numpy(), S["E"].cpu().numpy(),
                                                        TOBS, ens["n_bands"], ens["band_k0"])])
             if mode == "search_rj_rerun" and k % 2 == 1 and k + 1 < args.search_sweeps:
-                # the paper's continuous search: rerun on the current best-fit residual (walker 0), so
-                # each band's search moves on to the loudest source not yet in the model
-                srj_raw2, _ = run_search_rj(torch, L, S, ens, S["resid"], args, stream)
+                # the paper's continuous search: every walker's search continues on that walker's
+                # current residual, so each band's search moves on to the loudest source not yet
+                # in that walker's model, and each walker births from its own mixtures
+                if walker_search is None:
+                    walker_search = WalkerSearch(torch, L, S, ens, args, stream)
+                srj_raw2 = walker_search.rerun(S["resid"])
                 L.gbk_sweep_set_proposal(S["plan"], raw_table=srj_raw2, eps=args.mdn_eps,
                                          inmodel_frac=args.mdn_inmodel)
         st = stats.cpu().numpy()
         search[mode] = {"recovered_after_sweeps": curve, "seconds": t,
                         "birth_acceptance": float(st[1, 1]) / max(1.0, float(st[1, 0]))}
         if mode == "search_rj_rerun":
-            search[mode]["reruns"] = "search rerun on walker 0's residual after every second sweep (not in seconds)"
+            search[mode]["reruns"] = ("after every second sweep, one search per walker (32 sets of 369 bands x 4 x 32) "
+                                      "from the prior on that walker's current residual until converged "
+                                      "(n_it,max %d, at most %d sweeps), then fitted (not in seconds)"
+                                      % (args.search_rerun_stall, args.search_rerun_sweeps))
+            if walker_search is not None:
+                search[mode]["rerun_ms"] = walker_search.ms
+                search[mode]["rerun_sweeps"] = walker_search.sweeps
+                search[mode]["rerun_bands_snr_ge_7_all_walkers"] = walker_search.snr7
+                walker_search.close()
     search["injected"] = int(ens["truth"].shape[1]) * min(4, N_W)
     search["counted"] = "cold chains of walkers 0-3: injected sources matched within 1 bin in f0 and 0.3 in ln A"
     out["search"] = search
@@ -1202,6 +1280,9 @@ def main():
     ap.add_argument("--search-rj-sweeps", type=int, default=3000,
                     help="cap on the search-sampler sweeps of each phase (before and after the relaunch)")
     ap.add_argument("--search-stall", type=int, default=500, help="n_it,max of the search's convergence test")
+    ap.add_argument("--search-rerun-stall", type=int, default=100,
+                    help="n_it,max of the per-walker search reruns during the search from an empty model")
+    ap.add_argument("--search-rerun-sweeps", type=int, default=600, help="sweep cap of each per-walker search rerun")
     ap.add_argument("--gmm-iters", type=int, default=50, help="EM iterations of the mixture refit")
     ap.add_argument("--group-frac", type=float, default=0.5, help="fraction of in-model moves that are group stretches "
                                                                    "in the group-stretch ESS run (0: skip it)")

@@ -511,7 +511,13 @@ gbk_status gbk_sweep_transfer(gbk_sweep* plan, double* params, uint8_t* exists, 
  * (stall = 0) else stall += 1. Random numbers: Philox4x32-10 with the 64-bit key; start of
  * chain c = (b T + t) W + k from counters (c, m, 9, seed), m = 0, 1; stretch of chain c in
  * half h of sweep s from (c, h, 7, s) (words: partner, z, ln u); swap of (b, w) between t and
- * t - 1 from (b W + w, t, 8, s). SNR of a band's best point: sqrt(2 l_best). */
+ * t - 1 from (b W + w, t, 8, s). SNR of a band's best point: sqrt(2 l_best).
+ * A plan runs n_sets such searches side by side (the paper keeps one search per walker): set s
+ * searches the residual of walker w0 + s (gb_search_windows) with that walker's PSD row
+ * (psd_walker + s; a one-row PSD serves every set). Every per-band array then carries the sets
+ * first: band b of set s is the flattened band fb = s n_bands + b (u [n_sets][n_bands][T][W][8],
+ * betas [n_sets][n_bands][T], ...), and fb takes b's place in the counters above; with n_sets = 1
+ * fb = b. */
 typedef struct gbk_search_desc {
   int32_t n_bands, band_bins, n_temps, n_walkers;  /* n_walkers even, >= 4 */
   int64_t band_k0;        /* absolute first bin of band 0; windows [band_k0 + (b-1) N, +3N) in the grid */
@@ -521,6 +527,7 @@ typedef struct gbk_search_desc {
   int32_t stall_limit;    /* n_it,max: a band whose best point has not improved for this many sweeps
                              has converged and is frozen (no moves, swaps or best-point updates in
                              later sweeps until its stall count is reset); 0: never */
+  int32_t n_sets;         /* searches side by side, one per residual walker (0 means 1) */
 } gbk_search_desc;
 
 typedef struct gbk_search gbk_search;
@@ -529,19 +536,22 @@ typedef struct gbk_search gbk_search;
  * ([n_bands][2][3N] complex of the precision). */
 gbk_status gbk_search_create(gbk_ctx* ctx, const gbk_search_desc* desc, gbk_search** out);
 gbk_status gbk_search_destroy(gbk_search* plan);
-/* u [n_bands][n_temps][n_walkers][8] float64 (device) drawn from the prior (uniform box). */
+/* u [n_sets][n_bands][n_temps][n_walkers][8] float64 (device) drawn from the prior (uniform
+ * box). */
 gbk_status gb_search_init(gbk_search* plan, double* u, uint64_t key, uint32_t seed, void* stream);
-/* Copies walker `walker`'s fixed-point residual (gbk_residual, device) onto every band's window;
- * the windows stay until the next call. */
+/* Copies the fixed-point residual (gbk_residual, device) of walker `walker` + s onto the window of
+ * every band of set s (walker + n_sets <= the residual's walkers); the windows stay until the
+ * next call. */
 gbk_status gb_search_windows(gbk_search* plan, const gbk_residual* residual, int32_t walker, void* stream);
-/* ell [n_bands][n_temps][n_walkers] float64 (device) = l(u) of every walker, with the PSD of
- * psd_walker (the residual's walker; index 0 of a one-row PSD). */
+/* ell [n_sets][n_bands][n_temps][n_walkers] float64 (device) = l(u) of every walker, with set s
+ * taking the PSD row psd_walker + s (its residual's walker; row 0 of a one-row PSD). */
 gbk_status gb_search_eval(gbk_search* plan, const double* u, double* ell, const gbk_psd* psd, int32_t psd_walker,
                           void* stream);
 /* One sweep; u and ell (consistent, e.g. from gb_search_eval) are updated in place.
- *   betas     [n_bands][n_temps] float64 (device)
- *   best_ell  [n_bands] float64, best_u [n_bands][8], stall [n_bands] int32 (device, in/out;
- *             start best_ell at -inf); all three or none, and all three with a stall_limit: the
+ *   betas     [n_sets][n_bands][n_temps] float64 (device)
+ *   best_ell  [n_sets][n_bands] float64, best_u [n_sets][n_bands][8], stall [n_sets][n_bands]
+ *             int32 (device, in/out; start best_ell at -inf); all three or none, and all three
+ *             with a stall_limit: the
  *             bands whose stall count has reached it at the start of the sweep are left as they are
  *   stats     optional int64[2][2] (device): stretch proposals, accepted; swaps, accepted (added) */
 gbk_status gb_search_sweep(gbk_search* plan, double* u, double* ell, const double* betas, const gbk_psd* psd,
@@ -551,13 +561,15 @@ gbk_status gb_search_sweep(gbk_search* plan, double* u, double* ell, const doubl
  * point, then the same search again): every chain of a band whose best_ell is finite becomes
  * clip(best_u + sigma z, 0, 1) with z standard normal (Box-Muller on Philox words at counters
  * (chain, m, 10, seed), m = 0, 1); other bands keep their walkers. Follow with gb_search_eval.
- *   u [n_bands][n_temps][n_walkers][8] (device, updated); best_ell [n_bands], best_u [n_bands][8] */
+ *   u [n_sets][n_bands][n_temps][n_walkers][8] (device, updated); best_ell [n_sets][n_bands],
+ *   best_u [n_sets][n_bands][8] */
 gbk_status gb_search_ball(gbk_search* plan, double* u, const double* best_ell, const double* best_u, double sigma,
                           uint64_t key, uint32_t seed, void* stream);
 /* Training points of the search-RJ mixtures from the current state: for every band b the cold
  * walkers' u in the sweep's unit coordinates (the learned proposal's: f0 over the band's
  * allowance, own bins +- half a band clipped to [f_min, f_max]; the other coordinates
- * unchanged) into x[b][row0 + k][8] (float32, device, [n_bands][n_rows][8]), k < n_walkers;
+ * unchanged) into x[fb][row0 + k][8] (float32, device, [n_sets][n_bands][n_rows][8]),
+ * k < n_walkers;
  * rows of a band whose best point has sqrt(2 best_ell) < snr_min are NaN. Fit them with
  * gmm_fit (one group per band) for the sweep's mixture table. */
 gbk_status gb_search_samples(gbk_search* plan, const double* u, const double* best_ell, double snr_min, double f_min,

@@ -56,7 +56,7 @@ class GbkSearchDesc(ctypes.Structure):
     _fields_ = [("n_bands", _i32), ("band_bins", _i32), ("n_temps", _i32), ("n_walkers", _i32),
                 ("band_k0", ctypes.c_int64), ("ln_a_min", ctypes.c_double), ("ln_a_max", ctypes.c_double),
                 ("mc_min", ctypes.c_double), ("mc_max", ctypes.c_double), ("stretch_a", ctypes.c_double),
-                ("precision", _i32), ("stall_limit", _i32)]
+                ("precision", _i32), ("stall_limit", _i32), ("n_sets", _i32)]
 
 
 class GbkTraceRec(ctypes.Structure):
@@ -581,7 +581,7 @@ class SearchPlan:
 
     def __init__(self, ctx, n_bands, band_bins, band_k0, n_temps, n_walkers, precision=GBK_MIXED,
                  ln_a_min=math.log(1e-23), ln_a_max=math.log(10 ** -21.5), mc_min=0.3, mc_max=0.8, stretch_a=2.0,
-                 stall_limit=0):
+                 stall_limit=0, n_sets=1):
         d = GbkSearchDesc()
         d.n_bands, d.band_bins, d.n_temps, d.n_walkers = int(n_bands), int(band_bins), int(n_temps), int(n_walkers)
         d.band_k0 = int(band_k0)
@@ -589,6 +589,7 @@ class SearchPlan:
         d.stretch_a = float(stretch_a)
         d.precision = int(precision)
         d.stall_limit = int(stall_limit)
+        d.n_sets = int(n_sets)
         self.desc = d
         h = _vp()
         _check(lib().gbk_search_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)), "gbk_search_create")
@@ -633,10 +634,11 @@ def gb_search_sweep(plan, u, ell, betas, psd, key, sweep_index, psd_walker=0, be
 
 
 def gb_search_samples(plan, u, best_ell, snr_min, f_min, f_max, x, row0, stream=None):
-    """Cold walkers of every band into x [n_bands][n_rows][8] (float32) at rows row0 .. row0 + W."""
+    """Cold walkers of every band into x [n_sets][n_bands][n_rows][8] or [n_sets n_bands][n_rows][8]
+    (float32) at rows row0 .. row0 + W."""
     _check(lib().gb_search_samples(plan.handle, _dev(u, torch.float64, "u"), _dev(best_ell, torch.float64, "best_ell"),
                                    float(snr_min), float(f_min), float(f_max), _dev(x, torch.float32, "x"),
-                                   int(x.shape[1]), int(row0), _stream(stream)), "gb_search_samples")
+                                   int(x.shape[-2]), int(row0), _stream(stream)), "gb_search_samples")
 
 
 def gb_search_ball(plan, u, best_ell, best_u, sigma, key, seed, stream=None):

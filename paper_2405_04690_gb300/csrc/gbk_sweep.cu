@@ -1910,11 +1910,13 @@ extern "C" gbk_status gbk_sweep_transfer(gbk_sweep* plan, double* params, uint8_
 // ==================================================================== per-band search sampler
 // The search-RJ proposal's sampler (Sec. V.E, App. G): for every sub-band an independent,
 // parallel-tempered ensemble of single sources with stretch moves in the band's own-bin prior
-// box, looking for the highest-likelihood source left in one walker's residual.
+// box, looking for the highest-likelihood source left in one walker's residual. n_sets such
+// searches run side by side, set s on the residual of walker w0 + s; their bands are
+// flattened, fb = s n_bands + b (band geometry b = fb mod n_bands).
 struct gbk_search {
   gbk_ctx* ctx;
-  gbk_search_desc d;
-  void* rw;            // residual windows [B][2][3N] of the sampler's precision
+  gbk_search_desc d;   // n_sets >= 1
+  void* rw;            // residual windows [n_sets B][2][3N] of the sampler's precision
   bool have_windows;
 };
 
@@ -1925,18 +1927,19 @@ constexpr int kSearchWarps = 4;
 struct SearchArgs {
   SweepArgs sa;        // context, PSD and the residual windows (sa.rho) for the shared helpers
   gbk_search_desc d;
-  double* u;           // [B][T][W][8]
-  double* ell;         // [B][T][W]
-  const double* betas; // [B][T]
-  int psd_walker;
+  int nbt;             // n_sets x n_bands (flattened index fb)
+  double* u;           // [nbt][T][W][8]
+  double* ell;         // [nbt][T][W]
+  const double* betas; // [nbt][T]
+  int psd_walker;      // PSD row of set 0; set s uses psd_walker + s (a one-row PSD: row 0)
   long long* stats;    // [2][2]: stretch proposals, accepted; swaps, accepted
-  const int32_t* stall;  // [B] sweeps without a better point (NULL: no convergence test)
+  const int32_t* stall;  // [nbt] sweeps without a better point (NULL: no convergence test)
   int stall_limit;       // a band with stall >= stall_limit has converged: left as it is
 };
 
-// Has band b's search converged (App. G: n_it,max sweeps without a better point)?
-__device__ __forceinline__ bool search_frozen(const SearchArgs& a, int b) {
-  return a.stall && a.stall_limit > 0 && a.stall[b] >= a.stall_limit;
+// Has band fb's search converged (App. G: n_it,max sweeps without a better point)?
+__device__ __forceinline__ bool search_frozen(const SearchArgs& a, int fb) {
+  return a.stall && a.stall_limit > 0 && a.stall[fb] >= a.stall_limit;
 }
 
 // per warp: the FFT buffers and the set-up of a batch of 32 chains (one lane each)
@@ -1968,46 +1971,48 @@ __device__ __forceinline__ void search_from_unit(const gbk_search_desc& d, doubl
 }
 
 template <typename T, int N>
-__device__ __forceinline__ const typename CT<T>::C* search_window(const SearchArgs& a, int b) {
-  return reinterpret_cast<const typename CT<T>::C*>(a.sa.rho) + (int64_t)b * 2 * 3 * N;
+__device__ __forceinline__ const typename CT<T>::C* search_window(const SearchArgs& a, int fb) {
+  return reinterpret_cast<const typename CT<T>::C*>(a.sa.rho) + (int64_t)fb * 2 * 3 * N;
 }
 
-// Set-up of one source (one lane): parameters of u in band b's box and the waveform constants.
+// Set-up of one source (one lane): parameters of u in band fb's box and the waveform constants.
 template <typename T, int N>
-__device__ __forceinline__ void search_prep(const SearchArgs& a, SearchSmem<T, N>& S, int q, int b, const double* u) {
+__device__ __forceinline__ void search_prep(const SearchArgs& a, SearchSmem<T, N>& S, int q, int fb, const double* u) {
   double th[8];
-  search_from_unit(a.d, a.sa.c.grid.tobs, b, u, th);
+  search_from_unit(a.d, a.sa.c.grid.tobs, fb % a.d.n_bands, u, th);
   S.src[q] = make_src<T>(th, 1, 0, a.sa.c.grid.tobs, N);
 }
 
-// l = <R|h> - 1/2 <h|h> on band b's window for the prepared source q (the birth Delta lnL,
-// Eq. addsource); whole warp.
+// l = <R|h> - 1/2 <h|h> on band fb's window for the prepared source q (the birth Delta lnL,
+// Eq. addsource), with the PSD of the set's walker; whole warp.
 template <typename T, int N>
-__device__ double search_ell(const SearchArgs& a, SearchSmem<T, N>& S, int q, int b, int lane) {
+__device__ double search_ell(const SearchArgs& a, SearchSmem<T, N>& S, int q, int fb, int lane) {
   gen_band<T, N>(&S.src[q], orb_of<T>(a.sa.c, band_index(N)), tw_of<T>(a.sa.c, band_index(N)), a.sa.c.grid.tobs,
                  S.ba, S.bs, lane);
+  const int b = fb % a.d.n_bands;
   const int64_t gw = a.d.band_k0 + (int64_t)(b - 1) * N - a.sa.c.grid.k0;
   const int oa = band_off<N>(S.src[q].q, gw, a.sa.c);
-  const PsdWt<T> pw = walker_psd<T>(a.sa, a.psd_walker);
-  const double l = window_dll<T, N>(a.sa, search_window<T, N>(a, b), S.ba, oa, (const typename CT<T>::C*)nullptr, 0,
+  const PsdWt<T> pw = walker_psd<T>(a.sa, a.psd_walker + (a.sa.npsd > 1 ? fb / a.d.n_bands : 0));
+  const double l = window_dll<T, N>(a.sa, search_window<T, N>(a, fb), S.ba, oa, (const typename CT<T>::C*)nullptr, 0,
                                     gw, pw, lane);
   __syncwarp();
   return l;
 }
 
-// residual windows: R of one walker on every band's three sub-bands
+// residual windows: R of walker w0 + s on the three sub-bands of every band of set s
 template <typename T, int N>
 __global__ void __launch_bounds__(kSearchWarps * 32) k_search_windows(const SearchArgs a, const long long* resid,
                                                                       int64_t n_bins, int walker, int frac_bits) {
   typedef typename CT<T>::C C;
   constexpr int W3 = 3 * N;
   const int lane = threadIdx.x & 31;
-  const int b = blockIdx.x * kSearchWarps + (threadIdx.x >> 5);
-  if (b >= a.d.n_bands) return;
+  const int fb = blockIdx.x * kSearchWarps + (threadIdx.x >> 5);
+  if (fb >= a.nbt) return;
+  const int b = fb % a.d.n_bands;
   const T rs = (T)ldexp(1.0, kStrainExp - frac_bits);
   const int64_t gw = a.d.band_k0 + (int64_t)(b - 1) * N - a.sa.c.grid.k0;
-  const long long* rw = resid + (int64_t)walker * 2 * n_bins * 2;
-  C* out = reinterpret_cast<C*>(a.sa.rho) + (int64_t)b * 2 * W3;
+  const long long* rw = resid + (int64_t)(walker + fb / a.d.n_bands) * 2 * n_bins * 2;
+  C* out = reinterpret_cast<C*>(a.sa.rho) + (int64_t)fb * 2 * W3;
   for (int i = lane; i < W3; i += 32)
     for (int ch = 0; ch < 2; ++ch) {
       const longlong2 v = *reinterpret_cast<const longlong2*>(rw + 2 * (ch * n_bins + gw + i));
@@ -2033,7 +2038,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_eval(const SearchA
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   SearchSmem<T, N>& S = reinterpret_cast<SearchSmem<T, N>*>(smem_raw)[wid];
-  const int n = a.d.n_bands * a.d.n_temps * a.d.n_walkers;
+  const int n = a.nbt * a.d.n_temps * a.d.n_walkers;
   const int per = a.d.n_temps * a.d.n_walkers;
   // batches of bs <= 32 chains per warp: the float64 set-up lane-parallel, then one waveform at a time
   for (int g0 = (blockIdx.x * wpc + wid) * bs; g0 < n; g0 += gridDim.x * wpc * bs) {
@@ -2058,7 +2063,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_half(const SearchA
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   SearchSmem<T, N>& S = reinterpret_cast<SearchSmem<T, N>*>(smem_raw)[wid];
   const int T_ = a.d.n_temps, W = a.d.n_walkers, half = W / 2;
-  const int n = a.d.n_bands * T_ * half;
+  const int n = a.nbt * T_ * half;
   // batches of bs <= 32 chains of the half per warp: words, partner, z, Y, box test and the
   // float64 source set-up lane-parallel, then the waveforms and decisions one chain at a time
   for (int g0 = (blockIdx.x * wpc + wid) * bs; g0 < n; g0 += gridDim.x * wpc * bs) {
@@ -2066,10 +2071,10 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_half(const SearchA
     bool live = false;
     if (lane < cnt) {
       const int e = g0 + lane;
-      const int b = e / (T_ * half), r = e % (T_ * half);
+      const int fb = e / (T_ * half), r = e % (T_ * half);
       const int t = r / half, k = h * half + r % half;
-      const int64_t ck = ((int64_t)b * T_ + t) * W + k;
-      live = !search_frozen(a, b);
+      const int64_t ck = ((int64_t)fb * T_ + t) * W + k;
+      live = !search_frozen(a, fb);
       const U4 wv = philox4x32_10((uint32_t)ck, (uint32_t)h, 7u, sweep, k0, k1);
       const int j = (1 - h) * half + (int)ranged(wv.x, (uint32_t)half);
       const double zz = dadd(dmul(dsub(a.d.stretch_a, 1.0), u32(wv.y)), 1.0);
@@ -2085,22 +2090,22 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_half(const SearchA
       if (!live) inb = 0;   // a converged band: no move (and not counted)
       S.inb[lane] = inb;
       S.lz[lane] = log(z);
-      if (inb) search_prep<T, N>(a, S, lane, b, S.y[lane]);
+      if (inb) search_prep<T, N>(a, S, lane, fb, S.y[lane]);
     }
     const int n_live = __popc(__ballot_sync(0xffffffffu, live));
     __syncwarp();
     int n_acc = 0;
     for (int q = 0; q < cnt; ++q) {
       const int e = g0 + q;
-      const int b = e / (T_ * half), r = e % (T_ * half);
+      const int fb = e / (T_ * half), r = e % (T_ * half);
       const int t = r / half, k = h * half + r % half;
-      const int64_t ck = ((int64_t)b * T_ + t) * W + k;
+      const int64_t ck = ((int64_t)fb * T_ + t) * W + k;
       if (!S.inb[q]) continue;
-      const double ly = search_ell<T, N>(a, S, q, b, lane);
+      const double ly = search_ell<T, N>(a, S, q, fb, lane);
       const U4 wv = philox4x32_10((uint32_t)ck, (uint32_t)h, 7u, sweep, k0, k1);
       const double ul = u53(wv.z, wv.w);
       const double lu = ul > 0.0 ? log(ul) : -INFINITY;
-      const double la = a.betas[(int64_t)b * T_ + t] * (ly - a.ell[ck]) + 7.0 * S.lz[q];
+      const double la = a.betas[(int64_t)fb * T_ + t] * (ly - a.ell[ck]) + 7.0 * S.lz[q];
       const bool acc = __shfl_sync(0xffffffffu, (int)(lu < la), 0) != 0;
       if (acc) {
         if (lane == 0) a.ell[ck] = ly;
@@ -2116,12 +2121,12 @@ __global__ void __launch_bounds__(kSearchWarps * 32) k_search_half(const SearchA
   }
 }
 
-// Tempering swaps of walker index w between t and t-1, from the top down (one thread per (b, w)).
+// Tempering swaps of walker index w between t and t-1, from the top down (one thread per (fb, w)).
 __global__ void k_search_swap(const SearchArgs a, uint32_t sweep, uint32_t k0, uint32_t k1) {
   const int T_ = a.d.n_temps, W = a.d.n_walkers;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= a.d.n_bands * W) return;
-  const int b = x / W, w = x % W;
+  if (x >= a.nbt * W) return;
+  const int b = x / W, w = x % W;   // b: the flattened band index fb
   if (search_frozen(a, b)) return;
   int n = 0, na = 0;
   for (int t = T_ - 1; t > 0; --t) {
@@ -2150,9 +2155,10 @@ __global__ void k_search_swap(const SearchArgs a, uint32_t sweep, uint32_t k0, u
 }
 
 // best point of every band: the largest cold-chain l (first walker on ties) if it improves
+// (b: the flattened band index fb)
 __global__ void k_search_best(const SearchArgs a, double* best_ell, double* best_u, int32_t* stall) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= a.d.n_bands || search_frozen(a, b)) return;
+  if (b >= a.nbt || search_frozen(a, b)) return;
   const int W = a.d.n_walkers;
   const double* l = a.ell + (int64_t)b * a.d.n_temps * W;
   int k = 0;
@@ -2201,15 +2207,15 @@ __global__ void k_search_samples(const SearchArgs a, const double* __restrict__ 
                                  double f_min, double f_max, float* __restrict__ x, int n_rows, int row0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int W = a.d.n_walkers;
-  if (i >= a.d.n_bands * W) return;
-  const int b = i / W, k = i % W;
-  float* o = x + ((int64_t)b * n_rows + row0 + k) * 8;
-  const double be = best_ell[b];
+  if (i >= a.nbt * W) return;
+  const int fb = i / W, k = i % W, b = fb % a.d.n_bands;
+  float* o = x + ((int64_t)fb * n_rows + row0 + k) * 8;
+  const double be = best_ell[fb];
   if (!(be > 0.0 && sqrt(2.0 * be) >= snr_min)) {
     for (int c = 0; c < 8; ++c) o[c] = __int_as_float(0x7fc00000);
     return;
   }
-  const double* u = a.u + ((int64_t)b * a.d.n_temps * W + k) * 8;
+  const double* u = a.u + ((int64_t)fb * a.d.n_temps * W + k) * 8;
   const double tobs = a.sa.c.grid.tobs;
   const long long lob = a.d.band_k0 + (long long)b * a.d.band_bins;
   const double lo = __ddiv_rn((double)lob, tobs), hi = __ddiv_rn((double)(lob + a.d.band_bins), tobs);
@@ -2236,14 +2242,14 @@ static gbk_status search_launch(SearchArgs& a, int what, uint32_t sweep, uint32_
   size_t sm = 0;
   gbk_status s;
   if (what == 0) {
-    const int64_t n = (int64_t)a.d.n_bands * a.d.n_temps * a.d.n_walkers;
+    const int64_t n = (int64_t)a.nbt * a.d.n_temps * a.d.n_walkers;
     const int bs = search_batch(n);
     if ((s = prep(k_search_eval<T, N>, sizeof(SearchSmem<T, N>), (n + bs - 1) / bs, &grid, &thr, &sm, kSearchWarps)))
       return s;
     k_search_eval<T, N><<<grid, thr, sm, st>>>(a, bs);
     return check_launch("gb_search_eval");
   }
-  const int64_t n = (int64_t)a.d.n_bands * a.d.n_temps * (a.d.n_walkers / 2);
+  const int64_t n = (int64_t)a.nbt * a.d.n_temps * (a.d.n_walkers / 2);
   const int bs = search_batch(n);
   if ((s = prep(k_search_half<T, N>, sizeof(SearchSmem<T, N>), (n + bs - 1) / bs, &grid, &thr, &sm, kSearchWarps)))
     return s;
@@ -2276,6 +2282,7 @@ static SearchArgs search_args(gbk_search* p, double* u, double* ell, const doubl
     a.sa.npsd = psd->n_psd;
   }
   a.d = p->d;
+  a.nbt = p->d.n_sets * p->d.n_bands;
   a.u = u;
   a.ell = ell;
   a.betas = betas;
@@ -2288,11 +2295,12 @@ static SearchArgs search_args(gbk_search* p, double* u, double* ell, const doubl
 extern "C" gbk_status gbk_search_create(gbk_ctx* ctx, const gbk_search_desc* desc, gbk_search** out) {
   if (!ctx || !desc || !out) return set_error(GBK_EINVAL, "gbk_search_create: null argument");
   *out = nullptr;
-  const gbk_search_desc& d = *desc;
+  gbk_search_desc d = *desc;
+  if (d.n_sets == 0) d.n_sets = 1;
   if (d.n_bands < 1 || d.n_temps < 1 || d.n_walkers < 4 || (d.n_walkers & 1) || band_index(d.band_bins) < 0 ||
-      (int64_t)d.n_bands * d.n_temps * d.n_walkers > (1 << 26))
-    return set_error(GBK_EINVAL, "gbk_search_create: bad sizes (B=%d T=%d W=%d N=%d; W even, >= 4)", d.n_bands,
-                     d.n_temps, d.n_walkers, d.band_bins);
+      d.n_sets < 1 || (int64_t)d.n_sets * d.n_bands * d.n_temps * d.n_walkers > (1 << 26))
+    return set_error(GBK_EINVAL, "gbk_search_create: bad sizes (S=%d B=%d T=%d W=%d N=%d; W even, >= 4)", d.n_sets,
+                     d.n_bands, d.n_temps, d.n_walkers, d.band_bins);
   if (d.precision != GBK_MIXED && d.precision != GBK_FP64) return set_error(GBK_EINVAL, "gbk_search_create: bad precision");
   if (d.stall_limit < 0) return set_error(GBK_EINVAL, "gbk_search_create: stall_limit < 0");
   if (!(d.stretch_a > 1.0) || !(d.ln_a_min < d.ln_a_max) || !(d.mc_min < d.mc_max) || !(d.mc_min > 0.0))
@@ -2307,7 +2315,7 @@ extern "C" gbk_status gbk_search_create(gbk_ctx* ctx, const gbk_search_desc* des
   p->ctx = ctx;
   p->d = d;
   const size_t csz = d.precision == GBK_MIXED ? sizeof(float2) : sizeof(double2);
-  if (cudaMalloc(&p->rw, (size_t)d.n_bands * 2 * 3 * d.band_bins * csz) != cudaSuccess) {
+  if (cudaMalloc(&p->rw, (size_t)d.n_sets * d.n_bands * 2 * 3 * d.band_bins * csz) != cudaSuccess) {
     cudaGetLastError();
     free(p);
     return set_error(GBK_ENOMEM, "gbk_search_create: device allocation");
@@ -2326,7 +2334,7 @@ extern "C" gbk_status gbk_search_destroy(gbk_search* p) {
 
 extern "C" gbk_status gb_search_init(gbk_search* p, double* u, uint64_t key, uint32_t seed, void* stream) {
   if (!p || !u) return set_error(GBK_EINVAL, "gb_search_init: null argument");
-  const int n = p->d.n_bands * p->d.n_temps * p->d.n_walkers;
+  const int n = p->d.n_sets * p->d.n_bands * p->d.n_temps * p->d.n_walkers;
   k_search_init<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(u, n, seed, (uint32_t)(key & 0xffffffffu),
                                                                    (uint32_t)(key >> 32));
   return check_launch("gb_search_init");
@@ -2334,10 +2342,11 @@ extern "C" gbk_status gb_search_init(gbk_search* p, double* u, uint64_t key, uin
 
 extern "C" gbk_status gb_search_windows(gbk_search* p, const gbk_residual* residual, int32_t walker, void* stream) {
   if (!p || !residual || !residual->data) return set_error(GBK_EINVAL, "gb_search_windows: null argument");
-  if (walker < 0 || walker >= residual->n_walkers || residual->frac_bits < 40 || residual->frac_bits > 120)
-    return set_error(GBK_EINVAL, "gb_search_windows: walker %d outside the residual's %d", walker, residual->n_walkers);
+  if (walker < 0 || walker + p->d.n_sets > residual->n_walkers || residual->frac_bits < 40 || residual->frac_bits > 120)
+    return set_error(GBK_EINVAL, "gb_search_windows: walkers [%d, %d) outside the residual's %d", walker,
+                     walker + p->d.n_sets, residual->n_walkers);
   SearchArgs a = search_args(p, nullptr, nullptr, nullptr, nullptr, 0);
-  const int grid = (p->d.n_bands + kSearchWarps - 1) / kSearchWarps;
+  const int grid = (a.nbt + kSearchWarps - 1) / kSearchWarps;
   cudaStream_t st = (cudaStream_t)stream;
   const long long* r = (const long long*)residual->data;
   const int64_t nb = p->ctx->grid.n_bins;
@@ -2358,8 +2367,9 @@ extern "C" gbk_status gb_search_eval(gbk_search* p, const double* u, double* ell
                                      void* stream) {
   if (!p || !u || !ell || !psd || !psd->params) return set_error(GBK_EINVAL, "gb_search_eval: null argument");
   if (!p->have_windows) return set_error(GBK_EINVAL, "gb_search_eval: no residual windows (gb_search_windows)");
-  if (psd_walker < 0 || (psd->n_psd != 1 && psd_walker >= psd->n_psd))
-    return set_error(GBK_EINVAL, "gb_search_eval: psd_walker %d outside the PSD's %d", psd_walker, psd->n_psd);
+  if (psd_walker < 0 || (psd->n_psd != 1 && psd_walker + p->d.n_sets > psd->n_psd))
+    return set_error(GBK_EINVAL, "gb_search_eval: PSD rows [%d, %d) outside the PSD's %d", psd_walker,
+                     psd_walker + p->d.n_sets, psd->n_psd);
   SearchArgs a = search_args(p, const_cast<double*>(u), ell, nullptr, psd, psd_walker);
   cudaStream_t st = (cudaStream_t)stream;
   return p->d.precision == GBK_MIXED ? search_dispatch<float>(a, 0, 0, 0, 0, st) : search_dispatch<double>(a, 0, 0, 0, 0, st);
@@ -2370,8 +2380,9 @@ extern "C" gbk_status gb_search_sweep(gbk_search* p, double* u, double* ell, con
                                       double* best_u, int32_t* stall, int64_t* stats, void* stream) {
   if (!p || !u || !ell || !betas || !psd || !psd->params) return set_error(GBK_EINVAL, "gb_search_sweep: null argument");
   if (!p->have_windows) return set_error(GBK_EINVAL, "gb_search_sweep: no residual windows (gb_search_windows)");
-  if (psd_walker < 0 || (psd->n_psd != 1 && psd_walker >= psd->n_psd))
-    return set_error(GBK_EINVAL, "gb_search_sweep: psd_walker %d outside the PSD's %d", psd_walker, psd->n_psd);
+  if (psd_walker < 0 || (psd->n_psd != 1 && psd_walker + p->d.n_sets > psd->n_psd))
+    return set_error(GBK_EINVAL, "gb_search_sweep: PSD rows [%d, %d) outside the PSD's %d", psd_walker,
+                     psd_walker + p->d.n_sets, psd->n_psd);
   if ((best_ell || best_u || stall) && !(best_ell && best_u && stall))
     return set_error(GBK_EINVAL, "gb_search_sweep: best_ell, best_u and stall go together");
   if (p->d.stall_limit > 0 && !stall)
@@ -2386,12 +2397,12 @@ extern "C" gbk_status gb_search_sweep(gbk_search* p, double* u, double* ell, con
                                              : search_dispatch<double>(a, 1, sweep_index, k0, k1, st);
   if (s) return s;
   if (p->d.n_temps > 1) {
-    const int n = p->d.n_bands * p->d.n_walkers;
+    const int n = a.nbt * p->d.n_walkers;
     k_search_swap<<<(n + 127) / 128, 128, 0, st>>>(a, sweep_index, k0, k1);
     if ((s = check_launch("gb_search_sweep(swap)"))) return s;
   }
   if (best_ell) {
-    k_search_best<<<(p->d.n_bands + 127) / 128, 128, 0, st>>>(a, best_ell, best_u, stall);
+    k_search_best<<<(a.nbt + 127) / 128, 128, 0, st>>>(a, best_ell, best_u, stall);
     if ((s = check_launch("gb_search_sweep(best)"))) return s;
   }
   return GBK_OK;
@@ -2405,7 +2416,7 @@ extern "C" gbk_status gb_search_samples(gbk_search* p, const double* u, const do
     return set_error(GBK_EINVAL, "gb_search_samples: rows [%d, %d) outside %d", row0, row0 + p->d.n_walkers, n_rows);
   if (!(f_min < f_max)) return set_error(GBK_EINVAL, "gb_search_samples: f_min >= f_max");
   SearchArgs a = search_args(p, const_cast<double*>(u), nullptr, nullptr, nullptr, 0);
-  const int n = p->d.n_bands * p->d.n_walkers;
+  const int n = a.nbt * p->d.n_walkers;
   k_search_samples<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(a, best_ell, snr_min, f_min, f_max, x, n_rows,
                                                                        row0);
   return check_launch("gb_search_samples");
@@ -2416,8 +2427,9 @@ extern "C" gbk_status gb_search_ball(gbk_search* p, double* u, const double* bes
   if (!p || !u || !best_ell || !best_u) return set_error(GBK_EINVAL, "gb_search_ball: null argument");
   if (!(sigma > 0.0)) return set_error(GBK_EINVAL, "gb_search_ball: sigma must be > 0");
   const int per = p->d.n_temps * p->d.n_walkers;
-  const int n = p->d.n_bands * per;
-  k_search_ball<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(u, best_ell, best_u, p->d.n_bands, per, sigma, seed,
+  const int nbt = p->d.n_sets * p->d.n_bands;
+  const int n = nbt * per;
+  k_search_ball<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(u, best_ell, best_u, nbt, per, sigma, seed,
                                                                   (uint32_t)(key & 0xffffffffu), (uint32_t)(key >> 32));
   return check_launch("gb_search_ball");
 }

@@ -195,3 +195,66 @@ def test_search_fp64_with_convergence_matches_oracle():
     n_sw = sum(1 for r in trace if r["kind"] == 8)
     n_sw_acc = sum(1 for r in trace if r["kind"] == 8 and r["accepted"])
     assert st.tolist() == [[n_str, n_str_acc], [n_sw, n_sw_acc]]
+
+
+def test_search_sets_one_per_walker_match_oracle():
+    # two searches side by side in one plan (n_sets = 2), set s on walker s's residual and PSD
+    # row, with its own ladder and the convergence test: each set equals the oracle's search of
+    # that walker with the band index offset by s n_bands in the counters (FP64: walkers, best
+    # points and stall counts bit for bit, likelihoods to 1e-8, the training points)
+    torch = torch_cuda()
+    from oracle import constants as OC
+    from oracle import psd as OP
+    from paper_2405_04690_gb300 import _lib as L
+    from paper_2405_04690_gb300 import synth
+    cfg, state, dfix, s0 = small_ensemble(seed=31, n_temps=1, n_walkers=2, n_bands=3, n_max=2, n_per_band=2,
+                                          betas=(1.0,))
+    resid = state["resid"]                       # the two walkers' cold residuals differ
+    rows = np.array([[synth.SQRT_S_OMS, synth.SQRT_S_ACC], [1.15 * synth.SQRT_S_OMS, 0.9 * synth.SQRT_S_ACC]])
+    f = (cfg.k0 + np.arange(cfg.n_bins)) * OC.DF
+    ladders = [np.tile([1.0, 0.3], (3, 1)), np.tile([1.0, 0.45], (3, 1))]
+    n_sweeps, nbd = 6, 3
+    want = []
+    for st_i in range(2):
+        sc = SR.SearchConfig(tobs=cfg.tobs, k0=cfg.k0, n_bins=cfg.n_bins, band_k0=cfg.band_k0, nb=NB, n_bands=nbd,
+                             n_temps=2, n_walkers=8, betas=ladders[st_i], psd=OP.psd_ae(f, *rows[st_i]), key=KEY,
+                             stall_limit=2, band0=st_i * nbd)
+        rw = SR.windows(sc, resid[st_i], FRAC)
+        u = SR.init(sc, SEED)
+        ell = SR.evaluate(sc, rw, u)
+        best, bu, stall = np.full(nbd, -np.inf), np.zeros((nbd, 8)), np.zeros(nbd, dtype=np.int64)
+        for k in range(n_sweeps):
+            SR.search_sweep(sc, rw, u, ell, k, best, bu, stall)
+        want.append((u, ell, best, bu, stall, SR.samples(sc, u, best, SNR_MIN, F_MIN, F_MAX).astype(np.float32)))
+    dev = torch.device("cuda")
+    ctx = L.Context(cfg.tobs, 15.0, cfg.k0, cfg.n_bins)
+    plan = L.SearchPlan(ctx, nbd, NB, cfg.band_k0, 2, 8, L.GBK_FP64, stall_limit=2, n_sets=2)
+    R = torch.from_numpy(np.ascontiguousarray(resid)).to(dev)
+    PS = L.psd_struct(torch.from_numpy(rows).to(dev))
+    u = torch.empty((2, nbd, 2, 8, 8), dtype=torch.float64, device=dev)
+    ell = torch.empty((2, nbd, 2, 8), dtype=torch.float64, device=dev)
+    key = KEY[0] | (KEY[1] << 32)
+    L.gb_search_init(plan, u, key, SEED)
+    L.gb_search_windows(plan, L.residual_struct(R, FRAC), 0)
+    L.gb_search_eval(plan, u, ell, PS)
+    betas = torch.from_numpy(np.ascontiguousarray(np.stack(ladders))).to(dev)
+    be = torch.full((2, nbd), -np.inf, dtype=torch.float64, device=dev)
+    bu = torch.zeros((2, nbd, 8), dtype=torch.float64, device=dev)
+    stall = torch.zeros((2, nbd), dtype=torch.int32, device=dev)
+    for k in range(n_sweeps):
+        L.gb_search_sweep(plan, u, ell, betas, PS, key, k, best=(be, bu, stall))
+    x = torch.full((2, nbd, 8, 8), 7.0, dtype=torch.float32, device=dev)
+    L.gb_search_samples(plan, u, be, SNR_MIN, F_MIN, F_MAX, x, 0)
+    L.gbk_sync_status(ctx)
+    ug, lg, bg, bug, sg, xg = (t.cpu().numpy() for t in (u, ell, be, bu, stall, x))
+    for st_i in range(2):
+        wu, wl, wb, wbu, ws, wx = want[st_i]
+        scale = np.abs(wl).max(axis=(1, 2))[:, None, None]
+        assert np.array_equal(ug[st_i], wu), st_i
+        assert (np.abs(lg[st_i] - wl) <= 1e-8 * scale).all(), st_i
+        assert np.array_equal(bug[st_i], wbu) and np.array_equal(sg[st_i], ws), st_i
+        assert (np.abs(bg[st_i] - wb) <= 1e-8 * scale[:, 0, 0]).all(), st_i
+        np.testing.assert_allclose(xg[st_i], wx, rtol=1e-7, atol=0)
+    assert not np.array_equal(ug[0], ug[1])
+    plan.close()
+    ctx.close()

@@ -177,3 +177,43 @@ def test_converged_bands_are_left_as_they_are():
     # flat bands: best at sweep 0, stall 1 after sweep 1, 2 after sweep 2: converged from sweep 3
     assert SR.converged(cfg, stall)[:1] == [0] and 2 in SR.converged(cfg, stall)
     assert stall[0] == 2 and stall[2] == 2
+
+
+def test_band_offset_shifts_only_the_random_streams():
+    # a search among several side by side (band0 = i n_bands) is the same search as bands
+    # n_bands .. 2 n_bands - 1 of one search over twice the bands: same geometry, same counters,
+    # so the same walkers, likelihoods, decisions and best points; band0 = 0 gives other moves
+    nb = 2
+    cen = [np.array([0.3, 0.6, 0.5, 0.4, 0.5, 0.55, 0.45, 0.5]) + 0.05 * b for b in range(2 * nb)]
+
+    def g(b, x):
+        return -0.5 * float(np.sum((x - cen[b]) ** 2)) / 0.05 ** 2
+
+    wide = _cfg(n_bands=2 * nb, key=(3, 4))
+    wide.stall_limit = 2
+    sub = _cfg(n_bands=nb, key=(3, 4))
+    sub.band_k0 = wide.band_k0 + nb * wide.nb
+    sub.k0 = wide.k0
+    sub.band0 = nb
+    sub.stall_limit = 2
+    zero = _cfg(n_bands=nb, key=(3, 4))
+    zero.band_k0 = sub.band_k0
+    zero.k0 = wide.k0
+    u_w, u_s, u_z = SR.init(wide, 5), SR.init(sub, 5), SR.init(zero, 5)
+    assert np.array_equal(u_w[nb:], u_s) and not np.array_equal(u_s, u_z)
+    l_w = SR.evaluate(wide, None, u_w, g)
+    l_s = SR.evaluate(sub, None, u_s, lambda b, x: g(b + nb, x))
+    bw = (np.full(2 * nb, -np.inf), np.zeros((2 * nb, 8)), np.zeros(2 * nb, dtype=np.int64))
+    bs = (np.full(nb, -np.inf), np.zeros((nb, 8)), np.zeros(nb, dtype=np.int64))
+    tw, ts = [], []
+    for k in range(6):
+        SR.search_sweep(wide, None, u_w, l_w, k, *bw, fn=g, trace=tw)
+        SR.search_sweep(sub, None, u_s, l_s, k, *bs, fn=lambda b, x: g(b + nb, x), trace=ts)
+    assert np.array_equal(u_w[nb:], u_s) and np.array_equal(l_w[nb:], l_s)
+    assert np.array_equal(bw[0][nb:], bs[0]) and np.array_equal(bw[1][nb:], bs[1]) and np.array_equal(bw[2][nb:], bs[2])
+    keep = [dict(r, b=r["b"] - nb) for r in tw if r["b"] >= nb]
+    assert [(r["kind"], r["b"], r["t"], r["w"], r["accepted"]) for r in keep] == \
+        [(r["kind"], r["b"], r["t"], r["w"], r["accepted"]) for r in ts]
+    SR.ball(wide, u_w, bw[0], bw[1], 0.01, 9)
+    SR.ball(sub, u_s, bs[0], bs[1], 0.01, 9)
+    assert np.array_equal(u_w[nb:], u_s)
