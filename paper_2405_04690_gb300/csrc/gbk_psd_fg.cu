@@ -20,18 +20,28 @@
 namespace gbk {
 
 constexpr int kFgThreads = 256;
-constexpr int kFgChunk = 4096;
+constexpr int kFgChunk = 8192;
 constexpr int kFgEntries = 4;   // PSD walkers per block (share one residual load when they share a residual)
 constexpr int kPsdDim = 9;
 
 size_t total_loglike_scratch_bytes(int64_t n_bins);
 
+// The walker constants that scale every bin's terms are kept as float pairs (hi = the constant
+// rounded to float32, lo = the remainder) and applied as one rounded product x hi + x lo: the
+// rounding of a constant would be the same relative error in every bin, ~6e-8 x 2^20 bins = a
+// bias of ~0.1 nats in ln L; the product's own rounding is unbiased.
 struct FgEntry {
-  float iso_a, iso_e;   // 2^-64 / S_oms per channel (keeps the q-terms of both channels in one sum)
-  float aw_a, aw_e;     // S_acc / S_oms per channel
-  float k_a, k_e;       // A_fg / S_oms per channel (x 2^0: g and S_oms share the 2^128 scale of Q)
-  float alpha, s1l, s2l, fk;   // alpha, s1 log2(e), 2 s2 log2(e), f_k
+  float iso_a, iso_e, iso_al, iso_el;   // 2^-64 / S_oms per channel (keeps both channels' q-terms in one sum)
+  float aw_a, aw_e, aw_al, aw_el;       // S_acc / S_oms per channel
+  float k_a, k_e, k_al, k_el;           // A_fg / S_oms per channel (g and S_oms share the 2^128 scale of Q)
+  float alpha, s1l, s2l, fk;            // alpha, s1 log2(e), 2 s2 log2(e), f_k
 };
+
+__device__ __forceinline__ float mul2(float x, float hi, float lo) { return fmaf(x, hi, x * lo); }
+// u = 1 + aw rho + g k
+__device__ __forceinline__ float u_of(float awh, float awl, float kh, float kl, float rho, float g) {
+  return fmaf(g, kh, fmaf(g, kl, one_plus(awh, awl, rho)));
+}
 
 __device__ __forceinline__ float ex2a(float x) {
   float y;
@@ -48,18 +58,25 @@ __device__ __forceinline__ float lg2a(float x) {
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-// log2(1 + 2^x) without overflow
-__device__ __forceinline__ float softplus2(float x) { return fmaxf(x, 0.f) + lg2a(1.0f + ex2a(-fabsf(x))); }
+// log2(1 + 2^x) without overflow; for |x| > 25, 1 + 2^-|x| rounds to 1 and the value is
+// max(x, 0) (taken without the two special-function evaluations)
+__device__ __forceinline__ float softplus2(float x) {
+  return fabsf(x) > 25.f ? fmaxf(x, 0.f) : fmaxf(x, 0.f) + lg2a(1.0f + ex2a(-fabsf(x)));
+}
 
 __device__ __forceinline__ FgEntry fg_entry(const double* p) {
   FgEntry e;
   const double so_a = p[0] * p[0], sa_a = p[1] * p[1], so_e = p[2] * p[2], sa_e = p[3] * p[3];
-  e.iso_a = (float)(ldexp(1.0, -64) / so_a);
-  e.iso_e = (float)(ldexp(1.0, -64) / so_e);
-  e.aw_a = (float)(sa_a / so_a);
-  e.aw_e = (float)(sa_e / so_e);
-  e.k_a = (float)(p[4] / so_a);
-  e.k_e = (float)(p[4] / so_e);
+  auto pair = [](double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+  };
+  pair(ldexp(1.0, -64) / so_a, e.iso_a, e.iso_al);
+  pair(ldexp(1.0, -64) / so_e, e.iso_e, e.iso_el);
+  pair(sa_a / so_a, e.aw_a, e.aw_al);
+  pair(sa_e / so_e, e.aw_e, e.aw_el);
+  pair(p[4] / so_a, e.k_a, e.k_al);
+  pair(p[4] / so_e, e.k_e, e.k_el);
   e.alpha = (float)p[5];
   e.fk = (float)p[6];
   e.s1l = (float)(p[7] * 1.4426950408889634);
@@ -69,7 +86,8 @@ __device__ __forceinline__ FgEntry fg_entry(const double* p) {
 
 // One block: bins [chunk * kFgChunk, +kFgChunk) of entries [eg, eg + kFgEntries).
 // part[(chunk * nel + e) * 2 + {0, 1}] = sum_ch |R_ch|^2 2^64 iq / (u_ch S_oms,ch) and
-// sum (ln u_A + ln u_E); compensated float32 per thread, float64 across the block.
+// sum (ln u_A + ln u_E); compensated float32 per thread and (as float pairs) per warp, float64
+// only in the threads that add up the block.
 __global__ void __launch_bounds__(kFgThreads, 2)
 k_fg_part(const float* __restrict__ R, const float* __restrict__ iq, const float* __restrict__ rho,
           const float* __restrict__ lnf, const float* __restrict__ ff, const float* __restrict__ fgc,
@@ -93,12 +111,11 @@ k_fg_part(const float* __restrict__ R, const float* __restrict__ iq, const float
     s_r[threadIdx.x] = r;
   }
   __syncthreads();
-  FgEntry ent[kFgEntries];
+  const FgEntry* ent = s_e;   // read from shared memory where used (broadcast loads), not held in registers
   const float* rw[kFgEntries];
   bool act[kFgEntries], same[kFgEntries], gsame[kFgEntries];
 #pragma unroll
   for (int j = 0; j < kFgEntries; ++j) {
-    ent[j] = s_e[j];
     act[j] = eg + j < nel;
     rw[j] = R + (int64_t)s_r[j] * 2 * nb * 2;
     same[j] = j > 0 && s_r[j] == s_r[j - 1];   // entries of one residual read it once
@@ -122,12 +139,42 @@ k_fg_part(const float* __restrict__ R, const float* __restrict__ iq, const float
   // per-bin, per-entry terms; residual values of both channels at bin k given; the two
   // channels share one reciprocal: x / ua + y / ue = (x ue + y ua) / (ua ue)
   auto bin = [&](int j, float g, float iqk, float rhk, float ar, float ai, float er, float ei) {
-    const float ua = fmaf(ent[j].aw_a, rhk, 1.0f) + g * ent[j].k_a;
-    const float ue = fmaf(ent[j].aw_e, rhk, 1.0f) + g * ent[j].k_e;
+    const float ua = u_of(ent[j].aw_a, ent[j].aw_al, ent[j].k_a, ent[j].k_al, rhk, g);
+    const float ue = u_of(ent[j].aw_e, ent[j].aw_el, ent[j].k_e, ent[j].k_el, rhk, g);
     const float ax = ar * up, ay = ai * up, ex = er * up, ey = ei * up;
     const float uu = ua * ue;
-    sq[j].add(iqk * fmaf((ax * ax + ay * ay) * ent[j].iso_a, ue, (ex * ex + ey * ey) * ent[j].iso_e * ua) * rcpa(uu));
+    sq[j].add(iqk * fmaf(mul2(ax * ax + ay * ay, ent[j].iso_a, ent[j].iso_al), ue,
+                         mul2(ex * ex + ey * ey, ent[j].iso_e, ent[j].iso_el) * ua) * rcpa(uu));
     sl[j].add(0.6931471805599453f * lg2a(uu));
+  };
+  // two bins of one entry: one reciprocal of the product of their channel products (separate
+  // reciprocals if that product could overflow: windows at very low frequency); the logarithms
+  // stay per bin (the approximate log2 of the product added a bias of ~0.035 nats over 2^20 bins)
+  auto bin2 = [&](int j, float g0, float g1, float iq0, float iq1, float rh0, float rh1, float4 a, float4 e) {
+    const float ua0 = u_of(ent[j].aw_a, ent[j].aw_al, ent[j].k_a, ent[j].k_al, rh0, g0);
+    const float ue0 = u_of(ent[j].aw_e, ent[j].aw_el, ent[j].k_e, ent[j].k_el, rh0, g0);
+    const float ua1 = u_of(ent[j].aw_a, ent[j].aw_al, ent[j].k_a, ent[j].k_al, rh1, g1);
+    const float ue1 = u_of(ent[j].aw_e, ent[j].aw_el, ent[j].k_e, ent[j].k_el, rh1, g1);
+    const float ax0 = a.x * up, ay0 = a.y * up, ex0 = e.x * up, ey0 = e.y * up;
+    const float ax1 = a.z * up, ay1 = a.w * up, ex1 = e.z * up, ey1 = e.w * up;
+    const float uu0 = ua0 * ue0, uu1 = ua1 * ue1;
+    const float n0 = iq0 * fmaf(mul2(ax0 * ax0 + ay0 * ay0, ent[j].iso_a, ent[j].iso_al), ue0,
+                                mul2(ex0 * ex0 + ey0 * ey0, ent[j].iso_e, ent[j].iso_el) * ua0);
+    const float n1 = iq1 * fmaf(mul2(ax1 * ax1 + ay1 * ay1, ent[j].iso_a, ent[j].iso_al), ue1,
+                                mul2(ex1 * ex1 + ey1 * ey1, ent[j].iso_e, ent[j].iso_el) * ua1);
+    const float pu = uu0 * uu1;
+    if (pu < 1e37f) {
+      const float r = rcpa(pu);
+      sq[j].add(n0 * (uu1 * r));
+      sq[j].add(n1 * (uu0 * r));
+      sl[j].add(0.6931471805599453f * lg2a(uu0));
+      sl[j].add(0.6931471805599453f * lg2a(uu1));
+    } else {
+      sq[j].add(n0 * rcpa(uu0));
+      sq[j].add(n1 * rcpa(uu1));
+      sl[j].add(0.6931471805599453f * lg2a(uu0));
+      sl[j].add(0.6931471805599453f * lg2a(uu1));
+    }
   };
   const bool even = (nb & 1) == 0;
   for (int64_t k = kbeg + 2 * threadIdx.x; k < kend; k += 2 * kFgThreads) {
@@ -156,8 +203,7 @@ k_fg_part(const float* __restrict__ R, const float* __restrict__ iq, const float
           g0 = fg_g(j, lf2.x, ff2.x, c2.x);
           g1 = fg_g(j, lf2.y, ff2.y, c2.y);
         }
-        bin(j, g0, iq2.x, rh2.x, av[j].x, av[j].y, ev[j].x, ev[j].y);
-        bin(j, g1, iq2.y, rh2.y, av[j].z, av[j].w, ev[j].z, ev[j].w);
+        bin2(j, g0, g1, iq2.x, iq2.y, rh2.x, rh2.y, av[j], ev[j]);
       }
     } else {
       for (int64_t kk = k; kk < min(k + 2, kend); ++kk) {
@@ -175,11 +221,11 @@ k_fg_part(const float* __restrict__ R, const float* __restrict__ iq, const float
       }
     }
   }
-  __shared__ double red[kFgThreads / 32][kFgEntries][2];
+  __shared__ float2 red[kFgThreads / 32][kFgEntries][2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < kFgEntries; ++j) {
-    const double x0 = sq[j].warp_total(), x1 = sl[j].warp_total();
+    const float2 x0 = sq[j].warp_pair(), x1 = sl[j].warp_pair();
     if (lane == 0) { red[wid][j][0] = x0; red[wid][j][1] = x1; }
   }
   __syncthreads();
@@ -187,7 +233,7 @@ k_fg_part(const float* __restrict__ R, const float* __restrict__ iq, const float
     const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
     if (eg + j < nel) {
       double s = 0.0;
-      for (int w = 0; w < kFgThreads / 32; ++w) s += red[w][j][which];
+      for (int w = 0; w < kFgThreads / 32; ++w) s += (double)red[w][j][which].x + (double)red[w][j][which].y;
       part[((int64_t)chunk * nel + eg + j) * 2 + which] = s;
     }
   }
