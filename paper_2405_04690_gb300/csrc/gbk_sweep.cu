@@ -228,7 +228,10 @@ __device__ __forceinline__ void propose(const gbk_sweep_desc& d, const double* t
     z[c] = (float)ic * (float)(1.7320508075688772 / 16777216.0);
   }
   const double TWO_PI = 6.283185307179586, PI = 3.141592653589793;
-  nw[0] = th[0] * exp((double)((float)d.sigma[0] * z[0]));   // float64 exp: |Delta lnL| scales with A^2
+  // A' = A e^x, x = sigma_A z formed in float32 as above; e^x = 1 + expm1f(x) keeps the float64
+  // precision of A' (|expm1f error| ~1e-7 |x|, |x| ~ 0.05: |Delta lnL| scales with A^2) with
+  // one float64 fma in place of a float64 exp
+  nw[0] = fma(th[0], (double)expm1f((float)d.sigma[0] * z[0]), th[0]);
   nw[1] = th[1] + (double)((float)d.sigma[1] * z[1]);
   nw[2] = th[2] + (double)((float)d.sigma[2] * z[2]);
   nw[3] = wrap(th[3] + (double)((float)d.sigma[3] * z[3]), TWO_PI);
@@ -259,15 +262,25 @@ __device__ __forceinline__ double exp_t(double x, float) { return (double)expf((
 __device__ __forceinline__ double log_t(double x, double) { return log(x); }
 __device__ __forceinline__ double log_t(double x, float) { return (double)logf((float)x); }
 
-// Prior draw of a new source in band b from 8 words (f0 and A always in float64: the
-// likelihood of a loud source is sensitive to both at the 1e-7 level).
+// Amplitude of a prior draw, A = exp(ln A_min + (ln A_max - ln A_min) u): the float64 sweep in
+// float64; the mixed sweep as A_min (float64) times expf of the float32 offset (relative error
+// ~1e-7: a fixed map of u, which the stored parameters and the template then both follow).
+__device__ __forceinline__ double prior_amp(const gbk_sweep_desc& d, const PriorK&, double u, double) {
+  return exp(dadd(d.ln_a_min, dmul(dsub(d.ln_a_max, d.ln_a_min), u)));
+}
+__device__ __forceinline__ double prior_amp(const gbk_sweep_desc& d, const PriorK& pk, double u, float) {
+  return pk.a_min * (double)expf((float)(d.ln_a_max - d.ln_a_min) * (float)u);
+}
+
+// Prior draw of a new source in band b from 8 words (f0 always in float64: the likelihood of a
+// loud source is sensitive to it at the 1e-7 level).
 template <typename T>
-__device__ __forceinline__ void draw_birth(const gbk_sweep_desc& d, const BandGeom& bg, const uint32_t* w,
-                                           double* nw) {
+__device__ __forceinline__ void draw_birth(const gbk_sweep_desc& d, const PriorK& pk, const BandGeom& bg,
+                                           const uint32_t* w, double* nw) {
   const double TWO_PI = 6.283185307179586, PI = 3.141592653589793;
   const double f0 = dadd(bg.lo, dmul(dsub(bg.hi, bg.lo), u32(w[0])));
   nw[1] = f0;
-  nw[0] = exp(dadd(d.ln_a_min, dmul(dsub(d.ln_a_max, d.ln_a_min), u32(w[1]))));
+  nw[0] = prior_amp(d, pk, u32(w[1]), T());
   const double mc = dadd(d.mc_min, dmul(dsub(d.mc_max, d.mc_min), u32(w[2])));
   nw[2] = fdot_of(f0, mc, T());
   nw[3] = dmul(TWO_PI, u32(w[3]));
@@ -323,10 +336,10 @@ __device__ __forceinline__ void from_unit(const gbk_sweep_desc& d, const BandGeo
 
 // Draw from eps prior + (1 - eps) mixture: the prior branch is draw_birth on the same 8 words.
 template <typename T>
-__device__ __forceinline__ void mdn_draw(const SweepArgs& a, const MixRow<T>& m, const BandGeom& bg, uint32_t w_def,
-                                         uint32_t w_comp, const uint32_t* w_dims, double* nw) {
+__device__ __forceinline__ void mdn_draw(const SweepArgs& a, const PriorK& pk, const MixRow<T>& m, const BandGeom& bg,
+                                         uint32_t w_def, uint32_t w_comp, const uint32_t* w_dims, double* nw) {
   if (mix_u32(w_def) < a.mdn_eps) {
-    draw_birth<T>(a.d, bg, w_dims, nw);
+    draw_birth<T>(a.d, pk, bg, w_dims, nw);
     return;
   }
   T u[kMixDim];
@@ -899,7 +912,7 @@ __device__ __noinline__ void prep_inmodel(const SweepArgs& a, const PriorK& pk, 
   const bool grp = !indep && a.grp_f0 && a.grp_n[b] > 0 && mix_u32(w[46]) < a.grp_frac;   // group stretch
   double lnz = 0.0;
   if (indep)
-    mdn_draw<T>(a, *mrow, bg, w[36], w[37], w + 38, nw);
+    mdn_draw<T>(a, pk, *mrow, bg, w[36], w[37], w + 38, nw);
   else if (grp)
     lnz = group_stretch(a, b, th, w[1], w[2], nw);
   else
@@ -937,11 +950,11 @@ __device__ __noinline__ void prep_rj(const SweepArgs& a, const PriorK& pk, BandS
   if (!E[s]) {
     double nw[8];
     if (mrow) {
-      mdn_draw<T>(a, *mrow, bg, wv[10], wv[11], wv, nw);
+      mdn_draw<T>(a, pk, *mrow, bg, wv[10], wv[11], wv, nw);
       S.supp[l] = in_support<T>(pk, bg, nw) ? 1 : 0;
       if (S.supp[l]) S.lpn[l] = -mdn_logq<T>(a, pk, *mrow, bg, nw);
     } else {
-      draw_birth<T>(a.d, bg, wv, nw);
+      draw_birth<T>(a.d, pk, bg, wv, nw);
     }
 #pragma unroll
     for (int c = 0; c < 8; ++c) S.th[l][c] = nw[c];
