@@ -1169,6 +1169,8 @@ def run_kernel_case(args):
     total_loglike: three total_loglike calls on 64 walkers x 2 ch x 2^20 bins (1.07 GB of float32
     residual, larger than L2); dlogl_1024: three Delta lnL batches of 20,000 proposals with
     1024-bin bands (f0 log-uniform in 4-20 mHz, one walker's zero residual), mixed precision;
+    total_loglike_fg: three total_loglike_fg calls (per-channel noise + Galactic foreground, 9
+    parameters per walker) on the same 64-walker residual size;
     mdn_train: the learned proposal's network on 40,960 random pairs, batch 4096: device times
     of the forward pass, forward + backward, the Adam step and one step of a training epoch
     (printed as one JSON line, microseconds)."""
@@ -1187,6 +1189,18 @@ def run_kernel_case(args):
         out = torch.empty(w, dtype=torch.float64, device=dev)
         for _ in range(3):
             L.total_loglike(ctx, r, pp, out)
+    elif args.kernel_case == "total_loglike_fg":
+        g = synth.rng(9)
+        n, w, k0 = 1 << 20, 64, 3146
+        ctx = L.Context(TOBS, DT, k0, n)
+        p9 = np.tile(np.array([15e-12, 3e-15, 15e-12, 3e-15, 3.3e-44, 1.2, 2.8e-3, 1763.3, 1686.3]), (w, 1))
+        p9[:, :4] *= np.exp(g.uniform(-0.2, 0.2, (w, 4)))
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(9)
+        r = torch.randn((w, 2, n, 2), dtype=torch.float32, device=dev, generator=gen) * 1e-17
+        out = torch.empty(w, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            L.total_loglike_fg(ctx, r, torch.from_numpy(p9).to(dev), out)
     elif args.kernel_case == "mdn_train":
         from paper_2405_04690_gb300 import proposal as PR
         batch, n = 4096, 40960
@@ -1254,7 +1268,8 @@ def run_kernel_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel-case", choices=["total_loglike", "dlogl_1024", "mdn_train"], default=None,
+    ap.add_argument("--kernel-case", choices=["total_loglike", "total_loglike_fg", "dlogl_1024", "mdn_train"],
+                    default=None,
                     help="run one small single-kernel workload for a profiler capture and exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
