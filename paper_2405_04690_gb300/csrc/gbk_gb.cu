@@ -118,7 +118,7 @@ __device__ __forceinline__ float iq_at(const gbk_ctx& c, int64_t k, float) { ret
 __device__ __forceinline__ double iq_at(const gbk_ctx& c, int64_t k, double) { return __ldg(&c.iq_d[k]); }
 __device__ __forceinline__ float rho_at(const gbk_ctx& c, int64_t k, float) { return __ldg(&c.rho_f[k]); }
 __device__ __forceinline__ double rho_at(const gbk_ctx& c, int64_t k, double) { return __ldg(&c.rho_d[k]); }
-__device__ __forceinline__ float i2r(long long v, float) { return __ll2float_rn(v); }
+__device__ __forceinline__ float i2r(long long v, float) { return ll_to_float(v); }
 __device__ __forceinline__ double i2r(long long v, double) { return __ll2double_rn(v); }
 __device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
@@ -363,7 +363,7 @@ k_dlogl_block(const gbk_ctx c, const double* __restrict__ pnew, const double* __
 }
 
 // ---------------------------------------------------------------- residual add/sub
-__device__ __forceinline__ long long to_grid(float v, float s) { return __float2ll_rn(v * s); }
+__device__ __forceinline__ long long to_grid(float v, float s) { return float_to_ll(v * s); }
 __device__ __forceinline__ long long to_grid(double v, double s) { return __double2ll_rn(v * s); }
 
 template <typename T, int NMAX>

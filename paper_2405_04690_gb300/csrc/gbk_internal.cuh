@@ -21,6 +21,25 @@ constexpr double kLc = kLArm / kC;          // s, one-arm light time
 // below float32's normal range). Powers of two: the rescaling is exact.
 constexpr int kStrainExp = 64;
 
+// Conversions between the fixed-point residual (int64) and float32 without the 64-bit
+// conversion instructions, which run at the reduced float64 rate on this part. Values that fit
+// in 32 bits (most residual samples: |v| ~ 2^27 for a 1e-21 strain at 98 fraction bits) take one
+// 32-bit conversion, rounded exactly as the 64-bit one; larger ones split into 32-bit halves:
+// ll_to_float = RN(hi 2^32 + RN(lo)), at most one unit in the last place from the single
+// rounding (the rounding of lo moves the sum by up to 2^7). float_to_ll is exact: a float of
+// magnitude >= 2^31 is an integer, and both of its 32-bit halves are exact floats.
+__device__ __forceinline__ float ll_to_float(long long v) {
+  const int lo = (int)v;
+  if ((long long)lo == v) return (float)lo;
+  return fmaf((float)(int)(v >> 32), 4294967296.0f, (float)(unsigned)v);
+}
+__device__ __forceinline__ long long float_to_ll(float x) {
+  if (fabsf(x) < 2147483648.0f) return (long long)__float2int_rn(x);
+  const float h = floorf(x * 2.3283064365386963e-10f);   // x / 2^32, exact
+  const float l = fmaf(h, -4294967296.0f, x);            // x - h 2^32 in [0, 2^32), exact
+  return (long long)(((unsigned long long)(unsigned)(int)h << 32) | (unsigned long long)(unsigned)l);
+}
+
 // Band lengths: 128 << i for i = 0..3.
 constexpr int kNumBandSizes = 4;
 inline __host__ __device__ int band_index(int n) {

@@ -107,9 +107,9 @@ __device__ __forceinline__ const float* tab_rho(const gbk_ctx& c, float) { retur
 __device__ __forceinline__ const double* tab_rho(const gbk_ctx& c, double) { return c.rho_d; }
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
-__device__ __forceinline__ float i2t(long long v, float) { return __ll2float_rn(v); }
+__device__ __forceinline__ float i2t(long long v, float) { return ll_to_float(v); }
 __device__ __forceinline__ double i2t(long long v, double) { return __ll2double_rn(v); }
-__device__ __forceinline__ long long t2grid(float v, float s) { return __float2ll_rn(v * s); }
+__device__ __forceinline__ long long t2grid(float v, float s) { return float_to_ll(v * s); }
 __device__ __forceinline__ long long t2grid(double v, double s) { return __double2ll_rn(v * s); }
 template <typename T> struct SAcc;
 template <> struct SAcc<float> { typedef CompF S; };
