@@ -43,7 +43,8 @@ __device__ __forceinline__ bool gen_any(const gbk_ctx& c, const Src<T>* s, int n
 // constants (lane l of the warp computes the constants of batch item l in float64).
 template <typename T>
 __host__ __device__ constexpr size_t warp_bytes(int nmax, int nbuf, int nsrc) {
-  return (size_t)nbuf * 2 * nmax * sizeof(typename CT<T>::C) + (size_t)nsrc * sizeof(Src<T>) + 64 * sizeof(int);
+  return (size_t)nbuf * 2 * nmax * sizeof(typename CT<T>::C) + (size_t)nsrc * sizeof(Src<T>) + 64 * sizeof(int) +
+         32 * sizeof(double);
 }
 
 // ---------------------------------------------------------------- gb_waveform_batch
@@ -146,13 +147,11 @@ __device__ __forceinline__ void acc_bin(const gbk_ctx& c, const long long* __res
 template <typename T>
 __device__ __forceinline__ void eval_sums(const gbk_ctx& c, const typename CT<T>::C* ba, const typename CT<T>::C* br,
                                           bool za, bool zr, int64_t ka, int64_t kr, int nbi, int w,
-                                          const long long* __restrict__ resid, int32_t frac_bits,
-                                          const double* __restrict__ psdp, int32_t npsd, int lane, int jb, int je,
-                                          double& dd_out, double& rd_out) {
+                                          const long long* __restrict__ resid, int32_t frac_bits, T aw, int lane,
+                                          int jb, int je, double& dd_out, double& rd_out) {
   typedef typename CT<T>::C C;
   const int64_t nbins = c.grid.n_bins;
   const T rscale = (T)ldexp(1.0, kStrainExp - frac_bits);
-  const PsdW<T> pw = psd_walker<T>(c, psdp, npsd, w);
   const long long* rw = resid + (int64_t)w * 2 * nbins * 2;
   typename Acc<T>::S sdd, srd;
   sdd.init();
@@ -165,7 +164,7 @@ __device__ __forceinline__ void eval_sums(const gbk_ctx& c, const typename CT<T>
       C ra = zero, re = zero;
       const int64_t jr = k - kr;
       if (!zr && jr >= 0 && jr < nbi) { ra = br[jr]; re = br[nbi + jr]; }
-      acc_bin<T>(c, rw, k, csub(ba[j], ra), csub(ba[nbi + j], re), pw.aw, rscale, sdd, srd);
+      acc_bin<T>(c, rw, k, csub(ba[j], ra), csub(ba[nbi + j], re), aw, rscale, sdd, srd);
     }
   }
   // bins of r's band outside a's band: D = -r
@@ -175,7 +174,7 @@ __device__ __forceinline__ void eval_sums(const gbk_ctx& c, const typename CT<T>
       const int64_t ja = k - ka;
       if (!za && ja >= 0 && ja < nbi) continue;
       const C ra = br[j], re = br[nbi + j];
-      acc_bin<T>(c, rw, k, mkc(-ra.x, -ra.y), mkc(-re.x, -re.y), pw.aw, rscale, sdd, srd);
+      acc_bin<T>(c, rw, k, mkc(-ra.x, -ra.y), mkc(-re.x, -re.y), aw, rscale, sdd, srd);
     }
   }
   dd_out = sdd.warp_total();
@@ -186,12 +185,11 @@ __device__ __forceinline__ void eval_sums(const gbk_ctx& c, const typename CT<T>
 template <typename T>
 __device__ __forceinline__ void eval_pair(const gbk_ctx& c, const typename CT<T>::C* ba, const typename CT<T>::C* br,
                                           bool za, bool zr, int64_t ka, int64_t kr, int nbi, int w,
-                                          const long long* __restrict__ resid, int32_t frac_bits,
-                                          const double* __restrict__ psdp, int32_t npsd, int lane, double* out) {
+                                          const long long* __restrict__ resid, int32_t frac_bits, double cw, T aw,
+                                          int lane, double* out) {
   double dd, rd;
-  eval_sums<T>(c, ba, br, za, zr, ka, kr, nbi, w, resid, frac_bits, psdp, npsd, lane, 0, nbi, dd, rd);
-  const PsdW<T> pw = psd_walker<T>(c, psdp, npsd, w);
-  if (lane == 0) *out = pw.cw * (-0.5 * dd + rd);
+  eval_sums<T>(c, ba, br, za, zr, ka, kr, nbi, w, resid, frac_bits, aw, lane, 0, nbi, dd, rd);
+  if (lane == 0) *out = cw * (-0.5 * dd + rd);
 }
 
 // Batch of 16 proposals per warp: lanes 0-15 set up the new templates, 16-31 the old.
@@ -211,6 +209,8 @@ k_dlogl(const gbk_ctx c, const double* __restrict__ pnew, const double* __restri
   C* bs = br + 2 * NMAX;
   Src<T>* srcs = reinterpret_cast<Src<T>*>(bs + 2 * NMAX);   // [0,16) new, [16,32) old
   int* meta = reinterpret_cast<int*>(srcs + 32);            // [0,16) N, [16,32) walker
+  double* s_cw = reinterpret_cast<double*>(meta + 64);       // [16] PSD weights of the batch's walkers
+  T* s_aw = reinterpret_cast<T*>(s_cw + 16);                 // [16]
   const int wpc = blockDim.x >> 5;
   const int64_t stride_w = (int64_t)gridDim.x * wpc * 16;
   const int64_t nbins = c.grid.n_bins;
@@ -220,7 +220,16 @@ k_dlogl(const gbk_ctx c, const double* __restrict__ pnew, const double* __restri
       const int64_t me = base + l;
       if (me < n) {
         const int nbi = nb[me];
-        if (lane < 16) { meta[l] = nbi; meta[16 + l] = walker[me]; }
+        if (lane < 16) {
+          const int w = walker[me];
+          meta[l] = nbi;
+          meta[16 + l] = w;
+          if (w >= 0 && w < n_walkers && (npsd == 1 || w < npsd)) {   // once per proposal, lane-parallel
+            const PsdW<T> pw = psd_walker<T>(c, psdp, npsd, w);
+            s_cw[l] = pw.cw;
+            s_aw[l] = pw.aw;
+          }
+        }
         if (nbi <= NMAX && band_index(nbi) >= 0)
           srcs[lane] = make_src<T>(lane < 16 ? pnew : pold, n, me, c.grid.tobs, nbi);
       }
@@ -253,7 +262,7 @@ k_dlogl(const gbk_ctx c, const double* __restrict__ pnew, const double* __restri
       }
       if (!za) gen_any<T, NMAX>(c, sa, nbi, ba, bs, lane);
       if (!zr) gen_any<T, NMAX>(c, sr, nbi, br, bs, lane);
-      eval_pair<T>(c, ba, br, za, zr, ka, kr, nbi, w, resid, frac_bits, psdp, npsd, lane, dlogl + i);
+      eval_pair<T>(c, ba, br, za, zr, ka, kr, nbi, w, resid, frac_bits, s_cw[q], s_aw[q], lane, dlogl + i);
       __syncwarp();
     }
     __syncwarp();
@@ -345,16 +354,16 @@ k_dlogl_block(const gbk_ctx c, const double* __restrict__ pnew, const double* __
       if (wid < ne) {
         const int jb = wid * (nbi / ne);
         double dd, rd;
-        eval_sums<T>(c, ba, br, za, zr, ka, kr, nbi, w, resid, frac_bits, psdp, npsd, lane, jb, jb + nbi / ne, dd,
-                     rd);
+        // the PSD weight per warp (from a per-batch table, as in k_dlogl, this kernel ran 8 % slower)
+        eval_sums<T>(c, ba, br, za, zr, ka, kr, nbi, w, resid, frac_bits, psd_walker<T>(c, psdp, npsd, w).aw, lane, jb,
+                     jb + nbi / ne, dd, rd);
         if (lane == 0) { part[wid][0] = dd; part[wid][1] = rd; }
       }
       __syncthreads();
       if (tid == 0) {
         double dd = part[0][0], rd = part[0][1];
         for (int v = 1; v < ne; ++v) { dd += part[v][0]; rd += part[v][1]; }
-        const PsdW<T> pw = psd_walker<T>(c, psdp, npsd, w);
-        dlogl[i] = pw.cw * (-0.5 * dd + rd);
+        dlogl[i] = psd_walker<T>(c, psdp, npsd, w).cw * (-0.5 * dd + rd);
       }
       __syncthreads();   // the buffers are reused by the next proposal
     }
