@@ -194,3 +194,21 @@ def test_mixed_sweep_with_gpu_fitted_mixture_table_matches_oracle():
     prop = dict(raw_table=torch.from_numpy(table.astype(np.float32)).cuda(), eps=0.2, inmodel_frac=0.35)
     _, gtr, _ = _gpu_sweep(torch, cfg, state, "mixed", proposal=prop)
     _check(_replay_first_half(cfg, state, gtr, trace), {"indep", "gauss", "birth", "death"})
+
+
+def test_mixed_sweep_repeats_bit_for_bit():
+    # band tasks are taken from a counter, so which warp runs which band differs from run to run;
+    # every result (parameters, occupancy, fixed-point residuals, move counts, the decision trace)
+    # must not: two runs of three mixed sweeps from the same state are identical bit for bit
+    torch = torch_cuda()
+    cfg, state, _, _ = small_ensemble(seed=23, n_temps=3, n_walkers=3, n_bands=6, n_max=4)
+    runs = [_gpu_sweep(torch, cfg, copy_state(state), "mixed", sweeps=3) for _ in range(2)]
+    (a, ta, sa), (b, tb, sb) = runs
+    for k in ("params", "exists", "resid"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(sa, sb)
+    assert len(ta) == len(tb) > 0
+    def records(tr):   # the trace as a multiset of raw records (its order follows the warps' task order)
+        return sorted(r.tobytes() for r in tr)
+
+    assert records(ta) == records(tb)
