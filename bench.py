@@ -37,14 +37,29 @@ WORKLOAD = ("batched ensemble: 16 temps x 32 walkers x 2000 GBs (1-4 mHz, N=256,
             "full sweep (in-model 1/source + flip-all RJ + PT swaps), mixed precision")
 
 # Algorithmic float32 work (counted from the operations of the method):
-# slow-part response 621 flops per coarse sample, band FFT 5 N log2 N per channel,
-# Delta lnL 45 flops per band bin.
+# slow-part response 621 flops per coarse sample, 509 for a source whose series arguments
+# stay within 0.25 rad (2 pi f_max L/c <= 0.25, f below 4.77 mHz: the generator then cuts
+# its 14 Taylor series short), band FFT 5 N log2 N per channel, Delta lnL 45 flops per band bin.
 FLOPS_SLOW_PER_SAMPLE = 621
+FLOPS_SLOW_PER_SAMPLE_SHORT = 509
+SHORT_SERIES_ARG = 0.25
+L_OVER_C = 2.5e9 / 299792458.0
 FLOPS_PER_BIN = 45
 
 
-def flops_per_waveform(n=N_BAND):
-    return n * FLOPS_SLOW_PER_SAMPLE + 2 * 5 * n * int(math.log2(n))
+def short_series(f_max):
+    """True where the generator takes the shorter series (f_max: the largest |f| of the source)."""
+    return 2.0 * math.pi * f_max * L_OVER_C <= SHORT_SERIES_ARG
+
+
+def f_max_of(p):
+    """Largest |f| of each source ([8][n] parameters) over the observation."""
+    return np.maximum(np.abs(p[1]), np.abs(p[1] + p[2] * TOBS))
+
+
+def flops_per_waveform(n=N_BAND, short=False):
+    per = FLOPS_SLOW_PER_SAMPLE_SHORT if short else FLOPS_SLOW_PER_SAMPLE
+    return n * per + 2 * 5 * n * int(math.log2(n))
 
 
 def flops_per_evaluation(n=N_BAND):
@@ -295,7 +310,13 @@ def run_uneven(torch, L, dev, stream, seed, n_prop=200000, reps=10):
                      "old": torch.from_numpy(np.ascontiguousarray(p[:, idx])).to(dev),
                      "nb": torch.full((m,), n, dtype=torch.int32, device=dev),
                      "w": torch.zeros(m, dtype=torch.int32, device=dev),
-                     "out": torch.empty(m, dtype=torch.float64, device=dev), "m": m}
+                     "out": torch.empty(m, dtype=torch.float64, device=dev), "m": m,
+                     # per proposal: both waveforms (each with its own series length) and one
+                     # evaluation of N bins
+                     "flops": sum(n_short * flops_per_waveform(n, True) + (m - n_short) * flops_per_waveform(n)
+                                  for n_short in (int(short_series(f_max_of(new[:, idx])).sum()),
+                                                  int(short_series(f_max_of(p[:, idx])).sum())))
+                              + m * n * FLOPS_PER_BIN}
     per_n = {}
     for n, G in groups.items():
         best = L.gbk_autotune_dlogl(ctx, G["new"], G["old"], G["nb"], n, G["w"], R, P, G["out"], L.GBK_MIXED, stream)
@@ -308,7 +329,8 @@ def run_uneven(torch, L, dev, stream, seed, n_prop=200000, reps=10):
         ms = e0.elapsed_time(e1) / reps
         per_n[str(n)] = {"proposals": G["m"], "proposals_per_s": G["m"] / (ms * 1e-3),
                          "waveforms_per_s": 2 * G["m"] / (ms * 1e-3), "tuned_warps_per_cta": best[0],
-                         "tuned_ctas_per_sm": best[1] or "max"}
+                         "tuned_ctas_per_sm": best[1] or "max",
+                         "fp32_frac": G["flops"] / (ms * 1e-3) / 1e12 / PEAK_FP32_TFLOPS}
     graph = torch.cuda.CUDAGraph()
     cap = torch.cuda.Stream()
     cap.wait_stream(torch.cuda.current_stream())
@@ -812,7 +834,13 @@ def run_ours(args):
     # roofline of the band kernel (in-model + RJ): algorithmic flops / its device time
     wf, ev = float(st[4, 0]), float(st[4, 1])
     band_ms = kms[2] / args.steps
-    fl_step = (wf * flops_per_waveform() + ev * flops_per_evaluation()) / args.steps
+    # the short-series count where any source can take it: exact when every source does (this
+    # ensemble: its band allowances end half a band above the last band, ~4.0 mHz, and the
+    # chirp-mass prior's fdot adds < 1e-7 Hz over T), a lower bound otherwise
+    f_top = (ens["band_k0"] + (ens["n_bands"] + 0.5) * N_BAND) / TOBS + 1e-7
+    fl_wf = flops_per_waveform(N_BAND, short=short_series(F_LO))
+    fl_note = "exact" if short_series(f_top) else "lower bound (sources on both sides of the short-series limit)"
+    fl_step = (wf * fl_wf + ev * flops_per_evaluation()) / args.steps
     ach = fl_step / (band_ms * 1e-3) / 1e12
 
     # end to end through the C ABI with host buffers: the sampler state goes in from pinned
@@ -1101,7 +1129,8 @@ def run_ours(args):
                                      "(traffic scales with the band tasks)",
                      "kernel": "k_band<float,256> (in-model + flip-all RJ)",
                      "peak_note": "FP32 ALU: 152 SMs x 128 lanes x 2 (FMA) x 2.07 GHz (derived, not measured)",
-                     "flops_per_waveform": flops_per_waveform(), "flops_per_evaluation": flops_per_evaluation()},
+                     "flops_per_waveform": fl_wf, "flops_per_evaluation": flops_per_evaluation(),
+                     "flops_count": fl_note},
         "waveforms_per_s": wf / args.steps / (ms_step * 1e-3),
         "e2e": {"value": e2e_props / (e2e_ms * 1e-3), "unit": "proposals/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

@@ -632,7 +632,8 @@ __device__ __forceinline__ void copy_band(C* dst, const C* src, int n2, int lane
 }
 
 // H(t, w, b) <- sum of the band's present cached templates on its window, summed in slot
-// order (deterministic), written to global memory.
+// order (deterministic), written to global memory. Templates and sums pass through once
+// (evict-first loads and stores).
 template <typename T, int N>
 __device__ __noinline__ void write_hsum(const SweepArgs& a, int t, int w, int b, int lane) {
   typedef typename CT<T>::C C;
@@ -665,16 +666,16 @@ __device__ __noinline__ void write_hsum(const SweepArgs& a, int t, int w, int b,
         for (int u = 0; u < G; ++u) {
           const int j = i0 + 32 * u - o;
           if (j >= 0 && j < N) {
-            xa[u] = cadd(xa[u], h[j]);
-            xe[u] = cadd(xe[u], h[N + j]);
+            xa[u] = cadd(xa[u], __ldcs(h + j));
+            xe[u] = cadd(xe[u], __ldcs(h + N + j));
           }
         }
       }
     }
 #pragma unroll
     for (int u = 0; u < G; ++u) {
-      H[i0 + 32 * u] = xa[u];
-      H[W3 + i0 + 32 * u] = xe[u];
+      __stcs(H + i0 + 32 * u, xa[u]);
+      __stcs(H + W3 + i0 + 32 * u, xe[u]);
     }
   }
   __syncwarp();
@@ -1010,13 +1011,14 @@ __global__ void __launch_bounds__(kBandWarps * 32, kBandMinCtas) k_band(const Sw
     const BandGeom bg = band_geom(d, tobs, b);
     long long* Rw = a.resid + (int64_t)w * 2 * nb * 2;
     // r' for the band: cold chain from the snapshot; hotter chains from the opened window
-    // minus their own (cached) templates
+    // minus their own (cached) templates. These inputs are read once per task: evict-first
+    // loads keep L1 for the window, the templates and the tables the proposals reuse.
     if (cold) {
       const long long* rs_w = a.rsnap + (int64_t)w * 2 * nb * 2;
 #pragma unroll 4
       for (int i = lane; i < W3; i += 32)
         for (int ch = 0; ch < 2; ++ch) {
-          const longlong2 v = *reinterpret_cast<const longlong2*>(rs_w + 2 * (ch * nb + gw + i));
+          const longlong2 v = __ldcs(reinterpret_cast<const longlong2*>(rs_w + 2 * (ch * nb + gw + i)));
           rw[ch * W3 + i] = mkc(i2t(v.x, T()) * rs, i2t(v.y, T()) * rs);
         }
       __syncwarp();
@@ -1024,7 +1026,7 @@ __global__ void __launch_bounds__(kBandWarps * 32, kBandMinCtas) k_band(const Sw
       const C* rho = rho_ptr<T>(a, w, j);
       const C* H = hsum_ptr<T>(a, t, w, b);
 #pragma unroll 4
-      for (int i = lane; i < 2 * W3; i += 32) rw[i] = csub(rho[i], H[i]);
+      for (int i = lane; i < 2 * W3; i += 32) rw[i] = csub(__ldcs(rho + i), __ldcs(H + i));
       __syncwarp();
     }
     // ---- in-model proposals (Alg. 1)

@@ -99,6 +99,23 @@ __device__ __forceinline__ double2 expi_small(double x) {
   sincos(x, &s, &c);
   return make_double2(c, s);
 }
+// The same for |x| <= kLoArg = 0.25 rad, the series cut after x^7 (sin) and x^8 (cos):
+// the first dropped terms are below 5e-11 relative. float64 keeps sincos.
+constexpr double kLoArg = 0.25;
+__device__ __forceinline__ float2 expi_small_lo(float x) {
+  const float z = x * x;
+  float sp = 1.0f / 5040.0f;
+  sp = sp * -z + 1.0f / 120.0f;
+  sp = sp * -z + 1.0f / 6.0f;
+  sp = sp * -z + 1.0f;
+  float cp = 1.0f / 40320.0f;
+  cp = cp * -z + 1.0f / 720.0f;
+  cp = cp * -z + 1.0f / 24.0f;
+  cp = cp * -z + 0.5f;
+  cp = cp * -z + 1.0f;
+  return make_float2(cp, x * sp);
+}
+__device__ __forceinline__ double2 expi_small_lo(double x) { return expi_small(x); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ void fma_err(float a, float b, float p, float& e) { e = fmaf(a, b, -p); }
@@ -140,6 +157,23 @@ __device__ __forceinline__ double sincpi_poly(double s) {
   p = p * z + 1.0;
   return p;
 }
+// sin(pi s) / (pi s) for |pi s| <= kLoArg, cut after (pi s)^6 (first dropped term < 5e-11).
+__device__ __forceinline__ float sincpi_poly_lo(float s) {
+  float x = 3.14159265358979f * s;
+  float z = x * x;
+  float p = -1.0f / 5040.0f;
+  p = p * z + 1.0f / 120.0f;
+  p = p * z - 1.0f / 6.0f;
+  p = p * z + 1.0f;
+  return p;
+}
+__device__ __forceinline__ double sincpi_poly_lo(double s) { return sincpi_poly(s); }
+template <bool LO, typename T> __device__ __forceinline__ typename CT<T>::C expi_sm(T x) {
+  return LO ? expi_small_lo(x) : expi_small(x);
+}
+template <bool LO, typename T> __device__ __forceinline__ T sincpi_sm(T s) {
+  return LO ? sincpi_poly_lo(s) : sincpi_poly(s);
+}
 
 // Per-source constants, computed in float64 and rounded once. Phases are in cycles.
 // Every phase coefficient that multiplies an O(1) quantity is split into a float hi
@@ -160,6 +194,7 @@ struct Src {
   T c2p, s2p;      // cos 2psi, sin 2psi
   T hp, hc;        // A (1 + cos^2 i) S, 2 A cos i S with S = 2^64 (T / 2N) pi L / c
   bool zero;       // amplitude exactly zero
+  bool lo;         // every series argument of the slow part within kLoArg (float path)
 };
 
 template <typename T> __device__ __forceinline__ void split(double x, T& hi, T& lo) {
@@ -216,6 +251,9 @@ __device__ __noinline__ Src<T> make_src(const double* __restrict__ prm, int64_t 
   s.hp = (T)(amp * (1.0 + cosi * cosi) * scale);
   s.hc = (T)(2.0 * amp * cosi * scale);
   s.zero = (amp == 0.0);
+  // the slow part's largest series argument is 2 pi |f| L/c (the sinc of the amplitude and
+  // the links; the arm and craft-offset phases are smaller), f over the observation
+  s.lo = 6.283185307179586 * fmax(fabs(f0), fabs(f0 + fdot * tobs)) * kLc <= kLoArg;
   return s;
 }
 
@@ -268,7 +306,7 @@ __device__ __forceinline__ void stage_r2_first(const C* __restrict__ in, C* __re
 
 // Slow-part sample p of one source (band FFT input of the A and E channels): the TDI response
 // at the coarse time t_p = p T / N times the heterodyned carrier.
-template <typename T, int N>
+template <typename T, int N, bool LO>
 __device__ __forceinline__ void slow_sample(const Src<T>& src, const T* __restrict__ orb, int p, T dtp, T inv_n,
                                             typename CT<T>::C& outA, typename CT<T>::C& outE) {
   typedef typename CT<T>::C C;
@@ -291,14 +329,14 @@ __device__ __forceinline__ void slow_sample(const Src<T>& src, const T* __restri
   const T pif = (T)3.14159265358979323846 * flc;
   // exponentials with small arguments: E0 = e^{-i pi f L/c}, Ea = e^{i pi f L/c k.n_a},
   // Ej = e^{-2 pi i f k.dx_j / c}; D = E0^2
-  const C e0 = expi_small(-pif);
+  const C e0 = expi_sm<LO>(-pif);
   C ea[3], ej[3];
   T kn[3];
   C nhn[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const T kd = src.kx * dx[c][0] + src.ky * dx[c][1] + src.kz * dx[c][2];
-    ej[c] = expi_small((T)-6.28318530717958647692 * f * kd);
+    ej[c] = expi_sm<LO>((T)-6.28318530717958647692 * f * kd);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -308,7 +346,7 @@ __device__ __forceinline__ void slow_sample(const Src<T>& src, const T* __restri
     const T xp = un * un - vn * vn;
     const T xc = (T)2 * un * vn;
     nhn[a] = mkc(src.hp * (src.c2p * xp - src.s2p * xc), src.hc * (src.s2p * xp + src.c2p * xc));
-    ea[a] = expi_small(pif * kn[a]);
+    ea[a] = expi_sm<LO>(pif * kn[a]);
   }
   // link i->j (arm a, direction sign sg, receiver j), common factor E0 removed:
   //   y_ij = n.Hc.n sinc(pi f L/c (1 - sg k.n_a)) Ea^sg Ej
@@ -320,7 +358,7 @@ __device__ __forceinline__ void slow_sample(const Src<T>& src, const T* __restri
   for (int l = 0; l < 6; ++l) {
     const bool plus = (l & 1) == 0;
     const T sarg = flc * ((T)1 - (plus ? kn[arm[l]] : -kn[arm[l]]));
-    const T sc = sincpi_poly(sarg);
+    const T sc = sincpi_sm<LO>(sarg);
     const C ph = cmul(plus ? ea[arm[l]] : cconj(ea[arm[l]]), ej[rcv[l]]);
     y[l] = cmul(mkc(nhn[arm[l]].x * sc, nhn[arm[l]].y * sc), ph);
   }
@@ -357,7 +395,7 @@ __device__ __forceinline__ void slow_sample(const Src<T>& src, const T* __restri
   const T small = (src.dlo * pn + src.phl) + (q1e + src.fdl * pn2) - dop_l
                   - tp * (src.fkx * cah + src.fky * sah) - (T)1.5 * flc;
   const C car = expi_cycles(big + small);
-  const T amp = (T)2 * f * ((T)6.28318530717958647692 * flc) * sincpi_poly((T)2 * flc);
+  const T amp = (T)2 * f * ((T)6.28318530717958647692 * flc) * sincpi_sm<LO>((T)2 * flc);
   const C com = cscale(car, amp);
   outA = cmul(com, As);
   outE = cmul(com, Es);
@@ -423,12 +461,22 @@ __device__ __noinline__ void gen_band(const Src<T>* __restrict__ srcp, const T* 
   const T inv_n = (T)1 / (T)N;
   // The per-sample body is long; unrolling the sample loop multiplies the code that
   // every warp must fetch (GBK_SAMPLE_UNROLL, chosen by measurement).
+  if (sizeof(T) == 4 && src.lo) {   // the shorter series (one branch per warp: one source)
 #pragma unroll (kSampleUnroll)
-  for (int p = lane; p < N; p += 32) {
-    C sa, se;
-    slow_sample<T, N>(src, orb, p, dtp, inv_n, sa, se);
-    buf0[p] = sa;
-    buf0[N + p] = se;
+    for (int p = lane; p < N; p += 32) {
+      C sa, se;
+      slow_sample<T, N, true>(src, orb, p, dtp, inv_n, sa, se);
+      buf0[p] = sa;
+      buf0[N + p] = se;
+    }
+  } else {
+#pragma unroll (kSampleUnroll)
+    for (int p = lane; p < N; p += 32) {
+      C sa, se;
+      slow_sample<T, N, false>(src, orb, p, dtp, inv_n, sa, se);
+      buf0[p] = sa;
+      buf0[N + p] = se;
+    }
   }
   __syncwarp();
   band_fft<C, N, 32>(buf0, buf1, tw, lane, WarpSync());
@@ -447,12 +495,22 @@ __device__ __noinline__ void gen_band_block(const Src<T>* __restrict__ srcp, con
   const T inv_n = (T)1 / (T)N;
   // two samples per thread at a time (a CTA has registers to spare here: -1.4 % at N = 1024);
   // each sample's arithmetic is the warp generator's, so both give the same bits
+  if (sizeof(T) == 4 && src.lo) {
 #pragma unroll 2
-  for (int p = tid; p < N; p += NT) {
-    C sa, se;
-    slow_sample<T, N>(src, orb, p, dtp, inv_n, sa, se);
-    buf0[p] = sa;
-    buf0[N + p] = se;
+    for (int p = tid; p < N; p += NT) {
+      C sa, se;
+      slow_sample<T, N, true>(src, orb, p, dtp, inv_n, sa, se);
+      buf0[p] = sa;
+      buf0[N + p] = se;
+    }
+  } else {
+#pragma unroll 2
+    for (int p = tid; p < N; p += NT) {
+      C sa, se;
+      slow_sample<T, N, false>(src, orb, p, dtp, inv_n, sa, se);
+      buf0[p] = sa;
+      buf0[N + p] = se;
+    }
   }
   __syncthreads();
   band_fft<C, N, NT>(buf0, buf1, tw, tid, BlockSync());

@@ -80,6 +80,30 @@ def test_waveform_ragged_band_lengths(prec):
         assert rel_l2(got, np.concatenate([a, e])) < WF_TOL[prec]
 
 
+def test_waveform_on_both_sides_of_the_short_series_limit():
+    # The float generator evaluates shorter series for sources whose largest series argument
+    # 2 pi f_max L/c is at most 0.25 rad (f below 4.77 mHz over the observation); sources just
+    # below and just above that frequency match the oracle alike, and neither side is worse.
+    torch = torch_cuda()
+    from paper_2405_04690_gb300 import _lib as L
+    g = synth.rng(7)
+    p = synth.draw_sources(g, 48, 4.55e-3, 5.0e-3)
+    f_max = np.maximum(np.abs(p[1]), np.abs(p[1] + p[2] * OC.TOBS))
+    short = 2.0 * np.pi * f_max * OC.L_ARM / OC.C_LIGHT <= 0.25
+    assert 8 <= short.sum() <= 40
+    nb = np.full(48, 512)
+    k0, n = window(4.5e-3, 5.05e-3, 700)
+    ctx = _ctx(L, k0, n)
+    ks, ha, he, off = _run_waveforms(torch, L, ctx, p, nb, "mixed")
+    err = np.empty(48)
+    for i in range(48):
+        k, a, e = OW.fastslow_band(p[:, i], 512)
+        assert ks[i] == k
+        err[i] = rel_l2(np.concatenate([ha[off[i]:off[i] + 512], he[off[i]:off[i] + 512]]), np.concatenate([a, e]))
+    assert err.max() < WF_TOL["mixed"], err.max()
+    assert np.median(err[short]) < 2.0 * np.median(err[~short]), (np.median(err[short]), np.median(err[~short]))
+
+
 def test_waveform_invariants_on_gpu():
     # (a) A = 0 gives exact zeros; (b) phi0 + pi negates the band.
     torch = torch_cuda()
