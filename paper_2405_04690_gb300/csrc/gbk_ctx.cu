@@ -110,6 +110,7 @@ extern "C" gbk_status gbk_destroy(gbk_ctx* ctx) {
   cudaFree(ctx->psd_p);
   cudaFree(ctx->iq_f);
   cudaFree(ctx->rho_f);
+  cudaFree(ctx->iqrho_f);
   cudaFree(ctx->iq_d);
   cudaFree(ctx->rho_d);
   cudaFree(ctx->fg_lnf);
@@ -163,6 +164,7 @@ extern "C" gbk_status gbk_create(gbk_ctx** out_ctx, const gbk_grid* grid) {
   const int64_t nb = grid->n_bins;
   std::vector<double> q(nb), pa(nb), iq(nb), rho(nb);
   std::vector<float> iqf(nb), rhof(nb), lnff(nb), ff(nb), fgc(nb);
+  std::vector<float2> iqrf(nb);
   double s = 0.0, comp = 0.0;  // compensated sum of ln Q
   for (int64_t i = 0; i < nb; ++i) {
     const double f = (double)(grid->k0 + i) / grid->tobs;
@@ -171,6 +173,7 @@ extern "C" gbk_status gbk_create(gbk_ctx** out_ctx, const gbk_grid* grid) {
     iq[i] = ldexp(1.0 / q[i], -2 * kStrainExp);
     iqf[i] = (float)iq[i];
     rhof[i] = (float)rho[i];
+    iqrf[i] = make_float2(iqf[i], rhof[i]);
     const double x = 2.0 * M_PI * f * kLc, sx = sin(x);
     lnff[i] = (float)log2(f);
     ff[i] = (float)f;
@@ -187,6 +190,7 @@ extern "C" gbk_status gbk_create(gbk_ctx** out_ctx, const gbk_grid* grid) {
   if (e == cudaSuccess) e = upload(&c->rho_d, rho.data(), nb * sizeof(double));
   if (e == cudaSuccess) e = upload(&c->iq_f, iqf.data(), nb * sizeof(float));
   if (e == cudaSuccess) e = upload(&c->rho_f, rhof.data(), nb * sizeof(float));
+  if (e == cudaSuccess) e = upload(&c->iqrho_f, iqrf.data(), nb * sizeof(float2));
   if (e == cudaSuccess) e = upload(&c->fg_lnf, lnff.data(), nb * sizeof(float));
   if (e == cudaSuccess) e = upload(&c->fg_f, ff.data(), nb * sizeof(float));
   if (e == cudaSuccess) e = upload(&c->fg_c, fgc.data(), nb * sizeof(float));

@@ -74,6 +74,7 @@ struct gbk_ctx {
   double* psd_p;
   float* iq_f;
   float* rho_f;
+  float2* iqrho_f;     // (iq, rho) per bin, float32, for loads of both at once
   double* iq_d;
   double* rho_d;
   double sum_lnq;      // sum_k ln Q_k over the window, float64

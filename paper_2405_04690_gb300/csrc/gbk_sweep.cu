@@ -19,7 +19,7 @@ struct gbk_sweep {
   void* wcache;         // current waveform of every slot [T][W][B][n_max][2][N]
   void* hsum;           // sum of the present templates of every band on its window [T][W][B][2][3N]
   int32_t* setid;       // cache block of band (t, w, b) [T][W][B]; tempering swaps exchange ids
-  void* rwbuf;          // band windows of the band kernel's warps [SMs x 64][2][3N]
+  void* rwbuf;          // band windows of the band kernel's warps [SMs x 64][3N][2]
   size_t rwbuf_bytes;
   size_t rho_bytes, cache_bytes, hsum_bytes;
   cudaEvent_t ev[2][4][2];  // [parity][refresh, open, band, swap][begin, end] when timing
@@ -77,7 +77,7 @@ struct SweepArgs {
   int32_t trace_cap;
   int32_t* trace_count;
   long long* stats;
-  // band windows r' of the band kernel's warps (global, L1-cached): [warps][2][3N]
+  // band windows r' of the band kernel's warps (global, L1-cached): [warps][3N][2]
   void* rwbuf;
   // learned proposal: mixture row of every opened (walker, band) or NULL
   const void* mix;
@@ -517,11 +517,32 @@ __device__ __forceinline__ int cached_off(const double* th, int64_t gw, const gb
   return band_off<N>((long long)floor(th[1] * c.grid.tobs), gw, c);
 }
 
-// Delta lnL of swapping template r (br, window offset orr) for a (ba, offset oa) against
-// the window residual rw ([2][3N]); either may be absent. Window bin i is grid bin gw + i.
 __device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
-template <typename T, int N>
+// The band kernel's window keeps both channels of a bin together ([3N][A, E]) and the PSD
+// tables' (iq, rho) pairs are read together: per evaluated bin one 16-byte window load and one
+// 8-byte table load in float32 where there were four loads (band kernel -5 %: its evaluations
+// wait on load latency). The search sampler's windows, read by 128 chains each, keep [2][3N]
+// with separate table loads: interleaved, its sweep took 16 % longer; so did the swap kernel's
+// pass with the paired table loads (+9 %).
+__device__ __forceinline__ void ld_win(const float2* p, float2& x, float2& y) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  x = make_float2(v.x, v.y);
+  y = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void ld_win(const double2* p, double2& x, double2& y) { x = p[0]; y = p[1]; }
+__device__ __forceinline__ void st_win(float2* p, float2 x, float2 y) {
+  *reinterpret_cast<float4*>(p) = make_float4(x.x, x.y, y.x, y.y);
+}
+__device__ __forceinline__ void st_win(double2* p, double2 x, double2 y) { p[0] = x; p[1] = y; }
+// (iq, rho) of bin k: one 8-byte load in float32
+__device__ __forceinline__ float2 iqrho(const gbk_ctx& c, int64_t k, float) { return __ldg(&c.iqrho_f[k]); }
+__device__ __forceinline__ double2 iqrho(const gbk_ctx& c, int64_t k, double) { return make_double2(__ldg(&c.iq_d[k]), __ldg(&c.rho_d[k])); }
+
+// Delta lnL of swapping template r (br, window offset orr) for a (ba, offset oa) against
+// the window residual rw: [3N][2] if IL (the band kernel's window), [2][3N] otherwise; either
+// template may be absent. Window bin i is grid bin gw + i.
+template <typename T, int N, bool IL>
 __device__ __noinline__ double window_dll(const SweepArgs& a, const typename CT<T>::C* rw, const typename CT<T>::C* ba, int oa,
                              const typename CT<T>::C* br, int orr, int64_t gw, const PsdWt<T>& pw, int lane) {
   typedef typename CT<T>::C C;
@@ -533,16 +554,33 @@ __device__ __noinline__ double window_dll(const SweepArgs& a, const typename CT<
       // loads then meet L1 instead of L2 in the latency-bound loops below
     const int o0 = ba ? oa : orr;
     constexpr int kPer = 128 / (int)sizeof(C);          // complex bins per 128-byte line
-    const int nl = (N + kPer - 1) / kPer + 1;           // lines of N bins (unaligned start)
-    for (int i = lane; i < 2 * nl; i += 32) {
-      const int ch = i / nl, li = i % nl;
-      const int idx = (o0 & ~(kPer - 1)) + li * kPer;      // stays inside this warp's window
-      if (idx < W3) prefetch_l1(rw + ch * W3 + idx);
+    if (IL) {   // N bins of both channels: 2N complex values from bin o0 on
+      const int nl = (2 * N + kPer - 1) / kPer + 1;
+      for (int i = lane; i < nl; i += 32) {
+        const int idx = ((2 * o0) & ~(kPer - 1)) + i * kPer;
+        if (idx < 2 * W3) prefetch_l1(rw + idx);
+      }
+    } else {
+      const int nl = (N + kPer - 1) / kPer + 1;           // lines of N bins (unaligned start)
+      for (int i = lane; i < 2 * nl; i += 32) {
+        const int ch = i / nl, li = i % nl;
+        const int idx = (o0 & ~(kPer - 1)) + li * kPer;      // stays inside this warp's window
+        if (idx < W3) prefetch_l1(rw + ch * W3 + idx);
+      }
     }
     constexpr int nt = N / kPer;                          // lines of one channel of a template
     if (br)
       for (int i = lane; i < 2 * nt; i += 32) prefetch_l1(br + i * kPer);
-    {   // PSD-table lines of the evaluated bins
+    if (IL && sizeof(T) == 4) {   // lines of the (iq, rho) pairs of the evaluated bins
+      constexpr int kT = 128 / 8;
+      const int64_t k0 = (gw + o0) & ~(int64_t)(kT - 1);
+      constexpr int nq = N / kT + 1;
+      const int64_t kend = a.c.grid.n_bins;
+      for (int i = lane; i < nq; i += 32) {
+        const int64_t k = k0 + (int64_t)kT * i;
+        if (k < kend) prefetch_l1(a.c.iqrho_f + k);
+      }
+    } else {   // PSD-table lines of the evaluated bins
       constexpr int kT = 128 / (int)sizeof(T);           // table entries per line
       const int64_t k0 = (gw + o0) & ~(int64_t)(kT - 1);
       constexpr int nq = N / kT + 1;
@@ -557,8 +595,20 @@ __device__ __noinline__ double window_dll(const SweepArgs& a, const typename CT<
   }
   auto bin = [&](int i, C da, C de) {
     const int64_t k = gw + i;
-    const T wt = iqv(a.c, k, T()) * recip((T)1 + pw.aw * rhov(a.c, k, T()));
-    const C ra = rw[i], re = rw[W3 + i];
+    T wt;
+    if (IL) {
+      const C q = iqrho(a.c, k, T());
+      wt = q.x * recip((T)1 + pw.aw * q.y);
+    } else {
+      wt = iqv(a.c, k, T()) * recip((T)1 + pw.aw * rhov(a.c, k, T()));
+    }
+    C ra, re;
+    if (IL) {
+      ld_win(rw + 2 * i, ra, re);
+    } else {
+      ra = rw[i];
+      re = rw[W3 + i];
+    }
     sdd.add(wt * (da.x * da.x + da.y * da.y + de.x * de.x + de.y * de.y));
     srd.add(wt * (ra.x * da.x + ra.y * da.y + re.x * de.x + re.y * de.y));
   };
@@ -590,19 +640,21 @@ template <typename T, int N>
 __device__ __noinline__ void apply_change(const SweepArgs& a, typename CT<T>::C* rw, const typename CT<T>::C* ba, int oa,
                              const typename CT<T>::C* br, int orr, bool cold, long long* rglob, int64_t gw, T gs,
                              int lane) {
-  constexpr int W3 = 3 * N;
+  typedef typename CT<T>::C C;
   const int64_t nb = a.c.grid.n_bins;
   if (ba) {
     for (int j = lane; j < N; j += 32) {
-      rw[oa + j] = csub(rw[oa + j], ba[j]);
-      rw[W3 + oa + j] = csub(rw[W3 + oa + j], ba[N + j]);
+      C x, y;
+      ld_win(rw + 2 * (oa + j), x, y);
+      st_win(rw + 2 * (oa + j), csub(x, ba[j]), csub(y, ba[N + j]));
     }
     __syncwarp();
   }
   if (br) {
     for (int j = lane; j < N; j += 32) {
-      rw[orr + j] = cadd(rw[orr + j], br[j]);
-      rw[W3 + orr + j] = cadd(rw[W3 + orr + j], br[N + j]);
+      C x, y;
+      ld_win(rw + 2 * (orr + j), x, y);
+      st_win(rw + 2 * (orr + j), cadd(x, br[j]), cadd(y, br[N + j]));
     }
     __syncwarp();
   }
@@ -1017,17 +1069,18 @@ __global__ void __launch_bounds__(kBandWarps * 32, kBandMinCtas) k_band(const Sw
     if (cold) {
       const long long* rs_w = a.rsnap + (int64_t)w * 2 * nb * 2;
 #pragma unroll 4
-      for (int i = lane; i < W3; i += 32)
-        for (int ch = 0; ch < 2; ++ch) {
-          const longlong2 v = __ldcs(reinterpret_cast<const longlong2*>(rs_w + 2 * (ch * nb + gw + i)));
-          rw[ch * W3 + i] = mkc(i2t(v.x, T()) * rs, i2t(v.y, T()) * rs);
-        }
+      for (int i = lane; i < W3; i += 32) {
+        const longlong2 va = __ldcs(reinterpret_cast<const longlong2*>(rs_w + 2 * (gw + i)));
+        const longlong2 ve = __ldcs(reinterpret_cast<const longlong2*>(rs_w + 2 * (nb + gw + i)));
+        st_win(rw + 2 * i, mkc(i2t(va.x, T()) * rs, i2t(va.y, T()) * rs), mkc(i2t(ve.x, T()) * rs, i2t(ve.y, T()) * rs));
+      }
       __syncwarp();
     } else {
       const C* rho = rho_ptr<T>(a, w, j);
       const C* H = hsum_ptr<T>(a, t, w, b);
 #pragma unroll 4
-      for (int i = lane; i < 2 * W3; i += 32) rw[i] = csub(__ldcs(rho + i), __ldcs(H + i));
+      for (int i = lane; i < W3; i += 32)
+        st_win(rw + 2 * i, csub(__ldcs(rho + i), __ldcs(H + i)), csub(__ldcs(rho + W3 + i), __ldcs(H + W3 + i)));
       __syncwarp();
     }
     // ---- in-model proposals (Alg. 1)
@@ -1056,7 +1109,7 @@ __global__ void __launch_bounds__(kBandWarps * 32, kBandMinCtas) k_band(const Sw
           const C* hr = cache_ptr<T>(a, cb + k);
           const int oa = band_off<N>(S.src[q].q, gw, a.c);
           const int orr = cached_off<N>(P + k * 8, gw, a.c);
-          const double dll = window_dll<T, N>(a, rw, S.ba, oa, hr, orr, gw, pw, lane);
+          const double dll = window_dll<T, N, true>(a, rw, S.ba, oa, hr, orr, gw, pw, lane);
           const double la = beta * dll + S.lpn[q];
           const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
           if (lane == 0) record(a, ws, 0, t, w, b, k, jp, acc, dll, la, S.th[q], 1, 1);
@@ -1102,7 +1155,7 @@ __global__ void __launch_bounds__(kBandWarps * 32, kBandMinCtas) k_band(const Sw
           if (E[s]) {
             const C* hr = cache_ptr<T>(a, cb + s);
             const int orr = cached_off<N>(P + s * 8, gw, a.c);
-            const double dll = window_dll<T, N>(a, rw, (const C*)nullptr, 0, hr, orr, gw, pw, lane);
+            const double dll = window_dll<T, N, true>(a, rw, (const C*)nullptr, 0, hr, orr, gw, pw, lane);
             const double la = beta * dll - d.log_occ_odds + S.lpn[q];
             const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
             if (lane == 0) record(a, ws, 2, t, w, b, s, jp, acc, dll, la, P + s * 8, 0, 1);
@@ -1116,7 +1169,7 @@ __global__ void __launch_bounds__(kBandWarps * 32, kBandMinCtas) k_band(const Sw
           } else {
             gen_band<T, N>(&S.src[q], orb, tw, tobs, S.ba, S.bs, lane);
             const int oa = band_off<N>(S.src[q].q, gw, a.c);
-            const double dll = window_dll<T, N>(a, rw, S.ba, oa, (const C*)nullptr, 0, gw, pw, lane);
+            const double dll = window_dll<T, N, true>(a, rw, S.ba, oa, (const C*)nullptr, 0, gw, pw, lane);
             const double la = beta * dll + d.log_occ_odds + S.lpn[q];
             const bool acc = __shfl_sync(0xffffffffu, (int)(S.lu[q] < la), 0) != 0;
             if (lane == 0) record(a, ws, 1, t, w, b, s, jp, acc, dll, la, S.th[q], 1, 1);
@@ -2013,7 +2066,7 @@ __device__ double search_ell(const SearchArgs& a, SearchSmem<T, N>& S, int q, in
   const int64_t gw = a.d.band_k0 + (int64_t)(b - 1) * N - a.sa.c.grid.k0;
   const int oa = band_off<N>(S.src[q].q, gw, a.sa.c);
   const PsdWt<T> pw = walker_psd<T>(a.sa, a.psd_walker + (a.sa.npsd > 1 ? fb / a.d.n_bands : 0));
-  const double l = window_dll<T, N>(a.sa, search_window<T, N>(a, fb), S.ba, oa, (const typename CT<T>::C*)nullptr, 0,
+  const double l = window_dll<T, N, false>(a.sa, search_window<T, N>(a, fb), S.ba, oa, (const typename CT<T>::C*)nullptr, 0,
                                     gw, pw, lane);
   __syncwarp();
   return l;
