@@ -37,11 +37,12 @@ WORKLOAD = ("batched ensemble: 16 temps x 32 walkers x 2000 GBs (1-4 mHz, N=256,
             "full sweep (in-model 1/source + flip-all RJ + PT swaps), mixed precision")
 
 # Algorithmic float32 work (counted from the operations of the method):
-# slow-part response 621 flops per coarse sample, 509 for a source whose series arguments
-# stay within 0.25 rad (2 pi f_max L/c <= 0.25, f below 4.77 mHz: the generator then cuts
-# its 14 Taylor series short), band FFT 5 N log2 N per channel, Delta lnL 45 flops per band bin.
+# slow-part response 621 flops per coarse sample, 477 for a source with 2 pi f_max L/c <= 0.25
+# (f below 4.77 mHz: the generator then cuts its Taylor series short and forms each link
+# phase from its summed argument), band FFT 5 N log2 N per channel, Delta lnL 45 flops per
+# band bin.
 FLOPS_SLOW_PER_SAMPLE = 621
-FLOPS_SLOW_PER_SAMPLE_SHORT = 509
+FLOPS_SLOW_PER_SAMPLE_SHORT = 477
 SHORT_SERIES_ARG = 0.25
 L_OVER_C = 2.5e9 / 299792458.0
 FLOPS_PER_BIN = 45

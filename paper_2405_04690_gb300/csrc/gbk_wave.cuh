@@ -99,8 +99,10 @@ __device__ __forceinline__ double2 expi_small(double x) {
   sincos(x, &s, &c);
   return make_double2(c, s);
 }
-// The same for |x| <= kLoArg = 0.25 rad, the series cut after x^7 (sin) and x^8 (cos):
-// the first dropped terms are below 5e-11 relative. float64 keeps sincos.
+// The same for sources whose series arguments are small (the shorter-series path, see
+// Src::lo): the series cut after x^7 (sin) and x^8 (cos). Its largest argument there is a link
+// phase, (1/2 + 1/sqrt3) x kLoArg = 0.27 rad, where the first dropped terms are below 1e-10
+// relative. float64 keeps sincos.
 constexpr double kLoArg = 0.25;
 __device__ __forceinline__ float2 expi_small_lo(float x) {
   const float z = x * x;
@@ -121,6 +123,8 @@ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -
 __device__ __forceinline__ void fma_err(float a, float b, float p, float& e) { e = fmaf(a, b, -p); }
 __device__ __forceinline__ void fma_err(double a, double b, double p, double& e) { e = fma(a, b, -p); }
 
+__device__ __forceinline__ float fmaf_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaf_(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float rint_(float x) { return rintf(x); }
 __device__ __forceinline__ double rint_(double x) { return rint(x); }
 __device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
@@ -251,8 +255,9 @@ __device__ __noinline__ Src<T> make_src(const double* __restrict__ prm, int64_t 
   s.hp = (T)(amp * (1.0 + cosi * cosi) * scale);
   s.hc = (T)(2.0 * amp * cosi * scale);
   s.zero = (amp == 0.0);
-  // the slow part's largest series argument is 2 pi |f| L/c (the sinc of the amplitude and
-  // the links; the arm and craft-offset phases are smaller), f over the observation
+  // x = 2 pi |f| L/c over the observation bounds the slow part's series arguments: the sincs'
+  // pi s and the doubled arm delay reach x, a link phase pi f L/c k.n +- 2 pi f k.dx/c
+  // (craft offsets |dx| = L/sqrt3) (1/2 + 1/sqrt3) x
   s.lo = 6.283185307179586 * fmax(fabs(f0), fabs(f0 + fdot * tobs)) * kLc <= kLoArg;
   return s;
 }
@@ -329,14 +334,14 @@ __device__ __forceinline__ void slow_sample(const Src<T>& src, const T* __restri
   const T pif = (T)3.14159265358979323846 * flc;
   // exponentials with small arguments: E0 = e^{-i pi f L/c}, Ea = e^{i pi f L/c k.n_a},
   // Ej = e^{-2 pi i f k.dx_j / c}; D = E0^2
-  const C e0 = expi_sm<LO>(-pif);
   C ea[3], ej[3];
-  T kn[3];
+  T kn[3], jd[3];
   C nhn[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const T kd = src.kx * dx[c][0] + src.ky * dx[c][1] + src.kz * dx[c][2];
-    ej[c] = expi_sm<LO>((T)-6.28318530717958647692 * f * kd);
+    jd[c] = (T)-6.28318530717958647692 * f * kd;
+    if (!LO) ej[c] = expi_sm<LO>(jd[c]);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -346,7 +351,7 @@ __device__ __forceinline__ void slow_sample(const Src<T>& src, const T* __restri
     const T xp = un * un - vn * vn;
     const T xc = (T)2 * un * vn;
     nhn[a] = mkc(src.hp * (src.c2p * xp - src.s2p * xc), src.hc * (src.s2p * xp + src.c2p * xc));
-    ea[a] = expi_sm<LO>(pif * kn[a]);
+    if (!LO) ea[a] = expi_sm<LO>(pif * kn[a]);
   }
   // link i->j (arm a, direction sign sg, receiver j), common factor E0 removed:
   //   y_ij = n.Hc.n sinc(pi f L/c (1 - sg k.n_a)) Ea^sg Ej
@@ -359,11 +364,14 @@ __device__ __forceinline__ void slow_sample(const Src<T>& src, const T* __restri
     const bool plus = (l & 1) == 0;
     const T sarg = flc * ((T)1 - (plus ? kn[arm[l]] : -kn[arm[l]]));
     const T sc = sincpi_sm<LO>(sarg);
-    const C ph = cmul(plus ? ea[arm[l]] : cconj(ea[arm[l]]), ej[rcv[l]]);
+    // shorter series: the link phase from its summed argument (one series instead of two and
+    // a complex product)
+    const C ph = LO ? expi_sm<LO>(fmaf_(pif, plus ? kn[arm[l]] : -kn[arm[l]], jd[rcv[l]]))
+                    : cmul(plus ? ea[arm[l]] : cconj(ea[arm[l]]), ej[rcv[l]]);
     y[l] = cmul(mkc(nhn[arm[l]].x * sc, nhn[arm[l]].y * sc), ph);
   }
   // y index: 0=12 1=21 2=23 3=32 4=31 5=13
-  const C dd = cmul(e0, e0);
+  const C dd = LO ? expi_sm<LO>((T)-2 * pif) : [&] { const C e0 = expi_sm<LO>(-pif); return cmul(e0, e0); }();
   const C X = cadd(csub(y[4], y[1]), cmul(dd, csub(y[5], y[0])));
   const C Y = cadd(csub(y[0], y[3]), cmul(dd, csub(y[1], y[2])));
   const C Z = cadd(csub(y[2], y[5]), cmul(dd, csub(y[3], y[4])));
