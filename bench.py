@@ -68,7 +68,7 @@ def flops_per_evaluation(n=N_BAND):
 
 
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
-K_BAND_TRAFFIC = 8 * (1154.761e6 + 755.134e6)   # DRAM bytes per band-kernel launch (ncu, scaled)
+K_BAND_TRAFFIC = 8 * (1156.076e6 + 761.686e6)   # DRAM bytes per band-kernel launch (ncu, scaled)
 
 
 def measured_hbm_gbs():
@@ -1126,7 +1126,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": ach, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
                      "frac": ach / PEAK_FP32_TFLOPS, "traffic": K_BAND_TRAFFIC,
                      "traffic_note": "bytes per launch: ncu dram read + write of one k_band launch on the "
-                                     "2-temperature ensemble (1.910 GB) x 8 for the 16-temperature launch "
+                                     "2-temperature ensemble (1.918 GB) x 8 for the 16-temperature launch "
                                      "(traffic scales with the band tasks)",
                      "kernel": "k_band<float,256> (in-model + flip-all RJ)",
                      "peak_note": "FP32 ALU: 152 SMs x 128 lanes x 2 (FMA) x 2.07 GHz (derived, not measured)",
