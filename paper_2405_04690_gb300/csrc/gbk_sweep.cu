@@ -1369,7 +1369,7 @@ static int sweep_warps(size_t per_warp, int max_warps) {
 
 template <typename K>
 static gbk_status prep(K kernel, size_t per_warp, int64_t items, int* grid, int* threads, size_t* smem,
-                       int max_warps = kSwWarps) {
+                       int max_warps = kSwWarps, int64_t* resident_warps = nullptr) {
   const int wpc = sweep_warps(per_warp, max_warps);
   *threads = wpc * 32;
   *smem = per_warp * wpc;
@@ -1385,6 +1385,7 @@ static gbk_status prep(K kernel, size_t per_warp, int64_t items, int* grid, int*
   const int64_t need = (items + wpc - 1) / wpc;
   const int64_t cap = (int64_t)sms_of_device() * per_sm;
   *grid = (int)(need < cap ? (need > 0 ? need : 1) : cap);
+  if (resident_warps) *resident_warps = cap * wpc;
   return GBK_OK;
 }
 
@@ -2301,9 +2302,13 @@ __global__ void k_search_samples(const SearchArgs a, const double* __restrict__ 
   o[1] = (float)__ddiv_rn(dsub(f0, alo), dsub(ahi, alo));
 }
 
-// chains per warp batch: enough warps for ~12 per SM, at most 32 (one lane each), at least 4
-static int search_batch(int64_t n) {
-  const int64_t per = n / ((int64_t)sms_of_device() * 12);
+// chains per warp batch: the fewest that let one wave of the resident warps take all n chains,
+// at most 32 (one lane each), at least 4. (Sized for ~12 warps per SM and rounded down, the
+// bench's 23,616 chains per half made 1968 batches for 1824 resident warps: two waves, and the
+// sweep took 32 % longer.)
+static int search_batch(int64_t n, int64_t resident_warps) {
+  const int64_t slots = resident_warps > 0 ? resident_warps : 1;
+  const int64_t per = (n + slots - 1) / slots;
   return per < 4 ? 4 : (per > 32 ? 32 : (int)per);
 }
 
@@ -2314,16 +2319,19 @@ static gbk_status search_launch(SearchArgs& a, int what, uint32_t sweep, uint32_
   int grid = 0, thr = 0;
   size_t sm = 0;
   gbk_status s;
+  int64_t slots = 0;
   if (what == 0) {
     const int64_t n = (int64_t)a.nbt * a.d.n_temps * a.d.n_walkers;
-    const int bs = search_batch(n);
+    if ((s = prep(k_search_eval<T, N>, sizeof(SearchSmem<T, N>), 1, &grid, &thr, &sm, kSearchWarps, &slots))) return s;
+    const int bs = search_batch(n, slots);
     if ((s = prep(k_search_eval<T, N>, sizeof(SearchSmem<T, N>), (n + bs - 1) / bs, &grid, &thr, &sm, kSearchWarps)))
       return s;
     k_search_eval<T, N><<<grid, thr, sm, st>>>(a, bs);
     return check_launch("gb_search_eval");
   }
   const int64_t n = (int64_t)a.nbt * a.d.n_temps * (a.d.n_walkers / 2);
-  const int bs = search_batch(n);
+  if ((s = prep(k_search_half<T, N>, sizeof(SearchSmem<T, N>), 1, &grid, &thr, &sm, kSearchWarps, &slots))) return s;
+  const int bs = search_batch(n, slots);
   if ((s = prep(k_search_half<T, N>, sizeof(SearchSmem<T, N>), (n + bs - 1) / bs, &grid, &thr, &sm, kSearchWarps)))
     return s;
   for (int h = 0; h < 2; ++h) {
