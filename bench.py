@@ -959,6 +959,11 @@ def run_ours(args):
                            "ms_per_sweep": ms_sw, "walker_updates_per_s": T9 * W9 / (ms_sw * 1e-3),
                            "GB/s": sweep_bytes / (ms_sw * 1e-3) / 1e9,
                            "frac": sweep_bytes / (ms_sw * 1e-3) / 1e9 / peak,
+                           # each half evaluates T x W/2 proposals over every bin; the four
+                           # temperatures of a walker share its residual read, so the sweep is
+                           # bound by the per-entry arithmetic (compare the foreground pass's rate)
+                           "entry_bins_per_s": 2 * T9 * (W9 // 2) * (1 << 20) / (ms_sw * 1e-3),
+                           "foreground_pass_entry_bins_per_s": w3 * (1 << 20) / (ms9 * 1e-3),
                            "stretch_acceptance": float(s9[0, 1]) / max(1.0, float(s9[0, 0])),
                            "swap_acceptance": float(s9[1, 1]) / max(1.0, float(s9[1, 0]))}
         plan9.close()
