@@ -87,15 +87,23 @@ class Trainer:
         self.loss = torch.zeros(1, dtype=torch.float64, device=params.device)
         L.mdn_set_params(net, params)
 
-    def epoch(self, buf, batch, seed, max_steps=None):
-        """One pass over the buffer in a seeded random order (the gathers and Adam steps run
-        in one library call); returns the last minibatch loss."""
+    @staticmethod
+    def order(buf, batch, seed, max_steps=None):
+        """The seeded random order of one epoch over the buffer (whole minibatches), on the device."""
         g = np.random.Generator(np.random.PCG64(seed))
         steps = buf.n // batch if max_steps is None else min(buf.n // batch, max_steps)
-        order = torch.from_numpy(g.permutation(buf.n)[:steps * batch].astype(np.int32)).to(buf.x.device)
+        return torch.from_numpy(g.permutation(buf.n)[:steps * batch].astype(np.int32)).to(buf.x.device)
+
+    def epoch_ordered(self, buf, order, batch):
+        """One epoch in a given order (from order()): the gathers and Adam steps run in one
+        library call, stream-ordered, without waiting for the device."""
         L.mdn_train_epoch(self.net, self.p, self.m, self.v, buf.x[:buf.n], buf.u[:buf.n], order, batch, self.step,
                           self.lr, self.loss)
-        self.step += steps
+        self.step += order.numel() // batch
+
+    def epoch(self, buf, batch, seed, max_steps=None):
+        """One pass over the buffer in a seeded random order; returns the last minibatch loss."""
+        self.epoch_ordered(buf, self.order(buf, batch, seed, max_steps), batch)
         return float(self.loss.item())
 
     def mean_loss(self, buf, batch=4096, limit=None):
